@@ -1,0 +1,223 @@
+/*
+ * ifac.h -- C ABI of the GB300 (sm_103a) inverse-factorization library.
+ *
+ * Computes Z with Z^T S Z = I (so S^-1 = Z Z^T) for a block-sparse symmetric
+ * positive definite S, following Artemov, Rudberg, Rubensson, "Parallelization
+ * and scalability analysis of inverse factorization using the Chunks and
+ * Tasks programming model" (arXiv:1901.07993): iterative refinement from a
+ * scaled identity (Section 2.2, Eq. 2.1) and localized inverse factorization
+ * (Section 2.3, Algorithm 2), both driven by block-sparse products with
+ * norm-based block truncation (Section 5).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are square, n x n, stored as ifac_bsr: nb = ceil(n/bs) block
+ *    rows and columns of bs x bs blocks, CSR order of blocks, columns strictly
+ *    increasing within a block row, each block row-major, FP64.  Rows and
+ *    columns past n (padding of the last block) must hold a unit diagonal; the
+ *    library treats the padded matrix as the one to factor, and the padding
+ *    part of Z is the identity.
+ *  - Every pointer inside an ifac_bsr is DEVICE memory of the context's
+ *    device.  Inputs are borrowed: they must stay valid and unmodified until
+ *    the call returns.  Outputs (ifac_bsr* out parameters) are allocated by the
+ *    library through the context's allocator; the caller owns them and
+ *    releases them with ifac_bsr_free.
+ *  - All work is issued on the context's stream.  Calls that produce a
+ *    matrix synchronise that stream (output sizes are data dependent); scalar
+ *    results are valid on return.
+ *  - Return codes: 0 = success; > 0 = success with a warning (results valid);
+ *    < 0 = error, outputs left empty (all pointers NULL).  No C++ exception
+ *    crosses this boundary.  ifac_last_error() gives a message for the last
+ *    non-zero code on that context.
+ *  - A context must not be used from two host threads at once.
+ */
+#ifndef IFAC_H
+#define IFAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- */
+/* Status codes                                                      */
+/* ---------------------------------------------------------------- */
+#define IFAC_OK 0
+#define IFAC_WARN_TARGET_NOT_MET 1  /* stopped by the automatic rule above the target */
+#define IFAC_ERR_INVALID (-1)       /* malformed BSR or argument */
+#define IFAC_ERR_NOT_SPD (-2)       /* a leaf pivot was not positive */
+#define IFAC_ERR_NO_CONVERGENCE (-3)/* max_iter reached */
+#define IFAC_ERR_OOM (-4)           /* allocator returned NULL */
+#define IFAC_ERR_CUDA (-5)          /* a CUDA call failed */
+#define IFAC_ERR_UNSUPPORTED (-7)   /* block size / precision not built */
+
+/* Product precision (the arithmetic of the block products). */
+#define IFAC_FP64 0
+
+/* Stop reasons reported by the refinement drivers. */
+#define IFAC_STOP_RULE 1     /* ||delta_{i+1}||_F > ||delta_i||_F^(m+1) (Section 2.2) */
+#define IFAC_STOP_TARGET 2   /* ||delta||_F <= target */
+#define IFAC_STOP_MAXITER 3  /* max_iter sweeps done */
+#define IFAC_STOP_FIXED 4    /* fixed_iters corrections done */
+
+typedef struct {
+  int64_t n;        /* logical dimension */
+  int32_t bs;       /* block size */
+  int32_t nb;       /* block rows = block columns = ceil(n / bs) */
+  int64_t nnzb;     /* number of stored blocks */
+  int32_t* row_ptr; /* device [nb + 1], row_ptr[0] = 0, row_ptr[nb] = nnzb */
+  int32_t* col_idx; /* device [nnzb] */
+  double* val;      /* device [nnzb * bs * bs] */
+  double* norms;    /* device [nnzb] block Frobenius norms, or NULL (inputs);
+                       always filled on library outputs */
+} ifac_bsr;
+
+/* Device memory provider.  alloc returns NULL on failure; both are called
+ * with the context's stream.  Pass NULL to ifac_create to use the device's
+ * stream-ordered pool (cudaMallocAsync / cudaFreeAsync). */
+typedef struct {
+  void* (*alloc)(void* user, size_t bytes, void* stream);
+  void (*free)(void* user, void* ptr, void* stream);
+  void* user;
+} ifac_allocator;
+
+typedef struct ifac_ctx ifac_ctx;
+
+/* Options of the factorization drivers.  ifac_opts_default fills:
+ * m = 2, max_iter = 50, fixed_iters = 0, c_rule = 0, leaf_size = 512,
+ * prec = IFAC_FP64, profile = 0. */
+typedef struct {
+  int m;           /* refinement order: Z_{i+1} = Z_i sum_{k=0}^{m} b_k delta_i^k,
+                      b_0 = 1, b_k = (2k-1)/(2k) b_{k-1} (Eq. 2.1); 1..8 */
+  int max_iter;    /* cap on sweeps of one refinement */
+  int fixed_iters; /* inv_factor_refine only: > 0 runs exactly this many
+                      corrections and ignores the stop rule and target */
+  int c_rule;      /* inv_factor_refine start Z_0 = c I with beta the
+                      Gershgorin bound of S (Section 2.2):
+                      0 -> c = 1/sqrt(beta), 1 -> c = sqrt(2/beta) */
+  int leaf_size;   /* inv_factor_localized: sub-problems with more rows are
+                      split at the block-aligned midpoint (Algorithm 2) */
+  int prec;        /* IFAC_FP64 */
+  int profile;     /* != 0: time every numeric block-product launch with CUDA
+                      events on the context's stream (fills gemm_ms) */
+} ifac_opts;
+
+typedef struct {
+  int sweeps;          /* corrections applied (localized: summed over sub-problems) */
+  int stop_reason;     /* IFAC_STOP_* of the (top-level) refinement */
+  int levels;          /* localized: depth of the bisection tree */
+  int n_delta;         /* entries used in delta_fro */
+  double beta;         /* refine: Gershgorin bound of the truncated S */
+  double delta_fro[64];/* refine: ||delta_i||_F per evaluation;
+                          localized: top level, per sweep */
+  int64_t products;    /* block-sparse products performed */
+  int64_t block_pairs; /* stored-block pairs multiplied, over all products */
+  int64_t nnzb_Z;      /* stored blocks of the returned Z */
+  double flops;        /* 2 bs^3 block_pairs */
+  int64_t launches;    /* kernels this call launched */
+  int64_t gemm_launches; /* numeric block-product launches */
+  double gemm_ms;      /* their summed device time (opts.profile != 0) */
+} ifac_report;
+
+/* ---------------------------------------------------------------- */
+/* Context                                                           */
+/* ---------------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL
+ * = legacy default stream).  alloc: NULL for the built-in pool, else copied. */
+int ifac_create(ifac_ctx** ctx, void* stream, const ifac_allocator* alloc);
+void ifac_destroy(ifac_ctx* ctx);
+int ifac_set_stream(ifac_ctx* ctx, void* stream);
+const char* ifac_last_error(const ifac_ctx* ctx);
+void ifac_opts_default(ifac_opts* opts);
+
+/* ---------------------------------------------------------------- */
+/* Storage helpers                                                   */
+/* ---------------------------------------------------------------- */
+
+/* Copy a host BSR (arrays as in ifac_bsr) to a new library-owned device
+ * matrix; block norms are computed.  Validates the pattern (row_ptr
+ * monotone, columns in range and strictly increasing): IFAC_ERR_INVALID. */
+int ifac_bsr_upload(ifac_ctx* ctx, int64_t n, int32_t bs, int32_t nb, int64_t nnzb,
+                    const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                    ifac_bsr* out);
+
+/* Copy a device BSR to host arrays of sizes nb+1, nnzb, nnzb*bs*bs (any of
+ * the three may be NULL to skip it).  Synchronises the stream. */
+int ifac_bsr_download(ifac_ctx* ctx, const ifac_bsr* a, int32_t* row_ptr, int32_t* col_idx,
+                      double* val);
+
+/* Release a library-allocated matrix and zero the struct.  NULL-safe. */
+void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a);
+
+/* ---------------------------------------------------------------- */
+/* Block-sparse operations                                           */
+/* ---------------------------------------------------------------- */
+
+/* C = alpha * op(A) * op(B), op(X) = X^T when transX != 0; then every output
+ * block with Frobenius norm strictly below tau is removed (Section 5: blocks
+ * with norm smaller than the threshold are removed after every product).
+ * The output pattern before truncation is every (I, J) for which some K has
+ * op(A)_IK and op(B)_KJ stored.  A and B: same n and bs.  prec: IFAC_FP64. */
+int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB,
+                   double alpha, double tau, int prec, ifac_bsr* C);
+
+/* C = alpha A + beta B + gamma I on the union pattern (B may be NULL; the
+ * diagonal blocks are added when gamma != 0).  No truncation: the paper
+ * truncates after products and leaf routines only (Section 5). */
+int bsr_add(ifac_ctx* ctx, double alpha, const ifac_bsr* A, double beta, const ifac_bsr* B,
+            double gamma, ifac_bsr* C);
+
+/* C = A without its blocks of Frobenius norm < tau (the truncation of S,
+ * Section 5). */
+int bsr_truncate(ifac_ctx* ctx, const ifac_bsr* A, double tau, ifac_bsr* C);
+
+/* ||A||_F and the Gershgorin bound max_i sum_j |A_ij| (Section 2.2). */
+int bsr_fro(ifac_ctx* ctx, const ifac_bsr* A, double* out);
+int bsr_gershgorin(ifac_ctx* ctx, const ifac_bsr* A, double* out);
+
+/* Batched dense leaf routine of Algorithms 1-2 ("factorize S^-1 = Z Z^T"):
+ * for each of `count` row-major nl x nl SPD matrices at S + k*nl*nl (device),
+ * writes the upper-triangular Z = L^-T (S = L L^T, positive diagonal) to
+ * Z + k*nl*nl (device; may equal S for in-place).  info[k] (device int) is 0,
+ * or j+1 when pivot j of matrix k was not positive (that Z is undefined).
+ * Returns IFAC_ERR_NOT_SPD when any info is non-zero.  nl <= 1024. */
+int leaf_invchol_batched(ifac_ctx* ctx, int count, int nl, const double* S, double* Z, int* info);
+
+/* ---------------------------------------------------------------- */
+/* Factorizations                                                    */
+/* ---------------------------------------------------------------- */
+
+/* Iterative refinement with a scaled identity start (IRSI), Section 2.2:
+ * S is truncated at tau; beta = Gershgorin bound; Z_0 = c I; per sweep
+ * delta = I - Z^T (S Z) (two truncated products), the stop tests, then
+ * M = Z sum_{k=1}^{m} b_k delta^k and Z <- Z + M (Eq. 2.1).  Stops when
+ * ||delta||_F <= target, or ||delta_{i+1}||_F > ||delta_i||_F^(m+1), or after
+ * max_iter corrections; returns the last iterate (whose delta was last
+ * evaluated).  Returns IFAC_WARN_TARGET_NOT_MET when the rule stopped it
+ * above the target, IFAC_ERR_NO_CONVERGENCE at max_iter.  rep may be NULL. */
+int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
+                      const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
+
+/* Localized inverse factorization, Algorithm 2: the block range is halved
+ * (block-aligned midpoint, left half floor(nb/2)) until a range has at most
+ * leaf_size rows (or one block); leaves get Z = L^-T, truncated at tau; each
+ * parent forms Z_0 = diag(Z_A, Z_C), delta_0 = [0 X; X^T 0] with
+ * X = -Z_A^T (B Z_C), and refines with the localized update of Eq. (2.2):
+ * M = Z sum_{k>=1} b_k delta^k, Z' = Z + M, T = S M,
+ * delta' = delta - Z'^T T - T^T Z, stopping as Algorithm 4 (the first
+ * check never stops; then ||delta'|| > ||delta||^(m+1), or target, or
+ * max_iter).  All sub-problems of one depth are refined together.  S must
+ * already be in the wanted order (e.g. recursive coordinate bisection). */
+int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
+                         const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
+
+/* ||I - Z^T S Z||_F with untruncated products (the factorization error of
+ * Table 1). */
+int inv_factor_resid(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* Z, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IFAC_H */

@@ -1,0 +1,366 @@
+// api.cu -- the extern "C" boundary declared in include/ifac.h: contexts,
+// allocation, host<->device transfer, argument checks, and translation of
+// internal errors into status codes.
+#include <cstdio>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace ifac {
+
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  if (e == cudaErrorMemoryAllocation) fail(IFAC_ERR_OOM, buf);
+  fail(IFAC_ERR_CUDA, buf);
+}
+
+void* dalloc(ifac_ctx* ctx, size_t bytes) {
+  void* p = nullptr;
+  if (ctx->custom_alloc) {
+    p = ctx->alloc.alloc(ctx->alloc.user, bytes, ctx->stream);
+    if (!p) fail(IFAC_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    return p;
+  }
+  cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    fail(IFAC_ERR_OOM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed");
+  }
+  return p;
+}
+
+void dfree(ifac_ctx* ctx, void* p) {
+  if (!p) return;
+  if (ctx->custom_alloc) ctx->alloc.free(ctx->alloc.user, p, ctx->stream);
+  else cudaFreeAsync(p, ctx->stream);
+}
+
+void Mat::reset() {
+  if (!ctx) return;
+  dfree(ctx, m.row_ptr);
+  dfree(ctx, m.col_idx);
+  dfree(ctx, m.val);
+  dfree(ctx, m.norms);
+  m = ifac_bsr{};
+}
+
+Mat mat_alloc(ifac_ctx* ctx, int64_t n, int bs, int nb, int64_t nnzb) {
+  Mat M(ctx);
+  M.m.n = n;
+  M.m.bs = bs;
+  M.m.nb = nb;
+  M.m.nnzb = nnzb;
+  M.m.row_ptr = static_cast<int32_t*>(dalloc(ctx, sizeof(int32_t) * (nb + 1)));
+  M.m.col_idx = static_cast<int32_t*>(dalloc(ctx, sizeof(int32_t) * (nnzb ? nnzb : 1)));
+  M.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(nnzb ? nnzb : 1) * bs * bs));
+  M.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (nnzb ? nnzb : 1)));
+  return M;
+}
+
+void to_host(ifac_ctx* ctx, void* host, const void* dev, size_t bytes) {
+  if (bytes <= 4096) {
+    IFAC_CK(cudaMemcpyAsync(ctx->pinned, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    memcpy(host, ctx->pinned, bytes);
+  } else {
+    IFAC_CK(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+  }
+}
+
+void validate(const ifac_bsr* A, const char* name) {
+  std::string nm(name);
+  if (!A) fail(IFAC_ERR_INVALID, nm + " is NULL");
+  if (A->bs <= 0 || A->nb <= 0 || A->n <= 0) fail(IFAC_ERR_INVALID, nm + ": non-positive n, bs or nb");
+  if ((int64_t)A->nb != (A->n + A->bs - 1) / A->bs) fail(IFAC_ERR_INVALID, nm + ": nb != ceil(n/bs)");
+  if (A->nnzb < 0 || A->nnzb > (int64_t)A->nb * A->nb) fail(IFAC_ERR_INVALID, nm + ": bad nnzb");
+  if (A->nnzb > 0x7fffffffLL) fail(IFAC_ERR_UNSUPPORTED, nm + ": more than 2^31-1 blocks");
+  if (!A->row_ptr || !A->col_idx || (!A->val && A->nnzb > 0)) fail(IFAC_ERR_INVALID, nm + ": NULL array");
+}
+
+static cudaEvent_t next_event(ifac_ctx* ctx) {
+  if (ctx->events_used == ctx->events.size()) {
+    cudaEvent_t e;
+    IFAC_CK(cudaEventCreate(&e));
+    ctx->events.push_back(e);
+  }
+  return ctx->events[ctx->events_used++];
+}
+
+void prof_begin(ifac_ctx* ctx) {
+  if (ctx->profile) IFAC_CK(cudaEventRecord(next_event(ctx), ctx->stream));
+}
+
+void prof_end(ifac_ctx* ctx) {
+  if (ctx->profile) IFAC_CK(cudaEventRecord(next_event(ctx), ctx->stream));
+}
+
+double prof_collect(ifac_ctx* ctx) {
+  double ms = 0.0;
+  if (ctx->events_used) {
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i + 1 < ctx->events_used; i += 2) {
+      float t = 0.f;
+      IFAC_CK(cudaEventElapsedTime(&t, ctx->events[i], ctx->events[i + 1]));
+      ms += t;
+    }
+  }
+  ctx->events_used = 0;
+  return ms;
+}
+
+}  // namespace ifac
+
+using namespace ifac;
+
+template <typename F>
+static int guarded(ifac_ctx* ctx, F&& f) {
+  if (!ctx) return IFAC_ERR_INVALID;
+  try {
+    int prev;
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != ctx->device) cudaSetDevice(ctx->device);
+    int rc = f();
+    if (rc != 0) {
+      if (ctx->err.empty()) ctx->err = "status " + std::to_string(rc);
+    } else {
+      ctx->err.clear();
+    }
+    return rc;
+  } catch (const Error& e) {
+    ctx->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    ctx->err = "host allocation failed";
+    return IFAC_ERR_OOM;
+  } catch (...) {
+    ctx->err = "unexpected internal error";
+    return IFAC_ERR_CUDA;
+  }
+}
+
+extern "C" {
+
+void ifac_opts_default(ifac_opts* o) {
+  if (!o) return;
+  o->m = 2;
+  o->max_iter = 50;
+  o->fixed_iters = 0;
+  o->c_rule = 0;
+  o->leaf_size = 512;
+  o->prec = IFAC_FP64;
+  o->profile = 0;
+}
+
+int ifac_create(ifac_ctx** out, void* stream, const ifac_allocator* alloc) {
+  if (!out) return IFAC_ERR_INVALID;
+  *out = nullptr;
+  ifac_ctx* c = new (std::nothrow) ifac_ctx();
+  if (!c) return IFAC_ERR_OOM;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return IFAC_ERR_CUDA; }
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (alloc) {
+    if (!alloc->alloc || !alloc->free) { delete c; return IFAC_ERR_INVALID; }
+    c->custom_alloc = true;
+    c->alloc = *alloc;
+  } else {
+    // keep freed blocks in the device pool between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  if (cudaMallocHost(&c->pinned, 4096) != cudaSuccess) { delete c; return IFAC_ERR_CUDA; }
+  *out = c;
+  return IFAC_OK;
+}
+
+void ifac_destroy(ifac_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+int ifac_set_stream(ifac_ctx* ctx, void* stream) {
+  if (!ctx) return IFAC_ERR_INVALID;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return IFAC_OK;
+}
+
+const char* ifac_last_error(const ifac_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int ifac_bsr_upload(ifac_ctx* ctx, int64_t n, int32_t bs, int32_t nb, int64_t nnzb, const int32_t* row_ptr,
+                    const int32_t* col_idx, const double* val, ifac_bsr* out) {
+  if (out) *out = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    if (!out || !row_ptr || (nnzb > 0 && (!col_idx || !val))) fail(IFAC_ERR_INVALID, "upload: NULL argument");
+    if (bs <= 0 || nb <= 0 || n <= 0 || (int64_t)nb != (n + bs - 1) / bs) fail(IFAC_ERR_INVALID, "upload: bad n/bs/nb");
+    if (row_ptr[0] != 0 || row_ptr[nb] != nnzb) fail(IFAC_ERR_INVALID, "upload: row_ptr[0] != 0 or row_ptr[nb] != nnzb");
+    for (int i = 0; i < nb; ++i) {
+      if (row_ptr[i + 1] < row_ptr[i]) fail(IFAC_ERR_INVALID, "upload: row_ptr not monotone");
+      for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+        if (col_idx[p] < 0 || col_idx[p] >= nb) fail(IFAC_ERR_INVALID, "upload: column index out of range");
+        if (p > row_ptr[i] && col_idx[p] <= col_idx[p - 1]) fail(IFAC_ERR_INVALID, "upload: columns not strictly increasing");
+      }
+    }
+    Mat M = mat_alloc(ctx, n, bs, nb, nnzb);
+    IFAC_CK(cudaMemcpyAsync(M.m.row_ptr, row_ptr, sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, ctx->stream));
+    if (nnzb) {
+      IFAC_CK(cudaMemcpyAsync(M.m.col_idx, col_idx, sizeof(int32_t) * nnzb, cudaMemcpyHostToDevice, ctx->stream));
+      IFAC_CK(cudaMemcpyAsync(M.m.val, val, sizeof(double) * (size_t)nnzb * bs * bs, cudaMemcpyHostToDevice, ctx->stream));
+      block_norms(ctx, M.m, M.m.norms);
+    }
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    *out = M.release();
+    return IFAC_OK;
+  });
+}
+
+int ifac_bsr_download(ifac_ctx* ctx, const ifac_bsr* a, int32_t* row_ptr, int32_t* col_idx, double* val) {
+  return guarded(ctx, [&]() -> int {
+    validate(a, "A");
+    if (row_ptr) IFAC_CK(cudaMemcpyAsync(row_ptr, a->row_ptr, sizeof(int32_t) * (a->nb + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    if (col_idx && a->nnzb) IFAC_CK(cudaMemcpyAsync(col_idx, a->col_idx, sizeof(int32_t) * a->nnzb, cudaMemcpyDeviceToHost, ctx->stream));
+    if (val && a->nnzb) IFAC_CK(cudaMemcpyAsync(val, a->val, sizeof(double) * (size_t)a->nnzb * a->bs * a->bs, cudaMemcpyDeviceToHost, ctx->stream));
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    return IFAC_OK;
+  });
+}
+
+void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a) {
+  if (!ctx || !a) return;
+  Mat M(ctx);
+  M.m = *a;
+  M.reset();
+  *a = ifac_bsr{};
+}
+
+static void check_pair(const ifac_bsr* A, const ifac_bsr* B) {
+  if (A->n != B->n || A->bs != B->bs || A->nb != B->nb) fail(IFAC_ERR_INVALID, "operands differ in n or block size");
+}
+
+int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB, double alpha,
+                   double tau, int prec, ifac_bsr* C) {
+  if (C) *C = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(A, "A");
+    validate(B, "B");
+    check_pair(A, B);
+    if (!C) fail(IFAC_ERR_INVALID, "C is NULL");
+    if (prec != IFAC_FP64) fail(IFAC_ERR_UNSUPPORTED, "precision not built");
+    if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
+    Mat R = ifac::gemm(ctx, *A, transA != 0, *B, transB != 0, alpha, tau);
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    *C = R.release();
+    return IFAC_OK;
+  });
+}
+
+int bsr_add(ifac_ctx* ctx, double alpha, const ifac_bsr* A, double beta, const ifac_bsr* B, double gamma, ifac_bsr* C) {
+  if (C) *C = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(A, "A");
+    if (B) { validate(B, "B"); check_pair(A, B); }
+    if (!C) fail(IFAC_ERR_INVALID, "C is NULL");
+    Mat R = ifac::add(ctx, alpha, *A, beta, B, gamma);
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    *C = R.release();
+    return IFAC_OK;
+  });
+}
+
+int bsr_truncate(ifac_ctx* ctx, const ifac_bsr* A, double tau, ifac_bsr* C) {
+  if (C) *C = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(A, "A");
+    if (!C) fail(IFAC_ERR_INVALID, "C is NULL");
+    Mat R = ifac::truncate(ctx, *A, tau);
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    *C = R.release();
+    return IFAC_OK;
+  });
+}
+
+int bsr_fro(ifac_ctx* ctx, const ifac_bsr* A, double* out) {
+  return guarded(ctx, [&]() -> int {
+    validate(A, "A");
+    if (!out) fail(IFAC_ERR_INVALID, "out is NULL");
+    *out = fro_host(ctx, *A);
+    return IFAC_OK;
+  });
+}
+
+int bsr_gershgorin(ifac_ctx* ctx, const ifac_bsr* A, double* out) {
+  return guarded(ctx, [&]() -> int {
+    validate(A, "A");
+    if (!out) fail(IFAC_ERR_INVALID, "out is NULL");
+    *out = gershgorin_host(ctx, *A);
+    return IFAC_OK;
+  });
+}
+
+int leaf_invchol_batched(ifac_ctx* ctx, int count, int nl, const double* S, double* Z, int* info) {
+  return guarded(ctx, [&]() -> int {
+    if (count < 0 || nl <= 0 || nl > 1024 || !S || !Z || !info) fail(IFAC_ERR_INVALID, "leaf: bad arguments");
+    if (count == 0) return IFAC_OK;
+    if (S != Z)
+      IFAC_CK(cudaMemcpyAsync(Z, S, sizeof(double) * (size_t)count * nl * nl, cudaMemcpyDeviceToDevice, ctx->stream));
+    leaf_invchol(ctx, count, nl, Z, info);
+    std::vector<int> h(count);
+    to_host(ctx, h.data(), info, sizeof(int) * count);
+    for (int k = 0; k < count; ++k)
+      if (h[k]) fail(IFAC_ERR_NOT_SPD, "leaf " + std::to_string(k) + ": pivot " + std::to_string(h[k] - 1) + " not positive");
+    return IFAC_OK;
+  });
+}
+
+static void check_opts(const ifac_opts* o) {
+  if (!o) fail(IFAC_ERR_INVALID, "opts is NULL");
+  if (o->m < 1 || o->m > 8) fail(IFAC_ERR_INVALID, "m must be in 1..8");
+  if (o->max_iter < 0 || o->fixed_iters < 0) fail(IFAC_ERR_INVALID, "negative iteration count");
+  if (o->prec != IFAC_FP64) fail(IFAC_ERR_UNSUPPORTED, "precision not built");
+}
+
+int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target, const ifac_opts* opts,
+                      ifac_bsr* Z, ifac_report* rep) {
+  if (Z) *Z = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(S, "S");
+    check_opts(opts);
+    if (!Z) fail(IFAC_ERR_INVALID, "Z is NULL");
+    if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
+    return refine_irsi(ctx, *S, tau, target, *opts, Z, rep);
+  });
+}
+
+int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target, const ifac_opts* opts,
+                         ifac_bsr* Z, ifac_report* rep) {
+  if (Z) *Z = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(S, "S");
+    check_opts(opts);
+    if (!Z) fail(IFAC_ERR_INVALID, "Z is NULL");
+    if (opts->leaf_size < 1) fail(IFAC_ERR_INVALID, "leaf_size must be >= 1");
+    if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
+    return lif(ctx, *S, tau, target, *opts, Z, rep);
+  });
+}
+
+int inv_factor_resid(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* Z, double* out) {
+  return guarded(ctx, [&]() -> int {
+    validate(S, "S");
+    validate(Z, "Z");
+    check_pair(S, Z);
+    if (!out) fail(IFAC_ERR_INVALID, "out is NULL");
+    *out = resid(ctx, *S, *Z);
+    return IFAC_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,459 @@
+// drivers.cu -- the factorization drivers: refinement from a scaled identity
+// (Section 2.2, Eq. 2.1) and localized inverse factorization (Algorithm 2
+// with the localized update of Eq. 2.2 and the stop rule of Algorithm 4),
+// plus the direct factorization error ||I - Z^T S Z||_F.
+//
+// Localized inverse factorization is run level by level: the bisection tree
+// is built on the host, every leaf is factorized in one batched launch, and
+// then, from the deepest internal level up, all sub-problems of one depth are
+// refined together.  Their matrices are the block-diagonal restrictions of S
+// and Z to the sub-problems, so one block-sparse product serves every
+// sub-problem of the level (the products never couple two sub-problems); the
+// stop rule is applied per sub-problem, and a stopped sub-problem's rows are
+// removed from delta so its Z stays at the iterate the rule returned.
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace ifac {
+
+static double coef_b(int k) {
+  double b = 1.0;
+  for (int j = 1; j <= k; ++j) b = b * (double)(2 * j - 1) / (double)(2 * j);
+  return b;
+}
+
+// P = sum_{k=1}^{m} b_k delta^k, powers by successive truncated products
+static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau) {
+  Mat P = add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
+  Mat D;
+  for (int k = 2; k <= m; ++k) {
+    Mat Dn = gemm(ctx, k == 2 ? delta : D.m, false, delta, false, 1.0, tau);
+    D = std::move(Dn);
+    P = add(ctx, 1.0, P.m, coef_b(k), &D.m, 0.0);
+  }
+  return P;
+}
+
+static void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
+  ctx->products = 0;
+  ctx->pairs = 0;
+  ctx->launches = 0;
+  ctx->gemm_launches = 0;
+  ctx->events_used = 0;
+  ctx->profile = o.profile != 0;
+  if (r) *r = ifac_report{};
+}
+
+static void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
+  if (!r) return;
+  r->products = ctx->products;
+  r->block_pairs = ctx->pairs;
+  r->nnzb_Z = Z.nnzb;
+  r->flops = 2.0 * (double)Z.bs * Z.bs * Z.bs * (double)ctx->pairs;
+  r->gemm_ms = prof_collect(ctx);
+  r->launches = ctx->launches;
+  r->gemm_launches = ctx->gemm_launches;
+  ctx->profile = false;
+}
+
+// ---------------------------------------------------------------------------
+// refinement from a scaled identity
+// ---------------------------------------------------------------------------
+int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, const ifac_opts& o, ifac_bsr* Zout,
+                ifac_report* rep) {
+  report_init(ctx, rep, o);
+  Mat S = truncate(ctx, S_in, tau);
+  const double beta = gershgorin_host(ctx, S.m);
+  const double c = (o.c_rule == 1) ? std::sqrt(2.0 / beta) : 1.0 / std::sqrt(beta);
+  Mat Z = scaled_identity(ctx, S.m.n, S.m.bs, S.m.nb, c);
+  if (rep) rep->beta = beta;
+  double e_prev = INFINITY;
+  int stop = 0, it = 0;
+  double e = 0.0;
+  for (it = 0;; ++it) {
+    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau);   // S Z
+    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau);    // Z^T (S Z)
+    X.reset();
+    Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);        // I - Z^T S Z
+    Y.reset();
+    e = fro_host(ctx, D.m);
+    if (rep && rep->n_delta < 64) rep->delta_fro[rep->n_delta++] = e;
+    if (o.fixed_iters > 0) {
+      if (it == o.fixed_iters) stop = IFAC_STOP_FIXED;
+    } else if (e <= target) {
+      stop = IFAC_STOP_TARGET;
+    } else if (e > std::pow(e_prev, (double)(o.m + 1))) {
+      stop = IFAC_STOP_RULE;
+    } else if (it == o.max_iter) {
+      stop = IFAC_STOP_MAXITER;
+    }
+    if (stop) break;
+    Mat P = poly_P(ctx, D.m, o.m, tau);
+    D.reset();
+    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau);   // M = Z sum b_k delta^k
+    P.reset();
+    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);                // Z + M
+    e_prev = e;
+  }
+  if (rep) {
+    rep->sweeps = it;
+    rep->stop_reason = stop;
+  }
+  if (stop == IFAC_STOP_MAXITER) {
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    fail(IFAC_ERR_NO_CONVERGENCE, "no convergence in max_iter sweeps; ||delta||_F = " + std::to_string(e));
+  }
+  report_finish(ctx, rep, Z.m);
+  IFAC_CK(cudaStreamSynchronize(ctx->stream));
+  *Zout = Z.release();
+  return (stop == IFAC_STOP_RULE && e > target) ? IFAC_WARN_TARGET_NOT_MET : IFAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// localized inverse factorization helpers
+// ---------------------------------------------------------------------------
+enum FilterMode { F_ROWS_IN = 0, F_ROWS_OUT = 1, F_SAME = 2, F_COUPLE = 3 };
+
+__global__ void k_filter_mask(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int nb,
+                              const int32_t* __restrict__ seg, const int32_t* __restrict__ mid,
+                              const uint8_t* __restrict__ active, int mode, uint8_t* __restrict__ keep) {
+  int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= nb) return;
+  const int s = seg[row];
+  for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) {
+    const int J = ci[p];
+    bool k;
+    switch (mode) {
+      case F_ROWS_IN: k = s >= 0 && (!active || active[s]); break;
+      case F_ROWS_OUT: k = s < 0; break;
+      case F_SAME: k = s >= 0 && seg[J] == s; break;
+      default: k = s >= 0 && seg[J] == s && row < mid[s] && J >= mid[s]; break;
+    }
+    keep[p] = k ? 1 : 0;
+  }
+}
+
+static Mat filter(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* seg, const int32_t* mid, const uint8_t* active,
+                  int mode) {
+  Buf<uint8_t> keep(ctx, A.nnzb);
+  if (A.nnzb) {
+    k_filter_mask<<<cdiv((int64_t)A.nb * 32, 256), 256, 0, ctx->stream>>>(A.row_ptr, A.col_idx, A.nb, seg, mid,
+                                                                          active, mode, keep.p);
+    IFAC_CK_LAUNCH();
+  }
+  return select_blocks(ctx, A, nullptr, keep.p);
+}
+
+// explicit transpose: block q of A^T = (block src[q] of A)^T
+__global__ void k_transpose_blocks(const double* __restrict__ val, const double* __restrict__ norms,
+                                   const int32_t* __restrict__ src, int64_t nnzb, int bs, double* __restrict__ out,
+                                   double* __restrict__ onorms) {
+  const int bsz = bs * bs;
+  for (int64_t q = blockIdx.x; q < nnzb; q += gridDim.x) {
+    const double* s = val + (size_t)src[q] * bsz;
+    double* t = out + (size_t)q * bsz;
+    for (int e = threadIdx.x; e < bsz; e += blockDim.x) {
+      int r = e / bs, c = e % bs;
+      t[e] = s[c * bs + r];
+    }
+    if (threadIdx.x == 0) onorms[q] = norms[src[q]];
+  }
+}
+
+static Mat transpose_mat(ifac_ctx* ctx, const ifac_bsr& A) {
+  View v = view_rows(ctx, A, true);
+  Mat T(ctx);
+  T.m.n = A.n;
+  T.m.bs = A.bs;
+  T.m.nb = A.nb;
+  T.m.nnzb = A.nnzb;
+  T.m.row_ptr = v.own_rp.release();
+  T.m.col_idx = v.own_ci.release();
+  T.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(A.nnzb ? A.nnzb : 1) * A.bs * A.bs));
+  T.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (A.nnzb ? A.nnzb : 1)));
+  if (A.nnzb) {
+    int grid = (int)std::min<int64_t>(A.nnzb, 152 * 16);
+    k_transpose_blocks<<<grid, 256, 0, ctx->stream>>>(A.val, A.norms, v.src, A.nnzb, A.bs, T.m.val, T.m.norms);
+    IFAC_CK_LAUNCH();
+  }
+  return T;
+}
+
+// dense leaf buffers: identity everywhere, then the diagonal range of S of
+// each leaf copied in (block (I, J) of S with both rows in leaf k)
+__global__ void k_identity_fill(double* __restrict__ buf, int np, int count) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t per = (int64_t)np * np;
+  if (e >= per * count) return;
+  int64_t q = e % per;
+  buf[e] = ((q / np) == (q % np)) ? 1.0 : 0.0;
+}
+
+__global__ void k_leaf_gather(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const double* __restrict__ val, int nb, int bs, const int32_t* __restrict__ leaf_of,
+                              const int32_t* __restrict__ leaf_b0, int np, double* __restrict__ buf) {
+  // one CTA per block row
+  const int I = blockIdx.x;
+  if (I >= nb) return;
+  const int k = leaf_of[I], b0 = leaf_b0[k];
+  double* dst = buf + (size_t)k * np * np;
+  for (int p = rp[I]; p < rp[I + 1]; ++p) {
+    const int J = ci[p];
+    if (leaf_of[J] != k) continue;
+    const double* s = val + (size_t)p * bs * bs;
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+      int r = e / bs, c = e % bs;
+      dst[(size_t)((I - b0) * bs + r) * np + (J - b0) * bs + c] = s[e];
+    }
+  }
+}
+
+// blocks (I, J), I <= J inside each leaf, copied out of the dense factors
+__global__ void k_leaf_scatter(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int nb, int bs,
+                               const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ leaf_b0, int np,
+                               const double* __restrict__ buf, double* __restrict__ val, double* __restrict__ norms) {
+  __shared__ double red[8];
+  const int I = blockIdx.x;
+  if (I >= nb) return;
+  const int k = leaf_of[I], b0 = leaf_b0[k];
+  const double* src = buf + (size_t)k * np * np;
+  for (int p = rp[I]; p < rp[I + 1]; ++p) {
+    const int J = ci[p];
+    double ss = 0.0;
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+      int r = e / bs, c = e % bs;
+      double v = src[(size_t)((I - b0) * bs + r) * np + (J - b0) * bs + c];
+      val[(size_t)p * bs * bs + e] = v;
+      ss = fma(v, v, ss);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      norms[p] = sqrt(t);
+    }
+    __syncthreads();
+  }
+}
+
+struct Node {
+  int b0, bm, b1, depth;
+  bool leaf;
+};
+
+static void build_tree(int b0, int b1, int depth, int bs, int leaf_size, std::vector<Node>& out) {
+  const int nbs = b1 - b0;
+  if ((int64_t)nbs * bs <= leaf_size || nbs == 1) {
+    out.push_back({b0, b1, b1, depth, true});
+    return;
+  }
+  const int bm = b0 + nbs / 2;
+  out.push_back({b0, bm, b1, depth, false});
+  build_tree(b0, bm, depth + 1, bs, leaf_size, out);
+  build_tree(bm, b1, depth + 1, bs, leaf_size, out);
+}
+
+template <typename T>
+static Buf<T> upload_vec(ifac_ctx* ctx, const std::vector<T>& h) {
+  Buf<T> d(ctx, h.size());
+  if (!h.empty())
+    IFAC_CK(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+  return d;
+}
+
+// all leaves: Z_leaf = L^-T from the batched leaf routine, then truncation
+static Mat leaf_factors(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<Node>& leaves, double tau) {
+  const int nb = S.nb, bs = S.bs, count = (int)leaves.size();
+  int nl_max = 0;
+  std::vector<int32_t> leaf_of(nb), leaf_b0(count);
+  for (int k = 0; k < count; ++k) {
+    nl_max = std::max(nl_max, (leaves[k].b1 - leaves[k].b0) * bs);
+    leaf_b0[k] = leaves[k].b0;
+    for (int I = leaves[k].b0; I < leaves[k].b1; ++I) leaf_of[I] = k;
+  }
+  const int np = ((nl_max + 31) / 32) * 32;
+  Buf<int32_t> d_leaf_of = upload_vec(ctx, leaf_of), d_leaf_b0 = upload_vec(ctx, leaf_b0);
+  Buf<double> buf(ctx, (size_t)count * np * np);
+  int64_t tot = (int64_t)count * np * np;
+  k_identity_fill<<<cdiv(tot, 256), 256, 0, ctx->stream>>>(buf.p, np, count);
+  IFAC_CK_LAUNCH();
+  k_leaf_gather<<<nb, 256, 0, ctx->stream>>>(S.row_ptr, S.col_idx, S.val, nb, bs, d_leaf_of.p, d_leaf_b0.p, np, buf.p);
+  IFAC_CK_LAUNCH();
+  Buf<int> info(ctx, count);
+  leaf_invchol(ctx, count, np, buf.p, info.p);
+  std::vector<int> hinfo(count);
+  to_host(ctx, hinfo.data(), info.p, sizeof(int) * count);
+  for (int k = 0; k < count; ++k)
+    if (hinfo[k])
+      fail(IFAC_ERR_NOT_SPD, "leaf " + std::to_string(k) + " (block rows " + std::to_string(leaves[k].b0) + ".." +
+                                 std::to_string(leaves[k].b1 - 1) + "): pivot " + std::to_string(hinfo[k] - 1) +
+                                 " not positive");
+  // upper-triangular block pattern of every leaf
+  std::vector<int32_t> rp(nb + 1, 0), ci;
+  for (int I = 0; I < nb; ++I) {
+    const Node& L = leaves[leaf_of[I]];
+    for (int J = I; J < L.b1; ++J) ci.push_back(J);
+    rp[I + 1] = (int32_t)ci.size();
+  }
+  Mat Z = mat_alloc(ctx, S.n, bs, nb, (int64_t)ci.size());
+  IFAC_CK(cudaMemcpyAsync(Z.m.row_ptr, rp.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, ctx->stream));
+  IFAC_CK(cudaMemcpyAsync(Z.m.col_idx, ci.data(), sizeof(int32_t) * ci.size(), cudaMemcpyHostToDevice, ctx->stream));
+  k_leaf_scatter<<<nb, 256, 0, ctx->stream>>>(Z.m.row_ptr, Z.m.col_idx, nb, bs, d_leaf_of.p, d_leaf_b0.p, np, buf.p,
+                                              Z.m.val, Z.m.norms);
+  IFAC_CK_LAUNCH();
+  IFAC_CK(cudaStreamSynchronize(ctx->stream));  // host vectors rp/ci go out of scope
+  return compact(ctx, std::move(Z), nullptr, tau);
+}
+
+// per-sub-problem ||delta||_F: rows of sub-problem s are [b0_s, b1_s)
+__global__ void k_node_fro(const double* __restrict__ rowsq, const int32_t* __restrict__ nb0,
+                           const int32_t* __restrict__ nb1, int nnodes, double* __restrict__ out) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nnodes) return;
+  double t = 0.0;
+  for (int r = nb0[s]; r < nb1[s]; ++r) t += rowsq[r];
+  out[s] = sqrt(t);
+}
+
+// ---------------------------------------------------------------------------
+// localized inverse factorization
+// ---------------------------------------------------------------------------
+int lif(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, const ifac_opts& o, ifac_bsr* Zout,
+        ifac_report* rep) {
+  report_init(ctx, rep, o);
+  Mat S = truncate(ctx, S_in, tau);
+  const int nb = S.m.nb, bs = S.m.bs;
+  std::vector<Node> tree;
+  build_tree(0, nb, 0, bs, o.leaf_size, tree);
+  int max_depth = 0;
+  std::vector<Node> leaves;
+  for (const Node& n : tree) {
+    max_depth = std::max(max_depth, n.depth);
+    if (n.leaf) leaves.push_back(n);
+  }
+  Mat Z = leaf_factors(ctx, S.m, leaves, tau);
+  int total_sweeps = 0, top_stop = 0;
+  bool any_maxiter = false;
+  double top_e = 0.0;
+
+  for (int d = max_depth - 1; d >= 0; --d) {
+    std::vector<Node> nodes;
+    for (const Node& n : tree)
+      if (!n.leaf && n.depth == d) nodes.push_back(n);
+    if (nodes.empty()) continue;
+    const int nn = (int)nodes.size();
+    std::vector<int32_t> seg(nb, -1), mid(nn), nb0(nn), nb1(nn);
+    for (int s = 0; s < nn; ++s) {
+      mid[s] = nodes[s].bm;
+      nb0[s] = nodes[s].b0;
+      nb1[s] = nodes[s].b1;
+      for (int I = nodes[s].b0; I < nodes[s].b1; ++I) seg[I] = s;
+    }
+    Buf<int32_t> dseg = upload_vec(ctx, seg), dmid = upload_vec(ctx, mid), dnb0 = upload_vec(ctx, nb0),
+                 dnb1 = upload_vec(ctx, nb1);
+    Mat Sd = filter(ctx, S.m, dseg.p, dmid.p, nullptr, F_SAME);
+    Mat Bh = filter(ctx, S.m, dseg.p, dmid.p, nullptr, F_COUPLE);
+    Mat Zd = filter(ctx, Z.m, dseg.p, dmid.p, nullptr, F_ROWS_IN);
+    Mat Zrest = filter(ctx, Z.m, dseg.p, dmid.p, nullptr, F_ROWS_OUT);
+    Z.reset();
+    // delta_0 = [0 X; X^T 0], X = -Z_A^T (B Z_C)
+    Mat T = gemm(ctx, Bh.m, false, Zd.m, false, 1.0, tau);
+    Bh.reset();
+    Mat X = gemm(ctx, Zd.m, true, T.m, false, -1.0, tau);
+    T.reset();
+    Mat Xt = transpose_mat(ctx, X.m);
+    Mat delta = add(ctx, 1.0, X.m, 1.0, &Xt.m, 0.0);
+    X.reset();
+    Xt.reset();
+
+    std::vector<double> e_prev(nn, INFINITY), e(nn, 0.0);
+    std::vector<uint8_t> active(nn, 1);
+    std::vector<int> sweeps(nn, 0), stop(nn, 0);
+    Buf<uint8_t> dactive(ctx, nn);
+    Buf<double> rowsq(ctx, nb), node_e(ctx, nn);
+    for (int it = 0;; ++it) {
+      Mat P = poly_P(ctx, delta.m, o.m, tau);
+      Mat M = gemm(ctx, Zd.m, false, P.m, false, 1.0, tau);      // M = Z sum_{k>=1} b_k delta^k
+      P.reset();
+      Mat Zn = add(ctx, 1.0, Zd.m, 1.0, &M.m, 0.0);              // Z_{i+1} = Z_i + M
+      Mat TS = gemm(ctx, Sd.m, false, M.m, false, 1.0, tau);     // S M
+      M.reset();
+      Mat U = gemm(ctx, Zn.m, true, TS.m, false, 1.0, tau);      // Z_{i+1}^T (S M)
+      Mat V = gemm(ctx, TS.m, true, Zd.m, false, 1.0, tau);      // (M^T S) Z_i = (S M)^T Z_i
+      TS.reset();
+      Mat d1 = add(ctx, 1.0, delta.m, -1.0, &U.m, 0.0);
+      U.reset();
+      delta = add(ctx, 1.0, d1.m, -1.0, &V.m, 0.0);
+      d1.reset();
+      V.reset();
+      Zd = std::move(Zn);
+      // per-sub-problem norms
+      row_sq_norms(ctx, delta.m, rowsq.p);
+      k_node_fro<<<cdiv(nn, 128), 128, 0, ctx->stream>>>(rowsq.p, dnb0.p, dnb1.p, nn, node_e.p);
+      IFAC_CK_LAUNCH();
+      to_host(ctx, e.data(), node_e.p, sizeof(double) * nn);
+      bool any_active = false;
+      for (int s = 0; s < nn; ++s) {
+        if (!active[s]) continue;
+        sweeps[s]++;
+        int st = 0;
+        if (e[s] <= target) st = IFAC_STOP_TARGET;
+        else if (e[s] > std::pow(e_prev[s], (double)(o.m + 1))) st = IFAC_STOP_RULE;
+        else if (sweeps[s] >= o.max_iter) st = IFAC_STOP_MAXITER;
+        if (st) {
+          active[s] = 0;
+          stop[s] = st;
+          if (st == IFAC_STOP_MAXITER) any_maxiter = true;
+        } else {
+          any_active = true;
+        }
+        e_prev[s] = e[s];
+        if (d == 0 && rep && rep->n_delta < 64) rep->delta_fro[rep->n_delta++] = e[s];
+      }
+      if (!any_active) break;
+      // drop the rows of stopped sub-problems from delta
+      IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), nn, cudaMemcpyHostToDevice, ctx->stream));
+      delta = filter(ctx, delta.m, dseg.p, dmid.p, dactive.p, F_ROWS_IN);
+      IFAC_CK(cudaStreamSynchronize(ctx->stream));  // `active` is reused on the host
+    }
+    for (int s = 0; s < nn; ++s) total_sweeps += sweeps[s];
+    if (d == 0) {
+      top_stop = stop[0];
+      top_e = e[0];
+    }
+    delta.reset();
+    Sd.reset();
+    Z = add(ctx, 1.0, Zrest.m, 1.0, &Zd.m, 0.0);
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));  // host vectors of this level go out of scope
+  }
+  if (rep) {
+    rep->sweeps = total_sweeps;
+    rep->stop_reason = top_stop;
+    rep->levels = max_depth;
+  }
+  if (any_maxiter) fail(IFAC_ERR_NO_CONVERGENCE, "a sub-problem reached max_iter sweeps");
+  report_finish(ctx, rep, Z.m);
+  IFAC_CK(cudaStreamSynchronize(ctx->stream));
+  *Zout = Z.release();
+  if (max_depth == 0) return IFAC_OK;  // a single leaf: exact up to rounding
+  return (top_stop == IFAC_STOP_RULE && top_e > target) ? IFAC_WARN_TARGET_NOT_MET : IFAC_OK;
+}
+
+double resid(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& Z) {
+  int64_t p0 = ctx->products, q0 = ctx->pairs;
+  Mat X = gemm(ctx, S, false, Z, false, 1.0, 0.0);
+  Mat Y = gemm(ctx, Z, true, X.m, false, 1.0, 0.0);
+  X.reset();
+  Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
+  double e = fro_host(ctx, D.m);
+  ctx->products = p0;
+  ctx->pairs = q0;
+  return e;
+}
+
+}  // namespace ifac

@@ -1,0 +1,171 @@
+// internal.cuh -- shared declarations of the CUDA library behind ifac.h.
+//
+// Errors inside the library are C++ exceptions (ifac::Error) that the
+// extern "C" entry points in api.cu turn into status codes; device buffers
+// are owned by RAII holders so that an error path frees what it allocated.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ifac.h"
+
+struct ifac_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool custom_alloc = false;
+  ifac_allocator alloc{};
+  std::string err;
+  // counters of the current driver call
+  int64_t products = 0;
+  int64_t pairs = 0;
+  int64_t launches = 0;
+  int64_t gemm_launches = 0;
+  // optional event timing of the numeric product kernels
+  bool profile = false;
+  std::vector<cudaEvent_t> events;
+  size_t events_used = 0;
+  // small pinned host buffer for scalar read-backs
+  void* pinned = nullptr;
+};
+
+namespace ifac {
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define IFAC_CK(x) ::ifac::check_cuda((x), #x, __FILE__, __LINE__)
+#define IFAC_CK_LAUNCH() \
+  do { ++ctx->launches; ::ifac::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); } while (0)
+
+void* dalloc(ifac_ctx* ctx, size_t bytes);
+void dfree(ifac_ctx* ctx, void* p);
+
+// Typed device buffer owned by a context.
+template <typename T>
+struct Buf {
+  ifac_ctx* ctx = nullptr;
+  T* p = nullptr;
+  size_t n = 0;
+  Buf() = default;
+  Buf(ifac_ctx* c, size_t count) : ctx(c), n(count) {
+    p = static_cast<T*>(dalloc(c, (count ? count : 1) * sizeof(T)));
+  }
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  Buf(Buf&& o) noexcept : ctx(o.ctx), p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  Buf& operator=(Buf&& o) noexcept {
+    if (this != &o) { reset(); ctx = o.ctx; p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~Buf() { reset(); }
+  void reset() { if (p) dfree(ctx, p); p = nullptr; n = 0; }
+  T* release() { T* q = p; p = nullptr; n = 0; return q; }
+  T* get() const { return p; }
+};
+
+// A library-owned block-sparse matrix (all arrays device, norms always set).
+struct Mat {
+  ifac_ctx* ctx = nullptr;
+  ifac_bsr m{};
+  Mat() = default;
+  explicit Mat(ifac_ctx* c) : ctx(c) {}
+  Mat(const Mat&) = delete;
+  Mat& operator=(const Mat&) = delete;
+  Mat(Mat&& o) noexcept : ctx(o.ctx), m(o.m) { o.m = ifac_bsr{}; }
+  Mat& operator=(Mat&& o) noexcept {
+    if (this != &o) { reset(); ctx = o.ctx; m = o.m; o.m = ifac_bsr{}; }
+    return *this;
+  }
+  ~Mat() { reset(); }
+  void reset();
+  ifac_bsr release() { ifac_bsr r = m; m = ifac_bsr{}; return r; }
+  const ifac_bsr& operator*() const { return m; }
+};
+
+// Allocate the arrays of an n x n matrix with nnzb blocks.
+Mat mat_alloc(ifac_ctx* ctx, int64_t n, int bs, int nb, int64_t nnzb);
+
+// Read back a few device ints/int64/doubles (synchronises the stream).
+void to_host(ifac_ctx* ctx, void* host, const void* dev, size_t bytes);
+
+// ---- pattern utilities (pattern.cu) ----
+int words_per_row(int nb);
+// exclusive scan of in[0..n) into out[0..n], out[n] = total; returns total (syncs)
+int64_t scan_counts(ifac_ctx* ctx, const int32_t* in, int32_t* out, int n, bool want_total);
+// CSR view of op(X): rows of X^T with the index of the source block of X.
+struct View {
+  const int32_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const int32_t* src = nullptr;  // nullptr = identity
+  Buf<int32_t> own_rp, own_ci, own_src;
+};
+View view_rows(ifac_ctx* ctx, const ifac_bsr& A, bool trans);
+// Bitmap (nb x W words) of the pattern of op(A): bit (r, c) set when op(A)_rc is stored.
+Buf<uint32_t> pattern_bitmap(ifac_ctx* ctx, const ifac_bsr& A, bool trans);
+// Row pattern from a bitmap: allocates and fills rp[nb+1], ci[nnzb].
+struct Pattern {
+  Buf<int32_t> rp, ci, row;
+  int64_t nnzb = 0;
+};
+Pattern pattern_from_bitmap(ifac_ctx* ctx, const uint32_t* bm, int nb);
+// Symbolic product pattern of op(A) op(B).
+Pattern product_pattern(ifac_ctx* ctx, const View& arows, const ifac_bsr& B, bool transB, int nb);
+// Union pattern of A, B (nullable) and the diagonal (if diag).
+Pattern union_pattern(ifac_ctx* ctx, const ifac_bsr& A, const ifac_bsr* B, bool diag);
+// Expand row_ptr to a per-block row index.
+void expand_rows(ifac_ctx* ctx, const int32_t* rp, int nb, int32_t* row);
+// Keep blocks with !(norm < tau) of an (uncompacted) matrix; returns the compacted one.
+Mat compact(ifac_ctx* ctx, Mat&& full, const int32_t* row, double tau);
+// Keep blocks selected by a per-block mask (1 keep / 0 drop).
+Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const uint8_t* keep);
+
+// ---- numeric kernels ----
+// FP64 numeric block product into the pattern (rp/ci/row) of C; writes
+// C.val, C.norms; adds the number of block pairs to *pairs_dev.
+void gemm_numeric_fp64(ifac_ctx* ctx, const View& arows, bool tA_blocks, const ifac_bsr& A,
+                       const View& bcols, bool tB_blocks, const ifac_bsr& B, double alpha,
+                       ifac_bsr& C, const int32_t* crow, unsigned long long* pairs_dev);
+void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
+                 double gamma, ifac_bsr& C, const int32_t* crow);
+void block_norms(ifac_ctx* ctx, const ifac_bsr& A, double* norms);
+// per block-row sum of squared block norms
+void row_sq_norms(ifac_ctx* ctx, const ifac_bsr& A, double* rowsq);
+double fro_host(ifac_ctx* ctx, const ifac_bsr& A);
+double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
+Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
+
+// ---- operations used by drivers (ops.cu) ----
+Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau);
+Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma);
+Mat truncate(ifac_ctx* ctx, const ifac_bsr& A, double tau);
+Mat copy_mat(ifac_ctx* ctx, const ifac_bsr& A);
+void validate(const ifac_bsr* A, const char* name);
+
+// ---- leaf routine (leaf.cu) ----
+void leaf_invchol(ifac_ctx* ctx, int count, int nl, double* A, int* info);
+
+// ---- drivers (drivers.cu) ----
+int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S, double tau, double target, const ifac_opts& o,
+                ifac_bsr* Z, ifac_report* rep);
+int lif(ifac_ctx* ctx, const ifac_bsr& S, double tau, double target, const ifac_opts& o,
+        ifac_bsr* Z, ifac_report* rep);
+double resid(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& Z);
+
+// event pair around a profiled launch; prof_collect sums and recycles them
+void prof_begin(ifac_ctx* ctx);
+void prof_end(ifac_ctx* ctx);
+double prof_collect(ifac_ctx* ctx);
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ifac

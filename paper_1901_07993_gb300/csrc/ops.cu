@@ -1,0 +1,89 @@
+// ops.cu -- block-sparse operations composed from the pattern and numeric
+// kernels: the truncated product of Section 5, pattern-union sums,
+// truncation, copies and transposes.
+#include "internal.cuh"
+
+namespace ifac {
+
+// C = alpha op(A) op(B), then removal of blocks with norm < tau.
+//   rows of op(A): A's own rows, or the rows of A^T (blocks then used transposed)
+//   columns of op(B): rows of B^T when B is used as is, or B's rows when B^T
+Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau) {
+  const int nb = A.nb;
+  View arows = view_rows(ctx, A, tA);
+  Pattern P = product_pattern(ctx, arows, B, tB, nb);
+  View bcols = view_rows(ctx, B, !tB);
+  Mat C(ctx);
+  C.m.n = A.n;
+  C.m.bs = A.bs;
+  C.m.nb = nb;
+  C.m.nnzb = P.nnzb;
+  C.m.row_ptr = P.rp.release();
+  C.m.col_idx = P.ci.release();
+  C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
+  C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
+  Buf<unsigned long long> pairs(ctx, 1);
+  IFAC_CK(cudaMemsetAsync(pairs.p, 0, sizeof(unsigned long long), ctx->stream));
+  gemm_numeric_fp64(ctx, arows, tA, A, bcols, tB, B, alpha, C.m, P.row.p, pairs.p);
+  Mat R = compact(ctx, std::move(C), P.row.p, tau);
+  unsigned long long np = 0;
+  to_host(ctx, &np, pairs.p, sizeof(np));
+  ctx->products += 1;
+  ctx->pairs += (int64_t)np;
+  return R;
+}
+
+Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma) {
+  Pattern P = union_pattern(ctx, A, B, gamma != 0.0);
+  Mat C(ctx);
+  C.m.n = A.n;
+  C.m.bs = A.bs;
+  C.m.nb = A.nb;
+  C.m.nnzb = P.nnzb;
+  C.m.row_ptr = P.rp.release();
+  C.m.col_idx = P.ci.release();
+  C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
+  C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
+  add_numeric(ctx, alpha, A, beta, B, gamma, C.m, P.row.p);
+  return C;
+}
+
+__global__ void k_keep_norm(const double* __restrict__ norms, int64_t n, double tau, uint8_t* __restrict__ keep) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n) keep[p] = (norms[p] < tau) ? 0 : 1;
+}
+
+Mat truncate(ifac_ctx* ctx, const ifac_bsr& A, double tau) {
+  Buf<double> tmp;
+  const double* norms = A.norms;
+  if (!norms) {
+    tmp = Buf<double>(ctx, A.nnzb);
+    block_norms(ctx, A, tmp.p);
+    norms = tmp.p;
+  }
+  ifac_bsr a = A;
+  a.norms = const_cast<double*>(norms);
+  Buf<uint8_t> keep(ctx, A.nnzb);
+  if (A.nnzb) {
+    k_keep_norm<<<cdiv(A.nnzb, 256), 256, 0, ctx->stream>>>(norms, A.nnzb, tau, keep.p);
+    IFAC_CK_LAUNCH();
+  }
+  return select_blocks(ctx, a, nullptr, keep.p);
+}
+
+Mat copy_mat(ifac_ctx* ctx, const ifac_bsr& A) {
+  Mat C = mat_alloc(ctx, A.n, A.bs, A.nb, A.nnzb);
+  IFAC_CK(cudaMemcpyAsync(C.m.row_ptr, A.row_ptr, sizeof(int32_t) * (A.nb + 1), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (A.nnzb) {
+    IFAC_CK(cudaMemcpyAsync(C.m.col_idx, A.col_idx, sizeof(int32_t) * A.nnzb, cudaMemcpyDeviceToDevice, ctx->stream));
+    IFAC_CK(cudaMemcpyAsync(C.m.val, A.val, sizeof(double) * (size_t)A.nnzb * A.bs * A.bs, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    if (A.norms)
+      IFAC_CK(cudaMemcpyAsync(C.m.norms, A.norms, sizeof(double) * A.nnzb, cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      block_norms(ctx, C.m, C.m.norms);
+  }
+  return C;
+}
+
+}  // namespace ifac

@@ -1,0 +1,304 @@
+"""Python binding of the C ABI in include/ifac.h (argument marshalling only).
+
+Every computation runs in libifac.so's CUDA kernels; this module converts
+arguments, owns the returned device matrices (freed with ifac_bsr_free) and
+raises IfacError on negative status codes.  It never falls back to another
+implementation: if the library is missing, loading raises.
+
+Function names follow the C ABI: bsr_gemm_trunc, bsr_add, bsr_truncate,
+bsr_fro, bsr_gershgorin, leaf_invchol_batched, inv_factor_refine,
+inv_factor_localized, inv_factor_resid.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libifac.so")
+
+OK, WARN_TARGET_NOT_MET = 0, 1
+ERR_INVALID, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -7
+FP64 = 0
+STOP_RULE, STOP_TARGET, STOP_MAXITER, STOP_FIXED = 1, 2, 3, 4
+
+EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", "ifac_opts_default",
+           "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_add",
+           "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
+           "inv_factor_localized", "inv_factor_resid")
+
+
+class IfacError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ifac error {code}: {msg}")
+        self.code = code
+
+
+class _Bsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("bs", ctypes.c_int32), ("nb", ctypes.c_int32), ("nnzb", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("norms", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("max_iter", ctypes.c_int), ("fixed_iters", ctypes.c_int),
+                ("c_rule", ctypes.c_int), ("leaf_size", ctypes.c_int), ("prec", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("stop_reason", ctypes.c_int), ("levels", ctypes.c_int),
+                ("n_delta", ctypes.c_int), ("beta", ctypes.c_double), ("delta_fro", ctypes.c_double * 64),
+                ("products", ctypes.c_int64), ("block_pairs", ctypes.c_int64), ("nnzb_Z", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("launches", ctypes.c_int64), ("gemm_launches", ctypes.c_int64),
+                ("gemm_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libifac.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    p, i32, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    PB = ctypes.POINTER(_Bsr)
+    sig = {
+        "ifac_create": ([ctypes.POINTER(p), p, p], i32),
+        "ifac_destroy": ([p], None),
+        "ifac_set_stream": ([p, p], i32),
+        "ifac_last_error": ([p], ctypes.c_char_p),
+        "ifac_opts_default": ([ctypes.POINTER(_Opts)], None),
+        "ifac_bsr_upload": ([p, i64, i32, i32, i64, p, p, p, PB], i32),
+        "ifac_bsr_download": ([p, PB, p, p, p], i32),
+        "ifac_bsr_free": ([p, PB], None),
+        "bsr_gemm_trunc": ([p, PB, i32, PB, i32, d, d, i32, PB], i32),
+        "bsr_add": ([p, d, PB, d, PB, d, PB], i32),
+        "bsr_truncate": ([p, PB, d, PB], i32),
+        "bsr_fro": ([p, PB, ctypes.POINTER(d)], i32),
+        "bsr_gershgorin": ([p, PB, ctypes.POINTER(d)], i32),
+        "leaf_invchol_batched": ([p, i32, i32, p, p, p], i32),
+        "inv_factor_refine": ([p, PB, d, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
+        "inv_factor_localized": ([p, PB, d, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
+        "inv_factor_resid": ([p, PB, PB, ctypes.POINTER(d)], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _current_stream() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+class Context:
+    """A library context on the current device and (by default) torch's current stream."""
+
+    def __init__(self, stream: int | None = None):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.ifac_create(ctypes.byref(h), ctypes.c_void_p(_current_stream() if stream is None else stream),
+                                  None)
+        if rc != 0:
+            raise IfacError(rc, "ifac_create failed")
+        self.h = h
+
+    def check(self, rc: int) -> int:
+        if rc < 0:
+            raise IfacError(rc, self.lib.ifac_last_error(self.h).decode())
+        return rc
+
+    def set_stream(self, stream: int):
+        self.check(self.lib.ifac_set_stream(self.h, ctypes.c_void_p(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ifac_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceBSR:
+    """A library-allocated device matrix (freed when garbage-collected)."""
+
+    def __init__(self, ctx: Context, raw: _Bsr):
+        self.ctx = ctx
+        self.raw = raw
+
+    n = property(lambda self: int(self.raw.n))
+    bs = property(lambda self: int(self.raw.bs))
+    nb = property(lambda self: int(self.raw.nb))
+    nnzb = property(lambda self: int(self.raw.nnzb))
+
+    def ptr(self):
+        return ctypes.byref(self.raw)
+
+    def download(self) -> "HostMatrix":
+        rp = np.zeros(self.nb + 1, dtype=np.int32)
+        ci = np.zeros(self.nnzb, dtype=np.int32)
+        v = np.zeros((self.nnzb, self.bs, self.bs))
+        self.ctx.check(self.ctx.lib.ifac_bsr_download(self.ctx.h, self.ptr(), rp.ctypes.data, ci.ctypes.data,
+                                                      v.ctypes.data))
+        return HostMatrix(self.n, self.bs, rp, ci, v)
+
+    def free(self):
+        if self.raw is not None and self.ctx.h:
+            self.ctx.lib.ifac_bsr_free(self.ctx.h, ctypes.byref(self.raw))
+        self.raw = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+@dataclass
+class HostMatrix:
+    n: int
+    bs: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nb(self):
+        return len(self.row_ptr) - 1
+
+    @property
+    def nnzb(self):
+        return len(self.col_idx)
+
+
+@dataclass
+class Report:
+    sweeps: int
+    stop_reason: int
+    levels: int
+    beta: float
+    delta_fro: list
+    products: int
+    block_pairs: int
+    nnzb_Z: int
+    flops: float
+    launches: int = 0
+    gemm_launches: int = 0
+    gemm_ms: float = 0.0
+    status: int = 0
+
+
+def upload(ctx: Context, host) -> DeviceBSR:
+    """Copy a host BSR (n, bs, row_ptr, col_idx, val) to the device."""
+    rp = np.ascontiguousarray(host.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(host.col_idx, dtype=np.int32)
+    v = np.ascontiguousarray(host.val, dtype=np.float64)
+    raw = _Bsr()
+    ctx.check(ctx.lib.ifac_bsr_upload(ctx.h, int(host.n), int(host.bs), len(rp) - 1, len(ci), rp.ctypes.data,
+                                      ci.ctypes.data, v.ctypes.data, ctypes.byref(raw)))
+    return DeviceBSR(ctx, raw)
+
+
+def opts(m: int = 2, max_iter: int = 50, fixed_iters: int = 0, c_rule: int = 0, leaf_size: int = 512,
+         prec: int = FP64, profile: bool = False) -> _Opts:
+    o = _Opts()
+    load().ifac_opts_default(ctypes.byref(o))
+    o.m, o.max_iter, o.fixed_iters, o.c_rule, o.leaf_size, o.prec = m, max_iter, fixed_iters, c_rule, leaf_size, prec
+    o.profile = int(profile)
+    return o
+
+
+def _report(r: _Report, rc: int) -> Report:
+    return Report(r.sweeps, r.stop_reason, r.levels, r.beta, [r.delta_fro[i] for i in range(r.n_delta)],
+                  r.products, r.block_pairs, r.nnzb_Z, r.flops, r.launches, r.gemm_launches, r.gemm_ms, rc)
+
+
+def bsr_gemm_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, transB: bool, alpha: float = 1.0,
+                   tau: float = 0.0, prec: int = FP64) -> DeviceBSR:
+    C = _Bsr()
+    ctx.check(ctx.lib.bsr_gemm_trunc(ctx.h, A.ptr(), int(transA), B.ptr(), int(transB), alpha, tau, prec,
+                                     ctypes.byref(C)))
+    return DeviceBSR(ctx, C)
+
+
+def bsr_add(ctx: Context, alpha: float, A: DeviceBSR, beta: float = 0.0, B: DeviceBSR | None = None,
+            gamma: float = 0.0) -> DeviceBSR:
+    C = _Bsr()
+    ctx.check(ctx.lib.bsr_add(ctx.h, alpha, A.ptr(), beta, B.ptr() if B is not None else None, gamma,
+                              ctypes.byref(C)))
+    return DeviceBSR(ctx, C)
+
+
+def bsr_truncate(ctx: Context, A: DeviceBSR, tau: float) -> DeviceBSR:
+    C = _Bsr()
+    ctx.check(ctx.lib.bsr_truncate(ctx.h, A.ptr(), tau, ctypes.byref(C)))
+    return DeviceBSR(ctx, C)
+
+
+def bsr_fro(ctx: Context, A: DeviceBSR) -> float:
+    out = ctypes.c_double()
+    ctx.check(ctx.lib.bsr_fro(ctx.h, A.ptr(), ctypes.byref(out)))
+    return out.value
+
+
+def bsr_gershgorin(ctx: Context, A: DeviceBSR) -> float:
+    out = ctypes.c_double()
+    ctx.check(ctx.lib.bsr_gershgorin(ctx.h, A.ptr(), ctypes.byref(out)))
+    return out.value
+
+
+def leaf_invchol_batched(ctx: Context, S, Z=None, info=None):
+    """S: CUDA float64 tensor [count, nl, nl]; returns (Z, info) tensors."""
+    import torch
+    count, nl = S.shape[0], S.shape[1]
+    assert S.is_cuda and S.dtype == torch.float64 and S.is_contiguous()
+    if Z is None:
+        Z = torch.empty_like(S)
+    if info is None:
+        info = torch.zeros(count, dtype=torch.int32, device=S.device)
+    rc = ctx.lib.leaf_invchol_batched(ctx.h, count, nl, S.data_ptr(), Z.data_ptr(), info.data_ptr())
+    if rc != ERR_NOT_SPD:
+        ctx.check(rc)
+    return Z, info, rc
+
+
+def inv_factor_refine(ctx: Context, S: DeviceBSR, tau: float, target: float, o: _Opts | None = None):
+    Z = _Bsr()
+    rep = _Report()
+    rc = ctx.check(ctx.lib.inv_factor_refine(ctx.h, S.ptr(), tau, target, ctypes.byref(o or opts()),
+                                             ctypes.byref(Z), ctypes.byref(rep)))
+    return DeviceBSR(ctx, Z), _report(rep, rc)
+
+
+def inv_factor_localized(ctx: Context, S: DeviceBSR, tau: float, target: float, o: _Opts | None = None):
+    Z = _Bsr()
+    rep = _Report()
+    rc = ctx.check(ctx.lib.inv_factor_localized(ctx.h, S.ptr(), tau, target, ctypes.byref(o or opts()),
+                                                ctypes.byref(Z), ctypes.byref(rep)))
+    return DeviceBSR(ctx, Z), _report(rep, rc)
+
+
+def inv_factor_resid(ctx: Context, S: DeviceBSR, Z: DeviceBSR) -> float:
+    out = ctypes.c_double()
+    ctx.check(ctx.lib.inv_factor_resid(ctx.h, S.ptr(), Z.ptr(), ctypes.byref(out)))
+    return out.value
