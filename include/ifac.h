@@ -51,6 +51,7 @@ extern "C" {
 #define IFAC_ERR_OOM (-4)           /* allocator returned NULL */
 #define IFAC_ERR_CUDA (-5)          /* a CUDA call failed */
 #define IFAC_ERR_UNSUPPORTED (-7)   /* block size / precision not built */
+#define IFAC_ERR_TOO_LARGE (-8)     /* request exceeds a fixed scratch area */
 
 /* Product precision (the arithmetic of the block products). */
 #define IFAC_FP64 0
@@ -184,6 +185,33 @@ int bsr_gershgorin(ifac_ctx* ctx, const ifac_bsr* A, double* out);
  * or j+1 when pivot j of matrix k was not positive (that Z is undefined).
  * Returns IFAC_ERR_NOT_SPD when any info is non-zero.  nl <= 1024. */
 int leaf_invchol_batched(ifac_ctx* ctx, int count, int nl, const double* S, double* Z, int* info);
+
+/* The same batched leaf inverse Cholesky for callers that cannot allocate
+ * device memory when they call it: code running while a stream is being
+ * captured into a CUDA graph, frameworks that own the whole device-memory
+ * budget, or loops that cannot afford an allocation's synchronisation.  The
+ * paper has no counterpart; this is a library convenience.
+ *
+ * Arguments as leaf_invchol_batched, except that `stream` (a cudaStream_t)
+ * replaces the context.  It allocates nothing: its scratch (the diagonal-tile
+ * inverses, count * ceil(nl/32) * 1024 doubles, plus count * np * np doubles
+ * of identity-padded copies when nl is not a multiple of 32, np = nl rounded
+ * up to 32) lives in one fixed 32 MiB device array (4 Mi doubles) that every
+ * GPU loading the library holds until exit.  Larger requests return
+ * IFAC_ERR_TOO_LARGE and touch nothing.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress, with that device current); make this first call
+ *    before any stream capture.
+ *  - The call is asynchronous on `stream`: it returns after enqueueing and
+ *    does not read info back; info[k] (device) is set as in
+ *    leaf_invchol_batched once the stream reaches it.
+ *  - Every call uses the same scratch array, so calls whose work overlaps on
+ *    the GPU (other streams, other host threads) race; serialise them.  The
+ *    scratch keeps the previous call's contents; nothing in it needs to start
+ *    at zero, since every element is written before it is read.
+ * Returns IFAC_OK, IFAC_ERR_INVALID (bad arguments), IFAC_ERR_TOO_LARGE or
+ * IFAC_ERR_CUDA (a launch or copy failed). */
+int leaf_invchol_batched_noalloc(void* stream, int count, int nl, const double* S, double* Z, int* info);
 
 /* ---------------------------------------------------------------- */
 /* Factorizations                                                    */

@@ -226,3 +226,31 @@ void leaf_invchol(ifac_ctx* ctx, int count, int nl, double* A, int* info) {
 }
 
 }  // namespace ifac
+
+namespace ifac {
+
+// Same computation as leaf_invchol, with the scratch supplied by the caller
+// instead of allocated: wd holds count * ceil(nl/32) * 32 * 32 doubles and,
+// when nl is not a multiple of 32, pad holds count * np * np doubles
+// (np = nl rounded up to 32).  Returns the launch status.
+cudaError_t leaf_invchol_launch_scratch(cudaStream_t stream, int count, int nl, double* A, int* info, double* wd,
+                                        double* pad) {
+  if (count == 0) return cudaSuccess;
+  const int np = ((nl + TB - 1) / TB) * TB;
+  if (np == nl) {
+    k_leaf_invchol<<<count, NT, 0, stream>>>(A, nl, info, wd);
+    return cudaGetLastError();
+  }
+  int64_t tot = (int64_t)count * np * np;
+  k_pad_identity<<<cdiv(tot, 256), 256, 0, stream>>>(A, nl, pad, np, count);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_leaf_invchol<<<count, NT, 0, stream>>>(pad, np, info, wd);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t tot2 = (int64_t)count * nl * nl;
+  k_unpad<<<cdiv(tot2, 256), 256, 0, stream>>>(pad, np, A, nl, count);
+  return cudaGetLastError();
+}
+
+}  // namespace ifac

@@ -22,13 +22,14 @@ LIB_PATH = os.path.join(_HERE, "libifac.so")
 
 OK, WARN_TARGET_NOT_MET = 0, 1
 ERR_INVALID, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -7
+ERR_TOO_LARGE = -8
 FP64 = 0
 STOP_RULE, STOP_TARGET, STOP_MAXITER, STOP_FIXED = 1, 2, 3, 4
 
 EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", "ifac_opts_default",
            "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_add",
            "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
-           "inv_factor_localized", "inv_factor_resid")
+           "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc")
 
 
 class IfacError(RuntimeError):
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
         "inv_factor_refine": ([p, PB, d, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
         "inv_factor_localized": ([p, PB, d, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
         "inv_factor_resid": ([p, PB, PB, ctypes.POINTER(d)], i32),
+        "leaf_invchol_batched_noalloc": ([p, i32, i32, p, p, p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -302,3 +304,11 @@ def inv_factor_resid(ctx: Context, S: DeviceBSR, Z: DeviceBSR) -> float:
     out = ctypes.c_double()
     ctx.check(ctx.lib.inv_factor_resid(ctx.h, S.ptr(), Z.ptr(), ctypes.byref(out)))
     return out.value
+
+
+def leaf_invchol_batched_noalloc(stream: int, S, Z, info) -> int:
+    """Allocation-free leaf routine (see include/ifac.h): S, Z float64 CUDA
+    tensors [count, nl, nl], info int32 CUDA tensor [count]; enqueues on
+    `stream` and returns the status code without waiting."""
+    count, nl = S.shape[0], S.shape[1]
+    return load().leaf_invchol_batched_noalloc(stream, count, nl, S.data_ptr(), Z.data_ptr(), info.data_ptr())
