@@ -50,11 +50,14 @@ extern "C" {
 #define IFAC_ERR_NO_CONVERGENCE (-3)/* max_iter reached */
 #define IFAC_ERR_OOM (-4)           /* allocator returned NULL */
 #define IFAC_ERR_CUDA (-5)          /* a CUDA call failed */
+#define IFAC_ERR_TIMEOUT (-6)       /* a bounded device-side wait expired */
 #define IFAC_ERR_UNSUPPORTED (-7)   /* block size / precision not built */
 #define IFAC_ERR_TOO_LARGE (-8)     /* request exceeds a fixed scratch area */
 
 /* Product precision (the arithmetic of the block products). */
-#define IFAC_FP64 0
+#define IFAC_FP64 0 /* FP64 inputs, FP64 accumulation (FP64 pipe) */
+#define IFAC_TF32 1 /* inputs rounded to TF32, FP32 accumulation (tensor cores, bs = 64) */
+#define IFAC_BF16 2 /* inputs rounded to BF16, FP32 accumulation (tensor cores, bs = 64) */
 
 /* Stop reasons reported by the refinement drivers. */
 #define IFAC_STOP_RULE 1     /* ||delta_{i+1}||_F > ||delta_i||_F^(m+1) (Section 2.2) */
@@ -160,7 +163,12 @@ void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a);
  * block with Frobenius norm strictly below tau is removed (Section 5: blocks
  * with norm smaller than the threshold are removed after every product).
  * The output pattern before truncation is every (I, J) for which some K has
- * op(A)_IK and op(B)_KJ stored.  A and B: same n and bs.  prec: IFAC_FP64. */
+ * op(A)_IK and op(B)_KJ stored.  A and B: same n and bs.  prec: IFAC_FP64 (any
+ * bs in {16, 32, 64}), or IFAC_TF32 / IFAC_BF16 (bs = 64): the operands are
+ * rounded to that format (BF16 round-to-nearest-even from FP64; TF32 via FP32,
+ * round-to-nearest-even, then round-half-away), products are accumulated in
+ * FP32 on the tensor cores, and the result, its norms and the truncation are
+ * FP64.  IFAC_ERR_TIMEOUT if a device pipeline wait expired. */
 int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB,
                    double alpha, double tau, int prec, ifac_bsr* C);
 

@@ -1,0 +1,623 @@
+// gemm_tc.cu -- tensor-core numeric phase of C = alpha op(A) op(B) for
+// 64 x 64 blocks, with BF16 or TF32 inputs and FP32 accumulation in tensor
+// memory (the low-precision products of the mixed-precision schedule).
+//
+// Operands.  op(A) and op(B) are first copied in their own CSR order to a
+// low-precision array, each block stored K-major (op(A)_IK as [i][k],
+// op(B)_KJ as [j][k]), so that a transposed use of an FP64 matrix costs only
+// a transposed copy; one all-zero block is appended to each copy.
+//
+// Tiles.  The output is cut into tiles of TM x TN blocks (M = 128 rows, N =
+// 256 (BF16) or 128 (TF32) columns); only tiles that hold a block of C's
+// pattern are visited, by a persistent grid.  For a tile, K runs over the
+// union of the stored K's of its TM op(A) block rows; a block missing inside
+// the tile (op(A)_IK or op(B)_KJ not stored) is read from the zero block, so
+// every K step is one dense M x N x 64 contraction.
+//
+// Roles (192 threads, one CTA per SM):
+//   warp 0      : TMA producer -- one 64-row box per block and 128-byte
+//                 atom, 128-byte swizzle, into a STAGES-deep ring;
+//   warp 1      : tensor-memory allocation and the single MMA-issuing
+//                 thread (tcgen05.mma, accumulate in TMEM, tcgen05.commit
+//                 releases ring slots and hands the accumulator over);
+//   warps 2..5  : epilogue -- tcgen05.ld of the accumulator, alpha, FP64
+//                 Frobenius norm per output block, FP64 store into C.
+// Every mbarrier wait is bounded; on expiry the CTA records an error flag,
+// drains its own copies and MMAs, releases tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace ifac {
+namespace tc {
+
+constexpr int BS = 64;
+constexpr int TM = 2;
+constexpr int NTHREADS = 192;
+constexpr long long WAIT_LIMIT = 1ll << 27;
+
+template <int ELT>
+struct Cfg {
+  static constexpr int ATOM_ELEMS = 128 / ELT;          // elements in one 128-byte row
+  static constexpr int ATOMS = BS / ATOM_ELEMS;         // 128-byte atoms along K per block
+  static constexpr int MMA_K = 32 / ELT;                // 32 bytes of K per tcgen05.mma
+  static constexpr int KSTEPS = BS / MMA_K;             // MMAs per K block
+  static constexpr int TN = (ELT == 2) ? 4 : 2;         // block columns per tile
+  static constexpr int N = TN * BS;
+  static constexpr int M = TM * BS;
+  static constexpr int A_ATOM_BYTES = M * 128;          // one K atom of the A tile
+  static constexpr int B_ATOM_BYTES = N * 128;
+  static constexpr int A_BYTES = ATOMS * A_ATOM_BYTES;
+  static constexpr int B_BYTES = ATOMS * B_ATOM_BYTES;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (ELT == 2) ? 4 : 3;
+  static constexpr int TMEM_COLS = N;                   // FP32 accumulator columns
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+  static constexpr uint32_t TX_BYTES = (uint32_t)(TM + TN) * BS * BS * ELT;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase of `parity` completed; false on the CTA's
+// abort flag or (after WAIT_LIMIT polls) on timeout, which raises both flags.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* gerr,
+                                          bool honour_abort = true) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (honour_abort && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(gerr, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B format, both K-major, N, M.
+template <int ELT>
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4)                                       // D = F32
+         | ((ELT == 2 ? 1u : 2u) << 7)                   // A = BF16 / TF32
+         | ((ELT == 2 ? 1u : 2u) << 10)                  // B = BF16 / TF32
+         | ((uint32_t)(Cfg<ELT>::N >> 3) << 17)          // N
+         | ((uint32_t)(Cfg<ELT>::M >> 4) << 24);         // M
+}
+
+template <int ELT>
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  constexpr uint32_t idesc = instr_desc<ELT>();
+  if constexpr (ELT == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 columns of FP32 from tensor memory into 32 registers
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, int lo, int hi, int v) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+struct TileArgs {
+  const int32_t* tiles;  // packed (tile_row << 32 | tile_col) as two int32: [2*t] row, [2*t+1] col
+  int ntiles;
+  int nb;
+  const int32_t* arp;    // op(A) CSR
+  const int32_t* aci;
+  int a_zero;            // index of the zero block of the op(A) copy
+  const int32_t* brp;    // op(B) CSR (rows K)
+  const int32_t* bci;
+  int b_zero;
+  const int32_t* crp;    // C pattern
+  const int32_t* cci;
+  double* cval;
+  double* cnorm;
+  double alpha;
+  int* err;
+};
+
+template <int ELT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TileArgs args) {
+  using C = Cfg<ELT>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[C::STAGES], empty_bar[C::STAGES];
+  __shared__ __align__(8) uint64_t acc_full, acc_empty, drain_bar;
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ double partial[4][C::TN];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_full), 1);
+    mbar_init(smem_u32(&acc_empty), 1);
+    mbar_init(smem_u32(&drain_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
+                 "r"((uint32_t)C::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_slot;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, last_parity = 0;  // per stage: filled at least once / parity of the last fill
+      bool ok = true;
+      for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+        const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
+        int pa[TM], ea[TM];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) {
+          const int I = I0 + r;
+          pa[r] = (I < args.nb) ? args.arp[I] : 0;
+          ea[r] = (I < args.nb) ? args.arp[I + 1] : 0;
+        }
+        for (;;) {
+          int K = 0x7fffffff;
+#pragma unroll
+          for (int r = 0; r < TM; ++r)
+            if (pa[r] < ea[r]) K = min(K, args.aci[pa[r]]);
+          if (K == 0x7fffffff) break;
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
+          const uint32_t fb = smem_u32(&full_bar[stage]);
+          mbar_expect_tx(fb, C::TX_BYTES);
+          issued_mask |= 1u << stage;
+          last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+          const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
+          const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+          for (int r = 0; r < TM; ++r) {
+            int idx = args.a_zero;
+            if (pa[r] < ea[r] && args.aci[pa[r]] == K) idx = pa[r]++;
+#pragma unroll
+            for (int a = 0; a < C::ATOMS; ++a)
+              tma_load_2d(sa + a * C::A_ATOM_BYTES + r * BS * 128, &mapA, a * C::ATOM_ELEMS, idx * BS, fb);
+          }
+          int pb = args.brp[K];
+          const int eb = args.brp[K + 1];
+          pb = lower_bound_i32(args.bci, pb, eb, J0);
+#pragma unroll
+          for (int c = 0; c < C::TN; ++c) {
+            int idx = args.b_zero;
+            if (pb < eb && args.bci[pb] == J0 + c) idx = pb++;
+#pragma unroll
+            for (int a = 0; a < C::ATOMS; ++a)
+              tma_load_2d(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS, idx * BS, fb);
+          }
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      // copies this thread issued must land before the CTA exits
+      for (int s = 0; s < C::STAGES; ++s)
+        if (issued_mask & (1u << s))
+          mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer ------------------------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+        const int I0 = args.tiles[2 * t] * TM;
+        // number of K steps: size of the union of the op(A) rows' columns
+        int pa[TM], ea[TM], nk = 0;
+#pragma unroll
+        for (int r = 0; r < TM; ++r) {
+          const int I = I0 + r;
+          pa[r] = (I < args.nb) ? args.arp[I] : 0;
+          ea[r] = (I < args.nb) ? args.arp[I + 1] : 0;
+        }
+        for (;;) {
+          int K = 0x7fffffff;
+#pragma unroll
+          for (int r = 0; r < TM; ++r)
+            if (pa[r] < ea[r]) K = min(K, args.aci[pa[r]]);
+          if (K == 0x7fffffff) break;
+#pragma unroll
+          for (int r = 0; r < TM; ++r)
+            if (pa[r] < ea[r] && args.aci[pa[r]] == K) ++pa[r];
+          ++nk;
+        }
+        if (!mbar_wait(smem_u32(&acc_empty), acc_phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
+        tc_fence_after();
+        for (int k = 0; k < nk; ++k) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, args.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
+          const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < C::KSTEPS; ++kk) {
+            const int atom = kk / (C::ATOM_ELEMS / C::MMA_K), off = (kk % (C::ATOM_ELEMS / C::MMA_K)) * 32;
+            mma_issue<ELT>(tmem, smem_desc(sa + atom * C::A_ATOM_BYTES + off),
+                           smem_desc(sb + atom * C::B_ATOM_BYTES + off), (k > 0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&empty_bar[stage]));
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&acc_full));
+        acc_phase ^= 1u;
+      }
+      // every MMA this thread issued completes before tensor memory is released
+      mma_commit(smem_u32(&drain_bar));
+      mbar_wait(smem_u32(&drain_bar), 0, &abort_flag, args.err, false);
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const int q = warp & 3;            // tensor-memory lane quarter of this warp
+    const int row = q * 32 + lane;     // accumulator row 0..127
+    const int r_blk = row / BS, lr = row % BS;
+    const int et = threadIdx.x - 64;   // 0..127
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x) {
+      const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
+      const bool got = mbar_wait(smem_u32(&acc_full), acc_phase, &abort_flag, args.err);
+      __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
+      const int I = I0 + r_blk;
+#pragma unroll 1
+      for (int c = 0; c < C::TN; ++c) {
+        const int J = J0 + c;
+        int p = -1;
+        if (I < args.nb && J < args.nb) {
+          const int lo = args.crp[I], hi = args.crp[I + 1];
+          const int k = lower_bound_i32(args.cci, lo, hi, J);
+          if (k < hi && args.cci[k] == J) p = k;
+        }
+        double ss = 0.0;
+#pragma unroll
+        for (int h = 0; h < BS / 32; ++h) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * BS + h * 32), v);
+          if (p >= 0) {
+            double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
+#pragma unroll
+            for (int e = 0; e < 32; e += 2) {
+              double2 w;
+              w.x = (double)v[e] * args.alpha;
+              w.y = (double)v[e + 1] * args.alpha;
+              ss = fma(w.x, w.x, ss);
+              ss = fma(w.y, w.y, ss);
+              *reinterpret_cast<double2*>(dst + e) = w;
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) partial[q][c] = ss;
+      }
+      tc_fence_before();
+      epi_bar();
+      // norms: block row rb is covered by lane quarters 2rb and 2rb+1, summed in that order
+      if (et < TM * C::TN) {
+        const int rb = et / C::TN, c = et % C::TN;
+        const int Ib = I0 + rb, J = J0 + c;
+        if (Ib < args.nb && J < args.nb) {
+          const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
+          const int k = lower_bound_i32(args.cci, lo, hi, J);
+          if (k < hi && args.cci[k] == J) args.cnorm[k] = sqrt(partial[2 * rb][c] + partial[2 * rb + 1][c]);
+        }
+      }
+      epi_bar();
+      if (et == 0) mbar_arrive(smem_u32(&acc_empty));
+      acc_phase ^= 1u;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operand conversion and tile list
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// dst[q] = low-precision copy of block src[q] of X (K-major: transposed when tr)
+template <int ELT>
+__global__ void k_convert(const double* __restrict__ val, const int32_t* __restrict__ src, int64_t nblk, int tr,
+                          void* __restrict__ dst) {
+  constexpr int BSZ = BS * BS;
+  for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
+    const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
+    for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
+      const int r = e / BS, c = e % BS;
+      const double x = tr ? s[c * BS + r] : s[e];
+      if constexpr (ELT == 2) {
+        reinterpret_cast<__nv_bfloat16*>(dst)[(size_t)qb * BSZ + e] = __double2bfloat16(x);
+      } else {
+        reinterpret_cast<uint32_t*>(dst)[(size_t)qb * BSZ + e] = f32_to_tf32(__double2float_rn(x));
+      }
+    }
+  }
+}
+
+// flag[tile] = 1 for every tile holding a block of C's pattern
+__global__ void k_tile_flags(const int32_t* __restrict__ row, const int32_t* __restrict__ ci, int64_t nnz, int tn,
+                             int ntc, uint8_t* __restrict__ flag) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  flag[(size_t)(row[p] / TM) * ntc + ci[p] / tn] = 1;
+}
+
+__global__ void k_tile_list(const uint8_t* __restrict__ flag, int ntr, int ntc, int32_t* __restrict__ out,
+                            int* __restrict__ count) {
+  // single CTA; tiles come out in row-major tile order
+  __shared__ int wcount[32];
+  __shared__ int base, chunk_total;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int64_t tot = (int64_t)ntr * ntc;
+  for (int64_t s = 0; s < tot; s += blockDim.x) {
+    const int64_t i = s + threadIdx.x;
+    const bool f = i < tot && flag[i];
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcount[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int k = 0; k < nw; ++k) {
+        const int c = wcount[k];
+        wcount[k] = acc;
+        acc += c;
+      }
+      chunk_total = acc;
+    }
+    __syncthreads();
+    if (f) {
+      const int pos = base + wcount[w] + __popc(m & ((1u << lane) - 1u));
+      out[2 * pos] = (int32_t)(i / ntc);
+      out[2 * pos + 1] = (int32_t)(i % ntc);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += chunk_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+// pairs += |row K of op(B)| for every stored block (I, K) of op(A): the number
+// of (I, K, J) block triples, i.e. of stored-block products
+__global__ void k_count_pairs(const int32_t* __restrict__ arp, const int32_t* __restrict__ aci, int nb,
+                              const int32_t* __restrict__ brp, unsigned long long* __restrict__ pairs) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  unsigned long long c = 0;
+  if (row < nb)
+    for (int p = arp[row] + lane; p < arp[row + 1]; p += 32) c += (unsigned long long)(brp[aci[p] + 1] - brp[aci[p]]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0 && c) atomicAdd(pairs, c);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    IFAC_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) fail(IFAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D view of a low-precision block array: rows = (nblk) * 64, 64 elements per
+// row; boxes of one 128-byte atom x 64 rows, 128-byte swizzle
+template <int ELT>
+static CUtensorMap make_map(void* base, int64_t nblk) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)BS, (cuuint64_t)nblk * BS};
+  cuuint64_t strides[1] = {(cuuint64_t)BS * ELT};
+  cuuint32_t box[2] = {(cuuint32_t)Cfg<ELT>::ATOM_ELEMS, (cuuint32_t)BS};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encoder()(&m, ELT == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(IFAC_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return m;
+}
+
+template <int ELT>
+static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
+                const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, unsigned long long* pairs) {
+  using Cf = Cfg<ELT>;
+  const int nb = A.nb;
+  const size_t bbytes = (size_t)BS * BS * ELT;
+  // low-precision, K-major copies of op(A) and op(B) plus one zero block each
+  Buf<uint8_t> la(ctx, (size_t)(A.nnzb + 1) * bbytes), lb(ctx, (size_t)(B.nnzb + 1) * bbytes);
+  IFAC_CK(cudaMemsetAsync(la.p + (size_t)A.nnzb * bbytes, 0, bbytes, ctx->stream));
+  IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
+  if (A.nnzb) {
+    k_convert<ELT><<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, 0, ctx->stream>>>(A.val, arows.src, A.nnzb,
+                                                                                       tA ? 1 : 0, la.p);
+    IFAC_CK_LAUNCH();
+  }
+  if (B.nnzb) {
+    k_convert<ELT><<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, 0, ctx->stream>>>(B.val, brows.src, B.nnzb,
+                                                                                       tB ? 0 : 1, lb.p);
+    IFAC_CK_LAUNCH();
+  }
+  const CUtensorMap mapA = make_map<ELT>(la.p, A.nnzb + 1);
+  const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
+  // tiles holding a block of C's pattern
+  const int ntr = cdiv(nb, TM), ntc = cdiv(nb, Cf::TN);
+  Buf<uint8_t> flags(ctx, (size_t)ntr * ntc);
+  Buf<int32_t> tiles(ctx, (size_t)2 * ntr * ntc);
+  Buf<int> cnt(ctx, 2);  // [0] tiles, [1] error flag
+  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntr * ntc, ctx->stream));
+  IFAC_CK(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int), ctx->stream));
+  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, Cf::TN, ntc, flags.p);
+  IFAC_CK_LAUNCH();
+  k_tile_list<<<1, 1024, 0, ctx->stream>>>(flags.p, ntr, ntc, tiles.p, cnt.p);
+  IFAC_CK_LAUNCH();
+  k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
+  IFAC_CK_LAUNCH();
+  int ntiles = 0;
+  to_host(ctx, &ntiles, cnt.p, sizeof(int));
+  if (ntiles == 0) return;
+  static bool attr = false;
+  if (!attr) {
+    IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
+    attr = true;
+  }
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  TileArgs args;
+  args.tiles = tiles.p;
+  args.ntiles = ntiles;
+  args.nb = nb;
+  args.arp = arows.rp;
+  args.aci = arows.ci;
+  args.a_zero = (int)A.nnzb;
+  args.brp = brows.rp;
+  args.bci = brows.ci;
+  args.b_zero = (int)B.nnzb;
+  args.crp = C.row_ptr;
+  args.cci = C.col_idx;
+  args.cval = C.val;
+  args.cnorm = C.norms;
+  args.alpha = alpha;
+  args.err = cnt.p + 1;
+  prof_begin(ctx);
+  k_gemm_tc<ELT><<<std::min(ntiles, sms), NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mapA, mapB, args);
+  IFAC_CK_LAUNCH();
+  prof_end(ctx);
+  ++ctx->gemm_launches;
+  int err = 0;
+  to_host(ctx, &err, cnt.p + 1, sizeof(int));
+  if (err) fail(IFAC_ERR_TIMEOUT, "tensor-core block product: a pipeline wait timed out");
+}
+
+}  // namespace tc
+
+void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
+                     bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
+                     unsigned long long* pairs_dev) {
+  if (A.bs != tc::BS) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block product built for bs = 64");
+  if (C.nnzb == 0) return;
+  if (prec == IFAC_BF16) tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
+  else if (prec == IFAC_TF32) tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
+  else fail(IFAC_ERR_UNSUPPORTED, "unknown precision");
+}
+
+}  // namespace ifac

@@ -135,6 +135,11 @@ Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const ui
 void gemm_numeric_fp64(ifac_ctx* ctx, const View& arows, bool tA_blocks, const ifac_bsr& A,
                        const View& bcols, bool tB_blocks, const ifac_bsr& B, double alpha,
                        ifac_bsr& C, const int32_t* crow, unsigned long long* pairs_dev);
+// Tensor-core (TF32/BF16 in, FP32 accumulate) numeric block product, bs = 64.
+// brows: rows of op(B).
+void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
+                     bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
+                     unsigned long long* pairs_dev);
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
                  double gamma, ifac_bsr& C, const int32_t* crow);
 void block_norms(ifac_ctx* ctx, const ifac_bsr& A, double* norms);
@@ -145,7 +150,8 @@ double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
 Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 
 // ---- operations used by drivers (ops.cu) ----
-Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau);
+Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
+         int prec = IFAC_FP64);
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma);
 Mat truncate(ifac_ctx* ctx, const ifac_bsr& A, double tau);
 Mat copy_mat(ifac_ctx* ctx, const ifac_bsr& A);

@@ -8,11 +8,11 @@ namespace ifac {
 // C = alpha op(A) op(B), then removal of blocks with norm < tau.
 //   rows of op(A): A's own rows, or the rows of A^T (blocks then used transposed)
 //   columns of op(B): rows of B^T when B is used as is, or B's rows when B^T
-Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau) {
+Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
+         int prec) {
   const int nb = A.nb;
   View arows = view_rows(ctx, A, tA);
   Pattern P = product_pattern(ctx, arows, B, tB, nb);
-  View bcols = view_rows(ctx, B, !tB);
   Mat C(ctx);
   C.m.n = A.n;
   C.m.bs = A.bs;
@@ -24,7 +24,13 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
   Buf<unsigned long long> pairs(ctx, 1);
   IFAC_CK(cudaMemsetAsync(pairs.p, 0, sizeof(unsigned long long), ctx->stream));
-  gemm_numeric_fp64(ctx, arows, tA, A, bcols, tB, B, alpha, C.m, P.row.p, pairs.p);
+  if (prec == IFAC_FP64) {
+    View bcols = view_rows(ctx, B, !tB);
+    gemm_numeric_fp64(ctx, arows, tA, A, bcols, tB, B, alpha, C.m, P.row.p, pairs.p);
+  } else {
+    View brows = view_rows(ctx, B, tB);
+    gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, pairs.p);
+  }
   Mat R = compact(ctx, std::move(C), P.row.p, tau);
   unsigned long long np = 0;
   to_host(ctx, &np, pairs.p, sizeof(np));

@@ -1,0 +1,98 @@
+"""Tensor-core (tcgen05) block products with TF32 / BF16 inputs and FP32
+accumulation, through the C ABI, against the CPU oracle's FP64 product of the
+same inputs rounded the same way (BF16: round-to-nearest-even from FP64;
+TF32: FP64 -> FP32 round-to-nearest-even, then round half away from zero to
+10 fraction bits).  With identically rounded inputs the only difference left
+is FP32 accumulation, bounded element-wise by K * 2^-22 * (|A||B|)_ij."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_07993_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TF32, BF16 = 1, 2
+
+
+def round_bf16(x):
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def round_tf32(x):
+    u = x.astype(np.float32).view(np.uint32)
+    u = (u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
+    return u.view(np.float32).astype(np.float64)
+
+
+def rounded(h, prec):
+    f = round_tf32 if prec == TF32 else round_bf16
+    return synth.HostBSR(h.n, h.bs, h.row_ptr, h.col_idx, f(h.val))
+
+
+def abs_mat(h):
+    return synth.HostBSR(h.n, h.bs, h.row_ptr, h.col_idx, np.abs(h.val))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_1901_07993_gb300 import build as libbuild
+    from paper_1901_07993_gb300 import ifac
+    assert torch.cuda.is_available()
+    libbuild.build()
+    return ifac.Context()
+
+
+def _check(ctx, A, B, tA, tB, prec, alpha=1.0):
+    from paper_1901_07993_gb300 import ifac
+    ref = oracle.gemm(rounded(A, prec), rounded(B, prec), tA, tB, alpha, 0.0)
+    bound = oracle.gemm(abs_mat(rounded(A, prec)), abs_mat(rounded(B, prec)), tA, tB, abs(alpha), 0.0)
+    got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), tA, ifac.upload(ctx, B), tB, alpha, 0.0, prec).download()
+    assert np.array_equal(got.row_ptr, ref.row_ptr) and np.array_equal(got.col_idx, ref.col_idx)
+    kmax = A.nb * A.bs
+    err = np.abs(got.val - ref.val)
+    lim = kmax * 2.0 ** -22 * bound.val + 1e-300
+    assert np.all(err <= lim), float((err / lim).max())
+    return np.abs(got.val - oracle.gemm(A, B, tA, tB, alpha, 0.0).val).max()
+
+
+@pytest.mark.parametrize("prec", [TF32, BF16])
+@pytest.mark.parametrize("tA,tB", list(itertools.product([False, True], repeat=2)))
+def test_tc_random_blocks(ctx, prec, tA, tB):
+    nb = 9
+    A = synth.random_bsr(nb, 64, 0.4, seed=31, empty_rows=1, n=nb * 64 - 7)
+    B = synth.random_bsr(nb, 64, 0.4, seed=32, empty_rows=2, n=nb * 64 - 7)
+    _check(ctx, A, B, tA, tB, prec, alpha=-1.25)
+
+
+@pytest.mark.parametrize("prec", [TF32, BF16])
+def test_tc_overlap_products(ctx, prec):
+    """S S and S^T S on a 3D cluster (bs 64): dense-ish tiles, realistic values."""
+    S = synth.cluster_overlap(1536, 64, seed=2)
+    St = oracle.truncate(S, 1e-10)
+    St = synth.HostBSR(St.n, 64, St.row_ptr, St.col_idx, St.val)
+    e1 = _check(ctx, St, St, False, False, prec)
+    e2 = _check(ctx, St, St, True, False, prec)
+    # error against the unrounded FP64 product, stated (not a bound)
+    print(f"prec {prec}: max |C - C_fp64| = {max(e1, e2):.3e}")
+
+
+@pytest.mark.parametrize("prec", [TF32, BF16])
+def test_tc_truncation_and_sparse_tiles(ctx, prec):
+    """A sparse 1D-chain pattern (most tile blocks missing) with truncation."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(2000, 64, seed=4)
+    ref = oracle.gemm(rounded(S, prec), rounded(S, prec), False, False, 1.0, 0.0)
+    norms = np.sort(np.sqrt((ref.val ** 2).sum(axis=(1, 2))))
+    k = len(norms) // 3
+    tau = 0.5 * (norms[k - 1] + norms[k])
+    gap = norms[k] - norms[k - 1]
+    if gap < 1e-6 * norms[k]:
+        pytest.skip("no clear gap between block norms")
+    got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, S), False, ifac.upload(ctx, S), False, 1.0, tau, prec).download()
+    keep = oracle.truncate(ref, tau)
+    assert np.array_equal(got.col_idx, keep.col_idx) and np.array_equal(got.row_ptr, keep.row_ptr)
+    assert np.abs(got.val - keep.val).max() <= 1e-4 * np.abs(keep.val).max()
