@@ -102,7 +102,8 @@ typedef struct {
                       0 -> c = 1/sqrt(beta), 1 -> c = sqrt(2/beta) */
   int leaf_size;   /* inv_factor_localized: sub-problems with more rows are
                       split at the block-aligned midpoint (Algorithm 2) */
-  int prec;        /* IFAC_FP64 */
+  int prec;        /* IFAC_FP64; inv_factor_refine also takes IFAC_TF32 or
+                      IFAC_BF16: the mixed-precision schedule below */
   int profile;     /* != 0: time every numeric block-product launch with CUDA
                       events on the context's stream (fills gemm_ms) */
 } ifac_opts;
@@ -119,6 +120,8 @@ typedef struct {
   int64_t block_pairs; /* stored-block pairs multiplied, over all products */
   int64_t nnzb_Z;      /* stored blocks of the returned Z */
   double flops;        /* 2 bs^3 block_pairs */
+  int fp64_delta_evals;/* refine, mixed precision: delta evaluations with FP64 products */
+  int low_sweeps;      /* refine, mixed precision: corrections made in the low-precision phase */
   int64_t launches;    /* kernels this call launched */
   int64_t gemm_launches; /* numeric block-product launches */
   double gemm_ms;      /* their summed device time (opts.profile != 0) */
@@ -232,7 +235,17 @@ int leaf_invchol_batched_noalloc(void* stream, int count, int nl, const double* 
  * ||delta||_F <= target, or ||delta_{i+1}||_F > ||delta_i||_F^(m+1), or after
  * max_iter corrections; returns the last iterate (whose delta was last
  * evaluated).  Returns IFAC_WARN_TARGET_NOT_MET when the rule stopped it
- * above the target, IFAC_ERR_NO_CONVERGENCE at max_iter.  rep may be NULL. */
+ * above the target, IFAC_ERR_NO_CONVERGENCE at max_iter.  rep may be NULL.
+ *
+ * Mixed precision (opts->prec = IFAC_TF32 or IFAC_BF16, bs = 64): every
+ * block product of a sweep runs on the tensor cores with inputs rounded to
+ * that format and FP32 accumulation, while sums, block norms, truncation and
+ * delta = I - Y stay FP64; sweeps continue while ||delta||_F falls by at
+ * least 2x.  Then delta is evaluated with FP64 products (the correction M stays
+ * low precision, so convergence becomes linear with a rate near the format's
+ * unit roundoff), stopping at ||delta||_F <= target or when ||delta||_F no
+ * longer falls by 2x; the stop rule of Section 2.2 does not apply to this
+ * phase.  The returned Z is the last one whose delta was evaluated in FP64. */
 int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
                       const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
 

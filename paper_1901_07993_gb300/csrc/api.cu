@@ -320,11 +320,12 @@ int leaf_invchol_batched(ifac_ctx* ctx, int count, int nl, const double* S, doub
   });
 }
 
-static void check_opts(const ifac_opts* o) {
+static void check_opts(const ifac_opts* o, bool mixed_ok) {
   if (!o) fail(IFAC_ERR_INVALID, "opts is NULL");
   if (o->m < 1 || o->m > 8) fail(IFAC_ERR_INVALID, "m must be in 1..8");
   if (o->max_iter < 0 || o->fixed_iters < 0) fail(IFAC_ERR_INVALID, "negative iteration count");
-  if (o->prec != IFAC_FP64) fail(IFAC_ERR_UNSUPPORTED, "precision not built");
+  if (o->prec != IFAC_FP64 && !(mixed_ok && (o->prec == IFAC_TF32 || o->prec == IFAC_BF16)))
+    fail(IFAC_ERR_UNSUPPORTED, "precision not available for this call");
 }
 
 int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target, const ifac_opts* opts,
@@ -332,9 +333,10 @@ int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double targe
   if (Z) *Z = ifac_bsr{};
   return guarded(ctx, [&]() -> int {
     validate(S, "S");
-    check_opts(opts);
+    check_opts(opts, true);
     if (!Z) fail(IFAC_ERR_INVALID, "Z is NULL");
     if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
+    if (opts->prec != IFAC_FP64) return refine_irsi_mixed(ctx, *S, tau, target, *opts, Z, rep);
     return refine_irsi(ctx, *S, tau, target, *opts, Z, rep);
   });
 }
@@ -344,7 +346,7 @@ int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double ta
   if (Z) *Z = ifac_bsr{};
   return guarded(ctx, [&]() -> int {
     validate(S, "S");
-    check_opts(opts);
+    check_opts(opts, false);
     if (!Z) fail(IFAC_ERR_INVALID, "Z is NULL");
     if (opts->leaf_size < 1) fail(IFAC_ERR_INVALID, "leaf_size must be >= 1");
     if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");

@@ -25,11 +25,11 @@ static double coef_b(int k) {
 }
 
 // P = sum_{k=1}^{m} b_k delta^k, powers by successive truncated products
-static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau) {
+static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int prec = IFAC_FP64) {
   Mat P = add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
   Mat D;
   for (int k = 2; k <= m; ++k) {
-    Mat Dn = gemm(ctx, k == 2 ? delta : D.m, false, delta, false, 1.0, tau);
+    Mat Dn = gemm(ctx, k == 2 ? delta : D.m, false, delta, false, 1.0, tau, prec);
     D = std::move(Dn);
     P = add(ctx, 1.0, P.m, coef_b(k), &D.m, 0.0);
   }
@@ -109,6 +109,70 @@ int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, 
   IFAC_CK(cudaStreamSynchronize(ctx->stream));
   *Zout = Z.release();
   return (stop == IFAC_STOP_RULE && e > target) ? IFAC_WARN_TARGET_NOT_MET : IFAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mixed-precision refinement from a scaled identity
+// ---------------------------------------------------------------------------
+int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, const ifac_opts& o,
+                      ifac_bsr* Zout, ifac_report* rep) {
+  if (S_in.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "mixed precision needs bs = 64");
+  report_init(ctx, rep, o);
+  const int low = o.prec;
+  Mat S = truncate(ctx, S_in, tau);
+  const double beta = gershgorin_host(ctx, S.m);
+  const double c = (o.c_rule == 1) ? std::sqrt(2.0 / beta) : 1.0 / std::sqrt(beta);
+  Mat Z = scaled_identity(ctx, S.m.n, S.m.bs, S.m.nb, c);
+  if (rep) rep->beta = beta;
+  bool fp64_phase = false;
+  double e_prev = INFINITY, e = 0.0;
+  int stop = 0, sweeps = 0, fp64_evals = 0, low_sweeps = 0;
+  for (int it = 0;; ++it) {
+    const int dprec = fp64_phase ? IFAC_FP64 : low;
+    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec);   // S Z
+    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec);    // Z^T (S Z)
+    X.reset();
+    Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);               // I - Z^T S Z
+    Y.reset();
+    e = fro_host(ctx, D.m);
+    if (rep && rep->n_delta < 64) rep->delta_fro[rep->n_delta++] = e;
+    if (fp64_phase) {
+      ++fp64_evals;
+      if (e <= target) stop = IFAC_STOP_TARGET;
+      else if (!(e <= 0.5 * e_prev)) stop = IFAC_STOP_RULE;   // no longer halving: at the floor
+      else if (it >= o.max_iter) stop = IFAC_STOP_MAXITER;
+      if (stop) break;
+    } else if (!(e <= 0.5 * e_prev) || it >= o.max_iter) {
+      // the low-precision delta stopped falling by 2x: evaluate delta in FP64 for this Z
+      fp64_phase = true;
+      e_prev = INFINITY;
+      if (rep && rep->n_delta > 0) --rep->n_delta;
+      --it;
+      continue;
+    }
+    Mat P = poly_P(ctx, D.m, o.m, tau, low);
+    D.reset();
+    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low);      // M = Z sum b_k delta^k
+    P.reset();
+    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);
+    ++sweeps;
+    if (!fp64_phase) ++low_sweeps;
+    e_prev = e;
+  }
+  if (rep) {
+    rep->sweeps = sweeps;
+    rep->stop_reason = stop;
+    rep->fp64_delta_evals = fp64_evals;
+    rep->low_sweeps = low_sweeps;
+  }
+  if (stop == IFAC_STOP_MAXITER) {
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    fail(IFAC_ERR_NO_CONVERGENCE, "no convergence in max_iter sweeps; ||delta||_F = " + std::to_string(e));
+  }
+  report_finish(ctx, rep, Z.m);
+  IFAC_CK(cudaStreamSynchronize(ctx->stream));
+  *Zout = Z.release();
+  return (e > target) ? IFAC_WARN_TARGET_NOT_MET : IFAC_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -163,6 +163,8 @@ void leaf_invchol(ifac_ctx* ctx, int count, int nl, double* A, int* info);
 // ---- drivers (drivers.cu) ----
 int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S, double tau, double target, const ifac_opts& o,
                 ifac_bsr* Z, ifac_report* rep);
+int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S, double tau, double target, const ifac_opts& o,
+                      ifac_bsr* Z, ifac_report* rep);
 int lif(ifac_ctx* ctx, const ifac_bsr& S, double tau, double target, const ifac_opts& o,
         ifac_bsr* Z, ifac_report* rep);
 double resid(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& Z);

@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libifac.so")
 
 OK, WARN_TARGET_NOT_MET = 0, 1
+TF32, BF16 = 1, 2
 ERR_INVALID, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -7
 ERR_TOO_LARGE = -8
 FP64 = 0
@@ -54,8 +55,8 @@ class _Report(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("stop_reason", ctypes.c_int), ("levels", ctypes.c_int),
                 ("n_delta", ctypes.c_int), ("beta", ctypes.c_double), ("delta_fro", ctypes.c_double * 64),
                 ("products", ctypes.c_int64), ("block_pairs", ctypes.c_int64), ("nnzb_Z", ctypes.c_int64),
-                ("flops", ctypes.c_double), ("launches", ctypes.c_int64), ("gemm_launches", ctypes.c_int64),
-                ("gemm_ms", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("fp64_delta_evals", ctypes.c_int), ("low_sweeps", ctypes.c_int),
+                ("launches", ctypes.c_int64), ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -204,6 +205,8 @@ class Report:
     block_pairs: int
     nnzb_Z: int
     flops: float
+    fp64_delta_evals: int = 0
+    low_sweeps: int = 0
     launches: int = 0
     gemm_launches: int = 0
     gemm_ms: float = 0.0
@@ -232,7 +235,8 @@ def opts(m: int = 2, max_iter: int = 50, fixed_iters: int = 0, c_rule: int = 0, 
 
 def _report(r: _Report, rc: int) -> Report:
     return Report(r.sweeps, r.stop_reason, r.levels, r.beta, [r.delta_fro[i] for i in range(r.n_delta)],
-                  r.products, r.block_pairs, r.nnzb_Z, r.flops, r.launches, r.gemm_launches, r.gemm_ms, rc)
+                  r.products, r.block_pairs, r.nnzb_Z, r.flops, r.fp64_delta_evals, r.low_sweeps, r.launches,
+                  r.gemm_launches, r.gemm_ms, rc)
 
 
 def bsr_gemm_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, transB: bool, alpha: float = 1.0,

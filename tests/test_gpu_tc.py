@@ -3,7 +3,9 @@ accumulation, through the C ABI, against the CPU oracle's FP64 product of the
 same inputs rounded the same way (BF16: round-to-nearest-even from FP64;
 TF32: FP64 -> FP32 round-to-nearest-even, then round half away from zero to
 10 fraction bits).  With identically rounded inputs the only difference left
-is FP32 accumulation, bounded element-wise by K * 2^-22 * (|A||B|)_ij."""
+is FP32 accumulation, bounded element-wise by K * 2^-22 * (|A||B|)_ij, plus
+K * 2^-120 for terms below FP32's normal range, which the GPU flushes to zero
+(overlap matrices hold entries far below 1e-38)."""
 import itertools
 
 import numpy as np
@@ -54,8 +56,9 @@ def _check(ctx, A, B, tA, tB, prec, alpha=1.0):
     assert np.array_equal(got.row_ptr, ref.row_ptr) and np.array_equal(got.col_idx, ref.col_idx)
     kmax = A.nb * A.bs
     err = np.abs(got.val - ref.val)
-    lim = kmax * 2.0 ** -22 * bound.val + 1e-300
-    assert np.all(err <= lim), float((err / lim).max())
+    lim = kmax * 2.0 ** -22 * bound.val + kmax * 2.0 ** -120
+    worst = np.unravel_index(np.argmax(err / lim), err.shape)
+    assert np.all(err <= lim), (float(err[worst]), float(lim[worst]), float(ref.val[worst]))
     return np.abs(got.val - oracle.gemm(A, B, tA, tB, alpha, 0.0).val).max()
 
 
