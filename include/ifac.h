@@ -240,12 +240,15 @@ int leaf_invchol_batched_noalloc(void* stream, int count, int nl, const double* 
  * Mixed precision (opts->prec = IFAC_TF32 or IFAC_BF16, bs = 64): every
  * block product of a sweep runs on the tensor cores with inputs rounded to
  * that format and FP32 accumulation, while sums, block norms, truncation and
- * delta = I - Y stay FP64; sweeps continue while ||delta||_F falls by at
- * least 2x.  Then delta is evaluated with FP64 products (the correction M stays
- * low precision, so convergence becomes linear with a rate near the format's
- * unit roundoff), stopping at ||delta||_F <= target or when ||delta||_F no
- * longer falls by 2x; the stop rule of Section 2.2 does not apply to this
- * phase.  The returned Z is the last one whose delta was evaluated in FP64. */
+ * delta = I - Y stay FP64, until the automatic rule of Section 2.2
+ * (||delta_{i+1}||_F > ||delta_i||_F^(m+1): rounding dominates) fires.  From
+ * then on delta is evaluated with FP64 products for the same Z and after each
+ * correction (the correction M stays low precision, so convergence becomes
+ * linear with a rate near the format's unit roundoff), stopping at
+ * ||delta||_F <= target or when ||delta||_F no longer decreases.  The returned
+ * Z is the last one whose delta was evaluated with FP64 products.  With low-
+ * precision corrections Z converges to an inverse factor S^-1/2 Q with Q close
+ * to orthogonal, not to S^-1/2 itself. */
 int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
                       const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
 

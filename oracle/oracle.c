@@ -618,3 +618,199 @@ double om_resid(const om_mat* S, const om_mat* Z) {
 
 int64_t om_counter_products(void) { return g_products; }
 int64_t om_counter_pairs(void) { return g_pairs; }
+
+/* ------------------------------------------------------------------ */
+/* Adjoint of the refinement on a frozen block pattern                  */
+/* ------------------------------------------------------------------ */
+/*
+ * The differentiated function: K sweeps of Eq. (2.1) with m = 2 from
+ * Z_0 = c I (c held constant), every intermediate restricted to a block
+ * pattern that is fixed in advance (the patterns a tau-truncated run
+ * produced), and L = tr(Z_K^T F Z_K).  With Pi_X the projection onto the
+ * frozen pattern of X, one sweep is
+ *   X = Pi_X(S Z), Y = Pi_Y(Z^T X), delta = I - Y, D = Pi_D(delta delta),
+ *   P = delta/2 + 3 D/8, M = Pi_M(Z P), Z' = Z + M.
+ * Its reverse-mode derivative, applied step by step in reverse order:
+ *   Mh = Pi_M(Zh'),  Zh = Pi_Z(Zh') + Pi_Z(Mh P^T),  Ph = Pi_P(Z^T Mh),
+ *   Dh = 3/8 Pi_D(Ph),  deltah = 1/2 Pi_delta(Ph) + Pi_delta(Dh delta^T + delta^T Dh),
+ *   Yh = -Pi_Y(deltah),  Zh += Pi_Z(X Yh^T),  Xh = Pi_X(Z Yh),
+ *   Zh += Pi_Z(S^T Xh),  Sh += Pi_S(Xh Z^T),
+ * starting from Zh_K = Pi_{Z_K}((F + F^T) Z_K).
+ */
+
+/* C = alpha op(A) op(B) restricted to the pattern of P (blocks of P absent
+ * from the product are zero blocks). */
+static om_mat* om_gemm_masked(const om_mat* A, int tA, const om_mat* B, int tB, double alpha, const om_mat* P) {
+  om_mat* full = om_gemm(A, tA, B, tB, alpha, 0.0);
+  size_t bsz = (size_t)A->bs * A->bs;
+  om_builder out = ob_begin(A->n, A->bs, A->nb);
+  for (int I = 0; I < P->nb; ++I) {
+    int q = full->row_ptr[I];
+    for (int p = P->row_ptr[I]; p < P->row_ptr[I + 1]; ++p) {
+      int J = P->col_idx[p];
+      while (q < full->row_ptr[I + 1] && full->col_idx[q] < J) ++q;
+      double* dst = ob_push(&out, J);
+      if (q < full->row_ptr[I + 1] && full->col_idx[q] == J) memcpy(dst, full->val + (size_t)q * bsz, bsz * sizeof(double));
+      else memset(dst, 0, bsz * sizeof(double));
+    }
+    ob_end_row(&out, I);
+  }
+  om_free(full);
+  return out.m;
+}
+
+/* Pi_P(A): A restricted to the pattern of P. */
+static om_mat* om_project(const om_mat* A, const om_mat* P) {
+  size_t bsz = (size_t)A->bs * A->bs;
+  om_builder out = ob_begin(A->n, A->bs, A->nb);
+  for (int I = 0; I < P->nb; ++I) {
+    int q = A->row_ptr[I];
+    for (int p = P->row_ptr[I]; p < P->row_ptr[I + 1]; ++p) {
+      int J = P->col_idx[p];
+      while (q < A->row_ptr[I + 1] && A->col_idx[q] < J) ++q;
+      double* dst = ob_push(&out, J);
+      if (q < A->row_ptr[I + 1] && A->col_idx[q] == J) memcpy(dst, A->val + (size_t)q * bsz, bsz * sizeof(double));
+      else memset(dst, 0, bsz * sizeof(double));
+    }
+    ob_end_row(&out, I);
+  }
+  return out.m;
+}
+
+/* sum over stored blocks of <A_blk, B_blk> on A's pattern (B looked up) */
+static double om_dot_on(const om_mat* A, const om_mat* B) {
+  om_mat* Bp = om_project(B, A);
+  double s = 0.0;
+  size_t tot = (size_t)A->nnzb * A->bs * A->bs;
+  for (size_t e = 0; e < tot; ++e) s += A->val[e] * Bp->val[e];
+  om_free(Bp);
+  return s;
+}
+
+typedef struct {
+  int K;
+  om_mat** X;  /* frozen patterns (and values of the recording run) per sweep */
+  om_mat** Y;
+  om_mat** D;
+  om_mat** M;
+  om_mat** Z;  /* Z_0 .. Z_K */
+  om_mat* S;   /* truncated S */
+} om_tape;
+
+void om_tape_free(om_tape* t) {
+  if (!t) return;
+  for (int k = 0; k < t->K; ++k) {
+    om_free(t->X[k]); om_free(t->Y[k]); om_free(t->D[k]); om_free(t->M[k]);
+  }
+  for (int k = 0; k <= t->K; ++k) om_free(t->Z[k]);
+  free(t->X); free(t->Y); free(t->D); free(t->M); free(t->Z);
+  om_free(t->S);
+  free(t);
+}
+
+/* Recording run: K truncated sweeps (m = 2) from Z_0 = c I; keeps every
+ * intermediate (its pattern is the frozen pattern). */
+om_tape* om_tape_record(const om_mat* S_in, double c, int K, double tau) {
+  om_tape* t = (om_tape*)calloc(1, sizeof(om_tape));
+  t->K = K;
+  t->X = (om_mat**)calloc((size_t)K, sizeof(om_mat*));
+  t->Y = (om_mat**)calloc((size_t)K, sizeof(om_mat*));
+  t->D = (om_mat**)calloc((size_t)K, sizeof(om_mat*));
+  t->M = (om_mat**)calloc((size_t)K, sizeof(om_mat*));
+  t->Z = (om_mat**)calloc((size_t)K + 1, sizeof(om_mat*));
+  t->S = om_truncate(S_in, tau);
+  t->Z[0] = om_scaled_identity(t->S->n, t->S->bs, t->S->nb, c);
+  for (int k = 0; k < K; ++k) {
+    om_mat* Z = t->Z[k];
+    t->X[k] = om_gemm(t->S, 0, Z, 0, 1.0, tau);
+    t->Y[k] = om_gemm(Z, 1, t->X[k], 0, 1.0, tau);
+    om_mat* delta = om_add(-1.0, t->Y[k], 0.0, NULL, 1.0);
+    t->D[k] = om_gemm(delta, 0, delta, 0, 1.0, tau);
+    om_mat* P = om_add(0.5, delta, 0.375, t->D[k], 0.0);
+    t->M[k] = om_gemm(Z, 0, P, 0, 1.0, tau);
+    t->Z[k + 1] = om_add(1.0, Z, 1.0, t->M[k], 0.0);
+    om_free(delta); om_free(P);
+  }
+  return t;
+}
+
+/* Frozen-pattern forward for a (possibly perturbed) S on the tape's patterns;
+ * returns L = tr(Z_K^T F Z_K).  S_val must have the tape's S pattern. */
+double om_frozen_loss(const om_tape* t, const om_mat* S, const om_mat* F, double c) {
+  om_mat* Z = om_scaled_identity(S->n, S->bs, S->nb, c);
+  for (int k = 0; k < t->K; ++k) {
+    om_mat* X = om_gemm_masked(S, 0, Z, 0, 1.0, t->X[k]);
+    om_mat* Y = om_gemm_masked(Z, 1, X, 0, 1.0, t->Y[k]);
+    om_mat* delta = om_add(-1.0, Y, 0.0, NULL, 1.0);
+    om_mat* D = om_gemm_masked(delta, 0, delta, 0, 1.0, t->D[k]);
+    om_mat* P = om_add(0.5, delta, 0.375, D, 0.0);
+    om_mat* M = om_gemm_masked(Z, 0, P, 0, 1.0, t->M[k]);
+    om_mat* Zn = om_add(1.0, Z, 1.0, M, 0.0);
+    om_free(X); om_free(Y); om_free(delta); om_free(D); om_free(P); om_free(M); om_free(Z);
+    Z = Zn;
+  }
+  om_mat* FZ = om_gemm(F, 0, Z, 0, 1.0, 0.0);
+  double L = om_dot_on(Z, FZ);
+  om_free(FZ); om_free(Z);
+  return L;
+}
+
+/* Reverse pass: returns Sh = dL/dS on the pattern of the tape's S. */
+om_mat* om_adjoint(const om_tape* t, const om_mat* F) {
+  const int K = t->K;
+  const om_mat* S = t->S;
+  om_mat* ZK = t->Z[K];
+  om_mat* FZ = om_gemm(F, 0, ZK, 0, 1.0, 0.0);
+  om_mat* FtZ = om_gemm(F, 1, ZK, 0, 1.0, 0.0);
+  om_mat* G = om_add(1.0, FZ, 1.0, FtZ, 0.0);
+  om_mat* Zh = om_project(G, ZK);
+  om_free(FZ); om_free(FtZ); om_free(G);
+  om_mat* Sh = om_project(S, S);
+  memset(Sh->val, 0, (size_t)Sh->nnzb * S->bs * S->bs * sizeof(double));
+  for (int k = K - 1; k >= 0; --k) {
+    const om_mat* Z = t->Z[k];
+    const om_mat* X = t->X[k];
+    om_mat* delta = om_add(-1.0, t->Y[k], 0.0, NULL, 1.0);
+    om_mat* P = om_add(0.5, delta, 0.375, t->D[k], 0.0);
+    om_mat* Mh = om_project(Zh, t->M[k]);
+    om_mat* Zn = om_project(Zh, Z);
+    om_mat* t1 = om_gemm_masked(Mh, 0, P, 1, 1.0, Z);               /* Pi_Z(Mh P^T) */
+    om_mat* Zacc = om_add(1.0, Zn, 1.0, t1, 0.0);
+    om_free(Zn); om_free(t1);
+    om_mat* Ph = om_gemm_masked(Z, 1, Mh, 0, 1.0, P);                /* Pi_P(Z^T Mh) */
+    om_mat* Dh = om_project(Ph, t->D[k]);
+    om_mat* Dh38 = om_add(0.375, Dh, 0.0, NULL, 0.0);
+    om_mat* a1 = om_gemm_masked(Dh38, 0, delta, 1, 1.0, delta);      /* Pi_delta(Dh delta^T) */
+    om_mat* a2 = om_gemm_masked(delta, 1, Dh38, 0, 1.0, delta);      /* Pi_delta(delta^T Dh) */
+    om_mat* Phd = om_project(Ph, delta);
+    om_mat* s1 = om_add(0.5, Phd, 1.0, a1, 0.0);
+    om_mat* deltah = om_add(1.0, s1, 1.0, a2, 0.0);
+    om_mat* Yh0 = om_project(deltah, t->Y[k]);
+    om_mat* Yh = om_add(-1.0, Yh0, 0.0, NULL, 0.0);
+    om_mat* t2 = om_gemm_masked(X, 0, Yh, 1, 1.0, Z);                /* Pi_Z(X Yh^T) */
+    om_mat* Zacc2 = om_add(1.0, Zacc, 1.0, t2, 0.0);
+    om_mat* Xh = om_gemm_masked(Z, 0, Yh, 0, 1.0, X);                /* Pi_X(Z Yh) */
+    om_mat* t3 = om_gemm_masked(S, 1, Xh, 0, 1.0, Z);                /* Pi_Z(S^T Xh) */
+    om_mat* Zacc3 = om_add(1.0, Zacc2, 1.0, t3, 0.0);
+    om_mat* t4 = om_gemm_masked(Xh, 0, Z, 1, 1.0, S);                /* Pi_S(Xh Z^T) */
+    om_mat* Shn = om_add(1.0, Sh, 1.0, t4, 0.0);
+    om_free(Sh); Sh = Shn;
+    om_free(delta); om_free(P); om_free(Mh); om_free(Zacc); om_free(Ph); om_free(Dh); om_free(Dh38);
+    om_free(a1); om_free(a2); om_free(Phd); om_free(s1); om_free(deltah); om_free(Yh0); om_free(Yh);
+    om_free(t2); om_free(Zacc2); om_free(Xh); om_free(t3); om_free(t4);
+    om_free(Zh);
+    Zh = Zacc3;
+  }
+  om_free(Zh);
+  return Sh;
+}
+
+double om_tape_loss(const om_tape* t, const om_mat* F) {
+  om_mat* FZ = om_gemm(F, 0, t->Z[t->K], 0, 1.0, 0.0);
+  double L = om_dot_on(t->Z[t->K], FZ);
+  om_free(FZ);
+  return L;
+}
+
+const om_mat* om_tape_S(const om_tape* t) { return t->S; }
+const om_mat* om_tape_Z(const om_tape* t, int k) { return t->Z[k]; }

@@ -186,15 +186,14 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, in
 // the kernel
 // ---------------------------------------------------------------------------
 struct TileArgs {
-  const int32_t* tiles;  // packed (tile_row << 32 | tile_col) as two int32: [2*t] row, [2*t+1] col
+  const int32_t* tiles;  // [2*t] tile row, [2*t+1] tile column
   int ntiles;
   int nb;
-  const int32_t* arp;    // op(A) CSR
-  const int32_t* aci;
-  int a_zero;            // index of the zero block of the op(A) copy
-  const int32_t* brp;    // op(B) CSR (rows K)
-  const int32_t* bci;
-  int b_zero;
+  int W;                 // 32-bit words per bitmap row
+  const uint32_t* bmA;   // pattern bitmap of op(A): bit (I, K)
+  const int32_t* mapA;   // [nb*nb] index of op(A)_IK in the low-precision copy, or its zero block
+  const int32_t* mapB;   // [nb*nb] index of op(B)_KJ, or its zero block
+  int a_zero, b_zero;
   const int32_t* crp;    // C pattern
   const int32_t* cci;
   double* cval;
@@ -240,60 +239,73 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t issued_mask = 0, last_parity = 0;  // per stage: filled at least once / parity of the last fill
-      bool ok = true;
-      for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
-        const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
-        int pa[TM], ea[TM];
-#pragma unroll
-        for (int r = 0; r < TM; ++r) {
-          const int I = I0 + r;
-          pa[r] = (I < args.nb) ? args.arp[I] : 0;
-          ea[r] = (I < args.nb) ? args.arp[I + 1] : 0;
-        }
-        for (;;) {
-          int K = 0x7fffffff;
+    // The warp turns the K set of a tile (union of the bitmap rows of its op(A)
+    // block rows) into K-step records 32 at a time, lane-parallel; lane 0 then
+    // issues the loads of each record into the next ring slot.
+    __shared__ int rec[32][TM + Cfg<ELT>::TN];
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t issued_mask = 0, last_parity = 0;  // lane 0: stages filled / parity of their last fill
+    bool ok = true;
+    for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+      const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
+      for (int wbase = 0; wbase < args.W && ok; wbase += 32) {
+        const int w = wbase + lane;
+        uint32_t word = 0;
+        if (w < args.W) {
 #pragma unroll
           for (int r = 0; r < TM; ++r)
-            if (pa[r] < ea[r]) K = min(K, args.aci[pa[r]]);
-          if (K == 0x7fffffff) break;
-          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
-          const uint32_t fb = smem_u32(&full_bar[stage]);
-          mbar_expect_tx(fb, C::TX_BYTES);
-          issued_mask |= 1u << stage;
-          last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
-          const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
-          const uint32_t sb = sa + C::A_BYTES;
+            if (I0 + r < args.nb) word |= args.bmA[(size_t)(I0 + r) * args.W + w];
+        }
+        while (__any_sync(0xffffffffu, word != 0u) && ok) {
+          const bool has = word != 0u;
+          const unsigned m = __ballot_sync(0xffffffffu, has);
+          if (has) {
+            const int K = w * 32 + __ffs(word) - 1;
+            word &= word - 1u;
+            const int slot = __popc(m & ((1u << lane) - 1u));
 #pragma unroll
-          for (int r = 0; r < TM; ++r) {
-            int idx = args.a_zero;
-            if (pa[r] < ea[r] && args.aci[pa[r]] == K) idx = pa[r]++;
+            for (int r = 0; r < TM; ++r)
+              rec[slot][r] = (I0 + r < args.nb) ? args.mapA[(size_t)(I0 + r) * args.nb + K] : args.a_zero;
 #pragma unroll
-            for (int a = 0; a < C::ATOMS; ++a)
-              tma_load_2d(sa + a * C::A_ATOM_BYTES + r * BS * 128, &mapA, a * C::ATOM_ELEMS, idx * BS, fb);
+            for (int c = 0; c < C::TN; ++c)
+              rec[slot][TM + c] = (J0 + c < args.nb) ? args.mapB[(size_t)K * args.nb + J0 + c] : args.b_zero;
           }
-          int pb = args.brp[K];
-          const int eb = args.brp[K + 1];
-          pb = lower_bound_i32(args.bci, pb, eb, J0);
+          __syncwarp();
+          if (lane == 0) {
+            const int n = __popc(m);
+            for (int j = 0; j < n && ok; ++j) {
+              if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
+              const uint32_t fb = smem_u32(&full_bar[stage]);
+              mbar_expect_tx(fb, C::TX_BYTES);
+              issued_mask |= 1u << stage;
+              last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+              const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
+              const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-          for (int c = 0; c < C::TN; ++c) {
-            int idx = args.b_zero;
-            if (pb < eb && args.bci[pb] == J0 + c) idx = pb++;
+              for (int r = 0; r < TM; ++r)
 #pragma unroll
-            for (int a = 0; a < C::ATOMS; ++a)
-              tma_load_2d(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS, idx * BS, fb);
+                for (int a = 0; a < C::ATOMS; ++a)
+                  tma_load_2d(sa + a * C::A_ATOM_BYTES + r * BS * 128, &mapA, a * C::ATOM_ELEMS, rec[j][r] * BS, fb);
+#pragma unroll
+              for (int c = 0; c < C::TN; ++c)
+#pragma unroll
+                for (int a = 0; a < C::ATOMS; ++a)
+                  tma_load_2d(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS,
+                              rec[j][TM + c] * BS, fb);
+              if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+            }
           }
-          if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+          __syncwarp();
         }
       }
-      // copies this thread issued must land before the CTA exits
+    }
+    // copies lane 0 issued must land before the CTA exits
+    if (lane == 0)
       for (int s = 0; s < C::STAGES; ++s)
         if (issued_mask & (1u << s))
           mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
-    }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer ------------------------------
     if (lane == 0) {
@@ -302,24 +314,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
         const int I0 = args.tiles[2 * t] * TM;
-        // number of K steps: size of the union of the op(A) rows' columns
-        int pa[TM], ea[TM], nk = 0;
-#pragma unroll
-        for (int r = 0; r < TM; ++r) {
-          const int I = I0 + r;
-          pa[r] = (I < args.nb) ? args.arp[I] : 0;
-          ea[r] = (I < args.nb) ? args.arp[I + 1] : 0;
-        }
-        for (;;) {
-          int K = 0x7fffffff;
+        // number of K steps: size of the union of the op(A) rows' bitmaps
+        int nk = 0;
+        for (int w = 0; w < args.W; ++w) {
+          uint32_t word = 0;
 #pragma unroll
           for (int r = 0; r < TM; ++r)
-            if (pa[r] < ea[r]) K = min(K, args.aci[pa[r]]);
-          if (K == 0x7fffffff) break;
-#pragma unroll
-          for (int r = 0; r < TM; ++r)
-            if (pa[r] < ea[r] && args.aci[pa[r]] == K) ++pa[r];
-          ++nk;
+            if (I0 + r < args.nb) word |= args.bmA[(size_t)(I0 + r) * args.W + w];
+          nk += __popc(word);
         }
         if (!mbar_wait(smem_u32(&acc_empty), acc_phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
         tc_fence_after();
@@ -454,7 +456,9 @@ __global__ void k_tile_flags(const int32_t* __restrict__ row, const int32_t* __r
 
 __global__ void k_tile_list(const uint8_t* __restrict__ flag, int ntr, int ntc, int32_t* __restrict__ out,
                             int* __restrict__ count) {
-  // single CTA; tiles come out in row-major tile order
+  // single CTA; tiles come out grouped by GROUP tile rows: within a group,
+  // column by column, so concurrently running CTAs share op(B) panels in L2
+  constexpr int GROUP = 8;
   __shared__ int wcount[32];
   __shared__ int base, chunk_total;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -462,8 +466,15 @@ __global__ void k_tile_list(const uint8_t* __restrict__ flag, int ntr, int ntc, 
   __syncthreads();
   const int64_t tot = (int64_t)ntr * ntc;
   for (int64_t s = 0; s < tot; s += blockDim.x) {
-    const int64_t i = s + threadIdx.x;
-    const bool f = i < tot && flag[i];
+    const int64_t li = s + threadIdx.x;
+    int64_t i = 0;
+    if (li < tot) {  // li-th tile in grouped order -> row-major index i
+      const int64_t g = li / ((int64_t)GROUP * ntc);
+      const int64_t rows = min((int64_t)GROUP, (int64_t)ntr - g * GROUP);
+      const int64_t off = li - g * GROUP * ntc;
+      i = (g * GROUP + off % rows) * ntc + off / rows;
+    }
+    const bool f = li < tot && flag[i];
     const unsigned m = __ballot_sync(0xffffffffu, f);
     if (lane == 0) wcount[w] = __popc(m);
     __syncthreads();
@@ -487,6 +498,19 @@ __global__ void k_tile_list(const uint8_t* __restrict__ flag, int ntr, int ntc, 
     __syncthreads();
   }
   if (threadIdx.x == 0) *count = base;
+}
+
+// dense block-index map of a CSR pattern: map[I*nb + J] = q for block q, else zero_idx
+__global__ void k_map_fill(int32_t* __restrict__ map, int64_t n, int32_t zero_idx) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) map[i] = zero_idx;
+}
+
+__global__ void k_map_scatter(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int nb,
+                              int32_t* __restrict__ map) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= nb) return;
+  for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) map[(size_t)row * nb + ci[p]] = p;
 }
 
 // pairs += |row K of op(B)| for every stored block (I, K) of op(A): the number
@@ -559,6 +583,18 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   const CUtensorMap mapA = make_map<ELT>(la.p, A.nnzb + 1);
   const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
+  // K sets (bitmap rows of op(A)) and dense block-index maps of op(A), op(B)
+  Buf<uint32_t> bmA = pattern_bitmap(ctx, A, tA);
+  const int64_t nb2 = (int64_t)nb * nb;
+  Buf<int32_t> imA(ctx, nb2), imB(ctx, nb2);
+  k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imA.p, nb2, (int32_t)A.nnzb);
+  IFAC_CK_LAUNCH();
+  k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imB.p, nb2, (int32_t)B.nnzb);
+  IFAC_CK_LAUNCH();
+  k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, imA.p);
+  IFAC_CK_LAUNCH();
+  k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
+  IFAC_CK_LAUNCH();
   // tiles holding a block of C's pattern
   const int ntr = cdiv(nb, TM), ntc = cdiv(nb, Cf::TN);
   Buf<uint8_t> flags(ctx, (size_t)ntr * ntc);
@@ -586,11 +622,11 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.tiles = tiles.p;
   args.ntiles = ntiles;
   args.nb = nb;
-  args.arp = arows.rp;
-  args.aci = arows.ci;
+  args.W = words_per_row(nb);
+  args.bmA = bmA.p;
+  args.mapA = imA.p;
+  args.mapB = imB.p;
   args.a_zero = (int)A.nnzb;
-  args.brp = brows.rp;
-  args.bci = brows.ci;
   args.b_zero = (int)B.nnzb;
   args.crp = C.row_ptr;
   args.cci = C.col_idx;

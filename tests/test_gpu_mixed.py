@@ -3,7 +3,10 @@ norms and final delta evaluations) through the C ABI.  It has no pin beyond
 the FP64 oracle: the refinement from a scaled identity converges to the same
 S^-1/2 whatever the precision of the corrections, so the result is compared
 with the oracle's FP64 factor, and the error is stated; the direct FP64
-residual ||I - Z^T S Z||_F must reach the target."""
+residual ||I - Z^T S Z||_F must reach the target.  With low-precision
+corrections the iterates leave the polynomials in S, so Z converges to another
+inverse factor S^-1/2 Q (Q near orthogonal): its distance to the FP64 factor is
+stated, and bounded only loosely by the format's unit roundoff."""
 import numpy as np
 import pytest
 
@@ -39,7 +42,7 @@ def test_mixed_refine_reaches_target(ctx, prec, kind, n):
     rel = np.linalg.norm(za - zr) / np.linalg.norm(zr)
     print(f"{kind} n={n} prec={prec}: resid {resid:.2e}, rel err vs FP64 oracle {rel:.2e}, "
           f"low sweeps {rep.low_sweeps}, FP64 delta evals {rep.fp64_delta_evals}, deltas {rep.delta_fro}")
-    assert rep.fp64_delta_evals >= 1
+    assert rep.fp64_delta_evals >= 1 and rep.low_sweeps >= 2
     assert rep.delta_fro[-1] <= target
     assert resid <= 10 * target
-    assert rel <= 1e-8
+    assert rel <= (2e-3 if prec == 1 else 2e-2)
