@@ -265,6 +265,20 @@ int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double targe
 int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
                          const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
 
+/* Reverse-mode derivative of K refinement sweeps of Eq. (2.1) (m = 2, from
+ * Z_0 = c I, c = 1/sqrt(beta) of the truncated S, held constant) on a frozen
+ * block pattern, for the loss L = tr(Z_K^T F Z_K).  A recording run with
+ * truncation at tau (Section 5) fixes the block pattern of every
+ * intermediate; the differentiated function restricts every product to its
+ * recorded pattern, so L is a polynomial in the stored entries of S and the
+ * derivative is exact up to rounding.  The paper has no derivative; this is
+ * the hand-written adjoint of those sweeps (all FP64).  F: same n and bs as S
+ * (any pattern).  Outputs: *L, and Sbar = dL/dS with every stored entry of S
+ * an independent variable (not symmetrized), on the pattern of the caller's
+ * S (zero on blocks the truncation removed).  K in 0..64. */
+int inv_factor_refine_adjoint(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* F, int K, double tau,
+                              double* L, ifac_bsr* Sbar);
+
 /* ||I - Z^T S Z||_F with untruncated products (the factorization error of
  * Table 1). */
 int inv_factor_resid(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* Z, double* out);

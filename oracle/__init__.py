@@ -270,3 +270,75 @@ def resid(S, Z) -> float:
     """||I - Z^T S Z||_F with untruncated products."""
     with _Held(S, Z) as (hs, hz):
         return float(_load().om_resid(hs, hz))
+
+
+# ---------------------------------------------------------------------------
+# adjoint of the refinement on a frozen block pattern
+# ---------------------------------------------------------------------------
+def _load_adjoint():
+    lib = _load()
+    if not hasattr(lib, "_adj_ready"):
+        p, i32, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "om_tape_record": ([p, d, i32, d], p),
+            "om_tape_free": ([p], None),
+            "om_frozen_loss": ([p, p, p, d], d),
+            "om_adjoint": ([p, p], p),
+            "om_tape_loss": ([p, p], d),
+            "om_tape_S": ([p], p),
+            "om_tape_Z": ([p, i32], p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        lib._adj_ready = True
+    return lib
+
+
+def _copy_borrowed(h, bs: int) -> Mat:
+    lib = _load()
+    nb, nnzb, n = lib.om_nb(h), lib.om_nnzb(h), lib.om_n(h)
+    rp = np.zeros(nb + 1, dtype=np.int32)
+    ci = np.zeros(nnzb, dtype=np.int32)
+    v = np.zeros((nnzb, bs, bs))
+    lib.om_to_arrays(h, rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+    return Mat(int(n), bs, rp, ci, v)
+
+
+class Tape:
+    """Recording run of K truncated sweeps (m = 2) from Z_0 = c I; its block
+    patterns are the frozen patterns of the differentiated function."""
+
+    def __init__(self, S, c: float, K: int, tau: float):
+        lib = _load_adjoint()
+        self.bs, self.c, self.K = S.bs, c, K
+        with _Held(S) as (hs,):
+            self.h = lib.om_tape_record(hs, c, K, tau)
+
+    def S(self) -> Mat:
+        return _copy_borrowed(_load_adjoint().om_tape_S(self.h), self.bs)
+
+    def Z(self, k: int) -> Mat:
+        return _copy_borrowed(_load_adjoint().om_tape_Z(self.h, k), self.bs)
+
+    def loss(self, F) -> float:
+        with _Held(F) as (hf,):
+            return float(_load_adjoint().om_tape_loss(self.h, hf))
+
+    def frozen_loss(self, S, F) -> float:
+        """L for another S on the frozen patterns (S must have the tape's S pattern)."""
+        with _Held(S, F) as (hs, hf):
+            return float(_load_adjoint().om_frozen_loss(self.h, hs, hf, self.c))
+
+    def adjoint(self, F) -> Mat:
+        """dL/dS (all entries independent) on the pattern of the truncated S."""
+        with _Held(F) as (hf,):
+            return _from_c(_load_adjoint().om_adjoint(self.h, hf), self.bs)
+
+    def __del__(self):
+        try:
+            if self.h:
+                _load_adjoint().om_tape_free(self.h)
+        except Exception:
+            pass

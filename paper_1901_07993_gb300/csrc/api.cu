@@ -354,6 +354,20 @@ int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double ta
   });
 }
 
+int inv_factor_refine_adjoint(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* F, int K, double tau, double* L,
+                              ifac_bsr* Sbar) {
+  if (Sbar) *Sbar = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(S, "S");
+    validate(F, "F");
+    check_pair(S, F);
+    if (!L || !Sbar) fail(IFAC_ERR_INVALID, "L or Sbar is NULL");
+    if (K < 0 || K > 64) fail(IFAC_ERR_INVALID, "K must be in 0..64");
+    if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
+    return refine_adjoint(ctx, *S, *F, K, tau, L, Sbar);
+  });
+}
+
 int inv_factor_resid(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* Z, double* out) {
   return guarded(ctx, [&]() -> int {
     validate(S, "S");

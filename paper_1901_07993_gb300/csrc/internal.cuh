@@ -168,6 +168,8 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S, double tau, double targe
 int lif(ifac_ctx* ctx, const ifac_bsr& S, double tau, double target, const ifac_opts& o,
         ifac_bsr* Z, ifac_report* rep);
 double resid(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& Z);
+int refine_adjoint(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& F, int K, double tau, double* L,
+                   ifac_bsr* Sbar);
 
 // event pair around a profiled launch; prof_collect sums and recycles them
 void prof_begin(ifac_ctx* ctx);

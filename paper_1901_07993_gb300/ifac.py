@@ -30,7 +30,8 @@ STOP_RULE, STOP_TARGET, STOP_MAXITER, STOP_FIXED = 1, 2, 3, 4
 EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", "ifac_opts_default",
            "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_add",
            "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
-           "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc")
+           "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
+           "inv_factor_refine_adjoint")
 
 
 class IfacError(RuntimeError):
@@ -91,6 +92,7 @@ def load(path: str = LIB_PATH):
         "inv_factor_localized": ([p, PB, d, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
         "inv_factor_resid": ([p, PB, PB, ctypes.POINTER(d)], i32),
         "leaf_invchol_batched_noalloc": ([p, i32, i32, p, p, p], i32),
+        "inv_factor_refine_adjoint": ([p, PB, PB, i32, d, ctypes.POINTER(d), PB], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -302,6 +304,46 @@ def inv_factor_localized(ctx: Context, S: DeviceBSR, tau: float, target: float, 
     rc = ctx.check(ctx.lib.inv_factor_localized(ctx.h, S.ptr(), tau, target, ctypes.byref(o or opts()),
                                                 ctypes.byref(Z), ctypes.byref(rep)))
     return DeviceBSR(ctx, Z), _report(rep, rc)
+
+
+def inv_factor_refine_adjoint(ctx: Context, S, F, K: int = 6, tau: float = 1e-10):
+    """(L, Sbar): L = tr(Z_K^T F Z_K) after K frozen-pattern sweeps and
+    Sbar = dL/dS on S's pattern (see include/ifac.h).  S, F: DeviceBSR or
+    BorrowedBSR."""
+    Sb = _Bsr()
+    L = ctypes.c_double()
+    ctx.check(ctx.lib.inv_factor_refine_adjoint(ctx.h, S.ptr(), F.ptr(), K, tau, ctypes.byref(L), ctypes.byref(Sb)))
+    return L.value, DeviceBSR(ctx, Sb)
+
+
+class BorrowedBSR:
+    """An ifac_bsr over caller-owned CUDA tensors (row_ptr, col_idx int32;
+    val float64 [nnzb, bs, bs]); the tensors must outlive every call."""
+
+    def __init__(self, n: int, bs: int, row_ptr, col_idx, val):
+        self.keep = (row_ptr, col_idx, val)
+        self.raw = _Bsr(n, bs, row_ptr.numel() - 1, col_idx.numel(), row_ptr.data_ptr(), col_idx.data_ptr(),
+                        val.data_ptr(), None)
+
+    def ptr(self):
+        return ctypes.byref(self.raw)
+
+
+def device_tensors(M: DeviceBSR):
+    """Zero-copy torch views (row_ptr, col_idx, val) of a library-owned matrix;
+    they keep M alive."""
+    import torch
+
+    class _View:
+        def __init__(self, ptr, shape, typestr, owner):
+            self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}
+            self.owner = owner
+
+    nb, nnzb, bs = M.nb, M.nnzb, M.bs
+    rp = torch.as_tensor(_View(M.raw.row_ptr, (nb + 1,), "<i4", M), device="cuda")
+    ci = torch.as_tensor(_View(M.raw.col_idx or 0, (nnzb,), "<i4", M), device="cuda")
+    v = torch.as_tensor(_View(M.raw.val or 0, (nnzb, bs, bs), "<f8", M), device="cuda")
+    return rp, ci, v
 
 
 def inv_factor_resid(ctx: Context, S: DeviceBSR, Z: DeviceBSR) -> float:

@@ -186,3 +186,28 @@ def random_bsr(nb: int, bs: int, density: float, seed: int, n: int | None = None
     col_idx = np.nonzero(mask)[1].astype(np.int32)
     val = rng.standard_normal((len(col_idx), bs, bs)) * scale
     return HostBSR(n if n is not None else nb * bs, bs, row_ptr, col_idx, val)
+
+
+def fock_like(S: HostBSR, seed: int = 5) -> HostBSR:
+    """Symmetric matrix on the block pattern of S with entries N(0,1) * S_ij
+    (a stand-in for a Fock-like matrix).  Blocks (I, J), I <= J, draw their
+    N(0,1) factors in CSR order from numpy's PCG64 with the given seed;
+    diagonal blocks are symmetrized and block (J, I) is the transpose."""
+    rng = np.random.default_rng(seed)
+    nb, bs = S.nb, S.bs
+    rows = np.repeat(np.arange(nb), np.diff(S.row_ptr))
+    pos = {(int(i), int(j)): p for p, (i, j) in enumerate(zip(rows, S.col_idx))}
+    val = np.zeros_like(S.val)
+    for p, (i, j) in enumerate(zip(rows, S.col_idx)):
+        if i > j:
+            continue
+        g = rng.standard_normal((bs, bs))
+        if i == j:
+            g = np.triu(g) + np.triu(g, 1).T
+        val[p] = g * S.val[p]
+        if i != j:
+            q = pos.get((int(j), int(i)))
+            if q is None:
+                raise ValueError("S pattern is not symmetric")
+            val[q] = val[p].T
+    return HostBSR(S.n, S.bs, S.row_ptr.copy(), S.col_idx.copy(), val)
