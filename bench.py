@@ -4,7 +4,11 @@
 One step = one complete factorization of the workload's synthetic overlap
 matrix S (resident in HBM) through the C ABI: truncation of S, Gershgorin
 bound, every refinement sweep (block-sparse products with truncation, sums,
-norms, stop tests) until the stop rule, returning Z.
+norms, stop tests) until the stop rule, returning Z.  The default workload
+factorizes a 262,144-row 1D-chain overlap matrix (BSR 64 x 64, tau = 1e-12)
+to ||I - Z^T S Z||_F <= 1e-10 with TF32 tensor-core products and FP64 final
+delta evaluations; the same factorization with FP64 products and with BF16
+products is timed beside it ("compare").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload NAME]
@@ -34,12 +38,18 @@ WORKLOADS = {
     # 1D chain of 4096 normalized s-Gaussians, spacing 1.4 bohr +-0.1, exponents
     # (0.17, 0.62, 3.4); BSR 32x32; tau = 1e-10; FP64 refinement from I/sqrt(beta)
     "irsi-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="refine", m=2,
-                                  seed=0, leaf=512),
-    # the same chain through localized inverse factorization (512-row leaves)
+                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
+    # the same construction at n = 262,144 in BSR 64x64, tau = 1e-12 (the 1e-10
+    # target is reachable): TF32 products, FP64 delta at the end; FP64 and BF16 beside
+    "irsi-mixed-chain-n262144-bs64": dict(geom="chain", n=262144, bs=64, tau=1e-12, target=1e-10, method="refine",
+                                          m=2, seed=0, leaf=512, prec="tf32", compare=("fp64", "bf16"),
+                                          sample_n=4096),
+    # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
-                                 seed=0, leaf=512),
+                                 seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
 }
-DEFAULT_WORKLOAD = "irsi-chain-n4096-bs32"
+DEFAULT_WORKLOAD = "irsi-mixed-chain-n262144-bs64"
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 METRIC = "Inverse-factor time & block-GEMM TFLOP/s: mixed vs FP64 at ||I-Z*SZ||_F<=1e-10"
 UNIT = "factorizations/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
@@ -61,11 +71,19 @@ def fp64_peak_tflops():
     return bf16 * 1.25 / 2250.0, src
 
 
-def make_input(w):
+def tensor_peak_tflops(prec: str):
+    """Dense tensor peak for the product's input format: measured bf16, or
+    measured bf16 times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    bf16, _, src = _peaks()
+    return (bf16 if prec == "bf16" else bf16 * 1.1 / 2.25), src
+
+
+def make_input(w, n=None):
     from paper_1901_07993_gb300 import synth
+    n = n or w["n"]
     if w["geom"] == "chain":
-        return synth.chain_overlap(w["n"], w["bs"], seed=w["seed"])
-    return synth.cluster_overlap(w["n"], w["bs"], seed=w["seed"])
+        return synth.chain_overlap(n, w["bs"], seed=w["seed"])
+    return synth.cluster_overlap(n, w["bs"], seed=w["seed"])
 
 
 class ClockSampler:
@@ -161,10 +179,23 @@ def oracle_factorize(S, w):
     return oracle.lif(S, m=w["m"], tau=w["tau"], target=w["target"], leaf_size=w["leaf"])
 
 
-def cpu_baseline(S, w, budget_s: float = 10.0):
-    """The oracle, as it stands, on the same workload for about budget_s."""
+def cpu_sample(w):
+    """The input the CPU oracle factorizes, and the factor that turns its rate
+    into the workload's: the workload itself, or (for the large chain) the
+    same construction at sample_n rows, whose cost is n/sample_n times smaller
+    (the chain's factorization cost is linear in n)."""
+    if w.get("sample_n"):
+        return make_input(w, w["sample_n"]), w["sample_n"] / w["n"], \
+            (f"complete FP64 factorizations of the same construction at n = {w['sample_n']} "
+             f"(block rows 1/{w['n'] // w['sample_n']} of the workload), rate scaled by {w['sample_n']}/{w['n']}")
+    return make_input(w), 1.0, "complete FP64 factorizations of the same workload"
+
+
+def cpu_baseline(w, budget_s: float = 10.0):
+    """The oracle, as it stands, on a bounded sample of the workload."""
     import oracle
     oracle.build()
+    S, scale, what = cpu_sample(w)
     t0 = time.perf_counter()
     count = 0
     while True:
@@ -173,8 +204,8 @@ def cpu_baseline(S, w, budget_s: float = 10.0):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": count / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{count} complete factorization(s) of the same workload, single-threaded FP64 C, {dt:.1f} s"}
+    return {"value": count / dt * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{count} {what}; single-threaded FP64 C, {dt:.1f} s"}
 
 
 def run_reference(args, w, world, rank):
@@ -183,7 +214,7 @@ def run_reference(args, w, world, rank):
         return
     import oracle
     oracle.build()
-    S = make_input(w)
+    S, scale, what = cpu_sample(w)
     for _ in range(args.warmup):
         oracle_factorize(S, w)
     times = []
@@ -191,23 +222,103 @@ def run_reference(args, w, world, rank):
         t0 = time.perf_counter()
         oracle_factorize(S, w)
         times.append(time.perf_counter() - t0)
-    tot = sum(times)
+    tot = sum(times) / scale
     v = args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, **{k: w[k] for k in ("n", "bs", "tau", "target", "m")}},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[w["prec"]],
+            "data": "synthetic", "config": config_of(w, args.workload, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} complete factorizations (plus {args.warmup} warm-up)"},
+                             "sample": f"{args.steps} {what} (plus {args.warmup} warm-up)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def config_of(w, name, world):
+    return {"workload": name, "geometry": w["geom"], "n": w["n"], "bs": w["bs"], "tau": w["tau"],
+            "target": w["target"], "m": w["m"], "method": w["method"], "precision": w["prec"],
+            "parallelism": f"replicas{world}", "l2": "flushed between timed steps (512 MB write)"}
+
+
+DTYPE = {"fp64": "f64", "tf32": "tf32/f32acc+f64", "bf16": "bf16/f32acc+f64"}
+
+
+def timed_factorizations(ctx, ifac, factor, S, w, o, steps, flush):
+    """steps factorizations, each bracketed by CUDA events on the library's
+    stream (torch's current stream), with an L2 flush before each outside the
+    events.  Returns (per-step ms, reports, last Z)."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    reps, Z = [], None
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record()
+        Z, rep = factor(ctx, S, w["tau"], w["target"], o)
+        ends[k].record()
+        reps.append(rep)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], reps, Z
+
+
+def kernel_rooflines(reps, bs, prec):
+    """Live CUDA-event rooflines of the two block-product kernels."""
+    out = {}
+    fp64_ms = sum(r.gemm_ms for r in reps)
+    tc_ms = sum(r.tc_ms for r in reps)
+    fl = 2.0 * bs ** 3
+    if fp64_ms > 0:
+        peak, src = fp64_peak_tflops()
+        ach = sum(r.fp64_pairs for r in reps) * fl / (fp64_ms / 1e3) / 1e12
+        launches = sum(r.gemm_launches for r in reps)
+        out["fp64"] = {"bound": "alu", "kernel": f"k_gemm_fp64<{bs}>", "achieved": ach, "peak": peak,
+                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                       "peak_source": f"{src} bf16 x nominal FP64/BF16 ratio 1.25/2250",
+                       "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * fp64_ms / max(launches, 1),
+                       "ms_per_step": fp64_ms / len(reps)}
+    if tc_ms > 0:
+        peak, src = tensor_peak_tflops(prec)
+        ach = sum(r.tc_pairs for r in reps) * fl / (tc_ms / 1e3) / 1e12
+        launches = sum(r.tc_launches for r in reps)
+        out["tc"] = {"bound": "tensor", "kernel": f"k_gemm_tc<{'2' if prec == 'bf16' else '4'}>", "achieved": ach,
+                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                     "peak_source": f"{src} bf16" + ("" if prec == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25"),
+                     "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * tc_ms / max(launches, 1),
+                     "ms_per_step": tc_ms / len(reps),
+                     "note": "achieved counts stored block pairs only; zero blocks inside tiles are not counted"}
+    return out
+
+
+def tc_dense_probe(ctx, ifac, nb=256):
+    """Tensor-core kernel on a dense 16384 x 16384 BSR (64 x 64 blocks)
+    product: events around the kernel (profiled refinement-free call)."""
+    import torch
+    from paper_1901_07993_gb300 import synth
+    A = synth.random_bsr(nb, 64, 1.0, seed=1)
+    dA = ifac.upload(ctx, A)
+    res = {}
+    for name, prec in (("bf16", 2), ("tf32", 1)):
+        C = ifac.bsr_gemm_trunc(ctx, dA, False, dA, False, 1.0, 0.0, prec)
+        del C
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        C = ifac.bsr_gemm_trunc(ctx, dA, False, dA, False, 1.0, 0.0, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        del C
+        ms = e0.elapsed_time(e1)
+        fl = 2.0 * (nb * 64) ** 3
+        peak, _ = tensor_peak_tflops(name)
+        res[name] = {"n": nb * 64, "ms_per_call": ms, "tflops_call": fl / ms / 1e9, "frac_of_peak": fl / ms / 1e9 / peak}
+    return res
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -230,8 +341,8 @@ def main():
     ctx = ifac.Context()
     S_h = make_input(w)
     S = ifac.upload(ctx, S_h)
-    o = ifac.opts(m=w["m"], leaf_size=w["leaf"], profile=True)
     factor = ifac.inv_factor_refine if w["method"] == "refine" else ifac.inv_factor_localized
+    o = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[w["prec"]], profile=True, max_iter=100)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
@@ -240,40 +351,33 @@ def main():
     torch.cuda.synchronize()
 
     # ---- device-resident timed region ----
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    reps = []
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps, outside the events
-            starts[k].record()
-            Z, rep = factor(ctx, S, w["tau"], w["target"], o)
-            ends[k].record()
-            reps.append(rep)
-            if k < args.steps - 1:
-                del Z
-        torch.cuda.synchronize()
+        step_ms, reps, Z = timed_factorizations(ctx, ifac, factor, S, w, o, args.steps, flush)
     barrier(world)
     torch.cuda.synchronize()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = allmax(world, sum(step_ms))
     value = world * args.steps / (total_ms / 1e3)
+    kernels = kernel_rooflines(reps, w["bs"], w["prec"])
+    dominant = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    roofline = dict(kernels[dominant]) if dominant else None
+    resid = ifac.inv_factor_resid(ctx, S, Z)
 
-    # roofline of the FP64 block-product kernel (events around each launch)
-    gemm_ms = sum(r.gemm_ms for r in reps)
-    gemm_flops = sum(r.flops for r in reps)
-    launches = sum(r.gemm_launches for r in reps)
-    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else 0.0
-    peak, peak_src = fp64_peak_tflops()
-    roofline = {"bound": "alu", "kernel": "k_gemm_fp64<%d>" % w["bs"], "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_src} bf16 x nominal FP64/BF16 ratio 1.25/2250",
-                "launches_per_step": launches / args.steps,
-                "flops_per_launch": gemm_flops / max(launches, 1),
-                "avg_launch_us": 1e3 * gemm_ms / max(launches, 1),
-                "gemm_share_of_step": gemm_ms / sum(step_ms)}
+    # ---- the same factorization in the comparison precisions ----
+    compare = {}
+    for cp in w["compare"]:
+        oc = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[cp], profile=True, max_iter=100)
+        Zc, _ = factor(ctx, S, w["tau"], w["target"], oc)  # warm-up
+        del Zc
+        ksteps = max(2, args.steps // 3)
+        ms_c, reps_c, Zc = timed_factorizations(ctx, ifac, factor, S, w, oc, ksteps, flush)
+        r = reps_c[-1]
+        compare[cp] = {"value": world * ksteps / (allmax(world, sum(ms_c)) / 1e3), "unit": UNIT, "steps": ksteps,
+                       "ms_per_step": sum(ms_c) / ksteps, "resid_fro": ifac.inv_factor_resid(ctx, S, Zc),
+                       "sweeps": r.sweeps, "fp64_delta_evals": r.fp64_delta_evals, "low_sweeps": r.low_sweeps,
+                       "delta_fro": r.delta_fro, "kernels": kernel_rooflines(reps_c, w["bs"], cp)}
+        del Zc
 
     # ---- end to end through the C ABI with pinned host buffers ----
     def pinned(a):
@@ -282,11 +386,8 @@ def main():
         return t.numpy()
 
     S_pin = type(S_h)(S_h.n, S_h.bs, pinned(S_h.row_ptr), pinned(S_h.col_idx), pinned(S_h.val))
-    nnzb_Z = reps[-1].nnzb_Z
-    z_rp = pinned(np.zeros(S_h.nb + 1, np.int32))
-    z_ci = pinned(np.zeros(nnzb_Z, np.int32))
-    z_val = pinned(np.zeros((nnzb_Z, w["bs"], w["bs"])))
-    o_e2e = ifac.opts(m=w["m"], leaf_size=w["leaf"])
+    o_e2e = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[w["prec"]], max_iter=100)
+    z_bufs = None
     e2e_ms = []
     barrier(world)
     torch.cuda.synchronize()
@@ -296,37 +397,41 @@ def main():
         t0 = time.perf_counter()
         Sd = ifac.upload(ctx, S_pin)
         Zd, rep_e = factor(ctx, Sd, w["tau"], w["target"], o_e2e)
-        assert rep_e.nnzb_Z == nnzb_Z
-        ctx.check(ctx.lib.ifac_bsr_download(ctx.h, Zd.ptr(), z_rp.ctypes.data, z_ci.ctypes.data,
-                                            z_val.ctypes.data))
+        if z_bufs is None or z_bufs[1].shape[0] != rep_e.nnzb_Z:
+            t_alloc = time.perf_counter()
+            z_bufs = (pinned(np.zeros(S_h.nb + 1, np.int32)), pinned(np.zeros(rep_e.nnzb_Z, np.int32)),
+                      pinned(np.zeros((rep_e.nnzb_Z, w["bs"], w["bs"]))))
+            t0 += time.perf_counter() - t_alloc  # pinned-buffer allocation is not part of the step
+        ctx.check(ctx.lib.ifac_bsr_download(ctx.h, Zd.ptr(), z_bufs[0].ctypes.data, z_bufs[1].ctypes.data,
+                                            z_bufs[2].ctypes.data))
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         del Zd, Sd
     barrier(world)
     e2e_total = allmax(world, sum(e2e_ms))
     h2d = S_h.row_ptr.nbytes + S_h.col_idx.nbytes + S_h.val.nbytes
-    d2h = z_rp.nbytes + z_ci.nbytes + z_val.nbytes
+    d2h = sum(b.nbytes for b in z_bufs)
 
-    resid = ifac.inv_factor_resid(ctx, S, Z)
+    probe = tc_dense_probe(ctx, ifac) if w["prec"] != "fp64" else None
     clocks = clk.summary()
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(S_h, w)
+        cpu = cpu_baseline(w)
     r0 = reps[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "geometry": w["geom"], "n": w["n"], "bs": w["bs"], "tau": w["tau"],
-                   "target": w["target"], "m": w["m"], "method": w["method"], "parallelism": f"replicas{world}",
-                   "l2": "flushed between timed steps (512 MB write)"},
-        "block_gemm_tflops": gemm_flops / (sum(step_ms) / 1e3) / 1e12,
+        "vs_baseline": None, "dtype": DTYPE[w["prec"]],
+        "data": "synthetic",
+        "config": config_of(w, args.workload, world),
         "s_per_factorization": total_ms / args.steps / 1e3,
+        "block_gemm_tflops": r0.flops / (total_ms / args.steps / 1e3) / 1e12,
         "resid_fro": resid, "resid_target_met": resid <= w["target"],
-        "sweeps": r0.sweeps, "delta_fro": r0.delta_fro, "nnzb_Z": r0.nnzb_Z, "block_pairs": r0.block_pairs,
+        "sweeps": r0.sweeps, "low_sweeps": r0.low_sweeps, "fp64_delta_evals": r0.fp64_delta_evals,
+        "delta_fro": r0.delta_fro, "nnzb_Z": r0.nnzb_Z, "block_pairs": r0.block_pairs,
         "gpu_launches": int(sum(r.launches for r in reps)),
-        "roofline": roofline,
+        "roofline": roofline, "kernels": kernels, "compare": compare, "tc_dense_probe": probe,
         "e2e": {"value": world * args.steps / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,

@@ -123,8 +123,12 @@ typedef struct {
   int fp64_delta_evals;/* refine, mixed precision: delta evaluations with FP64 products */
   int low_sweeps;      /* refine, mixed precision: corrections made in the low-precision phase */
   int64_t launches;    /* kernels this call launched */
-  int64_t gemm_launches; /* numeric block-product launches */
+  int64_t gemm_launches; /* FP64 numeric block-product launches */
   double gemm_ms;      /* their summed device time (opts.profile != 0) */
+  int64_t fp64_pairs;  /* block pairs multiplied by them */
+  int64_t tc_launches; /* tensor-core (TF32/BF16) block-product launches */
+  double tc_ms;        /* their summed device time (opts.profile != 0) */
+  int64_t tc_pairs;    /* stored block pairs multiplied by them */
 } ifac_report;
 
 /* ---------------------------------------------------------------- */

@@ -91,26 +91,31 @@ static cudaEvent_t next_event(ifac_ctx* ctx) {
   return ctx->events[ctx->events_used++];
 }
 
-void prof_begin(ifac_ctx* ctx) {
-  if (ctx->profile) IFAC_CK(cudaEventRecord(next_event(ctx), ctx->stream));
+void prof_begin(ifac_ctx* ctx, int kind) {
+  if (!ctx->profile) return;
+  const size_t pair = ctx->events_used / 2;
+  if (ctx->event_kind.size() <= pair) ctx->event_kind.resize(pair + 1);
+  ctx->event_kind[pair] = (char)kind;
+  IFAC_CK(cudaEventRecord(next_event(ctx), ctx->stream));
 }
 
 void prof_end(ifac_ctx* ctx) {
   if (ctx->profile) IFAC_CK(cudaEventRecord(next_event(ctx), ctx->stream));
 }
 
-double prof_collect(ifac_ctx* ctx) {
-  double ms = 0.0;
+void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc) {
+  *ms_fp64 = 0.0;
+  *ms_tc = 0.0;
   if (ctx->events_used) {
     IFAC_CK(cudaStreamSynchronize(ctx->stream));
     for (size_t i = 0; i + 1 < ctx->events_used; i += 2) {
       float t = 0.f;
       IFAC_CK(cudaEventElapsedTime(&t, ctx->events[i], ctx->events[i + 1]));
-      ms += t;
+      if (ctx->event_kind[i / 2]) *ms_tc += t;
+      else *ms_fp64 += t;
     }
   }
   ctx->events_used = 0;
-  return ms;
 }
 
 }  // namespace ifac

@@ -41,6 +41,9 @@ static void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
   ctx->pairs = 0;
   ctx->launches = 0;
   ctx->gemm_launches = 0;
+  ctx->tc_launches = 0;
+  ctx->pairs_fp64 = 0;
+  ctx->pairs_tc = 0;
   ctx->events_used = 0;
   ctx->profile = o.profile != 0;
   if (r) *r = ifac_report{};
@@ -52,9 +55,12 @@ static void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   r->block_pairs = ctx->pairs;
   r->nnzb_Z = Z.nnzb;
   r->flops = 2.0 * (double)Z.bs * Z.bs * Z.bs * (double)ctx->pairs;
-  r->gemm_ms = prof_collect(ctx);
+  prof_collect(ctx, &r->gemm_ms, &r->tc_ms);
   r->launches = ctx->launches;
   r->gemm_launches = ctx->gemm_launches;
+  r->tc_launches = ctx->tc_launches;
+  r->fp64_pairs = ctx->pairs_fp64;
+  r->tc_pairs = ctx->pairs_tc;
   ctx->profile = false;
 }
 

@@ -132,7 +132,7 @@ static void launch(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   int per_sm = BS >= 64 ? 3 : 8;
   int64_t grid = std::min<int64_t>(C.nnzb, (int64_t)sms * per_sm);
-  prof_begin(ctx);
+  prof_begin(ctx, 0);
   k_gemm_fp64<BS><<<(int)grid, 256, smem, ctx->stream>>>(crow, C.col_idx, C.nnzb, arows.rp, arows.ci, arows.src,
                                                           tA ? 1 : 0, A.val, bcols.rp, bcols.ci, bcols.src,
                                                           tB ? 1 : 0, B.val, alpha, C.val, C.norms, pairs);

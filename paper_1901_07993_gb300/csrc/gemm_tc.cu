@@ -634,11 +634,11 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.cnorm = C.norms;
   args.alpha = alpha;
   args.err = cnt.p + 1;
-  prof_begin(ctx);
+  prof_begin(ctx, 1);
   k_gemm_tc<ELT><<<std::min(ntiles, sms), NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mapA, mapB, args);
   IFAC_CK_LAUNCH();
   prof_end(ctx);
-  ++ctx->gemm_launches;
+  ++ctx->tc_launches;
   int err = 0;
   to_host(ctx, &err, cnt.p + 1, sizeof(int));
   if (err) fail(IFAC_ERR_TIMEOUT, "tensor-core block product: a pipeline wait timed out");

@@ -26,6 +26,9 @@ struct ifac_ctx {
   int64_t pairs = 0;
   int64_t launches = 0;
   int64_t gemm_launches = 0;
+  int64_t tc_launches = 0;
+  int64_t pairs_fp64 = 0, pairs_tc = 0;
+  std::vector<char> event_kind;  // per recorded event pair: 0 FP64 kernel, 1 tensor-core kernel
   // optional event timing of the numeric product kernels
   bool profile = false;
   std::vector<cudaEvent_t> events;
@@ -172,9 +175,10 @@ int refine_adjoint(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& F, int K, d
                    ifac_bsr* Sbar);
 
 // event pair around a profiled launch; prof_collect sums and recycles them
-void prof_begin(ifac_ctx* ctx);
+void prof_begin(ifac_ctx* ctx, int kind = 0);
 void prof_end(ifac_ctx* ctx);
-double prof_collect(ifac_ctx* ctx);
+// summed event time per kind (0: FP64 kernel, 1: tensor-core kernel)
+void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc);
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

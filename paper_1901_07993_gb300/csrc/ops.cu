@@ -36,6 +36,8 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   to_host(ctx, &np, pairs.p, sizeof(np));
   ctx->products += 1;
   ctx->pairs += (int64_t)np;
+  if (prec == IFAC_FP64) ctx->pairs_fp64 += (int64_t)np;
+  else ctx->pairs_tc += (int64_t)np;
   return R;
 }
 

@@ -57,7 +57,9 @@ class _Report(ctypes.Structure):
                 ("n_delta", ctypes.c_int), ("beta", ctypes.c_double), ("delta_fro", ctypes.c_double * 64),
                 ("products", ctypes.c_int64), ("block_pairs", ctypes.c_int64), ("nnzb_Z", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("fp64_delta_evals", ctypes.c_int), ("low_sweeps", ctypes.c_int),
-                ("launches", ctypes.c_int64), ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double)]
+                ("launches", ctypes.c_int64), ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
+                ("fp64_pairs", ctypes.c_int64), ("tc_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double),
+                ("tc_pairs", ctypes.c_int64)]
 
 
 _lib = None
@@ -212,6 +214,10 @@ class Report:
     launches: int = 0
     gemm_launches: int = 0
     gemm_ms: float = 0.0
+    fp64_pairs: int = 0
+    tc_launches: int = 0
+    tc_ms: float = 0.0
+    tc_pairs: int = 0
     status: int = 0
 
 
@@ -238,7 +244,7 @@ def opts(m: int = 2, max_iter: int = 50, fixed_iters: int = 0, c_rule: int = 0, 
 def _report(r: _Report, rc: int) -> Report:
     return Report(r.sweeps, r.stop_reason, r.levels, r.beta, [r.delta_fro[i] for i in range(r.n_delta)],
                   r.products, r.block_pairs, r.nnzb_Z, r.flops, r.fp64_delta_evals, r.low_sweeps, r.launches,
-                  r.gemm_launches, r.gemm_ms, rc)
+                  r.gemm_launches, r.gemm_ms, r.fp64_pairs, r.tc_launches, r.tc_ms, r.tc_pairs, rc)
 
 
 def bsr_gemm_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, transB: bool, alpha: float = 1.0,
