@@ -245,7 +245,9 @@ int leaf_invchol_batched_noalloc(void* stream, int count, int nl, const double* 
  * block product of a sweep runs on the tensor cores with inputs rounded to
  * that format and FP32 accumulation, while sums, block norms, truncation and
  * delta = I - Y stay FP64, until the automatic rule of Section 2.2
- * (||delta_{i+1}||_F > ||delta_i||_F^(m+1): rounding dominates) fires.  From
+ * (||delta_{i+1}||_F > ||delta_i||_F^(m+1): rounding dominates) fires or
+ * ||delta||_F stops decreasing (the rule cannot fire once the rounding floor
+ * of ||delta||_F, which grows like sqrt(n), lies above 1).  From
  * then on delta is evaluated with FP64 products for the same Z and after each
  * correction (the correction M stays low precision, so convergence becomes
  * linear with a rate near the format's unit roundoff), stopping at

@@ -148,9 +148,11 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       else if (!(e < e_prev)) stop = IFAC_STOP_RULE;   // no longer decreasing: the FP64 floor
       else if (it >= o.max_iter) stop = IFAC_STOP_MAXITER;
       if (stop) break;
-    } else if (e > std::pow(e_prev, (double)(o.m + 1)) || it >= o.max_iter) {
-      // the automatic rule of Section 2.2 sees rounding (of the low-precision
-      // products) dominate: evaluate delta with FP64 products for this Z
+    } else if (e > std::pow(e_prev, (double)(o.m + 1)) || !(e < e_prev) || it >= o.max_iter) {
+      // rounding of the low-precision products dominates: the automatic rule
+      // of Section 2.2 fires, or -- when that floor of ||delta||_F lies above
+      // 1, where the rule cannot fire -- delta stops decreasing.  Evaluate
+      // delta with FP64 products for this Z.
       fp64_phase = true;
       e_prev = INFINITY;
       if (rep && rep->n_delta > 0) --rep->n_delta;
