@@ -118,6 +118,26 @@ void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc) {
   ctx->events_used = 0;
 }
 
+void reset_device_counters(ifac_ctx* ctx) {
+  IFAC_CK(cudaMemsetAsync(ctx->dev_pairs, 0, 2 * sizeof(unsigned long long), ctx->stream));
+}
+
+void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc) {
+  unsigned long long h[2] = {0, 0};
+  to_host(ctx, h, ctx->dev_pairs, sizeof(h));
+  *pairs_fp64 = (int64_t)h[0];
+  *pairs_tc = (int64_t)h[1];
+}
+
+void check_device_error(ifac_ctx* ctx) {
+  int e = 0;
+  to_host(ctx, &e, ctx->dev_err, sizeof(int));
+  if (e) {
+    IFAC_CK(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream));
+    fail(IFAC_ERR_TIMEOUT, "a bounded device-side wait expired (tensor-core pipeline)");
+  }
+}
+
 }  // namespace ifac
 
 using namespace ifac;
@@ -180,6 +200,11 @@ int ifac_create(ifac_ctx** out, void* stream, const ifac_allocator* alloc) {
     }
   }
   if (cudaMallocHost(&c->pinned, 4096) != cudaSuccess) { delete c; return IFAC_ERR_CUDA; }
+  void* words = nullptr;
+  if (cudaMalloc(&words, 64) != cudaSuccess) { cudaFreeHost(c->pinned); delete c; return IFAC_ERR_CUDA; }
+  cudaMemset(words, 0, 64);
+  c->dev_err = static_cast<int*>(words);
+  c->dev_pairs = reinterpret_cast<unsigned long long*>(static_cast<char*>(words) + 16);
   *out = c;
   return IFAC_OK;
 }
@@ -189,6 +214,7 @@ void ifac_destroy(ifac_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->dev_err) cudaFree(ctx->dev_err);
   delete ctx;
 }
 
@@ -261,7 +287,7 @@ int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr*
     if (prec != IFAC_FP64 && prec != IFAC_TF32 && prec != IFAC_BF16) fail(IFAC_ERR_INVALID, "unknown precision");
     if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
     Mat R = ifac::gemm(ctx, *A, transA != 0, *B, transB != 0, alpha, tau, prec);
-    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    check_device_error(ctx);
     *C = R.release();
     return IFAC_OK;
   });

@@ -46,11 +46,20 @@ static void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
   ctx->pairs_tc = 0;
   ctx->events_used = 0;
   ctx->profile = o.profile != 0;
+  reset_device_counters(ctx);
   if (r) *r = ifac_report{};
 }
 
 static void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
-  if (!r) return;
+  check_device_error(ctx);
+  read_device_counters(ctx, &ctx->pairs_fp64, &ctx->pairs_tc);
+  ctx->pairs = ctx->pairs_fp64 + ctx->pairs_tc;
+  if (!r) {
+    double a, b;
+    prof_collect(ctx, &a, &b);
+    ctx->profile = false;
+    return;
+  }
   r->products = ctx->products;
   r->block_pairs = ctx->pairs;
   r->nnzb_Z = Z.nnzb;

@@ -186,13 +186,18 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, in
 // the kernel
 // ---------------------------------------------------------------------------
 struct TileArgs {
-  const int32_t* tiles;  // [2*t] tile row, [2*t+1] tile column
-  int ntiles;
+  const int32_t* tiles;      // [2*t] tile row, [2*t+1] tile column
+  const int* ntiles;         // device: number of tiles
   int nb;
-  int W;                 // 32-bit words per bitmap row
-  const uint32_t* bmA;   // pattern bitmap of op(A): bit (I, K)
-  const int32_t* mapA;   // [nb*nb] index of op(A)_IK in the low-precision copy, or its zero block
-  const int32_t* mapB;   // [nb*nb] index of op(B)_KJ, or its zero block
+  int W;                     // 32-bit words per bitmap row
+  const uint32_t* bmA;       // pattern bitmap of op(A): bit (I, K)
+  const int32_t* mapA;       // [nb*nb] index of op(A)_IK in the low-precision copy, or its zero
+                             // block; NULL: binary search in the CSR of op(A) instead
+  const int32_t* mapB;       // same for op(B)_KJ
+  const int32_t* arp;        // CSR of op(A) (block q of the copy = entry q)
+  const int32_t* aci;
+  const int32_t* brp;        // CSR of op(B)
+  const int32_t* bci;
   int a_zero, b_zero;
   const int32_t* crp;    // C pattern
   const int32_t* cci;
@@ -215,6 +220,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int ntiles = *args.ntiles;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t phase = 0;
     uint32_t issued_mask = 0, last_parity = 0;  // lane 0: stages filled / parity of their last fill
     bool ok = true;
-    for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
       for (int wbase = 0; wbase < args.W && ok; wbase += 32) {
         const int w = wbase + lane;
@@ -264,12 +270,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int K = w * 32 + __ffs(word) - 1;
             word &= word - 1u;
             const int slot = __popc(m & ((1u << lane) - 1u));
+            if (args.mapA) {
 #pragma unroll
-            for (int r = 0; r < TM; ++r)
-              rec[slot][r] = (I0 + r < args.nb) ? args.mapA[(size_t)(I0 + r) * args.nb + K] : args.a_zero;
+              for (int r = 0; r < TM; ++r)
+                rec[slot][r] = (I0 + r < args.nb) ? args.mapA[(size_t)(I0 + r) * args.nb + K] : args.a_zero;
 #pragma unroll
-            for (int c = 0; c < C::TN; ++c)
-              rec[slot][TM + c] = (J0 + c < args.nb) ? args.mapB[(size_t)K * args.nb + J0 + c] : args.b_zero;
+              for (int c = 0; c < C::TN; ++c)
+                rec[slot][TM + c] = (J0 + c < args.nb) ? args.mapB[(size_t)K * args.nb + J0 + c] : args.b_zero;
+            } else {
+#pragma unroll
+              for (int r = 0; r < TM; ++r) {
+                int idx = args.a_zero;
+                if (I0 + r < args.nb) {
+                  const int hi = args.arp[I0 + r + 1];
+                  const int q = lower_bound_i32(args.aci, args.arp[I0 + r], hi, K);
+                  if (q < hi && args.aci[q] == K) idx = q;
+                }
+                rec[slot][r] = idx;
+              }
+              const int hi = args.brp[K + 1];
+              int q = lower_bound_i32(args.bci, args.brp[K], hi, J0);
+#pragma unroll
+              for (int c = 0; c < C::TN; ++c) {
+                int idx = args.b_zero;
+                if (q < hi && args.bci[q] == J0 + c) idx = q++;
+                rec[slot][TM + c] = idx;
+              }
+            }
           }
           __syncwarp();
           if (lane == 0) {
@@ -312,7 +339,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int stage = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int I0 = args.tiles[2 * t] * TM;
         // number of K steps: size of the union of the op(A) rows' bitmaps
         int nk = 0;
@@ -354,7 +381,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int r_blk = row / BS, lr = row % BS;
     const int et = threadIdx.x - 64;   // 0..127
     uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
       const bool got = mbar_wait(smem_u32(&acc_full), acc_phase, &abort_flag, args.err);
       __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
@@ -454,50 +481,59 @@ __global__ void k_tile_flags(const int32_t* __restrict__ row, const int32_t* __r
   flag[(size_t)(row[p] / TM) * ntc + ci[p] / tn] = 1;
 }
 
-__global__ void k_tile_list(const uint8_t* __restrict__ flag, int ntr, int ntc, int32_t* __restrict__ out,
-                            int* __restrict__ count) {
-  // single CTA; tiles come out grouped by GROUP tile rows: within a group,
-  // column by column, so concurrently running CTAs share op(B) panels in L2
-  constexpr int GROUP = 8;
-  __shared__ int wcount[32];
-  __shared__ int base, chunk_total;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
+// Tile compaction in grouped order: linear index li runs over groups of GROUP
+// tile rows, column by column inside a group, so that CTAs running at the same
+// time share op(B) panels in L2.  Three passes: count per chunk, scan, write.
+constexpr int GROUP = 8;
+constexpr int CHUNK = 1024;
+
+__device__ __forceinline__ int64_t grouped_to_rowmajor(int64_t li, int ntr, int ntc) {
+  const int64_t g = li / ((int64_t)GROUP * ntc);
+  const int64_t rows = min((int64_t)GROUP, (int64_t)ntr - g * GROUP);
+  const int64_t off = li - g * GROUP * ntc;
+  return (g * GROUP + off % rows) * ntc + off / rows;
+}
+
+__global__ void k_tile_count(const uint8_t* __restrict__ flag, int ntr, int ntc, int32_t* __restrict__ cnt) {
+  __shared__ int red[32];
   const int64_t tot = (int64_t)ntr * ntc;
-  for (int64_t s = 0; s < tot; s += blockDim.x) {
-    const int64_t li = s + threadIdx.x;
-    int64_t i = 0;
-    if (li < tot) {  // li-th tile in grouped order -> row-major index i
-      const int64_t g = li / ((int64_t)GROUP * ntc);
-      const int64_t rows = min((int64_t)GROUP, (int64_t)ntr - g * GROUP);
-      const int64_t off = li - g * GROUP * ntc;
-      i = (g * GROUP + off % rows) * ntc + off / rows;
-    }
-    const bool f = li < tot && flag[i];
-    const unsigned m = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) wcount[w] = __popc(m);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int acc = 0;
-      for (int k = 0; k < nw; ++k) {
-        const int c = wcount[k];
-        wcount[k] = acc;
-        acc += c;
-      }
-      chunk_total = acc;
-    }
-    __syncthreads();
-    if (f) {
-      const int pos = base + wcount[w] + __popc(m & ((1u << lane) - 1u));
-      out[2 * pos] = (int32_t)(i / ntc);
-      out[2 * pos + 1] = (int32_t)(i % ntc);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) base += chunk_total;
-    __syncthreads();
+  const int64_t li = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  const int f = (li < tot && flag[grouped_to_rowmajor(li, ntr, ntc)]) ? 1 : 0;
+  const unsigned m = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < CHUNK / 32; ++w) t += red[w];
+    cnt[blockIdx.x] = t;
   }
-  if (threadIdx.x == 0) *count = base;
+}
+
+__global__ void k_tile_write(const uint8_t* __restrict__ flag, int ntr, int ntc, const int32_t* __restrict__ off,
+                             int32_t* __restrict__ out) {
+  __shared__ int wbase[32];
+  const int64_t tot = (int64_t)ntr * ntc;
+  const int64_t li = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  const int64_t i = li < tot ? grouped_to_rowmajor(li, ntr, ntc) : 0;
+  const bool f = li < tot && flag[i];
+  const unsigned m = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wbase[w] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < CHUNK / 32; ++k) {
+      const int c = wbase[k];
+      wbase[k] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  if (f) {
+    const int pos = off[blockIdx.x] + wbase[w] + __popc(m & ((1u << lane) - 1u));
+    out[2 * pos] = (int32_t)(i / ntc);
+    out[2 * pos + 1] = (int32_t)(i % ntc);
+  }
 }
 
 // dense block-index map of a CSR pattern: map[I*nb + J] = q for block q, else zero_idx
@@ -583,34 +619,40 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   const CUtensorMap mapA = make_map<ELT>(la.p, A.nnzb + 1);
   const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
-  // K sets (bitmap rows of op(A)) and dense block-index maps of op(A), op(B)
+  // K sets (bitmap rows of op(A)); dense block-index maps of op(A), op(B)
+  // while they stay small, binary searches in the CSR patterns beyond that
   Buf<uint32_t> bmA = pattern_bitmap(ctx, A, tA);
   const int64_t nb2 = (int64_t)nb * nb;
-  Buf<int32_t> imA(ctx, nb2), imB(ctx, nb2);
-  k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imA.p, nb2, (int32_t)A.nnzb);
-  IFAC_CK_LAUNCH();
-  k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imB.p, nb2, (int32_t)B.nnzb);
-  IFAC_CK_LAUNCH();
-  k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, imA.p);
-  IFAC_CK_LAUNCH();
-  k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
-  IFAC_CK_LAUNCH();
-  // tiles holding a block of C's pattern
+  const bool dense_maps = nb2 <= (int64_t)4 << 20;
+  Buf<int32_t> imA, imB;
+  if (dense_maps) {
+    imA = Buf<int32_t>(ctx, nb2);
+    imB = Buf<int32_t>(ctx, nb2);
+    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imA.p, nb2, (int32_t)A.nnzb);
+    IFAC_CK_LAUNCH();
+    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imB.p, nb2, (int32_t)B.nnzb);
+    IFAC_CK_LAUNCH();
+    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, imA.p);
+    IFAC_CK_LAUNCH();
+    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
+    IFAC_CK_LAUNCH();
+  }
+  // tiles holding a block of C's pattern, compacted in grouped order
   const int ntr = cdiv(nb, TM), ntc = cdiv(nb, Cf::TN);
-  Buf<uint8_t> flags(ctx, (size_t)ntr * ntc);
-  Buf<int32_t> tiles(ctx, (size_t)2 * ntr * ntc);
-  Buf<int> cnt(ctx, 2);  // [0] tiles, [1] error flag
-  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntr * ntc, ctx->stream));
-  IFAC_CK(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int), ctx->stream));
+  const int64_t ntot = (int64_t)ntr * ntc;
+  const int nchunk = cdiv(ntot, CHUNK);
+  Buf<uint8_t> flags(ctx, (size_t)ntot);
+  Buf<int32_t> tiles(ctx, (size_t)2 * ntot), ccnt(ctx, nchunk), coff(ctx, nchunk + 1);
+  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntot, ctx->stream));
   k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, Cf::TN, ntc, flags.p);
   IFAC_CK_LAUNCH();
-  k_tile_list<<<1, 1024, 0, ctx->stream>>>(flags.p, ntr, ntc, tiles.p, cnt.p);
+  k_tile_count<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
+  IFAC_CK_LAUNCH();
+  scan_counts(ctx, ccnt.p, coff.p, nchunk, false);
+  k_tile_write<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, coff.p, tiles.p);
   IFAC_CK_LAUNCH();
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
-  int ntiles = 0;
-  to_host(ctx, &ntiles, cnt.p, sizeof(int));
-  if (ntiles == 0) return;
   static bool attr = false;
   if (!attr) {
     IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
@@ -620,12 +662,16 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   TileArgs args;
   args.tiles = tiles.p;
-  args.ntiles = ntiles;
+  args.ntiles = coff.p + nchunk;  // the scan's total
   args.nb = nb;
   args.W = words_per_row(nb);
   args.bmA = bmA.p;
-  args.mapA = imA.p;
-  args.mapB = imB.p;
+  args.mapA = dense_maps ? imA.p : nullptr;
+  args.mapB = dense_maps ? imB.p : nullptr;
+  args.arp = arows.rp;
+  args.aci = arows.ci;
+  args.brp = brows.rp;
+  args.bci = brows.ci;
   args.a_zero = (int)A.nnzb;
   args.b_zero = (int)B.nnzb;
   args.crp = C.row_ptr;
@@ -633,15 +679,15 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.cval = C.val;
   args.cnorm = C.norms;
   args.alpha = alpha;
-  args.err = cnt.p + 1;
+  args.err = ctx->dev_err;
+  // the grid does not depend on the tile count (read on the device), so no
+  // host read-back is needed here; idle CTAs return at once
+  const int64_t grid = std::min<int64_t>(ntot, sms);
   prof_begin(ctx, 1);
-  k_gemm_tc<ELT><<<std::min(ntiles, sms), NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mapA, mapB, args);
+  k_gemm_tc<ELT><<<(int)grid, NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mapA, mapB, args);
   IFAC_CK_LAUNCH();
   prof_end(ctx);
   ++ctx->tc_launches;
-  int err = 0;
-  to_host(ctx, &err, cnt.p + 1, sizeof(int));
-  if (err) fail(IFAC_ERR_TIMEOUT, "tensor-core block product: a pipeline wait timed out");
 }
 
 }  // namespace tc

@@ -35,6 +35,10 @@ struct ifac_ctx {
   size_t events_used = 0;
   // small pinned host buffer for scalar read-backs
   void* pinned = nullptr;
+  // device words: [0] error flag set by bounded waits that expired;
+  // counters [1] FP64 and [2] tensor-core block pairs of the current call
+  int* dev_err = nullptr;
+  unsigned long long* dev_pairs = nullptr;
 };
 
 namespace ifac {
@@ -179,6 +183,12 @@ void prof_begin(ifac_ctx* ctx, int kind = 0);
 void prof_end(ifac_ctx* ctx);
 // summed event time per kind (0: FP64 kernel, 1: tensor-core kernel)
 void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc);
+
+// Zero the device counters / read them back (read_* synchronises).
+void reset_device_counters(ifac_ctx* ctx);
+void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc);
+// Fails with IFAC_ERR_TIMEOUT (and clears the flag) if a device wait expired.
+void check_device_error(ifac_ctx* ctx);
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

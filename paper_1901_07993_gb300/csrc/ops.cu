@@ -22,22 +22,16 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   C.m.col_idx = P.ci.release();
   C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
-  Buf<unsigned long long> pairs(ctx, 1);
-  IFAC_CK(cudaMemsetAsync(pairs.p, 0, sizeof(unsigned long long), ctx->stream));
+  // multiplied block pairs accumulate in the context's device counters
   if (prec == IFAC_FP64) {
     View bcols = view_rows(ctx, B, !tB);
-    gemm_numeric_fp64(ctx, arows, tA, A, bcols, tB, B, alpha, C.m, P.row.p, pairs.p);
+    gemm_numeric_fp64(ctx, arows, tA, A, bcols, tB, B, alpha, C.m, P.row.p, ctx->dev_pairs);
   } else {
     View brows = view_rows(ctx, B, tB);
-    gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, pairs.p);
+    gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, ctx->dev_pairs + 1);
   }
   Mat R = compact(ctx, std::move(C), P.row.p, tau);
-  unsigned long long np = 0;
-  to_host(ctx, &np, pairs.p, sizeof(np));
   ctx->products += 1;
-  ctx->pairs += (int64_t)np;
-  if (prec == IFAC_FP64) ctx->pairs_fp64 += (int64_t)np;
-  else ctx->pairs_tc += (int64_t)np;
   return R;
 }
 
