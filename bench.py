@@ -44,6 +44,13 @@ WORKLOADS = {
     "irsi-mixed-chain-n262144-bs64": dict(geom="chain", n=262144, bs=64, tau=1e-12, target=1e-10, method="refine",
                                           m=2, seed=0, leaf=512, prec="tf32", compare=("fp64", "bf16"),
                                           sample_n=4096),
+    # one block-sparse product on a fully dense 256 x 256 pattern of 64 x 64
+    # blocks (n = 16384), BF16 inputs, FP32 accumulation: the tensor-core kernel alone
+    "product-dense-bf16-n16384": dict(geom="dense", n=16384, bs=64, tau=0.0, target=0.0, method="product", m=2,
+                                      seed=1, leaf=512, prec="bf16", compare=(), sample_n=None),
+    # the same at n = 8192 (operands of about L2 size): the profiling case
+    "product-dense-bf16-n8192": dict(geom="dense", n=8192, bs=64, tau=0.0, target=0.0, method="product", m=2,
+                                     seed=1, leaf=512, prec="bf16", compare=(), sample_n=None),
     # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
@@ -314,6 +321,47 @@ def tc_dense_probe(ctx, ifac, nb=256):
     return res
 
 
+def run_product(args, w, world, rank, local, ctx, ifac):
+    """One block-sparse product per step (dense pattern), CUDA events around the call."""
+    import torch
+    from paper_1901_07993_gb300 import synth
+    nb = w["n"] // w["bs"]
+    A = synth.random_bsr(nb, w["bs"], 1.0, seed=w["seed"])
+    dA = ifac.upload(ctx, A)
+    prec = PREC[w["prec"]]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        C = ifac.bsr_gemm_trunc(ctx, dA, False, dA, False, 1.0, 0.0, prec)
+        del C
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record()
+            C = ifac.bsr_gemm_trunc(ctx, dA, False, dA, False, 1.0, 0.0, prec)
+            ends[k].record()
+            del C
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total = allmax(world, sum(ms))
+    fl = 2.0 * w["n"] ** 3
+    peak, src = tensor_peak_tflops(w["prec"])
+    ach = fl / (sum(ms) / args.steps / 1e3) / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": "block-sparse product TFLOP/s (dense pattern, tensor cores)", "value": world * args.steps / (total / 1e3),
+            "unit": "products/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[w["prec"]], "data": "synthetic", "config": config_of(w, args.workload, world),
+            "roofline": {"bound": "tensor", "kernel": "k_gemm_tc (whole bsr_gemm_trunc call)", "achieved": ach,
+                         "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                         "peak_source": src}, "clocks": clk.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,6 +387,9 @@ def main():
     from paper_1901_07993_gb300 import ifac
     libbuild.build()
     ctx = ifac.Context()
+    if w["method"] == "product":
+        run_product(args, w, world, rank, local, ctx, ifac)
+        return
     S_h = make_input(w)
     S = ifac.upload(ctx, S_h)
     factor = ifac.inv_factor_refine if w["method"] == "refine" else ifac.inv_factor_localized
