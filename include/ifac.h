@@ -129,6 +129,7 @@ typedef struct {
   int64_t tc_launches; /* tensor-core (TF32/BF16) block-product launches */
   double tc_ms;        /* their summed device time (opts.profile != 0) */
   int64_t tc_pairs;    /* stored block pairs multiplied by them */
+  double resid_fro;    /* batched: ||I - Z^T S Z||_F with FP64 products (else 0) */
 } ifac_report;
 
 /* ---------------------------------------------------------------- */
@@ -270,6 +271,23 @@ int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double targe
  * already be in the wanted order (e.g. recursive coordinate bisection). */
 int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
                          const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
+
+/* Refinement from a scaled identity (as inv_factor_refine, Section 2.2) of
+ * `count` independent matrices S[0..count-1] in one launch sequence: the
+ * members sit on the diagonal of one block-diagonal matrix, so every block
+ * product of a sweep serves all of them.  Each member has its own Gershgorin
+ * bound, Z_0 = c_k I, ||delta||_F and stop test (target, the rule of Section
+ * 2.2, and -- for opts->prec TF32/BF16, where rounding of the low-precision
+ * products sets the floor -- ||delta||_F no longer decreasing, or max_iter);
+ * a stopped member leaves the batch.  All block products use opts->prec (on
+ * the tensor cores for TF32/BF16, bs = 64); the final residual of every
+ * member is evaluated with FP64 products and returned in rep[k].resid_fro.
+ * All members need the same bs.  Z[k] (count entries) receive the factors;
+ * rep may be NULL or hold count reports (batch-wide counters are repeated in
+ * each).  Returns IFAC_WARN_TARGET_NOT_MET if any member stopped above the
+ * target. */
+int inv_factor_refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, double target,
+                              const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
 
 /* Reverse-mode derivative of K refinement sweeps of Eq. (2.1) (m = 2, from
  * Z_0 = c I, c = 1/sqrt(beta) of the truncated S, held constant) on a frozen

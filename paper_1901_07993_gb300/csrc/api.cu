@@ -385,6 +385,23 @@ int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double ta
   });
 }
 
+int inv_factor_refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, double target,
+                              const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep) {
+  if (Z && count > 0)
+    for (int k = 0; k < count; ++k) Z[k] = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    if (count <= 0 || !S || !Z) fail(IFAC_ERR_INVALID, "batched: empty batch or NULL arrays");
+    check_opts(opts, true);
+    for (int k = 0; k < count; ++k) {
+      validate(S[k], "S[k]");
+      if (S[k]->bs != S[0]->bs) fail(IFAC_ERR_INVALID, "batched: members differ in block size");
+    }
+    if (opts->prec != IFAC_FP64 && S[0]->bs != 64) fail(IFAC_ERR_UNSUPPORTED, "tensor-core products need bs = 64");
+    if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
+    return refine_batched(ctx, count, S, tau, target, *opts, Z, rep);
+  });
+}
+
 int inv_factor_refine_adjoint(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* F, int K, double tau, double* L,
                               ifac_bsr* Sbar) {
   if (Sbar) *Sbar = ifac_bsr{};

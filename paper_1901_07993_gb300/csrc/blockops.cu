@@ -174,6 +174,12 @@ __global__ void k_max(const double* __restrict__ x, int64_t n, double* __restric
   }
 }
 
+void gershgorin_rows(ifac_ctx* ctx, const ifac_bsr& A, double* rs) {
+  const int64_t rows = (int64_t)A.nb * A.bs;
+  k_abs_rowsum<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(A.row_ptr, A.nb, A.bs, A.val, rs);
+  IFAC_CK_LAUNCH();
+}
+
 double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A) {
   int64_t rows = (int64_t)A.nb * A.bs;
   Buf<double> rs(ctx, rows), out(ctx, 1);

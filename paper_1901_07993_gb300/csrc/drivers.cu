@@ -392,6 +392,10 @@ static Mat leaf_factors(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<Node
   return compact(ctx, std::move(Z), nullptr, tau);
 }
 
+Mat filter_rows_active(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* seg, const uint8_t* active) {
+  return filter(ctx, A, seg, nullptr, active, F_ROWS_IN);
+}
+
 // per-sub-problem ||delta||_F: rows of sub-problem s are [b0_s, b1_s)
 __global__ void k_node_fro(const double* __restrict__ rowsq, const int32_t* __restrict__ nb0,
                            const int32_t* __restrict__ nb1, int nnodes, double* __restrict__ out) {
@@ -400,6 +404,13 @@ __global__ void k_node_fro(const double* __restrict__ rowsq, const int32_t* __re
   double t = 0.0;
   for (int r = nb0[s]; r < nb1[s]; ++r) t += rowsq[r];
   out[s] = sqrt(t);
+}
+
+void node_fro(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* nb0, const int32_t* nb1, int nn, double* out_dev) {
+  Buf<double> rowsq(ctx, A.nb);
+  row_sq_norms(ctx, A, rowsq.p);
+  k_node_fro<<<cdiv(nn, 128), 128, 0, ctx->stream>>>(rowsq.p, nb0, nb1, nn, out_dev);
+  IFAC_CK_LAUNCH();
 }
 
 // ---------------------------------------------------------------------------

@@ -154,6 +154,8 @@ void block_norms(ifac_ctx* ctx, const ifac_bsr& A, double* norms);
 void row_sq_norms(ifac_ctx* ctx, const ifac_bsr& A, double* rowsq);
 double fro_host(ifac_ctx* ctx, const ifac_bsr& A);
 double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
+// sum_j |A_ij| for every scalar row i (nb * bs values)
+void gershgorin_rows(ifac_ctx* ctx, const ifac_bsr& A, double* rs);
 Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 
 // ---- operations used by drivers (ops.cu) ----
@@ -175,6 +177,8 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S, double tau, double targe
 int lif(ifac_ctx* ctx, const ifac_bsr& S, double tau, double target, const ifac_opts& o,
         ifac_bsr* Z, ifac_report* rep);
 double resid(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& Z);
+int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, double target,
+                   const ifac_opts& o, ifac_bsr* Z, ifac_report* reps);
 int refine_adjoint(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& F, int K, double tau, double* L,
                    ifac_bsr* Sbar);
 

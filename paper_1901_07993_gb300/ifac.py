@@ -31,7 +31,7 @@ EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", 
            "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_add",
            "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
            "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
-           "inv_factor_refine_adjoint")
+           "inv_factor_refine_adjoint", "inv_factor_refine_batched")
 
 
 class IfacError(RuntimeError):
@@ -59,7 +59,7 @@ class _Report(ctypes.Structure):
                 ("flops", ctypes.c_double), ("fp64_delta_evals", ctypes.c_int), ("low_sweeps", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
                 ("fp64_pairs", ctypes.c_int64), ("tc_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double),
-                ("tc_pairs", ctypes.c_int64)]
+                ("tc_pairs", ctypes.c_int64), ("resid_fro", ctypes.c_double)]
 
 
 _lib = None
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "inv_factor_resid": ([p, PB, PB, ctypes.POINTER(d)], i32),
         "leaf_invchol_batched_noalloc": ([p, i32, i32, p, p, p], i32),
         "inv_factor_refine_adjoint": ([p, PB, PB, i32, d, ctypes.POINTER(d), PB], i32),
+        "inv_factor_refine_batched": ([p, i32, p, d, d, ctypes.POINTER(_Opts), p, p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +219,7 @@ class Report:
     tc_launches: int = 0
     tc_ms: float = 0.0
     tc_pairs: int = 0
+    resid_fro: float = 0.0
     status: int = 0
 
 
@@ -244,7 +246,7 @@ def opts(m: int = 2, max_iter: int = 50, fixed_iters: int = 0, c_rule: int = 0, 
 def _report(r: _Report, rc: int) -> Report:
     return Report(r.sweeps, r.stop_reason, r.levels, r.beta, [r.delta_fro[i] for i in range(r.n_delta)],
                   r.products, r.block_pairs, r.nnzb_Z, r.flops, r.fp64_delta_evals, r.low_sweeps, r.launches,
-                  r.gemm_launches, r.gemm_ms, r.fp64_pairs, r.tc_launches, r.tc_ms, r.tc_pairs, rc)
+                  r.gemm_launches, r.gemm_ms, r.fp64_pairs, r.tc_launches, r.tc_ms, r.tc_pairs, r.resid_fro, rc)
 
 
 def bsr_gemm_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, transB: bool, alpha: float = 1.0,
@@ -310,6 +312,23 @@ def inv_factor_localized(ctx: Context, S: DeviceBSR, tau: float, target: float, 
     rc = ctx.check(ctx.lib.inv_factor_localized(ctx.h, S.ptr(), tau, target, ctypes.byref(o or opts()),
                                                 ctypes.byref(Z), ctypes.byref(rep)))
     return DeviceBSR(ctx, Z), _report(rep, rc)
+
+
+def inv_factor_refine_batched(ctx: Context, Ss, tau: float, target: float, o: _Opts | None = None):
+    """Refine a list of DeviceBSR together; returns ([Z_k], [Report_k], status)."""
+    count = len(Ss)
+    ptrs = (ctypes.POINTER(_Bsr) * count)(*[ctypes.pointer(S.raw) for S in Ss])
+    Zs = (_Bsr * count)()
+    reps = (_Report * count)()
+    rc = ctx.check(ctx.lib.inv_factor_refine_batched(ctx.h, count, ctypes.cast(ptrs, ctypes.c_void_p), tau, target,
+                                                     ctypes.byref(o or opts()), ctypes.cast(Zs, ctypes.c_void_p),
+                                                     ctypes.cast(reps, ctypes.c_void_p)))
+    out = []
+    for k in range(count):
+        z = _Bsr()
+        ctypes.pointer(z)[0] = Zs[k]
+        out.append(DeviceBSR(ctx, z))
+    return out, [_report(reps[k], rc) for k in range(count)], rc
 
 
 def inv_factor_refine_adjoint(ctx: Context, S, F, K: int = 6, tau: float = 1e-10):
