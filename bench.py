@@ -51,6 +51,12 @@ WORKLOADS = {
     # the same at n = 8192 (operands of about L2 size): the profiling case
     "product-dense-bf16-n8192": dict(geom="dense", n=8192, bs=64, tau=0.0, target=0.0, method="product", m=2,
                                      seed=1, leaf=512, prec="bf16", compare=(), sample_n=None),
+    # 64 independent matrices refined together: 32 chains and 32 3D clusters,
+    # sizes log-uniform in [512, 8192] (seed 3, member j generated with seed
+    # 3000 + j), BSR 64x64, TF32 products, FP64 final residual of every member
+    "batch64-tf32-n512-8192": dict(geom="batch", n=0, bs=64, tau=1e-10, target=1e-10, method="batched", m=2,
+                                   seed=3, leaf=512, prec="tf32", compare=(), sample_n=None,
+                                   count=64, nmin=512, nmax=8192),
     # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
@@ -321,6 +327,66 @@ def tc_dense_probe(ctx, ifac, nb=256):
     return res
 
 
+def batch_inputs(w):
+    """Members of the batch workload: sizes log-uniform in [nmin, nmax] drawn
+    with numpy PCG64 (seed), alternating chain and 3D cluster."""
+    import numpy as np
+    from paper_1901_07993_gb300 import synth
+    rng = np.random.default_rng(w["seed"])
+    sizes = np.exp(rng.uniform(np.log(w["nmin"]), np.log(w["nmax"]), size=w["count"])).astype(int)
+    out = []
+    for j, n in enumerate(sizes):
+        if j % 2 == 0:
+            out.append(synth.chain_overlap(int(n), w["bs"], seed=1000 * w["seed"] + j))
+        else:
+            out.append(synth.cluster_overlap(int(n), w["bs"], seed=1000 * w["seed"] + j))
+    return out
+
+
+def run_batched(args, w, world, rank, local, ctx, ifac):
+    """One batched refinement of all members per step (inputs resident)."""
+    import numpy as np
+    import torch
+    members = batch_inputs(w)
+    dS = [ifac.upload(ctx, S) for S in members]
+    o = ifac.opts(m=w["m"], prec=PREC[w["prec"]], profile=True, max_iter=100)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        Zs, reps, rc = ifac.inv_factor_refine_batched(ctx, dS, w["tau"], w["target"], o)
+        del Zs
+    torch.cuda.synchronize()
+    ms, last = [], None
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            Zs, reps, rc = ifac.inv_factor_refine_batched(ctx, dS, w["tau"], w["target"], o)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            last = reps
+            del Zs
+    barrier(world)
+    total = allmax(world, sum(ms))
+    r0 = last[0]
+    kern = kernel_rooflines([last[0]], w["bs"], w["prec"])
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * args.steps / (total / 1e3), "unit": "batches/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[w["prec"]], "data": "synthetic",
+            "config": {**config_of(w, args.workload, world), "count": w["count"],
+                       "sizes": [int(S.n) for S in members]},
+            "members": [{"n": int(S.n), "kind": "chain" if j % 2 == 0 else "cluster", "sweeps": r.sweeps,
+                         "resid_fro_fp64": r.resid_fro, "stop": r.stop_reason}
+                        for j, (S, r) in enumerate(zip(members, last))],
+            "block_pairs": r0.block_pairs, "block_gemm_tflops": r0.flops / (total / args.steps / 1e3) / 1e12,
+            "kernels": kern, "roofline": max(kern.values(), key=lambda v: v["ms_per_step"]) if kern else None,
+            "gpu_launches": int(r0.launches * args.steps), "clocks": clk.summary()}), flush=True)
+
+
 def run_product(args, w, world, rank, local, ctx, ifac):
     """One block-sparse product per step (dense pattern), CUDA events around the call."""
     import torch
@@ -389,6 +455,9 @@ def main():
     ctx = ifac.Context()
     if w["method"] == "product":
         run_product(args, w, world, rank, local, ctx, ifac)
+        return
+    if w["method"] == "batched":
+        run_batched(args, w, world, rank, local, ctx, ifac)
         return
     S_h = make_input(w)
     S = ifac.upload(ctx, S_h)
