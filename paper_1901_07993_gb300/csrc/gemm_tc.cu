@@ -52,7 +52,7 @@ struct Cfg {
   static constexpr int B_BYTES = ATOMS * B_ATOM_BYTES;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (ELT == 2) ? 4 : 3;
-  static constexpr int TMEM_COLS = N;                   // FP32 accumulator columns
+  static constexpr int TMEM_COLS = 2 * N;               // two FP32 accumulators (double buffer)
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
   static constexpr uint32_t TX_BYTES = (uint32_t)(TM + TN) * BS * BS * ELT;
 };
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   using C = Cfg<ELT>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[C::STAGES], empty_bar[C::STAGES];
-  __shared__ __align__(8) uint64_t acc_full, acc_empty, drain_bar;
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain_bar;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
   __shared__ double partial[4][C::TN];
@@ -228,8 +228,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    mbar_init(smem_u32(&acc_full), 1);
-    mbar_init(smem_u32(&acc_empty), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), 1);
+    }
     mbar_init(smem_u32(&drain_bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -337,7 +339,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------ MMA issuer ------------------------------
     if (lane == 0) {
       int stage = 0;
-      uint32_t phase = 0, acc_phase = 0;
+      uint32_t phase = 0;
+      int tl = 0;  // this CTA's tile counter: accumulator buffer tl & 1, its phase (tl >> 1) & 1
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int I0 = args.tiles[2 * t] * TM;
@@ -350,7 +353,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (I0 + r < args.nb) word |= args.bmA[(size_t)(I0 + r) * args.W + w];
           nk += __popc(word);
         }
-        if (!mbar_wait(smem_u32(&acc_empty), acc_phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
+        const int ab = tl & 1;
+        const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
+        const uint32_t tacc = tmem + (uint32_t)(ab * C::N);
+        if (!mbar_wait(smem_u32(&acc_empty[ab]), aphase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
         tc_fence_after();
         for (int k = 0; k < nk; ++k) {
           if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, args.err)) { ok = false; break; }
@@ -360,15 +366,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < C::KSTEPS; ++kk) {
             const int atom = kk / (C::ATOM_ELEMS / C::MMA_K), off = (kk % (C::ATOM_ELEMS / C::MMA_K)) * 32;
-            mma_issue<ELT>(tmem, smem_desc(sa + atom * C::A_ATOM_BYTES + off),
+            mma_issue<ELT>(tacc, smem_desc(sa + atom * C::A_ATOM_BYTES + off),
                            smem_desc(sb + atom * C::B_ATOM_BYTES + off), (k > 0 || kk > 0) ? 1u : 0u);
           }
           mma_commit(smem_u32(&empty_bar[stage]));
           if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
-        mma_commit(smem_u32(&acc_full));
-        acc_phase ^= 1u;
+        mma_commit(smem_u32(&acc_full[ab]));
+        ++tl;
       }
       // every MMA this thread issued completes before tensor memory is released
       mma_commit(smem_u32(&drain_bar));
@@ -380,10 +386,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int row = q * 32 + lane;     // accumulator row 0..127
     const int r_blk = row / BS, lr = row % BS;
     const int et = threadIdx.x - 64;   // 0..127
-    uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int tl = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const int ab = tl & 1;
+      const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
       const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
-      const bool got = mbar_wait(smem_u32(&acc_full), acc_phase, &abort_flag, args.err);
+      const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
       __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
       if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int h = 0; h < BS / 32; ++h) {
           float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * BS + h * 32), v);
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
           if (p >= 0) {
             double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
 #pragma unroll
@@ -432,8 +440,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       epi_bar();
-      if (et == 0) mbar_arrive(smem_u32(&acc_empty));
-      acc_phase ^= 1u;
+      if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
     }
   }
   tc_fence_before();
