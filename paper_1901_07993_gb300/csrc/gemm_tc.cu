@@ -34,6 +34,7 @@ namespace tc {
 
 constexpr int BS = 64;
 constexpr int TM = 2;
+constexpr int CL = 2;  // CTAs per cluster: vertically adjacent tiles sharing one op(B) panel
 constexpr int NTHREADS = 192;
 constexpr long long WAIT_LIMIT = 1ll << 27;
 
@@ -109,6 +110,36 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// the same box into the same shared-memory offset of every CTA in `mask`,
+// signalling each CTA's mbarrier at the same offset
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -149,6 +180,14 @@ __device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint6
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// completion of this thread's MMAs arrives on the mbarrier at `bar` in every CTA of `mask`
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   bar),
+               "h"(mask)
+               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -221,12 +260,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int ntiles = *args.ntiles;
+  // A cluster of CL CTAs takes one super-tile of CL*TM x TN blocks; CTA `crank`
+  // computes block rows (super row * CL + crank) * TM.  Both CTAs step through
+  // the same K set (the union over the super-tile's rows), each loads its own
+  // op(A) blocks and half of the op(B) panel, multicast to both.
+  const uint32_t crank = cluster_rank();
+  const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
+  constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), CL);  // released by the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -242,6 +288,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // every CTA's barriers exist before any multicast lands
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
 
@@ -255,15 +302,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t phase = 0;
     uint32_t issued_mask = 0, last_parity = 0;  // lane 0: stages filled / parity of their last fill
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      const int S0 = args.tiles[2 * t] * (CL * TM);
+      const int I0 = S0 + (int)crank * TM, J0 = args.tiles[2 * t + 1] * C::TN;
       for (int wbase = 0; wbase < args.W && ok; wbase += 32) {
         const int w = wbase + lane;
         uint32_t word = 0;
         if (w < args.W) {
 #pragma unroll
-          for (int r = 0; r < TM; ++r)
-            if (I0 + r < args.nb) word |= args.bmA[(size_t)(I0 + r) * args.W + w];
+          for (int r = 0; r < CL * TM; ++r)
+            if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
         }
         while (__any_sync(0xffffffffu, word != 0u) && ok) {
           const bool has = word != 0u;
@@ -317,11 +365,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int a = 0; a < C::ATOMS; ++a)
                   tma_load_2d(sa + a * C::A_ATOM_BYTES + r * BS * 128, &mapA, a * C::ATOM_ELEMS, rec[j][r] * BS, fb);
 #pragma unroll
-              for (int c = 0; c < C::TN; ++c)
+              for (int c = (int)crank * (C::TN / CL); c < ((int)crank + 1) * (C::TN / CL); ++c)
 #pragma unroll
                 for (int a = 0; a < C::ATOMS; ++a)
-                  tma_load_2d(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS,
-                              rec[j][TM + c] * BS, fb);
+                  tma_load_2d_mc(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS,
+                                 rec[j][TM + c] * BS, fb, CL_MASK);
               if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
             }
           }
@@ -330,11 +378,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-    // copies lane 0 issued must land before the CTA exits
+    // before the CTA exits: the copies lane 0 issued (and the peer's multicast
+    // halves) have landed, and both CTAs' MMAs have released every slot, so no
+    // remote arrive can reach this CTA's barriers after it leaves
     if (lane == 0)
       for (int s = 0; s < C::STAGES; ++s)
-        if (issued_mask & (1u << s))
+        if (issued_mask & (1u << s)) {
           mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+          mbar_wait(smem_u32(&empty_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+        }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer ------------------------------
     if (lane == 0) {
@@ -342,15 +394,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t phase = 0;
       int tl = 0;  // this CTA's tile counter: accumulator buffer tl & 1, its phase (tl >> 1) & 1
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int I0 = args.tiles[2 * t] * TM;
-        // number of K steps: size of the union of the op(A) rows' bitmaps
+      for (int t = cid; t < ntiles && ok; t += ncl) {
+        const int S0 = args.tiles[2 * t] * (CL * TM);
+        // number of K steps: size of the union of the super-tile rows' bitmaps
         int nk = 0;
         for (int w = 0; w < args.W; ++w) {
           uint32_t word = 0;
 #pragma unroll
-          for (int r = 0; r < TM; ++r)
-            if (I0 + r < args.nb) word |= args.bmA[(size_t)(I0 + r) * args.W + w];
+          for (int r = 0; r < CL * TM; ++r)
+            if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
           nk += __popc(word);
         }
         const int ab = tl & 1;
@@ -369,7 +421,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mma_issue<ELT>(tacc, smem_desc(sa + atom * C::A_ATOM_BYTES + off),
                            smem_desc(sb + atom * C::B_ATOM_BYTES + off), (k > 0 || kk > 0) ? 1u : 0u);
           }
-          mma_commit(smem_u32(&empty_bar[stage]));
+          mma_commit_mc(smem_u32(&empty_bar[stage]), CL_MASK);
           if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
@@ -387,10 +439,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int r_blk = row / BS, lr = row % BS;
     const int et = threadIdx.x - 64;   // 0..127
     int tl = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+    for (int t = cid; t < ntiles; t += ncl, ++tl) {
       const int ab = tl & 1;
       const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
-      const int I0 = args.tiles[2 * t] * TM, J0 = args.tiles[2 * t + 1] * C::TN;
+      const int I0 = (args.tiles[2 * t] * CL + (int)crank) * TM, J0 = args.tiles[2 * t + 1] * C::TN;
       const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
       __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
       if (!__all_sync(0xffffffffu, got)) break;
@@ -445,6 +497,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();  // no CTA leaves while its peer may still signal its barriers
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -481,11 +534,11 @@ __global__ void k_convert(const double* __restrict__ val, const int32_t* __restr
 }
 
 // flag[tile] = 1 for every tile holding a block of C's pattern
-__global__ void k_tile_flags(const int32_t* __restrict__ row, const int32_t* __restrict__ ci, int64_t nnz, int tn,
-                             int ntc, uint8_t* __restrict__ flag) {
+__global__ void k_tile_flags(const int32_t* __restrict__ row, const int32_t* __restrict__ ci, int64_t nnz, int tm,
+                             int tn, int ntc, uint8_t* __restrict__ flag) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= nnz) return;
-  flag[(size_t)(row[p] / TM) * ntc + ci[p] / tn] = 1;
+  flag[(size_t)(row[p] / tm) * ntc + ci[p] / tn] = 1;
 }
 
 // Tile compaction in grouped order: linear index li runs over groups of GROUP
@@ -644,14 +697,15 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
     k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
     IFAC_CK_LAUNCH();
   }
-  // tiles holding a block of C's pattern, compacted in grouped order
-  const int ntr = cdiv(nb, TM), ntc = cdiv(nb, Cf::TN);
+  // super-tiles (CL x TM block rows, TN block columns) holding a block of C's
+  // pattern, compacted in grouped order
+  const int ntr = cdiv(nb, CL * TM), ntc = cdiv(nb, Cf::TN);
   const int64_t ntot = (int64_t)ntr * ntc;
   const int nchunk = cdiv(ntot, CHUNK);
   Buf<uint8_t> flags(ctx, (size_t)ntot);
   Buf<int32_t> tiles(ctx, (size_t)2 * ntot), ccnt(ctx, nchunk), coff(ctx, nchunk + 1);
   IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntot, ctx->stream));
-  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, Cf::TN, ntc, flags.p);
+  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, CL * TM, Cf::TN, ntc, flags.p);
   IFAC_CK_LAUNCH();
   k_tile_count<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
   IFAC_CK_LAUNCH();
@@ -688,10 +742,22 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.alpha = alpha;
   args.err = ctx->dev_err;
   // the grid does not depend on the tile count (read on the device), so no
-  // host read-back is needed here; idle CTAs return at once
-  const int64_t grid = std::min<int64_t>(ntot, sms);
+  // host read-back is needed here; idle clusters return at once
+  const int64_t clusters = std::min<int64_t>(ntot, sms / CL);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr_cl[1];
+  attr_cl[0].id = cudaLaunchAttributeClusterDimension;
+  attr_cl[0].val.clusterDim.x = CL;
+  attr_cl[0].val.clusterDim.y = 1;
+  attr_cl[0].val.clusterDim.z = 1;
+  cfg.attrs = attr_cl;
+  cfg.numAttrs = 1;
   prof_begin(ctx, 1);
-  k_gemm_tc<ELT><<<(int)grid, NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mapA, mapB, args);
+  IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<ELT>, mapA, mapB, args));
   IFAC_CK_LAUNCH();
   prof_end(ctx);
   ++ctx->tc_launches;
