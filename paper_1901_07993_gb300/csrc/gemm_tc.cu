@@ -34,7 +34,9 @@ namespace tc {
 
 constexpr int BS = 64;
 constexpr int TM = 2;
-constexpr int CL = 2;  // CTAs per cluster: vertically adjacent tiles sharing one op(B) panel
+#ifndef IFAC_TC_CLUSTER_BF16
+#define IFAC_TC_CLUSTER_BF16 2
+#endif
 constexpr int NTHREADS = 192;
 constexpr long long WAIT_LIMIT = 1ll << 27;
 
@@ -45,6 +47,7 @@ struct Cfg {
   static constexpr int MMA_K = 32 / ELT;                // 32 bytes of K per tcgen05.mma
   static constexpr int KSTEPS = BS / MMA_K;             // MMAs per K block
   static constexpr int TN = (ELT == 2) ? 4 : 2;         // block columns per tile
+  static constexpr int CL = (ELT == 2) ? IFAC_TC_CLUSTER_BF16 : 2;  // CTAs per cluster sharing one op(B) panel
   static constexpr int N = TN * BS;
   static constexpr int M = TM * BS;
   static constexpr int A_ATOM_BYTES = M * 128;          // one K atom of the A tile
@@ -266,13 +269,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // op(A) blocks and half of the op(B) panel, multicast to both.
   const uint32_t crank = cluster_rank();
   const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
+  constexpr int CL = C::CL;
   constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), CL);  // released by the MMAs of every CTA of the cluster
+      mbar_init(smem_u32(&empty_bar[s]), C::CL);  // released by the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -699,6 +703,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   // super-tiles (CL x TM block rows, TN block columns) holding a block of C's
   // pattern, compacted in grouped order
+  constexpr int CL = Cf::CL;
   const int ntr = cdiv(nb, CL * TM), ntc = cdiv(nb, Cf::TN);
   const int64_t ntot = (int64_t)ntr * ntc;
   const int nchunk = cdiv(ntot, CHUNK);
@@ -743,9 +748,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.err = ctx->dev_err;
   // the grid does not depend on the tile count (read on the device), so no
   // host read-back is needed here; idle clusters return at once
-  const int64_t clusters = std::min<int64_t>(ntot, sms / CL);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
   cfg.stream = ctx->stream;
@@ -756,6 +759,16 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   attr_cl[0].val.clusterDim.z = 1;
   cfg.attrs = attr_cl;
   cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)(sms / CL * CL), 1, 1);
+  static int max_clusters = 0;  // clusters of CL CTAs that fit at once (GPC boundaries)
+  if (!max_clusters) {
+    if (cudaOccupancyMaxActiveClusters(&max_clusters, k_gemm_tc<ELT>, &cfg) != cudaSuccess || max_clusters < 1) {
+      cudaGetLastError();
+      max_clusters = sms / CL;
+    }
+  }
+  const int64_t clusters = std::min<int64_t>(ntot, max_clusters);
+  cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
   prof_begin(ctx, 1);
   IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<ELT>, mapA, mapB, args));
   IFAC_CK_LAUNCH();
