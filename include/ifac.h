@@ -58,6 +58,8 @@ extern "C" {
 #define IFAC_FP64 0 /* FP64 inputs, FP64 accumulation (FP64 pipe) */
 #define IFAC_TF32 1 /* inputs rounded to TF32, FP32 accumulation (tensor cores, bs = 64) */
 #define IFAC_BF16 2 /* inputs rounded to BF16, FP32 accumulation (tensor cores, bs = 64) */
+#define IFAC_FP64_SPLIT 3 /* FP64-accurate: error-free splitting into BF16 slices on the
+                             tensor cores (Ozaki et al. 2012), FP64 accumulation, bs = 64 */
 
 /* Stop reasons reported by the refinement drivers. */
 #define IFAC_STOP_RULE 1     /* ||delta_{i+1}||_F > ||delta_i||_F^(m+1) (Section 2.2) */
@@ -176,7 +178,14 @@ void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a);
  * rounded to that format (BF16 round-to-nearest-even from FP64; TF32 via FP32,
  * round-to-nearest-even, then round-half-away), products are accumulated in
  * FP32 on the tensor cores, and the result, its norms and the truncation are
- * FP64.  IFAC_ERR_TIMEOUT if a device pipeline wait expired. */
+ * FP64.  IFAC_FP64_SPLIT (bs = 64): an FP64-accurate product on the tensor
+ * cores: each scalar row of op(A) and column of op(B) is scaled by a power of
+ * two and split into 7 slices of 7-bit integers held exactly in BF16; slice
+ * products accumulate exactly in FP32 over windows of 16 K blocks and are
+ * added, scaled, into the FP64 result (pairs of slice orders s + t <= 8).
+ * Element error <= about 2^-45 K_ij max_k|op(A)_ik| max_k|op(B)_kj| plus FP64
+ * rounding of the partial sums.  IFAC_ERR_TIMEOUT if a device pipeline wait
+ * expired. */
 int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB,
                    double alpha, double tau, int prec, ifac_bsr* C);
 

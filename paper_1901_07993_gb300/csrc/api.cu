@@ -284,7 +284,8 @@ int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr*
     validate(B, "B");
     check_pair(A, B);
     if (!C) fail(IFAC_ERR_INVALID, "C is NULL");
-    if (prec != IFAC_FP64 && prec != IFAC_TF32 && prec != IFAC_BF16) fail(IFAC_ERR_INVALID, "unknown precision");
+    if (prec != IFAC_FP64 && prec != IFAC_TF32 && prec != IFAC_BF16 && prec != IFAC_FP64_SPLIT)
+      fail(IFAC_ERR_INVALID, "unknown precision");
     if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
     Mat R = ifac::gemm(ctx, *A, transA != 0, *B, transB != 0, alpha, tau, prec);
     check_device_error(ctx);

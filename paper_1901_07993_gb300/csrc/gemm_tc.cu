@@ -247,6 +247,13 @@ struct TileArgs {
   double* cnorm;
   double alpha;
   int* err;
+  // K-step window of every tile (indices in the tile's K enumeration)
+  int kbeg, kend;
+  // accumulate mode: C += wscale * rscale[row] * cscale[col] * acc (no norms)
+  int accumulate;
+  const double* rscale;
+  const double* cscale;
+  double wscale;
 };
 
 template <int ELT>
@@ -309,7 +316,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int t = cid; t < ntiles && ok; t += ncl) {
       const int S0 = args.tiles[2 * t] * (CL * TM);
       const int I0 = S0 + (int)crank * TM, J0 = args.tiles[2 * t + 1] * C::TN;
-      for (int wbase = 0; wbase < args.W && ok; wbase += 32) {
+      int e = 0;  // K-step index of this round's first record
+      for (int wbase = 0; wbase < args.W && ok && e < args.kend; wbase += 32) {
         const int w = wbase + lane;
         uint32_t word = 0;
         if (w < args.W) {
@@ -353,9 +361,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
           __syncwarp();
+          const int n = __popc(m);
           if (lane == 0) {
-            const int n = __popc(m);
             for (int j = 0; j < n && ok; ++j) {
+              if (e + j < args.kbeg || e + j >= args.kend) continue;  // outside this launch's K window
               if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
               const uint32_t fb = smem_u32(&full_bar[stage]);
               mbar_expect_tx(fb, C::TX_BYTES);
@@ -378,6 +387,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
           ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+          e += n;
           __syncwarp();
         }
       }
@@ -409,6 +419,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
           nk += __popc(word);
         }
+        nk = max(0, min(nk, args.kend) - args.kbeg);
+        if (nk == 0) continue;  // no K step of this tile in the window (the epilogue skips it too)
         const int ab = tl & 1;
         const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
         const uint32_t tacc = tmem + (uint32_t)(ab * C::N);
@@ -443,9 +455,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int r_blk = row / BS, lr = row % BS;
     const int et = threadIdx.x - 64;   // 0..127
     int tl = 0;
-    for (int t = cid; t < ntiles; t += ncl, ++tl) {
+    for (int t = cid; t < ntiles; t += ncl) {
+      {  // same K-window test as the MMA thread
+        const int S0 = args.tiles[2 * t] * (CL * TM);
+        int nk = 0;
+        for (int w = 0; w < args.W; ++w) {
+          uint32_t word = 0;
+#pragma unroll
+          for (int r = 0; r < CL * TM; ++r)
+            if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
+          nk += __popc(word);
+        }
+        if (max(0, min(nk, args.kend) - args.kbeg) == 0) continue;
+      }
       const int ab = tl & 1;
       const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
+      ++tl;
       const int I0 = (args.tiles[2 * t] * CL + (int)crank) * TM, J0 = args.tiles[2 * t + 1] * C::TN;
       const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
       __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
@@ -466,7 +491,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int h = 0; h < BS / 32; ++h) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
-          if (p >= 0) {
+          if (p >= 0 && args.accumulate) {
+            double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
+            const double rs = args.rscale[(size_t)I * BS + lr] * args.wscale;
+            const double* cs = args.cscale + (size_t)J * BS + h * 32;
+#pragma unroll
+            for (int e = 0; e < 32; e += 2) {
+              double2 w = *reinterpret_cast<double2*>(dst + e);
+              w.x += (double)v[e] * cs[e] * rs;
+              w.y += (double)v[e + 1] * cs[e + 1] * rs;
+              *reinterpret_cast<double2*>(dst + e) = w;
+            }
+          } else if (p >= 0) {
             double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
 #pragma unroll
             for (int e = 0; e < 32; e += 2) {
@@ -489,7 +525,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (et < TM * C::TN) {
         const int rb = et / C::TN, c = et % C::TN;
         const int Ib = I0 + rb, J = J0 + c;
-        if (Ib < args.nb && J < args.nb) {
+        if (!args.accumulate && Ib < args.nb && J < args.nb) {
           const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
           const int k = lower_bound_i32(args.cci, lo, hi, J);
           if (k < hi && args.cci[k] == J) args.cnorm[k] = sqrt(partial[2 * rb][c] + partial[2 * rb + 1][c]);
@@ -746,6 +782,12 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.cnorm = C.norms;
   args.alpha = alpha;
   args.err = ctx->dev_err;
+  args.kbeg = 0;
+  args.kend = 0x7fffffff;
+  args.accumulate = 0;
+  args.rscale = nullptr;
+  args.cscale = nullptr;
+  args.wscale = 1.0;
   // the grid does not depend on the tile count (read on the device), so no
   // host read-back is needed here; idle clusters return at once
   cudaLaunchConfig_t cfg = {};
@@ -776,6 +818,229 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   ++ctx->tc_launches;
 }
 
+// ---------------------------------------------------------------------------
+// FP64-accurate products on the tensor cores by error-free splitting
+// (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012): every row i of op(A) is scaled
+// by a power of two sigma_i >= its largest magnitude and split into NS slices
+// of 7-bit integers (exact in BF16), a = sigma_i sum_s q_s 2^(-7 s) + rest;
+// likewise the columns of op(B) with tau_j.  A product of two slices
+// accumulates integers below 2^24 as long as at most 16 K blocks (1024 terms
+// of magnitude <= 2^14) are summed, so FP32 accumulation is exact; the kernel
+// runs the K set of every tile in windows of 16 K steps and adds
+// 2^(-7(s+t)) sigma_i tau_j acc into the FP64 result for every slice pair with
+// s + t <= NS + 1.
+// ---------------------------------------------------------------------------
+constexpr int SPLIT_BITS = 7;
+constexpr int KWIN = 16;
+
+// sigma for every scalar row of a (possibly transposed) row view: the power
+// of two 2^e with max_k |x_rk| = m 2^e, m in [0.5, 1) (1 for an all-zero row)
+__global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb, int tr,
+                            const double* __restrict__ val, double* __restrict__ out) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)nb * BS) return;
+  const int I = (int)(w / BS), r = (int)(w % BS);
+  double m = 0.0;
+  for (int q = rp[I]; q < rp[I + 1]; ++q) {
+    const double* blk = val + (size_t)(src ? src[q] : q) * BS * BS;
+    for (int c = lane; c < BS; c += 32) m = fmax(m, fabs(tr ? blk[c * BS + r] : blk[r * BS + c]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    int e = 0;
+    frexp(m, &e);
+    out[w] = (m > 0.0) ? ldexp(1.0, e) : 1.0;
+  }
+}
+
+// NS BF16 slice copies (K-major, op() CSR order) of a view; row r of block qb
+// is scaled by scale[sblk[qb] * BS + r]
+__global__ void k_split(const double* __restrict__ val, const int32_t* __restrict__ src, int64_t nblk, int tr,
+                        const int32_t* __restrict__ sblk, const double* __restrict__ scale, int ns,
+                        __nv_bfloat16* __restrict__ dst) {
+  constexpr int BSZ = BS * BS;
+  const size_t slice_stride = (size_t)(nblk + 1) * BSZ;
+  for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
+    const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
+    const double* sc = scale + (size_t)sblk[qb] * BS;
+    for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
+      const int r = e / BS, c = e % BS;
+      double y = (tr ? s[c * BS + r] : s[e]) / sc[r];
+      for (int k = 0; k < ns; ++k) {
+        y *= (double)(1 << SPLIT_BITS);
+        const double qv = rint(y);
+        y -= qv;
+        dst[k * slice_stride + (size_t)qb * BSZ + e] = __float2bfloat16_rn((float)qv);
+      }
+    }
+  }
+}
+
+// per super-tile K-step count (union over its block rows), maximum into *out
+__global__ void k_max_ksteps(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles, int rows_per_tile,
+                             const uint32_t* __restrict__ bm, int nb, int W, int* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *ntiles) return;
+  const int S0 = tiles[2 * t] * rows_per_tile;
+  int nk = 0;
+  for (int w = 0; w < W; ++w) {
+    uint32_t word = 0;
+    for (int r = 0; r < rows_per_tile; ++r)
+      if (S0 + r < nb) word |= bm[(size_t)(S0 + r) * W + w];
+    nk += __popc(word);
+  }
+  atomicMax(out, nk);
+}
+
+static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
+                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
+                      unsigned long long* pairs) {
+  using Cf = Cfg<2>;
+  constexpr int CL = Cf::CL;
+  const int nb = A.nb;
+  const int64_t rows = (int64_t)nb * BS;
+  // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T)
+  Buf<double> sig(ctx, rows), tau(ctx, rows);
+  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sig.p);
+  IFAC_CK_LAUNCH();
+  {
+    View bt = view_rows(ctx, B, !tB);
+    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, tau.p);
+    IFAC_CK_LAUNCH();
+  }
+  // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
+  Buf<int32_t> arow(ctx, A.nnzb);
+  if (A.nnzb) expand_rows(ctx, arows.rp, nb, arow.p);
+  const size_t bbytes = (size_t)BS * BS * 2;
+  Buf<uint8_t> la(ctx, (size_t)ns * (A.nnzb + 1) * bbytes), lb(ctx, (size_t)ns * (B.nnzb + 1) * bbytes);
+  for (int k = 0; k < ns; ++k) {
+    IFAC_CK(cudaMemsetAsync(la.p + ((size_t)k * (A.nnzb + 1) + A.nnzb) * bbytes, 0, bbytes, ctx->stream));
+    IFAC_CK(cudaMemsetAsync(lb.p + ((size_t)k * (B.nnzb + 1) + B.nnzb) * bbytes, 0, bbytes, ctx->stream));
+  }
+  if (A.nnzb) {
+    k_split<<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
+        A.val, arows.src, A.nnzb, tA ? 1 : 0, arow.p, sig.p, ns, reinterpret_cast<__nv_bfloat16*>(la.p));
+    IFAC_CK_LAUNCH();
+  }
+  if (B.nnzb) {
+    k_split<<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
+        B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, tau.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
+    IFAC_CK_LAUNCH();
+  }
+  std::vector<CUtensorMap> mA(ns), mB(ns);
+  for (int k = 0; k < ns; ++k) {
+    mA[k] = make_map<2>(la.p + (size_t)k * (A.nnzb + 1) * bbytes, A.nnzb + 1);
+    mB[k] = make_map<2>(lb.p + (size_t)k * (B.nnzb + 1) * bbytes, B.nnzb + 1);
+  }
+  // K sets, block maps, tile list (as for the plain tensor-core product)
+  Buf<uint32_t> bmA = pattern_bitmap(ctx, A, tA);
+  const int64_t nb2 = (int64_t)nb * nb;
+  const bool dense_maps = nb2 <= (int64_t)4 << 20;
+  Buf<int32_t> imA, imB;
+  if (dense_maps) {
+    imA = Buf<int32_t>(ctx, nb2);
+    imB = Buf<int32_t>(ctx, nb2);
+    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imA.p, nb2, (int32_t)A.nnzb);
+    IFAC_CK_LAUNCH();
+    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imB.p, nb2, (int32_t)B.nnzb);
+    IFAC_CK_LAUNCH();
+    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, imA.p);
+    IFAC_CK_LAUNCH();
+    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
+    IFAC_CK_LAUNCH();
+  }
+  const int ntr = cdiv(nb, CL * TM), ntc = cdiv(nb, Cf::TN);
+  const int64_t ntot = (int64_t)ntr * ntc;
+  const int nchunk = cdiv(ntot, CHUNK);
+  Buf<uint8_t> flags(ctx, (size_t)ntot);
+  Buf<int32_t> tiles(ctx, (size_t)2 * ntot), ccnt(ctx, nchunk), coff(ctx, nchunk + 1);
+  Buf<int> kmax(ctx, 1);
+  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntot, ctx->stream));
+  IFAC_CK(cudaMemsetAsync(kmax.p, 0, sizeof(int), ctx->stream));
+  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, CL * TM, Cf::TN, ntc, flags.p);
+  IFAC_CK_LAUNCH();
+  k_tile_count<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
+  IFAC_CK_LAUNCH();
+  scan_counts(ctx, ccnt.p, coff.p, nchunk, false);
+  k_tile_write<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, coff.p, tiles.p);
+  IFAC_CK_LAUNCH();
+  k_max_ksteps<<<cdiv(ntot, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
+                                                         words_per_row(nb), kmax.p);
+  IFAC_CK_LAUNCH();
+  k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
+  IFAC_CK_LAUNCH();
+  int kmax_h = 0;
+  to_host(ctx, &kmax_h, kmax.p, sizeof(int));
+  IFAC_CK(cudaMemsetAsync(C.val, 0, sizeof(double) * (size_t)C.nnzb * BS * BS, ctx->stream));
+  static bool attr = false;
+  if (!attr) {
+    IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
+    attr = true;
+  }
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  TileArgs args;
+  args.tiles = tiles.p;
+  args.ntiles = coff.p + nchunk;
+  args.nb = nb;
+  args.W = words_per_row(nb);
+  args.bmA = bmA.p;
+  args.mapA = dense_maps ? imA.p : nullptr;
+  args.mapB = dense_maps ? imB.p : nullptr;
+  args.arp = arows.rp;
+  args.aci = arows.ci;
+  args.brp = brows.rp;
+  args.bci = brows.ci;
+  args.a_zero = (int)A.nnzb;
+  args.b_zero = (int)B.nnzb;
+  args.crp = C.row_ptr;
+  args.cci = C.col_idx;
+  args.cval = C.val;
+  args.cnorm = C.norms;
+  args.alpha = 1.0;
+  args.err = ctx->dev_err;
+  args.accumulate = 1;
+  args.rscale = sig.p;
+  args.cscale = tau.p;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr_cl[1];
+  attr_cl[0].id = cudaLaunchAttributeClusterDimension;
+  attr_cl[0].val.clusterDim.x = CL;
+  attr_cl[0].val.clusterDim.y = 1;
+  attr_cl[0].val.clusterDim.z = 1;
+  cfg.attrs = attr_cl;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)(sms / CL * CL), 1, 1);
+  int max_clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&max_clusters, k_gemm_tc<2>, &cfg) != cudaSuccess || max_clusters < 1) {
+    cudaGetLastError();
+    max_clusters = sms / CL;
+  }
+  cfg.gridDim = dim3((unsigned)(std::min<int64_t>(ntot, max_clusters) * CL), 1, 1);
+  const int nwin = std::max(1, cdiv(kmax_h, KWIN));
+  for (int win = 0; win < nwin; ++win) {
+    args.kbeg = win * KWIN;
+    args.kend = (win + 1) * KWIN;
+    for (int si = 1; si <= ns; ++si)
+      for (int ti = 1; si + ti <= ns + 1; ++ti) {
+        args.wscale = alpha * ldexp(1.0, -SPLIT_BITS * (si + ti));
+        prof_begin(ctx, 1);
+        IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA[si - 1], mB[ti - 1], args));
+        IFAC_CK_LAUNCH();
+        prof_end(ctx);
+        ++ctx->tc_launches;
+      }
+  }
+  block_norms(ctx, C, C.norms);
+}
+
 }  // namespace tc
 
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
@@ -785,6 +1050,7 @@ void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const 
   if (C.nnzb == 0) return;
   if (prec == IFAC_BF16) tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
   else if (prec == IFAC_TF32) tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
+  else if (prec == IFAC_FP64_SPLIT) tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
   else fail(IFAC_ERR_UNSUPPORTED, "unknown precision");
 }
 

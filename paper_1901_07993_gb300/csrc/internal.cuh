@@ -38,6 +38,7 @@ struct ifac_ctx {
   // device words: [0] error flag set by bounded waits that expired;
   // counters [1] FP64 and [2] tensor-core block pairs of the current call
   int* dev_err = nullptr;
+  int split_slices = 7;  // BF16 slices per operand for IFAC_FP64_SPLIT products
   unsigned long long* dev_pairs = nullptr;
 };
 

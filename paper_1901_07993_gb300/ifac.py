@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libifac.so")
 
 OK, WARN_TARGET_NOT_MET = 0, 1
-TF32, BF16 = 1, 2
+TF32, BF16, FP64_SPLIT = 1, 2, 3
 ERR_INVALID, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -7
 ERR_TOO_LARGE = -8
 FP64 = 0

@@ -1,0 +1,148 @@
+"""FP64-accurate block products on the tensor cores (error-free splitting into
+BF16 slices, Ozaki et al. 2012) through the C ABI, against the CPU oracle's
+FP64 product.
+
+Bound used element-wise: every scalar row i of op(A) is split relative to a
+power of two sigma_i < 2 max_k |a_ik|, every column j of op(B) relative to
+tau_j < 2 max_k |b_kj|; the dropped slice pairs and the split remainders cost
+at most 2^-46 sigma_i tau_j per product term, and each of the at most
+28 * ceil(K/16) FP64 additions into C rounds once.  So
+    |C - C_ref| <= K (2^-44 r_i c_j) + (28 ceil(K/16) + K) 2^-53 (|A||B|)_ij
+with r_i = max_k |a_ik|, c_j = max_k |b_kj|, K = scalar inner length."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_07993_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+FP64_SPLIT = 3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_1901_07993_gb300 import build as libbuild
+    from paper_1901_07993_gb300 import ifac
+    assert torch.cuda.is_available()
+    libbuild.build()
+    return ifac.Context()
+
+
+def dense(h):
+    nb, bs = h.nb, h.bs
+    D = np.zeros((nb * bs, nb * bs))
+    for I in range(nb):
+        for q in range(h.row_ptr[I], h.row_ptr[I + 1]):
+            J = h.col_idx[q]
+            D[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs] = h.val[q]
+    return D
+
+
+def _check(ctx, A, B, tA, tB, alpha=1.0):
+    from paper_1901_07993_gb300 import ifac
+    ref = oracle.gemm(A, B, tA, tB, alpha, 0.0)
+    got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), tA, ifac.upload(ctx, B), tB, alpha, 0.0,
+                              FP64_SPLIT).download()
+    assert np.array_equal(got.row_ptr, ref.row_ptr) and np.array_equal(got.col_idx, ref.col_idx)
+    Ad, Bd = dense(A), dense(B)
+    Ad = Ad.T if tA else Ad
+    Bd = Bd.T if tB else Bd
+    r = np.abs(Ad).max(axis=1)
+    c = np.abs(Bd).max(axis=0)
+    absab = np.abs(Ad) @ np.abs(Bd)
+    K = A.nb * A.bs
+    lim_d = abs(alpha) * (K * 2.0 ** -44 * np.outer(r, c) + (28 * -(-A.nb // 16) + K) * 2.0 ** -53 * absab)
+    bs = A.bs
+    worst = 0.0
+    for I in range(A.nb):
+        for q in range(ref.row_ptr[I], ref.row_ptr[I + 1]):
+            J = ref.col_idx[q]
+            lim = lim_d[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs]
+            err = np.abs(got.val[q] - ref.val[q])
+            assert np.all(err <= lim), (I, J, float(err.max()), float(lim.min()))
+            worst = max(worst, float((err / np.maximum(lim, 1e-300)).max()))
+    return worst, np.abs(got.val - ref.val).max() / max(np.abs(ref.val).max(), 1e-300)
+
+
+@pytest.mark.parametrize("tA,tB", list(itertools.product([False, True], repeat=2)))
+def test_split_random_blocks(ctx, tA, tB):
+    """Ragged n, empty rows, all four transpose cases, alpha not a power of two."""
+    nb = 9
+    A = synth.random_bsr(nb, 64, 0.4, seed=41, empty_rows=1, n=nb * 64 - 7)
+    B = synth.random_bsr(nb, 64, 0.4, seed=42, empty_rows=2, n=nb * 64 - 7)
+    _, rel = _check(ctx, A, B, tA, tB, alpha=-1.25)
+    assert rel < 1e-13  # FP64 class (TF32 and BF16 products give 1e-4 .. 1e-2)
+
+
+def test_split_truncation(ctx):
+    """Norm-based truncation after the split product keeps the oracle's blocks
+    (block magnitudes spread over 10^-8 .. 1, threshold in a gap between
+    product norms far above the product's absolute error)."""
+    from paper_1901_07993_gb300 import ifac
+    rng = np.random.default_rng(48)
+
+    def spread(h):
+        v = h.val * 10.0 ** -rng.uniform(0, 8, size=(h.nnzb, 1, 1))
+        return synth.HostBSR(h.n, h.bs, h.row_ptr, h.col_idx, v)
+
+    A = spread(synth.random_bsr(12, 64, 0.35, seed=49))
+    B = spread(synth.random_bsr(12, 64, 0.35, seed=50))
+    ref = oracle.gemm(A, B, False, False, 1.0, 0.0)
+    norms = np.sort(np.sqrt((ref.val ** 2).sum(axis=(1, 2))))
+    sel = norms[(norms > 1e-6 * norms[-1]) & (norms < 1e-1 * norms[-1])]
+    k = int(np.argmax(sel[1:] / sel[:-1]))
+    tau = np.sqrt(sel[k] * sel[k + 1])
+    assert sel[k + 1] > 1.01 * sel[k]
+    got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), False, ifac.upload(ctx, B), False, 1.0, tau,
+                              FP64_SPLIT).download()
+    keep = oracle.truncate(ref, tau)
+    assert 0 < keep.nnzb < ref.nnzb
+    assert np.array_equal(got.col_idx, keep.col_idx) and np.array_equal(got.row_ptr, keep.row_ptr)
+    assert np.abs(got.val - keep.val).max() <= 1e-13 * np.abs(keep.val).max()
+
+
+def test_split_many_k_windows(ctx):
+    """A dense 40 x 40 block product: 40 K steps per tile, three windows of 16."""
+    A = synth.random_bsr(40, 64, 1.0, seed=43)
+    B = synth.random_bsr(40, 64, 1.0, seed=44)
+    _, rel = _check(ctx, A, B, False, True)
+    assert rel < 1e-13  # FP64 class (TF32 and BF16 products give 1e-4 .. 1e-2)
+
+
+def test_split_wide_dynamic_range(ctx):
+    """Rows and columns scaled over 2^-300 .. 2^300: the per-row/column
+    power-of-two scales keep every slice product exact."""
+    rng = np.random.default_rng(45)
+    A = synth.random_bsr(6, 64, 0.6, seed=46)
+    B = synth.random_bsr(6, 64, 0.6, seed=47)
+    rs = np.ldexp(1.0, rng.integers(-300, 300, size=6 * 64))
+    cs = np.ldexp(1.0, rng.integers(-300, 300, size=6 * 64))
+    Av = A.val.copy()
+    for I in range(A.nb):
+        for q in range(A.row_ptr[I], A.row_ptr[I + 1]):
+            Av[q] *= rs[I * 64:(I + 1) * 64, None]
+    Bv = B.val.copy()
+    for I in range(B.nb):
+        for q in range(B.row_ptr[I], B.row_ptr[I + 1]):
+            J = B.col_idx[q]
+            Bv[q] *= cs[None, J * 64:(J + 1) * 64]
+    A = synth.HostBSR(A.n, 64, A.row_ptr, A.col_idx, Av)
+    B = synth.HostBSR(B.n, 64, B.row_ptr, B.col_idx, Bv)
+    _check(ctx, A, B, False, False)
+
+
+def test_split_overlap_delta(ctx):
+    """delta = I - Z^T S Z from a converged FP64 refinement: the products
+    carry the FP64 accuracy that the low-precision formats lose."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(1500, 64, seed=4)
+    Sd = ifac.upload(ctx, S)
+    Z, _ = ifac.inv_factor_refine(ctx, Sd, 1e-12, 1e-12, ifac.opts())
+    Zh = Z.download()
+    X = oracle.gemm(S, Zh, False, False, 1.0, 0.0)
+    _check(ctx, S, Zh, False, False)
+    worst, rel = _check(ctx, Zh, X, True, False)
+    assert rel < 1e-13  # FP64 class (TF32 and BF16 products give 1e-4 .. 1e-2)
