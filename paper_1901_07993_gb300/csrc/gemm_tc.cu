@@ -39,6 +39,10 @@ constexpr int TM = 2;
 #endif
 constexpr int NTHREADS = 192;
 constexpr long long WAIT_LIMIT = 1ll << 27;
+// split mode: K steps per exact FP32 window, table sizes
+constexpr int KW = 16;
+constexpr int MAX_UNITS = 16;
+constexpr int MAX_PAIRS = 32;
 
 template <int ELT>
 struct Cfg {
@@ -247,13 +251,18 @@ struct TileArgs {
   double* cnorm;
   double alpha;
   int* err;
-  // K-step window of every tile (indices in the tile's K enumeration)
-  int kbeg, kend;
-  // accumulate mode: C += wscale * rscale[row] * cscale[col] * acc (no norms)
-  int accumulate;
-  const double* rscale;
-  const double* cscale;
-  double wscale;
+  // split mode (FP64-accurate products): the copies of op(A) and op(B) hold
+  // NS BF16 slices each; pair p multiplies the slices starting at rows
+  // pair_ya[p] / pair_yb[p] of the tensor maps; the pairs of unit u,
+  // [unit_end[u-1], unit_end[u]), share one FP32 accumulator and its weight
+  // unit_w[u]; the epilogue adds (acc tau_j)(sigma_i w_u) into C (no norms)
+  int split;
+  int nunits;
+  int unit_end[MAX_UNITS];
+  int pair_ya[MAX_PAIRS], pair_yb[MAX_PAIRS];
+  double unit_w[MAX_UNITS];
+  const double* rscale;  // sigma, per scalar row of op(A)
+  const double* cscale;  // tau, per scalar column of op(B)
 };
 
 template <int ELT>
@@ -266,6 +275,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
   __shared__ double partial[4][C::TN];
+  __shared__ int s_unit_end[MAX_UNITS], s_pair_ya[MAX_PAIRS], s_pair_yb[MAX_PAIRS];
+  __shared__ double s_unit_w[MAX_UNITS];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -281,6 +292,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
+    for (int u = 0; u < MAX_UNITS; ++u) {
+      s_unit_end[u] = args.unit_end[u];
+      s_unit_w[u] = args.unit_w[u];
+    }
+    for (int p = 0; p < MAX_PAIRS; ++p) {
+      s_pair_ya[p] = args.pair_ya[p];
+      s_pair_yb[p] = args.pair_yb[p];
+    }
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), C::CL);  // released by the MMAs of every CTA of the cluster
@@ -303,21 +322,70 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
 
+  // number of K steps of tile t: size of the union of its super-tile rows' bitmaps
+  auto tile_nk = [&](int t) {
+    const int S0 = args.tiles[2 * t] * (CL * TM);
+    int nk = 0;
+    for (int w = 0; w < args.W; ++w) {
+      uint32_t word = 0;
+#pragma unroll
+      for (int r = 0; r < CL * TM; ++r)
+        if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
+      nk += __popc(word);
+    }
+    return nk;
+  };
+
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
     // The warp turns the K set of a tile (union of the bitmap rows of its op(A)
     // block rows) into K-step records 32 at a time, lane-parallel; lane 0 then
-    // issues the loads of each record into the next ring slot.
+    // issues the loads of each record into the next ring slot.  In split mode
+    // the records are gathered into windows of KW, and every window is loaded
+    // once per slice pair, unit by unit.
     __shared__ int rec[32][TM + Cfg<ELT>::TN];
+    __shared__ int wrec[KW + 32][TM + Cfg<ELT>::TN];
     int stage = 0;
     uint32_t phase = 0;
     uint32_t issued_mask = 0, last_parity = 0;  // lane 0: stages filled / parity of their last fill
     bool ok = true;
+    // lane 0: one ring slot with the blocks of record r, slices at rows ya / yb
+    auto issue = [&](const int* r, int ya, int yb) -> bool {
+      if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) return false;
+      const uint32_t fb = smem_u32(&full_bar[stage]);
+      mbar_expect_tx(fb, C::TX_BYTES);
+      issued_mask |= 1u << stage;
+      last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+      const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
+      const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int a = 0; a < C::ATOMS; ++a)
+          tma_load_2d(sa + a * C::A_ATOM_BYTES + i * BS * 128, &mapA, a * C::ATOM_ELEMS, ya + r[i] * BS, fb);
+#pragma unroll
+      for (int c = (int)crank * (C::TN / CL); c < ((int)crank + 1) * (C::TN / CL); ++c)
+#pragma unroll
+        for (int a = 0; a < C::ATOMS; ++a)
+          tma_load_2d_mc(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS, yb + r[TM + c] * BS,
+                         fb, CL_MASK);
+      if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+      return true;
+    };
+    // lane 0, split mode: the cnt records of the open window for every slice pair
+    auto issue_window = [&](int cnt) -> bool {
+      int p = 0;
+      for (int u = 0; u < args.nunits; ++u)
+        for (; p < s_unit_end[u]; ++p)
+          for (int j = 0; j < cnt; ++j)
+            if (!issue(wrec[j], s_pair_ya[p], s_pair_yb[p])) return false;
+      return true;
+    };
     for (int t = cid; t < ntiles && ok; t += ncl) {
       const int S0 = args.tiles[2 * t] * (CL * TM);
       const int I0 = S0 + (int)crank * TM, J0 = args.tiles[2 * t + 1] * C::TN;
-      int e = 0;  // K-step index of this round's first record
-      for (int wbase = 0; wbase < args.W && ok && e < args.kend; wbase += 32) {
+      int npend = 0;  // split mode: records in the open window (warp-uniform)
+      for (int wbase = 0; wbase < args.W && ok; wbase += 32) {
         const int w = wbase + lane;
         uint32_t word = 0;
         if (w < args.W) {
@@ -362,34 +430,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           __syncwarp();
           const int n = __popc(m);
-          if (lane == 0) {
-            for (int j = 0; j < n && ok; ++j) {
-              if (e + j < args.kbeg || e + j >= args.kend) continue;  // outside this launch's K window
-              if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
-              const uint32_t fb = smem_u32(&full_bar[stage]);
-              mbar_expect_tx(fb, C::TX_BYTES);
-              issued_mask |= 1u << stage;
-              last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
-              const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
-              const uint32_t sb = sa + C::A_BYTES;
+          if (!args.split) {
+            if (lane == 0)
+              for (int j = 0; j < n && ok; ++j) ok = issue(rec[j], 0, 0);
+          } else {
+            if (lane < n) {
 #pragma unroll
-              for (int r = 0; r < TM; ++r)
+              for (int i = 0; i < TM + C::TN; ++i) wrec[npend + lane][i] = rec[lane][i];
+            }
+            __syncwarp();
+            npend += n;  // < KW + 32
+            while (npend >= KW && ok) {
+              if (lane == 0) ok = issue_window(KW);
+              ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+              const int rest = npend - KW;  // < 32
+              int tmp[TM + C::TN];
+              if (lane < rest) {
 #pragma unroll
-                for (int a = 0; a < C::ATOMS; ++a)
-                  tma_load_2d(sa + a * C::A_ATOM_BYTES + r * BS * 128, &mapA, a * C::ATOM_ELEMS, rec[j][r] * BS, fb);
+                for (int i = 0; i < TM + C::TN; ++i) tmp[i] = wrec[KW + lane][i];
+              }
+              __syncwarp();
+              if (lane < rest) {
 #pragma unroll
-              for (int c = (int)crank * (C::TN / CL); c < ((int)crank + 1) * (C::TN / CL); ++c)
-#pragma unroll
-                for (int a = 0; a < C::ATOMS; ++a)
-                  tma_load_2d_mc(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS,
-                                 rec[j][TM + c] * BS, fb, CL_MASK);
-              if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+                for (int i = 0; i < TM + C::TN; ++i) wrec[lane][i] = tmp[i];
+              }
+              __syncwarp();
+              npend = rest;
             }
           }
           ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-          e += n;
           __syncwarp();
         }
+      }
+      if (args.split && npend > 0 && ok) {
+        if (lane == 0) ok = issue_window(npend);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       }
     }
     // before the CTA exits: the copies lane 0 issued (and the peer's multicast
@@ -406,28 +481,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      int tl = 0;  // this CTA's tile counter: accumulator buffer tl & 1, its phase (tl >> 1) & 1
+      int tl = 0;  // accumulator hand-overs so far: buffer tl & 1, its phase (tl >> 1) & 1
       bool ok = true;
-      for (int t = cid; t < ntiles && ok; t += ncl) {
-        const int S0 = args.tiles[2 * t] * (CL * TM);
-        // number of K steps: size of the union of the super-tile rows' bitmaps
-        int nk = 0;
-        for (int w = 0; w < args.W; ++w) {
-          uint32_t word = 0;
-#pragma unroll
-          for (int r = 0; r < CL * TM; ++r)
-            if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
-          nk += __popc(word);
-        }
-        nk = max(0, min(nk, args.kend) - args.kbeg);
-        if (nk == 0) continue;  // no K step of this tile in the window (the epilogue skips it too)
+      // nsteps ring slots contracted into one accumulator, then handed to the epilogue
+      auto run_acc = [&](int nsteps) -> bool {
         const int ab = tl & 1;
         const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
         const uint32_t tacc = tmem + (uint32_t)(ab * C::N);
-        if (!mbar_wait(smem_u32(&acc_empty[ab]), aphase ^ 1u, &abort_flag, args.err)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&acc_empty[ab]), aphase ^ 1u, &abort_flag, args.err)) return false;
         tc_fence_after();
-        for (int k = 0; k < nk; ++k) {
-          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, args.err)) { ok = false; break; }
+        for (int k = 0; k < nsteps; ++k) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, args.err)) return false;
           tc_fence_after();
           const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
           const uint32_t sb = sa + C::A_BYTES;
@@ -440,9 +504,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mma_commit_mc(smem_u32(&empty_bar[stage]), CL_MASK);
           if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
         }
-        if (!ok) break;
         mma_commit(smem_u32(&acc_full[ab]));
         ++tl;
+        return true;
+      };
+      for (int t = cid; t < ntiles && ok; t += ncl) {
+        const int nk = tile_nk(t);
+        if (nk == 0) continue;  // (a tile holds a block of C's pattern, so nk >= 1)
+        if (!args.split) {
+          ok = run_acc(nk);
+        } else {
+          for (int kb = 0; kb < nk && ok; kb += KW) {
+            const int cnt = min(KW, nk - kb);
+            int p = 0;
+            for (int u = 0; u < args.nunits && ok; ++u) {
+              ok = run_acc((s_unit_end[u] - p) * cnt);
+              p = s_unit_end[u];
+            }
+          }
+        }
       }
       // every MMA this thread issued completes before tensor memory is released
       mma_commit(smem_u32(&drain_bar));
@@ -455,84 +535,116 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int r_blk = row / BS, lr = row % BS;
     const int et = threadIdx.x - 64;   // 0..127
     int tl = 0;
-    for (int t = cid; t < ntiles; t += ncl) {
-      {  // same K-window test as the MMA thread
-        const int S0 = args.tiles[2 * t] * (CL * TM);
-        int nk = 0;
-        for (int w = 0; w < args.W; ++w) {
-          uint32_t word = 0;
-#pragma unroll
-          for (int r = 0; r < CL * TM; ++r)
-            if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
-          nk += __popc(word);
-        }
-        if (max(0, min(nk, args.kend) - args.kbeg) == 0) continue;
-      }
-      const int ab = tl & 1;
-      const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
-      ++tl;
+    bool good = true;
+    for (int t = cid; t < ntiles && good; t += ncl) {
+      const int nk = tile_nk(t);
+      if (nk == 0) continue;
       const int I0 = (args.tiles[2 * t] * CL + (int)crank) * TM, J0 = args.tiles[2 * t + 1] * C::TN;
-      const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
-      __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
-      if (!__all_sync(0xffffffffu, got)) break;
-      tc_fence_after();
-      const int I = I0 + r_blk;
-#pragma unroll 1
+      const int I = I0 + r_blk;  // warp-uniform: a warp's 32 rows lie in one block row
+      int pc[C::TN];             // position of C_{I, J0+c} in C, or -1
+#pragma unroll
       for (int c = 0; c < C::TN; ++c) {
         const int J = J0 + c;
-        int p = -1;
+        pc[c] = -1;
         if (I < args.nb && J < args.nb) {
           const int lo = args.crp[I], hi = args.crp[I + 1];
           const int k = lower_bound_i32(args.cci, lo, hi, J);
-          if (k < hi && args.cci[k] == J) p = k;
+          if (k < hi && args.cci[k] == J) pc[c] = k;
         }
-        double ss = 0.0;
+      }
+      if (!args.split) {
+        const int ab = tl & 1;
+        const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
+        ++tl;
+        const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
+        __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
+        if (!__all_sync(0xffffffffu, got)) break;
+        tc_fence_after();
+#pragma unroll 1
+        for (int c = 0; c < C::TN; ++c) {
+          const int p = pc[c];
+          double ss = 0.0;
 #pragma unroll
-        for (int h = 0; h < BS / 32; ++h) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
-          if (p >= 0 && args.accumulate) {
-            double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
-            const double rs = args.rscale[(size_t)I * BS + lr] * args.wscale;
-            const double* cs = args.cscale + (size_t)J * BS + h * 32;
+          for (int h = 0; h < BS / 32; ++h) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
+            if (p >= 0) {
+              double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
 #pragma unroll
-            for (int e = 0; e < 32; e += 2) {
-              double2 w = *reinterpret_cast<double2*>(dst + e);
-              w.x += (double)v[e] * cs[e] * rs;
-              w.y += (double)v[e + 1] * cs[e + 1] * rs;
-              *reinterpret_cast<double2*>(dst + e) = w;
-            }
-          } else if (p >= 0) {
-            double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
-#pragma unroll
-            for (int e = 0; e < 32; e += 2) {
-              double2 w;
-              w.x = (double)v[e] * args.alpha;
-              w.y = (double)v[e + 1] * args.alpha;
-              ss = fma(w.x, w.x, ss);
-              ss = fma(w.y, w.y, ss);
-              *reinterpret_cast<double2*>(dst + e) = w;
+              for (int e = 0; e < 32; e += 2) {
+                double2 w;
+                w.x = (double)v[e] * args.alpha;
+                w.y = (double)v[e + 1] * args.alpha;
+                ss = fma(w.x, w.x, ss);
+                ss = fma(w.y, w.y, ss);
+                *reinterpret_cast<double2*>(dst + e) = w;
+              }
             }
           }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0) partial[q][c] = ss;
-      }
-      tc_fence_before();
-      epi_bar();
-      // norms: block row rb is covered by lane quarters 2rb and 2rb+1, summed in that order
-      if (et < TM * C::TN) {
-        const int rb = et / C::TN, c = et % C::TN;
-        const int Ib = I0 + rb, J = J0 + c;
-        if (!args.accumulate && Ib < args.nb && J < args.nb) {
-          const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
-          const int k = lower_bound_i32(args.cci, lo, hi, J);
-          if (k < hi && args.cci[k] == J) args.cnorm[k] = sqrt(partial[2 * rb][c] + partial[2 * rb + 1][c]);
+          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          if (lane == 0) partial[q][c] = ss;
+        }
+        tc_fence_before();
+        epi_bar();
+        // norms: block row rb is covered by lane quarters 2rb and 2rb+1, summed in that order
+        if (et < TM * C::TN) {
+          const int rb = et / C::TN, c = et % C::TN;
+          const int Ib = I0 + rb, J = J0 + c;
+          if (Ib < args.nb && J < args.nb) {
+            const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
+            const int k = lower_bound_i32(args.cci, lo, hi, J);
+            if (k < hi && args.cci[k] == J) args.cnorm[k] = sqrt(partial[2 * rb][c] + partial[2 * rb + 1][c]);
+          }
+        }
+        epi_bar();
+        if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
+      } else {
+        // C += (acc * tau_j) * (sigma_i * w_u), one hand-over per window and unit
+        const double rsig = (I < args.nb) ? args.rscale[(size_t)I * BS + lr] : 0.0;
+        for (int kb = 0; kb < nk && good; kb += KW) {
+          for (int u = 0; u < args.nunits; ++u) {
+            const int ab = tl & 1;
+            const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
+            ++tl;
+            const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, got)) { good = false; break; }
+            tc_fence_after();
+            const double rs = rsig * s_unit_w[u];
+#pragma unroll 1
+            for (int c = 0; c < C::TN; ++c) {
+              const int p = pc[c];
+#pragma unroll
+              for (int h = 0; h < BS / 32; ++h) {
+                double2 dv[16], cv[16];
+                double* dst = args.cval + (size_t)(p < 0 ? 0 : p) * BS * BS + (size_t)lr * BS + h * 32;
+                if (p >= 0) {
+                  const double2* cs = reinterpret_cast<const double2*>(args.cscale + (size_t)(J0 + c) * BS + h * 32);
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) {
+                    dv[e] = reinterpret_cast<const double2*>(dst)[e];
+                    cv[e] = __ldg(cs + e);
+                  }
+                }
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
+                if (p >= 0) {
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) {
+                    dv[e].x = fma((double)v[2 * e] * cv[e].x, rs, dv[e].x);
+                    dv[e].y = fma((double)v[2 * e + 1] * cv[e].y, rs, dv[e].y);
+                    reinterpret_cast<double2*>(dst)[e] = dv[e];
+                  }
+                }
+              }
+            }
+            tc_fence_before();
+            epi_bar();
+            if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
+          }
         }
       }
-      epi_bar();
-      if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
     }
   }
   tc_fence_before();
@@ -782,12 +894,15 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.cnorm = C.norms;
   args.alpha = alpha;
   args.err = ctx->dev_err;
-  args.kbeg = 0;
-  args.kend = 0x7fffffff;
-  args.accumulate = 0;
+  args.split = 0;
+  args.nunits = 0;
+  for (int u = 0; u < MAX_UNITS; ++u) {
+    args.unit_end[u] = 0;
+    args.unit_w[u] = 0.0;
+  }
+  for (int p = 0; p < MAX_PAIRS; ++p) args.pair_ya[p] = args.pair_yb[p] = 0;
   args.rscale = nullptr;
   args.cscale = nullptr;
-  args.wscale = 1.0;
   // the grid does not depend on the tile count (read on the device), so no
   // host read-back is needed here; idle clusters return at once
   cudaLaunchConfig_t cfg = {};
@@ -826,14 +941,14 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
 // by a power of two sigma_i >= its largest magnitude and split into NS slices
 // of 7-bit integers (exact in BF16), a = sigma_i sum_s q_s 2^(-7 s) + rest;
 // likewise the columns of op(B) with tau_j.  A product of two slices
-// accumulates integers below 2^24 as long as at most 16 K blocks (1024 terms
-// of magnitude <= 2^14) are summed, so FP32 accumulation is exact; the kernel
-// runs the K set of every tile in windows of 16 K steps and adds
-// 2^(-7(s+t)) sigma_i tau_j acc into the FP64 result for every slice pair with
-// s + t <= NS + 1.
+// (first slices |q| <= 128, later ones |q| <= 64) is a sum of integers, exact
+// in FP32 while its magnitude bound stays <= 2^24.  Slice pairs with equal
+// weight 2^(-7(s+t)), s + t <= NS + 1, are packed greedily into units whose
+// bound over a window of KW = 16 K blocks (1024 terms) stays <= 2^24 (13 units
+// for NS = 7); per tile and window, each unit is one accumulator that the
+// epilogue adds, scaled, into the FP64 result.
 // ---------------------------------------------------------------------------
 constexpr int SPLIT_BITS = 7;
-constexpr int KWIN = 16;
 
 // sigma for every scalar row of a (possibly transposed) row view: the power
 // of two 2^e with max_k |x_rk| = m 2^e, m in [0.5, 1) (1 for an all-zero row)
@@ -880,22 +995,6 @@ __global__ void k_split(const double* __restrict__ val, const int32_t* __restric
   }
 }
 
-// per super-tile K-step count (union over its block rows), maximum into *out
-__global__ void k_max_ksteps(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles, int rows_per_tile,
-                             const uint32_t* __restrict__ bm, int nb, int W, int* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= *ntiles) return;
-  const int S0 = tiles[2 * t] * rows_per_tile;
-  int nk = 0;
-  for (int w = 0; w < W; ++w) {
-    uint32_t word = 0;
-    for (int r = 0; r < rows_per_tile; ++r)
-      if (S0 + r < nb) word |= bm[(size_t)(S0 + r) * W + w];
-    nk += __popc(word);
-  }
-  atomicMax(out, nk);
-}
-
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
                       unsigned long long* pairs) {
@@ -931,11 +1030,11 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
         B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, tau.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
     IFAC_CK_LAUNCH();
   }
-  std::vector<CUtensorMap> mA(ns), mB(ns);
-  for (int k = 0; k < ns; ++k) {
-    mA[k] = make_map<2>(la.p + (size_t)k * (A.nnzb + 1) * bbytes, A.nnzb + 1);
-    mB[k] = make_map<2>(lb.p + (size_t)k * (B.nnzb + 1) * bbytes, B.nnzb + 1);
-  }
+  // one tensor map over all slices of each operand (slice s at row s (nnzb + 1) BS)
+  if ((int64_t)ns * (std::max(A.nnzb, B.nnzb) + 1) * BS > (int64_t)0x7fffffff)
+    fail(IFAC_ERR_TOO_LARGE, "split product: slice copies exceed the 2^31-row tensor-map range");
+  const CUtensorMap mA = make_map<2>(la.p, (int64_t)ns * (A.nnzb + 1));
+  const CUtensorMap mB = make_map<2>(lb.p, (int64_t)ns * (B.nnzb + 1));
   // K sets, block maps, tile list (as for the plain tensor-core product)
   Buf<uint32_t> bmA = pattern_bitmap(ctx, A, tA);
   const int64_t nb2 = (int64_t)nb * nb;
@@ -958,9 +1057,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const int nchunk = cdiv(ntot, CHUNK);
   Buf<uint8_t> flags(ctx, (size_t)ntot);
   Buf<int32_t> tiles(ctx, (size_t)2 * ntot), ccnt(ctx, nchunk), coff(ctx, nchunk + 1);
-  Buf<int> kmax(ctx, 1);
   IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntot, ctx->stream));
-  IFAC_CK(cudaMemsetAsync(kmax.p, 0, sizeof(int), ctx->stream));
   k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, CL * TM, Cf::TN, ntc, flags.p);
   IFAC_CK_LAUNCH();
   k_tile_count<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
@@ -968,13 +1065,8 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   scan_counts(ctx, ccnt.p, coff.p, nchunk, false);
   k_tile_write<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, coff.p, tiles.p);
   IFAC_CK_LAUNCH();
-  k_max_ksteps<<<cdiv(ntot, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
-                                                         words_per_row(nb), kmax.p);
-  IFAC_CK_LAUNCH();
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
-  int kmax_h = 0;
-  to_host(ctx, &kmax_h, kmax.p, sizeof(int));
   IFAC_CK(cudaMemsetAsync(C.val, 0, sizeof(double) * (size_t)C.nnzb * BS * BS, ctx->stream));
   static bool attr = false;
   if (!attr) {
@@ -1003,9 +1095,42 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.cnorm = C.norms;
   args.alpha = 1.0;
   args.err = ctx->dev_err;
-  args.accumulate = 1;
+  args.split = 1;
   args.rscale = sig.p;
   args.cscale = tau.p;
+  {
+    // units: slice pairs of equal weight packed while sum over the unit of
+    // max|q_s| max|q_t| * 64 * KW stays <= 2^24
+    const auto qmax = [](int s) { return s == 1 ? 128 : 64; };
+    const int64_t cap = ((int64_t)1 << 24) / (64 * KW);
+    int nu = 0, np = 0;
+    for (int g = 2; g <= ns + 1; ++g) {
+      int64_t used = 0;
+      bool open = false;
+      for (int si = 1; si < g; ++si) {
+        const int ti = g - si;
+        if (si > ns || ti > ns) continue;
+        const int64_t cost = (int64_t)qmax(si) * qmax(ti);
+        if (open && used + cost > cap) {
+          args.unit_end[nu++] = np;
+          used = 0;
+          open = false;
+        }
+        if (!open) {
+          if (nu >= MAX_UNITS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many accumulation units");
+          args.unit_w[nu] = alpha * ldexp(1.0, -SPLIT_BITS * g);
+          open = true;
+        }
+        if (np >= MAX_PAIRS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many slice pairs");
+        args.pair_ya[np] = (si - 1) * (int)(A.nnzb + 1) * BS;
+        args.pair_yb[np] = (ti - 1) * (int)(B.nnzb + 1) * BS;
+        ++np;
+        used += cost;
+      }
+      if (open) args.unit_end[nu++] = np;
+    }
+    args.nunits = nu;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
@@ -1024,20 +1149,11 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     max_clusters = sms / CL;
   }
   cfg.gridDim = dim3((unsigned)(std::min<int64_t>(ntot, max_clusters) * CL), 1, 1);
-  const int nwin = std::max(1, cdiv(kmax_h, KWIN));
-  for (int win = 0; win < nwin; ++win) {
-    args.kbeg = win * KWIN;
-    args.kend = (win + 1) * KWIN;
-    for (int si = 1; si <= ns; ++si)
-      for (int ti = 1; si + ti <= ns + 1; ++ti) {
-        args.wscale = alpha * ldexp(1.0, -SPLIT_BITS * (si + ti));
-        prof_begin(ctx, 1);
-        IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA[si - 1], mB[ti - 1], args));
-        IFAC_CK_LAUNCH();
-        prof_end(ctx);
-        ++ctx->tc_launches;
-      }
-  }
+  prof_begin(ctx, 1);
+  IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA, mB, args));
+  IFAC_CK_LAUNCH();
+  prof_end(ctx);
+  ++ctx->tc_launches;
   block_norms(ctx, C, C.norms);
 }
 

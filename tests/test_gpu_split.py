@@ -146,3 +146,20 @@ def test_split_overlap_delta(ctx):
     _check(ctx, S, Zh, False, False)
     worst, rel = _check(ctx, Zh, X, True, False)
     assert rel < 1e-13  # FP64 class (TF32 and BF16 products give 1e-4 .. 1e-2)
+
+
+@pytest.mark.parametrize("nb", [16, 17])
+def test_split_exact_at_fp32_bound(ctx, nb):
+    """All entries 1 - 2^-9: the leading slices are 128 and -32, so the first
+    unit's accumulator reaches exactly 2^24 over a full window of 16 K blocks
+    (1024 terms); the product K (1 - 2^-9)^2 is representable and must come
+    out exact (nb = 17 adds a one-block second window)."""
+    from paper_1901_07993_gb300 import ifac
+    n = nb * 64
+    v = 1.0 - 2.0 ** -9
+    rp = np.arange(0, nb * nb + 1, nb, dtype=np.int32)
+    ci = np.tile(np.arange(nb, dtype=np.int32), nb)
+    A = synth.HostBSR(n, 64, rp, ci, np.full((nb * nb, 64, 64), v))
+    got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), False, ifac.upload(ctx, A), True, 1.0, 0.0,
+                              FP64_SPLIT).download()
+    assert np.all(got.val == n * v * v)
