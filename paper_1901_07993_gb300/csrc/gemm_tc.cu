@@ -217,6 +217,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// FP32 -> FP64 by moving the fields (exact; zero, subnormals, inf and NaN
+// take the conversion instruction), keeping the epilogue off the FP64 pipe
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// x 2^sh as a 64-bit integer, rounded half up when sh < 0 (|x| <= 2^24)
+__device__ __forceinline__ long long fixed_term(int x, int sh) {
+  if (sh >= 0) return (long long)x << sh;
+  if (sh < -30) return 0;
+  return (long long)((x + (1 << (-sh - 1))) >> (-sh));
+}
+
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, int lo, int hi, int v) {
@@ -255,14 +273,13 @@ struct TileArgs {
   // NS BF16 slices each; pair p multiplies the slices starting at rows
   // pair_ya[p] / pair_yb[p] of the tensor maps; the pairs of unit u,
   // [unit_end[u-1], unit_end[u]), share one FP32 accumulator and its weight
-  // unit_w[u]; the epilogue adds (acc tau_j)(sigma_i w_u) into C (no norms)
+  // weight 2^sh_u in the 64-bit fixed-point sums that the epilogue keeps in
+  // C's value array (no norms; converted after the kernel)
   int split;
   int nunits;
   int unit_end[MAX_UNITS];
   int pair_ya[MAX_PAIRS], pair_yb[MAX_PAIRS];
-  double unit_w[MAX_UNITS];
-  const double* rscale;  // sigma, per scalar row of op(A)
-  const double* cscale;  // tau, per scalar column of op(B)
+  int unit_sh[MAX_UNITS];
 };
 
 template <int ELT>
@@ -276,7 +293,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ volatile int abort_flag;
   __shared__ double partial[4][C::TN];
   __shared__ int s_unit_end[MAX_UNITS], s_pair_ya[MAX_PAIRS], s_pair_yb[MAX_PAIRS];
-  __shared__ double s_unit_w[MAX_UNITS];
+  __shared__ int s_unit_sh[MAX_UNITS];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     abort_flag = 0;
     for (int u = 0; u < MAX_UNITS; ++u) {
       s_unit_end[u] = args.unit_end[u];
-      s_unit_w[u] = args.unit_w[u];
+      s_unit_sh[u] = args.unit_sh[u];
     }
     for (int p = 0; p < MAX_PAIRS; ++p) {
       s_pair_ya[p] = args.pair_ya[p];
@@ -534,6 +551,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int row = q * 32 + lane;     // accumulator row 0..127
     const int r_blk = row / BS, lr = row % BS;
     const int et = threadIdx.x - 64;   // 0..127
+    const float alpha_f = (float)args.alpha;
     int tl = 0;
     bool good = true;
     for (int t = cid; t < ntiles && good; t += ncl) {
@@ -563,7 +581,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll 1
         for (int c = 0; c < C::TN; ++c) {
           const int p = pc[c];
-          double ss = 0.0;
+          float ssf = 0.0f;  // this thread's 64 squares (FP32: the values carry FP32 accumulation anyway)
 #pragma unroll
           for (int h = 0; h < BS / 32; ++h) {
             float v[32];
@@ -572,15 +590,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
 #pragma unroll
               for (int e = 0; e < 32; e += 2) {
+                const float a = v[e] * alpha_f, b = v[e + 1] * alpha_f;
+                ssf = fmaf(a, a, ssf);
+                ssf = fmaf(b, b, ssf);
                 double2 w;
-                w.x = (double)v[e] * args.alpha;
-                w.y = (double)v[e + 1] * args.alpha;
-                ss = fma(w.x, w.x, ss);
-                ss = fma(w.y, w.y, ss);
+                w.x = f32_to_f64(a);
+                w.y = f32_to_f64(b);
                 *reinterpret_cast<double2*>(dst + e) = w;
               }
             }
           }
+          double ss = (double)ssf;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
           if (lane == 0) partial[q][c] = ss;
@@ -600,8 +620,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         epi_bar();
         if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
       } else {
-        // C += (acc * tau_j) * (sigma_i * w_u), one hand-over per window and unit
-        const double rsig = (I < args.nb) ? args.rscale[(size_t)I * BS + lr] : 0.0;
+        // C_int += acc 2^sh_u, one hand-over per window and unit; C is held as
+        // 64-bit fixed point (scale 2^-f relative to sigma_i tau_j) until the
+        // conversion after the kernel
         for (int kb = 0; kb < nk && good; kb += KW) {
           for (int u = 0; u < args.nunits; ++u) {
             const int ab = tl & 1;
@@ -611,30 +632,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             __syncwarp();
             if (!__all_sync(0xffffffffu, got)) { good = false; break; }
             tc_fence_after();
-            const double rs = rsig * s_unit_w[u];
+            const int sh = s_unit_sh[u];
 #pragma unroll 1
             for (int c = 0; c < C::TN; ++c) {
               const int p = pc[c];
 #pragma unroll
               for (int h = 0; h < BS / 32; ++h) {
-                double2 dv[16], cv[16];
-                double* dst = args.cval + (size_t)(p < 0 ? 0 : p) * BS * BS + (size_t)lr * BS + h * 32;
+                longlong2 dv[16];
+                longlong2* dst = reinterpret_cast<longlong2*>(args.cval + (size_t)(p < 0 ? 0 : p) * BS * BS +
+                                                              (size_t)lr * BS + h * 32);
                 if (p >= 0) {
-                  const double2* cs = reinterpret_cast<const double2*>(args.cscale + (size_t)(J0 + c) * BS + h * 32);
 #pragma unroll
-                  for (int e = 0; e < 16; ++e) {
-                    dv[e] = reinterpret_cast<const double2*>(dst)[e];
-                    cv[e] = __ldg(cs + e);
-                  }
+                  for (int e = 0; e < 16; ++e) dv[e] = dst[e];
                 }
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
                 if (p >= 0) {
 #pragma unroll
                   for (int e = 0; e < 16; ++e) {
-                    dv[e].x = fma((double)v[2 * e] * cv[e].x, rs, dv[e].x);
-                    dv[e].y = fma((double)v[2 * e + 1] * cv[e].y, rs, dv[e].y);
-                    reinterpret_cast<double2*>(dst)[e] = dv[e];
+                    dv[e].x += fixed_term(__float2int_rn(v[2 * e]), sh);
+                    dv[e].y += fixed_term(__float2int_rn(v[2 * e + 1]), sh);
+                    dst[e] = dv[e];
                   }
                 }
               }
@@ -896,13 +914,8 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.err = ctx->dev_err;
   args.split = 0;
   args.nunits = 0;
-  for (int u = 0; u < MAX_UNITS; ++u) {
-    args.unit_end[u] = 0;
-    args.unit_w[u] = 0.0;
-  }
+  for (int u = 0; u < MAX_UNITS; ++u) args.unit_end[u] = args.unit_sh[u] = 0;
   for (int p = 0; p < MAX_PAIRS; ++p) args.pair_ya[p] = args.pair_yb[p] = 0;
-  args.rscale = nullptr;
-  args.cscale = nullptr;
   // the grid does not depend on the tile count (read on the device), so no
   // host read-back is needed here; idle clusters return at once
   cudaLaunchConfig_t cfg = {};
@@ -950,48 +963,105 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
 // ---------------------------------------------------------------------------
 constexpr int SPLIT_BITS = 7;
 
-// sigma for every scalar row of a (possibly transposed) row view: the power
-// of two 2^e with max_k |x_rk| = m 2^e, m in [0.5, 1) (1 for an all-zero row)
+// GB300's FP64 pipe is narrow, so the splitting below works on the bit
+// patterns of the FP64 inputs with integer arithmetic only.
+
+// exponent e of sigma = 2^e for every scalar row of a (possibly transposed)
+// row view: max_k |x_rk| = m 2^e with m in [0.5, 1) (e = 0 for an all-zero row)
 __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb, int tr,
-                            const double* __restrict__ val, double* __restrict__ out) {
+                            const double* __restrict__ val, int* __restrict__ eout, double* __restrict__ sout) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)nb * BS) return;
   const int I = (int)(w / BS), r = (int)(w % BS);
-  double m = 0.0;
+  unsigned long long m = 0;  // |x| bit patterns order like the magnitudes
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
     const double* blk = val + (size_t)(src ? src[q] : q) * BS * BS;
-    for (int c = lane; c < BS; c += 32) m = fmax(m, fabs(tr ? blk[c * BS + r] : blk[r * BS + c]));
+    for (int c = lane; c < BS; c += 32) {
+      const unsigned long long u =
+          (unsigned long long)__double_as_longlong(tr ? blk[c * BS + r] : blk[r * BS + c]) & 0x7fffffffffffffffull;
+      m = u > m ? u : m;
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+    m = u > m ? u : m;
+  }
   if (lane == 0) {
+    const int ea = (int)(m >> 52);
     int e = 0;
-    frexp(m, &e);
-    out[w] = (m > 0.0) ? ldexp(1.0, e) : 1.0;
+    if (ea > 0) e = ea - 1022;                       // [2^(ea-1023), 2^(ea-1022))
+    else if (m != 0) e = (64 - __clzll((long long)m)) - 1074;  // subnormal: [2^(L-1075), 2^(L-1074))
+    eout[w] = e;
+    sout[w] = (m != 0) ? ldexp(1.0, e) : 1.0;
   }
 }
 
 // NS BF16 slice copies (K-major, op() CSR order) of a view; row r of block qb
-// is scaled by scale[sblk[qb] * BS + r]
+// has scale exponent sexp[sblk[qb] * BS + r].  With Y = x 2^(55 - e) held as a
+// 64-bit integer (|Y| < 2^55; bits below 2^-55 of sigma dropped by rounding),
+// digit k is q_k = round(Y_k / 2^(55 - 7k)), Y_{k+1} = Y_k - q_k 2^(55 - 7k).
 __global__ void k_split(const double* __restrict__ val, const int32_t* __restrict__ src, int64_t nblk, int tr,
-                        const int32_t* __restrict__ sblk, const double* __restrict__ scale, int ns,
+                        const int32_t* __restrict__ sblk, const int* __restrict__ sexp, int ns,
                         __nv_bfloat16* __restrict__ dst) {
   constexpr int BSZ = BS * BS;
   const size_t slice_stride = (size_t)(nblk + 1) * BSZ;
   for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
     const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
-    const double* sc = scale + (size_t)sblk[qb] * BS;
+    const int* se = sexp + (size_t)sblk[qb] * BS;
     for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
       const int r = e / BS, c = e % BS;
-      double y = (tr ? s[c * BS + r] : s[e]) / sc[r];
-      for (int k = 0; k < ns; ++k) {
-        y *= (double)(1 << SPLIT_BITS);
-        const double qv = rint(y);
-        y -= qv;
-        dst[k * slice_stride + (size_t)qb * BSZ + e] = __float2bfloat16_rn((float)qv);
+      const unsigned long long u = (unsigned long long)__double_as_longlong(tr ? s[c * BS + r] : s[e]);
+      const int ea = (int)((u >> 52) & 0x7ff);
+      unsigned long long mant = u & 0xfffffffffffffull;
+      int eb = ea;
+      if (ea) mant |= 1ull << 52;
+      else eb = 1;
+      // |x| = mant 2^(eb - 1075);  |Y| = mant 2^(eb - 1020 - e)
+      const int sh = eb - 1020 - se[r];
+      unsigned long long Y = 0;
+      if (sh >= 0) Y = mant << sh;  // sh <= 2 since |x| < sigma
+      else if (sh > -63) Y = (mant + (1ull << (-sh - 1))) >> (-sh);
+      long long y = (u >> 63) ? -(long long)Y : (long long)Y;
+      for (int k = 1; k <= ns; ++k) {
+        const int d = 55 - SPLIT_BITS * k;
+        const long long q = (y + (1ll << (d - 1))) >> d;
+        y -= q << d;
+        dst[(size_t)(k - 1) * slice_stride + (size_t)qb * BSZ + e] = __float2bfloat16_rn((float)(int)q);
       }
     }
+  }
+}
+
+// C_IJ = (S_int * scale) sigma_i tau_j from the fixed-point sums the split
+// kernel accumulated in place, then the FP64 block norms
+__global__ void k_split_finish(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t nnzb,
+                               double* __restrict__ cval, const double* __restrict__ sig,
+                               const double* __restrict__ tau, double scale, double* __restrict__ cnorm) {
+  __shared__ double red[32];
+  constexpr int BSZ = BS * BS;
+  for (int64_t p = blockIdx.x; p < nnzb; p += gridDim.x) {
+    const int I = crow[p], J = cci[p];
+    double* c = cval + (size_t)p * BSZ;
+    double ss = 0.0;
+    for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
+      const long long x = __double_as_longlong(c[e]);
+      const double v = (double)x * scale * sig[(size_t)I * BS + e / BS] * tau[(size_t)J * BS + e % BS];
+      c[e] = v;
+      ss = fma(v, v, ss);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[wid] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      cnorm[p] = sqrt(t);
+    }
+    __syncthreads();
   }
 }
 
@@ -1002,13 +1072,17 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   constexpr int CL = Cf::CL;
   const int nb = A.nb;
   const int64_t rows = (int64_t)nb * BS;
+  if (ns < 1 || ns > 7) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 7 slices");
   // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T)
   Buf<double> sig(ctx, rows), tau(ctx, rows);
-  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sig.p);
+  Buf<int> sige(ctx, rows), taue(ctx, rows);
+  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sige.p,
+                                                             sig.p);
   IFAC_CK_LAUNCH();
   {
     View bt = view_rows(ctx, B, !tB);
-    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, tau.p);
+    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, taue.p,
+                                                               tau.p);
     IFAC_CK_LAUNCH();
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
@@ -1022,12 +1096,12 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   }
   if (A.nnzb) {
     k_split<<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
-        A.val, arows.src, A.nnzb, tA ? 1 : 0, arow.p, sig.p, ns, reinterpret_cast<__nv_bfloat16*>(la.p));
+        A.val, arows.src, A.nnzb, tA ? 1 : 0, arow.p, sige.p, ns, reinterpret_cast<__nv_bfloat16*>(la.p));
     IFAC_CK_LAUNCH();
   }
   if (B.nnzb) {
     k_split<<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
-        B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, tau.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
+        B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, taue.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
     IFAC_CK_LAUNCH();
   }
   // one tensor map over all slices of each operand (slice s at row s (nnzb + 1) BS)
@@ -1096,8 +1170,10 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.alpha = 1.0;
   args.err = ctx->dev_err;
   args.split = 1;
-  args.rscale = sig.p;
-  args.cscale = tau.p;
+  // fixed point: |sum| <= K 2^f < 2^62 for the scalar inner length K <= nb BS
+  int lgK = 0;
+  while (((int64_t)1 << lgK) < (int64_t)nb * BS) ++lgK;
+  const int fbits = std::min(56, 62 - lgK);
   {
     // units: slice pairs of equal weight packed while sum over the unit of
     // max|q_s| max|q_t| * 64 * KW stays <= 2^24
@@ -1118,7 +1194,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
         }
         if (!open) {
           if (nu >= MAX_UNITS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many accumulation units");
-          args.unit_w[nu] = alpha * ldexp(1.0, -SPLIT_BITS * g);
+          args.unit_sh[nu] = fbits - SPLIT_BITS * g;
           open = true;
         }
         if (np >= MAX_PAIRS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many slice pairs");
@@ -1154,7 +1230,9 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   IFAC_CK_LAUNCH();
   prof_end(ctx);
   ++ctx->tc_launches;
-  block_norms(ctx, C, C.norms);
+  k_split_finish<<<(int)std::min<int64_t>(C.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
+      crow, C.col_idx, C.nnzb, C.val, sig.p, tau.p, alpha * ldexp(1.0, -fbits), C.norms);
+  IFAC_CK_LAUNCH();
 }
 
 }  // namespace tc
