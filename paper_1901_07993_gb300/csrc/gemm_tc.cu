@@ -14,14 +14,16 @@
 // the tile (op(A)_IK or op(B)_KJ not stored) is read from the zero block, so
 // every K step is one dense M x N x 64 contraction.
 //
-// Roles (192 threads, one CTA per SM):
+// Roles (320 threads, one CTA per SM):
 //   warp 0      : TMA producer -- one 64-row box per block and 128-byte
 //                 atom, 128-byte swizzle, into a STAGES-deep ring;
 //   warp 1      : tensor-memory allocation and the single MMA-issuing
 //                 thread (tcgen05.mma, accumulate in TMEM, tcgen05.commit
 //                 releases ring slots and hands the accumulator over);
-//   warps 2..5  : epilogue -- tcgen05.ld of the accumulator, alpha, FP64
-//                 Frobenius norm per output block, FP64 store into C.
+//   warps 2..9  : epilogue, two warps per tensor-memory lane quarter, each
+//                 on half of the tile's column blocks -- tcgen05.ld of the
+//                 accumulator, alpha, Frobenius norm per output block, FP64
+//                 store into C.
 // Every mbarrier wait is bounded; on expiry the CTA records an error flag,
 // drains its own copies and MMAs, releases tensor memory and returns.
 #include <cuda.h>
@@ -37,7 +39,8 @@ constexpr int TM = 2;
 #ifndef IFAC_TC_CLUSTER_BF16
 #define IFAC_TC_CLUSTER_BF16 2
 #endif
-constexpr int NTHREADS = 192;
+constexpr int NEPI = 8;                    // epilogue warps: two per tensor-memory lane quarter
+constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr long long WAIT_LIMIT = 1ll << 27;
 // split mode: K steps per exact FP32 window, table sizes
 constexpr int KW = 16;
@@ -235,7 +238,7 @@ __device__ __forceinline__ long long fixed_term(int x, int sh) {
   return (long long)((x + (1 << (-sh - 1))) >> (-sh));
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory"); }
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, int lo, int hi, int v) {
   while (lo < hi) {
@@ -267,6 +270,10 @@ struct TileArgs {
   const int32_t* cci;
   double* cval;
   double* cnorm;
+  // split mode: fixed-point sums, per C block 2048 longlong2 in hand-over
+  // order ((row half, column half, pair e) x 32 lanes), so that a warp's
+  // read-modify-write of one register pair covers 512 contiguous bytes
+  longlong2* cpart;
   double alpha;
   int* err;
   // split mode (FP64-accurate products): the copies of op(A) and op(B) hold
@@ -548,9 +555,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     // ------------------------------ epilogue ------------------------------
     const int q = warp & 3;            // tensor-memory lane quarter of this warp
+    const int c0 = ((warp - 2) >> 2) * (C::TN / 2), c1 = c0 + C::TN / 2;  // this warp's column blocks
     const int row = q * 32 + lane;     // accumulator row 0..127
     const int r_blk = row / BS, lr = row % BS;
-    const int et = threadIdx.x - 64;   // 0..127
+    const int et = threadIdx.x - 64;   // 0 .. 32 NEPI - 1
     const float alpha_f = (float)args.alpha;
     int tl = 0;
     bool good = true;
@@ -579,7 +587,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!__all_sync(0xffffffffu, got)) break;
         tc_fence_after();
 #pragma unroll 1
-        for (int c = 0; c < C::TN; ++c) {
+        for (int c = c0; c < c1; ++c) {
           const int p = pc[c];
           float ssf = 0.0f;  // this thread's 64 squares (FP32: the values carry FP32 accumulation anyway)
 #pragma unroll
@@ -634,16 +642,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_after();
             const int sh = s_unit_sh[u];
 #pragma unroll 1
-            for (int c = 0; c < C::TN; ++c) {
+            for (int c = c0; c < c1; ++c) {
               const int p = pc[c];
 #pragma unroll
               for (int h = 0; h < BS / 32; ++h) {
                 longlong2 dv[16];
-                longlong2* dst = reinterpret_cast<longlong2*>(args.cval + (size_t)(p < 0 ? 0 : p) * BS * BS +
-                                                              (size_t)lr * BS + h * 32);
+                longlong2* dst = args.cpart + (size_t)(p < 0 ? 0 : p) * (BS * BS / 2) +
+                                 (size_t)(((q & 1) * 2 + h) * 16) * 32 + lane;
                 if (p >= 0) {
 #pragma unroll
-                  for (int e = 0; e < 16; ++e) dv[e] = dst[e];
+                  for (int e = 0; e < 16; ++e) dv[e] = dst[e * 32];
                 }
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
@@ -652,7 +660,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   for (int e = 0; e < 16; ++e) {
                     dv[e].x += fixed_term(__float2int_rn(v[2 * e]), sh);
                     dv[e].y += fixed_term(__float2int_rn(v[2 * e + 1]), sh);
-                    dst[e] = dv[e];
+                    dst[e * 32] = dv[e];
                   }
                 }
               }
@@ -913,6 +921,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.alpha = alpha;
   args.err = ctx->dev_err;
   args.split = 0;
+  args.cpart = nullptr;
   args.nunits = 0;
   for (int u = 0; u < MAX_UNITS; ++u) args.unit_end[u] = args.unit_sh[u] = 0;
   for (int p = 0; p < MAX_PAIRS; ++p) args.pair_ya[p] = args.pair_yb[p] = 0;
@@ -969,7 +978,7 @@ constexpr int SPLIT_BITS = 7;
 // exponent e of sigma = 2^e for every scalar row of a (possibly transposed)
 // row view: max_k |x_rk| = m 2^e with m in [0.5, 1) (e = 0 for an all-zero row)
 __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb, int tr,
-                            const double* __restrict__ val, int* __restrict__ eout, double* __restrict__ sout) {
+                            const double* __restrict__ val, int* __restrict__ eout) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)nb * BS) return;
@@ -994,7 +1003,6 @@ __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __res
     if (ea > 0) e = ea - 1022;                       // [2^(ea-1023), 2^(ea-1022))
     else if (m != 0) e = (64 - __clzll((long long)m)) - 1074;  // subnormal: [2^(L-1075), 2^(L-1074))
     eout[w] = e;
-    sout[w] = (m != 0) ? ldexp(1.0, e) : 1.0;
   }
 }
 
@@ -1034,21 +1042,71 @@ __global__ void k_split(const double* __restrict__ val, const int32_t* __restric
   }
 }
 
-// C_IJ = (S_int * scale) sigma_i tau_j from the fixed-point sums the split
-// kernel accumulated in place, then the FP64 block norms
-__global__ void k_split_finish(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t nnzb,
-                               double* __restrict__ cval, const double* __restrict__ sig,
-                               const double* __restrict__ tau, double scale, double* __restrict__ cnorm) {
-  __shared__ double red[32];
-  constexpr int BSZ = BS * BS;
+// x 2^E rounded to nearest (ties to even), built from the integer's bits;
+// results outside the normal range take the FP64 pipe
+__device__ __forceinline__ double i64_ldexp(long long x, int E) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = x < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long ux = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  int len = 64 - __clzll((long long)ux);
+  unsigned long long mant;
+  if (len > 53) {
+    const int sh = len - 53;
+    mant = ux >> sh;
+    const unsigned long long rem = ux & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      if (++mant == (1ull << 53)) {
+        mant >>= 1;
+        ++len;
+      }
+    }
+  } else {
+    mant = ux << (53 - len);
+  }
+  const int field = len - 1 + E + 1023;  // value = mant 2^(len - 53 + E), mant in [2^52, 2^53)
+  if (field < 1 || field > 2046) return (double)x * ldexp(1.0, E);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)field << 52) | (mant & 0xfffffffffffffull)));
+}
+
+// C_IJ = S_int 2^(e_i + e_j + ea) * am from the fixed-point sums of the
+// split kernel (alpha = am 2^ea; am = +-1 when alpha is a signed power of
+// two): coalesced reads in hand-over order, a transpose through shared
+// memory, row-major FP64 writes, then the FP64 block norms
+__global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict__ crow,
+                                                      const int32_t* __restrict__ cci, int64_t nnzb,
+                                                      const longlong2* __restrict__ part, double* __restrict__ cval,
+                                                      const int* __restrict__ sige, const int* __restrict__ taue,
+                                                      int ea, double am, double* __restrict__ cnorm) {
+  __shared__ double tile[BS][BS + 1];
+  __shared__ double red[8];
+  const bool unit = (am == 1.0 || am == -1.0);
   for (int64_t p = blockIdx.x; p < nnzb; p += gridDim.x) {
     const int I = crow[p], J = cci[p];
-    double* c = cval + (size_t)p * BSZ;
+    const longlong2* src = part + (size_t)p * (BS * BS / 2);
+    for (int i = threadIdx.x; i < BS * BS / 2; i += blockDim.x) {
+      const int lane = i & 31, e = (i >> 5) & 15, h = (i >> 9) & 1, qq = i >> 10;
+      const int r = qq * 32 + lane, col = h * 32 + 2 * e;
+      longlong2 x = src[i];
+      if (unit && am < 0.0) {
+        x.x = -x.x;
+        x.y = -x.y;
+      }
+      const int er = ea + sige[(size_t)I * BS + r];
+      double v0 = i64_ldexp(x.x, er + taue[(size_t)J * BS + col]);
+      double v1 = i64_ldexp(x.y, er + taue[(size_t)J * BS + col + 1]);
+      if (!unit) {
+        v0 *= am;
+        v1 *= am;
+      }
+      tile[r][col] = v0;
+      tile[r][col + 1] = v1;
+    }
+    __syncthreads();
+    double* c = cval + (size_t)p * BS * BS;
     double ss = 0.0;
-    for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
-      const long long x = __double_as_longlong(c[e]);
-      const double v = (double)x * scale * sig[(size_t)I * BS + e / BS] * tau[(size_t)J * BS + e % BS];
-      c[e] = v;
+    for (int k = threadIdx.x; k < BS * BS; k += blockDim.x) {
+      const double v = tile[k / BS][k % BS];
+      c[k] = v;
       ss = fma(v, v, ss);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1058,10 +1116,9 @@ __global__ void k_split_finish(const int32_t* __restrict__ crow, const int32_t* 
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      for (int w = 0; w < 8; ++w) t += red[w];
       cnorm[p] = sqrt(t);
     }
-    __syncthreads();
   }
 }
 
@@ -1074,15 +1131,12 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const int64_t rows = (int64_t)nb * BS;
   if (ns < 1 || ns > 7) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 7 slices");
   // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T)
-  Buf<double> sig(ctx, rows), tau(ctx, rows);
   Buf<int> sige(ctx, rows), taue(ctx, rows);
-  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sige.p,
-                                                             sig.p);
+  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sige.p);
   IFAC_CK_LAUNCH();
   {
     View bt = view_rows(ctx, B, !tB);
-    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, taue.p,
-                                                               tau.p);
+    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, taue.p);
     IFAC_CK_LAUNCH();
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
@@ -1141,7 +1195,8 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   IFAC_CK_LAUNCH();
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
-  IFAC_CK(cudaMemsetAsync(C.val, 0, sizeof(double) * (size_t)C.nnzb * BS * BS, ctx->stream));
+  Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
+  IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
   static bool attr = false;
   if (!attr) {
     IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
@@ -1170,6 +1225,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.alpha = 1.0;
   args.err = ctx->dev_err;
   args.split = 1;
+  args.cpart = part.p;
   // fixed point: |sum| <= K 2^f < 2^62 for the scalar inner length K <= nb BS
   int lgK = 0;
   while (((int64_t)1 << lgK) < (int64_t)nb * BS) ++lgK;
@@ -1230,8 +1286,12 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   IFAC_CK_LAUNCH();
   prof_end(ctx);
   ++ctx->tc_launches;
-  k_split_finish<<<(int)std::min<int64_t>(C.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
-      crow, C.col_idx, C.nnzb, C.val, sig.p, tau.p, alpha * ldexp(1.0, -fbits), C.norms);
+  {
+    int ea = 0;
+    const double am = std::frexp(alpha, &ea) * 2.0;  // alpha = am 2^(ea - 1), am in [1, 2)
+    k_split_finish<<<(int)std::min<int64_t>(C.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
+        crow, C.col_idx, C.nnzb, part.p, C.val, sige.p, taue.p, ea - 1 - fbits, am, C.norms);
+  }
   IFAC_CK_LAUNCH();
 }
 
