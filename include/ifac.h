@@ -92,7 +92,7 @@ typedef struct ifac_ctx ifac_ctx;
 
 /* Options of the factorization drivers.  ifac_opts_default fills:
  * m = 2, max_iter = 50, fixed_iters = 0, c_rule = 0, leaf_size = 512,
- * prec = IFAC_FP64, profile = 0. */
+ * prec = IFAC_FP64, profile = 0, delta_prec = IFAC_FP64_SPLIT. */
 typedef struct {
   int m;           /* refinement order: Z_{i+1} = Z_i sum_{k=0}^{m} b_k delta_i^k,
                       b_0 = 1, b_k = (2k-1)/(2k) b_{k-1} (Eq. 2.1); 1..8 */
@@ -104,10 +104,18 @@ typedef struct {
                       0 -> c = 1/sqrt(beta), 1 -> c = sqrt(2/beta) */
   int leaf_size;   /* inv_factor_localized: sub-problems with more rows are
                       split at the block-aligned midpoint (Algorithm 2) */
-  int prec;        /* IFAC_FP64; inv_factor_refine also takes IFAC_TF32 or
-                      IFAC_BF16: the mixed-precision schedule below */
+  int prec;        /* IFAC_FP64; or IFAC_FP64_SPLIT (bs = 64): the FP64
+                      schedule with every block product on the split
+                      tensor-core kernel; inv_factor_refine and the batched
+                      call also take IFAC_TF32 or IFAC_BF16: the
+                      mixed-precision schedule below */
   int profile;     /* != 0: time every numeric block-product launch with CUDA
                       events on the context's stream (fills gemm_ms) */
+  int delta_prec;  /* products of the FP64-accurate delta evaluations that
+                      follow low-precision sweeps (inv_factor_refine with
+                      prec TF32/BF16: the FP64 phase; batched: the final
+                      residual): IFAC_FP64 (FP64 pipe) or IFAC_FP64_SPLIT
+                      (tensor cores; used when bs = 64, else IFAC_FP64) */
 } ifac_opts;
 
 typedef struct {

@@ -178,6 +178,7 @@ void ifac_opts_default(ifac_opts* o) {
   o->leaf_size = 512;
   o->prec = IFAC_FP64;
   o->profile = 0;
+  o->delta_prec = IFAC_FP64_SPLIT;
 }
 
 int ifac_create(ifac_ctx** out, void* stream, const ifac_allocator* alloc) {
@@ -356,8 +357,32 @@ static void check_opts(const ifac_opts* o, bool mixed_ok) {
   if (!o) fail(IFAC_ERR_INVALID, "opts is NULL");
   if (o->m < 1 || o->m > 8) fail(IFAC_ERR_INVALID, "m must be in 1..8");
   if (o->max_iter < 0 || o->fixed_iters < 0) fail(IFAC_ERR_INVALID, "negative iteration count");
-  if (o->prec != IFAC_FP64 && !(mixed_ok && (o->prec == IFAC_TF32 || o->prec == IFAC_BF16)))
+  if (o->prec != IFAC_FP64 && o->prec != IFAC_FP64_SPLIT &&
+      !(mixed_ok && (o->prec == IFAC_TF32 || o->prec == IFAC_BF16)))
     fail(IFAC_ERR_UNSUPPORTED, "precision not available for this call");
+  if (o->delta_prec != IFAC_FP64 && o->delta_prec != IFAC_FP64_SPLIT)
+    fail(IFAC_ERR_INVALID, "delta_prec must be IFAC_FP64 or IFAC_FP64_SPLIT");
+}
+
+// opts->prec == IFAC_FP64_SPLIT: the driver runs its FP64 schedule while
+// gemm() routes every FP64 product through the split tensor-core kernel
+struct SplitScope {
+  ifac_ctx* c;
+  int old;
+  SplitScope(ifac_ctx* c_, bool on) : c(c_), old(c_->fp64_prec) {
+    if (on) c->fp64_prec = IFAC_FP64_SPLIT;
+  }
+  ~SplitScope() { c->fp64_prec = old; }
+};
+
+static ifac_opts split_opts(const ifac_opts* in, int bs, bool* split) {
+  ifac_opts o = *in;
+  *split = o.prec == IFAC_FP64_SPLIT;
+  if (*split) {
+    if (bs != 64) fail(IFAC_ERR_UNSUPPORTED, "split tensor-core products need bs = 64");
+    o.prec = IFAC_FP64;
+  }
+  return o;
 }
 
 int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target, const ifac_opts* opts,
@@ -368,8 +393,11 @@ int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double targe
     check_opts(opts, true);
     if (!Z) fail(IFAC_ERR_INVALID, "Z is NULL");
     if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
-    if (opts->prec != IFAC_FP64) return refine_irsi_mixed(ctx, *S, tau, target, *opts, Z, rep);
-    return refine_irsi(ctx, *S, tau, target, *opts, Z, rep);
+    bool split = false;
+    const ifac_opts o = split_opts(opts, S->bs, &split);
+    SplitScope scope(ctx, split);
+    if (o.prec != IFAC_FP64) return refine_irsi_mixed(ctx, *S, tau, target, o, Z, rep);
+    return refine_irsi(ctx, *S, tau, target, o, Z, rep);
   });
 }
 
@@ -382,7 +410,10 @@ int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double ta
     if (!Z) fail(IFAC_ERR_INVALID, "Z is NULL");
     if (opts->leaf_size < 1) fail(IFAC_ERR_INVALID, "leaf_size must be >= 1");
     if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
-    return lif(ctx, *S, tau, target, *opts, Z, rep);
+    bool split = false;
+    const ifac_opts o = split_opts(opts, S->bs, &split);
+    SplitScope scope(ctx, split);
+    return lif(ctx, *S, tau, target, o, Z, rep);
   });
 }
 
@@ -399,7 +430,10 @@ int inv_factor_refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S
     }
     if (opts->prec != IFAC_FP64 && S[0]->bs != 64) fail(IFAC_ERR_UNSUPPORTED, "tensor-core products need bs = 64");
     if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
-    return refine_batched(ctx, count, S, tau, target, *opts, Z, rep);
+    bool split = false;
+    const ifac_opts o = split_opts(opts, S[0]->bs, &split);
+    SplitScope scope(ctx, split);
+    return refine_batched(ctx, count, S, tau, target, o, Z, rep);
   });
 }
 

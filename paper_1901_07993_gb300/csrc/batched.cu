@@ -206,8 +206,9 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   // FP64 residual of every member
   std::vector<double> resid(count, 0.0);
   {
-    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, 0.0, IFAC_FP64);
-    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, 0.0, IFAC_FP64);
+    const int rprec = delta_prec_of(o, bs);
+    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, 0.0, rprec);
+    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, 0.0, rprec);
     X.reset();
     Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     node_fro(ctx, D.m, dnb0.p, dnb1.p, count, ne.p);

@@ -50,6 +50,12 @@ static void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
   if (r) *r = ifac_report{};
 }
 
+// precision of FP64-accurate delta products: the split tensor-core product
+// where the options ask for it and it is built (bs = 64), else the FP64 pipe
+int delta_prec_of(const ifac_opts& o, int bs) {
+  return (o.delta_prec == IFAC_FP64_SPLIT && bs == 64) ? IFAC_FP64_SPLIT : IFAC_FP64;
+}
+
 static void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   check_device_error(ctx);
   read_device_counters(ctx, &ctx->pairs_fp64, &ctx->pairs_tc);
@@ -143,7 +149,7 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
   double e_prev = INFINITY, e = 0.0;
   int stop = 0, sweeps = 0, fp64_evals = 0, low_sweeps = 0;
   for (int it = 0;; ++it) {
-    const int dprec = fp64_phase ? IFAC_FP64 : low;
+    const int dprec = fp64_phase ? delta_prec_of(o, S.m.bs) : low;
     Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec);   // S Z
     Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec);    // Z^T (S Z)
     X.reset();

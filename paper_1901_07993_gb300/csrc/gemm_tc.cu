@@ -1122,6 +1122,22 @@ __global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict_
   }
 }
 
+// largest K-step count over the tiles (union of a super-tile's bitmap rows)
+__global__ void k_max_ksteps(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles, int rows_per_tile,
+                             const uint32_t* __restrict__ bm, int nb, int W, int* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *ntiles) return;
+  const int S0 = tiles[2 * t] * rows_per_tile;
+  int nk = 0;
+  for (int w = 0; w < W; ++w) {
+    uint32_t word = 0;
+    for (int r = 0; r < rows_per_tile; ++r)
+      if (S0 + r < nb) word |= bm[(size_t)(S0 + r) * W + w];
+    nk += __popc(word);
+  }
+  atomicMax(out, nk);
+}
+
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
                       unsigned long long* pairs) {
@@ -1195,6 +1211,15 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   IFAC_CK_LAUNCH();
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
+  int kmax = 0;
+  {
+    Buf<int> dk(ctx, 1);
+    IFAC_CK(cudaMemsetAsync(dk.p, 0, sizeof(int), ctx->stream));
+    k_max_ksteps<<<cdiv(ntot, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
+                                                           words_per_row(nb), dk.p);
+    IFAC_CK_LAUNCH();
+    to_host(ctx, &kmax, dk.p, sizeof(int));
+  }
   Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
   IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
   static bool attr = false;
@@ -1226,9 +1251,10 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.err = ctx->dev_err;
   args.split = 1;
   args.cpart = part.p;
-  // fixed point: |sum| <= K 2^f < 2^62 for the scalar inner length K <= nb BS
+  // fixed point: |sum| <= K 2^f <= 2^62 for the scalar inner length K of the
+  // longest tile; f = 56 keeps every unit's weight 2^(f - 7g) integral
   int lgK = 0;
-  while (((int64_t)1 << lgK) < (int64_t)nb * BS) ++lgK;
+  while (((int64_t)1 << lgK) < (int64_t)std::max(kmax, 1) * BS) ++lgK;
   const int fbits = std::min(56, 62 - lgK);
   {
     // units: slice pairs of equal weight packed while sum over the unit of

@@ -39,6 +39,7 @@ struct ifac_ctx {
   // counters [1] FP64 and [2] tensor-core block pairs of the current call
   int* dev_err = nullptr;
   int split_slices = 7;  // BF16 slices per operand for IFAC_FP64_SPLIT products
+  int fp64_prec = IFAC_FP64;  // IFAC_FP64_SPLIT: gemm() runs FP64 products of bs = 64 on the split kernel
   unsigned long long* dev_pairs = nullptr;
 };
 
@@ -156,6 +157,7 @@ void row_sq_norms(ifac_ctx* ctx, const ifac_bsr& A, double* rowsq);
 double fro_host(ifac_ctx* ctx, const ifac_bsr& A);
 double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
 // sum_j |A_ij| for every scalar row i (nb * bs values)
+int delta_prec_of(const ifac_opts& o, int bs);
 void gershgorin_rows(ifac_ctx* ctx, const ifac_bsr& A, double* rs);
 Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 

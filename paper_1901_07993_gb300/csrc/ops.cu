@@ -11,6 +11,7 @@ namespace ifac {
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
          int prec) {
   const int nb = A.nb;
+  if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && A.bs == 64) prec = IFAC_FP64_SPLIT;
   View arows = view_rows(ctx, A, tA);
   Pattern P = product_pattern(ctx, arows, B, tB, nb);
   Mat C(ctx);
