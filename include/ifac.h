@@ -140,6 +140,9 @@ typedef struct {
   double tc_ms;        /* their summed device time (opts.profile != 0) */
   int64_t tc_pairs;    /* stored block pairs multiplied by them */
   double resid_fro;    /* batched: ||I - Z^T S Z||_F with FP64 products (else 0) */
+  int64_t split_launches; /* FP64-accurate split tensor-core block-product launches */
+  double split_ms;     /* their summed device time (opts.profile != 0) */
+  int64_t split_pairs; /* stored block pairs multiplied by them */
 } ifac_report;
 
 /* ---------------------------------------------------------------- */
@@ -184,7 +187,8 @@ void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a);
  * op(A)_IK and op(B)_KJ stored.  A and B: same n and bs.  prec: IFAC_FP64 (any
  * bs in {16, 32, 64}), or IFAC_TF32 / IFAC_BF16 (bs = 64): the operands are
  * rounded to that format (BF16 round-to-nearest-even from FP64; TF32 via FP32,
- * round-to-nearest-even, then round-half-away), products are accumulated in
+ * round-to-nearest-even, then round-half-away; magnitudes below 2^-126 become
+ * zero), products are accumulated in
  * FP32 on the tensor cores, and the result, its norms and the truncation are
  * FP64.  IFAC_FP64_SPLIT (bs = 64): an FP64-accurate product on the tensor
  * cores: each scalar row of op(A) and column of op(B) is scaled by a power of

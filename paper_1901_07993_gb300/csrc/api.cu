@@ -103,30 +103,35 @@ void prof_end(ifac_ctx* ctx) {
   if (ctx->profile) IFAC_CK(cudaEventRecord(next_event(ctx), ctx->stream));
 }
 
-void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc) {
+void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc, double* ms_split) {
   *ms_fp64 = 0.0;
   *ms_tc = 0.0;
+  if (ms_split) *ms_split = 0.0;
   if (ctx->events_used) {
     IFAC_CK(cudaStreamSynchronize(ctx->stream));
     for (size_t i = 0; i + 1 < ctx->events_used; i += 2) {
       float t = 0.f;
       IFAC_CK(cudaEventElapsedTime(&t, ctx->events[i], ctx->events[i + 1]));
-      if (ctx->event_kind[i / 2]) *ms_tc += t;
-      else *ms_fp64 += t;
+      const int k = ctx->event_kind[i / 2];
+      if (k == 0) *ms_fp64 += t;
+      else if (k == 1 || !ms_split) *ms_tc += t;
+      else *ms_split += t;
     }
   }
   ctx->events_used = 0;
 }
 
 void reset_device_counters(ifac_ctx* ctx) {
-  IFAC_CK(cudaMemsetAsync(ctx->dev_pairs, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  IFAC_CK(cudaMemsetAsync(ctx->dev_pairs, 0, 3 * sizeof(unsigned long long), ctx->stream));
 }
 
-void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc) {
-  unsigned long long h[2] = {0, 0};
+void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc, int64_t* pairs_split) {
+  unsigned long long h[3] = {0, 0, 0};
   to_host(ctx, h, ctx->dev_pairs, sizeof(h));
   *pairs_fp64 = (int64_t)h[0];
   *pairs_tc = (int64_t)h[1];
+  if (pairs_split) *pairs_split = (int64_t)h[2];
+  else *pairs_tc += (int64_t)h[2];
 }
 
 void check_device_error(ifac_ctx* ctx) {

@@ -90,6 +90,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   ctx->launches = 0;
   ctx->gemm_launches = 0;
   ctx->tc_launches = 0;
+  ctx->split_launches = 0;
   ctx->events_used = 0;
   ctx->profile = o.profile != 0;
   reset_device_counters(ctx);
@@ -216,9 +217,11 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   }
   check_device_error(ctx);
   int64_t pf = 0, pt = 0;
-  read_device_counters(ctx, &pf, &pt);
+  int64_t ps = 0;
+  read_device_counters(ctx, &pf, &pt, &ps);
   double ms_fp64 = 0.0, ms_tc = 0.0;
-  prof_collect(ctx, &ms_fp64, &ms_tc);
+  double ms_split = 0.0;
+  prof_collect(ctx, &ms_fp64, &ms_tc, &ms_split);
   ctx->profile = false;
   // split Z into the members
   std::vector<int32_t> zrp(nb + 1);
@@ -252,15 +255,18 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       r.resid_fro = resid[k];
       // batch-wide counters are reported on every member
       r.products = ctx->products;
-      r.block_pairs = pf + pt;
+      r.block_pairs = pf + pt + ps;
       r.fp64_pairs = pf;
       r.tc_pairs = pt;
-      r.flops = 2.0 * (double)bs * bs * bs * (double)(pf + pt);
+      r.split_pairs = ps;
+      r.flops = 2.0 * (double)bs * bs * bs * (double)(pf + pt + ps);
       r.launches = ctx->launches;
       r.gemm_launches = ctx->gemm_launches;
       r.tc_launches = ctx->tc_launches;
       r.gemm_ms = ms_fp64;
       r.tc_ms = ms_tc;
+      r.split_launches = ctx->split_launches;
+      r.split_ms = ms_split;
     }
     outs.push_back(std::move(Zk));
   }

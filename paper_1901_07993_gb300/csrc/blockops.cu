@@ -6,6 +6,8 @@
 // order, so each element is rounded exactly as the plain definition is.
 // Reductions run in a fixed order (per row, then over rows), so results are
 // deterministic from run to run.
+#include <cmath>
+
 #include "internal.cuh"
 
 namespace ifac {
@@ -32,52 +34,118 @@ __device__ __forceinline__ double block_reduce_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-// one CTA per output block (grid-stride)
+// alpha x, rounded to nearest.  GB300's FP64 pipe is narrow, so the common
+// scales avoid it: alpha = +-1 is a sign change and alpha = 2^k an exponent
+// change on the bit pattern (same result), other alphas one multiply.
+struct Scale {
+  int mode;  // 0 multiply, 1 identity, 2 negate, 3 power of two
+  int k;     // mode 3: alpha = 2^k
+  double alpha;
+};
+
+static Scale make_scale(double alpha) {
+  Scale s{0, 0, alpha};
+  if (alpha == 1.0) s.mode = 1;
+  else if (alpha == -1.0) s.mode = 2;
+  else if (alpha > 0.0 && std::isfinite(alpha)) {
+    int e = 0;
+    if (std::frexp(alpha, &e) == 0.5) {
+      s.mode = 3;
+      s.k = e - 1;
+    }
+  }
+  return s;
+}
+
+__device__ __forceinline__ double scaled(const Scale& s, double x) {
+  if (s.mode == 1) return x;
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  if (s.mode == 2) return __hiloint2double(hi ^ (int)0x80000000, lo);
+  if (s.mode == 3) {
+    const int ex = (hi >> 20) & 0x7ff, en = ex + s.k;
+    if (ex > 0 && ex < 0x7ff && en > 0 && en < 0x7ff) return __hiloint2double(hi + (s.k << 20), lo);
+  }
+  return __dmul_rn(s.alpha, x);
+}
+
+__device__ __forceinline__ double add_elem(const Scale& sa, const double* a, const Scale& sb, const double* b,
+                                           bool diag, double gamma, int e) {
+  double v = 0.0;
+  if (a) v = scaled(sa, a[e]);
+  if (b) {
+    const double t = scaled(sb, b[e]);
+    v = a ? __dadd_rn(v, t) : t;
+  }
+  if (diag) v = (a || b) ? __dadd_rn(v, gamma) : gamma;
+  return v;
+}
+
+// one warp per output block (grid-stride over blocks).  Element by element
+// v = 0 + alpha a + beta b + gamma [diagonal], left to right, each step
+// rounded; the leading 0 + x is x.  The FP64 Frobenius norm of the block.
+// Lanes take consecutive elements (VEC of them: two for even bs * bs).
+template <int VEC>
 __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t cnnz, int bs,
-                      double alpha, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
-                      const double* __restrict__ aval, double beta, const int32_t* __restrict__ brp,
+                      Scale sa, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                      const double* __restrict__ aval, Scale sb, const int32_t* __restrict__ brp,
                       const int32_t* __restrict__ bci, const double* __restrict__ bval, double gamma,
                       double* __restrict__ cval, double* __restrict__ cnorm) {
-  __shared__ double red[32];
-  __shared__ int sa, sb;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int bsz = bs * bs;
-  for (int64_t p = blockIdx.x; p < cnnz; p += gridDim.x) {
+  for (int64_t p = w0; p < cnnz; p += nw) {
     const int I = crow[p], J = cci[p];
-    if (threadIdx.x == 0) {
+    int qa = -1, qb = -1;
+    if (lane == 0) {
       int q = find_col(aci, arp[I], arp[I + 1], J);
-      sa = (q < arp[I + 1] && aci[q] == J) ? q : -1;
-      sb = -1;
+      qa = (q < arp[I + 1] && aci[q] == J) ? q : -1;
       if (bval) {
         int r = find_col(bci, brp[I], brp[I + 1], J);
-        sb = (r < brp[I + 1] && bci[r] == J) ? r : -1;
+        qb = (r < brp[I + 1] && bci[r] == J) ? r : -1;
       }
     }
-    __syncthreads();
-    const int qa = sa, qb = sb;
+    qa = __shfl_sync(0xffffffffu, qa, 0);
+    qb = __shfl_sync(0xffffffffu, qb, 0);
     const double* a = qa >= 0 ? aval + (size_t)qa * bsz : nullptr;
     const double* b = qb >= 0 ? bval + (size_t)qb * bsz : nullptr;
     double* c = cval + (size_t)p * bsz;
+    const bool dblk = I == J && gamma != 0.0;
     double ss = 0.0;
-    for (int e = threadIdx.x; e < bsz; e += blockDim.x) {
-      double v = 0.0;
-      if (a) v = __dadd_rn(v, __dmul_rn(alpha, a[e]));
-      if (b) v = __dadd_rn(v, __dmul_rn(beta, b[e]));
-      if (I == J && (e / bs) == (e % bs)) v = __dadd_rn(v, gamma);
-      c[e] = v;
-      ss = fma(v, v, ss);
+    for (int e = lane * VEC; e < bsz; e += 32 * VEC) {
+      if constexpr (VEC == 2) {
+        double2 v;
+        v.x = add_elem(sa, a, sb, b, dblk && e / bs == e % bs, gamma, e);
+        v.y = add_elem(sa, a, sb, b, dblk && (e + 1) / bs == (e + 1) % bs, gamma, e + 1);
+        *reinterpret_cast<double2*>(c + e) = v;
+        ss = fma(v.x, v.x, ss);
+        ss = fma(v.y, v.y, ss);
+      } else {
+        const double v = add_elem(sa, a, sb, b, dblk && e / bs == e % bs, gamma, e);
+        c[e] = v;
+        ss = fma(v, v, ss);
+      }
     }
-    double t = block_reduce_sum(ss, red);
-    if (threadIdx.x == 0) cnorm[p] = sqrt(t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) cnorm[p] = sqrt(ss);
   }
 }
 
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
                  ifac_bsr& C, const int32_t* crow) {
   if (C.nnzb == 0) return;
-  int grid = (int)std::min<int64_t>(C.nnzb, 152 * 16);
-  k_add<<<grid, 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, alpha, A.row_ptr, A.col_idx, A.val, beta,
-                                       B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr,
-                                       gamma, C.val, C.norms);
+  const int64_t warps = std::min<int64_t>(C.nnzb, 152 * 64);
+  const Scale sa = make_scale(alpha), sb = make_scale(beta);
+  const int32_t* brp = B ? B->row_ptr : nullptr;
+  const int32_t* bci = B ? B->col_idx : nullptr;
+  const double* bv = B ? B->val : nullptr;
+  if ((C.bs * C.bs) % 2 == 0)  // pairs never straddle two blocks
+    k_add<2><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
+                                                             A.val, sb, brp, bci, bv, gamma, C.val, C.norms);
+  else
+    k_add<1><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
+                                                             A.val, sb, brp, bci, bv, gamma, C.val, C.norms);
   IFAC_CK_LAUNCH();
 }
 

@@ -42,8 +42,10 @@ static void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
   ctx->launches = 0;
   ctx->gemm_launches = 0;
   ctx->tc_launches = 0;
+  ctx->split_launches = 0;
   ctx->pairs_fp64 = 0;
   ctx->pairs_tc = 0;
+  ctx->pairs_split = 0;
   ctx->events_used = 0;
   ctx->profile = o.profile != 0;
   reset_device_counters(ctx);
@@ -58,8 +60,8 @@ int delta_prec_of(const ifac_opts& o, int bs) {
 
 static void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   check_device_error(ctx);
-  read_device_counters(ctx, &ctx->pairs_fp64, &ctx->pairs_tc);
-  ctx->pairs = ctx->pairs_fp64 + ctx->pairs_tc;
+  read_device_counters(ctx, &ctx->pairs_fp64, &ctx->pairs_tc, &ctx->pairs_split);
+  ctx->pairs = ctx->pairs_fp64 + ctx->pairs_tc + ctx->pairs_split;
   if (!r) {
     double a, b;
     prof_collect(ctx, &a, &b);
@@ -70,10 +72,12 @@ static void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   r->block_pairs = ctx->pairs;
   r->nnzb_Z = Z.nnzb;
   r->flops = 2.0 * (double)Z.bs * Z.bs * Z.bs * (double)ctx->pairs;
-  prof_collect(ctx, &r->gemm_ms, &r->tc_ms);
+  prof_collect(ctx, &r->gemm_ms, &r->tc_ms, &r->split_ms);
   r->launches = ctx->launches;
   r->gemm_launches = ctx->gemm_launches;
   r->tc_launches = ctx->tc_launches;
+  r->split_launches = ctx->split_launches;
+  r->split_pairs = ctx->pairs_split;
   r->fp64_pairs = ctx->pairs_fp64;
   r->tc_pairs = ctx->pairs_tc;
   ctx->profile = false;

@@ -27,6 +27,7 @@
 // Every mbarrier wait is bounded; on expiry the CTA records an error flag,
 // drains its own copies and MMAs, releases tensor memory and returns.
 #include <cuda.h>
+#include <type_traits>
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -692,21 +693,67 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   return r;
 }
 
-// dst[q] = low-precision copy of block src[q] of X (K-major: transposed when tr)
+// FP64 -> BF16 (round to nearest even) and FP64 -> FP32 (round to nearest
+// even) -> TF32 (round half away from zero at 10 fraction bits), on the bit
+// patterns: GB300's FP64 pipe is narrow.  Magnitudes below 2^-126 become
+// zero (the tensor-core formats' normal range starts there; the products of
+// such inputs would be below FP32's normal range as well).
+__device__ __forceinline__ uint32_t f64_to_f32_bits_rne(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int ex = (int)((u >> 52) & 0x7ff);
+  if (ex == 0x7ff) return sign | 0x7f800000u | (((u & 0xfffffffffffffull) != 0) ? 0x400000u : 0u);
+  const int e32 = ex - 1023 + 127;
+  if (e32 < 1) return sign;  // below the normal range: zero
+  const unsigned long long m = u & 0xfffffffffffffull;
+  uint32_t mant = (uint32_t)(m >> 29);
+  const uint32_t rem = (uint32_t)(m & 0x1fffffffull);
+  uint32_t bits = ((uint32_t)e32 << 23) | mant;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) ++bits;  // carries into the exponent
+  if (e32 > 254 || bits >= 0x7f800000u) return sign | 0x7f800000u;
+  return sign | bits;
+}
+
+__device__ __forceinline__ uint16_t f64_to_bf16_bits_rne(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint16_t sign = (uint16_t)((u >> 48) & 0x8000u);
+  const int ex = (int)((u >> 52) & 0x7ff);
+  if (ex == 0x7ff) return sign | 0x7f80u | (((u & 0xfffffffffffffull) != 0) ? 0x40u : 0u);
+  const int e8 = ex - 1023 + 127;
+  if (e8 < 1) return sign;
+  const unsigned long long m = u & 0xfffffffffffffull;
+  const uint32_t mant = (uint32_t)(m >> 45);
+  const unsigned long long rem = m & 0x1fffffffffffull, half = 0x100000000000ull;
+  uint32_t bits = ((uint32_t)e8 << 7) | mant;
+  if (rem > half || (rem == half && (mant & 1u))) ++bits;
+  if (e8 > 254 || bits >= 0x7f80u) return sign | 0x7f80u;
+  return sign | (uint16_t)bits;
+}
+
+// dst[q] = low-precision copy of block src[q] of X (K-major: transposed when
+// tr).  Reads are coalesced; a transposed copy goes through shared memory.
 template <int ELT>
-__global__ void k_convert(const double* __restrict__ val, const int32_t* __restrict__ src, int64_t nblk, int tr,
-                          void* __restrict__ dst) {
+__global__ void __launch_bounds__(256) k_convert(const double* __restrict__ val, const int32_t* __restrict__ src,
+                                                 int64_t nblk, int tr, void* __restrict__ dst) {
   constexpr int BSZ = BS * BS;
+  using T = typename std::conditional<ELT == 2, uint16_t, uint32_t>::type;
+  __shared__ T tile[BS][BS + 1];
+  T* out = reinterpret_cast<T*>(dst);
   for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
     const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
+    T* d = out + (size_t)qb * BSZ;
     for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
-      const int r = e / BS, c = e % BS;
-      const double x = tr ? s[c * BS + r] : s[e];
-      if constexpr (ELT == 2) {
-        reinterpret_cast<__nv_bfloat16*>(dst)[(size_t)qb * BSZ + e] = __double2bfloat16(x);
-      } else {
-        reinterpret_cast<uint32_t*>(dst)[(size_t)qb * BSZ + e] = f32_to_tf32(__double2float_rn(x));
-      }
+      const double x = s[e];
+      T y;
+      if constexpr (ELT == 2) y = f64_to_bf16_bits_rne(x);
+      else y = f32_to_tf32(__uint_as_float(f64_to_f32_bits_rne(x)));
+      if (tr) tile[e / BS][e % BS] = y;
+      else d[e] = y;
+    }
+    if (tr) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < BSZ; e += blockDim.x) d[e] = tile[e % BS][e / BS];
+      __syncthreads();
     }
   }
 }
@@ -1307,11 +1354,11 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     max_clusters = sms / CL;
   }
   cfg.gridDim = dim3((unsigned)(std::min<int64_t>(ntot, max_clusters) * CL), 1, 1);
-  prof_begin(ctx, 1);
+  prof_begin(ctx, 2);
   IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA, mB, args));
   IFAC_CK_LAUNCH();
   prof_end(ctx);
-  ++ctx->tc_launches;
+  ++ctx->split_launches;
   {
     int ea = 0;
     const double am = std::frexp(alpha, &ea) * 2.0;  // alpha = am 2^(ea - 1), am in [1, 2)

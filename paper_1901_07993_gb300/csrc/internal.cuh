@@ -26,9 +26,9 @@ struct ifac_ctx {
   int64_t pairs = 0;
   int64_t launches = 0;
   int64_t gemm_launches = 0;
-  int64_t tc_launches = 0;
-  int64_t pairs_fp64 = 0, pairs_tc = 0;
-  std::vector<char> event_kind;  // per recorded event pair: 0 FP64 kernel, 1 tensor-core kernel
+  int64_t tc_launches = 0, split_launches = 0;
+  int64_t pairs_fp64 = 0, pairs_tc = 0, pairs_split = 0;
+  std::vector<char> event_kind;  // per recorded event pair: 0 FP64, 1 tensor-core (TF32/BF16), 2 split kernel
   // optional event timing of the numeric product kernels
   bool profile = false;
   std::vector<cudaEvent_t> events;
@@ -189,11 +189,11 @@ int refine_adjoint(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& F, int K, d
 void prof_begin(ifac_ctx* ctx, int kind = 0);
 void prof_end(ifac_ctx* ctx);
 // summed event time per kind (0: FP64 kernel, 1: tensor-core kernel)
-void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc);
+void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc, double* ms_split = nullptr);
 
 // Zero the device counters / read them back (read_* synchronises).
 void reset_device_counters(ifac_ctx* ctx);
-void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc);
+void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc, int64_t* pairs_split = nullptr);
 // Fails with IFAC_ERR_TIMEOUT (and clears the flag) if a device wait expired.
 void check_device_error(ifac_ctx* ctx);
 

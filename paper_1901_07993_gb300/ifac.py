@@ -59,7 +59,8 @@ class _Report(ctypes.Structure):
                 ("flops", ctypes.c_double), ("fp64_delta_evals", ctypes.c_int), ("low_sweeps", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
                 ("fp64_pairs", ctypes.c_int64), ("tc_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double),
-                ("tc_pairs", ctypes.c_int64), ("resid_fro", ctypes.c_double)]
+                ("tc_pairs", ctypes.c_int64), ("resid_fro", ctypes.c_double), ("split_launches", ctypes.c_int64),
+                ("split_ms", ctypes.c_double), ("split_pairs", ctypes.c_int64)]
 
 
 _lib = None
@@ -221,6 +222,9 @@ class Report:
     tc_pairs: int = 0
     resid_fro: float = 0.0
     status: int = 0
+    split_launches: int = 0
+    split_ms: float = 0.0
+    split_pairs: int = 0
 
 
 def upload(ctx: Context, host) -> DeviceBSR:
@@ -248,7 +252,8 @@ def opts(m: int = 2, max_iter: int = 50, fixed_iters: int = 0, c_rule: int = 0, 
 def _report(r: _Report, rc: int) -> Report:
     return Report(r.sweeps, r.stop_reason, r.levels, r.beta, [r.delta_fro[i] for i in range(r.n_delta)],
                   r.products, r.block_pairs, r.nnzb_Z, r.flops, r.fp64_delta_evals, r.low_sweeps, r.launches,
-                  r.gemm_launches, r.gemm_ms, r.fp64_pairs, r.tc_launches, r.tc_ms, r.tc_pairs, r.resid_fro, rc)
+                  r.gemm_launches, r.gemm_ms, r.fp64_pairs, r.tc_launches, r.tc_ms, r.tc_pairs, r.resid_fro, rc,
+                  r.split_launches, r.split_ms, r.split_pairs)
 
 
 def bsr_gemm_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, transB: bool, alpha: float = 1.0,

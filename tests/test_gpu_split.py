@@ -184,7 +184,7 @@ def test_split_refine_matches_oracle(ctx):
     # 2e-12 here (FP64 pipe: 3e-13); the norms agree down to that floor
     assert np.allclose(rep.delta_fro, rep_ref.delta_fro, rtol=1e-6, atol=1e-11)
     assert _rel(Z.download(), Z_ref) <= 1e-10
-    assert rep.tc_pairs == rep.block_pairs and rep.fp64_pairs == 0
+    assert rep.split_pairs == rep.block_pairs and rep.fp64_pairs == 0 and rep.tc_pairs == 0
 
 
 def test_split_localized_matches_oracle(ctx):

@@ -99,3 +99,31 @@ def test_tc_truncation_and_sparse_tiles(ctx, prec):
     keep = oracle.truncate(ref, tau)
     assert np.array_equal(got.col_idx, keep.col_idx) and np.array_equal(got.row_ptr, keep.row_ptr)
     assert np.abs(got.val - keep.val).max() <= 1e-4 * np.abs(keep.val).max()
+
+
+@pytest.mark.parametrize("prec", [TF32, BF16])
+def test_tc_input_rounding_exact(ctx, prec):
+    """C = A I on the tensor cores is A rounded to the input format, exactly:
+    ties at the rounding position (to even for BF16, the FP32 step of TF32;
+    away from zero for TF32's last step), carries into the exponent, signed
+    values and magnitudes near and below 2^-126 (zero below)."""
+    from paper_1901_07993_gb300 import ifac
+    rng = np.random.default_rng(7)
+    nb, bs = 2, 64
+    v = rng.standard_normal((nb * nb, bs, bs))
+    special = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, 1 + 2.0 ** -24,
+                        1 + 3 * 2.0 ** -24, 2 - 2.0 ** -9, 2 - 2.0 ** -12, 2.0 ** -126, 1.5 * 2.0 ** -126,
+                        2.0 ** -127, 0.0, -0.0, 3.0e38, 1e-300, 2.0 ** 100 * (1 + 2.0 ** -8)])
+    flat = v.reshape(-1)
+    flat[:len(special)] = special
+    flat[len(special):2 * len(special)] = -special
+    rp = np.arange(0, nb * nb + 1, nb, dtype=np.int32)
+    ci = np.tile(np.arange(nb, dtype=np.int32), nb)
+    A = synth.HostBSR(nb * bs, bs, rp, ci, v)
+    eye = np.zeros((nb, bs, bs))
+    eye[:] = np.eye(bs)
+    I = synth.HostBSR(nb * bs, bs, np.arange(nb + 1, dtype=np.int32), np.arange(nb, dtype=np.int32), eye)
+    got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), False, ifac.upload(ctx, I), False, 1.0, 0.0, prec).download()
+    want = rounded(A, prec).val
+    want = np.where(np.abs(want) < 2.0 ** -126, 0.0, want)
+    assert np.array_equal(got.val, want)
