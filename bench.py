@@ -51,6 +51,14 @@ WORKLOADS = {
     # the same at n = 8192 (operands of about L2 size): the profiling case
     "product-dense-bf16-n8192": dict(geom="dense", n=8192, bs=64, tau=0.0, target=0.0, method="product", m=2,
                                      seed=1, leaf=512, prec="bf16", compare=(), sample_n=None),
+    # the split FP64-accurate product (7 BF16 slices, 28 slice pairs) on the
+    # same dense pattern at n = 8192: the profiling case of the split kernel
+    "product-dense-split-n8192": dict(geom="dense", n=8192, bs=64, tau=0.0, target=0.0, method="product", m=2,
+                                      seed=1, leaf=512, prec="split", compare=(), sample_n=None),
+    # the mixed-precision refinement at n = 65,536: the profiling case of the
+    # kernels of the default workload (a quarter of its rows)
+    "irsi-mixed-chain-n65536-bs64": dict(geom="chain", n=65536, bs=64, tau=1e-12, target=1e-10, method="refine",
+                                         m=2, seed=0, leaf=512, prec="tf32", compare=(), sample_n=4096),
     # 64 independent matrices refined together: 32 chains and 32 3D clusters,
     # sizes log-uniform in [512, 8192] (seed 3, member j generated with seed
     # 3000 + j), BSR 64x64, TF32 products, FP64 final residual of every member
@@ -67,7 +75,7 @@ WORKLOADS = {
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
 }
 DEFAULT_WORKLOAD = "irsi-mixed-chain-n262144-bs64"
-PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "split": 3}
 METRIC = "Inverse-factor time & block-GEMM TFLOP/s: mixed vs FP64 at ||I-Z*SZ||_F<=1e-10"
 UNIT = "factorizations/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
@@ -258,7 +266,7 @@ def config_of(w, name, world):
             "parallelism": f"replicas{world}", "l2": "flushed between timed steps (512 MB write)"}
 
 
-DTYPE = {"fp64": "f64", "tf32": "tf32/f32acc+f64", "bf16": "bf16/f32acc+f64"}
+DTYPE = {"fp64": "f64", "tf32": "tf32/f32acc+f64", "bf16": "bf16/f32acc+f64", "split": "f64 (bf16 slices, exact f32acc)"}
 
 
 def timed_factorizations(ctx, ifac, factor, S, w, o, steps, flush):
@@ -472,8 +480,11 @@ def run_product(args, w, world, rank, local, ctx, ifac):
     ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total = allmax(world, sum(ms))
     fl = 2.0 * w["n"] ** 3
-    peak, src = tensor_peak_tflops(w["prec"])
-    ach = fl / (sum(ms) / args.steps / 1e3) / 1e12
+    split = w["prec"] == "split"
+    peak, src = tensor_peak_tflops("bf16" if split else w["prec"])
+    ach = (SPLIT_PAIRS if split else 1) * fl / (sum(ms) / args.steps / 1e3) / 1e12
+    extra = {"fp64_equivalent_tflops": ach / SPLIT_PAIRS,
+             "note": f"achieved = {SPLIT_PAIRS} BF16 slice-pair products per block pair"} if split else {}
     if rank == 0:
         print(json.dumps({
             "metric": "block-sparse product TFLOP/s (dense pattern, tensor cores)", "value": world * args.steps / (total / 1e3),
@@ -482,7 +493,7 @@ def run_product(args, w, world, rank, local, ctx, ifac):
             "dtype": DTYPE[w["prec"]], "data": "synthetic", "config": config_of(w, args.workload, world),
             "roofline": {"bound": "tensor", "kernel": "k_gemm_tc (whole bsr_gemm_trunc call)", "achieved": ach,
                          "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                         "peak_source": src}, "clocks": clk.summary()}), flush=True)
+                         "peak_source": src, **extra}, "clocks": clk.summary()}), flush=True)
 
 
 def main():
