@@ -154,6 +154,12 @@ typedef struct {
 int ifac_create(ifac_ctx** ctx, void* stream, const ifac_allocator* alloc);
 void ifac_destroy(ifac_ctx* ctx);
 int ifac_set_stream(ifac_ctx* ctx, void* stream);
+/* Slices per operand of the context's IFAC_FP64_SPLIT products, 4..8
+ * (default 7): s slices keep about 7 s bits of every scaled row and column,
+ * the product uses the s (s + 1) / 2 slice pairs with s_a + s_b <= s + 1,
+ * and the element error is about 2^-(7 s - 3) K max|op(A)_i.| max|op(B)_.j|.
+ * IFAC_ERR_INVALID outside 4..8. */
+int ifac_set_split_slices(ifac_ctx* ctx, int slices);
 const char* ifac_last_error(const ifac_ctx* ctx);
 void ifac_opts_default(ifac_opts* opts);
 
@@ -298,11 +304,13 @@ int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double ta
  * members sit on the diagonal of one block-diagonal matrix, so every block
  * product of a sweep serves all of them.  Each member has its own Gershgorin
  * bound, Z_0 = c_k I, ||delta||_F and stop test (target, the rule of Section
- * 2.2, and -- for opts->prec TF32/BF16, where rounding of the low-precision
- * products sets the floor -- ||delta||_F no longer decreasing, or max_iter);
- * a stopped member leaves the batch.  All block products use opts->prec (on
- * the tensor cores for TF32/BF16, bs = 64); the final residual of every
- * member is evaluated with FP64 products and returned in rep[k].resid_fro.
+ * 2.2, or max_iter); a stopped member leaves the batch.  With opts->prec
+ * TF32/BF16 (tensor cores, bs = 64) every member follows the mixed-precision
+ * schedule of inv_factor_refine: low-precision sweeps until its floor, then
+ * delta with FP64-accurate products (opts->delta_prec) and M in opts->prec
+ * until the target or until ||delta||_F stops falling.  The final residual
+ * of every member is evaluated with FP64-accurate products (delta_prec) and
+ * returned in rep[k].resid_fro.
  * All members need the same bs.  Z[k] (count entries) receive the factors;
  * rep may be NULL or hold count reports (batch-wide counters are repeated in
  * each).  Returns IFAC_WARN_TARGET_NOT_MET if any member stopped above the

@@ -230,6 +230,12 @@ int ifac_set_stream(ifac_ctx* ctx, void* stream) {
   return IFAC_OK;
 }
 
+int ifac_set_split_slices(ifac_ctx* ctx, int slices) {
+  if (!ctx || slices < 4 || slices > 8) return IFAC_ERR_INVALID;
+  ctx->split_slices = slices;
+  return IFAC_OK;
+}
+
 const char* ifac_last_error(const ifac_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
 int ifac_bsr_upload(ifac_ctx* ctx, int64_t n, int32_t bs, int32_t nb, int64_t nnzb, const int32_t* row_ptr,

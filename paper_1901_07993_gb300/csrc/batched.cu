@@ -7,9 +7,10 @@
 // sequence refines the whole batch.  Each member keeps its own Gershgorin
 // bound, start Z_0 = c_i I, delta norm and stop test; a member that stopped
 // is removed from S and delta, so it costs nothing further and its Z stays at
-// the iterate its stop test returned.  All products run in opts.prec; the
-// final residual ||I - Z_i^T S_i Z_i||_F of every member is evaluated with
-// FP64 products.
+// the iterate its stop test returned.  With TF32/BF16 products the members
+// follow the mixed-precision schedule (low-precision sweeps, then delta with
+// FP64-accurate products); the final residual ||I - Z_i^T S_i Z_i||_F of
+// every member is evaluated with FP64-accurate products.
 #include <cmath>
 #include <vector>
 
@@ -145,64 +146,108 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
     IFAC_CK_LAUNCH();
     block_norms(ctx, Z.m, Z.m.norms);
   }
-  // sweeps
+  // sweeps.  Stage 0 runs every product in opts.prec.  With TF32/BF16 a
+  // member whose low-precision floor is reached (the rule of Section 2.2
+  // fires, or ||delta||_F stops falling) is parked at its current Z; stage 1
+  // then evaluates delta of the parked members with FP64-accurate products
+  // (opts.delta_prec), M staying in opts.prec, until the target or until
+  // ||delta||_F stops falling -- the schedule of the single-matrix refinement.
   const bool low = o.prec != IFAC_FP64;
+  const int dprec = delta_prec_of(o, bs);
   std::vector<double> e(count, 0.0), e_prev(count, INFINITY);
-  std::vector<uint8_t> active(count, 1);
-  std::vector<int> sweeps(count, 0), stop(count, 0);
+  std::vector<uint8_t> active(count, 1), parked(count, 0);
+  std::vector<int> sweeps(count, 0), stop(count, 0), fp64_evals(count, 0), low_sweeps(count, 0);
   std::vector<std::vector<double>> hist(count);
   Buf<uint8_t> dactive(ctx, count);
   Buf<double> ne(ctx, count);
   Mat Sa = copy_mat(ctx, S.m);
-  for (int it = 0;; ++it) {
-    Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, o.prec);   // S Z
-    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, o.prec);     // Z^T (S Z)
-    X.reset();
-    Mat Dall = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);              // I - Z^T S Z
-    Y.reset();
-    IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
-    Mat D = filter_rows_active(ctx, Dall.m, dseg.p, dactive.p);
-    Dall.reset();
-    node_fro(ctx, D.m, dnb0.p, dnb1.p, count, ne.p);
-    to_host(ctx, e.data(), ne.p, sizeof(double) * count);
-    bool any = false;
-    for (int k = 0; k < count; ++k) {
-      if (!active[k]) continue;
-      hist[k].push_back(e[k]);
-      int st = 0;
-      if (e[k] <= target) st = IFAC_STOP_TARGET;
-      else if (e[k] > std::pow(e_prev[k], (double)(o.m + 1)) || (low && !(e[k] < e_prev[k]))) st = IFAC_STOP_RULE;
-      else if (sweeps[k] >= o.max_iter) st = IFAC_STOP_MAXITER;
-      if (st) {
-        active[k] = 0;
-        stop[k] = st;
-      } else {
-        any = true;
-      }
-      e_prev[k] = e[k];
+  for (int stage = 0; stage < (low ? 2 : 1); ++stage) {
+    if (stage == 1) {
+      bool any_parked = false;
+      for (int k = 0; k < count; ++k)
+        if (parked[k]) {
+          active[k] = 1;
+          e_prev[k] = INFINITY;
+          any_parked = true;
+        }
+      if (!any_parked) break;
+      IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
+      Sa = filter_rows_active(ctx, S.m, dseg.p, dactive.p);
+      IFAC_CK(cudaStreamSynchronize(ctx->stream));  // the host flags are reused below
     }
-    if (!any) break;
-    IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
-    D = filter_rows_active(ctx, D.m, dseg.p, dactive.p);
-    Sa = filter_rows_active(ctx, Sa.m, dseg.p, dactive.p);
-    IFAC_CK(cudaStreamSynchronize(ctx->stream));  // the host flags are reused next sweep
-    Mat P = add(ctx, 0.5, D.m, 0.0, nullptr, 0.0);
-    {  // P = sum_{k=1}^{m} b_k delta^k
-      Mat Dk;
-      double b = 0.5;
-      for (int k = 2; k <= o.m; ++k) {
-        b = b * (double)(2 * k - 1) / (double)(2 * k);
-        Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec);
-        Dk = std::move(Dn);
-        P = add(ctx, 1.0, P.m, b, &Dk.m, 0.0);
+    const int pd = stage == 0 ? o.prec : dprec;
+    for (int it = 0;; ++it) {
+      Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd);   // S Z
+      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd);     // Z^T (S Z)
+      X.reset();
+      Mat Dall = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);          // I - Z^T S Z
+      Y.reset();
+      IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
+      Mat D = filter_rows_active(ctx, Dall.m, dseg.p, dactive.p);
+      Dall.reset();
+      node_fro(ctx, D.m, dnb0.p, dnb1.p, count, ne.p);
+      to_host(ctx, e.data(), ne.p, sizeof(double) * count);
+      bool any = false;
+      for (int k = 0; k < count; ++k) {
+        if (!active[k]) continue;
+        int st = 0;
+        bool park = false;
+        if (stage == 1) ++fp64_evals[k];
+        if (e[k] <= target) {
+          st = IFAC_STOP_TARGET;
+        } else if (stage == 0) {
+          if (e[k] > std::pow(e_prev[k], (double)(o.m + 1)) || (low && !(e[k] < e_prev[k]))) {
+            if (low) park = true;
+            else st = IFAC_STOP_RULE;
+          } else if (sweeps[k] >= o.max_iter) {
+            st = IFAC_STOP_MAXITER;
+          }
+        } else if (!(e[k] < e_prev[k])) {
+          st = IFAC_STOP_RULE;  // the FP64 floor
+        } else if (sweeps[k] >= o.max_iter) {
+          st = IFAC_STOP_MAXITER;
+        }
+        if (park) {  // delta is evaluated again, with FP64-accurate products, in stage 1
+          active[k] = 0;
+          parked[k] = 1;
+          continue;
+        }
+        hist[k].push_back(e[k]);
+        if (st) {
+          active[k] = 0;
+          parked[k] = 0;
+          stop[k] = st;
+        } else {
+          any = true;
+        }
+        e_prev[k] = e[k];
       }
+      if (!any) break;
+      IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
+      D = filter_rows_active(ctx, D.m, dseg.p, dactive.p);
+      Sa = filter_rows_active(ctx, Sa.m, dseg.p, dactive.p);
+      IFAC_CK(cudaStreamSynchronize(ctx->stream));  // the host flags are reused next sweep
+      Mat P = add(ctx, 0.5, D.m, 0.0, nullptr, 0.0);
+      {  // P = sum_{k=1}^{m} b_k delta^k
+        Mat Dk;
+        double b = 0.5;
+        for (int k = 2; k <= o.m; ++k) {
+          b = b * (double)(2 * k - 1) / (double)(2 * k);
+          Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec);
+          Dk = std::move(Dn);
+          P = add(ctx, 1.0, P.m, b, &Dk.m, 0.0);
+        }
+      }
+      D.reset();
+      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec);   // M = Z sum b_k delta^k
+      P.reset();
+      Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);
+      for (int k = 0; k < count; ++k)
+        if (active[k]) {
+          ++sweeps[k];
+          if (stage == 0 && low) ++low_sweeps[k];
+        }
     }
-    D.reset();
-    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec);   // M = Z sum b_k delta^k
-    P.reset();
-    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);
-    for (int k = 0; k < count; ++k)
-      if (active[k]) ++sweeps[k];
   }
   // FP64 residual of every member
   std::vector<double> resid(count, 0.0);
@@ -253,6 +298,8 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       for (int i = 0; i < r.n_delta; ++i) r.delta_fro[i] = hist[k][i];
       r.nnzb_Z = p1 - p0;
       r.resid_fro = resid[k];
+      r.fp64_delta_evals = fp64_evals[k];
+      r.low_sweeps = low_sweeps[k];
       // batch-wide counters are reported on every member
       r.products = ctx->products;
       r.block_pairs = pf + pt + ps;
@@ -274,7 +321,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   IFAC_CK(cudaStreamSynchronize(ctx->stream));
   for (int k = 0; k < count; ++k) Zout[k] = outs[k].release();
   bool target_met = true;
-  for (int k = 0; k < count; ++k) target_met = target_met && e_prev[k] <= target;
+  for (int k = 0; k < count; ++k) target_met = target_met && stop[k] == IFAC_STOP_TARGET;
   return target_met ? IFAC_OK : IFAC_WARN_TARGET_NOT_MET;
 }
 

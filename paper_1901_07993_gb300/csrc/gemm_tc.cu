@@ -46,7 +46,7 @@ constexpr long long WAIT_LIMIT = 1ll << 27;
 // split mode: K steps per exact FP32 window, table sizes
 constexpr int KW = 16;
 constexpr int MAX_UNITS = 16;
-constexpr int MAX_PAIRS = 32;
+constexpr int MAX_PAIRS = 40;
 
 template <int ELT>
 struct Cfg {
@@ -1054,9 +1054,9 @@ __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __res
 }
 
 // NS BF16 slice copies (K-major, op() CSR order) of a view; row r of block qb
-// has scale exponent sexp[sblk[qb] * BS + r].  With Y = x 2^(55 - e) held as a
-// 64-bit integer (|Y| < 2^55; bits below 2^-55 of sigma dropped by rounding),
-// digit k is q_k = round(Y_k / 2^(55 - 7k)), Y_{k+1} = Y_k - q_k 2^(55 - 7k).
+// has scale exponent sexp[sblk[qb] * BS + r].  With Y = x 2^(62 - e) held as a
+// 64-bit integer (|Y| < 2^62; bits below 2^-62 of sigma dropped by rounding),
+// digit k is q_k = round(Y_k / 2^(62 - 7k)), Y_{k+1} = Y_k - q_k 2^(62 - 7k).
 __global__ void k_split(const double* __restrict__ val, const int32_t* __restrict__ src, int64_t nblk, int tr,
                         const int32_t* __restrict__ sblk, const int* __restrict__ sexp, int ns,
                         __nv_bfloat16* __restrict__ dst) {
@@ -1073,14 +1073,14 @@ __global__ void k_split(const double* __restrict__ val, const int32_t* __restric
       int eb = ea;
       if (ea) mant |= 1ull << 52;
       else eb = 1;
-      // |x| = mant 2^(eb - 1075);  |Y| = mant 2^(eb - 1020 - e)
-      const int sh = eb - 1020 - se[r];
+      // |x| = mant 2^(eb - 1075);  |Y| = mant 2^(eb - 1013 - e)
+      const int sh = eb - 1013 - se[r];
       unsigned long long Y = 0;
-      if (sh >= 0) Y = mant << sh;  // sh <= 2 since |x| < sigma
+      if (sh >= 0) Y = mant << sh;  // sh <= 9 since |x| < sigma
       else if (sh > -63) Y = (mant + (1ull << (-sh - 1))) >> (-sh);
       long long y = (u >> 63) ? -(long long)Y : (long long)Y;
       for (int k = 1; k <= ns; ++k) {
-        const int d = 55 - SPLIT_BITS * k;
+        const int d = 62 - SPLIT_BITS * k;
         const long long q = (y + (1ll << (d - 1))) >> d;
         y -= q << d;
         dst[(size_t)(k - 1) * slice_stride + (size_t)qb * BSZ + e] = __float2bfloat16_rn((float)(int)q);
@@ -1192,7 +1192,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   constexpr int CL = Cf::CL;
   const int nb = A.nb;
   const int64_t rows = (int64_t)nb * BS;
-  if (ns < 1 || ns > 7) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 7 slices");
+  if (ns < 1 || ns > 8) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 8 slices");
   // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T)
   Buf<int> sige(ctx, rows), taue(ctx, rows);
   k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sige.p);

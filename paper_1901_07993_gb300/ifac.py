@@ -31,7 +31,7 @@ EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", 
            "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_add",
            "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
            "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
-           "inv_factor_refine_adjoint", "inv_factor_refine_batched")
+           "inv_factor_refine_adjoint", "inv_factor_refine_batched", "ifac_set_split_slices")
 
 
 class IfacError(RuntimeError):
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "ifac_create": ([ctypes.POINTER(p), p, p], i32),
         "ifac_destroy": ([p], None),
         "ifac_set_stream": ([p, p], i32),
+        "ifac_set_split_slices": ([p, i32], i32),
         "ifac_last_error": ([p], ctypes.c_char_p),
         "ifac_opts_default": ([ctypes.POINTER(_Opts)], None),
         "ifac_bsr_upload": ([p, i64, i32, i32, i64, p, p, p, PB], i32),
@@ -135,6 +136,9 @@ class Context:
 
     def set_stream(self, stream: int):
         self.check(self.lib.ifac_set_stream(self.h, ctypes.c_void_p(stream)))
+
+    def set_split_slices(self, slices: int):
+        self.check(self.lib.ifac_set_split_slices(self.h, int(slices)))
 
     def close(self):
         if getattr(self, "h", None):

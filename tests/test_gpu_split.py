@@ -5,9 +5,10 @@ FP64 product.
 Bound used element-wise: every scalar row i of op(A) is split relative to a
 power of two sigma_i < 2 max_k |a_ik|, every column j of op(B) relative to
 tau_j < 2 max_k |b_kj|; the dropped slice pairs and the split remainders cost
-at most 2^-46 sigma_i tau_j per product term, and each of the at most
-28 * ceil(K/16) FP64 additions into C rounds once.  So
-    |C - C_ref| <= K (2^-44 r_i c_j) + (28 ceil(K/16) + K) 2^-53 (|A||B|)_ij
+at most about 2^-(7 NS - 3) sigma_i tau_j per product term (NS slices; 2^-46
+for the default 7), and the conversion of the fixed-point sum rounds once per
+unit and window (at most 16 ceil(K/16) times).  With a factor 4 of margin:
+    |C - C_ref| <= K 2^-(7 NS - 5) r_i c_j + (16 ceil(K/16) + K) 2^-53 (|A||B|)_ij
 with r_i = max_k |a_ik|, c_j = max_k |b_kj|, K = scalar inner length."""
 import itertools
 
@@ -41,7 +42,7 @@ def dense(h):
     return D
 
 
-def _check(ctx, A, B, tA, tB, alpha=1.0):
+def _check(ctx, A, B, tA, tB, alpha=1.0, ns=7):
     from paper_1901_07993_gb300 import ifac
     ref = oracle.gemm(A, B, tA, tB, alpha, 0.0)
     got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), tA, ifac.upload(ctx, B), tB, alpha, 0.0,
@@ -54,7 +55,7 @@ def _check(ctx, A, B, tA, tB, alpha=1.0):
     c = np.abs(Bd).max(axis=0)
     absab = np.abs(Ad) @ np.abs(Bd)
     K = A.nb * A.bs
-    lim_d = abs(alpha) * (K * 2.0 ** -44 * np.outer(r, c) + (28 * -(-A.nb // 16) + K) * 2.0 ** -53 * absab)
+    lim_d = abs(alpha) * (K * 2.0 ** -(7 * ns - 5) * np.outer(r, c) + (16 * -(-A.nb // 16) + K) * 2.0 ** -53 * absab)
     bs = A.bs
     worst = 0.0
     for I in range(A.nb):
@@ -75,6 +76,20 @@ def test_split_random_blocks(ctx, tA, tB):
     B = synth.random_bsr(nb, 64, 0.4, seed=42, empty_rows=2, n=nb * 64 - 7)
     _, rel = _check(ctx, A, B, tA, tB, alpha=-1.25)
     assert rel < 1e-13  # FP64 class (TF32 and BF16 products give 1e-4 .. 1e-2)
+
+
+@pytest.mark.parametrize("ns", [5, 8])
+def test_split_slice_count(ctx, ns):
+    """Fewer or more slices move the bound by 2^-7 per slice; 8 slices use
+    36 pairs in 16 accumulation units."""
+    A = synth.random_bsr(20, 64, 0.5, seed=51)
+    B = synth.random_bsr(20, 64, 0.5, seed=52)
+    ctx.set_split_slices(ns)
+    try:
+        _, rel = _check(ctx, A, B, False, True, alpha=0.75, ns=ns)
+    finally:
+        ctx.set_split_slices(7)
+    assert rel < (1e-13 if ns == 8 else 1e-9)
 
 
 def test_split_truncation(ctx):
