@@ -232,11 +232,19 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-// x 2^sh as a 64-bit integer, rounded half up when sh < 0 (|x| <= 2^24)
-__device__ __forceinline__ long long fixed_term(int x, int sh) {
-  if (sh >= 0) return (long long)x << sh;
-  if (sh < -30) return 0;
-  return (long long)((x + (1 << (-sh - 1))) >> (-sh));
+// d + x 2^sh in 64-bit integers, x 2^sh rounded half up when sh < 0
+// (|x| <= 2^24); `bad` records a signed overflow of the term or the sum
+__device__ __forceinline__ long long fixed_add(long long d, int x, int sh, bool& bad) {
+  long long t;
+  if (sh >= 0) {
+    t = (long long)((unsigned long long)(long long)x << sh);
+    bad |= (t >> sh) != (long long)x;
+  } else {
+    t = (sh < -30) ? 0 : (long long)((x + (1 << (-sh - 1))) >> (-sh));
+  }
+  const long long r = (long long)((unsigned long long)d + (unsigned long long)t);
+  bad |= ((d ^ r) & (t ^ r)) < 0;
+  return r;
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory"); }
@@ -288,6 +296,7 @@ struct TileArgs {
   int unit_end[MAX_UNITS];
   int pair_ya[MAX_PAIRS], pair_yb[MAX_PAIRS];
   int unit_sh[MAX_UNITS];
+  int* ovf;  // set to 1 on a fixed-point overflow (the host then redoes the product with a safe scale)
 };
 
 template <int ELT>
@@ -657,12 +666,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
                 if (p >= 0) {
+                  bool bad = false;
 #pragma unroll
                   for (int e = 0; e < 16; ++e) {
-                    dv[e].x += fixed_term(__float2int_rn(v[2 * e]), sh);
-                    dv[e].y += fixed_term(__float2int_rn(v[2 * e + 1]), sh);
+                    dv[e].x = fixed_add(dv[e].x, __float2int_rn(v[2 * e]), sh, bad);
+                    dv[e].y = fixed_add(dv[e].y, __float2int_rn(v[2 * e + 1]), sh, bad);
                     dst[e * 32] = dv[e];
                   }
+                  if (bad) *args.ovf = 1;
                 }
               }
             }
@@ -969,6 +980,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.err = ctx->dev_err;
   args.split = 0;
   args.cpart = nullptr;
+  args.ovf = nullptr;
   args.nunits = 0;
   for (int u = 0; u < MAX_UNITS; ++u) args.unit_end[u] = args.unit_sh[u] = 0;
   for (int p = 0; p < MAX_PAIRS; ++p) args.pair_ya[p] = args.pair_yb[p] = 0;
@@ -1298,12 +1310,17 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.err = ctx->dev_err;
   args.split = 1;
   args.cpart = part.p;
-  // fixed point: |sum| <= K 2^f <= 2^62 for the scalar inner length K of the
-  // longest tile; f = 56 keeps every unit's weight 2^(f - 7g) integral
+  // fixed point, scale 2^-f relative to sigma_i tau_j.  Safe: |sum| <= K 2^f
+  // <= 2^62 for the scalar inner length K of the longest tile.  The kernel
+  // first runs with f = 54 (any sum below 2^9 sigma_i tau_j, the usual case,
+  // keeps 2^-54 of resolution) and reports an overflow, after which the
+  // product is redone with the safe f.  f <= 56 keeps every weight 2^(f - 7g)
+  // of the 7-slice product integral.
   int lgK = 0;
   while (((int64_t)1 << lgK) < (int64_t)std::max(kmax, 1) * BS) ++lgK;
-  const int fbits = std::min(56, 62 - lgK);
-  {
+  const int f_safe = std::min(56, 62 - lgK);
+  const int f_try = std::max(f_safe, 54);
+  auto set_units = [&](int fbits) {
     // units: slice pairs of equal weight packed while sum over the unit of
     // max|q_s| max|q_t| * 64 * KW stays <= 2^24
     const auto qmax = [](int s) { return s == 1 ? 128 : 64; };
@@ -1335,7 +1352,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
       if (open) args.unit_end[nu++] = np;
     }
     args.nunits = nu;
-  }
+  };
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
@@ -1354,11 +1371,24 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     max_clusters = sms / CL;
   }
   cfg.gridDim = dim3((unsigned)(std::min<int64_t>(ntot, max_clusters) * CL), 1, 1);
-  prof_begin(ctx, 2);
-  IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA, mB, args));
-  IFAC_CK_LAUNCH();
-  prof_end(ctx);
-  ++ctx->split_launches;
+  Buf<int> dovf(ctx, 1);
+  int fbits = f_try;
+  for (;;) {
+    set_units(fbits);
+    args.ovf = dovf.p;
+    IFAC_CK(cudaMemsetAsync(dovf.p, 0, sizeof(int), ctx->stream));
+    prof_begin(ctx, 2);
+    IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA, mB, args));
+    IFAC_CK_LAUNCH();
+    prof_end(ctx);
+    ++ctx->split_launches;
+    if (fbits == f_safe) break;
+    int ovf = 0;
+    to_host(ctx, &ovf, dovf.p, sizeof(int));
+    if (!ovf) break;
+    fbits = f_safe;
+    IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
+  }
   {
     int ea = 0;
     const double am = std::frexp(alpha, &ea) * 2.0;  // alpha = am 2^(ea - 1), am in [1, 2)

@@ -168,7 +168,9 @@ def test_split_exact_at_fp32_bound(ctx, nb):
     """All entries 1 - 2^-9: the leading slices are 128 and -32, so the first
     unit's accumulator reaches exactly 2^24 over a full window of 16 K blocks
     (1024 terms); the product K (1 - 2^-9)^2 is representable and must come
-    out exact (nb = 17 adds a one-block second window)."""
+    out exact (nb = 17 adds a one-block second window).  The sums (about
+    1000 sigma tau) overflow the first, finer fixed-point scale, so this also
+    runs the redo with the safe scale."""
     from paper_1901_07993_gb300 import ifac
     n = nb * 64
     v = 1.0 - 2.0 ** -9
