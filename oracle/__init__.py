@@ -86,6 +86,7 @@ def _load():
             "om_coef_b": ([i32], d),
             "om_irsi": ([p, ctypes.POINTER(_Opts), ctypes.POINTER(_Rep)], p),
             "om_lif": ([p, ctypes.POINTER(_Opts), ctypes.POINTER(_Rep)], p),
+            "om_rinch": ([p, ctypes.POINTER(_Opts), ctypes.POINTER(_Rep)], p),
             "om_invchol_dense": ([i32, p, p], i32),
             "om_resid": ([p, p], d),
             "om_counter_products": ([], i64),
@@ -252,6 +253,16 @@ def lif(S, m: int = 2, tau: float = 1e-10, target: float = 0.0, max_iter: int = 
     r = _Rep()
     with _Held(S) as (h,):
         z = _load().om_lif(h, ctypes.byref(o), ctypes.byref(r))
+    return _from_c(z, S.bs), _report(r)
+
+
+def rinch(S, tau: float = 1e-10, leaf_size: int = 512):
+    """Recursive inverse Cholesky (Algorithm 1) with the dense leaf routine
+    below leaf_size rows.  Returns (Z, Report); Report.levels = recursion depth."""
+    o = _opts(2, tau, 0.0, 50, 0, 0, leaf_size)
+    r = _Rep()
+    with _Held(S) as (h,):
+        z = _load().om_rinch(h, ctypes.byref(o), ctypes.byref(r))
     return _from_c(z, S.bs), _report(r)
 
 

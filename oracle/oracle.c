@@ -24,6 +24,8 @@
  *    refinement of Eq. (2.2) and the stop rule as in Algorithm 4.
  *  - om_invchol_dense: the leaf routine "factorize S^-1 = Z Z^T" of
  *    Algorithms 1-2, as Cholesky S = L L^T and Z = L^-T.
+ *  - om_rinch: recursive inverse Cholesky, Algorithm 1 (left-looking, two
+ *    blocks per dimension), with the leaf routine above at the lowest level.
  *
  * Every loop is the definition written out; there is no blocking, fusion or
  * reordering beyond the block structure the paper's storage itself has.
@@ -471,6 +473,53 @@ int om_invchol_dense(int n, const double* S, double* Z) {
   return 0;
 }
 
+/* Leaf routine on the principal sub-matrix [b0, b1) of S: the dense inverse
+ * Cholesky factor Z = L^-T, its blocks on and above the diagonal kept, then
+ * truncated (Section 5: truncation after leaf-level routines).  Returned in
+ * the sub-matrix's own index space; *status = -2 when a pivot fails. */
+static om_mat* leaf_factor(const om_mat* S, int b0, int b1, double tau, int* status) {
+  int bs = S->bs, nbs = b1 - b0, nl = nbs * bs;
+  size_t bsz = (size_t)bs * bs;
+  double* dS = (double*)calloc((size_t)nl * nl, sizeof(double));
+  double* dZ = (double*)calloc((size_t)nl * nl, sizeof(double));
+  for (int I = b0; I < b1; ++I)
+    for (int p = S->row_ptr[I]; p < S->row_ptr[I + 1]; ++p) {
+      int J = S->col_idx[p];
+      if (J < b0 || J >= b1) continue;
+      for (int r = 0; r < bs; ++r)
+        for (int c = 0; c < bs; ++c)
+          dS[(size_t)((I - b0) * bs + r) * nl + (J - b0) * bs + c] = S->val[(size_t)p * bsz + r * bs + c];
+    }
+  if (om_invchol_dense(nl, dS, dZ) != 0) *status = -2;
+  om_builder out = ob_begin((int64_t)nl, bs, nbs);
+  double* tmp = (double*)malloc(bsz * sizeof(double));
+  for (int I = 0; I < nbs; ++I) {
+    for (int J = I; J < nbs; ++J) {
+      for (int r = 0; r < bs; ++r)
+        for (int c = 0; c < bs; ++c) tmp[r * bs + c] = dZ[(size_t)(I * bs + r) * nl + J * bs + c];
+      if (!(block_fro(tmp, bs) < tau)) memcpy(ob_push(&out, J), tmp, bsz * sizeof(double));
+    }
+    ob_end_row(&out, I);
+  }
+  free(tmp); free(dS); free(dZ);
+  return out.m;
+}
+
+/* A (na x na, own index space) placed at block offset off of an nbs-block
+ * square matrix, zero elsewhere. */
+static om_mat* om_embed(const om_mat* A, int nbs, int off) {
+  size_t bsz = (size_t)A->bs * A->bs;
+  om_builder b = ob_begin((int64_t)nbs * A->bs, A->bs, nbs);
+  for (int I = 0; I < nbs; ++I) {
+    int li = I - off;
+    if (li >= 0 && li < A->nb)
+      for (int p = A->row_ptr[li]; p < A->row_ptr[li + 1]; ++p)
+        memcpy(ob_push(&b, A->col_idx[p] + off), A->val + (size_t)p * bsz, bsz * sizeof(double));
+    ob_end_row(&b, I);
+  }
+  return b.m;
+}
+
 /* ------------------------------------------------------------------ */
 /* LIF: localized inverse factorization (Algorithm 2)                   */
 /* ------------------------------------------------------------------ */
@@ -529,34 +578,7 @@ static om_mat* lif_rec(lif_ctx* L, const om_mat* S, int b0, int b1, int depth) {
   int bs = S->bs, nbs = b1 - b0;
   size_t bsz = (size_t)bs * bs;
   if (depth > L->depth_max) L->depth_max = depth;
-  if ((int64_t)nbs * bs <= o->leaf_size || nbs == 1) {
-    int nl = nbs * bs;
-    double* dS = (double*)calloc((size_t)nl * nl, sizeof(double));
-    double* dZ = (double*)calloc((size_t)nl * nl, sizeof(double));
-    for (int I = b0; I < b1; ++I)
-      for (int p = S->row_ptr[I]; p < S->row_ptr[I + 1]; ++p) {
-        int J = S->col_idx[p];
-        if (J < b0 || J >= b1) continue;
-        for (int r = 0; r < bs; ++r)
-          for (int c = 0; c < bs; ++c)
-            dS[(size_t)((I - b0) * bs + r) * nl + (J - b0) * bs + c] = S->val[(size_t)p * bsz + r * bs + c];
-      }
-    if (om_invchol_dense(nl, dS, dZ) != 0) L->status = -2;
-    /* blocks on and above the diagonal (Z is upper triangular), truncated */
-    om_builder out = ob_begin((int64_t)nl, bs, nbs);
-    for (int I = 0; I < nbs; ++I) {
-      for (int J = I; J < nbs; ++J) {
-        double* tmp = (double*)malloc(bsz * sizeof(double));
-        for (int r = 0; r < bs; ++r)
-          for (int c = 0; c < bs; ++c) tmp[r * bs + c] = dZ[(size_t)(I * bs + r) * nl + J * bs + c];
-        if (!(block_fro(tmp, bs) < o->tau)) memcpy(ob_push(&out, J), tmp, bsz * sizeof(double));
-        free(tmp);
-      }
-      ob_end_row(&out, I);
-    }
-    free(dS); free(dZ);
-    return out.m;
-  }
+  if ((int64_t)nbs * bs <= o->leaf_size || nbs == 1) return leaf_factor(S, b0, b1, o->tau, &L->status);
   int bm = b0 + nbs / 2;
   om_mat* ZA = lif_rec(L, S, b0, bm, depth + 1);
   om_mat* ZC = lif_rec(L, S, bm, b1, depth + 1);
@@ -607,6 +629,68 @@ om_mat* om_lif(const om_mat* S_in, const om_opts* o, om_report* rep) {
 /* ------------------------------------------------------------------ */
 
 /* ||I - Z^T S Z||_F with untruncated products. */
+/* ------------------------------------------------------------------ */
+/* RINCH: recursive inverse Cholesky (Algorithm 1)                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const om_opts* o;
+  int depth_max;
+  int status;
+} rinch_ctx;
+
+/* Inverse factor of the principal sub-matrix on block range [b0, b1) of S,
+ * in the sub-matrix's own index space.  With S = [S00 S01; S01^T S11] split
+ * at the block-aligned midpoint (the same split as LIF):
+ *   Z00 = rinch(S00),  R = Z00^T S01,  Q = -R^T R + S11,  Z11 = rinch(Q),
+ *   Z01 = -(Z00 R) Z11,  Z10 = 0,
+ * every product truncated at tau, sums not truncated.  The off-diagonal
+ * pieces live embedded in the sub-problem's index space (rows [0, na), cols
+ * [na, nbs)), so every product is between square matrices. */
+static om_mat* rinch_rec(rinch_ctx* R, const om_mat* S, int b0, int b1, int depth) {
+  const om_opts* o = R->o;
+  int bs = S->bs, nbs = b1 - b0;
+  if (depth > R->depth_max) R->depth_max = depth;
+  if ((int64_t)nbs * bs <= o->leaf_size || nbs == 1) return leaf_factor(S, b0, b1, o->tau, &R->status);
+  int bm = b0 + nbs / 2, na = bm - b0;
+  om_mat* Z00 = rinch_rec(R, S, b0, bm, depth + 1);
+  om_mat* Z00e = om_embed(Z00, nbs, 0);
+  om_free(Z00);
+  om_mat* S01 = om_sub_embedded(S, b0, b1, b0, bm, bm, b1);
+  om_mat* Rm = om_gemm(Z00e, 1, S01, 0, 1.0, o->tau);     /* R = Z00^T S01 */
+  om_free(S01);
+  om_mat* RtR = om_gemm(Rm, 1, Rm, 0, 1.0, o->tau);       /* R^T R */
+  om_mat* S11 = om_sub_embedded(S, b0, b1, bm, b1, bm, b1);
+  om_mat* Q = om_add(-1.0, RtR, 1.0, S11, 0.0);           /* Q = -R^T R + S11 */
+  om_free(RtR); om_free(S11);
+  om_mat* Z11 = rinch_rec(R, Q, na, nbs, depth + 1);
+  om_free(Q);
+  om_mat* Z11e = om_embed(Z11, nbs, na);
+  om_free(Z11);
+  om_mat* T = om_gemm(Z00e, 0, Rm, 0, 1.0, o->tau);       /* Z00 R */
+  om_mat* Z01 = om_gemm(T, 0, Z11e, 0, -1.0, o->tau);     /* Z01 = -(Z00 R) Z11 */
+  om_free(T); om_free(Rm);
+  om_mat* Zu = om_add(1.0, Z00e, 1.0, Z01, 0.0);
+  om_mat* Z = om_add(1.0, Zu, 1.0, Z11e, 0.0);
+  om_free(Z00e); om_free(Z01); om_free(Zu); om_free(Z11e);
+  return Z;
+}
+
+om_mat* om_rinch(const om_mat* S_in, const om_opts* o, om_report* rep) {
+  memset(rep, 0, sizeof(*rep));
+  rep_reset_counters();
+  om_mat* S = om_truncate(S_in, o->tau);
+  rinch_ctx R = {o, 0, 0};
+  om_mat* Z = rinch_rec(&R, S, 0, S->nb, 0);
+  Z->n = S_in->n;
+  om_free(S);
+  rep->levels = R.depth_max;
+  rep->status = R.status;
+  rep->products = g_products;
+  rep->block_pairs = g_pairs;
+  return Z;
+}
+
 double om_resid(const om_mat* S, const om_mat* Z) {
   om_mat* X = om_gemm(S, 0, Z, 0, 1.0, 0.0);
   om_mat* Y = om_gemm(Z, 1, X, 0, 1.0, 0.0);
