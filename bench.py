@@ -73,6 +73,10 @@ WORKLOADS = {
     # recording run + reverse pass (dL/dS), FP64
     "adjoint-chain-n16384-bs32": dict(geom="chain", n=16384, bs=32, tau=1e-10, target=0.0, method="adjoint", m=2,
                                       seed=0, leaf=512, prec="fp64", compare=(), sample_n=None, K=6, fseed=5),
+    # the 16,384-row chain through recursive inverse Cholesky (Algorithm 1;
+    # 512-row leaves, 5 levels), FP64
+    "rinch-chain-n16384-bs32": dict(geom="chain", n=16384, bs=32, tau=1e-10, target=1e-8, method="rinch", m=2,
+                                    seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
     # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
@@ -205,6 +209,8 @@ def oracle_factorize(S, w):
     import oracle
     if w["method"] == "refine":
         return oracle.irsi(S, m=w["m"], tau=w["tau"], target=w["target"])
+    if w["method"] == "rinch":
+        return oracle.rinch(S, tau=w["tau"], leaf_size=w["leaf"])
     return oracle.lif(S, m=w["m"], tau=w["tau"], target=w["target"], leaf_size=w["leaf"])
 
 
@@ -540,7 +546,11 @@ def main():
         return
     S_h = make_input(w)
     S = ifac.upload(ctx, S_h)
-    factor = ifac.inv_factor_refine if w["method"] == "refine" else ifac.inv_factor_localized
+    if w["method"] == "rinch":
+        def factor(ctx_, S_, tau, target, o_):
+            return ifac.inv_factor_rinch(ctx_, S_, tau, o_)
+    else:
+        factor = ifac.inv_factor_refine if w["method"] == "refine" else ifac.inv_factor_localized
     o = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[w["prec"]], profile=True, max_iter=100)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 

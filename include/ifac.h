@@ -299,6 +299,21 @@ int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double targe
 int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
                          const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
 
+/* Recursive inverse Cholesky (Algorithm 1, left-looking, two blocks per
+ * dimension): S = [S00 S01; S01^T S11] split at the block-aligned midpoint
+ * while the range has more than opts->leaf_size rows,
+ *   Z00 = rinch(S00), R = Z00^T S01, Q = -R^T R + S11, Z11 = rinch(Q),
+ *   Z01 = -(Z00 R) Z11, Z10 = 0,
+ * and at the lowest level the dense leaf routine Z = L^-T (S = L L^T).  S is
+ * truncated at tau first; every product and every leaf factor is truncated
+ * (Section 5).  Without truncation Z is the inverse Cholesky factor (block
+ * upper triangular, Z^T S Z = I).  opts: leaf_size; prec IFAC_FP64 or
+ * IFAC_FP64_SPLIT (bs = 64).  rep (may be NULL): levels = recursion depth,
+ * products, block_pairs, nnzb_Z, flops.  IFAC_ERR_NOT_SPD if a leaf (S00 or
+ * a Schur complement Q) is not positive definite. */
+int inv_factor_rinch(ifac_ctx* ctx, const ifac_bsr* S, double tau, const ifac_opts* opts, ifac_bsr* Z,
+                     ifac_report* rep);
+
 /* Refinement from a scaled identity (as inv_factor_refine, Section 2.2) of
  * `count` independent matrices S[0..count-1] in one launch sequence: the
  * members sit on the diagonal of one block-diagonal matrix, so every block

@@ -428,6 +428,22 @@ int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double ta
   });
 }
 
+int inv_factor_rinch(ifac_ctx* ctx, const ifac_bsr* S, double tau, const ifac_opts* opts, ifac_bsr* Z,
+                     ifac_report* rep) {
+  if (Z) *Z = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(S, "S");
+    check_opts(opts, false);
+    if (!Z) fail(IFAC_ERR_INVALID, "Z is NULL");
+    if (opts->leaf_size < 1) fail(IFAC_ERR_INVALID, "leaf_size must be >= 1");
+    if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
+    bool split = false;
+    const ifac_opts o = split_opts(opts, S->bs, &split);
+    SplitScope scope(ctx, split);
+    return rinch(ctx, *S, tau, o, Z, rep);
+  });
+}
+
 int inv_factor_refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, double target,
                               const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep) {
   if (Z && count > 0)

@@ -36,7 +36,7 @@ static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int p
   return P;
 }
 
-static void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
+void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
   ctx->products = 0;
   ctx->pairs = 0;
   ctx->launches = 0;
@@ -58,7 +58,7 @@ int delta_prec_of(const ifac_opts& o, int bs) {
   return (o.delta_prec == IFAC_FP64_SPLIT && bs == 64) ? IFAC_FP64_SPLIT : IFAC_FP64;
 }
 
-static void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
+void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   check_device_error(ctx);
   read_device_counters(ctx, &ctx->pairs_fp64, &ctx->pairs_tc, &ctx->pairs_split);
   ctx->pairs = ctx->pairs_fp64 + ctx->pairs_tc + ctx->pairs_split;
@@ -286,9 +286,9 @@ __global__ void k_identity_fill(double* __restrict__ buf, int np, int count) {
 __global__ void k_leaf_gather(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                               const double* __restrict__ val, int nb, int bs, const int32_t* __restrict__ leaf_of,
                               const int32_t* __restrict__ leaf_b0, int np, double* __restrict__ buf) {
-  // one CTA per block row
+  // one CTA per block row; rows outside every leaf (leaf_of < 0) are skipped
   const int I = blockIdx.x;
-  if (I >= nb) return;
+  if (I >= nb || leaf_of[I] < 0) return;
   const int k = leaf_of[I], b0 = leaf_b0[k];
   double* dst = buf + (size_t)k * np * np;
   for (int p = rp[I]; p < rp[I + 1]; ++p) {
@@ -308,7 +308,7 @@ __global__ void k_leaf_scatter(const int32_t* __restrict__ rp, const int32_t* __
                                const double* __restrict__ buf, double* __restrict__ val, double* __restrict__ norms) {
   __shared__ double red[8];
   const int I = blockIdx.x;
-  if (I >= nb) return;
+  if (I >= nb || leaf_of[I] < 0) return;
   const int k = leaf_of[I], b0 = leaf_b0[k];
   const double* src = buf + (size_t)k * np * np;
   for (int p = rp[I]; p < rp[I + 1]; ++p) {
@@ -358,11 +358,12 @@ static Buf<T> upload_vec(ifac_ctx* ctx, const std::vector<T>& h) {
   return d;
 }
 
-// all leaves: Z_leaf = L^-T from the batched leaf routine, then truncation
+// all leaves: Z_leaf = L^-T from the batched leaf routine, then truncation;
+// block rows outside every leaf get no blocks
 static Mat leaf_factors(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<Node>& leaves, double tau) {
   const int nb = S.nb, bs = S.bs, count = (int)leaves.size();
   int nl_max = 0;
-  std::vector<int32_t> leaf_of(nb), leaf_b0(count);
+  std::vector<int32_t> leaf_of(nb, -1), leaf_b0(count);
   for (int k = 0; k < count; ++k) {
     nl_max = std::max(nl_max, (leaves[k].b1 - leaves[k].b0) * bs);
     leaf_b0[k] = leaves[k].b0;
@@ -388,8 +389,10 @@ static Mat leaf_factors(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<Node
   // upper-triangular block pattern of every leaf
   std::vector<int32_t> rp(nb + 1, 0), ci;
   for (int I = 0; I < nb; ++I) {
-    const Node& L = leaves[leaf_of[I]];
-    for (int J = I; J < L.b1; ++J) ci.push_back(J);
+    if (leaf_of[I] >= 0) {
+      const Node& L = leaves[leaf_of[I]];
+      for (int J = I; J < L.b1; ++J) ci.push_back(J);
+    }
     rp[I + 1] = (int32_t)ci.size();
   }
   Mat Z = mat_alloc(ctx, S.n, bs, nb, (int64_t)ci.size());
@@ -400,6 +403,13 @@ static Mat leaf_factors(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<Node
   IFAC_CK_LAUNCH();
   IFAC_CK(cudaStreamSynchronize(ctx->stream));  // host vectors rp/ci go out of scope
   return compact(ctx, std::move(Z), nullptr, tau);
+}
+
+Mat leaf_factors_ranges(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<std::pair<int, int>>& ranges,
+                        double tau) {
+  std::vector<Node> leaves;
+  for (const auto& r : ranges) leaves.push_back({r.first, r.second, r.second, 0, true});
+  return leaf_factors(ctx, S, leaves, tau);
 }
 
 Mat filter_rows_active(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* seg, const uint8_t* active) {

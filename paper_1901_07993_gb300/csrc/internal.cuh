@@ -158,6 +158,14 @@ double fro_host(ifac_ctx* ctx, const ifac_bsr& A);
 double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
 // sum_j |A_ij| for every scalar row i (nb * bs values)
 int delta_prec_of(const ifac_opts& o, int bs);
+// driver report: counters reset at entry, filled (with the device counters) at exit
+void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o);
+void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z);
+// Z_leaf = L^-T (upper triangular blocks, truncated) of the principal
+// sub-matrices [first, second) of S in one batched leaf launch; other rows empty
+Mat leaf_factors_ranges(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<std::pair<int, int>>& ranges,
+                        double tau);
+int rinch(ifac_ctx* ctx, const ifac_bsr& S, double tau, const ifac_opts& o, ifac_bsr* Zout, ifac_report* rep);
 void gershgorin_rows(ifac_ctx* ctx, const ifac_bsr& A, double* rs);
 Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 

@@ -31,7 +31,8 @@ EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", 
            "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_add",
            "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
            "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
-           "inv_factor_refine_adjoint", "inv_factor_refine_batched", "ifac_set_split_slices")
+           "inv_factor_refine_adjoint", "inv_factor_refine_batched", "ifac_set_split_slices",
+           "inv_factor_rinch")
 
 
 class IfacError(RuntimeError):
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
         "leaf_invchol_batched": ([p, i32, i32, p, p, p], i32),
         "inv_factor_refine": ([p, PB, d, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
         "inv_factor_localized": ([p, PB, d, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
+        "inv_factor_rinch": ([p, PB, d, ctypes.POINTER(_Opts), PB, ctypes.POINTER(_Report)], i32),
         "inv_factor_resid": ([p, PB, PB, ctypes.POINTER(d)], i32),
         "leaf_invchol_batched_noalloc": ([p, i32, i32, p, p, p], i32),
         "inv_factor_refine_adjoint": ([p, PB, PB, i32, d, ctypes.POINTER(d), PB], i32),
@@ -322,6 +324,15 @@ def inv_factor_localized(ctx: Context, S: DeviceBSR, tau: float, target: float, 
     rep = _Report()
     rc = ctx.check(ctx.lib.inv_factor_localized(ctx.h, S.ptr(), tau, target, ctypes.byref(o or opts()),
                                                 ctypes.byref(Z), ctypes.byref(rep)))
+    return DeviceBSR(ctx, Z), _report(rep, rc)
+
+
+def inv_factor_rinch(ctx: Context, S: DeviceBSR, tau: float, o: _Opts | None = None):
+    """Recursive inverse Cholesky (Algorithm 1); opts.leaf_size sets the leaf level."""
+    Z = _Bsr()
+    rep = _Report()
+    rc = ctx.check(ctx.lib.inv_factor_rinch(ctx.h, S.ptr(), tau, ctypes.byref(o or opts()), ctypes.byref(Z),
+                                            ctypes.byref(rep)))
     return DeviceBSR(ctx, Z), _report(rep, rc)
 
 
