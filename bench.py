@@ -74,9 +74,15 @@ WORKLOADS = {
     "adjoint-chain-n16384-bs32": dict(geom="chain", n=16384, bs=32, tau=1e-10, target=0.0, method="adjoint", m=2,
                                       seed=0, leaf=512, prec="fp64", compare=(), sample_n=None, K=6, fseed=5),
     # the 16,384-row chain through recursive inverse Cholesky (Algorithm 1;
-    # 512-row leaves, 5 levels), FP64
+    # 128-row leaves, 7 levels: the fastest of 64/128/256/512 on the box), FP64
     "rinch-chain-n16384-bs32": dict(geom="chain", n=16384, bs=32, tau=1e-10, target=1e-8, method="rinch", m=2,
-                                    seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
+                                    seed=0, leaf=128, prec="fp64", compare=(), sample_n=None),
+    # the 4096-row 3D cluster through localized inverse factorization that
+    # switches to recursive inverse Cholesky at 2048 rows (the paper switches
+    # below 16384), 128-row leaves, FP64
+    "lif-rinch-cluster-n4096-bs32": dict(geom="cluster", n=4096, bs=32, tau=1e-10, target=1e-10,
+                                         method="localized", m=2, seed=0, leaf=128, prec="fp64", compare=(),
+                                         sample_n=None, rinch_rows=2048),
     # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
@@ -211,7 +217,8 @@ def oracle_factorize(S, w):
         return oracle.irsi(S, m=w["m"], tau=w["tau"], target=w["target"])
     if w["method"] == "rinch":
         return oracle.rinch(S, tau=w["tau"], leaf_size=w["leaf"])
-    return oracle.lif(S, m=w["m"], tau=w["tau"], target=w["target"], leaf_size=w["leaf"])
+    return oracle.lif(S, m=w["m"], tau=w["tau"], target=w["target"], leaf_size=w["leaf"],
+                      rinch_rows=w.get("rinch_rows", 0))
 
 
 def cpu_sample(w):
@@ -551,7 +558,8 @@ def main():
             return ifac.inv_factor_rinch(ctx_, S_, tau, o_)
     else:
         factor = ifac.inv_factor_refine if w["method"] == "refine" else ifac.inv_factor_localized
-    o = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[w["prec"]], profile=True, max_iter=100)
+    o = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[w["prec"]], profile=True, max_iter=100,
+                  rinch_rows=w.get("rinch_rows", 0))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
@@ -595,7 +603,8 @@ def main():
         return t.numpy()
 
     S_pin = type(S_h)(S_h.n, S_h.bs, pinned(S_h.row_ptr), pinned(S_h.col_idx), pinned(S_h.val))
-    o_e2e = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[w["prec"]], max_iter=100)
+    o_e2e = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[w["prec"]], max_iter=100,
+                      rinch_rows=w.get("rinch_rows", 0))
     z_bufs = None
     e2e_ms = []
     barrier(world)

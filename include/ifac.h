@@ -92,7 +92,7 @@ typedef struct ifac_ctx ifac_ctx;
 
 /* Options of the factorization drivers.  ifac_opts_default fills:
  * m = 2, max_iter = 50, fixed_iters = 0, c_rule = 0, leaf_size = 512,
- * prec = IFAC_FP64, profile = 0, delta_prec = IFAC_FP64_SPLIT. */
+ * prec = IFAC_FP64, profile = 0, delta_prec = IFAC_FP64_SPLIT, rinch_rows = 0. */
 typedef struct {
   int m;           /* refinement order: Z_{i+1} = Z_i sum_{k=0}^{m} b_k delta_i^k,
                       b_0 = 1, b_k = (2k-1)/(2k) b_{k-1} (Eq. 2.1); 1..8 */
@@ -116,6 +116,11 @@ typedef struct {
                       prec TF32/BF16: the FP64 phase; batched: the final
                       residual): IFAC_FP64 (FP64 pipe) or IFAC_FP64_SPLIT
                       (tensor cores; used when bs = 64, else IFAC_FP64) */
+  int rinch_rows;  /* inv_factor_localized: sub-problems with at most this
+                      many rows (when above leaf_size) are factorized by
+                      recursive inverse Cholesky (Algorithm 1, leaf_size
+                      leaves) instead of being split further -- the paper
+                      switches to RINCH below 16384 rows; 0 = off */
 } ifac_opts;
 
 typedef struct {

@@ -55,7 +55,7 @@ def build(force: bool = False) -> str:
 class _Opts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("tau", ctypes.c_double), ("target", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("fixed_iters", ctypes.c_int),
-                ("c_rule", ctypes.c_int), ("leaf_size", ctypes.c_int)]
+                ("c_rule", ctypes.c_int), ("leaf_size", ctypes.c_int), ("rinch_rows", ctypes.c_int)]
 
 
 class _Rep(ctypes.Structure):
@@ -228,8 +228,8 @@ class Report:
     status: int = 0
 
 
-def _opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size) -> _Opts:
-    return _Opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size)
+def _opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size, rinch_rows=0) -> _Opts:
+    return _Opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size, rinch_rows)
 
 
 def _report(r: _Rep) -> Report:
@@ -247,9 +247,11 @@ def irsi(S, m: int = 2, tau: float = 1e-10, target: float = 0.0, max_iter: int =
     return _from_c(z, S.bs), _report(r)
 
 
-def lif(S, m: int = 2, tau: float = 1e-10, target: float = 0.0, max_iter: int = 50, leaf_size: int = 512):
-    """Localized inverse factorization (Algorithm 2). Returns (Z, Report)."""
-    o = _opts(m, tau, target, max_iter, 0, 0, leaf_size)
+def lif(S, m: int = 2, tau: float = 1e-10, target: float = 0.0, max_iter: int = 50, leaf_size: int = 512,
+        rinch_rows: int = 0):
+    """Localized inverse factorization (Algorithm 2); sub-problems with at most
+    rinch_rows rows (when above leaf_size) are factorized by RINCH. Returns (Z, Report)."""
+    o = _opts(m, tau, target, max_iter, 0, 0, leaf_size, rinch_rows)
     r = _Rep()
     with _Held(S) as (h,):
         z = _load().om_lif(h, ctypes.byref(o), ctypes.byref(r))

@@ -53,7 +53,9 @@ typedef struct {
   int max_iter;     /* hard cap on sweeps per refinement */
   int fixed_iters;  /* IRSI only: if > 0, run exactly this many corrections */
   int c_rule;       /* IRSI start: 0 -> c = 1/sqrt(beta), 1 -> c = sqrt(2/beta) */
-  int leaf_size;    /* LIF: recurse while a sub-problem has more rows */
+  int leaf_size;    /* LIF, RINCH: recurse while a sub-problem has more rows */
+  int rinch_rows;   /* LIF: sub-problems with at most this many rows (> leaf_size)
+                       are factorized by RINCH instead of split further; 0 = off */
 } om_opts;
 
 enum { OM_STOP_RULE = 1, OM_STOP_TARGET = 2, OM_STOP_MAXITER = 3, OM_STOP_FIXED = 4 };
@@ -526,6 +528,13 @@ static om_mat* om_embed(const om_mat* A, int nbs, int off) {
 
 typedef struct {
   const om_opts* o;
+  int depth_max;
+  int status;
+} rinch_ctx;
+static om_mat* rinch_rec(rinch_ctx* R, const om_mat* S, int b0, int b1, int depth);
+
+typedef struct {
+  const om_opts* o;
   om_report* rep;
   int depth_max;
   int status;
@@ -579,6 +588,12 @@ static om_mat* lif_rec(lif_ctx* L, const om_mat* S, int b0, int b1, int depth) {
   size_t bsz = (size_t)bs * bs;
   if (depth > L->depth_max) L->depth_max = depth;
   if ((int64_t)nbs * bs <= o->leaf_size || nbs == 1) return leaf_factor(S, b0, b1, o->tau, &L->status);
+  if ((int64_t)nbs * bs <= o->rinch_rows) {  /* the switch to RINCH for small sub-problems */
+    rinch_ctx R = {o, 0, 0};
+    om_mat* Z = rinch_rec(&R, S, b0, b1, 0);
+    if (R.status) L->status = R.status;
+    return Z;
+  }
   int bm = b0 + nbs / 2;
   om_mat* ZA = lif_rec(L, S, b0, bm, depth + 1);
   om_mat* ZC = lif_rec(L, S, bm, b1, depth + 1);
@@ -632,12 +647,6 @@ om_mat* om_lif(const om_mat* S_in, const om_opts* o, om_report* rep) {
 /* ------------------------------------------------------------------ */
 /* RINCH: recursive inverse Cholesky (Algorithm 1)                      */
 /* ------------------------------------------------------------------ */
-
-typedef struct {
-  const om_opts* o;
-  int depth_max;
-  int status;
-} rinch_ctx;
 
 /* Inverse factor of the principal sub-matrix on block range [b0, b1) of S,
  * in the sub-matrix's own index space.  With S = [S00 S01; S01^T S11] split

@@ -184,6 +184,7 @@ void ifac_opts_default(ifac_opts* o) {
   o->prec = IFAC_FP64;
   o->profile = 0;
   o->delta_prec = IFAC_FP64_SPLIT;
+  o->rinch_rows = 0;
 }
 
 int ifac_create(ifac_ctx** out, void* stream, const ifac_allocator* alloc) {
@@ -371,6 +372,7 @@ static void check_opts(const ifac_opts* o, bool mixed_ok) {
   if (o->prec != IFAC_FP64 && o->prec != IFAC_FP64_SPLIT &&
       !(mixed_ok && (o->prec == IFAC_TF32 || o->prec == IFAC_BF16)))
     fail(IFAC_ERR_UNSUPPORTED, "precision not available for this call");
+  if (o->rinch_rows < 0) fail(IFAC_ERR_INVALID, "rinch_rows must be >= 0");
   if (o->delta_prec != IFAC_FP64 && o->delta_prec != IFAC_FP64_SPLIT)
     fail(IFAC_ERR_INVALID, "delta_prec must be IFAC_FP64 or IFAC_FP64_SPLIT");
 }

@@ -442,14 +442,25 @@ int lif(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, const if
   Mat S = truncate(ctx, S_in, tau);
   const int nb = S.m.nb, bs = S.m.bs;
   std::vector<Node> tree;
-  build_tree(0, nb, 0, bs, o.leaf_size, tree);
+  // sub-problems up to rinch_rows rows (when above leaf_size) are the tree's
+  // leaves and are factorized by recursive inverse Cholesky (Algorithm 1)
+  const bool to_rinch = o.rinch_rows > o.leaf_size;
+  build_tree(0, nb, 0, bs, to_rinch ? o.rinch_rows : o.leaf_size, tree);
   int max_depth = 0;
   std::vector<Node> leaves;
   for (const Node& n : tree) {
     max_depth = std::max(max_depth, n.depth);
     if (n.leaf) leaves.push_back(n);
   }
-  Mat Z = leaf_factors(ctx, S.m, leaves, tau);
+  Mat Z;
+  if (to_rinch) {
+    std::vector<std::pair<int, int>> ranges;
+    for (const Node& n : leaves) ranges.push_back({n.b0, n.b1});
+    int rl = 0;
+    Z = rinch_ranges(ctx, S.m, ranges, tau, o.leaf_size, &rl);
+  } else {
+    Z = leaf_factors(ctx, S.m, leaves, tau);
+  }
   int total_sweeps = 0, top_stop = 0;
   bool any_maxiter = false;
   double top_e = 0.0;

@@ -166,6 +166,9 @@ void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z);
 Mat leaf_factors_ranges(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<std::pair<int, int>>& ranges,
                         double tau);
 int rinch(ifac_ctx* ctx, const ifac_bsr& S, double tau, const ifac_opts& o, ifac_bsr* Zout, ifac_report* rep);
+// recursive inverse Cholesky of the disjoint ranges [first, second) of S together
+Mat rinch_ranges(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<std::pair<int, int>>& ranges, double tau,
+                 int leaf_size, int* levels);
 void gershgorin_rows(ifac_ctx* ctx, const ifac_bsr& A, double* rs);
 Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 

@@ -104,6 +104,13 @@ Mat rinch_rec(ifac_ctx* ctx, const ifac_bsr& S, const Ranges& ranges, double tau
 
 }  // namespace
 
+Mat rinch_ranges(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<std::pair<int, int>>& ranges, double tau,
+                 int leaf_size, int* levels) {
+  Ranges r;
+  r.r = ranges;
+  return rinch_rec(ctx, S, r, tau, leaf_size, 0, levels);
+}
+
 int rinch(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, const ifac_opts& o, ifac_bsr* Zout, ifac_report* rep) {
   report_init(ctx, rep, o);
   Mat S = truncate(ctx, S_in, tau);

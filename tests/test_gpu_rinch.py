@@ -79,3 +79,16 @@ def test_rinch_not_spd(ctx):
     with pytest.raises(ifac.IfacError) as ei:
         ifac.inv_factor_rinch(ctx, ifac.upload(ctx, bad), 0.0, ifac.opts(leaf_size=128))
     assert ei.value.code == ifac.ERR_NOT_SPD
+
+
+@pytest.mark.parametrize("kind,n,bs,leaf,rrows", [("chain", 4096, 32, 128, 1024), ("cluster", 1024, 32, 64, 256)])
+def test_lif_switch_to_rinch_matches_oracle(ctx, kind, n, bs, leaf, rrows):
+    """LIF whose sub-problems of at most rrows rows are factorized by RINCH."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(n, bs, seed=2) if kind == "chain" else synth.cluster_overlap(n, bs, seed=2)
+    Z_ref, rep_ref = oracle.lif(S, tau=1e-10, target=1e-10, leaf_size=leaf, rinch_rows=rrows)
+    Z, rep = ifac.inv_factor_localized(ctx, ifac.upload(ctx, S), 1e-10, 1e-10,
+                                       ifac.opts(leaf_size=leaf, rinch_rows=rrows))
+    assert rep.levels == rep_ref.levels and rep.sweeps == rep_ref.sweeps
+    assert rep.block_pairs == rep_ref.block_pairs
+    assert _rel(Z.download(), Z_ref) <= 1e-10
