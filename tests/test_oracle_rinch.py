@@ -72,11 +72,11 @@ def test_lif_switch_to_rinch_equals_larger_leaves(oracle_mod):
     """Without truncation RINCH on a range returns that range's inverse
     Cholesky factor, which is what the dense leaf routine returns; so LIF
     switching to RINCH at R rows equals LIF with R-row dense leaves."""
-    S = synth.cluster_overlap(1024, 32, seed=8)
-    Za, ra = oracle_mod.lif(S, tau=0.0, target=1e-12, leaf_size=64, rinch_rows=256)
-    Zb, rb = oracle_mod.lif(S, tau=0.0, target=1e-12, leaf_size=256)
+    S = synth.cluster_overlap(512, 16, seed=8)
+    Za, ra = oracle_mod.lif(S, tau=0.0, target=1e-12, leaf_size=32, rinch_rows=128)
+    Zb, rb = oracle_mod.lif(S, tau=0.0, target=1e-12, leaf_size=128)
     assert ra.levels == rb.levels
     za, zb = Za.to_dense(), Zb.to_dense()
     assert np.abs(za - zb).max() <= 1e-10 * np.abs(zb).max()
-    r_more = oracle_mod.lif(S, tau=0.0, target=1e-12, leaf_size=64)[1]
+    r_more = oracle_mod.lif(S, tau=0.0, target=1e-12, leaf_size=32)[1]
     assert r_more.levels > ra.levels
