@@ -92,7 +92,8 @@ typedef struct ifac_ctx ifac_ctx;
 
 /* Options of the factorization drivers.  ifac_opts_default fills:
  * m = 2, max_iter = 50, fixed_iters = 0, c_rule = 0, leaf_size = 512,
- * prec = IFAC_FP64, profile = 0, delta_prec = IFAC_FP64_SPLIT, rinch_rows = 0. */
+ * prec = IFAC_FP64, profile = 0, delta_prec = IFAC_FP64_SPLIT, rinch_rows = 0,
+ * local_delta = 0. */
 typedef struct {
   int m;           /* refinement order: Z_{i+1} = Z_i sum_{k=0}^{m} b_k delta_i^k,
                       b_0 = 1, b_k = (2k-1)/(2k) b_{k-1} (Eq. 2.1); 1..8 */
@@ -121,6 +122,11 @@ typedef struct {
                       recursive inverse Cholesky (Algorithm 1, leaf_size
                       leaves) instead of being split further -- the paper
                       switches to RINCH below 16384 rows; 0 = off */
+  int local_delta; /* inv_factor_refine (FP64): 0 evaluates delta = I - Z^T S Z
+                      directly every sweep; 1 evaluates delta_0 directly and
+                      then updates it locally by Eq. (2.2),
+                      delta' = delta - Z'^T (S M) - (S M)^T Z, as the paper's
+                      runs do for all methods */
 } ifac_opts;
 
 typedef struct {

@@ -55,7 +55,8 @@ def build(force: bool = False) -> str:
 class _Opts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("tau", ctypes.c_double), ("target", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("fixed_iters", ctypes.c_int),
-                ("c_rule", ctypes.c_int), ("leaf_size", ctypes.c_int), ("rinch_rows", ctypes.c_int)]
+                ("c_rule", ctypes.c_int), ("leaf_size", ctypes.c_int), ("rinch_rows", ctypes.c_int),
+                ("local_delta", ctypes.c_int)]
 
 
 class _Rep(ctypes.Structure):
@@ -228,8 +229,8 @@ class Report:
     status: int = 0
 
 
-def _opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size, rinch_rows=0) -> _Opts:
-    return _Opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size, rinch_rows)
+def _opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size, rinch_rows=0, local_delta=0) -> _Opts:
+    return _Opts(m, tau, target, max_iter, fixed_iters, c_rule, leaf_size, rinch_rows, local_delta)
 
 
 def _report(r: _Rep) -> Report:
@@ -238,9 +239,10 @@ def _report(r: _Rep) -> Report:
 
 
 def irsi(S, m: int = 2, tau: float = 1e-10, target: float = 0.0, max_iter: int = 50,
-         fixed_iters: int = 0, c_rule: int = 0):
-    """Iterative refinement from Z_0 = c I (Eq. 2.1, direct delta). Returns (Z, Report)."""
-    o = _opts(m, tau, target, max_iter, fixed_iters, c_rule, 0)
+         fixed_iters: int = 0, c_rule: int = 0, local_delta: bool = False):
+    """Iterative refinement from Z_0 = c I (Eq. 2.1): direct delta each sweep,
+    or the local update of Eq. (2.2) after a direct delta_0. Returns (Z, Report)."""
+    o = _opts(m, tau, target, max_iter, fixed_iters, c_rule, 0, 0, int(local_delta))
     r = _Rep()
     with _Held(S) as (h,):
         z = _load().om_irsi(h, ctypes.byref(o), ctypes.byref(r))

@@ -18,8 +18,10 @@
  *  - om_gershgorin: beta = max_i sum_j |S_ij| (Section 2.2, Eq. for c with
  *    the Gershgorin estimate of the spectral radius).
  *  - om_irsi: iterative refinement from a scaled identity, Eq. (2.1) with
- *    delta_i = I - Z_i^T S Z_i evaluated directly each sweep, Z_0 = c I, and
- *    the automatic stop ||delta_{i+1}||_F > ||delta_i||_F^{m+1} (Section 2.2).
+ *    delta_i = I - Z_i^T S Z_i evaluated directly each sweep (or, with
+ *    local_delta, updated by Eq. (2.2) after a direct delta_0), Z_0 = c I,
+ *    and the automatic stop ||delta_{i+1}||_F > ||delta_i||_F^{m+1}
+ *    (Section 2.2).
  *  - om_lif: localized inverse factorization, Algorithm 2, with the localized
  *    refinement of Eq. (2.2) and the stop rule as in Algorithm 4.
  *  - om_invchol_dense: the leaf routine "factorize S^-1 = Z Z^T" of
@@ -56,6 +58,8 @@ typedef struct {
   int leaf_size;    /* LIF, RINCH: recurse while a sub-problem has more rows */
   int rinch_rows;   /* LIF: sub-problems with at most this many rows (> leaf_size)
                        are factorized by RINCH instead of split further; 0 = off */
+  int local_delta;  /* IRSI: 0 direct delta each sweep, 1 the local update of
+                       Eq. (2.2) after a direct delta_0 */
 } om_opts;
 
 enum { OM_STOP_RULE = 1, OM_STOP_TARGET = 2, OM_STOP_MAXITER = 3, OM_STOP_FIXED = 4 };
@@ -394,6 +398,15 @@ static void rep_reset_counters(void) { g_products = 0; g_pairs = 0; }
 /* IRSI: iterative refinement from a scaled identity                    */
 /* ------------------------------------------------------------------ */
 
+/* delta = I - Z^T (S Z), both products truncated */
+static om_mat* irsi_direct_delta(const om_mat* S, const om_mat* Z, double tau) {
+  om_mat* X = om_gemm(S, 0, Z, 0, 1.0, tau);        /* S Z */
+  om_mat* Y = om_gemm(Z, 1, X, 0, 1.0, tau);        /* Z^T (S Z) */
+  om_mat* delta = om_add(-1.0, Y, 0.0, NULL, 1.0);  /* I - Z^T S Z */
+  om_free(X); om_free(Y);
+  return delta;
+}
+
 om_mat* om_irsi(const om_mat* S_in, const om_opts* o, om_report* rep) {
   memset(rep, 0, sizeof(*rep));
   rep_reset_counters();
@@ -403,11 +416,8 @@ om_mat* om_irsi(const om_mat* S_in, const om_opts* o, om_report* rep) {
   double c = (o->c_rule == 1) ? sqrt(2.0 / beta) : 1.0 / sqrt(beta);
   om_mat* Z = om_scaled_identity(S->n, S->bs, S->nb, c);
   double e_prev = INFINITY;
+  om_mat* delta = irsi_direct_delta(S, Z, o->tau);
   for (int it = 0;; ++it) {
-    om_mat* X = om_gemm(S, 0, Z, 0, 1.0, o->tau);       /* S Z */
-    om_mat* Y = om_gemm(Z, 1, X, 0, 1.0, o->tau);       /* Z^T (S Z) */
-    om_mat* delta = om_add(-1.0, Y, 0.0, NULL, 1.0);    /* I - Z^T S Z */
-    om_free(X); om_free(Y);
     double e = om_fro(delta);
     if (rep->n_delta < 64) rep->delta_fro[rep->n_delta++] = e;
     int stop = 0;
@@ -429,8 +439,23 @@ om_mat* om_irsi(const om_mat* S_in, const om_opts* o, om_report* rep) {
     om_mat* P = poly_P(delta, o->m, o->tau);
     om_mat* M = om_gemm(Z, 0, P, 0, 1.0, o->tau);       /* M = Z sum b_k delta^k */
     om_mat* Zn = om_add(1.0, Z, 1.0, M, 0.0);           /* Z + M */
-    om_free(P); om_free(M); om_free(delta); om_free(Z);
+    om_free(P);
+    if (o->local_delta) {
+      /* Eq. (2.2): delta' = delta - Z_{i+1}^T (S M) - (M^T S) Z_i, M^T S = (S M)^T */
+      om_mat* T = om_gemm(S, 0, M, 0, 1.0, o->tau);
+      om_mat* U = om_gemm(Zn, 1, T, 0, 1.0, o->tau);
+      om_mat* V = om_gemm(T, 1, Z, 0, 1.0, o->tau);
+      om_mat* d1 = om_add(1.0, delta, -1.0, U, 0.0);
+      om_mat* dn = om_add(1.0, d1, -1.0, V, 0.0);
+      om_free(T); om_free(U); om_free(V); om_free(d1); om_free(delta);
+      delta = dn;
+    }
+    om_free(M); om_free(Z);
     Z = Zn;
+    if (!o->local_delta) {
+      om_free(delta);
+      delta = irsi_direct_delta(S, Z, o->tau);
+    }
     e_prev = e;
   }
   om_free(S);

@@ -185,6 +185,7 @@ void ifac_opts_default(ifac_opts* o) {
   o->profile = 0;
   o->delta_prec = IFAC_FP64_SPLIT;
   o->rinch_rows = 0;
+  o->local_delta = 0;
 }
 
 int ifac_create(ifac_ctx** out, void* stream, const ifac_allocator* alloc) {

@@ -97,12 +97,14 @@ int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, 
   double e_prev = INFINITY;
   int stop = 0, it = 0;
   double e = 0.0;
-  for (it = 0;; ++it) {
-    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau);   // S Z
-    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau);    // Z^T (S Z)
+  auto direct_delta = [&](const ifac_bsr& Zc) {
+    Mat X = gemm(ctx, S.m, false, Zc, false, 1.0, tau);    // S Z
+    Mat Y = gemm(ctx, Zc, true, X.m, false, 1.0, tau);     // Z^T (S Z)
     X.reset();
-    Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);        // I - Z^T S Z
-    Y.reset();
+    return add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);         // I - Z^T S Z
+  };
+  Mat D = direct_delta(Z.m);
+  for (it = 0;; ++it) {
     e = fro_host(ctx, D.m);
     if (rep && rep->n_delta < 64) rep->delta_fro[rep->n_delta++] = e;
     if (o.fixed_iters > 0) {
@@ -116,10 +118,21 @@ int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, 
     }
     if (stop) break;
     Mat P = poly_P(ctx, D.m, o.m, tau);
-    D.reset();
     Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau);   // M = Z sum b_k delta^k
     P.reset();
-    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);                // Z + M
+    Mat Zn = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);           // Z + M
+    if (o.local_delta) {
+      // Eq. (2.2): delta' = delta - Z_{i+1}^T (S M) - (M^T S) Z_i, M^T S = (S M)^T
+      Mat T = gemm(ctx, S.m, false, M.m, false, 1.0, tau);
+      Mat U = gemm(ctx, Zn.m, true, T.m, false, 1.0, tau);
+      Mat V = gemm(ctx, T.m, true, Z.m, false, 1.0, tau);
+      T.reset();
+      Mat D1 = add(ctx, 1.0, D.m, -1.0, &U.m, 0.0);
+      D = add(ctx, 1.0, D1.m, -1.0, &V.m, 0.0);
+    }
+    M.reset();
+    Z = std::move(Zn);
+    if (!o.local_delta) D = direct_delta(Z.m);
     e_prev = e;
   }
   if (rep) {

@@ -50,7 +50,8 @@ class _Bsr(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("max_iter", ctypes.c_int), ("fixed_iters", ctypes.c_int),
                 ("c_rule", ctypes.c_int), ("leaf_size", ctypes.c_int), ("prec", ctypes.c_int),
-                ("profile", ctypes.c_int), ("delta_prec", ctypes.c_int), ("rinch_rows", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("delta_prec", ctypes.c_int), ("rinch_rows", ctypes.c_int),
+                ("local_delta", ctypes.c_int)]
 
 
 class _Report(ctypes.Structure):
@@ -245,7 +246,8 @@ def upload(ctx: Context, host) -> DeviceBSR:
 
 
 def opts(m: int = 2, max_iter: int = 50, fixed_iters: int = 0, c_rule: int = 0, leaf_size: int = 512,
-         prec: int = FP64, profile: bool = False, delta_prec: int | None = None, rinch_rows: int = 0) -> _Opts:
+         prec: int = FP64, profile: bool = False, delta_prec: int | None = None, rinch_rows: int = 0,
+         local_delta: bool = False) -> _Opts:
     o = _Opts()
     load().ifac_opts_default(ctypes.byref(o))
     o.m, o.max_iter, o.fixed_iters, o.c_rule, o.leaf_size, o.prec = m, max_iter, fixed_iters, c_rule, leaf_size, prec
@@ -253,6 +255,7 @@ def opts(m: int = 2, max_iter: int = 50, fixed_iters: int = 0, c_rule: int = 0, 
     if delta_prec is not None:
         o.delta_prec = delta_prec
     o.rinch_rows = rinch_rows
+    o.local_delta = int(local_delta)
     return o
 
 

@@ -79,3 +79,17 @@ def test_localized_zero_tau_invariant(ctx):
     dS = ifac.upload(ctx, S)
     Z, rep = ifac.inv_factor_localized(ctx, dS, 0.0, 0.0, ifac.opts(leaf_size=512))
     assert ifac.inv_factor_resid(ctx, dS, Z) < 1e-11
+
+
+@pytest.mark.parametrize("kind,n,bs,tau,m", [("chain", 4096, 32, 1e-10, 2), ("cluster", 1024, 32, 1e-8, 4),
+                                             ("chain", 2000, 32, 1e-5, 4)])
+def test_refine_local_delta_matches_oracle(ctx, kind, n, bs, tau, m):
+    """IRSI with the local delta update of Eq. (2.2), as in the paper's runs."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(n, bs, seed=0) if kind == "chain" else synth.cluster_overlap(n, bs, seed=0)
+    Z_ref, rep_ref = oracle.irsi(S, m=m, tau=tau, target=1e-10, local_delta=True)
+    Z, rep = ifac.inv_factor_refine(ctx, ifac.upload(ctx, S), tau, 1e-10, ifac.opts(m=m, local_delta=True))
+    assert rep.sweeps == rep_ref.sweeps and rep.stop_reason == rep_ref.stop_reason
+    assert np.allclose(rep.delta_fro, rep_ref.delta_fro, rtol=1e-6, atol=1e-12)
+    assert _rel(Z.download(), Z_ref) <= TOL
+    assert rep.products == rep_ref.products and rep.block_pairs == rep_ref.block_pairs

@@ -52,6 +52,23 @@ def test_irsi_matches_eigen_recurrence(oracle_mod, m, c_rule):
         assert np.allclose(rep.delta_fro[: k + 1], deltas, rtol=1e-9, atol=1e-13)
 
 
+@pytest.mark.parametrize("m", [2, 4])
+def test_irsi_local_delta_matches_eigen_recurrence(oracle_mod, m):
+    """Without truncation the local update of Eq. (2.2) is exact, so the
+    locally updated delta norms and iterates follow the same closed form."""
+    S = synth.cluster_overlap(256, 32, seed=3)
+    Sd = S.to_dense()
+    c = 1 / np.sqrt(np.abs(Sd).sum(axis=1).max())
+    for k in (1, 4):
+        Z, rep = oracle_mod.irsi(S, m=m, tau=0.0, fixed_iters=k, local_delta=True)
+        Zc, deltas = _closed_form_irsi(Sd, k, m, c)
+        assert rep.sweeps == k
+        assert np.linalg.norm(Z.to_dense() - Zc) / np.linalg.norm(Zc) < 1e-12
+        assert np.allclose(rep.delta_fro[: k + 1], deltas, rtol=1e-8, atol=1e-12)
+        # local delta costs 3 more products per sweep than the 2 of a direct delta
+        assert rep.products == 2 + k * (1 + (m - 1) + 3)
+
+
 def test_irsi_converges_to_inverse_sqrt(oracle_mod):
     S = synth.chain_overlap(256, 32, seed=4)
     Sd = S.to_dense()
