@@ -139,6 +139,7 @@ void check_device_error(ifac_ctx* ctx) {
   to_host(ctx, &e, ctx->dev_err, sizeof(int));
   if (e) {
     IFAC_CK(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream));
+    if (e == 2) fail(IFAC_ERR_CUDA, "split product: fixed-point overflow (scale bound violated)");
     fail(IFAC_ERR_TIMEOUT, "a bounded device-side wait expired (tensor-core pipeline)");
   }
 }

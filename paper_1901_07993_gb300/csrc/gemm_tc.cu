@@ -264,6 +264,7 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, in
 struct TileArgs {
   const int32_t* tiles;      // [2*t] tile row, [2*t+1] tile column
   const int* ntiles;         // device: number of tiles
+  const int* tile_nk;        // device: K steps of each tile
   int nb;
   int W;                     // 32-bit words per bitmap row
   const uint32_t* bmA;       // pattern bitmap of op(A): bit (I, K)
@@ -296,7 +297,7 @@ struct TileArgs {
   int unit_end[MAX_UNITS];
   int pair_ya[MAX_PAIRS], pair_yb[MAX_PAIRS];
   int unit_sh[MAX_UNITS];
-  int* ovf;  // set to 1 on a fixed-point overflow (the host then redoes the product with a safe scale)
+  int* ovf;  // set to 2 on a fixed-point overflow (reported as an error by the host)
 };
 
 template <int ELT>
@@ -357,18 +358,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = tmem_base_slot;
 
   // number of K steps of tile t: size of the union of its super-tile rows' bitmaps
-  auto tile_nk = [&](int t) {
-    const int S0 = args.tiles[2 * t] * (CL * TM);
-    int nk = 0;
-    for (int w = 0; w < args.W; ++w) {
-      uint32_t word = 0;
-#pragma unroll
-      for (int r = 0; r < CL * TM; ++r)
-        if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
-      nk += __popc(word);
-    }
-    return nk;
-  };
+  auto tile_nk = [&](int t) { return args.tile_nk[t]; };
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
@@ -673,7 +663,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     dv[e].y = fixed_add(dv[e].y, __float2int_rn(v[2 * e + 1]), sh, bad);
                     dst[e * 32] = dv[e];
                   }
-                  if (bad) *args.ovf = 1;
+                  if (bad) *args.ovf = 2;
                 }
               }
             }
@@ -879,6 +869,30 @@ static EncodeTiledFn encoder() {
 
 // 2D view of a low-precision block array: rows = (nblk) * 64, 64 elements per
 // row; boxes of one 128-byte atom x 64 rows, 128-byte swizzle
+// K-step count of every super-tile (size of the union of its rows' bitmaps),
+// one warp per tile; the largest count into *kmax when kmax != NULL
+__global__ void k_tile_ksteps(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles, int rows_per_tile,
+                              const uint32_t* __restrict__ bm, int nb, int W, int* __restrict__ nk_out,
+                              int* __restrict__ kmax) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= *ntiles) return;
+  const int S0 = tiles[2 * t] * rows_per_tile;
+  int nk = 0;
+  for (int w = lane; w < W; w += 32) {
+    uint32_t word = 0;
+    for (int r = 0; r < rows_per_tile; ++r)
+      if (S0 + r < nb) word |= bm[(size_t)(S0 + r) * W + w];
+    nk += __popc(word);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(0xffffffffu, nk, o);
+  if (lane == 0) {
+    nk_out[t] = nk;
+    if (kmax) atomicMax(kmax, nk);
+  }
+}
+
 template <int ELT>
 static CUtensorMap make_map(void* base, int64_t nblk) {
   CUtensorMap m;
@@ -951,6 +965,10 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   IFAC_CK_LAUNCH();
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
+  Buf<int> tnk(ctx, (size_t)ntot);
+  k_tile_ksteps<<<cdiv(ntot * 32, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
+                                                               words_per_row(nb), tnk.p, nullptr);
+  IFAC_CK_LAUNCH();
   static bool attr = false;
   if (!attr) {
     IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
@@ -961,6 +979,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   TileArgs args;
   args.tiles = tiles.p;
   args.ntiles = coff.p + nchunk;  // the scan's total
+  args.tile_nk = tnk.p;
   args.nb = nb;
   args.W = words_per_row(nb);
   args.bmA = bmA.p;
@@ -1035,26 +1054,32 @@ constexpr int SPLIT_BITS = 7;
 // patterns of the FP64 inputs with integer arithmetic only.
 
 // exponent e of sigma = 2^e for every scalar row of a (possibly transposed)
-// row view: max_k |x_rk| = m 2^e with m in [0.5, 1) (e = 0 for an all-zero row)
+// row view: max_k |x_rk| = m 2^e with m in [0.5, 1) (e = 0 for an all-zero row);
+// the largest scaled row 1-norm sum_k |x_rk| / sigma (FP32, magnitudes
+// truncated to 24 bits) into *l1max as FP32 bits
 __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb, int tr,
-                            const double* __restrict__ val, int* __restrict__ eout) {
+                            const double* __restrict__ val, int* __restrict__ eout, unsigned int* __restrict__ l1max) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)nb * BS) return;
   const int I = (int)(w / BS), r = (int)(w % BS);
   unsigned long long m = 0;  // |x| bit patterns order like the magnitudes
+  float l1 = 0.0f;
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
     const double* blk = val + (size_t)(src ? src[q] : q) * BS * BS;
     for (int c = lane; c < BS; c += 32) {
       const unsigned long long u =
           (unsigned long long)__double_as_longlong(tr ? blk[c * BS + r] : blk[r * BS + c]) & 0x7fffffffffffffffull;
       m = u > m ? u : m;
+      const int e32 = (int)(u >> 52) - 896;  // FP32 exponent field of |x|
+      if (e32 > 0) l1 += __uint_as_float(e32 > 254 ? 0x7f7fffffu : (((uint32_t)e32 << 23) | (uint32_t)((u >> 29) & 0x7fffffu)));
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
     m = u > m ? u : m;
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
   }
   if (lane == 0) {
     const int ea = (int)(m >> 52);
@@ -1062,6 +1087,11 @@ __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __res
     if (ea > 0) e = ea - 1022;                       // [2^(ea-1023), 2^(ea-1022))
     else if (m != 0) e = (64 - __clzll((long long)m)) - 1074;  // subnormal: [2^(L-1075), 2^(L-1074))
     eout[w] = e;
+    if (m != 0) {
+      // entries below 2^-126 were left out: add their largest possible share
+      const float s = ldexpf(l1, -e) + (float)(rp[I + 1] - rp[I]) * (float)BS * ldexpf(1.0f, -126 - e);
+      atomicMax(l1max, __float_as_uint(fminf(s, 3.0e38f)));
+    }
   }
 }
 
@@ -1181,22 +1211,6 @@ __global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict_
   }
 }
 
-// largest K-step count over the tiles (union of a super-tile's bitmap rows)
-__global__ void k_max_ksteps(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles, int rows_per_tile,
-                             const uint32_t* __restrict__ bm, int nb, int W, int* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= *ntiles) return;
-  const int S0 = tiles[2 * t] * rows_per_tile;
-  int nk = 0;
-  for (int w = 0; w < W; ++w) {
-    uint32_t word = 0;
-    for (int r = 0; r < rows_per_tile; ++r)
-      if (S0 + r < nb) word |= bm[(size_t)(S0 + r) * W + w];
-    nk += __popc(word);
-  }
-  atomicMax(out, nk);
-}
-
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
                       unsigned long long* pairs) {
@@ -1207,11 +1221,15 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   if (ns < 1 || ns > 8) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 8 slices");
   // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T)
   Buf<int> sige(ctx, rows), taue(ctx, rows);
-  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sige.p);
+  Buf<unsigned int> l1(ctx, 2);
+  IFAC_CK(cudaMemsetAsync(l1.p, 0, 2 * sizeof(unsigned int), ctx->stream));
+  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sige.p,
+                                                             l1.p);
   IFAC_CK_LAUNCH();
   {
     View bt = view_rows(ctx, B, !tB);
-    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, taue.p);
+    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, taue.p,
+                                                               l1.p + 1);
     IFAC_CK_LAUNCH();
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
@@ -1271,13 +1289,16 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
   int kmax = 0;
+  float l1h[2] = {0.f, 0.f};
+  Buf<int> tnk(ctx, (size_t)ntot);
   {
     Buf<int> dk(ctx, 1);
     IFAC_CK(cudaMemsetAsync(dk.p, 0, sizeof(int), ctx->stream));
-    k_max_ksteps<<<cdiv(ntot, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
-                                                           words_per_row(nb), dk.p);
+    k_tile_ksteps<<<cdiv(ntot * 32, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
+                                                                 words_per_row(nb), tnk.p, dk.p);
     IFAC_CK_LAUNCH();
     to_host(ctx, &kmax, dk.p, sizeof(int));
+    to_host(ctx, l1h, l1.p, sizeof(l1h));
   }
   Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
   IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
@@ -1291,6 +1312,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   TileArgs args;
   args.tiles = tiles.p;
   args.ntiles = coff.p + nchunk;
+  args.tile_nk = tnk.p;
   args.nb = nb;
   args.W = words_per_row(nb);
   args.bmA = bmA.p;
@@ -1310,16 +1332,18 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.err = ctx->dev_err;
   args.split = 1;
   args.cpart = part.p;
-  // fixed point, scale 2^-f relative to sigma_i tau_j.  Safe: |sum| <= K 2^f
-  // <= 2^62 for the scalar inner length K of the longest tile.  The kernel
-  // first runs with f = 54 (any sum below 2^9 sigma_i tau_j, the usual case,
-  // keeps 2^-54 of resolution) and reports an overflow, after which the
-  // product is redone with the safe f.  f <= 56 keeps every weight 2^(f - 7g)
-  // of the 7-slice product integral.
+  // fixed point, scale 2^-f relative to sigma_i tau_j, with every partial sum
+  // below 2^62: |sum_ij| <= min(sum_k |a_ik| / sigma_i, sum_k |b_kj| / tau_j)
+  // (|a / sigma|, |b / tau| < 1), bounded by the largest scaled row / column
+  // 1-norm (FP32, so with a margin), and by the scalar inner length K of the
+  // longest tile.  f <= 56 keeps every weight 2^(f - 7g) of the 7-slice
+  // product integral.  An overflow would still be detected and reported.
   int lgK = 0;
   while (((int64_t)1 << lgK) < (int64_t)std::max(kmax, 1) * BS) ++lgK;
-  const int f_safe = std::min(56, 62 - lgK);
-  const int f_try = std::max(f_safe, 54);
+  const double l1b = std::min((double)l1h[0], (double)l1h[1]) * 1.125 + 2.0;
+  int lgB = 0;
+  while (std::ldexp(1.0, lgB) < l1b && lgB < 62) ++lgB;
+  const int fbits = std::min(56, 62 - std::min(lgK, lgB));
   auto set_units = [&](int fbits) {
     // units: slice pairs of equal weight packed while sum over the unit of
     // max|q_s| max|q_t| * 64 * KW stays <= 2^24
@@ -1371,24 +1395,13 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     max_clusters = sms / CL;
   }
   cfg.gridDim = dim3((unsigned)(std::min<int64_t>(ntot, max_clusters) * CL), 1, 1);
-  Buf<int> dovf(ctx, 1);
-  int fbits = f_try;
-  for (;;) {
-    set_units(fbits);
-    args.ovf = dovf.p;
-    IFAC_CK(cudaMemsetAsync(dovf.p, 0, sizeof(int), ctx->stream));
-    prof_begin(ctx, 2);
-    IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA, mB, args));
-    IFAC_CK_LAUNCH();
-    prof_end(ctx);
-    ++ctx->split_launches;
-    if (fbits == f_safe) break;
-    int ovf = 0;
-    to_host(ctx, &ovf, dovf.p, sizeof(int));
-    if (!ovf) break;
-    fbits = f_safe;
-    IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
-  }
+  set_units(fbits);
+  args.ovf = ctx->dev_err;
+  prof_begin(ctx, 2);
+  IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA, mB, args));
+  IFAC_CK_LAUNCH();
+  prof_end(ctx);
+  ++ctx->split_launches;
   {
     int ea = 0;
     const double am = std::frexp(alpha, &ea) * 2.0;  // alpha = am 2^(ea - 1), am in [1, 2)
