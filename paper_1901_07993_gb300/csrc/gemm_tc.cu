@@ -266,16 +266,8 @@ struct TileArgs {
   const int* ntiles;         // device: number of tiles
   const int* tile_nk;        // device: K steps of each tile
   int nb;
-  int W;                     // 32-bit words per bitmap row
-  const uint32_t* bmA;       // pattern bitmap of op(A): bit (I, K)
-  const int32_t* mapA;       // [nb*nb] index of op(A)_IK in the low-precision copy, or its zero
-                             // block; NULL: binary search in the CSR of op(A) instead
-  const int32_t* mapB;       // same for op(B)_KJ
-  const int32_t* arp;        // CSR of op(A) (block q of the copy = entry q)
-  const int32_t* aci;
-  const int32_t* brp;        // CSR of op(B)
-  const int32_t* bci;
-  int a_zero, b_zero;
+  const int32_t* rec;        // plan: per K step, copy indices of op(A)_IK (super-tile rows) and op(B)_KJ
+  const int32_t* rec_off;    // first record of each tile
   const int32_t* crp;    // C pattern
   const int32_t* cci;
   double* cval;
@@ -312,6 +304,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ double partial[4][C::TN];
   __shared__ int s_unit_end[MAX_UNITS], s_pair_ya[MAX_PAIRS], s_pair_yb[MAX_PAIRS];
   __shared__ int s_unit_sh[MAX_UNITS];
+  __shared__ float ep_stage[NEPI][32 * 17];  // plain epilogue: per-warp transpose for coalesced stores
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -362,13 +355,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
-    // The warp turns the K set of a tile (union of the bitmap rows of its op(A)
-    // block rows) into K-step records 32 at a time, lane-parallel; lane 0 then
-    // issues the loads of each record into the next ring slot.  In split mode
-    // the records are gathered into windows of KW, and every window is loaded
-    // once per slice pair, unit by unit.
+    // The warp reads the tile's K-step records from the plan 32 at a time,
+    // lane-parallel; lane 0 then issues the loads of each record into the next
+    // ring slot.  In split mode the records come in windows of KW, and every
+    // window is loaded once per slice pair, unit by unit.
     __shared__ int rec[32][TM + Cfg<ELT>::TN];
-    __shared__ int wrec[KW + 32][TM + Cfg<ELT>::TN];
+    __shared__ int wrec[KW][TM + Cfg<ELT>::TN];
     int stage = 0;
     uint32_t phase = 0;
     uint32_t issued_mask = 0, last_parity = 0;  // lane 0: stages filled / parity of their last fill
@@ -405,90 +397,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!issue(wrec[j], s_pair_ya[p], s_pair_yb[p])) return false;
       return true;
     };
+    constexpr int RECW = CL * TM + C::TN;  // plan record: op(A) rows of the super-tile, then op(B) columns
     for (int t = cid; t < ntiles && ok; t += ncl) {
-      const int S0 = args.tiles[2 * t] * (CL * TM);
-      const int I0 = S0 + (int)crank * TM, J0 = args.tiles[2 * t + 1] * C::TN;
-      int npend = 0;  // split mode: records in the open window (warp-uniform)
-      for (int wbase = 0; wbase < args.W && ok; wbase += 32) {
-        const int w = wbase + lane;
-        uint32_t word = 0;
-        if (w < args.W) {
+      const int nk = args.tile_nk[t];
+      const int32_t* base = args.rec + (size_t)args.rec_off[t] * RECW;
+      if (!args.split) {
+        for (int k0 = 0; k0 < nk && ok; k0 += 32) {
+          const int n = min(32, nk - k0);
+          if (lane < n) {
+            const int32_t* r = base + (size_t)(k0 + lane) * RECW;
 #pragma unroll
-          for (int r = 0; r < CL * TM; ++r)
-            if (S0 + r < args.nb) word |= args.bmA[(size_t)(S0 + r) * args.W + w];
-        }
-        while (__any_sync(0xffffffffu, word != 0u) && ok) {
-          const bool has = word != 0u;
-          const unsigned m = __ballot_sync(0xffffffffu, has);
-          if (has) {
-            const int K = w * 32 + __ffs(word) - 1;
-            word &= word - 1u;
-            const int slot = __popc(m & ((1u << lane) - 1u));
-            if (args.mapA) {
+            for (int i = 0; i < TM; ++i) rec[lane][i] = r[(int)crank * TM + i];
 #pragma unroll
-              for (int r = 0; r < TM; ++r)
-                rec[slot][r] = (I0 + r < args.nb) ? args.mapA[(size_t)(I0 + r) * args.nb + K] : args.a_zero;
-#pragma unroll
-              for (int c = 0; c < C::TN; ++c)
-                rec[slot][TM + c] = (J0 + c < args.nb) ? args.mapB[(size_t)K * args.nb + J0 + c] : args.b_zero;
-            } else {
-#pragma unroll
-              for (int r = 0; r < TM; ++r) {
-                int idx = args.a_zero;
-                if (I0 + r < args.nb) {
-                  const int hi = args.arp[I0 + r + 1];
-                  const int q = lower_bound_i32(args.aci, args.arp[I0 + r], hi, K);
-                  if (q < hi && args.aci[q] == K) idx = q;
-                }
-                rec[slot][r] = idx;
-              }
-              const int hi = args.brp[K + 1];
-              int q = lower_bound_i32(args.bci, args.brp[K], hi, J0);
-#pragma unroll
-              for (int c = 0; c < C::TN; ++c) {
-                int idx = args.b_zero;
-                if (q < hi && args.bci[q] == J0 + c) idx = q++;
-                rec[slot][TM + c] = idx;
-              }
-            }
+            for (int c = 0; c < C::TN; ++c) rec[lane][TM + c] = r[CL * TM + c];
           }
           __syncwarp();
-          const int n = __popc(m);
-          if (!args.split) {
-            if (lane == 0)
-              for (int j = 0; j < n && ok; ++j) ok = issue(rec[j], 0, 0);
-          } else {
-            if (lane < n) {
-#pragma unroll
-              for (int i = 0; i < TM + C::TN; ++i) wrec[npend + lane][i] = rec[lane][i];
-            }
-            __syncwarp();
-            npend += n;  // < KW + 32
-            while (npend >= KW && ok) {
-              if (lane == 0) ok = issue_window(KW);
-              ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-              const int rest = npend - KW;  // < 32
-              int tmp[TM + C::TN];
-              if (lane < rest) {
-#pragma unroll
-                for (int i = 0; i < TM + C::TN; ++i) tmp[i] = wrec[KW + lane][i];
-              }
-              __syncwarp();
-              if (lane < rest) {
-#pragma unroll
-                for (int i = 0; i < TM + C::TN; ++i) wrec[lane][i] = tmp[i];
-              }
-              __syncwarp();
-              npend = rest;
-            }
-          }
+          if (lane == 0)
+            for (int j = 0; j < n && ok; ++j) ok = issue(rec[j], 0, 0);
           ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
           __syncwarp();
         }
-      }
-      if (args.split && npend > 0 && ok) {
-        if (lane == 0) ok = issue_window(npend);
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      } else {
+        for (int kb = 0; kb < nk && ok; kb += KW) {
+          const int cnt = min(KW, nk - kb);
+          if (lane < cnt) {
+            const int32_t* r = base + (size_t)(kb + lane) * RECW;
+#pragma unroll
+            for (int i = 0; i < TM; ++i) wrec[lane][i] = r[(int)crank * TM + i];
+#pragma unroll
+            for (int c = 0; c < C::TN; ++c) wrec[lane][TM + c] = r[CL * TM + c];
+          }
+          __syncwarp();
+          if (lane == 0) ok = issue_window(cnt);
+          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+          __syncwarp();
+        }
       }
     }
     // before the CTA exits: the copies lane 0 issued (and the peer's multicast
@@ -557,7 +500,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp & 3;            // tensor-memory lane quarter of this warp
     const int c0 = ((warp - 2) >> 2) * (C::TN / 2), c1 = c0 + C::TN / 2;  // this warp's column blocks
     const int row = q * 32 + lane;     // accumulator row 0..127
-    const int r_blk = row / BS, lr = row % BS;
+    const int r_blk = row / BS;
     const int et = threadIdx.x - 64;   // 0 .. 32 NEPI - 1
     const float alpha_f = (float)args.alpha;
     int tl = 0;
@@ -594,17 +537,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int h = 0; h < BS / 32; ++h) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
-            if (p >= 0) {
-              double* dst = args.cval + (size_t)p * BS * BS + (size_t)lr * BS + h * 32;
+            if (p >= 0) {  // warp-uniform
+              // 32 rows x 16 columns at a time through shared memory, so that
+              // each store instruction writes two 128-byte row segments
+              float* sw = ep_stage[warp - 2];
+              double* blk = args.cval + (size_t)p * BS * BS + (size_t)((q & 1) * 32) * BS + h * 32;
+              const int cc = lane & 15, rr = lane >> 4;
 #pragma unroll
-              for (int e = 0; e < 32; e += 2) {
-                const float a = v[e] * alpha_f, b = v[e + 1] * alpha_f;
-                ssf = fmaf(a, a, ssf);
-                ssf = fmaf(b, b, ssf);
-                double2 w;
-                w.x = f32_to_f64(a);
-                w.y = f32_to_f64(b);
-                *reinterpret_cast<double2*>(dst + e) = w;
+              for (int half = 0; half < 2; ++half) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                  const float a = v[half * 16 + e] * alpha_f;
+                  ssf = fmaf(a, a, ssf);
+                  sw[lane * 17 + e] = a;
+                }
+                __syncwarp();
+#pragma unroll 4
+                for (int k = 0; k < 32; k += 2)
+                  blk[(size_t)(k + rr) * BS + half * 16 + cc] = f32_to_f64(sw[(k + rr) * 17 + cc]);
+                __syncwarp();
               }
             }
           }
@@ -893,6 +844,147 @@ __global__ void k_tile_ksteps(const int32_t* __restrict__ tiles, const int* __re
   }
 }
 
+// Plan records of every super-tile: for each K step of the union of its rows'
+// bitmaps, the copy index of op(A)_IK for each of its ROWS block rows and of
+// op(B)_KJ for each of its COLS block columns (the zero block when absent).
+// One warp per tile, K steps 32 at a time, lane-parallel; the records of
+// tile t start at off[t].
+template <int ROWS, int COLS>
+__global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles,
+                            const int32_t* __restrict__ off, const uint32_t* __restrict__ bm, int nb, int W,
+                            const int32_t* __restrict__ mapA, const int32_t* __restrict__ mapB,
+                            const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                            const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, int a_zero, int b_zero,
+                            int32_t* __restrict__ rec) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= *ntiles) return;
+  const int I0 = tiles[2 * t] * ROWS, J0 = tiles[2 * t + 1] * COLS;
+  int e = off[t];
+  for (int wbase = 0; wbase < W; wbase += 32) {
+    const int w = wbase + lane;
+    uint32_t word = 0;
+    if (w < W) {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r)
+        if (I0 + r < nb) word |= bm[(size_t)(I0 + r) * W + w];
+    }
+    while (__any_sync(0xffffffffu, word != 0u)) {
+      const bool has = word != 0u;
+      const unsigned m = __ballot_sync(0xffffffffu, has);
+      if (has) {
+        const int K = w * 32 + __ffs(word) - 1;
+        word &= word - 1u;
+        int32_t* out = rec + (size_t)(e + __popc(m & ((1u << lane) - 1u))) * (ROWS + COLS);
+        if (mapA) {
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) out[r] = (I0 + r < nb) ? mapA[(size_t)(I0 + r) * nb + K] : a_zero;
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) out[ROWS + c] = (J0 + c < nb) ? mapB[(size_t)K * nb + J0 + c] : b_zero;
+        } else {
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) {
+            int idx = a_zero;
+            if (I0 + r < nb) {
+              const int hi = arp[I0 + r + 1];
+              const int q = lower_bound_i32(aci, arp[I0 + r], hi, K);
+              if (q < hi && aci[q] == K) idx = q;
+            }
+            out[r] = idx;
+          }
+          const int hi = brp[K + 1];
+          int q = lower_bound_i32(bci, brp[K], hi, J0);
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) {
+            int idx = b_zero;
+            if (q < hi && bci[q] == J0 + c) idx = q++;
+            out[ROWS + c] = idx;
+          }
+        }
+      }
+      e += __popc(m);
+    }
+  }
+}
+
+// The tile plan of a product: super-tiles of ROWS x COLS blocks holding a
+// block of C's pattern (grouped order), their K-step counts and records.
+struct Plan {
+  Buf<int32_t> tiles, coff, tnk, off, rec;
+  int nchunk = 0;
+  int64_t ntot = 0;
+  int ntiles = 0;
+  int kmax = 0;
+};
+
+template <int ROWS, int COLS>
+static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool tA, const View& brows,
+                      const ifac_bsr& B, const ifac_bsr& C, const int32_t* crow, bool want_kmax) {
+  const int nb = A.nb, W = words_per_row(nb);
+  Plan P;
+  // K sets (bitmap rows of op(A)); dense block-index maps of op(A), op(B)
+  // while they stay small, binary searches in the CSR patterns beyond that
+  Buf<uint32_t> bmA = pattern_bitmap(ctx, A, tA);
+  const int64_t nb2 = (int64_t)nb * nb;
+  const bool dense_maps = nb2 <= (int64_t)4 << 20;
+  Buf<int32_t> imA, imB;
+  if (dense_maps) {
+    imA = Buf<int32_t>(ctx, nb2);
+    imB = Buf<int32_t>(ctx, nb2);
+    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imA.p, nb2, (int32_t)A.nnzb);
+    IFAC_CK_LAUNCH();
+    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imB.p, nb2, (int32_t)B.nnzb);
+    IFAC_CK_LAUNCH();
+    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, imA.p);
+    IFAC_CK_LAUNCH();
+    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
+    IFAC_CK_LAUNCH();
+  }
+  const int ntr = cdiv(nb, ROWS), ntc = cdiv(nb, COLS);
+  P.ntot = (int64_t)ntr * ntc;
+  P.nchunk = cdiv(P.ntot, CHUNK);
+  Buf<uint8_t> flags(ctx, (size_t)P.ntot);
+  Buf<int32_t> ccnt(ctx, P.nchunk);
+  P.tiles = Buf<int32_t>(ctx, (size_t)2 * P.ntot);
+  P.coff = Buf<int32_t>(ctx, P.nchunk + 1);
+  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)P.ntot, ctx->stream));
+  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, ROWS, COLS, ntc, flags.p);
+  IFAC_CK_LAUNCH();
+  k_tile_count<<<P.nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
+  IFAC_CK_LAUNCH();
+  scan_counts(ctx, ccnt.p, P.coff.p, P.nchunk, false);
+  k_tile_write<<<P.nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, P.coff.p, P.tiles.p);
+  IFAC_CK_LAUNCH();
+  const int* ntiles = P.coff.p + P.nchunk;
+  int nt = 0;  // the per-tile kernels and arrays are sized by the tile count, not by all ntr x ntc positions
+  to_host(ctx, &nt, ntiles, sizeof(int));
+  P.ntiles = nt;
+  P.tnk = Buf<int32_t>(ctx, (size_t)std::max(nt, 1));
+  P.off = Buf<int32_t>(ctx, (size_t)nt + 1);
+  Buf<int> dk(ctx, 1);
+  IFAC_CK(cudaMemsetAsync(dk.p, 0, sizeof(int), ctx->stream));
+  int64_t total = 0;
+  if (nt > 0) {
+    k_tile_ksteps<<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(P.tiles.p, ntiles, ROWS, bmA.p, nb, W,
+                                                                         P.tnk.p, want_kmax ? dk.p : nullptr);
+    IFAC_CK_LAUNCH();
+    total = scan_counts(ctx, P.tnk.p, P.off.p, nt, true);
+  }
+  if (total > (int64_t)0x7fffffff / (ROWS + COLS))
+    fail(IFAC_ERR_TOO_LARGE, "tensor-core product: tile plan exceeds 2^31 entries");
+  if (want_kmax) to_host(ctx, &P.kmax, dk.p, sizeof(int));
+  P.rec = Buf<int32_t>(ctx, (size_t)std::max<int64_t>(total, 1) * (ROWS + COLS));
+  if (nt > 0) {
+    k_tile_plan<ROWS, COLS><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
+        P.tiles.p, ntiles, P.off.p, bmA.p, nb, W, dense_maps ? imA.p : nullptr, dense_maps ? imB.p : nullptr,
+        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, P.rec.p);
+    IFAC_CK_LAUNCH();
+  }
+  // the plan kernel has read the maps and the bitmap before they are freed
+  // (stream-ordered frees)
+  return P;
+}
+
 template <int ELT>
 static CUtensorMap make_map(void* base, int64_t nblk) {
   CUtensorMap m;
@@ -929,45 +1021,9 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   const CUtensorMap mapA = make_map<ELT>(la.p, A.nnzb + 1);
   const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
-  // K sets (bitmap rows of op(A)); dense block-index maps of op(A), op(B)
-  // while they stay small, binary searches in the CSR patterns beyond that
-  Buf<uint32_t> bmA = pattern_bitmap(ctx, A, tA);
-  const int64_t nb2 = (int64_t)nb * nb;
-  const bool dense_maps = nb2 <= (int64_t)4 << 20;
-  Buf<int32_t> imA, imB;
-  if (dense_maps) {
-    imA = Buf<int32_t>(ctx, nb2);
-    imB = Buf<int32_t>(ctx, nb2);
-    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imA.p, nb2, (int32_t)A.nnzb);
-    IFAC_CK_LAUNCH();
-    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imB.p, nb2, (int32_t)B.nnzb);
-    IFAC_CK_LAUNCH();
-    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, imA.p);
-    IFAC_CK_LAUNCH();
-    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
-    IFAC_CK_LAUNCH();
-  }
-  // super-tiles (CL x TM block rows, TN block columns) holding a block of C's
-  // pattern, compacted in grouped order
   constexpr int CL = Cf::CL;
-  const int ntr = cdiv(nb, CL * TM), ntc = cdiv(nb, Cf::TN);
-  const int64_t ntot = (int64_t)ntr * ntc;
-  const int nchunk = cdiv(ntot, CHUNK);
-  Buf<uint8_t> flags(ctx, (size_t)ntot);
-  Buf<int32_t> tiles(ctx, (size_t)2 * ntot), ccnt(ctx, nchunk), coff(ctx, nchunk + 1);
-  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntot, ctx->stream));
-  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, CL * TM, Cf::TN, ntc, flags.p);
-  IFAC_CK_LAUNCH();
-  k_tile_count<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
-  IFAC_CK_LAUNCH();
-  scan_counts(ctx, ccnt.p, coff.p, nchunk, false);
-  k_tile_write<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, coff.p, tiles.p);
-  IFAC_CK_LAUNCH();
+  Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false);
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
-  IFAC_CK_LAUNCH();
-  Buf<int> tnk(ctx, (size_t)ntot);
-  k_tile_ksteps<<<cdiv(ntot * 32, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
-                                                               words_per_row(nb), tnk.p, nullptr);
   IFAC_CK_LAUNCH();
   static bool attr = false;
   if (!attr) {
@@ -977,20 +1033,12 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   TileArgs args;
-  args.tiles = tiles.p;
-  args.ntiles = coff.p + nchunk;  // the scan's total
-  args.tile_nk = tnk.p;
+  args.tiles = P.tiles.p;
+  args.ntiles = P.coff.p + P.nchunk;  // the scan's total
+  args.tile_nk = P.tnk.p;
   args.nb = nb;
-  args.W = words_per_row(nb);
-  args.bmA = bmA.p;
-  args.mapA = dense_maps ? imA.p : nullptr;
-  args.mapB = dense_maps ? imB.p : nullptr;
-  args.arp = arows.rp;
-  args.aci = arows.ci;
-  args.brp = brows.rp;
-  args.bci = brows.ci;
-  args.a_zero = (int)A.nnzb;
-  args.b_zero = (int)B.nnzb;
+  args.rec = P.rec.p;
+  args.rec_off = P.off.p;
   args.crp = C.row_ptr;
   args.cci = C.col_idx;
   args.cval = C.val;
@@ -1003,8 +1051,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.nunits = 0;
   for (int u = 0; u < MAX_UNITS; ++u) args.unit_end[u] = args.unit_sh[u] = 0;
   for (int p = 0; p < MAX_PAIRS; ++p) args.pair_ya[p] = args.pair_yb[p] = 0;
-  // the grid does not depend on the tile count (read on the device), so no
-  // host read-back is needed here; idle clusters return at once
+  // at most one cluster per tile; idle clusters return at once
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
@@ -1024,7 +1071,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
       max_clusters = sms / CL;
     }
   }
-  const int64_t clusters = std::min<int64_t>(ntot, max_clusters);
+  const int64_t clusters = std::min<int64_t>(std::max(P.ntiles, 1), max_clusters);
   cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
   prof_begin(ctx, 1);
   IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<ELT>, mapA, mapB, args));
@@ -1256,50 +1303,13 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     fail(IFAC_ERR_TOO_LARGE, "split product: slice copies exceed the 2^31-row tensor-map range");
   const CUtensorMap mA = make_map<2>(la.p, (int64_t)ns * (A.nnzb + 1));
   const CUtensorMap mB = make_map<2>(lb.p, (int64_t)ns * (B.nnzb + 1));
-  // K sets, block maps, tile list (as for the plain tensor-core product)
-  Buf<uint32_t> bmA = pattern_bitmap(ctx, A, tA);
-  const int64_t nb2 = (int64_t)nb * nb;
-  const bool dense_maps = nb2 <= (int64_t)4 << 20;
-  Buf<int32_t> imA, imB;
-  if (dense_maps) {
-    imA = Buf<int32_t>(ctx, nb2);
-    imB = Buf<int32_t>(ctx, nb2);
-    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imA.p, nb2, (int32_t)A.nnzb);
-    IFAC_CK_LAUNCH();
-    k_map_fill<<<cdiv(nb2, 256), 256, 0, ctx->stream>>>(imB.p, nb2, (int32_t)B.nnzb);
-    IFAC_CK_LAUNCH();
-    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, imA.p);
-    IFAC_CK_LAUNCH();
-    k_map_scatter<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(brows.rp, brows.ci, nb, imB.p);
-    IFAC_CK_LAUNCH();
-  }
-  const int ntr = cdiv(nb, CL * TM), ntc = cdiv(nb, Cf::TN);
-  const int64_t ntot = (int64_t)ntr * ntc;
-  const int nchunk = cdiv(ntot, CHUNK);
-  Buf<uint8_t> flags(ctx, (size_t)ntot);
-  Buf<int32_t> tiles(ctx, (size_t)2 * ntot), ccnt(ctx, nchunk), coff(ctx, nchunk + 1);
-  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)ntot, ctx->stream));
-  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, CL * TM, Cf::TN, ntc, flags.p);
-  IFAC_CK_LAUNCH();
-  k_tile_count<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
-  IFAC_CK_LAUNCH();
-  scan_counts(ctx, ccnt.p, coff.p, nchunk, false);
-  k_tile_write<<<nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, coff.p, tiles.p);
-  IFAC_CK_LAUNCH();
+  // tile plan (as for the plain tensor-core product) with the longest tile's K steps
+  Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
-  int kmax = 0;
+  const int kmax = P.kmax;
   float l1h[2] = {0.f, 0.f};
-  Buf<int> tnk(ctx, (size_t)ntot);
-  {
-    Buf<int> dk(ctx, 1);
-    IFAC_CK(cudaMemsetAsync(dk.p, 0, sizeof(int), ctx->stream));
-    k_tile_ksteps<<<cdiv(ntot * 32, 256), 256, 0, ctx->stream>>>(tiles.p, coff.p + nchunk, CL * TM, bmA.p, nb,
-                                                                 words_per_row(nb), tnk.p, dk.p);
-    IFAC_CK_LAUNCH();
-    to_host(ctx, &kmax, dk.p, sizeof(int));
-    to_host(ctx, l1h, l1.p, sizeof(l1h));
-  }
+  to_host(ctx, l1h, l1.p, sizeof(l1h));
   Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
   IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
   static bool attr = false;
@@ -1310,20 +1320,12 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   TileArgs args;
-  args.tiles = tiles.p;
-  args.ntiles = coff.p + nchunk;
-  args.tile_nk = tnk.p;
+  args.tiles = P.tiles.p;
+  args.ntiles = P.coff.p + P.nchunk;
+  args.tile_nk = P.tnk.p;
   args.nb = nb;
-  args.W = words_per_row(nb);
-  args.bmA = bmA.p;
-  args.mapA = dense_maps ? imA.p : nullptr;
-  args.mapB = dense_maps ? imB.p : nullptr;
-  args.arp = arows.rp;
-  args.aci = arows.ci;
-  args.brp = brows.rp;
-  args.bci = brows.ci;
-  args.a_zero = (int)A.nnzb;
-  args.b_zero = (int)B.nnzb;
+  args.rec = P.rec.p;
+  args.rec_off = P.off.p;
   args.crp = C.row_ptr;
   args.cci = C.col_idx;
   args.cval = C.val;
@@ -1394,7 +1396,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     cudaGetLastError();
     max_clusters = sms / CL;
   }
-  cfg.gridDim = dim3((unsigned)(std::min<int64_t>(ntot, max_clusters) * CL), 1, 1);
+  cfg.gridDim = dim3((unsigned)(std::min<int64_t>(std::max(P.ntiles, 1), max_clusters) * CL), 1, 1);
   set_units(fbits);
   args.ovf = ctx->dev_err;
   prof_begin(ctx, 2);
