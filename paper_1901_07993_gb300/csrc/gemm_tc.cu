@@ -820,47 +820,26 @@ static EncodeTiledFn encoder() {
 
 // 2D view of a low-precision block array: rows = (nblk) * 64, 64 elements per
 // row; boxes of one 128-byte atom x 64 rows, 128-byte swizzle
-// K-step count of every super-tile (size of the union of its rows' bitmaps),
-// one warp per tile; the largest count into *kmax when kmax != NULL
-__global__ void k_tile_ksteps(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles, int rows_per_tile,
-                              const uint32_t* __restrict__ bm, int nb, int W, int* __restrict__ nk_out,
-                              int* __restrict__ kmax) {
-  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (t >= *ntiles) return;
-  const int S0 = tiles[2 * t] * rows_per_tile;
-  int nk = 0;
-  for (int w = lane; w < W; w += 32) {
-    uint32_t word = 0;
-    for (int r = 0; r < rows_per_tile; ++r)
-      if (S0 + r < nb) word |= bm[(size_t)(S0 + r) * W + w];
-    nk += __popc(word);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nk += __shfl_xor_sync(0xffffffffu, nk, o);
-  if (lane == 0) {
-    nk_out[t] = nk;
-    if (kmax) atomicMax(kmax, nk);
-  }
-}
 
-// Plan records of every super-tile: for each K step of the union of its rows'
-// bitmaps, the copy index of op(A)_IK for each of its ROWS block rows and of
-// op(B)_KJ for each of its COLS block columns (the zero block when absent).
-// One warp per tile, K steps 32 at a time, lane-parallel; the records of
-// tile t start at off[t].
-template <int ROWS, int COLS>
+// Plan records of every super-tile: for each K of the union of its rows'
+// bitmaps at which some op(B)_KJ of its columns is stored, the copy index of
+// op(A)_IK for each of its ROWS block rows and of op(B)_KJ for each of its
+// COLS block columns (the zero block when absent); K steps whose op(B) blocks
+// are all absent contribute nothing and are left out.  One warp per tile,
+// candidate K's 32 at a time, lane-parallel.  COUNT: the number of records
+// into nk[t] (and the largest into *kmax); else the records, from off[t] on.
+template <int ROWS, int COLS, bool COUNT>
 __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles,
                             const int32_t* __restrict__ off, const uint32_t* __restrict__ bm, int nb, int W,
                             const int32_t* __restrict__ mapA, const int32_t* __restrict__ mapB,
                             const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                             const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, int a_zero, int b_zero,
-                            int32_t* __restrict__ rec) {
+                            int32_t* __restrict__ rec, int32_t* __restrict__ nk_out, int* __restrict__ kmax) {
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= *ntiles) return;
   const int I0 = tiles[2 * t] * ROWS, J0 = tiles[2 * t + 1] * COLS;
-  int e = off[t];
+  int e = COUNT ? 0 : off[t];
   for (int wbase = 0; wbase < W; wbase += 32) {
     const int w = wbase + lane;
     uint32_t word = 0;
@@ -870,40 +849,58 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
         if (I0 + r < nb) word |= bm[(size_t)(I0 + r) * W + w];
     }
     while (__any_sync(0xffffffffu, word != 0u)) {
-      const bool has = word != 0u;
-      const unsigned m = __ballot_sync(0xffffffffu, has);
-      if (has) {
+      int ra[ROWS], rb[COLS];
+      bool valid = false;
+      if (word != 0u) {
         const int K = w * 32 + __ffs(word) - 1;
         word &= word - 1u;
-        int32_t* out = rec + (size_t)(e + __popc(m & ((1u << lane) - 1u))) * (ROWS + COLS);
         if (mapA) {
 #pragma unroll
-          for (int r = 0; r < ROWS; ++r) out[r] = (I0 + r < nb) ? mapA[(size_t)(I0 + r) * nb + K] : a_zero;
-#pragma unroll
-          for (int c = 0; c < COLS; ++c) out[ROWS + c] = (J0 + c < nb) ? mapB[(size_t)K * nb + J0 + c] : b_zero;
+          for (int c = 0; c < COLS; ++c) rb[c] = (J0 + c < nb) ? mapB[(size_t)K * nb + J0 + c] : b_zero;
         } else {
-#pragma unroll
-          for (int r = 0; r < ROWS; ++r) {
-            int idx = a_zero;
-            if (I0 + r < nb) {
-              const int hi = arp[I0 + r + 1];
-              const int q = lower_bound_i32(aci, arp[I0 + r], hi, K);
-              if (q < hi && aci[q] == K) idx = q;
-            }
-            out[r] = idx;
-          }
           const int hi = brp[K + 1];
           int q = lower_bound_i32(bci, brp[K], hi, J0);
 #pragma unroll
           for (int c = 0; c < COLS; ++c) {
             int idx = b_zero;
             if (q < hi && bci[q] == J0 + c) idx = q++;
-            out[ROWS + c] = idx;
+            rb[c] = idx;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < COLS; ++c) valid |= rb[c] != b_zero;
+        if (!COUNT && valid) {
+          if (mapA) {
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) ra[r] = (I0 + r < nb) ? mapA[(size_t)(I0 + r) * nb + K] : a_zero;
+          } else {
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+              int idx = a_zero;
+              if (I0 + r < nb) {
+                const int hi = arp[I0 + r + 1];
+                const int q = lower_bound_i32(aci, arp[I0 + r], hi, K);
+                if (q < hi && aci[q] == K) idx = q;
+              }
+              ra[r] = idx;
+            }
           }
         }
       }
+      const unsigned m = __ballot_sync(0xffffffffu, valid);
+      if (!COUNT && valid) {
+        int32_t* out = rec + (size_t)(e + __popc(m & ((1u << lane) - 1u))) * (ROWS + COLS);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) out[r] = ra[r];
+#pragma unroll
+        for (int c = 0; c < COLS; ++c) out[ROWS + c] = rb[c];
+      }
       e += __popc(m);
     }
+  }
+  if (COUNT && lane == 0) {
+    nk_out[t] = e;
+    if (kmax) atomicMax(kmax, e);
   }
 }
 
@@ -965,8 +962,10 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
   IFAC_CK(cudaMemsetAsync(dk.p, 0, sizeof(int), ctx->stream));
   int64_t total = 0;
   if (nt > 0) {
-    k_tile_ksteps<<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(P.tiles.p, ntiles, ROWS, bmA.p, nb, W,
-                                                                         P.tnk.p, want_kmax ? dk.p : nullptr);
+    k_tile_plan<ROWS, COLS, true><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
+        P.tiles.p, ntiles, nullptr, bmA.p, nb, W, dense_maps ? imA.p : nullptr, dense_maps ? imB.p : nullptr,
+        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, nullptr, P.tnk.p,
+        want_kmax ? dk.p : nullptr);
     IFAC_CK_LAUNCH();
     total = scan_counts(ctx, P.tnk.p, P.off.p, nt, true);
   }
@@ -975,9 +974,9 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
   if (want_kmax) to_host(ctx, &P.kmax, dk.p, sizeof(int));
   P.rec = Buf<int32_t>(ctx, (size_t)std::max<int64_t>(total, 1) * (ROWS + COLS));
   if (nt > 0) {
-    k_tile_plan<ROWS, COLS><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
+    k_tile_plan<ROWS, COLS, false><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
         P.tiles.p, ntiles, P.off.p, bmA.p, nb, W, dense_maps ? imA.p : nullptr, dense_maps ? imB.p : nullptr,
-        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, P.rec.p);
+        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, P.rec.p, nullptr, nullptr);
     IFAC_CK_LAUNCH();
   }
   // the plan kernel has read the maps and the bitmap before they are freed
