@@ -1103,7 +1103,47 @@ constexpr int SPLIT_BITS = 7;
 // row view: max_k |x_rk| = m 2^e with m in [0.5, 1) (e = 0 for an all-zero row);
 // the largest scaled row 1-norm sum_k |x_rk| / sigma (FP32, magnitudes
 // truncated to 24 bits) into *l1max as FP32 bits
-__global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb, int tr,
+__device__ __forceinline__ void row_scale_out(unsigned long long m, float l1, int nblocks, int* eout,
+                                              unsigned int* l1max) {
+  const int ea = (int)(m >> 52);
+  int e = 0;
+  if (ea > 0) e = ea - 1022;                       // [2^(ea-1023), 2^(ea-1022))
+  else if (m != 0) e = (64 - __clzll((long long)m)) - 1074;  // subnormal: [2^(L-1075), 2^(L-1074))
+  *eout = e;
+  if (m != 0) {
+    // entries below 2^-126 were left out: add their largest possible share
+    const float s = ldexpf(l1, -e) + (float)nblocks * (float)BS * ldexpf(1.0f, -126 - e);
+    atomicMax(l1max, __float_as_uint(fminf(s, 3.0e38f)));
+  }
+}
+
+__device__ __forceinline__ void row_scale_acc(double x, unsigned long long& m, float& l1) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  m = u > m ? u : m;
+  const int e32 = (int)(u >> 52) - 896;  // FP32 exponent field of |x|
+  if (e32 > 0)
+    l1 += __uint_as_float(e32 > 254 ? 0x7f7fffffu : (((uint32_t)e32 << 23) | (uint32_t)((u >> 29) & 0x7fffffu)));
+}
+
+// transposed views: one CTA of BS threads per block row; thread r takes
+// column r of each stored block (op(X) row r), reads coalesced across threads
+__global__ void __launch_bounds__(BS) k_row_scale_t(const int32_t* __restrict__ rp, const int32_t* __restrict__ src,
+                                                    int nb, const double* __restrict__ val, int* __restrict__ eout,
+                                                    unsigned int* __restrict__ l1max) {
+  const int I = blockIdx.x, r = threadIdx.x;
+  if (I >= nb) return;
+  unsigned long long m = 0;
+  float l1 = 0.0f;
+  for (int q = rp[I]; q < rp[I + 1]; ++q) {
+    const double* blk = val + (size_t)(src ? src[q] : q) * BS * BS;
+#pragma unroll 8
+    for (int k = 0; k < BS; ++k) row_scale_acc(blk[k * BS + r], m, l1);
+  }
+  row_scale_out(m, l1, rp[I + 1] - rp[I], eout + (size_t)I * BS + r, l1max);
+}
+
+// rows stored as rows: one warp per scalar row, lanes along the row (coalesced)
+__global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb,
                             const double* __restrict__ val, int* __restrict__ eout, unsigned int* __restrict__ l1max) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -1113,13 +1153,7 @@ __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __res
   float l1 = 0.0f;
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
     const double* blk = val + (size_t)(src ? src[q] : q) * BS * BS;
-    for (int c = lane; c < BS; c += 32) {
-      const unsigned long long u =
-          (unsigned long long)__double_as_longlong(tr ? blk[c * BS + r] : blk[r * BS + c]) & 0x7fffffffffffffffull;
-      m = u > m ? u : m;
-      const int e32 = (int)(u >> 52) - 896;  // FP32 exponent field of |x|
-      if (e32 > 0) l1 += __uint_as_float(e32 > 254 ? 0x7f7fffffu : (((uint32_t)e32 << 23) | (uint32_t)((u >> 29) & 0x7fffffu)));
-    }
+    for (int c = lane; c < BS; c += 32) row_scale_acc(blk[r * BS + c], m, l1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1127,53 +1161,75 @@ __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __res
     m = u > m ? u : m;
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
   }
-  if (lane == 0) {
-    const int ea = (int)(m >> 52);
-    int e = 0;
-    if (ea > 0) e = ea - 1022;                       // [2^(ea-1023), 2^(ea-1022))
-    else if (m != 0) e = (64 - __clzll((long long)m)) - 1074;  // subnormal: [2^(L-1075), 2^(L-1074))
-    eout[w] = e;
-    if (m != 0) {
-      // entries below 2^-126 were left out: add their largest possible share
-      const float s = ldexpf(l1, -e) + (float)(rp[I + 1] - rp[I]) * (float)BS * ldexpf(1.0f, -126 - e);
-      atomicMax(l1max, __float_as_uint(fminf(s, 3.0e38f)));
-    }
+  if (lane == 0) row_scale_out(m, l1, rp[I + 1] - rp[I], eout + w, l1max);
+}
+
+// sigma exponents (and the scaled 1-norm bound) of the rows of a row view
+static void row_scales(ifac_ctx* ctx, const int32_t* rp, const int32_t* src, int nb, bool tr, const double* val,
+                       int* eout, unsigned int* l1max) {
+  if (tr) {
+    k_row_scale_t<<<nb, BS, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+  } else {
+    k_row_scale<<<cdiv((int64_t)nb * BS * 32, 256), 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
   }
+  IFAC_CK_LAUNCH();
 }
 
 // NS BF16 slice copies (K-major, op() CSR order) of a view; row r of block qb
 // has scale exponent sexp[sblk[qb] * BS + r].  With Y = x 2^(62 - e) held as a
 // 64-bit integer (|Y| < 2^62; bits below 2^-62 of sigma dropped by rounding),
 // digit k is q_k = round(Y_k / 2^(62 - 7k)), Y_{k+1} = Y_k - q_k 2^(62 - 7k).
-__global__ void k_split(const double* __restrict__ val, const int32_t* __restrict__ src, int64_t nblk, int tr,
-                        const int32_t* __restrict__ sblk, const int* __restrict__ sexp, int ns,
-                        __nv_bfloat16* __restrict__ dst) {
+__device__ __forceinline__ void split_digits(double x, int e, int ns, int (&q)[8]) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ea = (int)((u >> 52) & 0x7ff);
+  unsigned long long mant = u & 0xfffffffffffffull;
+  int eb = ea;
+  if (ea) mant |= 1ull << 52;
+  else eb = 1;
+  // |x| = mant 2^(eb - 1075);  |Y| = mant 2^(eb - 1013 - e)
+  const int sh = eb - 1013 - e;
+  unsigned long long Y = 0;
+  if (sh >= 0) Y = mant << sh;  // sh <= 9 since |x| < sigma
+  else if (sh > -63) Y = (mant + (1ull << (-sh - 1))) >> (-sh);
+  long long y = (u >> 63) ? -(long long)Y : (long long)Y;
+#pragma unroll
+  for (int k = 1; k <= 8; ++k) {
+    if (k > ns) break;
+    const int d = 62 - SPLIT_BITS * k;
+    const long long qk = (y + (1ll << (d - 1))) >> d;
+    y -= qk << d;
+    q[k - 1] = (int)qk;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_split(const double* __restrict__ val, const int32_t* __restrict__ src,
+                                               int64_t nblk, int tr, const int32_t* __restrict__ sblk,
+                                               const int* __restrict__ sexp, int ns,
+                                               __nv_bfloat16* __restrict__ dst) {
   constexpr int BSZ = BS * BS;
+  __shared__ double tile[BS][BS + 1];
   const size_t slice_stride = (size_t)(nblk + 1) * BSZ;
   for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
     const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
     const int* se = sexp + (size_t)sblk[qb] * BS;
-    for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
-      const int r = e / BS, c = e % BS;
-      const unsigned long long u = (unsigned long long)__double_as_longlong(tr ? s[c * BS + r] : s[e]);
-      const int ea = (int)((u >> 52) & 0x7ff);
-      unsigned long long mant = u & 0xfffffffffffffull;
-      int eb = ea;
-      if (ea) mant |= 1ull << 52;
-      else eb = 1;
-      // |x| = mant 2^(eb - 1075);  |Y| = mant 2^(eb - 1013 - e)
-      const int sh = eb - 1013 - se[r];
-      unsigned long long Y = 0;
-      if (sh >= 0) Y = mant << sh;  // sh <= 9 since |x| < sigma
-      else if (sh > -63) Y = (mant + (1ull << (-sh - 1))) >> (-sh);
-      long long y = (u >> 63) ? -(long long)Y : (long long)Y;
-      for (int k = 1; k <= ns; ++k) {
-        const int d = 62 - SPLIT_BITS * k;
-        const long long q = (y + (1ll << (d - 1))) >> d;
-        y -= q << d;
-        dst[(size_t)(k - 1) * slice_stride + (size_t)qb * BSZ + e] = __float2bfloat16_rn((float)(int)q);
+    if (tr) {  // coalesced read, transposed through shared memory
+      for (int e = threadIdx.x; e < BSZ; e += blockDim.x) tile[e / BS][e % BS] = s[e];
+      __syncthreads();
+    }
+    for (int e2 = threadIdx.x; e2 < BSZ / 2; e2 += blockDim.x) {
+      const int e = 2 * e2, r = e / BS, c = e % BS;  // elements (r, c) and (r, c + 1) of op(X)'s block
+      const double x0 = tr ? tile[c][r] : s[e], x1 = tr ? tile[c + 1][r] : s[e + 1];
+      int q0[8], q1[8];
+      split_digits(x0, se[r], ns, q0);
+      split_digits(x1, se[r], ns, q1);
+      for (int k = 0; k < ns; ++k) {
+        __nv_bfloat162 v;
+        v.x = __float2bfloat16_rn((float)q0[k]);
+        v.y = __float2bfloat16_rn((float)q1[k]);
+        *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)k * slice_stride + (size_t)qb * BSZ + e) = v;
       }
     }
+    if (tr) __syncthreads();
   }
 }
 
@@ -1269,14 +1325,10 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   Buf<int> sige(ctx, rows), taue(ctx, rows);
   Buf<unsigned int> l1(ctx, 2);
   IFAC_CK(cudaMemsetAsync(l1.p, 0, 2 * sizeof(unsigned int), ctx->stream));
-  k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.src, nb, tA ? 1 : 0, A.val, sige.p,
-                                                             l1.p);
-  IFAC_CK_LAUNCH();
+  row_scales(ctx, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p);
   {
     View bt = view_rows(ctx, B, !tB);
-    k_row_scale<<<cdiv(rows * 32, 256), 256, 0, ctx->stream>>>(bt.rp, bt.src, nb, tB ? 0 : 1, B.val, taue.p,
-                                                               l1.p + 1);
-    IFAC_CK_LAUNCH();
+    row_scales(ctx, bt.rp, bt.src, nb, !tB, B.val, taue.p, l1.p + 1);
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
   Buf<int32_t> arow(ctx, A.nnzb);
