@@ -127,3 +127,22 @@ def test_tc_input_rounding_exact(ctx, prec):
     want = rounded(A, prec).val
     want = np.where(np.abs(want) < 2.0 ** -126, 0.0, want)
     assert np.array_equal(got.val, want)
+
+
+@pytest.mark.parametrize("prec", [TF32, BF16, 3])
+def test_tc_large_pattern_csr_lookups(ctx, prec):
+    """nb = 2188 block rows (nb^2 above the dense-map limit of 4M): the tile
+    plan finds blocks by binary search in the CSR patterns.  TF32/BF16 against
+    the rounded-input bound, the split product against the FP64 product."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(140000, 64, seed=9)
+    S = oracle.truncate(S, 1e-12)
+    S = synth.HostBSR(S.n, 64, S.row_ptr, S.col_idx, S.val)
+    dS = ifac.upload(ctx, S)
+    got = ifac.bsr_gemm_trunc(ctx, dS, True, dS, False, 1.0, 0.0, prec).download()
+    if prec == 3:
+        ref = oracle.gemm(S, S, True, False, 1.0, 0.0)
+        assert np.array_equal(got.col_idx, ref.col_idx) and np.array_equal(got.row_ptr, ref.row_ptr)
+        assert np.abs(got.val - ref.val).max() <= 1e-13 * np.abs(ref.val).max()
+    else:
+        _check(ctx, S, S, True, False, prec)
