@@ -227,15 +227,16 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       D = filter_rows_active(ctx, D.m, dseg.p, dactive.p);
       Sa = filter_rows_active(ctx, Sa.m, dseg.p, dactive.p);
       IFAC_CK(cudaStreamSynchronize(ctx->stream));  // the host flags are reused next sweep
-      Mat P = add(ctx, 0.5, D.m, 0.0, nullptr, 0.0);
-      {  // P = sum_{k=1}^{m} b_k delta^k
+      Mat P;
+      {  // P = sum_{k=1}^{m} b_k delta^k (first two terms in one sum)
         Mat Dk;
         double b = 0.5;
+        if (o.m < 2) P = add(ctx, 0.5, D.m, 0.0, nullptr, 0.0);
         for (int k = 2; k <= o.m; ++k) {
           b = b * (double)(2 * k - 1) / (double)(2 * k);
           Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec);
           Dk = std::move(Dn);
-          P = add(ctx, 1.0, P.m, b, &Dk.m, 0.0);
+          P = (k == 2) ? add(ctx, 0.5, D.m, b, &Dk.m, 0.0) : add(ctx, 1.0, P.m, b, &Dk.m, 0.0);
         }
       }
       D.reset();

@@ -25,11 +25,15 @@ static double coef_b(int k) {
 }
 
 // P = sum_{k=1}^{m} b_k delta^k, powers by successive truncated products
+// P = sum_{k=1}^{m} b_k delta^k, powers by truncated products.  The first two
+// terms are summed in one call, b_1 delta + b_2 delta^2, which rounds exactly
+// as (0 + b_1 delta) + b_2 delta^2 (b_1 = 1/2 scales exactly).
 static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int prec = IFAC_FP64) {
-  Mat P = add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
-  Mat D;
-  for (int k = 2; k <= m; ++k) {
-    Mat Dn = gemm(ctx, k == 2 ? delta : D.m, false, delta, false, 1.0, tau, prec);
+  if (m < 2) return add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
+  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec);
+  Mat P = add(ctx, coef_b(1), delta, coef_b(2), &D.m, 0.0);
+  for (int k = 3; k <= m; ++k) {
+    Mat Dn = gemm(ctx, D.m, false, delta, false, 1.0, tau, prec);
     D = std::move(Dn);
     P = add(ctx, 1.0, P.m, coef_b(k), &D.m, 0.0);
   }

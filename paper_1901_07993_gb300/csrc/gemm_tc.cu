@@ -837,7 +837,10 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
                             int32_t* __restrict__ rec, int32_t* __restrict__ nk_out, int* __restrict__ kmax) {
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (t >= *ntiles) return;
+  if (t >= *ntiles) {  // the grid covers an upper bound of the tile count
+    if (COUNT && lane == 0) nk_out[t] = 0;
+    return;
+  }
   const int I0 = tiles[2 * t] * ROWS, J0 = tiles[2 * t + 1] * COLS;
   int e = COUNT ? 0 : off[t];
   for (int wbase = 0; wbase < W; wbase += 32) {
@@ -910,7 +913,7 @@ struct Plan {
   Buf<int32_t> tiles, coff, tnk, off, rec;
   int nchunk = 0;
   int64_t ntot = 0;
-  int ntiles = 0;
+  int ntiles = 0;  // upper bound of the tile count (the count itself stays on the device)
   int kmax = 0;
 };
 
@@ -953,8 +956,9 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
   k_tile_write<<<P.nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, P.coff.p, P.tiles.p);
   IFAC_CK_LAUNCH();
   const int* ntiles = P.coff.p + P.nchunk;
-  int nt = 0;  // the per-tile kernels and arrays are sized by the tile count, not by all ntr x ntc positions
-  to_host(ctx, &nt, ntiles, sizeof(int));
+  // the per-tile kernels and arrays are sized by a bound of the tile count
+  // (every tile holds a block of C), not by all ntr x ntc positions
+  const int nt = (int)std::min<int64_t>(P.ntot, C.nnzb);
   P.ntiles = nt;
   P.tnk = Buf<int32_t>(ctx, (size_t)std::max(nt, 1));
   P.off = Buf<int32_t>(ctx, (size_t)nt + 1);
