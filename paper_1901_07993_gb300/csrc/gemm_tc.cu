@@ -265,6 +265,7 @@ struct TileArgs {
   const int32_t* tiles;      // [2*t] tile row, [2*t+1] tile column
   const int* ntiles;         // device: number of tiles
   const int* tile_nk;        // device: K steps of each tile
+  int nwin;                  // split mode: the largest number of K windows of a tile
   int nb;
   const int32_t* rec;        // plan: per K step, copy indices of op(A)_IK (super-tile rows) and op(B)_KJ
   const int32_t* rec_off;    // first record of each tile
@@ -350,8 +351,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
 
-  // number of K steps of tile t: size of the union of its super-tile rows' bitmaps
-  auto tile_nk = [&](int t) { return args.tile_nk[t]; };
+  // work items: this cluster's tiles (cid, cid + ncl, ...), in split mode once
+  // per K window, window-major: every cluster runs window w of its tiles before
+  // window w + 1, so the slices of one K range are shared through L2, while a
+  // tile's fixed-point sums are only ever updated by the one cluster that owns it
+  const int mt = ntiles > cid ? (ntiles - cid + ncl - 1) / ncl : 0;
+  const int nitems = mt * (args.split ? args.nwin : 1);
+  auto item = [&](int j, int& t, int& kb, int& cnt) -> bool {
+    t = cid + (j % mt) * ncl;
+    const int nk = args.tile_nk[t];
+    if (!args.split) {
+      kb = 0;
+      cnt = nk;
+      return cnt > 0;
+    }
+    kb = (j / mt) * KW;
+    if (kb >= nk) return false;
+    cnt = min(KW, nk - kb);
+    return true;
+  };
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
@@ -398,12 +416,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       return true;
     };
     constexpr int RECW = CL * TM + C::TN;  // plan record: op(A) rows of the super-tile, then op(B) columns
-    for (int t = cid; t < ntiles && ok; t += ncl) {
-      const int nk = args.tile_nk[t];
-      const int32_t* base = args.rec + (size_t)args.rec_off[t] * RECW;
+    for (int it = 0; it < nitems && ok; ++it) {
+      int t, kb, cnt;
+      if (!item(it, t, kb, cnt)) continue;
+      const int32_t* base = args.rec + (size_t)(args.rec_off[t] + kb) * RECW;
       if (!args.split) {
-        for (int k0 = 0; k0 < nk && ok; k0 += 32) {
-          const int n = min(32, nk - k0);
+        for (int k0 = 0; k0 < cnt && ok; k0 += 32) {
+          const int n = min(32, cnt - k0);
           if (lane < n) {
             const int32_t* r = base + (size_t)(k0 + lane) * RECW;
 #pragma unroll
@@ -418,20 +437,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           __syncwarp();
         }
       } else {
-        for (int kb = 0; kb < nk && ok; kb += KW) {
-          const int cnt = min(KW, nk - kb);
-          if (lane < cnt) {
-            const int32_t* r = base + (size_t)(kb + lane) * RECW;
+        if (lane < cnt) {
+          const int32_t* r = base + (size_t)lane * RECW;
 #pragma unroll
-            for (int i = 0; i < TM; ++i) wrec[lane][i] = r[(int)crank * TM + i];
+          for (int i = 0; i < TM; ++i) wrec[lane][i] = r[(int)crank * TM + i];
 #pragma unroll
-            for (int c = 0; c < C::TN; ++c) wrec[lane][TM + c] = r[CL * TM + c];
-          }
-          __syncwarp();
-          if (lane == 0) ok = issue_window(cnt);
-          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-          __syncwarp();
+          for (int c = 0; c < C::TN; ++c) wrec[lane][TM + c] = r[CL * TM + c];
         }
+        __syncwarp();
+        if (lane == 0) ok = issue_window(cnt);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        __syncwarp();
       }
     }
     // before the CTA exits: the copies lane 0 issued (and the peer's multicast
@@ -475,19 +491,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ++tl;
         return true;
       };
-      for (int t = cid; t < ntiles && ok; t += ncl) {
-        const int nk = tile_nk(t);
-        if (nk == 0) continue;  // (a tile holds a block of C's pattern, so nk >= 1)
+      for (int it = 0; it < nitems && ok; ++it) {
+        int t, kb, cnt;
+        if (!item(it, t, kb, cnt)) continue;  // (a tile holds a block of C's pattern, so nk >= 1)
         if (!args.split) {
-          ok = run_acc(nk);
+          ok = run_acc(cnt);
         } else {
-          for (int kb = 0; kb < nk && ok; kb += KW) {
-            const int cnt = min(KW, nk - kb);
-            int p = 0;
-            for (int u = 0; u < args.nunits && ok; ++u) {
-              ok = run_acc((s_unit_end[u] - p) * cnt);
-              p = s_unit_end[u];
-            }
+          int p = 0;
+          for (int u = 0; u < args.nunits && ok; ++u) {
+            ok = run_acc((s_unit_end[u] - p) * cnt);
+            p = s_unit_end[u];
           }
         }
       }
@@ -505,9 +518,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const float alpha_f = (float)args.alpha;
     int tl = 0;
     bool good = true;
-    for (int t = cid; t < ntiles && good; t += ncl) {
-      const int nk = tile_nk(t);
-      if (nk == 0) continue;
+    for (int it = 0; it < nitems && good; ++it) {
+      int t, kb, cnt;
+      if (!item(it, t, kb, cnt)) continue;
       const int I0 = (args.tiles[2 * t] * CL + (int)crank) * TM, J0 = args.tiles[2 * t + 1] * C::TN;
       const int I = I0 + r_blk;  // warp-uniform: a warp's 32 rows lie in one block row
       int pc[C::TN];             // position of C_{I, J0+c} in C, or -1
@@ -579,49 +592,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         epi_bar();
         if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
       } else {
-        // C_int += acc 2^sh_u, one hand-over per window and unit; C is held as
-        // 64-bit fixed point (scale 2^-f relative to sigma_i tau_j) until the
+        // C_int += acc 2^sh_u, one hand-over per unit of this window; C is held
+        // as 64-bit fixed point (scale 2^-f relative to sigma_i tau_j) until the
         // conversion after the kernel
-        for (int kb = 0; kb < nk && good; kb += KW) {
-          for (int u = 0; u < args.nunits; ++u) {
-            const int ab = tl & 1;
-            const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
-            ++tl;
-            const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
-            __syncwarp();
-            if (!__all_sync(0xffffffffu, got)) { good = false; break; }
-            tc_fence_after();
-            const int sh = s_unit_sh[u];
+        for (int u = 0; u < args.nunits; ++u) {
+          const int ab = tl & 1;
+          const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
+          ++tl;
+          const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
+          __syncwarp();
+          if (!__all_sync(0xffffffffu, got)) { good = false; break; }
+          tc_fence_after();
+          const int sh = s_unit_sh[u];
 #pragma unroll 1
-            for (int c = c0; c < c1; ++c) {
-              const int p = pc[c];
+          for (int c = c0; c < c1; ++c) {
+            const int p = pc[c];
 #pragma unroll
-              for (int h = 0; h < BS / 32; ++h) {
-                longlong2 dv[16];
-                longlong2* dst = args.cpart + (size_t)(p < 0 ? 0 : p) * (BS * BS / 2) +
-                                 (size_t)(((q & 1) * 2 + h) * 16) * 32 + lane;
-                if (p >= 0) {
+            for (int h = 0; h < BS / 32; ++h) {
+              longlong2 dv[16];
+              longlong2* dst = args.cpart + (size_t)(p < 0 ? 0 : p) * (BS * BS / 2) +
+                               (size_t)(((q & 1) * 2 + h) * 16) * 32 + lane;
+              if (p >= 0) {
 #pragma unroll
-                  for (int e = 0; e < 16; ++e) dv[e] = dst[e * 32];
+                for (int e = 0; e < 16; ++e) dv[e] = dst[e * 32];
+              }
+              float v[32];
+              tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
+              if (p >= 0) {
+                bool bad = false;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                  dv[e].x = fixed_add(dv[e].x, __float2int_rn(v[2 * e]), sh, bad);
+                  dv[e].y = fixed_add(dv[e].y, __float2int_rn(v[2 * e + 1]), sh, bad);
+                  dst[e * 32] = dv[e];
                 }
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
-                if (p >= 0) {
-                  bool bad = false;
-#pragma unroll
-                  for (int e = 0; e < 16; ++e) {
-                    dv[e].x = fixed_add(dv[e].x, __float2int_rn(v[2 * e]), sh, bad);
-                    dv[e].y = fixed_add(dv[e].y, __float2int_rn(v[2 * e + 1]), sh, bad);
-                    dst[e * 32] = dv[e];
-                  }
-                  if (bad) *args.ovf = 2;
-                }
+                if (bad) *args.ovf = 2;
               }
             }
-            tc_fence_before();
-            epi_bar();
-            if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
           }
+          tc_fence_before();
+          epi_bar();
+          if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
         }
       }
     }
@@ -1039,6 +1050,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.tiles = P.tiles.p;
   args.ntiles = P.coff.p + P.nchunk;  // the scan's total
   args.tile_nk = P.tnk.p;
+  args.nwin = 1;
   args.nb = nb;
   args.rec = P.rec.p;
   args.rec_off = P.off.p;
@@ -1378,6 +1390,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.tiles = P.tiles.p;
   args.ntiles = P.coff.p + P.nchunk;
   args.tile_nk = P.tnk.p;
+  args.nwin = cdiv(std::max(kmax, 1), KW);
   args.nb = nb;
   args.rec = P.rec.p;
   args.rec_off = P.off.p;
