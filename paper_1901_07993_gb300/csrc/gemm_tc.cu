@@ -1195,6 +1195,8 @@ static void row_scales(ifac_ctx* ctx, const int32_t* rp, const int32_t* src, int
 // has scale exponent sexp[sblk[qb] * BS + r].  With Y = x 2^(62 - e) held as a
 // 64-bit integer (|Y| < 2^62; bits below 2^-62 of sigma dropped by rounding),
 // digit k is q_k = round(Y_k / 2^(62 - 7k)), Y_{k+1} = Y_k - q_k 2^(62 - 7k).
+constexpr int SPLIT_TILE_BYTES = BS * (BS + 1) * (int)sizeof(double);
+
 __device__ __forceinline__ void split_digits(double x, int e, int ns, int (&q)[8]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int ea = (int)((u >> 52) & 0x7ff);
@@ -1223,7 +1225,8 @@ __global__ void __launch_bounds__(256) k_split(const double* __restrict__ val, c
                                                const int* __restrict__ sexp, int ns,
                                                __nv_bfloat16* __restrict__ dst) {
   constexpr int BSZ = BS * BS;
-  __shared__ double tile[BS][BS + 1];
+  extern __shared__ double tile_raw[];  // transposed views only: BS x (BS + 1) doubles
+  double(*tile)[BS + 1] = reinterpret_cast<double(*)[BS + 1]>(tile_raw);
   const size_t slice_stride = (size_t)(nblk + 1) * BSZ;
   for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
     const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
@@ -1356,12 +1359,12 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     IFAC_CK(cudaMemsetAsync(lb.p + ((size_t)k * (B.nnzb + 1) + B.nnzb) * bbytes, 0, bbytes, ctx->stream));
   }
   if (A.nnzb) {
-    k_split<<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
+    k_split<<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, tA ? SPLIT_TILE_BYTES : 0, ctx->stream>>>(
         A.val, arows.src, A.nnzb, tA ? 1 : 0, arow.p, sige.p, ns, reinterpret_cast<__nv_bfloat16*>(la.p));
     IFAC_CK_LAUNCH();
   }
   if (B.nnzb) {
-    k_split<<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
+    k_split<<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, tB ? 0 : SPLIT_TILE_BYTES, ctx->stream>>>(
         B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, taue.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
     IFAC_CK_LAUNCH();
   }
