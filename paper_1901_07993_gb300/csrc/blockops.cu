@@ -112,6 +112,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
     double* c = cval + (size_t)p * bsz;
     const bool dblk = I == J && gamma != 0.0;
     double ss = 0.0;
+#pragma unroll 4
     for (int e = lane * VEC; e < bsz; e += 32 * VEC) {
       if constexpr (VEC == 2) {
         double2 v;

@@ -306,19 +306,23 @@ __global__ void k_copy_blocks(const double* __restrict__ src, const int32_t* __r
   }
 }
 
-Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const uint8_t* keep) {
-  (void)row;
-  int nb = A.nb;
+// row pointers of the kept blocks (keep[p] = 1), returns their number
+static int64_t count_kept(ifac_ctx* ctx, const ifac_bsr& A, const uint8_t* keep, Buf<int32_t>& rp_new) {
+  const int nb = A.nb;
   Buf<int32_t> cnt(ctx, nb);
-  int grid = cdiv((int64_t)nb * 32, 256);
   if (A.nnzb > 0) {
-    k_row_keep_count<<<grid, 256, 0, ctx->stream>>>(A.row_ptr, nb, keep, cnt.p);
+    k_row_keep_count<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(A.row_ptr, nb, keep, cnt.p);
     IFAC_CK_LAUNCH();
   } else {
     IFAC_CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * nb, ctx->stream));
   }
-  Buf<int32_t> rp_new(ctx, nb + 1);
-  int64_t tot = scan_counts(ctx, cnt.p, rp_new.p, nb, true);
+  rp_new = Buf<int32_t>(ctx, nb + 1);
+  return scan_counts(ctx, cnt.p, rp_new.p, nb, true);
+}
+
+// a new matrix of the kept blocks of A, in order
+static Mat gather_kept(ifac_ctx* ctx, const ifac_bsr& A, const uint8_t* keep, Buf<int32_t>&& rp_new, int64_t tot) {
+  const int nb = A.nb;
   Mat R(ctx);
   R.m.n = A.n;
   R.m.bs = A.bs;
@@ -329,6 +333,7 @@ Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const ui
   R.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (tot ? tot : 1)));
   R.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(tot ? tot : 1) * A.bs * A.bs));
   if (A.nnzb > 0 && tot > 0) {
+    const int grid = cdiv((int64_t)nb * 32, 256);
     Buf<int32_t> dest(ctx, A.nnzb);
     k_row_keep_dest<<<grid, 256, 0, ctx->stream>>>(A.row_ptr, nb, keep, R.m.row_ptr, A.col_idx, A.norms,
                                                    R.m.col_idx, R.m.norms, dest.p);
@@ -340,14 +345,23 @@ Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const ui
   return R;
 }
 
+Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const uint8_t* keep) {
+  (void)row;
+  Buf<int32_t> rp_new;
+  const int64_t tot = count_kept(ctx, A, keep, rp_new);
+  return gather_kept(ctx, A, keep, std::move(rp_new), tot);
+}
+
 Mat compact(ifac_ctx* ctx, Mat&& full, const int32_t* row, double tau) {
+  (void)row;
   if (full.m.nnzb == 0 || !(tau > 0)) return std::move(full);
   Buf<uint8_t> keep(ctx, full.m.nnzb);
   k_keep_from_norms<<<cdiv(full.m.nnzb, 256), 256, 0, ctx->stream>>>(full.m.norms, full.m.nnzb, tau, keep.p);
   IFAC_CK_LAUNCH();
-  Mat R = select_blocks(ctx, full.m, row, keep.p);
-  if (R.m.nnzb == full.m.nnzb) return std::move(full);  // nothing dropped
-  return R;
+  Buf<int32_t> rp_new;
+  const int64_t tot = count_kept(ctx, full.m, keep.p, rp_new);
+  if (tot == full.m.nnzb) return std::move(full);  // nothing dropped: no copy
+  return gather_kept(ctx, full.m, keep.p, std::move(rp_new), tot);
 }
 
 }  // namespace ifac
