@@ -123,11 +123,9 @@ template <int BS>
 static void launch(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& bcols, bool tB,
                    const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, unsigned long long* pairs) {
   size_t smem = sizeof(double) * 2 * BS * BS;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(attr_set, ctx->device))
     IFAC_CK(cudaFuncSetAttribute(k_gemm_fp64<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   int per_sm = BS >= 64 ? 3 : 8;

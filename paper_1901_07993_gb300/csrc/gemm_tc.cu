@@ -1039,11 +1039,9 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false);
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
   IFAC_CK_LAUNCH();
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr, ctx->device))
     IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
-    attr = true;
-  }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   TileArgs args;
@@ -1079,12 +1077,15 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   cfg.attrs = attr_cl;
   cfg.numAttrs = 1;
   cfg.gridDim = dim3((unsigned)(sms / CL * CL), 1, 1);
-  static int max_clusters = 0;  // clusters of CL CTAs that fit at once (GPC boundaries)
+  static int max_clusters_dev[64] = {};  // clusters of CL CTAs that fit at once (GPC boundaries), per device
+  int& max_clusters = max_clusters_dev[ctx->device & 63];
   if (!max_clusters) {
-    if (cudaOccupancyMaxActiveClusters(&max_clusters, k_gemm_tc<ELT>, &cfg) != cudaSuccess || max_clusters < 1) {
+    int mc = 0;
+    if (cudaOccupancyMaxActiveClusters(&mc, k_gemm_tc<ELT>, &cfg) != cudaSuccess || mc < 1) {
       cudaGetLastError();
-      max_clusters = sms / CL;
+      mc = sms / CL;
     }
+    max_clusters = mc;
   }
   const int64_t clusters = std::min<int64_t>(std::max(P.ntiles, 1), max_clusters);
   cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
@@ -1382,11 +1383,9 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   to_host(ctx, l1h, l1.p, sizeof(l1h));
   Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
   IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr, ctx->device))
     IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
-    attr = true;
-  }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   TileArgs args;

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <utility>
@@ -158,6 +159,12 @@ double fro_host(ifac_ctx* ctx, const ifac_bsr& A);
 double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
 // sum_j |A_ij| for every scalar row i (nb * bs values)
 int delta_prec_of(const ifac_opts& o, int bs);
+// true the first time it is called with this flag word for `device` (per
+// process): per-device one-time settings such as kernel attributes
+inline bool first_on_device(std::atomic<unsigned long long>& seen, int device) {
+  const unsigned long long bit = 1ull << (device & 63);
+  return !(seen.fetch_or(bit) & bit);
+}
 // driver report: counters reset at entry, filled (with the device counters) at exit
 void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o);
 void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z);
