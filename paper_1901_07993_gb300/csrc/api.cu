@@ -151,9 +151,18 @@ using namespace ifac;
 template <typename F>
 static int guarded(ifac_ctx* ctx, F&& f) {
   if (!ctx) return IFAC_ERR_INVALID;
+  // run on the context's device; the caller's current device is restored on return
+  struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+      if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+      else prev = -1;
+    }
+    ~DeviceScope() {
+      if (prev >= 0) cudaSetDevice(prev);
+    }
+  } scope(ctx->device);
   try {
-    int prev;
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != ctx->device) cudaSetDevice(ctx->device);
     int rc = f();
     if (rc != 0) {
       if (ctx->err.empty()) ctx->err = "status " + std::to_string(rc);
