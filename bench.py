@@ -91,6 +91,12 @@ WORKLOADS = {
     "table1-paper-settings": dict(geom="pair", n=0, bs=32, tau=1e-5, target=0.0, method="table1", m=4,
                                   seed=0, leaf=512, prec="fp64", compare=(), sample_n=None,
                                   cases=(("chain", 65536, 4096), ("cluster", 16384, 2048))),
+    # the config-2 recipe (3D cluster, LIF, 512-row leaves, tau 1e-10) at
+    # n = 8192 in BSR 64x64 with every product on the split FP64-accurate
+    # tensor-core kernel (the FP64 pipe needs seconds at n = 4096 already)
+    "lif-split-cluster-n8192-bs64": dict(geom="cluster", n=8192, bs=64, tau=1e-10, target=1e-10,
+                                         method="localized", m=2, seed=0, leaf=512, prec="split", compare=(),
+                                         sample_n=None),
     # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
