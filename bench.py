@@ -96,7 +96,7 @@ WORKLOADS = {
     # tensor-core kernel (the FP64 pipe needs seconds at n = 4096 already)
     "lif-split-cluster-n8192-bs64": dict(geom="cluster", n=8192, bs=64, tau=1e-10, target=1e-10,
                                          method="localized", m=2, seed=0, leaf=512, prec="split", compare=(),
-                                         sample_n=None),
+                                         sample_n=1024, cost_exp=3),
     # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
@@ -237,13 +237,16 @@ def oracle_factorize(S, w):
 
 def cpu_sample(w):
     """The input the CPU oracle factorizes, and the factor that turns its rate
-    into the workload's: the workload itself, or (for the large chain) the
-    same construction at sample_n rows, whose cost is n/sample_n times smaller
-    (the chain's factorization cost is linear in n)."""
+    into the workload's: the workload itself, or the same construction at
+    sample_n rows, whose cost is (n/sample_n)^p times smaller -- p = 1 for the
+    chain (banded factors), p = 3 for the 3D clusters (block-dense factors)."""
     if w.get("sample_n"):
-        return make_input(w, w["sample_n"]), w["sample_n"] / w["n"], \
+        p = w.get("cost_exp", 1)
+        scale = (w["sample_n"] / w["n"]) ** p
+        return make_input(w, w["sample_n"]), scale, \
             (f"complete FP64 factorizations of the same construction at n = {w['sample_n']} "
-             f"(block rows 1/{w['n'] // w['sample_n']} of the workload), rate scaled by {w['sample_n']}/{w['n']}")
+             f"(block rows 1/{w['n'] // w['sample_n']} of the workload), rate scaled by "
+             f"({w['sample_n']}/{w['n']})^{p}")
     return make_input(w), 1.0, "complete FP64 factorizations of the same workload"
 
 
