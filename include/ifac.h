@@ -208,13 +208,17 @@ void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a);
  * zero), products are accumulated in
  * FP32 on the tensor cores, and the result, its norms and the truncation are
  * FP64.  IFAC_FP64_SPLIT (bs = 64): an FP64-accurate product on the tensor
- * cores: each scalar row of op(A) and column of op(B) is scaled by a power of
- * two and split into 7 slices of 7-bit integers held exactly in BF16; slice
- * products accumulate exactly in FP32 over windows of 16 K blocks and are
- * added, scaled, into the FP64 result (pairs of slice orders s + t <= 8).
- * Element error <= about 2^-45 K_ij max_k|op(A)_ik| max_k|op(B)_kj| plus FP64
- * rounding of the partial sums.  IFAC_ERR_TIMEOUT if a device pipeline wait
- * expired. */
+ * cores (error-free splitting, Ozaki et al. 2012): each scalar row i of op(A)
+ * and column j of op(B) is scaled by a power of two sigma_i, tau_j above its
+ * largest magnitude and split into s slices of 7-bit integers held exactly in
+ * BF16 (s = 7 unless ifac_set_split_slices); slice products accumulate
+ * exactly in FP32 over windows of 16 K blocks, pairs of slice orders
+ * s_a + s_b <= s + 1, and are summed in 64-bit fixed point at 2^-f sigma_i
+ * tau_j, f <= 56 chosen so that no partial sum can overflow; the result is
+ * converted to FP64 once.  Element error about 2^-(7 s - 3) K_ij sigma_i tau_j
+ * (2^-46 for s = 7) plus 2^-f sigma_i tau_j per window.  IFAC_ERR_TIMEOUT if
+ * a device pipeline wait expired; IFAC_ERR_CUDA if a fixed-point sum
+ * overflowed (not expected: the scale is bounded from the operands). */
 int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB,
                    double alpha, double tau, int prec, ifac_bsr* C);
 
