@@ -221,14 +221,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// FP32 -> FP64 by moving the fields (exact; zero, subnormals, inf and NaN
-// take the conversion instruction), keeping the epilogue off the FP64 pipe
+// FP32 -> FP64 by moving the fields (exact, subnormals normalised; inf and
+// NaN take the conversion instruction), keeping the epilogue off the FP64 pipe
 __device__ __forceinline__ double f32_to_f64(float f) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t ex = (u >> 23) & 0xffu;
-  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  if (ex == 0u || ex == 0xffu) return (double)f;
-  const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const uint32_t sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+  if (ex == 0xffu) return (double)f;  // inf, NaN
+  if (ex == 0u) {
+    if (man == 0u) return __hiloint2double((int)sign, 0);
+    // subnormal: man 2^-149 with man < 2^23, normal in FP64
+    const int len = 32 - __clz((int)man);                       // bit length, 1..23
+    const uint32_t e64 = (uint32_t)(len - 1 - 149 + 1023);      // exponent field
+    const unsigned long long m52 = ((unsigned long long)man << (53 - len)) & 0xfffffffffffffull;
+    return __hiloint2double((int)(sign | (e64 << 20) | (uint32_t)(m52 >> 32)), (int)(uint32_t)m52);
+  }
+  const uint32_t hi = sign | ((ex + 896u) << 20) | (man >> 3);
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
