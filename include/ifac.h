@@ -222,6 +222,18 @@ void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a);
 int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB,
                    double alpha, double tau, int prec, ifac_bsr* C);
 
+/* The same product for a result the caller knows to be symmetric, such as
+ * Z^T (S Z) with S symmetric (delta = I - Z^T S Z, Eq. 2.1) or delta delta:
+ * only the output blocks (I, J) with J >= I are formed (same pattern rule,
+ * arithmetic and truncation as bsr_gemm_trunc) and block (J, I) is set to the
+ * transpose of block (I, J); a diagonal block is the product's own
+ * (symmetric up to rounding).  Nothing checks that op(A) op(B) is symmetric:
+ * otherwise the strict lower triangle is simply the transposed upper one.
+ * bs = 64 (IFAC_ERR_UNSUPPORTED otherwise); the other arguments, ownership
+ * and errors as bsr_gemm_trunc. */
+int bsr_gemm_sym_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB,
+                       double alpha, double tau, int prec, ifac_bsr* C);
+
 /* C = alpha A + beta B + gamma I on the union pattern (B may be NULL; the
  * diagonal blocks are added when gamma != 0).  No truncation: the paper
  * truncates after products and leaf routines only (Section 5). */

@@ -318,6 +318,26 @@ int bsr_gemm_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr*
   });
 }
 
+int bsr_gemm_sym_trunc(ifac_ctx* ctx, const ifac_bsr* A, int transA, const ifac_bsr* B, int transB, double alpha,
+                       double tau, int prec, ifac_bsr* C) {
+  if (C) *C = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(A, "A");
+    validate(B, "B");
+    check_pair(A, B);
+    if (!C) fail(IFAC_ERR_INVALID, "C is NULL");
+    if (prec != IFAC_FP64 && prec != IFAC_TF32 && prec != IFAC_BF16 && prec != IFAC_FP64_SPLIT)
+      fail(IFAC_ERR_INVALID, "unknown precision");
+    if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
+    if (A->bs != 64) fail(IFAC_ERR_UNSUPPORTED, "symmetric product built for bs = 64");
+    Mat U = ifac::gemm(ctx, *A, transA != 0, *B, transB != 0, alpha, tau, prec, true);
+    Mat R = ifac::sym_sum(ctx, 1.0, U.m, 0.0, nullptr, 0.0);
+    check_device_error(ctx);
+    *C = R.release();
+    return IFAC_OK;
+  });
+}
+
 int bsr_add(ifac_ctx* ctx, double alpha, const ifac_bsr* A, double beta, const ifac_bsr* B, double gamma, ifac_bsr* C) {
   if (C) *C = ifac_bsr{};
   return guarded(ctx, [&]() -> int {

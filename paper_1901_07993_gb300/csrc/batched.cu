@@ -177,10 +177,14 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
     }
     const int pd = stage == 0 ? o.prec : dprec;
     for (int it = 0;; ++it) {
-      Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd);   // S Z
-      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd);     // Z^T (S Z)
+      // with low-precision sweeps, the upper block triangle of the symmetric
+      // Z^T S Z is formed and the lower one taken from it
+      const bool sym = low;
+      Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd);        // S Z
+      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym);     // Z^T (S Z)
       X.reset();
-      Mat Dall = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);          // I - Z^T S Z
+      Mat Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0)      // I - Z^T S Z
+                     : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
       Y.reset();
       IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
       Mat D = filter_rows_active(ctx, Dall.m, dseg.p, dactive.p);
@@ -234,7 +238,12 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         if (o.m < 2) P = add(ctx, 0.5, D.m, 0.0, nullptr, 0.0);
         for (int k = 2; k <= o.m; ++k) {
           b = b * (double)(2 * k - 1) / (double)(2 * k);
-          Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec);
+          Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec, low);
+          if (low && k == 2 && o.m == 2) {  // delta^2 completed by symmetry inside the sum
+            P = sym_sum(ctx, b, Dn.m, 0.5, &D.m, 0.0);
+            break;
+          }
+          if (low) Dn = sym_sum(ctx, 1.0, Dn.m, 0.0, nullptr, 0.0);
           Dk = std::move(Dn);
           P = (k == 2) ? add(ctx, 0.5, D.m, b, &Dk.m, 0.0) : add(ctx, 1.0, P.m, b, &Dk.m, 0.0);
         }

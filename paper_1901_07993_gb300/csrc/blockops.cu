@@ -150,6 +150,99 @@ void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, co
   IFAC_CK_LAUNCH();
 }
 
+// C = alpha (U + strict_upper(U)^T) + beta B + gamma I, one warp per output
+// block.  Block (I, J), J >= I, is add_elem of alpha U_IJ and beta B_IJ;
+// block (I, J), J < I, takes alpha U_JI^T in place of alpha U_IJ, moved
+// through shared memory in stripes of four output rows (four 32-byte column
+// segments of U_JI per source row), so reads and writes are whole sectors.
+// bs = 64.
+constexpr int SYM_WARPS = 8;
+
+__global__ void __launch_bounds__(32 * SYM_WARPS)
+    k_sym(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t cnnz, Scale sa,
+          const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval, Scale sb,
+          const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bval,
+          double gamma, double* __restrict__ cval, double* __restrict__ cnorm) {
+  constexpr int BS = 64, BSZ = BS * BS;
+  __shared__ double stripe[SYM_WARPS][4][BS + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double(*st)[BS + 1] = stripe[wid];
+  for (int64_t p = w0; p < cnnz; p += nw) {
+    const int I = crow[p], J = cci[p];
+    const bool lower = J < I;
+    const int r = lower ? J : I, c = lower ? I : J;
+    int qu = -1, qb = -1;
+    if (lane == 0) {
+      const int k = find_col(uci, urp[r], urp[r + 1], c);
+      qu = (k < urp[r + 1] && uci[k] == c) ? k : -1;
+      if (bval) {
+        const int m = find_col(bci, brp[I], brp[I + 1], J);
+        qb = (m < brp[I + 1] && bci[m] == J) ? m : -1;
+      }
+    }
+    qu = __shfl_sync(0xffffffffu, qu, 0);
+    qb = __shfl_sync(0xffffffffu, qb, 0);
+    const double* u = qu >= 0 ? uval + (size_t)qu * BSZ : nullptr;
+    const double* b = qb >= 0 ? bval + (size_t)qb * BSZ : nullptr;
+    double* out = cval + (size_t)p * BSZ;
+    const bool dblk = I == J && gamma != 0.0;
+    double ss = 0.0;
+    if (!lower || !u) {
+#pragma unroll 4
+      for (int e = lane * 2; e < BSZ; e += 64) {
+        double2 v;
+        v.x = add_elem(sa, lower ? nullptr : u, sb, b, dblk && e / BS == e % BS, gamma, e);
+        v.y = add_elem(sa, lower ? nullptr : u, sb, b, dblk && (e + 1) / BS == (e + 1) % BS, gamma, e + 1);
+        *reinterpret_cast<double2*>(out + e) = v;
+        ss = fma(v.x, v.x, ss);
+        ss = fma(v.y, v.y, ss);
+      }
+    } else {
+      for (int r0 = 0; r0 < BS; r0 += 4) {
+        // alpha U_JI, source rows s = 0..63, columns r0..r0+3
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int idx = k * 32 + lane, s = idx >> 2, j = idx & 3;
+          st[j][s] = scaled(sa, u[s * BS + r0 + j]);
+        }
+        __syncwarp();
+        // output rows r0..r0+3: alpha U_JI^T (+ beta B_IJ), columns 0..63
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int idx = k * 64 + lane * 2, j = idx >> 6, col = idx & 63, e = (r0 + j) * BS + col;
+          double2 v;
+          v.x = st[j][col];
+          v.y = st[j][col + 1];
+          if (b) {
+            v.x = __dadd_rn(v.x, scaled(sb, b[e]));
+            v.y = __dadd_rn(v.y, scaled(sb, b[e + 1]));
+          }
+          *reinterpret_cast<double2*>(out + e) = v;
+          ss = fma(v.x, v.x, ss);
+          ss = fma(v.y, v.y, ss);
+        }
+        __syncwarp();
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) cnorm[p] = sqrt(ss);
+  }
+}
+
+void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
+                 ifac_bsr& C, const int32_t* crow) {
+  if (C.nnzb == 0) return;
+  if (U.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "symmetric completion needs bs = 64");
+  const int64_t ctas = std::min<int64_t>(cdiv(C.nnzb, SYM_WARPS), 152 * 8);
+  k_sym<<<(int)ctas, 32 * SYM_WARPS, 0, ctx->stream>>>(
+      crow, C.col_idx, C.nnzb, make_scale(alpha), U.row_ptr, U.col_idx, U.val, make_scale(beta),
+      B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr, gamma, C.val, C.norms);
+  IFAC_CK_LAUNCH();
+}
+
 __global__ void k_block_norms(const double* __restrict__ val, int64_t nnzb, int bsz, double* __restrict__ norms) {
   __shared__ double red[32];
   for (int64_t p = blockIdx.x; p < nnzb; p += gridDim.x) {

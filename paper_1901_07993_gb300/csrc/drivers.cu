@@ -24,16 +24,21 @@ static double coef_b(int k) {
   return b;
 }
 
-// P = sum_{k=1}^{m} b_k delta^k, powers by successive truncated products
 // P = sum_{k=1}^{m} b_k delta^k, powers by truncated products.  The first two
 // terms are summed in one call, b_1 delta + b_2 delta^2, which rounds exactly
-// as (0 + b_1 delta) + b_2 delta^2 (b_1 = 1/2 scales exactly).
-static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int prec = IFAC_FP64) {
+// as (0 + b_1 delta) + b_2 delta^2 (b_1 = 1/2 scales exactly).  sym: delta is
+// symmetric, and each power (a polynomial in delta, so symmetric too) is formed
+// on its upper block triangle only and completed by symmetry.
+static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int prec = IFAC_FP64,
+                  bool sym = false) {
   if (m < 2) return add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
-  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec);
+  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym);
+  if (sym && m == 2) return sym_sum(ctx, coef_b(2), D.m, coef_b(1), &delta, 0.0);
+  if (sym) D = sym_sum(ctx, 1.0, D.m, 0.0, nullptr, 0.0);
   Mat P = add(ctx, coef_b(1), delta, coef_b(2), &D.m, 0.0);
   for (int k = 3; k <= m; ++k) {
-    Mat Dn = gemm(ctx, D.m, false, delta, false, 1.0, tau, prec);
+    Mat Dn = gemm(ctx, D.m, false, delta, false, 1.0, tau, prec, sym);
+    if (sym) Dn = sym_sum(ctx, 1.0, Dn.m, 0.0, nullptr, 0.0);
     D = std::move(Dn);
     P = add(ctx, 1.0, P.m, coef_b(k), &D.m, 0.0);
   }
@@ -171,10 +176,12 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
   int stop = 0, sweeps = 0, fp64_evals = 0, low_sweeps = 0;
   for (int it = 0;; ++it) {
     const int dprec = fp64_phase ? delta_prec_of(o, S.m.bs) : low;
-    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec);   // S Z
-    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec);    // Z^T (S Z)
+    // Z^T S Z is symmetric: its upper block triangle is formed and the
+    // lower one taken from it, halving the second product
+    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec);         // S Z
+    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true);    // Z^T (S Z), J >= I
     X.reset();
-    Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);               // I - Z^T S Z
+    Mat D = sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);                 // I - Z^T S Z
     Y.reset();
     e = fro_host(ctx, D.m);
     if (rep && rep->n_delta < 64) rep->delta_fro[rep->n_delta++] = e;
@@ -195,7 +202,7 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       --it;
       continue;
     }
-    Mat P = poly_P(ctx, D.m, o.m, tau, low);
+    Mat P = poly_P(ctx, D.m, o.m, tau, low, true);
     D.reset();
     Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low);      // M = Z sum b_k delta^k
     P.reset();

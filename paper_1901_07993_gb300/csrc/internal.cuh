@@ -128,10 +128,14 @@ struct Pattern {
   int64_t nnzb = 0;
 };
 Pattern pattern_from_bitmap(ifac_ctx* ctx, const uint32_t* bm, int nb);
-// Symbolic product pattern of op(A) op(B).
-Pattern product_pattern(ifac_ctx* ctx, const View& arows, const ifac_bsr& B, bool transB, int nb);
+// Symbolic product pattern of op(A) op(B); upper: only the blocks (I, J)
+// with J >= I.
+Pattern product_pattern(ifac_ctx* ctx, const View& arows, const ifac_bsr& B, bool transB, int nb,
+                        bool upper = false);
 // Union pattern of A, B (nullable) and the diagonal (if diag).
 Pattern union_pattern(ifac_ctx* ctx, const ifac_bsr& A, const ifac_bsr* B, bool diag);
+// Pattern of U + U^T, B (nullable) and the diagonal (if diag).
+Pattern sym_pattern(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr* B, bool diag);
 // Expand row_ptr to a per-block row index.
 void expand_rows(ifac_ctx* ctx, const int32_t* rp, int nb, int32_t* row);
 // Keep blocks with !(norm < tau) of an (uncompacted) matrix; returns the compacted one.
@@ -152,12 +156,15 @@ void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const 
                      unsigned long long* pairs_dev);
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
                  double gamma, ifac_bsr& C, const int32_t* crow);
+// C = alpha (U + strict_upper(U)^T) + beta B + gamma I on the pattern of sym_pattern
+void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
+                 ifac_bsr& C, const int32_t* crow);
 void block_norms(ifac_ctx* ctx, const ifac_bsr& A, double* norms);
 // per block-row sum of squared block norms
 void row_sq_norms(ifac_ctx* ctx, const ifac_bsr& A, double* rowsq);
 double fro_host(ifac_ctx* ctx, const ifac_bsr& A);
 double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
-// sum_j |A_ij| for every scalar row i (nb * bs values)
+// precision of the FP64-accurate delta evaluations of the mixed schedule
 int delta_prec_of(const ifac_opts& o, int bs);
 // true the first time it is called with this flag word for `device` (per
 // process): per-device one-time settings such as kernel attributes
@@ -176,13 +183,18 @@ int rinch(ifac_ctx* ctx, const ifac_bsr& S, double tau, const ifac_opts& o, ifac
 // recursive inverse Cholesky of the disjoint ranges [first, second) of S together
 Mat rinch_ranges(ifac_ctx* ctx, const ifac_bsr& S, const std::vector<std::pair<int, int>>& ranges, double tau,
                  int leaf_size, int* levels);
+// sum_j |A_ij| for every scalar row i (nb * bs values)
 void gershgorin_rows(ifac_ctx* ctx, const ifac_bsr& A, double* rs);
 Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 
 // ---- operations used by drivers (ops.cu) ----
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec = IFAC_FP64);
+         int prec = IFAC_FP64, bool upper = false);
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma);
+// the symmetric matrix whose upper block triangle (J >= I) is held by U,
+// times alpha, plus beta B and gamma I: alpha (U + strict_upper(U)^T) +
+// beta B + gamma I, rounded as add() rounds alpha A + beta B + gamma I
+Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma);
 Mat truncate(ifac_ctx* ctx, const ifac_bsr& A, double tau);
 Mat copy_mat(ifac_ctx* ctx, const ifac_bsr& A);
 void validate(const ifac_bsr* A, const char* name);

@@ -8,12 +8,14 @@ namespace ifac {
 // C = alpha op(A) op(B), then removal of blocks with norm < tau.
 //   rows of op(A): A's own rows, or the rows of A^T (blocks then used transposed)
 //   columns of op(B): rows of B^T when B is used as is, or B's rows when B^T
+//   upper: only the blocks (I, J) with J >= I are formed (a product known to
+//   be symmetric, completed by sym_sum)
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec) {
+         int prec, bool upper) {
   const int nb = A.nb;
   if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && A.bs == 64) prec = IFAC_FP64_SPLIT;
   View arows = view_rows(ctx, A, tA);
-  Pattern P = product_pattern(ctx, arows, B, tB, nb);
+  Pattern P = product_pattern(ctx, arows, B, tB, nb, upper);
   Mat C(ctx);
   C.m.n = A.n;
   C.m.bs = A.bs;
@@ -35,6 +37,21 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   Mat R = compact(ctx, std::move(C), P.row.p, tau);
   ctx->products += 1;
   return R;
+}
+
+Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma) {
+  Pattern P = sym_pattern(ctx, U, B, gamma != 0.0);
+  Mat C(ctx);
+  C.m.n = U.n;
+  C.m.bs = U.bs;
+  C.m.nb = U.nb;
+  C.m.nnzb = P.nnzb;
+  C.m.row_ptr = P.rp.release();
+  C.m.col_idx = P.ci.release();
+  C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * U.bs * U.bs));
+  C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
+  sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p);
+  return C;
 }
 
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma) {

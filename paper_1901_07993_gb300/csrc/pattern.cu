@@ -208,12 +208,25 @@ __global__ void k_product_rows(const int32_t* __restrict__ arp, const int32_t* _
   }
 }
 
-Pattern product_pattern(ifac_ctx* ctx, const View& arows, const ifac_bsr& B, bool transB, int nb) {
+// keep the bits of row i at columns j >= i (the upper block triangle)
+__global__ void k_bitmap_upper(int nb, int W, uint32_t* __restrict__ bm) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nb * W) return;
+  const int i = (int)(e / W), w = (int)(e % W);
+  if (w < (i >> 5)) bm[e] = 0u;
+  else if (w == (i >> 5)) bm[e] &= ~((1u << (i & 31)) - 1u);
+}
+
+Pattern product_pattern(ifac_ctx* ctx, const View& arows, const ifac_bsr& B, bool transB, int nb, bool upper) {
   int W = words_per_row(nb);
   Buf<uint32_t> bmB = pattern_bitmap(ctx, B, transB);
   Buf<uint32_t> bmC(ctx, (size_t)nb * W);
   k_product_rows<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, W, bmB.p, bmC.p);
   IFAC_CK_LAUNCH();
+  if (upper) {
+    k_bitmap_upper<<<cdiv((int64_t)nb * W, 256), 256, 0, ctx->stream>>>(nb, W, bmC.p);
+    IFAC_CK_LAUNCH();
+  }
   return pattern_from_bitmap(ctx, bmC.p, nb);
 }
 
@@ -229,6 +242,24 @@ Pattern union_pattern(ifac_ctx* ctx, const ifac_bsr& A, const ifac_bsr* B, bool 
     Buf<uint32_t> bb = pattern_bitmap(ctx, *B, false);
     size_t n = (size_t)nb * W;
     k_or_into<<<cdiv(n, 256), 256, 0, ctx->stream>>>(bm.p, bb.p, n);
+    IFAC_CK_LAUNCH();
+  }
+  if (diag) {
+    k_bitmap_diag<<<cdiv(nb, 256), 256, 0, ctx->stream>>>(nb, W, bm.p);
+    IFAC_CK_LAUNCH();
+  }
+  return pattern_from_bitmap(ctx, bm.p, nb);
+}
+
+Pattern sym_pattern(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr* B, bool diag) {
+  int nb = U.nb, W = words_per_row(nb);
+  Buf<uint32_t> bm = pattern_bitmap(ctx, U, false);
+  if (U.nnzb > 0) {
+    k_bitmap<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(U.row_ptr, U.col_idx, nb, W, 1, bm.p);
+    IFAC_CK_LAUNCH();
+  }
+  if (B && B->nnzb > 0) {
+    k_bitmap<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(B->row_ptr, B->col_idx, nb, W, 0, bm.p);
     IFAC_CK_LAUNCH();
   }
   if (diag) {

@@ -5,9 +5,9 @@ arguments, owns the returned device matrices (freed with ifac_bsr_free) and
 raises IfacError on negative status codes.  It never falls back to another
 implementation: if the library is missing, loading raises.
 
-Function names follow the C ABI: bsr_gemm_trunc, bsr_add, bsr_truncate,
-bsr_fro, bsr_gershgorin, leaf_invchol_batched, inv_factor_refine,
-inv_factor_localized, inv_factor_resid.
+Function names follow the C ABI: bsr_gemm_trunc, bsr_gemm_sym_trunc, bsr_add,
+bsr_truncate, bsr_fro, bsr_gershgorin, leaf_invchol_batched,
+inv_factor_refine, inv_factor_localized, inv_factor_rinch, inv_factor_resid.
 """
 from __future__ import annotations
 
@@ -28,8 +28,8 @@ FP64 = 0
 STOP_RULE, STOP_TARGET, STOP_MAXITER, STOP_FIXED = 1, 2, 3, 4
 
 EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", "ifac_opts_default",
-           "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_add",
-           "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
+           "ifac_bsr_upload", "ifac_bsr_download", "ifac_bsr_free", "bsr_gemm_trunc", "bsr_gemm_sym_trunc",
+           "bsr_add", "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
            "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
            "inv_factor_refine_adjoint", "inv_factor_refine_batched", "ifac_set_split_slices",
            "inv_factor_rinch")
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "ifac_bsr_download": ([p, PB, p, p, p], i32),
         "ifac_bsr_free": ([p, PB], None),
         "bsr_gemm_trunc": ([p, PB, i32, PB, i32, d, d, i32, PB], i32),
+        "bsr_gemm_sym_trunc": ([p, PB, i32, PB, i32, d, d, i32, PB], i32),
         "bsr_add": ([p, d, PB, d, PB, d, PB], i32),
         "bsr_truncate": ([p, PB, d, PB], i32),
         "bsr_fro": ([p, PB, ctypes.POINTER(d)], i32),
@@ -271,6 +272,14 @@ def bsr_gemm_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, trans
     C = _Bsr()
     ctx.check(ctx.lib.bsr_gemm_trunc(ctx.h, A.ptr(), int(transA), B.ptr(), int(transB), alpha, tau, prec,
                                      ctypes.byref(C)))
+    return DeviceBSR(ctx, C)
+
+
+def bsr_gemm_sym_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, transB: bool, alpha: float = 1.0,
+                       tau: float = 0.0, prec: int = FP64) -> DeviceBSR:
+    C = _Bsr()
+    ctx.check(ctx.lib.bsr_gemm_sym_trunc(ctx.h, A.ptr(), int(transA), B.ptr(), int(transB), alpha, tau, prec,
+                                         ctypes.byref(C)))
     return DeviceBSR(ctx, C)
 
 
