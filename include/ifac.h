@@ -154,6 +154,10 @@ typedef struct {
   int64_t split_launches; /* FP64-accurate split tensor-core block-product launches */
   double split_ms;     /* their summed device time (opts.profile != 0) */
   int64_t split_pairs; /* stored block pairs multiplied by them */
+  int64_t split_slice_pairs; /* sum over those block pairs of the BF16 slice
+                                pairs each took: s (s + 1) / 2 with s slices
+                                per operand (the mixed schedule lowers s for
+                                early delta evaluations) */
 } ifac_report;
 
 /* ---------------------------------------------------------------- */
@@ -165,11 +169,13 @@ typedef struct {
 int ifac_create(ifac_ctx** ctx, void* stream, const ifac_allocator* alloc);
 void ifac_destroy(ifac_ctx* ctx);
 int ifac_set_stream(ifac_ctx* ctx, void* stream);
-/* Slices per operand of the context's IFAC_FP64_SPLIT products, 4..8
+/* Slices per operand of the context's IFAC_FP64_SPLIT products, 3..8
  * (default 7): s slices keep about 7 s bits of every scaled row and column,
  * the product uses the s (s + 1) / 2 slice pairs with s_a + s_b <= s + 1,
  * and the element error is about 2^-(7 s - 3) K max|op(A)_i.| max|op(B)_.j|.
- * IFAC_ERR_INVALID outside 4..8. */
+ * IFAC_ERR_INVALID outside 3..8.  The mixed-precision refinement takes this
+ * count as its maximum and uses fewer slices for delta evaluations whose
+ * result only needs to resolve the next sweep (see inv_factor_refine). */
 int ifac_set_split_slices(ifac_ctx* ctx, int slices);
 const char* ifac_last_error(const ifac_ctx* ctx);
 void ifac_opts_default(ifac_opts* opts);
@@ -309,7 +315,18 @@ int leaf_invchol_batched_noalloc(void* stream, int count, int nl, const double* 
  * ||delta||_F <= target or when ||delta||_F no longer decreases.  The returned
  * Z is the last one whose delta was evaluated with FP64 products.  With low-
  * precision corrections Z converges to an inverse factor S^-1/2 Q with Q close
- * to orthogonal, not to S^-1/2 itself. */
+ * to orthogonal, not to S^-1/2 itself.  In the mixed schedule Z^T (S Z) and
+ * delta^k are formed on their upper block triangle and completed by symmetry
+ * (as bsr_gemm_sym_trunc).  With split FP64-accurate evaluations
+ * (opts->delta_prec = IFAC_FP64_SPLIT) each evaluation takes the fewest
+ * slices s (at least 3, at most the context's count) whose error level
+ * 2^-(7 s - 3) sqrt(n) is at most max(target, u e) / 10, with u the low
+ * format's unit roundoff (TF32 2^-11, BF16 2^-8) and e the predicted
+ * ||delta||_F: a tenth of the last low-precision value for the first, u times
+ * the previous value after that (a sweep with low-precision M reduces
+ * ||delta||_F by about u).  An evaluation whose own ||delta||_F shows that it
+ * needed more slices is repeated with all of them, so the error stays below
+ * a tenth of the target at the stop test. */
 int inv_factor_refine(ifac_ctx* ctx, const ifac_bsr* S, double tau, double target,
                       const ifac_opts* opts, ifac_bsr* Z, ifac_report* rep);
 

@@ -122,16 +122,18 @@ void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc, double* ms_spli
 }
 
 void reset_device_counters(ifac_ctx* ctx) {
-  IFAC_CK(cudaMemsetAsync(ctx->dev_pairs, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  IFAC_CK(cudaMemsetAsync(ctx->dev_pairs, 0, 4 * sizeof(unsigned long long), ctx->stream));
 }
 
-void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc, int64_t* pairs_split) {
-  unsigned long long h[3] = {0, 0, 0};
+void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc, int64_t* pairs_split,
+                          int64_t* slice_pairs) {
+  unsigned long long h[4] = {0, 0, 0, 0};
   to_host(ctx, h, ctx->dev_pairs, sizeof(h));
   *pairs_fp64 = (int64_t)h[0];
   *pairs_tc = (int64_t)h[1];
   if (pairs_split) *pairs_split = (int64_t)h[2];
   else *pairs_tc += (int64_t)h[2];
+  if (slice_pairs) *slice_pairs = (int64_t)h[3];
 }
 
 void check_device_error(ifac_ctx* ctx) {
@@ -222,7 +224,7 @@ int ifac_create(ifac_ctx** out, void* stream, const ifac_allocator* alloc) {
   if (cudaMalloc(&words, 64) != cudaSuccess) { cudaFreeHost(c->pinned); delete c; return IFAC_ERR_CUDA; }
   cudaMemset(words, 0, 64);
   c->dev_err = static_cast<int*>(words);
-  c->dev_pairs = reinterpret_cast<unsigned long long*>(static_cast<char*>(words) + 16);
+  c->dev_pairs = reinterpret_cast<unsigned long long*>(static_cast<char*>(words) + 16);  // 4 counters
   *out = c;
   return IFAC_OK;
 }
@@ -243,7 +245,7 @@ int ifac_set_stream(ifac_ctx* ctx, void* stream) {
 }
 
 int ifac_set_split_slices(ifac_ctx* ctx, int slices) {
-  if (!ctx || slices < 4 || slices > 8) return IFAC_ERR_INVALID;
+  if (!ctx || slices < 3 || slices > 8) return IFAC_ERR_INVALID;
   ctx->split_slices = slices;
   return IFAC_OK;
 }

@@ -154,7 +154,8 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   // ||delta||_F stops falling -- the schedule of the single-matrix refinement.
   const bool low = o.prec != IFAC_FP64;
   const int dprec = delta_prec_of(o, bs);
-  std::vector<double> e(count, 0.0), e_prev(count, INFINITY);
+  std::vector<double> e(count, 0.0), e_prev(count, INFINITY), e_pred(count, INFINITY);
+  const double u = unit_roundoff(o.prec);
   std::vector<uint8_t> active(count, 1), parked(count, 0);
   std::vector<int> sweeps(count, 0), stop(count, 0), fp64_evals(count, 0), low_sweeps(count, 0);
   std::vector<std::vector<double>> hist(count);
@@ -176,21 +177,50 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       IFAC_CK(cudaStreamSynchronize(ctx->stream));  // the host flags are reused below
     }
     const int pd = stage == 0 ? o.prec : dprec;
+    bool all_slices = false;
     for (int it = 0;; ++it) {
-      // with low-precision sweeps, the upper block triangle of the symmetric
-      // Z^T S Z is formed and the lower one taken from it
-      const bool sym = low;
-      Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd);        // S Z
-      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym);     // Z^T (S Z)
-      X.reset();
-      Mat Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0)      // I - Z^T S Z
-                     : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
-      Y.reset();
+      // split evaluations take as many slices as the active member that needs
+      // the most (from its last ||delta||_F)
+      int ns = ctx->split_slices;
+      if (pd == IFAC_FP64_SPLIT && !all_slices) {
+        ns = 3;
+        for (int k = 0; k < count; ++k)
+          if (active[k])
+            ns = std::max(ns, delta_slices(ctx, e_pred[k], target, u, (int64_t)(nb1[k] - nb0[k]) * bs));
+      }
+      Mat Dall;
+      {
+        SlicesScope scope(ctx, ns);
+        // with low-precision sweeps, the upper block triangle of the
+        // symmetric Z^T S Z is formed and the lower one taken from it
+        const bool sym = low;
+        Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd);        // S Z
+        Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym);     // Z^T (S Z)
+        X.reset();
+        Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0)          // I - Z^T S Z
+                   : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
+      }
       IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
       Mat D = filter_rows_active(ctx, Dall.m, dseg.p, dactive.p);
       Dall.reset();
       node_fro(ctx, D.m, dnb0.p, dnb1.p, count, ne.p);
       to_host(ctx, e.data(), ne.p, sizeof(double) * count);
+      if (ns < ctx->split_slices) {
+        // a member's delta far below its predicted size: evaluate again with
+        // all slices
+        bool redo = false;
+        for (int k = 0; k < count; ++k)
+          if (active[k] && split_delta_error(ns, (int64_t)(nb1[k] - nb0[k]) * bs) > delta_need(e[k], target, u))
+            redo = true;
+        if (redo) {
+          all_slices = true;
+          --it;
+          continue;
+        }
+      }
+      all_slices = false;
+      for (int k = 0; k < count; ++k)  // parked members: the same Z in stage 1
+        if (active[k]) e_pred[k] = stage == 0 ? 0.1 * e[k] : u * e[k];
       bool any = false;
       for (int k = 0; k < count; ++k) {
         if (!active[k]) continue;
@@ -272,8 +302,8 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   }
   check_device_error(ctx);
   int64_t pf = 0, pt = 0;
-  int64_t ps = 0;
-  read_device_counters(ctx, &pf, &pt, &ps);
+  int64_t ps = 0, pss = 0;
+  read_device_counters(ctx, &pf, &pt, &ps, &pss);
   double ms_fp64 = 0.0, ms_tc = 0.0;
   double ms_split = 0.0;
   prof_collect(ctx, &ms_fp64, &ms_tc, &ms_split);
@@ -316,6 +346,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       r.fp64_pairs = pf;
       r.tc_pairs = pt;
       r.split_pairs = ps;
+      r.split_slice_pairs = pss;
       r.flops = 2.0 * (double)bs * bs * bs * (double)(pf + pt + ps);
       r.launches = ctx->launches;
       r.gemm_launches = ctx->gemm_launches;

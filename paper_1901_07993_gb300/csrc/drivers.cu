@@ -55,6 +55,7 @@ void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
   ctx->pairs_fp64 = 0;
   ctx->pairs_tc = 0;
   ctx->pairs_split = 0;
+  ctx->slice_pairs = 0;
   ctx->events_used = 0;
   ctx->profile = o.profile != 0;
   reset_device_counters(ctx);
@@ -67,9 +68,39 @@ int delta_prec_of(const ifac_opts& o, int bs) {
   return (o.delta_prec == IFAC_FP64_SPLIT && bs == 64) ? IFAC_FP64_SPLIT : IFAC_FP64;
 }
 
+// A split product with s slices per operand errs by about 2^-(7 s - 3)
+// relative to the row and column maxima of its operands; for Z^T (S Z) near
+// convergence that puts the error of ||delta||_F at about 2^-(7 s - 3)
+// ||I||_F = 2^-(7 s - 3) sqrt(n) (seven slices: 7e-12 at n = 262,144, as
+// measured).
+double split_delta_error(int slices, int64_t n) {
+  return std::ldexp(std::sqrt((double)n), -(7 * slices - 3));
+}
+
+double unit_roundoff(int prec) { return prec == IFAC_BF16 ? std::ldexp(1.0, -8) : std::ldexp(1.0, -11); }
+
+// Once the low-precision floor is reached, a sweep whose delta is exact
+// leaves ||delta'||_F of about u ||delta||_F (the correction M carries the
+// low format's rounding; measured: 0.7 u to 1.4 u with TF32), and an error
+// in delta passes into delta' about one to one.  An evaluation error below a
+// tenth of u e therefore costs no convergence; below the target, no false
+// stop.
+double delta_need(double e, double target, double u) { return 0.1 * std::max(target, u * e); }
+
+// the fewest slices (at least 3, at most the context's count) whose error
+// meets delta_need for the predicted ||delta||_F
+int delta_slices(const ifac_ctx* ctx, double e_pred, double target, double u, int64_t n) {
+  const int full = ctx->split_slices;
+  if (!(e_pred < 1.0e300)) return full;
+  const double need = delta_need(e_pred, target, u);
+  int s = 3;
+  while (s < full && split_delta_error(s, n) > need) ++s;
+  return std::min(full, s);
+}
+
 void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   check_device_error(ctx);
-  read_device_counters(ctx, &ctx->pairs_fp64, &ctx->pairs_tc, &ctx->pairs_split);
+  read_device_counters(ctx, &ctx->pairs_fp64, &ctx->pairs_tc, &ctx->pairs_split, &ctx->slice_pairs);
   ctx->pairs = ctx->pairs_fp64 + ctx->pairs_tc + ctx->pairs_split;
   if (!r) {
     double a, b;
@@ -87,6 +118,7 @@ void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   r->tc_launches = ctx->tc_launches;
   r->split_launches = ctx->split_launches;
   r->split_pairs = ctx->pairs_split;
+  r->split_slice_pairs = ctx->slice_pairs;
   r->fp64_pairs = ctx->pairs_fp64;
   r->tc_pairs = ctx->pairs_tc;
   ctx->profile = false;
@@ -171,19 +203,36 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
   const double c = (o.c_rule == 1) ? std::sqrt(2.0 / beta) : 1.0 / std::sqrt(beta);
   Mat Z = scaled_identity(ctx, S.m.n, S.m.bs, S.m.nb, c);
   if (rep) rep->beta = beta;
-  bool fp64_phase = false;
-  double e_prev = INFINITY, e = 0.0;
+  bool fp64_phase = false, all_slices = false;
+  double e_prev = INFINITY, e = 0.0, e_pred = INFINITY;
+  const double u = unit_roundoff(low);
   int stop = 0, sweeps = 0, fp64_evals = 0, low_sweeps = 0;
   for (int it = 0;; ++it) {
     const int dprec = fp64_phase ? delta_prec_of(o, S.m.bs) : low;
-    // Z^T S Z is symmetric: its upper block triangle is formed and the
-    // lower one taken from it, halving the second product
-    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec);         // S Z
-    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true);    // Z^T (S Z), J >= I
-    X.reset();
-    Mat D = sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);                 // I - Z^T S Z
-    Y.reset();
+    // split evaluations take as many slices as this delta needs (predicted
+    // from the last one)
+    const int ns = (dprec == IFAC_FP64_SPLIT && !all_slices) ? delta_slices(ctx, e_pred, target, u, S.m.n)
+                                                             : ctx->split_slices;
+    Mat D;
+    {
+      SlicesScope scope(ctx, ns);
+      // Z^T S Z is symmetric: its upper block triangle is formed and the
+      // lower one taken from it, halving the second product
+      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec);         // S Z
+      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true);    // Z^T (S Z), J >= I
+      X.reset();
+      D = sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);                     // I - Z^T S Z
+    }
     e = fro_host(ctx, D.m);
+    if (dprec == IFAC_FP64_SPLIT && ns < ctx->split_slices && split_delta_error(ns, S.m.n) > delta_need(e, target, u)) {
+      // delta came out below its predicted size, past what this many slices
+      // resolve: evaluate it again with all of them
+      all_slices = true;
+      --it;
+      continue;
+    }
+    all_slices = false;
+    e_pred = u * e;
     if (rep && rep->n_delta < 64) rep->delta_fro[rep->n_delta++] = e;
     if (fp64_phase) {
       ++fp64_evals;
@@ -198,6 +247,7 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       // delta with FP64 products for this Z.
       fp64_phase = true;
       e_prev = INFINITY;
+      e_pred = 0.1 * e;  // the same Z; its low-precision ||delta||_F may sit on that format's floor
       if (rep && rep->n_delta > 0) --rep->n_delta;
       --it;
       continue;

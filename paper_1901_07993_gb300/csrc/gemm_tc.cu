@@ -806,15 +806,36 @@ __global__ void k_map_scatter(const int32_t* __restrict__ rp, const int32_t* __r
 
 // pairs += |row K of op(B)| for every stored block (I, K) of op(A): the number
 // of (I, K, J) block triples, i.e. of stored-block products
+// stored block pairs (op(A)_IK, op(B)_KJ) of the product: all of them, or
+// with upper only those with J >= I (found by binary search in the sorted
+// op(B) row K).  wpairs (nullable) also gets w per pair.  Warp per row I.
 __global__ void k_count_pairs(const int32_t* __restrict__ arp, const int32_t* __restrict__ aci, int nb,
-                              const int32_t* __restrict__ brp, unsigned long long* __restrict__ pairs) {
+                              const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, int upper,
+                              unsigned long long* __restrict__ pairs, unsigned long long* __restrict__ wpairs,
+                              int w) {
   const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   unsigned long long c = 0;
   if (row < nb)
-    for (int p = arp[row] + lane; p < arp[row + 1]; p += 32) c += (unsigned long long)(brp[aci[p] + 1] - brp[aci[p]]);
+    for (int p = arp[row] + lane; p < arp[row + 1]; p += 32) {
+      const int K = aci[p];
+      int lo = brp[K];
+      const int hi = brp[K + 1];
+      if (upper) {
+        int h = hi;
+        while (lo < h) {
+          const int mid = (lo + h) >> 1;
+          if (bci[mid] < row) lo = mid + 1;
+          else h = mid;
+        }
+      }
+      c += (unsigned long long)(hi - lo);
+    }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0 && c) atomicAdd(pairs, c);
+  if (lane == 0 && c) {
+    atomicAdd(pairs, c);
+    if (wpairs) atomicAdd(wpairs, c * (unsigned long long)w);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1022,7 +1043,8 @@ static CUtensorMap make_map(void* base, int64_t nblk) {
 
 template <int ELT>
 static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
-                const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, unsigned long long* pairs) {
+                const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
+                unsigned long long* pairs) {
   using Cf = Cfg<ELT>;
   const int nb = A.nb;
   const size_t bbytes = (size_t)BS * BS * ELT;
@@ -1044,7 +1066,8 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
   constexpr int CL = Cf::CL;
   Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false);
-  k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
+  k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
+                                                                      upper ? 1 : 0, pairs, nullptr, 0);
   IFAC_CK_LAUNCH();
   static std::atomic<unsigned long long> attr{0};
   if (first_on_device(attr, ctx->device))
@@ -1341,7 +1364,7 @@ __global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict_
 }
 
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
-                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
+                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                       unsigned long long* pairs) {
   using Cf = Cfg<2>;
   constexpr int CL = Cf::CL;
@@ -1383,7 +1406,10 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const CUtensorMap mB = make_map<2>(lb.p, (int64_t)ns * (B.nnzb + 1));
   // tile plan (as for the plain tensor-core product) with the longest tile's K steps
   Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
-  k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, pairs);
+  // block pairs, and block pairs times the ns (ns + 1) / 2 slice pairs
+  k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
+                                                                      upper ? 1 : 0, pairs, pairs + 1,
+                                                                      ns * (ns + 1) / 2);
   IFAC_CK_LAUNCH();
   const int kmax = P.kmax;
   float l1h[2] = {0.f, 0.f};
@@ -1493,13 +1519,14 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
 }  // namespace tc
 
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
-                     bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
+                     bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev) {
   if (A.bs != tc::BS) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block product built for bs = 64");
   if (C.nnzb == 0) return;
-  if (prec == IFAC_BF16) tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
-  else if (prec == IFAC_TF32) tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
-  else if (prec == IFAC_FP64_SPLIT) tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, pairs_dev);
+  if (prec == IFAC_BF16) tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev);
+  else if (prec == IFAC_TF32) tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev);
+  else if (prec == IFAC_FP64_SPLIT)
+    tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev);
   else fail(IFAC_ERR_UNSUPPORTED, "unknown precision");
 }
 

@@ -28,7 +28,7 @@ struct ifac_ctx {
   int64_t launches = 0;
   int64_t gemm_launches = 0;
   int64_t tc_launches = 0, split_launches = 0;
-  int64_t pairs_fp64 = 0, pairs_tc = 0, pairs_split = 0;
+  int64_t pairs_fp64 = 0, pairs_tc = 0, pairs_split = 0, slice_pairs = 0;
   std::vector<char> event_kind;  // per recorded event pair: 0 FP64, 1 tensor-core (TF32/BF16), 2 split kernel
   // optional event timing of the numeric product kernels
   bool profile = false;
@@ -149,10 +149,12 @@ Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const ui
 void gemm_numeric_fp64(ifac_ctx* ctx, const View& arows, bool tA_blocks, const ifac_bsr& A,
                        const View& bcols, bool tB_blocks, const ifac_bsr& B, double alpha,
                        ifac_bsr& C, const int32_t* crow, unsigned long long* pairs_dev);
-// Tensor-core (TF32/BF16 in, FP32 accumulate) numeric block product, bs = 64.
-// brows: rows of op(B).
+// Tensor-core (TF32/BF16 in, FP32 accumulate, or split FP64-accurate)
+// numeric block product, bs = 64.  brows: rows of op(B).  upper: C holds only
+// blocks with J >= I.  pairs_dev[0] counts the block pairs multiplied; for
+// split products pairs_dev[1] counts block pairs times slice pairs.
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
-                     bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow,
+                     bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev);
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
                  double gamma, ifac_bsr& C, const int32_t* crow);
@@ -166,6 +168,24 @@ double fro_host(ifac_ctx* ctx, const ifac_bsr& A);
 double gershgorin_host(ifac_ctx* ctx, const ifac_bsr& A);
 // precision of the FP64-accurate delta evaluations of the mixed schedule
 int delta_prec_of(const ifac_opts& o, int bs);
+// unit roundoff of a low-precision product format (TF32 2^-11, BF16 2^-8)
+double unit_roundoff(int prec);
+// error level of a split delta evaluation of an n-row matrix with s slices
+double split_delta_error(int slices, int64_t n);
+// the accuracy a delta evaluation of the mixed schedule needs when
+// ||delta||_F = e: a tenth of what the next low-precision sweep leaves
+double delta_need(double e, double target, double u);
+// slices for an evaluation whose ||delta||_F is predicted at e_pred
+int delta_slices(const ifac_ctx* ctx, double e_pred, double target, double u, int64_t n);
+// sets the context's split slice count for the scope's lifetime
+struct SlicesScope {
+  ifac_ctx* c;
+  int old;
+  SlicesScope(ifac_ctx* c_, int s) : c(c_), old(c_->split_slices) { c->split_slices = s; }
+  ~SlicesScope() { c->split_slices = old; }
+  SlicesScope(const SlicesScope&) = delete;
+  SlicesScope& operator=(const SlicesScope&) = delete;
+};
 // true the first time it is called with this flag word for `device` (per
 // process): per-device one-time settings such as kernel attributes
 inline bool first_on_device(std::atomic<unsigned long long>& seen, int device) {
@@ -223,7 +243,10 @@ void prof_collect(ifac_ctx* ctx, double* ms_fp64, double* ms_tc, double* ms_spli
 
 // Zero the device counters / read them back (read_* synchronises).
 void reset_device_counters(ifac_ctx* ctx);
-void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc, int64_t* pairs_split = nullptr);
+// block pairs multiplied on the FP64 pipe, by TF32/BF16 and by split products
+// (split block pairs times slice pairs in slice_pairs, if given)
+void read_device_counters(ifac_ctx* ctx, int64_t* pairs_fp64, int64_t* pairs_tc, int64_t* pairs_split = nullptr,
+                          int64_t* slice_pairs = nullptr);
 // Fails with IFAC_ERR_TIMEOUT (and clears the flag) if a device wait expired.
 void check_device_error(ifac_ctx* ctx);
 

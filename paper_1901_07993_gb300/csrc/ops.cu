@@ -31,7 +31,7 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
     gemm_numeric_fp64(ctx, arows, tA, A, bcols, tB, B, alpha, C.m, P.row.p, ctx->dev_pairs);
   } else {
     View brows = view_rows(ctx, B, tB);
-    gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p,
+    gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, upper,
                     ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1));
   }
   Mat R = compact(ctx, std::move(C), P.row.p, tau);

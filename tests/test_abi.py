@@ -35,3 +35,31 @@ def test_opts_default_without_gpu():
     libbuild.build()
     o = ifac.opts()
     assert (o.m, o.max_iter, o.leaf_size, o.prec) == (2, 50, 512, ifac.FP64)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of ifac_bsr, ifac_opts and ifac_report have the C
+    structs' sizes and field offsets (compiled against the header with gcc)."""
+    import shutil
+    import subprocess
+    import pytest
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"ifac_bsr": ifac._Bsr, "ifac_opts": ifac._Opts, "ifac_report": ifac._Report}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ifac.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
