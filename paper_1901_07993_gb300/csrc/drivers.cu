@@ -206,6 +206,9 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
   bool fp64_phase = false, all_slices = false;
   double e_prev = INFINITY, e = 0.0, e_pred = INFINITY;
   const double u = unit_roundoff(low);
+  // S's converted copies serve every X = S Z of the refinement
+  OperandCache scache;
+  scache.want_ns = ctx->split_slices;
   int stop = 0, sweeps = 0, fp64_evals = 0, low_sweeps = 0;
   for (int it = 0;; ++it) {
     const int dprec = fp64_phase ? delta_prec_of(o, S.m.bs) : low;
@@ -218,8 +221,8 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       SlicesScope scope(ctx, ns);
       // Z^T S Z is symmetric: its upper block triangle is formed and the
       // lower one taken from it, halving the second product
-      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec);         // S Z
-      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true);    // Z^T (S Z), J >= I
+      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache);  // S Z
+      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true);             // Z^T (S Z), J >= I
       X.reset();
       D = sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);                     // I - Z^T S Z
     }

@@ -1044,25 +1044,35 @@ static CUtensorMap make_map(void* base, int64_t nblk) {
 template <int ELT>
 static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
                 const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                unsigned long long* pairs) {
+                unsigned long long* pairs, OperandCache* ac) {
   using Cf = Cfg<ELT>;
   const int nb = A.nb;
   const size_t bbytes = (size_t)BS * BS * ELT;
   // low-precision, K-major copies of op(A) and op(B) plus one zero block each
-  Buf<uint8_t> la(ctx, (size_t)(A.nnzb + 1) * bbytes), lb(ctx, (size_t)(B.nnzb + 1) * bbytes);
-  IFAC_CK(cudaMemsetAsync(la.p + (size_t)A.nnzb * bbytes, 0, bbytes, ctx->stream));
-  IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
-  if (A.nnzb) {
-    k_convert<ELT><<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, 0, ctx->stream>>>(A.val, arows.src, A.nnzb,
-                                                                                       tA ? 1 : 0, la.p);
-    IFAC_CK_LAUNCH();
+  // (op(A)'s taken from the cache when it holds one of this format)
+  Buf<uint8_t> la, lb(ctx, (size_t)(B.nnzb + 1) * bbytes);
+  const bool hit = ac && ac->conv_elt == ELT;
+  if (!hit) {
+    la = Buf<uint8_t>(ctx, (size_t)(A.nnzb + 1) * bbytes);
+    IFAC_CK(cudaMemsetAsync(la.p + (size_t)A.nnzb * bbytes, 0, bbytes, ctx->stream));
+    if (A.nnzb) {
+      k_convert<ELT><<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, 0, ctx->stream>>>(A.val, arows.src, A.nnzb,
+                                                                                         tA ? 1 : 0, la.p);
+      IFAC_CK_LAUNCH();
+    }
+    if (ac) {
+      ac->conv = std::move(la);
+      ac->conv_elt = ELT;
+    }
   }
+  uint8_t* const la_p = ac ? ac->conv.p : la.p;
+  IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
   if (B.nnzb) {
     k_convert<ELT><<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, 0, ctx->stream>>>(B.val, brows.src, B.nnzb,
                                                                                        tB ? 0 : 1, lb.p);
     IFAC_CK_LAUNCH();
   }
-  const CUtensorMap mapA = make_map<ELT>(la.p, A.nnzb + 1);
+  const CUtensorMap mapA = make_map<ELT>(la_p, A.nnzb + 1);
   const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
   constexpr int CL = Cf::CL;
   Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false);
@@ -1365,35 +1375,46 @@ __global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict_
 
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                      unsigned long long* pairs) {
+                      unsigned long long* pairs, OperandCache* ac) {
   using Cf = Cfg<2>;
   constexpr int CL = Cf::CL;
   const int nb = A.nb;
   const int64_t rows = (int64_t)nb * BS;
   if (ns < 1 || ns > 8) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 8 slices");
-  // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T)
-  Buf<int> sige(ctx, rows), taue(ctx, rows);
+  // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T);
+  // op(A)'s scales and slices come from the cache when it holds at least ns
+  const bool hit = ac && ac->split_ns >= ns;
+  const int nsa = hit ? ac->split_ns : (ac ? std::min(8, std::max(ns, ac->want_ns)) : ns);
+  Buf<int> sige, taue(ctx, rows);
   Buf<unsigned int> l1(ctx, 2);
   IFAC_CK(cudaMemsetAsync(l1.p, 0, 2 * sizeof(unsigned int), ctx->stream));
-  row_scales(ctx, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p);
+  if (!hit) {
+    sige = Buf<int>(ctx, rows);
+    row_scales(ctx, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p);
+  }
   {
     View bt = view_rows(ctx, B, !tB);
     row_scales(ctx, bt.rp, bt.src, nb, !tB, B.val, taue.p, l1.p + 1);
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
-  Buf<int32_t> arow(ctx, A.nnzb);
-  if (A.nnzb) expand_rows(ctx, arows.rp, nb, arow.p);
   const size_t bbytes = (size_t)BS * BS * 2;
-  Buf<uint8_t> la(ctx, (size_t)ns * (A.nnzb + 1) * bbytes), lb(ctx, (size_t)ns * (B.nnzb + 1) * bbytes);
-  for (int k = 0; k < ns; ++k) {
-    IFAC_CK(cudaMemsetAsync(la.p + ((size_t)k * (A.nnzb + 1) + A.nnzb) * bbytes, 0, bbytes, ctx->stream));
+  Buf<uint8_t> la, lb(ctx, (size_t)ns * (B.nnzb + 1) * bbytes);
+  for (int k = 0; k < ns; ++k)
     IFAC_CK(cudaMemsetAsync(lb.p + ((size_t)k * (B.nnzb + 1) + B.nnzb) * bbytes, 0, bbytes, ctx->stream));
+  if (!hit) {
+    la = Buf<uint8_t>(ctx, (size_t)nsa * (A.nnzb + 1) * bbytes);
+    for (int k = 0; k < nsa; ++k)
+      IFAC_CK(cudaMemsetAsync(la.p + ((size_t)k * (A.nnzb + 1) + A.nnzb) * bbytes, 0, bbytes, ctx->stream));
+    if (A.nnzb) {
+      Buf<int32_t> arow(ctx, A.nnzb);
+      expand_rows(ctx, arows.rp, nb, arow.p);
+      k_split<<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, tA ? SPLIT_TILE_BYTES : 0, ctx->stream>>>(
+          A.val, arows.src, A.nnzb, tA ? 1 : 0, arow.p, sige.p, nsa, reinterpret_cast<__nv_bfloat16*>(la.p));
+      IFAC_CK_LAUNCH();
+    }
   }
-  if (A.nnzb) {
-    k_split<<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, tA ? SPLIT_TILE_BYTES : 0, ctx->stream>>>(
-        A.val, arows.src, A.nnzb, tA ? 1 : 0, arow.p, sige.p, ns, reinterpret_cast<__nv_bfloat16*>(la.p));
-    IFAC_CK_LAUNCH();
-  }
+  uint8_t* const la_p = hit ? ac->split.p : la.p;
+  const int* const sige_p = hit ? ac->sexp.p : sige.p;
   if (B.nnzb) {
     k_split<<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, tB ? 0 : SPLIT_TILE_BYTES, ctx->stream>>>(
         B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, taue.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
@@ -1402,7 +1423,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   // one tensor map over all slices of each operand (slice s at row s (nnzb + 1) BS)
   if ((int64_t)ns * (std::max(A.nnzb, B.nnzb) + 1) * BS > (int64_t)0x7fffffff)
     fail(IFAC_ERR_TOO_LARGE, "split product: slice copies exceed the 2^31-row tensor-map range");
-  const CUtensorMap mA = make_map<2>(la.p, (int64_t)ns * (A.nnzb + 1));
+  const CUtensorMap mA = make_map<2>(la_p, (int64_t)ns * (A.nnzb + 1));
   const CUtensorMap mB = make_map<2>(lb.p, (int64_t)ns * (B.nnzb + 1));
   // tile plan (as for the plain tensor-core product) with the longest tile's K steps
   Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
@@ -1414,6 +1435,14 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const int kmax = P.kmax;
   float l1h[2] = {0.f, 0.f};
   to_host(ctx, l1h, l1.p, sizeof(l1h));
+  if (hit) {
+    l1h[0] = ac->l1;
+  } else if (ac) {
+    ac->l1 = l1h[0];
+    ac->split = std::move(la);
+    ac->sexp = std::move(sige);
+    ac->split_ns = nsa;
+  }
   Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
   IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
   static std::atomic<unsigned long long> attr{0};
@@ -1511,7 +1540,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     int ea = 0;
     const double am = std::frexp(alpha, &ea) * 2.0;  // alpha = am 2^(ea - 1), am in [1, 2)
     k_split_finish<<<(int)std::min<int64_t>(C.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
-        crow, C.col_idx, C.nnzb, part.p, C.val, sige.p, taue.p, ea - 1 - fbits, am, C.norms);
+        crow, C.col_idx, C.nnzb, part.p, C.val, sige_p, taue.p, ea - 1 - fbits, am, C.norms);
   }
   IFAC_CK_LAUNCH();
 }
@@ -1520,13 +1549,13 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
 
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                     unsigned long long* pairs_dev) {
+                     unsigned long long* pairs_dev, OperandCache* acache) {
   if (A.bs != tc::BS) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block product built for bs = 64");
   if (C.nnzb == 0) return;
-  if (prec == IFAC_BF16) tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev);
-  else if (prec == IFAC_TF32) tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev);
+  if (prec == IFAC_BF16) tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache);
+  else if (prec == IFAC_TF32) tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache);
   else if (prec == IFAC_FP64_SPLIT)
-    tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev);
+    tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache);
   else fail(IFAC_ERR_UNSUPPORTED, "unknown precision");
 }
 

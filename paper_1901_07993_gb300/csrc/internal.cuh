@@ -127,7 +127,9 @@ struct Pattern {
   Buf<int32_t> rp, ci, row;
   int64_t nnzb = 0;
 };
-Pattern pattern_from_bitmap(ifac_ctx* ctx, const uint32_t* bm, int nb);
+// known_nnzb >= 0: the number of set bits is known (e.g. a transposed
+// pattern), so it is not read back from the device
+Pattern pattern_from_bitmap(ifac_ctx* ctx, const uint32_t* bm, int nb, int64_t known_nnzb = -1);
 // Symbolic product pattern of op(A) op(B); upper: only the blocks (I, J)
 // with J >= I.
 Pattern product_pattern(ifac_ctx* ctx, const View& arows, const ifac_bsr& B, bool transB, int nb,
@@ -149,13 +151,36 @@ Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const ui
 void gemm_numeric_fp64(ifac_ctx* ctx, const View& arows, bool tA_blocks, const ifac_bsr& A,
                        const View& bcols, bool tB_blocks, const ifac_bsr& B, double alpha,
                        ifac_bsr& C, const int32_t* crow, unsigned long long* pairs_dev);
+// Converted copies of an op(A) operand that several products share (S in
+// X = S Z across the sweeps of one refinement): the K-major TF32 / BF16 copy,
+// and the BF16 slices with their row scale exponents and scaled 1-norm bound.
+// Slice k does not depend on the slice count, so slices held for s serve any
+// split product with at most s.  The owner resets it when op(A) changes.
+struct OperandCache {
+  int conv_elt = 0;        // bytes per element of conv (4 TF32, 2 BF16); 0 empty
+  Buf<uint8_t> conv;       // (nnzb + 1) blocks, the last one zero
+  int split_ns = 0;        // slices held (0 empty)
+  int want_ns = 0;         // slices to compute when filling (at least the product's)
+  Buf<uint8_t> split;      // split_ns slices, slice-major, (nnzb + 1) blocks each
+  Buf<int> sexp;           // row scale exponents of op(A)
+  float l1 = 0.f;          // scaled row 1-norm bound of op(A)
+  void reset() {
+    conv_elt = 0;
+    conv.reset();
+    split_ns = 0;
+    split.reset();
+    sexp.reset();
+    l1 = 0.f;
+  }
+};
+
 // Tensor-core (TF32/BF16 in, FP32 accumulate, or split FP64-accurate)
 // numeric block product, bs = 64.  brows: rows of op(B).  upper: C holds only
 // blocks with J >= I.  pairs_dev[0] counts the block pairs multiplied; for
 // split products pairs_dev[1] counts block pairs times slice pairs.
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                     unsigned long long* pairs_dev);
+                     unsigned long long* pairs_dev, OperandCache* acache = nullptr);
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
                  double gamma, ifac_bsr& C, const int32_t* crow);
 // C = alpha (U + strict_upper(U)^T) + beta B + gamma I on the pattern of sym_pattern
@@ -209,7 +234,7 @@ Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 
 // ---- operations used by drivers (ops.cu) ----
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec = IFAC_FP64, bool upper = false);
+         int prec = IFAC_FP64, bool upper = false, OperandCache* acache = nullptr);
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma);
 // the symmetric matrix whose upper block triangle (J >= I) is held by U,
 // times alpha, plus beta B and gamma I: alpha (U + strict_upper(U)^T) +

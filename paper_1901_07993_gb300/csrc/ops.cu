@@ -10,8 +10,9 @@ namespace ifac {
 //   columns of op(B): rows of B^T when B is used as is, or B's rows when B^T
 //   upper: only the blocks (I, J) with J >= I are formed (a product known to
 //   be symmetric, completed by sym_sum)
+//   acache: converted copies of op(A) kept across calls (tensor-core products)
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec, bool upper) {
+         int prec, bool upper, OperandCache* acache) {
   const int nb = A.nb;
   if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && A.bs == 64) prec = IFAC_FP64_SPLIT;
   View arows = view_rows(ctx, A, tA);
@@ -32,7 +33,7 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   } else {
     View brows = view_rows(ctx, B, tB);
     gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, upper,
-                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1));
+                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache);
   }
   Mat R = compact(ctx, std::move(C), P.row.p, tau);
   ctx->products += 1;

@@ -131,7 +131,7 @@ __global__ void k_row_fill(const uint32_t* __restrict__ bm, int nb, int W, const
   }
 }
 
-Pattern pattern_from_bitmap(ifac_ctx* ctx, const uint32_t* bm, int nb) {
+Pattern pattern_from_bitmap(ifac_ctx* ctx, const uint32_t* bm, int nb, int64_t known_nnzb) {
   int W = words_per_row(nb);
   Pattern P;
   P.rp = Buf<int32_t>(ctx, nb + 1);
@@ -139,7 +139,8 @@ Pattern pattern_from_bitmap(ifac_ctx* ctx, const uint32_t* bm, int nb) {
   int grid = cdiv((int64_t)nb * 32, 256);
   k_row_popc<<<grid, 256, 0, ctx->stream>>>(bm, nb, W, cnt.p);
   IFAC_CK_LAUNCH();
-  P.nnzb = scan_counts(ctx, cnt.p, P.rp.p, nb, true);
+  P.nnzb = scan_counts(ctx, cnt.p, P.rp.p, nb, known_nnzb < 0);
+  if (known_nnzb >= 0) P.nnzb = known_nnzb;
   P.ci = Buf<int32_t>(ctx, P.nnzb);
   P.row = Buf<int32_t>(ctx, P.nnzb);
   if (P.nnzb > 0) {
@@ -178,7 +179,7 @@ View view_rows(ifac_ctx* ctx, const ifac_bsr& A, bool trans) {
     return v;
   }
   Buf<uint32_t> bm = pattern_bitmap(ctx, A, true);
-  Pattern P = pattern_from_bitmap(ctx, bm.p, A.nb);
+  Pattern P = pattern_from_bitmap(ctx, bm.p, A.nb, A.nnzb);  // A^T has A's blocks
   v.own_src = Buf<int32_t>(ctx, P.nnzb);
   if (P.nnzb > 0) {
     k_find_src<<<cdiv(P.nnzb, 256), 256, 0, ctx->stream>>>(A.row_ptr, A.col_idx, P.nnzb, P.row.p, P.ci.p, v.own_src.p);
