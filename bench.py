@@ -17,9 +17,10 @@ Prints one JSON line.  `value` is factorizations per second over all ranks
 (each rank factorizes its own copy: weak scaling, no collective on the data
 path).  `e2e` repeats the measurement with S in pinned host memory and Z read
 back to pinned host memory inside the timed region.  `roofline` rates the
-FP64 block-product kernel by its algorithmic flops (2 bs^3 per multiplied
-block pair) over its CUDA-event time.  `--impl reference` times the CPU
-oracle on the same workload.
+block-product kernel with the most device time by its algorithmic flops
+(2 bs^3 per multiplied stored block pair; per slice pair for split products)
+over its CUDA-event time; `kernels` lists every block-product kernel of the
+run.  `--impl reference` times the CPU oracle on the same workload.
 """
 from __future__ import annotations
 
@@ -107,6 +108,24 @@ PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "split": 3}
 METRIC = "Inverse-factor time & block-GEMM TFLOP/s: mixed vs FP64 at ||I-Z*SZ||_F<=1e-10"
 UNIT = "factorizations/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# block-product kernels, averaged over the launches of one factorization: an
+# ncu capture of the first factorization of irsi-mixed-chain-n65536-bs64 (28
+# TF32 and 8 split launches, --clock-control none).  The 262,144-row chain runs
+# the same sweeps and slice counts on four times the block rows, stored blocks
+# and block pairs, so its figures are the captured ones times four.  Keyed by
+# workload, then by kernel_rooflines' kernel key.
+_TRAFFIC_M65 = {"tc": 4713918464 / 28, "split": 4932833792 / 8}
+DRAM_TRAFFIC = {
+    "irsi-mixed-chain-n65536-bs64": {
+        k: (v, "ncu capture of this workload's first factorization")
+        for k, v in _TRAFFIC_M65.items()},
+    "irsi-mixed-chain-n262144-bs64": {
+        k: (4 * v, "ncu capture of the 65,536-row chain's first factorization, times 4 (block rows, "
+                   "stored blocks and block pairs scale with n on the chain)")
+        for k, v in _TRAFFIC_M65.items()},
+}
 
 
 def _peaks():
@@ -331,9 +350,12 @@ def timed_factorizations(ctx, ifac, factor, S, w, o, steps, flush):
 SPLIT_PAIRS = 28  # slice pairs (s, t) with s + t <= 8 of the default 7-slice split product
 
 
-def kernel_rooflines(reps, bs, prec):
-    """Live CUDA-event rooflines of the two block-product kernels."""
+def kernel_rooflines(reps, bs, prec, traffic=None):
+    """Live CUDA-event rooflines of the block-product kernels.  `traffic` maps
+    a kernel key to (DRAM bytes per launch, source) from an ncu capture of the
+    same workload; kernels without one report null."""
     out = {}
+    traffic = traffic or {}
     fp64_ms = sum(r.gemm_ms for r in reps)
     tc_ms = sum(r.tc_ms for r in reps)
     fl = 2.0 * bs ** 3
@@ -351,7 +373,8 @@ def kernel_rooflines(reps, bs, prec):
         ach = sum(r.tc_pairs for r in reps) * fl / (tc_ms / 1e3) / 1e12
         launches = sum(r.tc_launches for r in reps)
         out["tc"] = {"bound": "tensor", "kernel": f"k_gemm_tc<{'2' if prec == 'bf16' else '4'}>", "achieved": ach,
-                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "traffic": traffic["tc"][0] if "tc" in traffic else None,
                      "peak_source": f"{src} bf16" + ("" if prec == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25"),
                      "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * tc_ms / max(launches, 1),
                      "ms_per_step": tc_ms / len(reps),
@@ -364,7 +387,8 @@ def kernel_rooflines(reps, bs, prec):
         ach = sum(r.split_slice_pairs for r in reps) * fl / (split_ms / 1e3) / 1e12
         launches = sum(r.split_launches for r in reps)
         out["split"] = {"bound": "tensor", "kernel": "k_gemm_tc<2> (split FP64)", "achieved": ach,
-                        "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                        "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                        "traffic": traffic["split"][0] if "split" in traffic else None,
                         "peak_source": f"{src} bf16", "fp64_equivalent_tflops": eq,
                         "fp64_equivalent_over_fp64_peak": eq / fp64_pk,
                         "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * split_ms / max(launches, 1),
@@ -374,6 +398,10 @@ def kernel_rooflines(reps, bs, prec):
                         "note": "achieved = BF16 slice-pair products on stored block pairs, s (s + 1) / 2 per "
                                 "block pair with s slices (28 at s = 7; early delta evaluations take fewer); "
                                 "zero blocks inside tiles are not counted"}
+    for k, v in out.items():
+        if v.get("traffic") is not None:
+            v["traffic_unit"] = "bytes per launch"
+            v["traffic_source"] = traffic[k][1]
     return out
 
 
@@ -659,7 +687,7 @@ def main():
     torch.cuda.synchronize()
     total_ms = allmax(world, sum(step_ms))
     value = world * args.steps / (total_ms / 1e3)
-    kernels = kernel_rooflines(reps, w["bs"], w["prec"])
+    kernels = kernel_rooflines(reps, w["bs"], w["prec"], DRAM_TRAFFIC.get(args.workload))
     dominant = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
     roofline = dict(kernels[dominant]) if dominant else None
     resid = ifac.inv_factor_resid(ctx, S, Z)
