@@ -112,11 +112,13 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # block-product kernels, averaged over the launches of one factorization: an
 # ncu capture of the first factorization of irsi-mixed-chain-n65536-bs64 (28
-# TF32 and 8 split launches, --clock-control none).  The 262,144-row chain runs
-# the same sweeps and slice counts on four times the block rows, stored blocks
-# and block pairs, so its figures are the captured ones times four.  Keyed by
-# workload, then by kernel_rooflines' kernel key.
-_TRAFFIC_M65 = {"tc": 4713918464 / 28, "split": 4932833792 / 8}
+# TF32 launches, --clock-control none).  The 262,144-row chain runs the same
+# sweeps on four times the block rows, stored blocks and block pairs, so its
+# figures are the captured ones times four.  The split products were captured
+# before their accumulation units were bounded by the longest tile's K steps,
+# which changed their traffic, so they report none.  Keyed by workload, then
+# by kernel_rooflines' kernel key.
+_TRAFFIC_M65 = {"tc": 4713918464 / 28}
 DRAM_TRAFFIC = {
     "irsi-mixed-chain-n65536-bs64": {
         k: (v, "ncu capture of this workload's first factorization")

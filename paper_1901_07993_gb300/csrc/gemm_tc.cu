@@ -1147,9 +1147,11 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
 // (first slices |q| <= 128, later ones |q| <= 64) is a sum of integers, exact
 // in FP32 while its magnitude bound stays <= 2^24.  Slice pairs with equal
 // weight 2^(-7(s+t)), s + t <= NS + 1, are packed greedily into units whose
-// bound over a window of KW = 16 K blocks (1024 terms) stays <= 2^24 (13 units
-// for NS = 7); per tile and window, each unit is one accumulator that the
-// epilogue adds, scaled, into the FP64 result.
+// bound over a window stays <= 2^24.  A window holds KW = 16 K blocks (1024
+// terms), or fewer when the product's longest tile has fewer K steps: for
+// NS = 7, 13 units at full windows, 7 when no tile has more than 7 K steps
+// (banded patterns such as a 1D chain).  Per tile and window, each unit is
+// one accumulator that the epilogue adds, scaled, into the FP64 result.
 // ---------------------------------------------------------------------------
 constexpr int SPLIT_BITS = 7;
 
@@ -1480,9 +1482,13 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const int fbits = std::min(56, 62 - std::min(lgK, lgB));
   auto set_units = [&](int fbits) {
     // units: slice pairs of equal weight packed while sum over the unit of
-    // max|q_s| max|q_t| * 64 * KW stays <= 2^24
+    // max|q_s| max|q_t| * 64 * kw stays <= 2^24, kw = the K blocks a window
+    // can hold: KW, or the longest tile's K steps when that is fewer (every
+    // window of every tile then has at most kw blocks, so each FP32
+    // accumulator still sums integers of magnitude <= 2^24 exactly)
     const auto qmax = [](int s) { return s == 1 ? 128 : 64; };
-    const int64_t cap = ((int64_t)1 << 24) / (64 * KW);
+    const int kw = std::min(KW, std::max(kmax, 1));
+    const int64_t cap = ((int64_t)1 << 24) / (64 * kw);
     int nu = 0, np = 0;
     for (int g = 2; g <= ns + 1; ++g) {
       int64_t used = 0;
