@@ -314,7 +314,8 @@ def run_reference(args, w, world, rank):
     v = args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[w["prec"]],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64",  # the oracle computes every step in FP64
             "data": "synthetic", "config": config_of(w, args.workload, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} {what} (plus {args.warmup} warm-up)"},
