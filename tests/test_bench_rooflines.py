@@ -1,6 +1,7 @@
-"""Host-side roofline arithmetic of bench.py (no GPU): achieved rates from
-block-pair counts and CUDA-event times, fractions of the peak, and the DRAM
-traffic figures taken from an ncu capture."""
+"""Host-side arithmetic of bench.py (no GPU): achieved rates from
+block-pair counts and CUDA-event times, fractions of the peak, the DRAM
+traffic figures taken from an ncu capture, and the clock samples of the
+timed region."""
 import os
 import sys
 from types import SimpleNamespace
@@ -65,3 +66,23 @@ def test_traffic_table_names_existing_workloads():
         assert bench.WORKLOADS[name]["prec"] == "tf32"  # the capture ran TF32 sweeps and split delta
         assert set(table) <= {"tc", "split", "fp64"}
     assert bench.DEFAULT_WORKLOAD in bench.DRAM_TRAFFIC
+
+
+def test_clock_summary_parses_samples_and_reasons(tmp_path):
+    """The nvidia-smi sample file of the timed region: median SM clock, the
+    largest max clock, and every throttle reason seen Active."""
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",  # skipped
+    ]
+    with open(s.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    s.proc = object()  # as if sampling ran
+    c = s.summary()
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s.proc = None
+    assert s.summary() is None
