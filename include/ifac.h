@@ -263,10 +263,10 @@ int bsr_gershgorin(ifac_ctx* ctx, const ifac_bsr* A, double* out);
 int leaf_invchol_batched(ifac_ctx* ctx, int count, int nl, const double* S, double* Z, int* info);
 
 /* The same batched leaf inverse Cholesky for callers that cannot allocate
- * device memory when they call it: code running while a stream is being
- * captured into a CUDA graph, frameworks that own the whole device-memory
- * budget, or loops that cannot afford an allocation's synchronisation.  The
- * paper has no counterpart; this is a library convenience.
+ * device memory when they call it: frameworks that own the whole
+ * device-memory budget and forbid allocations behind their allocator's back,
+ * or loops that cannot afford an allocation's synchronisation with the
+ * device.  The paper has no counterpart; this is a library convenience.
  *
  * Arguments as leaf_invchol_batched, except that `stream` (a cudaStream_t)
  * replaces the context.  It allocates nothing: its scratch (the diagonal-tile
@@ -275,9 +275,12 @@ int leaf_invchol_batched(ifac_ctx* ctx, int count, int nl, const double* S, doub
  * up to 32) lives in one fixed 32 MiB device array (4 Mi doubles) that every
  * GPU loading the library holds until exit.  Larger requests return
  * IFAC_ERR_TOO_LARGE and touch nothing.
+ *  - S and Z must be equal (in place) or not overlap at all; a partial
+ *    overlap returns IFAC_ERR_INVALID and touches nothing.
  *  - The first call on a device looks up that array's device address
  *    (cudaGetSymbolAddress, with that device current); make this first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the process, so a
+ *    device reset (cudaDeviceReset) between calls is not supported.
  *  - The call is asynchronous on `stream`: it returns after enqueueing and
  *    does not read info back; info[k] (device) is set as in
  *    leaf_invchol_batched once the stream reaches it.
@@ -394,6 +397,24 @@ int inv_factor_refine_adjoint(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* 
 /* ||I - Z^T S Z||_F with untruncated products (the factorization error of
  * Table 1). */
 int inv_factor_resid(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* Z, double* out);
+
+/* ---------------------------------------------------------------- */
+/* Failure-path self-test                                            */
+/* ---------------------------------------------------------------- */
+
+/* Exercises the bounded device-side waits of the tensor-core product kernel
+ * without a fault: one launch of that kernel (two CTAs, a one-tile product of
+ * 64 x 64 zero blocks) whose copy and MMA stages are told to do no work, so
+ * the epilogue's first wait for an accumulator never completes and expires
+ * after wait_limit polls (1..2^30; about 2^20 polls take milliseconds).  The
+ * kernel then records the error flag, releases its tensor memory and
+ * returns; nothing was copied or multiplied, so nothing is left in flight.
+ * Returns IFAC_ERR_TIMEOUT (the status every library call returns when one
+ * of its waits expires) and clears the flag, leaving the context usable;
+ * IFAC_ERR_INVALID for a wait_limit outside the range.  Synchronises the
+ * context's stream.  Not part of the paper's method: it tests the library's
+ * failure handling (the bound on every wait inside the pipeline). */
+int ifac_selftest_wait_timeout(ifac_ctx* ctx, int64_t wait_limit);
 
 #ifdef __cplusplus
 }

@@ -524,4 +524,13 @@ int inv_factor_resid(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* Z, double
   });
 }
 
+int ifac_selftest_wait_timeout(ifac_ctx* ctx, int64_t wait_limit) {
+  return guarded(ctx, [&]() -> int {
+    if (wait_limit < 1 || wait_limit > ((int64_t)1 << 30)) fail(IFAC_ERR_INVALID, "wait_limit must be in 1..2^30");
+    tc_wait_timeout_selftest(ctx, (long long)wait_limit);
+    check_device_error(ctx);  // IFAC_ERR_TIMEOUT, flag cleared
+    return IFAC_OK;
+  });
+}
+
 }  // extern "C"

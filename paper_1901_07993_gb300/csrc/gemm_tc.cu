@@ -14,6 +14,12 @@
 // the tile (op(A)_IK or op(B)_KJ not stored) is read from the zero block, so
 // every K step is one dense M x N x 64 contraction.
 //
+// Pairs.  Two CTAs take one super-tile of 2 TM x TN blocks: each computes
+// TM block rows against the same op(B) panel and walks the same K set (the
+// union over the super-tile's rows), so the panel is read from HBM once and
+// from L2 by the second CTA.  Each CTA loads its own copy of every tile it
+// contracts (no cluster, no cross-CTA signalling).
+//
 // Roles (320 threads, one CTA per SM):
 //   warp 0      : TMA producer -- one 64-row box per block and 128-byte
 //                 atom, 128-byte swizzle, into a STAGES-deep ring;
@@ -37,9 +43,7 @@ namespace tc {
 
 constexpr int BS = 64;
 constexpr int TM = 2;
-#ifndef IFAC_TC_CLUSTER_BF16
-#define IFAC_TC_CLUSTER_BF16 2
-#endif
+constexpr int PAIR = 2;                    // CTAs per super-tile (consecutive blockIdx.x)
 constexpr int NEPI = 8;                    // epilogue warps: two per tensor-memory lane quarter
 constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr long long WAIT_LIMIT = 1ll << 27;
@@ -55,7 +59,6 @@ struct Cfg {
   static constexpr int MMA_K = 32 / ELT;                // 32 bytes of K per tcgen05.mma
   static constexpr int KSTEPS = BS / MMA_K;             // MMAs per K block
   static constexpr int TN = (ELT == 2) ? 4 : 2;         // block columns per tile
-  static constexpr int CL = (ELT == 2) ? IFAC_TC_CLUSTER_BF16 : 2;  // CTAs per cluster sharing one op(B) panel
   static constexpr int N = TN * BS;
   static constexpr int M = TM * BS;
   static constexpr int A_ATOM_BYTES = M * 128;          // one K atom of the A tile
@@ -101,10 +104,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait: true when the phase of `parity` completed; false on the CTA's
-// abort flag or (after WAIT_LIMIT polls) on timeout, which raises both flags.
+// abort flag or (after `limit` polls) on timeout, which raises both flags.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* gerr,
-                                          bool honour_abort = true) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+                                          bool honour_abort = true, long long limit = WAIT_LIMIT) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(bar, parity)) return true;
     if (honour_abort && *abort_flag) return false;
   }
@@ -119,36 +122,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
           dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
-}
-
-// the same box into the same shared-memory offset of every CTA in `mask`,
-// signalling each CTA's mbarrier at the same offset
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
@@ -191,14 +164,6 @@ __device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint6
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// completion of this thread's MMAs arrives on the mbarrier at `bar` in every CTA of `mask`
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   bar),
-               "h"(mask)
-               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -254,6 +219,35 @@ __device__ __forceinline__ long long fixed_add(long long d, int x, int sh, bool&
   return r;
 }
 
+// Sum of squares of FP32 values for the block norms that truncation tests,
+// accurate to about 2^-42 relative without the FP64 pipe: each square of
+// x 2^32 is split exactly into p + e (FMA), p is added to the running sum with
+// an error-free two-sum, and the errors are collected in a second FP32 word.
+// The scale 2^32 keeps squares of |x| in [2^-95, 2^28) normal, and 64 of
+// them finite; larger magnitudes (rare) are squared in FP64, smaller ones
+// contribute below 2^-190 each.
+struct SqAcc {
+  float hi = 0.0f, lo = 0.0f;
+  double big = 0.0;
+  __device__ __forceinline__ void add(float x) {
+    if (fabsf(x) < 268435456.0f) {
+      const float y = x * 4294967296.0f;
+      const float p = y * y;
+      const float e = fmaf(y, y, -p);
+      const float s = hi + p;
+      const float bp = s - hi;
+      const float err = (hi - (s - bp)) + (p - bp);
+      hi = s;
+      lo += err + e;
+    } else {
+      big = fma((double)x, (double)x, big);
+    }
+  }
+  __device__ __forceinline__ double value() const {
+    return ((double)hi + (double)lo) * 5.421010862427522e-20 + big;  // 2^-64
+  }
+};
+
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory"); }
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, int lo, int hi, int v) {
@@ -298,6 +292,11 @@ struct TileArgs {
   int pair_ya[MAX_PAIRS], pair_yb[MAX_PAIRS];
   int unit_sh[MAX_UNITS];
   int* ovf;  // set to 2 on a fixed-point overflow (reported as an error by the host)
+  // failure-path self-test only (0 in every product): the producer and the MMA
+  // issuer do no work, so the epilogue's first accumulator wait expires after
+  // wait_limit polls and the kernel reports a timeout
+  int stall;
+  long long wait_limit;
 };
 
 template <int ELT>
@@ -315,16 +314,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ float ep_stage[NEPI][32 * 17];  // plain epilogue: per-warp transpose for coalesced stores
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long wl = args.wait_limit;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int ntiles = *args.ntiles;
-  // A cluster of CL CTAs takes one super-tile of CL*TM x TN blocks; CTA `crank`
-  // computes block rows (super row * CL + crank) * TM.  Both CTAs step through
-  // the same K set (the union over the super-tile's rows), each loads its own
-  // op(A) blocks and half of the op(B) panel, multicast to both.
-  const uint32_t crank = cluster_rank();
-  const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
-  constexpr int CL = C::CL;
-  constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
+  // CTAs 2c and 2c + 1 (pair c of ncl) take one super-tile of PAIR*TM x TN
+  // blocks; CTA `crank` of the pair computes block rows (super row * PAIR +
+  // crank) * TM.  Both step through the same K set (the union over the
+  // super-tile's rows) and load the whole op(B) panel into their own shared
+  // memory.
+  const int crank = (int)(blockIdx.x % PAIR);
+  const int cid = (int)(blockIdx.x / PAIR), ncl = (int)(gridDim.x / PAIR);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -338,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), C::CL);  // released by the MMAs of every CTA of the cluster
+      mbar_init(smem_u32(&empty_bar[s]), 1);  // released by this CTA's MMAs
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -354,14 +353,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync_all();  // every CTA's barriers exist before any multicast lands
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
 
-  // work items: this cluster's tiles (cid, cid + ncl, ...), in split mode once
-  // per K window, window-major: every cluster runs window w of its tiles before
+  // work items: this pair's tiles (cid, cid + ncl, ...), in split mode once
+  // per K window, window-major: every pair runs window w of its tiles before
   // window w + 1, so the slices of one K range are shared through L2, while a
-  // tile's fixed-point sums are only ever updated by the one cluster that owns it
+  // tile's fixed-point sums are only ever updated by the one CTA that owns its rows
   const int mt = ntiles > cid ? (ntiles - cid + ncl - 1) / ncl : 0;
   const int nitems = mt * (args.split ? args.nwin : 1);
   auto item = [&](int j, int& t, int& kb, int& cnt) -> bool {
@@ -392,7 +390,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     // lane 0: one ring slot with the blocks of record r, slices at rows ya / yb
     auto issue = [&](const int* r, int ya, int yb) -> bool {
-      if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) return false;
+      if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err, true, wl)) return false;
       const uint32_t fb = smem_u32(&full_bar[stage]);
       mbar_expect_tx(fb, C::TX_BYTES);
       issued_mask |= 1u << stage;
@@ -405,11 +403,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int a = 0; a < C::ATOMS; ++a)
           tma_load_2d(sa + a * C::A_ATOM_BYTES + i * BS * 128, &mapA, a * C::ATOM_ELEMS, ya + r[i] * BS, fb);
 #pragma unroll
-      for (int c = (int)crank * (C::TN / CL); c < ((int)crank + 1) * (C::TN / CL); ++c)
+      for (int c = 0; c < C::TN; ++c)
 #pragma unroll
         for (int a = 0; a < C::ATOMS; ++a)
-          tma_load_2d_mc(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS, yb + r[TM + c] * BS,
-                         fb, CL_MASK);
+          tma_load_2d(sb + a * C::B_ATOM_BYTES + c * BS * 128, &mapB, a * C::ATOM_ELEMS, yb + r[TM + c] * BS, fb);
       if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
       return true;
     };
@@ -422,8 +419,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!issue(wrec[j], s_pair_ya[p], s_pair_yb[p])) return false;
       return true;
     };
-    constexpr int RECW = CL * TM + C::TN;  // plan record: op(A) rows of the super-tile, then op(B) columns
-    for (int it = 0; it < nitems && ok; ++it) {
+    constexpr int RECW = PAIR * TM + C::TN;  // plan record: op(A) rows of the super-tile, then op(B) columns
+    for (int it = 0; it < nitems && ok && !args.stall; ++it) {
       int t, kb, cnt;
       if (!item(it, t, kb, cnt)) continue;
       const int32_t* base = args.rec + (size_t)(args.rec_off[t] + kb) * RECW;
@@ -433,9 +430,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (lane < n) {
             const int32_t* r = base + (size_t)(k0 + lane) * RECW;
 #pragma unroll
-            for (int i = 0; i < TM; ++i) rec[lane][i] = r[(int)crank * TM + i];
+            for (int i = 0; i < TM; ++i) rec[lane][i] = r[crank * TM + i];
 #pragma unroll
-            for (int c = 0; c < C::TN; ++c) rec[lane][TM + c] = r[CL * TM + c];
+            for (int c = 0; c < C::TN; ++c) rec[lane][TM + c] = r[PAIR * TM + c];
           }
           __syncwarp();
           if (lane == 0)
@@ -447,9 +444,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane < cnt) {
           const int32_t* r = base + (size_t)lane * RECW;
 #pragma unroll
-          for (int i = 0; i < TM; ++i) wrec[lane][i] = r[(int)crank * TM + i];
+          for (int i = 0; i < TM; ++i) wrec[lane][i] = r[crank * TM + i];
 #pragma unroll
-          for (int c = 0; c < C::TN; ++c) wrec[lane][TM + c] = r[CL * TM + c];
+          for (int c = 0; c < C::TN; ++c) wrec[lane][TM + c] = r[PAIR * TM + c];
         }
         __syncwarp();
         if (lane == 0) ok = issue_window(cnt);
@@ -457,14 +454,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
       }
     }
-    // before the CTA exits: the copies lane 0 issued (and the peer's multicast
-    // halves) have landed, and both CTAs' MMAs have released every slot, so no
-    // remote arrive can reach this CTA's barriers after it leaves
+    // before the CTA exits: the copies lane 0 issued have landed and the MMAs
+    // have released every slot
     if (lane == 0)
       for (int s = 0; s < C::STAGES; ++s)
         if (issued_mask & (1u << s)) {
-          mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
-          mbar_wait(smem_u32(&empty_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+          mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false, wl);
+          mbar_wait(smem_u32(&empty_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false, wl);
         }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer ------------------------------
@@ -478,10 +474,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int ab = tl & 1;
         const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
         const uint32_t tacc = tmem + (uint32_t)(ab * C::N);
-        if (!mbar_wait(smem_u32(&acc_empty[ab]), aphase ^ 1u, &abort_flag, args.err)) return false;
+        if (!mbar_wait(smem_u32(&acc_empty[ab]), aphase ^ 1u, &abort_flag, args.err, true, wl)) return false;
         tc_fence_after();
         for (int k = 0; k < nsteps; ++k) {
-          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, args.err)) return false;
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, args.err, true, wl)) return false;
           tc_fence_after();
           const uint32_t sa = smem_base + stage * C::STAGE_BYTES;
           const uint32_t sb = sa + C::A_BYTES;
@@ -491,14 +487,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mma_issue<ELT>(tacc, smem_desc(sa + atom * C::A_ATOM_BYTES + off),
                            smem_desc(sb + atom * C::B_ATOM_BYTES + off), (k > 0 || kk > 0) ? 1u : 0u);
           }
-          mma_commit_mc(smem_u32(&empty_bar[stage]), CL_MASK);
+          mma_commit(smem_u32(&empty_bar[stage]));
           if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
         }
         mma_commit(smem_u32(&acc_full[ab]));
         ++tl;
         return true;
       };
-      for (int it = 0; it < nitems && ok; ++it) {
+      for (int it = 0; it < nitems && ok && !args.stall; ++it) {
         int t, kb, cnt;
         if (!item(it, t, kb, cnt)) continue;  // (a tile holds a block of C's pattern, so nk >= 1)
         if (!args.split) {
@@ -513,7 +509,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       // every MMA this thread issued completes before tensor memory is released
       mma_commit(smem_u32(&drain_bar));
-      mbar_wait(smem_u32(&drain_bar), 0, &abort_flag, args.err, false);
+      mbar_wait(smem_u32(&drain_bar), 0, &abort_flag, args.err, false, wl);
     }
   } else {
     // ------------------------------ epilogue ------------------------------
@@ -528,7 +524,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int it = 0; it < nitems && good; ++it) {
       int t, kb, cnt;
       if (!item(it, t, kb, cnt)) continue;
-      const int I0 = (args.tiles[2 * t] * CL + (int)crank) * TM, J0 = args.tiles[2 * t + 1] * C::TN;
+      const int I0 = (args.tiles[2 * t] * PAIR + crank) * TM, J0 = args.tiles[2 * t + 1] * C::TN;
       const int I = I0 + r_blk;  // warp-uniform: a warp's 32 rows lie in one block row
       int pc[C::TN];             // position of C_{I, J0+c} in C, or -1
 #pragma unroll
@@ -545,14 +541,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int ab = tl & 1;
         const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
         ++tl;
-        const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
+        const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err, true, wl);
         __syncwarp();  // lanes leave the poll independently; tcgen05.ld needs the whole warp
         if (!__all_sync(0xffffffffu, got)) break;
         tc_fence_after();
 #pragma unroll 1
         for (int c = c0; c < c1; ++c) {
           const int p = pc[c];
-          float ssf = 0.0f;  // this thread's 64 squares (FP32: the values carry FP32 accumulation anyway)
+          SqAcc sq;  // this thread's 64 squares, accurate to about 2^-42 (FP32 pipe)
 #pragma unroll
           for (int h = 0; h < BS / 32; ++h) {
             float v[32];
@@ -568,7 +564,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                   const float a = v[half * 16 + e] * alpha_f;
-                  ssf = fmaf(a, a, ssf);
+                  sq.add(a);
                   sw[lane * 17 + e] = a;
                 }
                 __syncwarp();
@@ -579,7 +575,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
             }
           }
-          double ss = (double)ssf;
+          double ss = sq.value();
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
           if (lane == 0) partial[q][c] = ss;
@@ -606,7 +602,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int ab = tl & 1;
           const uint32_t aphase = (uint32_t)(tl >> 1) & 1u;
           ++tl;
-          const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
+          const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err, true, wl);
           __syncwarp();
           if (!__all_sync(0xffffffffu, got)) { good = false; break; }
           tc_fence_after();
@@ -646,7 +642,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync_all();  // no CTA leaves while its peer may still signal its barriers
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -1074,8 +1069,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   const CUtensorMap mapA = make_map<ELT>(la_p, A.nnzb + 1);
   const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
-  constexpr int CL = Cf::CL;
-  Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false);
+  Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false);
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
                                                                       upper ? 1 : 0, pairs, nullptr, 0);
   IFAC_CK_LAUNCH();
@@ -1104,33 +1098,12 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.nunits = 0;
   for (int u = 0; u < MAX_UNITS; ++u) args.unit_end[u] = args.unit_sh[u] = 0;
   for (int p = 0; p < MAX_PAIRS; ++p) args.pair_ya[p] = args.pair_yb[p] = 0;
-  // at most one cluster per tile; idle clusters return at once
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr_cl[1];
-  attr_cl[0].id = cudaLaunchAttributeClusterDimension;
-  attr_cl[0].val.clusterDim.x = CL;
-  attr_cl[0].val.clusterDim.y = 1;
-  attr_cl[0].val.clusterDim.z = 1;
-  cfg.attrs = attr_cl;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3((unsigned)(sms / CL * CL), 1, 1);
-  static int max_clusters_dev[64] = {};  // clusters of CL CTAs that fit at once (GPC boundaries), per device
-  int& max_clusters = max_clusters_dev[ctx->device & 63];
-  if (!max_clusters) {
-    int mc = 0;
-    if (cudaOccupancyMaxActiveClusters(&mc, k_gemm_tc<ELT>, &cfg) != cudaSuccess || mc < 1) {
-      cudaGetLastError();
-      mc = sms / CL;
-    }
-    max_clusters = mc;
-  }
-  const int64_t clusters = std::min<int64_t>(std::max(P.ntiles, 1), max_clusters);
-  cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
+  args.stall = 0;
+  args.wait_limit = WAIT_LIMIT;
+  // one CTA per SM, in pairs; at most one pair per tile (idle pairs return at once)
+  const int64_t pairs_grid = std::min<int64_t>(std::max(P.ntiles, 1), sms / PAIR);
   prof_begin(ctx, 1);
-  IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<ELT>, mapA, mapB, args));
+  k_gemm_tc<ELT><<<(unsigned)(pairs_grid * PAIR), NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mapA, mapB, args);
   IFAC_CK_LAUNCH();
   prof_end(ctx);
   ++ctx->tc_launches;
@@ -1379,7 +1352,6 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                       unsigned long long* pairs, OperandCache* ac) {
   using Cf = Cfg<2>;
-  constexpr int CL = Cf::CL;
   const int nb = A.nb;
   const int64_t rows = (int64_t)nb * BS;
   if (ns < 1 || ns > 8) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 8 slices");
@@ -1428,7 +1400,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const CUtensorMap mA = make_map<2>(la_p, (int64_t)ns * (A.nnzb + 1));
   const CUtensorMap mB = make_map<2>(lb.p, (int64_t)ns * (B.nnzb + 1));
   // tile plan (as for the plain tensor-core product) with the longest tile's K steps
-  Plan P = make_plan<CL * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
+  Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
   // block pairs, and block pairs times the ns (ns + 1) / 2 slice pairs
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
                                                                       upper ? 1 : 0, pairs, pairs + 1,
@@ -1468,6 +1440,8 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   args.err = ctx->dev_err;
   args.split = 1;
   args.cpart = part.p;
+  args.stall = 0;
+  args.wait_limit = WAIT_LIMIT;
   // fixed point, scale 2^-f relative to sigma_i tau_j, with every partial sum
   // below 2^62: |sum_ij| <= min(sum_k |a_ik| / sigma_i, sum_k |b_kj| / tau_j)
   // (|a / sigma|, |b / tau| < 1), bounded by the largest scaled row / column
@@ -1517,28 +1491,11 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     }
     args.nunits = nu;
   };
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = Cf::SMEM_BYTES;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute attr_cl[1];
-  attr_cl[0].id = cudaLaunchAttributeClusterDimension;
-  attr_cl[0].val.clusterDim.x = CL;
-  attr_cl[0].val.clusterDim.y = 1;
-  attr_cl[0].val.clusterDim.z = 1;
-  cfg.attrs = attr_cl;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3((unsigned)(sms / CL * CL), 1, 1);
-  int max_clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&max_clusters, k_gemm_tc<2>, &cfg) != cudaSuccess || max_clusters < 1) {
-    cudaGetLastError();
-    max_clusters = sms / CL;
-  }
-  cfg.gridDim = dim3((unsigned)(std::min<int64_t>(std::max(P.ntiles, 1), max_clusters) * CL), 1, 1);
+  const int64_t pairs_grid = std::min<int64_t>(std::max(P.ntiles, 1), sms / PAIR);
   set_units(fbits);
   args.ovf = ctx->dev_err;
   prof_begin(ctx, 2);
-  IFAC_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc<2>, mA, mB, args));
+  k_gemm_tc<2><<<(unsigned)(pairs_grid * PAIR), NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mA, mB, args);
   IFAC_CK_LAUNCH();
   prof_end(ctx);
   ++ctx->split_launches;
@@ -1551,7 +1508,49 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   IFAC_CK_LAUNCH();
 }
 
+// Failure-path self-test of the bounded waits: one pair of CTAs over a
+// one-tile product (1 x 1 blocks of a 64-row matrix) whose producer and MMA
+// issuer do no work, so the epilogue's accumulator wait expires after
+// wait_limit polls.  Nothing is copied or multiplied; every CTA releases its
+// tensor memory and returns, and the host sees the device error flag.
+static void stall_selftest(ifac_ctx* ctx, long long wait_limit) {
+  using Cf = Cfg<2>;
+  Buf<uint8_t> zeros(ctx, (size_t)2 * BS * BS * 2);
+  IFAC_CK(cudaMemsetAsync(zeros.p, 0, zeros.n, ctx->stream));
+  const CUtensorMap m = make_map<2>(zeros.p, 2);
+  // tiles {0, 0}; one tile; one K step; plan records all zero; C pattern: one block
+  Buf<int32_t> small(ctx, 32);
+  const int32_t host[32] = {0, 0, /*ntiles*/ 1, /*nk*/ 1, /*rec_off*/ 0, 1, /*crp*/ 0, 1, /*cci*/ 0};
+  IFAC_CK(cudaMemcpyAsync(small.p, host, sizeof(host), cudaMemcpyHostToDevice, ctx->stream));
+  Buf<double> cval(ctx, (size_t)BS * BS + 1);
+  TileArgs args{};
+  args.tiles = small.p;
+  args.ntiles = small.p + 2;
+  args.tile_nk = small.p + 3;
+  args.nwin = 1;
+  args.nb = 1;
+  args.rec = small.p + 9;  // zeros
+  args.rec_off = small.p + 4;
+  args.crp = small.p + 6;
+  args.cci = small.p + 8;
+  args.cval = cval.p;
+  args.cnorm = cval.p + BS * BS;
+  args.alpha = 1.0;
+  args.err = ctx->dev_err;
+  args.split = 0;
+  args.stall = 1;
+  args.wait_limit = wait_limit;
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr, ctx->device))
+    IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
+  k_gemm_tc<2><<<PAIR, NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(m, m, args);
+  IFAC_CK_LAUNCH();
+  IFAC_CK(cudaStreamSynchronize(ctx->stream));
+}
+
 }  // namespace tc
+
+void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit) { tc::stall_selftest(ctx, wait_limit); }
 
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,

@@ -181,6 +181,9 @@ struct OperandCache {
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache = nullptr);
+// Failure-path self-test: a tensor-core launch whose pipeline never fills, so
+// its bounded waits expire after wait_limit polls (sets the device error flag).
+void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit);
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
                  double gamma, ifac_bsr& C, const int32_t* crow);
 // C = alpha (U + strict_upper(U)^T) + beta B + gamma I on the pattern of sym_pattern

@@ -2,11 +2,10 @@
 // not allocate device memory.
 //
 // Some callers cannot call cudaMalloc (or any allocating routine) at the
-// moment they need this routine: code that runs while a CUDA stream is being
-// captured into a graph (allocation calls are not allowed there), code inside
-// a host framework that owns the device memory budget and forbids hidden
-// allocations, or latency-critical loops where an allocation's implicit
-// synchronisation is not acceptable.  leaf_invchol_batched allocates its
+// moment they need this routine: code inside a host framework that owns the
+// whole device-memory budget and forbids hidden allocations (its own caching
+// allocator would otherwise be bypassed), or latency-critical loops where an
+// allocation's implicit synchronisation with the device is not acceptable.  leaf_invchol_batched allocates its
 // scratch (the inverses of the diagonal tiles, and identity-padded copies when
 // nl is not a multiple of 32) from the context's pool; this variant takes that
 // scratch from one fixed array in device memory instead and allocates nothing.
@@ -15,7 +14,9 @@
 // library holds IFAC_NOALLOC_SCRATCH_DOUBLES doubles (32 MiB) until the
 // process exits.  In host code `g_leaf_scratch` names a host-side stand-in,
 // not device memory, so its device address is looked up once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// cudaGetSymbolAddress and passed to the kernels.  The cached address belongs
+// to the device's current context: resetting the device (cudaDeviceReset)
+// between calls is not supported.
 #include <mutex>
 
 #include "internal.cuh"
@@ -61,6 +62,10 @@ extern "C" int leaf_invchol_batched_noalloc(void* stream, int count, int nl, con
   int rc = scratch_for_current_device(&scratch);
   if (rc != IFAC_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // in place (S == Z) or disjoint: a partial overlap has no defined copy
+  const uintptr_t bytes = sizeof(double) * (uintptr_t)count * (uintptr_t)nl * (uintptr_t)nl;
+  const uintptr_t s0 = reinterpret_cast<uintptr_t>(S), z0 = reinterpret_cast<uintptr_t>(Z);
+  if (S != Z && s0 < z0 + bytes && z0 < s0 + bytes) return IFAC_ERR_INVALID;
   if (S != Z) {
     if (cudaMemcpyAsync(Z, S, sizeof(double) * (size_t)count * nl * nl, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return IFAC_ERR_CUDA;

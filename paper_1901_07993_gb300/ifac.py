@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libifac.so")
 OK, WARN_TARGET_NOT_MET = 0, 1
 TF32, BF16, FP64_SPLIT = 1, 2, 3
 ERR_INVALID, ERR_NOT_SPD, ERR_NO_CONVERGENCE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -7
-ERR_TOO_LARGE = -8
+ERR_TIMEOUT, ERR_TOO_LARGE = -6, -8
 FP64 = 0
 STOP_RULE, STOP_TARGET, STOP_MAXITER, STOP_FIXED = 1, 2, 3, 4
 
@@ -32,7 +32,7 @@ EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", 
            "bsr_add", "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
            "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
            "inv_factor_refine_adjoint", "inv_factor_refine_batched", "ifac_set_split_slices",
-           "inv_factor_rinch")
+           "inv_factor_rinch", "ifac_selftest_wait_timeout")
 
 
 class IfacError(RuntimeError):
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "leaf_invchol_batched_noalloc": ([p, i32, i32, p, p, p], i32),
         "inv_factor_refine_adjoint": ([p, PB, PB, i32, d, ctypes.POINTER(d), PB], i32),
         "inv_factor_refine_batched": ([p, i32, p, d, d, ctypes.POINTER(_Opts), p, p], i32),
+        "ifac_selftest_wait_timeout": ([p, i64], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -122,14 +123,34 @@ def _current_stream() -> int:
     return 0
 
 
-class Context:
-    """A library context on the current device and (by default) torch's current stream."""
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
-    def __init__(self, stream: int | None = None):
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
+
+
+class Context:
+    """A library context on the current device and (by default) torch's current stream.
+
+    allocator: optional (alloc, free) pair of Python callables, alloc(bytes,
+    stream) -> device address or 0 on failure, free(address, stream); the
+    library then takes every device buffer from it (ifac_allocator)."""
+
+    def __init__(self, stream: int | None = None, allocator=None):
         self.lib = load()
         h = ctypes.c_void_p()
+        arg = None
+        if allocator is not None:
+            a_fn, f_fn = allocator
+            # the callbacks must outlive the context
+            self._alloc_cb = _ALLOC_FN(lambda user, nbytes, st: a_fn(int(nbytes), st or 0) or None)
+            self._free_cb = _FREE_FN(lambda user, ptr, st: f_fn(ptr, st or 0))
+            self._alloc = _Allocator(self._alloc_cb, self._free_cb, None)
+            arg = ctypes.byref(self._alloc)
         rc = self.lib.ifac_create(ctypes.byref(h), ctypes.c_void_p(_current_stream() if stream is None else stream),
-                                  None)
+                                  arg)
         if rc != 0:
             raise IfacError(rc, "ifac_create failed")
         self.h = h
@@ -412,6 +433,12 @@ def inv_factor_resid(ctx: Context, S: DeviceBSR, Z: DeviceBSR) -> float:
     out = ctypes.c_double()
     ctx.check(ctx.lib.inv_factor_resid(ctx.h, S.ptr(), Z.ptr(), ctypes.byref(out)))
     return out.value
+
+
+def selftest_wait_timeout(ctx: Context, wait_limit: int) -> int:
+    """Failure-path self-test of the bounded device waits (include/ifac.h):
+    returns the status code (IFAC_ERR_TIMEOUT expected) without raising."""
+    return ctx.lib.ifac_selftest_wait_timeout(ctx.h, int(wait_limit))
 
 
 def leaf_invchol_batched_noalloc(stream: int, S, Z, info) -> int:

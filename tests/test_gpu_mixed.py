@@ -6,7 +6,11 @@ with the oracle's FP64 factor, and the error is stated; the direct FP64
 residual ||I - Z^T S Z||_F must reach the target.  With low-precision
 corrections the iterates leave the polynomials in S, so Z converges to another
 inverse factor S^-1/2 Q (Q near orthogonal): its distance to the FP64 factor is
-stated, and bounded only loosely by the format's unit roundoff."""
+stated, and bounded by three times the distance measured on GB300 for each
+case (chain n = 4096: TF32 7.0e-5, BF16 5.5e-4; 3D cluster n = 1024: TF32
+7.2e-4, BF16 5.5e-3), so that a change in the low-precision products shows.
+The residual is the oracle's FP64 ||I - Z^T S Z||_F of the downloaded factor,
+not the library's own."""
 import numpy as np
 import pytest
 
@@ -34,15 +38,19 @@ def test_mixed_refine_reaches_target(ctx, prec, kind, n):
     tau, target = 1e-13, 1e-10
     dS = ifac.upload(ctx, S)
     Z, rep = ifac.inv_factor_refine(ctx, dS, tau, target, ifac.opts(prec=prec, max_iter=80))
-    resid = ifac.inv_factor_resid(ctx, dS, Z)
-    Z_ref, rep_ref = oracle.irsi(S, tau=tau, target=target, max_iter=80)
     a = Z.download()
-    za = oracle.Mat(a.n, 64, a.row_ptr, a.col_idx, a.val).to_dense()
+    Zh = oracle.Mat(a.n, 64, a.row_ptr, a.col_idx, a.val)
+    resid = oracle.resid(S, Zh)
+    resid_gpu = ifac.inv_factor_resid(ctx, dS, Z)
+    Z_ref, rep_ref = oracle.irsi(S, tau=tau, target=target, max_iter=80)
+    za = Zh.to_dense()
     zr = Z_ref.to_dense()
     rel = np.linalg.norm(za - zr) / np.linalg.norm(zr)
-    print(f"{kind} n={n} prec={prec}: resid {resid:.2e}, rel err vs FP64 oracle {rel:.2e}, "
+    print(f"{kind} n={n} prec={prec}: resid {resid:.2e} (library {resid_gpu:.2e}), rel err vs FP64 oracle {rel:.2e}, "
           f"low sweeps {rep.low_sweeps}, FP64 delta evals {rep.fp64_delta_evals}, deltas {rep.delta_fro}")
     assert rep.fp64_delta_evals >= 1 and rep.low_sweeps >= 2
     assert rep.delta_fro[-1] <= target
     assert resid <= 10 * target
-    assert rel <= (2e-3 if prec == 1 else 2e-2)
+    assert abs(resid_gpu - resid) <= 1e-3 * resid + 1e-13
+    measured = {("chain", 1): 7.0e-5, ("chain", 2): 5.5e-4, ("cluster", 1): 7.2e-4, ("cluster", 2): 5.5e-3}
+    assert rel <= 3 * measured[(kind, prec)]

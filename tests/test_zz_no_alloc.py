@@ -1,15 +1,17 @@
 """The allocation-free leaf inverse Cholesky (leaf_invchol_batched_noalloc).
 
 It exists for callers that cannot allocate device memory when they need the
-leaf routine (work recorded into a CUDA graph during stream capture, hosts
-that own the whole device-memory budget, loops that cannot pay an
-allocation's synchronisation): it takes its scratch from a fixed 32 MiB
-device array inside the library instead of the context's allocator.
+leaf routine (hosts that own the whole device-memory budget, loops that
+cannot pay an allocation's synchronisation with the device): it takes its
+scratch from a fixed 32 MiB device array inside the library instead of the
+context's allocator.
 
 Called through the C ABI with ctypes, twice in a row per case (the shared
 scratch keeps the previous call's contents), its output must match the
 allocating entry point leaf_invchol_batched within the tolerance the other
-leaf tests use.  Kept in a file that pytest collects last.
+leaf tests use, and the oracle's dense inverse Cholesky factor.  The
+in-place form (S == Z) is run too, and a partial overlap of S and Z is
+rejected.  Kept in a file that pytest collects last.
 """
 import ctypes
 
@@ -52,6 +54,13 @@ def test_noalloc_matches_allocating_leaf_routine(count, nl):
     assert rc_ref == 0
     Z_ref = Z_ref.cpu().numpy()
 
+    import oracle
+    Sh = S.cpu().numpy()
+    Z_or = [oracle.invchol(Sh[k]) for k in range(count)]
+    for k in range(count):
+        err = np.linalg.norm(Z_ref[k] - Z_or[k]) / np.linalg.norm(Z_or[k])
+        assert err <= TOL, ("allocating routine vs oracle", k, err)
+
     for call in range(2):
         Z = torch.full_like(S, float("nan"))
         info = torch.full((count,), -1, dtype=torch.int32, device="cuda")
@@ -63,6 +72,21 @@ def test_noalloc_matches_allocating_leaf_routine(count, nl):
         for k in range(count):
             err = np.linalg.norm(Zh[k] - Z_ref[k]) / np.linalg.norm(Z_ref[k])
             assert err <= TOL, (call, k, err)
+            err = np.linalg.norm(Zh[k] - Z_or[k]) / np.linalg.norm(Z_or[k])
+            assert err <= TOL, ("vs oracle", call, k, err)
+
+    # in place (S == Z): the factors overwrite the inputs
+    for call in range(2):
+        W = S.clone()
+        info = torch.full((count,), -1, dtype=torch.int32, device="cuda")
+        rc = fn(stream, count, nl, W.data_ptr(), W.data_ptr(), info.data_ptr())
+        assert rc == ifac.OK, ("in place", call, rc)
+        torch.cuda.current_stream().synchronize()
+        assert info.cpu().tolist() == [0] * count
+        Wh = W.cpu().numpy()
+        for k in range(count):
+            err = np.linalg.norm(Wh[k] - Z_ref[k]) / np.linalg.norm(Z_ref[k])
+            assert err <= TOL, ("in place", call, k, err)
 
 
 def test_noalloc_reports_not_spd_and_rejects_oversize():
@@ -94,3 +118,13 @@ def test_noalloc_reports_not_spd_and_rejects_oversize():
     rc = ifac.load().leaf_invchol_batched_noalloc(stream, count, nl, tiny.data_ptr(), tiny.data_ptr(),
                                                   tiny.data_ptr())
     assert rc == ifac.ERR_TOO_LARGE
+    # S and Z overlapping without being equal: rejected before any copy
+    buf = torch.tensor(np.concatenate([S, S]), device="cuda")
+    before = buf.clone()
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    off = 64 * 64 * 8  # Z starts one matrix into S
+    rc = ifac.load().leaf_invchol_batched_noalloc(stream, 2, 64, buf.data_ptr(), buf.data_ptr() + off,
+                                                  info.data_ptr())
+    assert rc == ifac.ERR_INVALID
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(buf, before)
