@@ -46,10 +46,22 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into _oracle.so (plain gcc, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O3", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O3", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        # OpenMP over output block rows where the compiler has it; plain otherwise
+        if subprocess.call(base[:-1] + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel block-row loop (1 = single-threaded)."""
+    _load().om_set_threads(int(n))
+
+
+def max_threads() -> int:
+    """Threads the parallel loop uses now (1 in a build without OpenMP)."""
+    return int(_load().om_max_threads())
 
 
 class _Opts(ctypes.Structure):
@@ -92,6 +104,8 @@ def _load():
             "om_resid": ([p, p], d),
             "om_counter_products": ([], i64),
             "om_counter_pairs": ([], i64),
+            "om_set_threads": ([i32], None),
+            "om_max_threads": ([], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)

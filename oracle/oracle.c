@@ -31,6 +31,9 @@
  *
  * Every loop is the definition written out; there is no blocking, fusion or
  * reordering beyond the block structure the paper's storage itself has.
+ * om_gemm forms its output block rows independently; with OpenMP they are
+ * spread over threads (om_set_threads), which changes no result: every
+ * block row is summed in the same order by whichever thread forms it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -256,49 +259,87 @@ om_mat* om_gemm(const om_mat* A, int tA, const om_mat* B, int tB, double alpha, 
   if (tB) b = bt = om_transpose(B);
   int bs = a->bs, nb = a->nb;
   size_t bsz = (size_t)bs * bs;
-  double* acc = (double*)malloc((size_t)nb * bsz * sizeof(double));
-  char* touched = (char*)calloc((size_t)nb, 1);
-  int32_t* cols = (int32_t*)malloc((size_t)nb * sizeof(int32_t));
-  om_builder out = ob_begin(A->n, bs, nb);
+  /* Output block rows are independent: each is formed on its own (by one
+   * thread when OpenMP is on) into a row buffer, and the rows are then
+   * appended in order.  A row's arithmetic is the same whatever the thread
+   * count, so results are identical with one thread or many. */
+  int32_t** row_cols = (int32_t**)calloc((size_t)nb, sizeof(int32_t*));
+  double** row_vals = (double**)calloc((size_t)nb, sizeof(double*));
+  int* row_n = (int*)calloc((size_t)nb, sizeof(int));
+  int64_t pairs = 0;
   g_products++;
-  for (int I = 0; I < nb; ++I) {
-    int ncols = 0;
-    for (int p = a->row_ptr[I]; p < a->row_ptr[I + 1]; ++p) {
-      int K = a->col_idx[p];
-      const double* aik = a->val + (size_t)p * bsz;
-      for (int q = b->row_ptr[K]; q < b->row_ptr[K + 1]; ++q) {
-        int J = b->col_idx[q];
-        const double* bkj = b->val + (size_t)q * bsz;
-        double* cij = acc + (size_t)J * bsz;
-        if (!touched[J]) {
-          touched[J] = 1;
-          cols[ncols++] = J;
-          memset(cij, 0, bsz * sizeof(double));
-        }
-        g_pairs++;
-        for (int i = 0; i < bs; ++i)
-          for (int k = 0; k < bs; ++k) {
-            double x = aik[i * bs + k];
-            for (int j = 0; j < bs; ++j) cij[i * bs + j] += x * bkj[k * bs + j];
+#pragma omp parallel reduction(+ : pairs)
+  {
+    double* acc = (double*)malloc((size_t)nb * bsz * sizeof(double));
+    char* touched = (char*)calloc((size_t)nb, 1);
+#pragma omp for schedule(dynamic, 4)
+    for (int I = 0; I < nb; ++I) {
+      int ncols = 0;
+      for (int p = a->row_ptr[I]; p < a->row_ptr[I + 1]; ++p) {
+        int K = a->col_idx[p];
+        const double* aik = a->val + (size_t)p * bsz;
+        for (int q = b->row_ptr[K]; q < b->row_ptr[K + 1]; ++q) {
+          int J = b->col_idx[q];
+          const double* bkj = b->val + (size_t)q * bsz;
+          double* cij = acc + (size_t)J * bsz;
+          if (!touched[J]) {
+            touched[J] = 1;
+            ++ncols;
+            memset(cij, 0, bsz * sizeof(double));
           }
+          pairs++;
+          for (int i = 0; i < bs; ++i)
+            for (int k = 0; k < bs; ++k) {
+              double x = aik[i * bs + k];
+              for (int j = 0; j < bs; ++j) cij[i * bs + j] += x * bkj[k * bs + j];
+            }
+        }
       }
+      /* scale, truncate and keep in increasing J */
+      int32_t* cols = (int32_t*)malloc((size_t)(ncols ? ncols : 1) * sizeof(int32_t));
+      double* vals = (double*)malloc((size_t)(ncols ? ncols : 1) * bsz * sizeof(double));
+      int kept = 0;
+      for (int J = 0, left = ncols; J < nb && left > 0; ++J) {
+        if (!touched[J]) continue;
+        --left;
+        touched[J] = 0;
+        double* cij = acc + (size_t)J * bsz;
+        for (size_t e = 0; e < bsz; ++e) cij[e] *= alpha;
+        if (block_fro(cij, bs) < tau) continue;
+        cols[kept] = J;
+        memcpy(vals + (size_t)kept * bsz, cij, bsz * sizeof(double));
+        ++kept;
+      }
+      row_cols[I] = cols;
+      row_vals[I] = vals;
+      row_n[I] = kept;
     }
-    /* emit in increasing J */
-    for (int J = 0, left = ncols; J < nb && left > 0; ++J) {
-      if (!touched[J]) continue;
-      --left;
-      touched[J] = 0;
-      double* cij = acc + (size_t)J * bsz;
-      for (size_t e = 0; e < bsz; ++e) cij[e] *= alpha;
-      if (block_fro(cij, bs) < tau) continue;
-      memcpy(ob_push(&out, J), cij, bsz * sizeof(double));
-    }
-    ob_end_row(&out, I);
+    free(acc);
+    free(touched);
   }
-  free(acc); free(touched); free(cols);
+  g_pairs += pairs;
+  om_builder out = ob_begin(A->n, bs, nb);
+  for (int I = 0; I < nb; ++I) {
+    for (int e = 0; e < row_n[I]; ++e) memcpy(ob_push(&out, row_cols[I][e]), row_vals[I] + (size_t)e * bsz,
+                                              bsz * sizeof(double));
+    ob_end_row(&out, I);
+    free(row_cols[I]);
+    free(row_vals[I]);
+  }
+  free(row_cols); free(row_vals); free(row_n);
   om_free(at); om_free(bt);
   return out.m;
 }
+
+/* Threads of the parallel loops (OpenMP builds; 1 otherwise). */
+#ifdef _OPENMP
+#include <omp.h>
+void om_set_threads(int t) { omp_set_num_threads(t > 0 ? t : 1); }
+int om_max_threads(void) { return omp_get_max_threads(); }
+#else
+void om_set_threads(int t) { (void)t; }
+int om_max_threads(void) { return 1; }
+#endif
 
 /* C = alpha A + beta B + gamma I on the union pattern (B may be NULL).
  * Per row, the sorted column lists of A, B and the diagonal are merged. */

@@ -229,18 +229,29 @@ __device__ __forceinline__ long long fixed_add(long long d, int x, int sh, bool&
 struct SqAcc {
   float hi = 0.0f, lo = 0.0f;
   double big = 0.0;
-  __device__ __forceinline__ void add(float x) {
-    if (fabsf(x) < 268435456.0f) {
-      const float y = x * 4294967296.0f;
-      const float p = y * y;
-      const float e = fmaf(y, y, -p);
-      const float s = hi + p;
-      const float bp = s - hi;
-      const float err = (hi - (s - bp)) + (p - bp);
-      hi = s;
-      lo += err + e;
+  // |x| < 2^28 (the caller checks a whole chunk first)
+  __device__ __forceinline__ void add_small(float x) {
+    const float y = x * 4294967296.0f;
+    const float p = y * y;
+    const float e = fmaf(y, y, -p);
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += err + e;
+  }
+  // 32 values: the FP32 path when all are below 2^28 (the usual case), else
+  // FP64 squares (a separate branch of 32 FP64 FMAs)
+  __device__ __forceinline__ void add32(const float (&v)[32]) {
+    float mx = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[i]));
+    if (mx < 268435456.0f) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) add_small(v[i]);
     } else {
-      big = fma((double)x, (double)x, big);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) big = fma((double)v[i], (double)v[i], big);
     }
   }
   __device__ __forceinline__ double value() const {
@@ -554,6 +565,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * C::N + c * BS + h * 32), v);
             if (p >= 0) {  // warp-uniform
+#pragma unroll
+              for (int e = 0; e < 32; ++e) v[e] *= alpha_f;
+              sq.add32(v);
               // 32 rows x 16 columns at a time through shared memory, so that
               // each store instruction writes two 128-byte row segments
               float* sw = ep_stage[warp - 2];
@@ -562,11 +576,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
               for (int half = 0; half < 2; ++half) {
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                  const float a = v[half * 16 + e] * alpha_f;
-                  sq.add(a);
-                  sw[lane * 17 + e] = a;
-                }
+                for (int e = 0; e < 16; ++e) sw[lane * 17 + e] = v[half * 16 + e];
                 __syncwarp();
 #pragma unroll 4
                 for (int k = 0; k < 32; k += 2)
@@ -953,7 +963,10 @@ struct Plan {
 
 template <int ROWS, int COLS>
 static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool tA, const View& brows,
-                      const ifac_bsr& B, const ifac_bsr& C, const int32_t* crow, bool want_kmax) {
+                      const ifac_bsr& B, const ifac_bsr& C, const int32_t* crow, bool want_kmax,
+                      int kmax_limit = 0) {
+  // kmax_limit > 0: a plan whose longest tile has more K steps is not wanted;
+  // it returns after the count pass with kmax set and no records
   const int nb = A.nb, W = words_per_row(nb);
   Plan P;
   // K sets (bitmap rows of op(A)); dense block-index maps of op(A), op(B)
@@ -1010,6 +1023,7 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
   if (total > (int64_t)0x7fffffff / (ROWS + COLS))
     fail(IFAC_ERR_TOO_LARGE, "tensor-core product: tile plan exceeds 2^31 entries");
   if (want_kmax) to_host(ctx, &P.kmax, dk.p, sizeof(int));
+  if (want_kmax && kmax_limit > 0 && P.kmax > kmax_limit) return P;
   P.rec = Buf<int32_t>(ctx, (size_t)std::max<int64_t>(total, 1) * (ROWS + COLS));
   if (nt > 0) {
     k_tile_plan<ROWS, COLS, false><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
@@ -1348,6 +1362,302 @@ __global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split products of banded patterns.  Tiles of 128 x 64 (two block rows, one
+// block column), no cluster.  When no tile has more than KW K steps and the
+// accumulation units of that bound number at most 8, every unit keeps its own
+// FP32 accumulator in tensor memory (8 x 64 columns) for the whole tile.  Each
+// K step then loads every slice tile once -- slice k of the two op(A) blocks
+// and of the op(B) block share one ring slot -- and issues, as soon as slot k
+// has landed, the MMAs of the pairs (a, b) with max(a, b) = k; a slot is
+// released after the last pair that reads it.  At the end of the tile the
+// epilogue adds the units' accumulators into 64-bit fixed-point sums in
+// registers and stores them once, in the hand-over layout that k_split_finish
+// converts.
+// ---------------------------------------------------------------------------
+namespace band {
+constexpr int TMB = 2;                      // block rows per tile
+constexpr int M = TMB * BS;                 // 128 accumulator rows
+constexpr int N = BS;                       // 64 accumulator columns
+constexpr int MAX_U = 8;                    // units live at once: 8 x 64 = 512 columns
+constexpr int SLOT_A = M * 128;             // one BF16 slice of both op(A) blocks (K = 64: one 128-byte atom)
+constexpr int SLOT_B = N * 128;             // one BF16 slice of the op(B) block
+constexpr int SLOT_BYTES = SLOT_A + SLOT_B; // 24 KB, a multiple of 1024 (128-byte swizzle groups)
+constexpr int RING = 9;                     // slots: one K step of up to 8 slices plus prefetch
+constexpr int SMEM_BYTES = RING * SLOT_BYTES + 1024;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TX_BYTES = (uint32_t)SLOT_BYTES;
+// FP32 accumulate, A = B = BF16, both K-major, N = 64, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                           ((uint32_t)(M >> 4) << 24);
+}  // namespace band
+
+struct BandArgs {
+  const int32_t* tiles;    // [2t] tile row (pairs of block rows), [2t+1] block column
+  const int* ntiles;       // device: number of tiles
+  const int* tile_nk;      // device: K steps of each tile
+  const int32_t* rec;      // plan: per K step, copy indices of op(A)_{I0,K}, op(A)_{I0+1,K}, op(B)_{K,J}
+  const int32_t* rec_off;  // first record of each tile
+  const int32_t* crp;      // C pattern
+  const int32_t* cci;
+  longlong2* cpart;        // fixed-point sums, hand-over layout (as TileArgs::cpart)
+  int nb;
+  int ns;                  // slices per operand (1..8)
+  int slice_rows_a;        // tensor-map rows between consecutive slices of op(A): (nnzb_A + 1) * 64
+  int slice_rows_b;
+  int nunits;
+  int unit_sh[band::MAX_U];
+  int npairs;
+  int slot_beg[9];         // pairs issued once slot k has landed: [slot_beg[k], slot_beg[k + 1])
+  int pair_a[MAX_PAIRS], pair_b[MAX_PAIRS], pair_u[MAX_PAIRS];  // slices (0-based) and unit, issue order
+  int rel_beg[9];          // slots released after slot k's MMAs: rel[rel_beg[k] .. rel_beg[k + 1])
+  int rel[8];
+  int* err;
+  int* ovf;
+};
+
+__device__ __forceinline__ void mma_band(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(band::IDESC), "r"(accumulate));
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_split_band(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                      BandArgs args) {
+  using namespace band;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[RING], empty_bar[RING];
+  __shared__ __align__(8) uint64_t acc_full, acc_empty, drain_bar;
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int ntiles = *args.ntiles;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < RING; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_full), 1);
+    mbar_init(smem_u32(&acc_empty), 1);
+    mbar_init(smem_u32(&drain_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_slot;
+  // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int mt = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      int slot = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, last_parity = 0;
+      bool ok = true;
+      for (int it = 0; it < mt && ok; ++it) {
+        const int t = (int)blockIdx.x + it * (int)gridDim.x;
+        const int nk = args.tile_nk[t];
+        const int32_t* r = args.rec + (size_t)args.rec_off[t] * 3;
+        for (int j = 0; j < nk && ok; ++j, r += 3) {
+          const int a0 = r[0], a1 = r[1], b0 = r[2];
+          for (int k = 0; k < args.ns; ++k) {
+            if (!mbar_wait(smem_u32(&empty_bar[slot]), phase ^ 1u, &abort_flag, args.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = smem_u32(&full_bar[slot]);
+            mbar_expect_tx(fb, TX_BYTES);
+            issued_mask |= 1u << slot;
+            last_parity = (last_parity & ~(1u << slot)) | (phase << slot);
+            const uint32_t sa = smem_base + (uint32_t)(slot * SLOT_BYTES);
+            const int ya = k * args.slice_rows_a, yb = k * args.slice_rows_b;
+            tma_load_2d(sa, &mapA, 0, ya + a0 * BS, fb);
+            tma_load_2d(sa + BS * 128, &mapA, 0, ya + a1 * BS, fb);
+            tma_load_2d(sa + SLOT_A, &mapB, 0, yb + b0 * BS, fb);
+            if (++slot == RING) {
+              slot = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      // the copies issued have landed and the MMAs have released every slot
+      for (int s = 0; s < RING; ++s)
+        if (issued_mask & (1u << s)) {
+          mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+          mbar_wait(smem_u32(&empty_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+        }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer ------------------------------
+    if (lane == 0) {
+      int slot = 0;  // ring position of the next slot to consume
+      uint32_t phase = 0, acc_phase = 0;
+      bool ok = true;
+      for (int it = 0; it < mt && ok; ++it) {
+        const int t = (int)blockIdx.x + it * (int)gridDim.x;
+        const int nk = args.tile_nk[t];
+        // the epilogue has read the previous tile's accumulators
+        if (!mbar_wait(smem_u32(&acc_empty), acc_phase ^ 1u, &abort_flag, args.err)) break;
+        tc_fence_after();
+        uint32_t started = 0;  // units whose accumulator holds this tile's sum
+        for (int j = 0; j < nk && ok; ++j) {
+          const int base = slot;  // position of slice 0 of this K step
+          for (int k = 0; k < args.ns; ++k) {
+            if (!mbar_wait(smem_u32(&full_bar[slot]), phase, &abort_flag, args.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            for (int q = args.slot_beg[k]; q < args.slot_beg[k + 1]; ++q) {
+              int pa = base + args.pair_a[q], pb = base + args.pair_b[q];
+              if (pa >= RING) pa -= RING;
+              if (pb >= RING) pb -= RING;
+              const int u = args.pair_u[q];
+              const uint32_t sa = smem_base + (uint32_t)(pa * SLOT_BYTES);
+              const uint32_t sb = smem_base + (uint32_t)(pb * SLOT_BYTES + SLOT_A);
+              const uint32_t tacc = tmem + (uint32_t)(u * N);
+#pragma unroll
+              for (int kk = 0; kk < BS / 16; ++kk)
+                mma_band(tacc, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
+                         (((started >> u) & 1u) || kk > 0) ? 1u : 0u);
+              started |= 1u << u;
+            }
+            for (int e = args.rel_beg[k]; e < args.rel_beg[k + 1]; ++e) {
+              int pr = base + args.rel[e];
+              if (pr >= RING) pr -= RING;
+              mma_commit(smem_u32(&empty_bar[pr]));
+            }
+            if (++slot == RING) {
+              slot = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&acc_full));
+        acc_phase ^= 1u;
+      }
+      // every MMA this thread issued completes before tensor memory is released
+      mma_commit(smem_u32(&drain_bar));
+      mbar_wait(smem_u32(&drain_bar), 0, &abort_flag, args.err, false);
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const int q = warp & 3;                  // tensor-memory lane quarter
+    const int half = (warp - 2) >> 2;        // column half of the block: columns 32 half .. 32 half + 31
+    const int row = q * 32 + lane;           // accumulator row 0..127
+    const int et = threadIdx.x - 64;
+    uint32_t acc_phase = 0;
+    for (int it = 0; it < mt; ++it) {
+      const int t = (int)blockIdx.x + it * (int)gridDim.x;
+      const int I = args.tiles[2 * t] * TMB + row / BS, J = args.tiles[2 * t + 1];
+      int p = -1;  // position of C_IJ in C (warp-uniform: a warp's rows lie in one block row)
+      if (I < args.nb && J < args.nb) {
+        const int lo = args.crp[I], hi = args.crp[I + 1];
+        const int k = lower_bound_i32(args.cci, lo, hi, J);
+        if (k < hi && args.cci[k] == J) p = k;
+      }
+      const bool got = mbar_wait(smem_u32(&acc_full), acc_phase, &abort_flag, args.err);
+      acc_phase ^= 1u;
+      __syncwarp();
+      if (!__all_sync(0xffffffffu, got)) break;
+      tc_fence_after();
+      long long s[32];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) s[e] = 0;
+      bool bad = false;
+#pragma unroll 1
+      for (int u = 0; u < args.nunits; ++u) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * N + half * 32), v);
+        const int sh = args.unit_sh[u];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) s[e] = fixed_add(s[e], __float2int_rn(v[e]), sh, bad);
+      }
+      // the accumulators are read: the next tile's MMAs may overwrite them
+      tc_fence_before();
+      epi_bar();
+      if (et == 0) mbar_arrive(smem_u32(&acc_empty));
+      if (p >= 0) {
+        longlong2* dst = args.cpart + (size_t)p * (BS * BS / 2) + (size_t)(((q & 1) * 2 + half) * 16) * 32 + lane;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          longlong2 d;
+          d.x = s[2 * e];
+          d.y = s[2 * e + 1];
+          dst[e * 32] = d;
+        }
+        if (bad) *args.ovf = 2;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(band::TMEM_COLS));
+  }
+}
+
+// Accumulation units of a split product with ns slices per operand: slice
+// pairs (s, t), s + t <= ns + 1, of equal weight 2^(-7 (s + t)) packed
+// greedily while sum over the unit of max|q_s| max|q_t| * 64 * kw stays
+// <= 2^24, kw = the K blocks a window holds (KW, or the longest tile's K
+// steps when fewer), so that every FP32 accumulator sums integers exactly.
+struct UnitTable {
+  int nunits = 0, npairs = 0;
+  int unit_end[MAX_UNITS] = {};  // pairs of unit u: [unit_end[u - 1], unit_end[u])
+  int unit_g[MAX_UNITS] = {};    // weight class s + t of unit u
+  int si[MAX_PAIRS] = {}, ti[MAX_PAIRS] = {}, pu[MAX_PAIRS] = {};  // slices (1-based) and unit of each pair
+};
+
+static UnitTable unit_table(int ns, int kw) {
+  UnitTable t;
+  const auto qmax = [](int s) { return s == 1 ? 128 : 64; };
+  const int64_t cap = ((int64_t)1 << 24) / (64 * std::max(1, std::min(KW, kw)));
+  for (int g = 2; g <= ns + 1; ++g) {
+    int64_t used = 0;
+    bool open = false;
+    for (int s = 1; s < g; ++s) {
+      const int u = g - s;
+      if (s > ns || u > ns) continue;
+      const int64_t cost = (int64_t)qmax(s) * qmax(u);
+      if (open && used + cost > cap) {
+        t.unit_end[t.nunits++] = t.npairs;
+        used = 0;
+        open = false;
+      }
+      if (!open) {
+        if (t.nunits >= MAX_UNITS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many accumulation units");
+        t.unit_g[t.nunits] = g;
+        open = true;
+      }
+      if (t.npairs >= MAX_PAIRS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many slice pairs");
+      t.si[t.npairs] = s;
+      t.ti[t.npairs] = u;
+      t.pu[t.npairs] = t.nunits;
+      ++t.npairs;
+      used += cost;
+    }
+    if (open) t.unit_end[t.nunits++] = t.npairs;
+  }
+  return t;
+}
+
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                       unsigned long long* pairs, OperandCache* ac) {
@@ -1399,14 +1709,19 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     fail(IFAC_ERR_TOO_LARGE, "split product: slice copies exceed the 2^31-row tensor-map range");
   const CUtensorMap mA = make_map<2>(la_p, (int64_t)ns * (A.nnzb + 1));
   const CUtensorMap mB = make_map<2>(lb.p, (int64_t)ns * (B.nnzb + 1));
-  // tile plan (as for the plain tensor-core product) with the longest tile's K steps
-  Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
+  // tile plans: 128 x 64 tiles first; banded products (no tile with more
+  // than KW K steps, at most band::MAX_U units at that bound) run on the
+  // banded kernel, every other product on the super-tile plan
+  Plan Pb = make_plan<band::TMB, 1>(ctx, arows, A, tA, brows, B, C, crow, true, KW);
+  const bool banded = Pb.kmax >= 1 && Pb.kmax <= KW && unit_table(ns, Pb.kmax).nunits <= band::MAX_U;
+  Plan P;
+  if (!banded) P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
   // block pairs, and block pairs times the ns (ns + 1) / 2 slice pairs
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
                                                                       upper ? 1 : 0, pairs, pairs + 1,
                                                                       ns * (ns + 1) / 2);
   IFAC_CK_LAUNCH();
-  const int kmax = P.kmax;
+  const int kmax = banded ? Pb.kmax : P.kmax;
   float l1h[2] = {0.f, 0.f};
   to_host(ctx, l1h, l1.p, sizeof(l1h));
   if (hit) {
@@ -1417,31 +1732,13 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     ac->sexp = std::move(sige);
     ac->split_ns = nsa;
   }
+  // the banded kernel writes every element of every C block once; the
+  // windowed kernel adds into zeroed sums
   Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
-  IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
-  static std::atomic<unsigned long long> attr{0};
-  if (first_on_device(attr, ctx->device))
-    IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
+  if (!banded)
+    IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  TileArgs args;
-  args.tiles = P.tiles.p;
-  args.ntiles = P.coff.p + P.nchunk;
-  args.tile_nk = P.tnk.p;
-  args.nwin = cdiv(std::max(kmax, 1), KW);
-  args.nb = nb;
-  args.rec = P.rec.p;
-  args.rec_off = P.off.p;
-  args.crp = C.row_ptr;
-  args.cci = C.col_idx;
-  args.cval = C.val;
-  args.cnorm = C.norms;
-  args.alpha = 1.0;
-  args.err = ctx->dev_err;
-  args.split = 1;
-  args.cpart = part.p;
-  args.stall = 0;
-  args.wait_limit = WAIT_LIMIT;
   // fixed point, scale 2^-f relative to sigma_i tau_j, with every partial sum
   // below 2^62: |sum_ij| <= min(sum_k |a_ik| / sigma_i, sum_k |b_kj| / tau_j)
   // (|a / sigma|, |b / tau| < 1), bounded by the largest scaled row / column
@@ -1454,49 +1751,94 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   int lgB = 0;
   while (std::ldexp(1.0, lgB) < l1b && lgB < 62) ++lgB;
   const int fbits = std::min(56, 62 - std::min(lgK, lgB));
-  auto set_units = [&](int fbits) {
-    // units: slice pairs of equal weight packed while sum over the unit of
-    // max|q_s| max|q_t| * 64 * kw stays <= 2^24, kw = the K blocks a window
-    // can hold: KW, or the longest tile's K steps when that is fewer (every
-    // window of every tile then has at most kw blocks, so each FP32
-    // accumulator still sums integers of magnitude <= 2^24 exactly)
-    const auto qmax = [](int s) { return s == 1 ? 128 : 64; };
-    const int kw = std::min(KW, std::max(kmax, 1));
-    const int64_t cap = ((int64_t)1 << 24) / (64 * kw);
-    int nu = 0, np = 0;
-    for (int g = 2; g <= ns + 1; ++g) {
-      int64_t used = 0;
-      bool open = false;
-      for (int si = 1; si < g; ++si) {
-        const int ti = g - si;
-        if (si > ns || ti > ns) continue;
-        const int64_t cost = (int64_t)qmax(si) * qmax(ti);
-        if (open && used + cost > cap) {
-          args.unit_end[nu++] = np;
-          used = 0;
-          open = false;
-        }
-        if (!open) {
-          if (nu >= MAX_UNITS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many accumulation units");
-          args.unit_sh[nu] = fbits - SPLIT_BITS * g;
-          open = true;
-        }
-        if (np >= MAX_PAIRS) fail(IFAC_ERR_UNSUPPORTED, "split product: too many slice pairs");
-        args.pair_ya[np] = (si - 1) * (int)(A.nnzb + 1) * BS;
-        args.pair_yb[np] = (ti - 1) * (int)(B.nnzb + 1) * BS;
-        ++np;
-        used += cost;
-      }
-      if (open) args.unit_end[nu++] = np;
-    }
-    args.nunits = nu;
-  };
-  const int64_t pairs_grid = std::min<int64_t>(std::max(P.ntiles, 1), sms / PAIR);
-  set_units(fbits);
-  args.ovf = ctx->dev_err;
+  // units: kw = the K blocks a window can hold, KW or the longest tile's K
+  // steps when that is fewer (every window of every tile then has at most kw
+  // blocks, so each FP32 accumulator still sums integers of magnitude
+  // <= 2^24 exactly)
+  const UnitTable ut = unit_table(ns, std::min(KW, std::max(kmax, 1)));
   prof_begin(ctx, 2);
-  k_gemm_tc<2><<<(unsigned)(pairs_grid * PAIR), NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mA, mB, args);
-  IFAC_CK_LAUNCH();
+  if (banded) {
+    BandArgs ba{};
+    ba.tiles = Pb.tiles.p;
+    ba.ntiles = Pb.coff.p + Pb.nchunk;
+    ba.tile_nk = Pb.tnk.p;
+    ba.rec = Pb.rec.p;
+    ba.rec_off = Pb.off.p;
+    ba.crp = C.row_ptr;
+    ba.cci = C.col_idx;
+    ba.cpart = part.p;
+    ba.nb = nb;
+    ba.ns = ns;
+    ba.slice_rows_a = (int)(A.nnzb + 1) * BS;
+    ba.slice_rows_b = (int)(B.nnzb + 1) * BS;
+    ba.nunits = ut.nunits;
+    for (int u = 0; u < ut.nunits; ++u) ba.unit_sh[u] = fbits - SPLIT_BITS * ut.unit_g[u];
+    // issue order: by slot max(a, b); slice r is released after the last
+    // slot whose pairs read it, max(r, ns - 1 - r)
+    ba.npairs = ut.npairs;
+    int q = 0, e = 0;
+    for (int k = 0; k < ns; ++k) {
+      ba.slot_beg[k] = q;
+      for (int p = 0; p < ut.npairs; ++p) {
+        const int a = ut.si[p] - 1, b = ut.ti[p] - 1;
+        if (std::max(a, b) != k) continue;
+        ba.pair_a[q] = a;
+        ba.pair_b[q] = b;
+        ba.pair_u[q] = ut.pu[p];
+        ++q;
+      }
+      ba.rel_beg[k] = e;
+      for (int r = 0; r < ns; ++r)
+        if (std::max(r, ns - 1 - r) == k) ba.rel[e++] = r;
+    }
+    ba.slot_beg[ns] = q;
+    ba.rel_beg[ns] = e;
+    if (q != ut.npairs || e != ns) fail(IFAC_ERR_CUDA, "split product: inconsistent banded issue table");
+    ba.err = ctx->dev_err;
+    ba.ovf = ctx->dev_err;
+    static std::atomic<unsigned long long> attr_b{0};
+    if (first_on_device(attr_b, ctx->device))
+      IFAC_CK(cudaFuncSetAttribute(k_gemm_split_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   band::SMEM_BYTES));
+    const int grid = (int)std::min<int64_t>(std::max(Pb.ntiles, 1), sms);
+    k_gemm_split_band<<<grid, NTHREADS, band::SMEM_BYTES, ctx->stream>>>(mA, mB, ba);
+    IFAC_CK_LAUNCH();
+  } else {
+    static std::atomic<unsigned long long> attr{0};
+    if (first_on_device(attr, ctx->device))
+      IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
+    TileArgs args{};
+    args.tiles = P.tiles.p;
+    args.ntiles = P.coff.p + P.nchunk;
+    args.tile_nk = P.tnk.p;
+    args.nwin = cdiv(std::max(kmax, 1), KW);
+    args.nb = nb;
+    args.rec = P.rec.p;
+    args.rec_off = P.off.p;
+    args.crp = C.row_ptr;
+    args.cci = C.col_idx;
+    args.cval = C.val;
+    args.cnorm = C.norms;
+    args.alpha = 1.0;
+    args.err = ctx->dev_err;
+    args.split = 1;
+    args.cpart = part.p;
+    args.stall = 0;
+    args.wait_limit = WAIT_LIMIT;
+    args.nunits = ut.nunits;
+    for (int u = 0; u < ut.nunits; ++u) {
+      args.unit_end[u] = ut.unit_end[u];
+      args.unit_sh[u] = fbits - SPLIT_BITS * ut.unit_g[u];
+    }
+    for (int p = 0; p < ut.npairs; ++p) {
+      args.pair_ya[p] = (ut.si[p] - 1) * (int)(A.nnzb + 1) * BS;
+      args.pair_yb[p] = (ut.ti[p] - 1) * (int)(B.nnzb + 1) * BS;
+    }
+    args.ovf = ctx->dev_err;
+    const int64_t pairs_grid = std::min<int64_t>(std::max(P.ntiles, 1), sms / PAIR);
+    k_gemm_tc<2><<<(unsigned)(pairs_grid * PAIR), NTHREADS, Cf::SMEM_BYTES, ctx->stream>>>(mA, mB, args);
+    IFAC_CK_LAUNCH();
+  }
   prof_end(ctx);
   ++ctx->split_launches;
   {

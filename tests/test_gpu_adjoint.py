@@ -86,8 +86,12 @@ def test_adjoint_central_differences_n16384(ctx):
 
 def test_adjoint_central_differences_200_entries_n16384(ctx):
     """Config-5 size: dL/dS on 200 random stored entries (of S's pattern)
-    against central differences h = 1e-6 max(1, |S_ij|) of the FP64 loss
-    L(S +- h e_ij) that the library's forward pass returns."""
+    against central differences h = 1e-4 max(1, |S_ij|) of the FP64 loss
+    L(S +- h e_ij) that the library's forward pass returns.  Each forward
+    re-records its block pattern by truncation at tau and sums in its own
+    order, so L carries noise of about 1e-16 |L| and a jump where a block
+    norm crosses tau; the larger step keeps both far below the tolerance
+    (the truncation error of the difference is O(h^2))."""
     from paper_1901_07993_gb300 import ifac
     S = synth.chain_overlap(16384, 32, seed=0)
     F = synth.fock_like(S, seed=5)
@@ -98,10 +102,10 @@ def test_adjoint_central_differences_200_entries_n16384(ctx):
     g = G.download()
     rng = np.random.default_rng(200)
     picks = rng.integers(0, S.nnzb, size=200)
-    worst = 0.0
+    worst, errs = 0.0, []
     for q in picks:
         r, c = rng.integers(0, 32, size=2)
-        h = 1e-6 * max(1.0, abs(S.val[q, r, c]))
+        h = 1e-4 * max(1.0, abs(S.val[q, r, c]))
         vals = []
         for sgn in (1.0, -1.0):
             v = S.val.copy()
@@ -112,7 +116,8 @@ def test_adjoint_central_differences_200_entries_n16384(ctx):
         fd = (vals[0] - vals[1]) / (2 * h)
         err = abs(fd - g.val[q, r, c]) / max(1.0, abs(fd))
         worst = max(worst, err)
-    print(f"200 entries: worst relative FD error {worst:.2e}")
+        errs.append(err)
+    print(f"200 entries: worst relative FD error {worst:.2e}, median {np.median(errs):.2e}, |L| {abs(L0):.3e}")
     assert worst <= 1e-5, worst
 
 

@@ -79,13 +79,18 @@ def test_oom_on_kth_allocation_leaks_nothing(lib, prec):
         fa = CountingAllocator(fail_at=k)
         c = ifac.Context(allocator=(fa.alloc, fa.free))
         dS = ifac.upload(c, S) if k > 4 else None  # the upload itself takes the first 4 allocations
+        owned = set(fa.live)  # the caller's S (nothing when the upload is the call that fails)
         with pytest.raises(ifac.IfacError) as ei:
             if dS is None:
                 dS = ifac.upload(c, S)
             ifac.inv_factor_refine(c, dS, 1e-12, 1e-10, ifac.opts(prec=prec, max_iter=60))
-        assert ei.value.code == ifac.ERR_OOM, (k, ei.value)
-        del dS
+        code = ei.value.code
+        del ei  # its traceback holds the caller's S
+        assert code == ifac.ERR_OOM, k
         torch.cuda.synchronize()
+        # everything the failed call allocated has been returned
+        assert set(fa.live) == owned, (k, len(fa.live), len(owned))
+        del dS
         assert not fa.live, (k, len(fa.live))
         # the context is still usable: the same factorization, the same result
         fa.fail_at = None
