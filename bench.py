@@ -636,6 +636,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparison precisions, the end-to-end leg and the dense probe (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -697,7 +699,7 @@ def main():
 
     # ---- the same factorization in the comparison precisions ----
     compare = {}
-    for cp in w["compare"]:
+    for cp in (() if args.no_compare else w["compare"]):
         oc = ifac.opts(m=w["m"], leaf_size=w["leaf"], prec=PREC[cp], profile=True, max_iter=100)
         Zc, _ = factor(ctx, S, w["tau"], w["target"], oc)  # warm-up
         del Zc
@@ -723,7 +725,7 @@ def main():
     e2e_ms = []
     barrier(world)
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(0 if args.no_compare else args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -741,9 +743,9 @@ def main():
     barrier(world)
     e2e_total = allmax(world, sum(e2e_ms))
     h2d = S_h.row_ptr.nbytes + S_h.col_idx.nbytes + S_h.val.nbytes
-    d2h = sum(b.nbytes for b in z_bufs)
+    d2h = sum(b.nbytes for b in z_bufs) if z_bufs else 0
 
-    probe = tc_dense_probe(ctx, ifac) if w["prec"] != "fp64" else None
+    probe = tc_dense_probe(ctx, ifac) if w["prec"] != "fp64" and not args.no_compare else None
     clocks = clk.summary()
     if rank != 0:
         return
@@ -765,7 +767,7 @@ def main():
         "gpu_launches": int(sum(r.launches for r in reps)),
         "roofline": roofline, "kernels": kernels, "compare": compare, "tc_dense_probe": probe,
         "e2e": {"value": world * args.steps / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h} if e2e_ms else None,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

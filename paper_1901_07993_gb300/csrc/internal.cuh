@@ -181,6 +181,13 @@ struct OperandCache {
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache = nullptr);
+// TF32 (elt 4) / BF16 (elt 2) product of a banded pattern on 128 x 64 tiles
+// (gemm_band.cu).  mapA / mapB: CUtensorMap of the K-major low-precision
+// copies of op(A) and op(B); tiles, ntiles, tile_nk, rec, rec_off: the 2 x 1
+// tile plan (copy indices of op(A)_{I0,K}, op(A)_{I0+1,K}, op(B)_{K,J}).
+void band_lp_product(ifac_ctx* ctx, int elt, const void* mapA, const void* mapB, const int32_t* tiles,
+                     const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
+                     int tiles_bound, double alpha, ifac_bsr& C);
 // Failure-path self-test: a tensor-core launch whose pipeline never fills, so
 // its bounded waits expire after wait_limit polls (sets the device error flag).
 void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit);
