@@ -110,23 +110,19 @@ UNIT = "factorizations/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# block-product kernels, averaged over the launches of one factorization: an
-# ncu capture of the first factorization of irsi-mixed-chain-n65536-bs64 (28
-# TF32 launches, --clock-control none).  The 262,144-row chain runs the same
-# sweeps on four times the block rows, stored blocks and block pairs, so its
-# figures are the captured ones times four.  The split products were captured
-# before their accumulation units were bounded by the longest tile's K steps,
-# which changed their traffic, so they report none.  Keyed by workload, then
-# by kernel_rooflines' kernel key.
-_TRAFFIC_M65 = {"tc": 4713918464 / 28}
+# block-product kernels, averaged over the launches of the first
+# factorization of the workload, from an ncu capture of that workload
+# (--clock-control none, one pass; profiles/ holds the summaries and the
+# commands).  A kernel changed since its capture has no entry.  Keyed by
+# workload, then by kernel_rooflines' kernel key.
 DRAM_TRAFFIC = {
-    "irsi-mixed-chain-n65536-bs64": {
-        k: (v, "ncu capture of this workload's first factorization")
-        for k, v in _TRAFFIC_M65.items()},
     "irsi-mixed-chain-n262144-bs64": {
-        k: (4 * v, "ncu capture of the 65,536-row chain's first factorization, times 4 (block rows, "
-                   "stored blocks and block pairs scale with n on the chain)")
-        for k, v in _TRAFFIC_M65.items()},
+        "tc": (846232310.9, "ncu capture of this workload's first factorization: k_gemm_band_lp<4>, 28 launches"),
+        "split": (2369070208.0, "ncu capture of this workload's first factorization: k_gemm_split_band, 8 launches"),
+    },
+    "irsi-mixed-chain-n65536-bs64": {
+        "tc": (165576850.3, "ncu capture of this workload's first factorization: k_gemm_band_lp<4>, 28 launches"),
+    },
 }
 
 
@@ -137,6 +133,12 @@ def _peaks():
         return float(m["bf16_tflops"]), float(m["hbm_gbs"]), "measured"
     except Exception:
         return 1900.0, 6800.0, "fallback"
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth (MEASURED_PEAKS.json), else the fallback."""
+    _, hbm, src = _peaks()
+    return hbm, src
 
 
 def fp64_peak_tflops():
@@ -259,40 +261,83 @@ def oracle_factorize(S, w):
                       rinch_rows=w.get("rinch_rows", 0))
 
 
-def cpu_sample(w):
-    """The input the CPU oracle factorizes, and the factor that turns its rate
-    into the workload's: the workload itself, or the same construction at
-    sample_n rows, whose cost is (n/sample_n)^p times smaller -- p = 1 for the
-    chain (banded factors), p = 3 for the 3D clusters (block-dense factors)."""
-    if w.get("sample_n"):
-        p = w.get("cost_exp", 1)
-        scale = (w["sample_n"] / w["n"]) ** p
-        return make_input(w, w["sample_n"]), scale, \
-            (f"complete FP64 factorizations of the same construction at n = {w['sample_n']} "
-             f"(block rows 1/{w['n'] // w['sample_n']} of the workload), rate scaled by "
-             f"({w['sample_n']}/{w['n']})^{p}")
-    return make_input(w), 1.0, "complete FP64 factorizations of the same workload"
+def nproc() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
-def cpu_baseline(w, budget_s: float = 10.0):
-    """The oracle, as it stands, on a bounded sample of the workload."""
+def cpu_sizes(w):
+    """Two sizes of the workload's construction at which the oracle is timed
+    to measure how its cost grows with n: n/16 and n/4 for the chain (at
+    least 16,384 rows for the 262,144-row workload), the sample size and half
+    of it for the 3D clusters (block-dense factors, cubic cost)."""
+    if w["geom"] == "chain" and w["n"] >= 65536:
+        return w["n"] // 16, w["n"] // 4
+    s = w.get("sample_n") or w["n"]
+    return max(s // 2, w["bs"] * 4), s
+
+
+def _oracle_seconds(S, w, threads, runs=1):
+    import oracle
+    oracle.set_threads(threads)
+    best = float("inf")
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        oracle_factorize(S, w)
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def cpu_baseline(w, full_budget_s: float = 20.0):
+    """The oracle, as it stands, on the machine's host cores: single-threaded and
+    with all cores (OpenMP over output block rows), each timed at two sizes
+    of the workload's construction to measure the cost exponent p of
+    t ~ n^p.  The all-core oracle also factorizes the full workload when its
+    predicted time is within full_budget_s (then `value` is measured, not
+    scaled); the single-threaded figure is scaled from the larger size with
+    the measured exponent."""
+    import math
+
     import oracle
     oracle.build()
-    S, scale, what = cpu_sample(w)
-    t0 = time.perf_counter()
-    count = 0
-    while True:
-        oracle_factorize(S, w)
-        count += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": count / dt * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{count} {what}; single-threaded FP64 C, {dt:.1f} s"}
+    cores = nproc()
+    n1, n2 = cpu_sizes(w)
+    S1, S2 = make_input(w, n1), make_input(w, n2)
+    t = {}
+    for th in (1, cores):
+        _oracle_seconds(S1, w, th)  # warm-up (page-in, first touch)
+        t[(th, n1)] = _oracle_seconds(S1, w, th, runs=2)
+        t[(th, n2)] = _oracle_seconds(S2, w, th, runs=1 if th == 1 else 2)
+    exps = {th: math.log(t[(th, n2)] / t[(th, n1)]) / math.log(n2 / n1) for th in (1, cores)}
+    n = w["n"]
+    pred_all = t[(cores, n2)] * (n / n2) ** exps[cores]
+    if n == n2:
+        t_all, how = t[(cores, n2)], "measured on the workload itself"
+    elif pred_all <= full_budget_s:
+        t_all, how = _oracle_seconds(make_input(w), w, cores, runs=1), "measured on the workload itself"
+    else:
+        t_all, how = pred_all, f"scaled from n = {n2} with the measured exponent"
+    t_one = t[(1, n2)] * (n / n2) ** exps[1]
+    oracle.set_threads(cores)
+    return {"value": 1.0 / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"complete FP64 factorizations by the C oracle with OpenMP over output block rows on "
+                       f"{cores} cores ({how}); timed at n = {n1} and {n2}: "
+                       f"{t[(cores, n1)]:.3g} s and {t[(cores, n2)]:.3g} s, cost exponent {exps[cores]:.2f}"),
+            "single_thread": {"value": 1.0 / t_one, "unit": UNIT, "cores": 1,
+                              "seconds_at": {str(n1): t[(1, n1)], str(n2): t[(1, n2)]},
+                              "cost_exponent": exps[1],
+                              "sample": f"scaled from n = {n2} to n = {n} by (n/{n2})^{exps[1]:.2f}"},
+            "all_core_cost_exponent": exps[cores], "parallel_speedup_at_n2": t[(1, n2)] / t[(cores, n2)]}
 
 
 def run_reference(args, w, world, rank):
-    """CPU oracle arm (rank 0 only)."""
+    """CPU oracle arm (rank 0 only): every step is one factorization of the
+    workload by the oracle with all host cores, when that fits the time
+    budget; otherwise of the larger sample size, scaled by the measured cost
+    exponent."""
     if rank != 0:
         return
     if w["method"] not in ("refine", "rinch", "localized"):
@@ -300,10 +345,24 @@ def run_reference(args, w, world, rank):
                           f"workload {args.workload} ({w['method']}) has no single-factorization reference"}),
               flush=True)
         return
+    import math
+
     import oracle
     oracle.build()
-    S, scale, what = cpu_sample(w)
-    for _ in range(args.warmup):
+    cores = nproc()
+    oracle.set_threads(cores)
+    S = make_input(w)
+    t_first = _oracle_seconds(S, w, cores)
+    scale, what = 1.0, "complete FP64 factorizations of the workload itself"
+    if t_first * (args.steps + args.warmup) > 300.0:
+        n1, n2 = cpu_sizes(w)
+        S1, S = make_input(w, n1), make_input(w, n2)
+        t1, t2 = _oracle_seconds(S1, w, cores), _oracle_seconds(S, w, cores)
+        p = math.log(t2 / t1) / math.log(n2 / n1)
+        scale = (n2 / w["n"]) ** p
+        what = (f"complete FP64 factorizations of the same construction at n = {n2}, rate scaled by "
+                f"({n2}/{w['n']})^{p:.2f} (exponent measured at n = {n1} and {n2})")
+    for _ in range(max(args.warmup - 1, 0)):
         oracle_factorize(S, w)
     times = []
     for _ in range(args.steps):
@@ -317,8 +376,9 @@ def run_reference(args, w, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64",  # the oracle computes every step in FP64
             "data": "synthetic", "config": config_of(w, args.workload, world),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} {what} (plus {args.warmup} warm-up)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} {what} (plus {args.warmup} warm-up), OpenMP over output "
+                                       f"block rows on {cores} cores"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -354,57 +414,69 @@ SPLIT_PAIRS = 28  # slice pairs (s, t) with s + t <= 8 of the default 7-slice sp
 
 
 def kernel_rooflines(reps, bs, prec, traffic=None):
-    """Live CUDA-event rooflines of the block-product kernels.  `traffic` maps
-    a kernel key to (DRAM bytes per launch, source) from an ncu capture of the
-    same workload; kernels without one report null."""
+    """Live CUDA-event rooflines of the block-product kernels.
+
+    Work per kernel is the method's (2 bs^3 flops per multiplied stored block
+    pair; zero blocks inside tiles and split slice pairs are not counted) and
+    its algorithmic bytes as the library reports them (every operand block
+    read once at the width the kernel reads it, every result block written
+    once).  The bound is the roofline that binds at that arithmetic
+    intensity: HBM (measured copy bandwidth) below the ridge point, the
+    tensor (TF32/BF16, split: BF16) or FP64 peak above it; both fractions are
+    given.  `traffic` maps a kernel key to (DRAM bytes per launch, source)
+    from an ncu capture of the same kernel and workload; kernels without one
+    report null."""
     out = {}
     traffic = traffic or {}
-    fp64_ms = sum(r.gemm_ms for r in reps)
-    tc_ms = sum(r.tc_ms for r in reps)
     fl = 2.0 * bs ** 3
-    if fp64_ms > 0:
-        peak, src = fp64_peak_tflops()
-        ach = sum(r.fp64_pairs for r in reps) * fl / (fp64_ms / 1e3) / 1e12
-        launches = sum(r.gemm_launches for r in reps)
-        out["fp64"] = {"bound": "alu", "kernel": f"k_gemm_fp64<{bs}>", "achieved": ach, "peak": peak,
-                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                       "peak_source": f"{src} bf16 x nominal FP64/BF16 ratio 1.25/2250",
-                       "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * fp64_ms / max(launches, 1),
-                       "ms_per_step": fp64_ms / len(reps)}
-    if tc_ms > 0:
-        peak, src = tensor_peak_tflops(prec)
-        ach = sum(r.tc_pairs for r in reps) * fl / (tc_ms / 1e3) / 1e12
-        launches = sum(r.tc_launches for r in reps)
-        out["tc"] = {"bound": "tensor", "kernel": f"k_gemm_tc<{'2' if prec == 'bf16' else '4'}>", "achieved": ach,
-                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                     "traffic": traffic["tc"][0] if "tc" in traffic else None,
-                     "peak_source": f"{src} bf16" + ("" if prec == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25"),
-                     "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * tc_ms / max(launches, 1),
-                     "ms_per_step": tc_ms / len(reps),
-                     "note": "achieved counts stored block pairs only; zero blocks inside tiles are not counted"}
-    split_ms = sum(r.split_ms for r in reps)
-    if split_ms > 0:
-        peak, src = tensor_peak_tflops("bf16")
-        fp64_pk, _ = fp64_peak_tflops()
-        eq = sum(r.split_pairs for r in reps) * fl / (split_ms / 1e3) / 1e12
-        ach = sum(r.split_slice_pairs for r in reps) * fl / (split_ms / 1e3) / 1e12
-        launches = sum(r.split_launches for r in reps)
-        out["split"] = {"bound": "tensor", "kernel": "k_gemm_tc<2> (split FP64)", "achieved": ach,
-                        "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                        "traffic": traffic["split"][0] if "split" in traffic else None,
-                        "peak_source": f"{src} bf16", "fp64_equivalent_tflops": eq,
-                        "fp64_equivalent_over_fp64_peak": eq / fp64_pk,
-                        "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * split_ms / max(launches, 1),
-                        "ms_per_step": split_ms / len(reps),
-                        "slice_pairs_per_block_pair": sum(r.split_slice_pairs for r in reps)
-                        / max(sum(r.split_pairs for r in reps), 1),
-                        "note": "achieved = BF16 slice-pair products on stored block pairs, s (s + 1) / 2 per "
-                                "block pair with s slices (28 at s = 7; early delta evaluations take fewer); "
-                                "zero blocks inside tiles are not counted"}
-    for k, v in out.items():
-        if v.get("traffic") is not None:
-            v["traffic_unit"] = "bytes per launch"
-            v["traffic_source"] = traffic[k][1]
+    hbm, hbm_src = hbm_peak_gbs()
+    kinds = (("fp64", "gemm_ms", "fp64_pairs", "gemm_launches", "fp64_bytes", f"k_gemm_fp64<{bs}>"),
+             ("tc", "tc_ms", "tc_pairs", "tc_launches", "tc_bytes", f"k_gemm_tc/k_gemm_band_lp<{'2' if prec == 'bf16' else '4'}>"),
+             ("split", "split_ms", "split_pairs", "split_launches", "split_bytes", "k_gemm_split_band / k_gemm_tc<2> (split FP64)"))
+    for key, ms_f, pairs_f, launch_f, bytes_f, kname in kinds:
+        ms = sum(getattr(r, ms_f) for r in reps)
+        if ms <= 0:
+            continue
+        launches = sum(getattr(r, launch_f) for r in reps)
+        flops = sum(getattr(r, pairs_f) for r in reps) * fl
+        nbytes = sum(getattr(r, bytes_f) for r in reps)
+        tflops = flops / (ms / 1e3) / 1e12
+        gbs = nbytes / (ms / 1e3) / 1e9
+        if key == "fp64":
+            cpk, csrc = fp64_peak_tflops()
+            cbound, csrc = "alu", f"{csrc} bf16 x nominal FP64/BF16 ratio 1.25/2250"
+        else:
+            cp = "bf16" if key == "split" else prec
+            cpk, csrc = tensor_peak_tflops(cp)
+            cbound = "tensor"
+            csrc = f"{csrc} bf16" + ("" if cp == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25")
+        intensity = flops / max(nbytes, 1.0)
+        ridge = cpk * 1e12 / (hbm * 1e9)
+        mem_bound = intensity < ridge
+        e = {"bound": "hbm" if mem_bound else cbound, "kernel": kname,
+             "achieved": gbs if mem_bound else tflops, "peak": hbm if mem_bound else cpk,
+             "unit": "GB/s" if mem_bound else "TFLOP/s",
+             "frac": (gbs / hbm) if mem_bound else (tflops / cpk),
+             "traffic": traffic[key][0] if key in traffic else None,
+             "peak_source": hbm_src + " copy bandwidth" if mem_bound else csrc,
+             "algorithmic_bytes_per_launch": nbytes / max(launches, 1),
+             "flops_per_launch": flops / max(launches, 1),
+             "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+             "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
+             "tflops": tflops, "compute_peak_tflops": cpk, "compute_frac": tflops / cpk,
+             "launches_per_step": launches / len(reps), "avg_launch_us": 1e3 * ms / max(launches, 1),
+             "ms_per_step": ms / len(reps)}
+        if key == "split":
+            e["slice_pairs_per_block_pair"] = sum(r.split_slice_pairs for r in reps) / max(
+                sum(r.split_pairs for r in reps), 1)
+            e["bf16_slice_tflops"] = sum(r.split_slice_pairs for r in reps) * fl / (ms / 1e3) / 1e12
+            e["note"] = ("flops are the FP64 product's 2 bs^3 per stored block pair; the BF16 slice products "
+                         "(s (s + 1) / 2 per block pair) are bf16_slice_tflops")
+        if e["traffic"] is not None:
+            e["traffic_unit"] = "bytes per launch"
+            e["traffic_source"] = traffic[key][1]
+            e["traffic_over_algorithmic"] = e["traffic"] / max(e["algorithmic_bytes_per_launch"], 1.0)
+        out[key] = e
     return out
 
 

@@ -158,6 +158,13 @@ typedef struct {
                                 pairs each took: s (s + 1) / 2 with s slices
                                 per operand (the mixed schedule lowers s for
                                 early delta evaluations) */
+  double fp64_bytes;   /* algorithmic bytes of the FP64 product launches: per
+                          product (nnzb(A) + nnzb(B) + nnzb(C)) bs^2 8, C before
+                          truncation (each block read or written once) */
+  double tc_bytes;     /* the same for the TF32/BF16 launches: operands at 4 / 2
+                          bytes (the converted copies), C at 8 (FP64) */
+  double split_bytes;  /* the same for the split launches: s BF16 slices of
+                          each operand (2 s bytes), C as 64-bit sums (8) */
 } ifac_report;
 
 /* ---------------------------------------------------------------- */

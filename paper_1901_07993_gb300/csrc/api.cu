@@ -72,6 +72,22 @@ void to_host(ifac_ctx* ctx, void* host, const void* dev, size_t bytes) {
   }
 }
 
+void to_host_many(ifac_ctx* ctx, std::initializer_list<HostRead> reads) {
+  size_t off = 0;
+  for (const HostRead& r : reads) {
+    if (off + r.bytes > 4096) fail(IFAC_ERR_INVALID, "to_host_many: more than 4096 bytes");
+    IFAC_CK(cudaMemcpyAsync(static_cast<char*>(ctx->pinned) + off, r.dev, r.bytes, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    off += (r.bytes + 15) & ~(size_t)15;
+  }
+  IFAC_CK(cudaStreamSynchronize(ctx->stream));
+  off = 0;
+  for (const HostRead& r : reads) {
+    memcpy(r.host, static_cast<char*>(ctx->pinned) + off, r.bytes);
+    off += (r.bytes + 15) & ~(size_t)15;
+  }
+}
+
 void validate(const ifac_bsr* A, const char* name) {
   std::string nm(name);
   if (!A) fail(IFAC_ERR_INVALID, nm + " is NULL");

@@ -92,6 +92,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   ctx->gemm_launches = 0;
   ctx->tc_launches = 0;
   ctx->split_launches = 0;
+  ctx->bytes_fp64 = ctx->bytes_tc = ctx->bytes_split = 0;
   ctx->events_used = 0;
   ctx->profile = o.profile != 0;
   reset_device_counters(ctx);
@@ -194,8 +195,9 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         // with low-precision sweeps, the upper block triangle of the
         // symmetric Z^T S Z is formed and the lower one taken from it
         const bool sym = low;
-        Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd);        // S Z
-        Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym);     // Z^T (S Z)
+        OperandCache zcache;  // Z's copy (op(B) of S Z) serves again as op(A) = Z^T
+        Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd, false, nullptr, &zcache);  // S Z
+        Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym, &zcache);               // Z^T (S Z)
         X.reset();
         Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0)          // I - Z^T S Z
                    : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
@@ -293,8 +295,9 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   std::vector<double> resid(count, 0.0);
   {
     const int rprec = delta_prec_of(o, bs);
-    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, 0.0, rprec);
-    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, 0.0, rprec);
+    OperandCache zcache;
+    Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, 0.0, rprec, false, nullptr, &zcache);
+    Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, 0.0, rprec, false, &zcache);
     X.reset();
     Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     node_fro(ctx, D.m, dnb0.p, dnb1.p, count, ne.p);
@@ -355,6 +358,9 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       r.tc_ms = ms_tc;
       r.split_launches = ctx->split_launches;
       r.split_ms = ms_split;
+      r.fp64_bytes = ctx->bytes_fp64;
+      r.tc_bytes = ctx->bytes_tc;
+      r.split_bytes = ctx->bytes_split;
     }
     outs.push_back(std::move(Zk));
   }

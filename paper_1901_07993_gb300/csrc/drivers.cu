@@ -56,6 +56,7 @@ void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
   ctx->pairs_tc = 0;
   ctx->pairs_split = 0;
   ctx->slice_pairs = 0;
+  ctx->bytes_fp64 = ctx->bytes_tc = ctx->bytes_split = 0;
   ctx->events_used = 0;
   ctx->profile = o.profile != 0;
   reset_device_counters(ctx);
@@ -119,6 +120,9 @@ void report_finish(ifac_ctx* ctx, ifac_report* r, const ifac_bsr& Z) {
   r->split_launches = ctx->split_launches;
   r->split_pairs = ctx->pairs_split;
   r->split_slice_pairs = ctx->slice_pairs;
+  r->fp64_bytes = ctx->bytes_fp64;
+  r->tc_bytes = ctx->bytes_tc;
+  r->split_bytes = ctx->bytes_split;
   r->fp64_pairs = ctx->pairs_fp64;
   r->tc_pairs = ctx->pairs_tc;
   ctx->profile = false;
@@ -139,8 +143,9 @@ int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, 
   int stop = 0, it = 0;
   double e = 0.0;
   auto direct_delta = [&](const ifac_bsr& Zc) {
-    Mat X = gemm(ctx, S.m, false, Zc, false, 1.0, tau);    // S Z
-    Mat Y = gemm(ctx, Zc, true, X.m, false, 1.0, tau);     // Z^T (S Z)
+    OperandCache zcache;  // split products: Z's slices (op(B) of S Z) serve op(A) = Z^T
+    Mat X = gemm(ctx, S.m, false, Zc, false, 1.0, tau, IFAC_FP64, false, nullptr, &zcache);  // S Z
+    Mat Y = gemm(ctx, Zc, true, X.m, false, 1.0, tau, IFAC_FP64, false, &zcache);            // Z^T (S Z)
     X.reset();
     return add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);         // I - Z^T S Z
   };
@@ -221,8 +226,10 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       SlicesScope scope(ctx, ns);
       // Z^T S Z is symmetric: its upper block triangle is formed and the
       // lower one taken from it, halving the second product
-      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache);  // S Z
-      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true);             // Z^T (S Z), J >= I
+      // Z's converted copy (op(B) of S Z) serves again as op(A) = Z^T
+      OperandCache zcache;
+      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache, &zcache);  // S Z
+      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true, &zcache);             // Z^T (S Z), J >= I
       X.reset();
       D = sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);                     // I - Z^T S Z
     }
@@ -647,8 +654,9 @@ int lif(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, const if
 
 double resid(ifac_ctx* ctx, const ifac_bsr& S, const ifac_bsr& Z) {
   int64_t p0 = ctx->products, q0 = ctx->pairs;
-  Mat X = gemm(ctx, S, false, Z, false, 1.0, 0.0);
-  Mat Y = gemm(ctx, Z, true, X.m, false, 1.0, 0.0);
+  OperandCache zcache;
+  Mat X = gemm(ctx, S, false, Z, false, 1.0, 0.0, IFAC_FP64, false, nullptr, &zcache);
+  Mat Y = gemm(ctx, Z, true, X.m, false, 1.0, 0.0, IFAC_FP64, false, &zcache);
   X.reset();
   Mat D = add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
   double e = fro_host(ctx, D.m);

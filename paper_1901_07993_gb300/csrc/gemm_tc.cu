@@ -647,7 +647,8 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
                             const int32_t* __restrict__ mapA, const int32_t* __restrict__ mapB,
                             const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                             const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, int a_zero, int b_zero,
-                            int32_t* __restrict__ rec, int32_t* __restrict__ nk_out, int* __restrict__ kmax) {
+                            const int32_t* __restrict__ amap, int32_t* __restrict__ rec, int32_t* __restrict__ nk_out,
+                            int* __restrict__ kmax) {
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= *ntiles) {  // the grid covers an upper bound of the tile count
@@ -707,7 +708,7 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
       if (!COUNT && valid) {
         int32_t* out = rec + (size_t)(e + __popc(m & ((1u << lane) - 1u))) * (ROWS + COLS);
 #pragma unroll
-        for (int r = 0; r < ROWS; ++r) out[r] = ra[r];
+        for (int r = 0; r < ROWS; ++r) out[r] = (amap && ra[r] != a_zero) ? amap[ra[r]] : ra[r];
 #pragma unroll
         for (int c = 0; c < COLS; ++c) out[ROWS + c] = rb[c];
       }
@@ -733,7 +734,12 @@ struct Plan {
 template <int ROWS, int COLS>
 static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool tA, const View& brows,
                       const ifac_bsr& B, const ifac_bsr& C, const int32_t* crow, bool want_kmax,
-                      int kmax_limit = 0) {
+                      int kmax_limit = 0, const int32_t* amap = nullptr, const HostRead* extra = nullptr) {
+  // amap (nullable): copy index of each op(A) view position, when op(A)'s
+  // low-precision copy is not in view order (a shared copy of a transposed
+  // operand, held in the stored order).  extra (nullable): one more small
+  // read-back the caller needs, taken with the plan's sizes in one
+  // synchronisation.
   // kmax_limit > 0: a plan whose longest tile has more K steps is not wanted;
   // it returns after the count pass with kmax set and no records
   const int nb = A.nb, W = words_per_row(nb);
@@ -784,20 +790,36 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
   if (nt > 0) {
     k_tile_plan<ROWS, COLS, true><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
         P.tiles.p, ntiles, nullptr, bmA.p, nb, W, dense_maps ? imA.p : nullptr, dense_maps ? imB.p : nullptr,
-        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, nullptr, P.tnk.p,
+        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, nullptr, nullptr, P.tnk.p,
         want_kmax ? dk.p : nullptr);
     IFAC_CK_LAUNCH();
-    total = scan_counts(ctx, P.tnk.p, P.off.p, nt, true);
+    scan_counts(ctx, P.tnk.p, P.off.p, nt, false);
+  }
+  {
+    // the record count, the longest tile and the caller's extra read-back
+    // behind one synchronisation
+    int32_t tot32 = 0;
+    const HostRead none{nullptr, nullptr, 0};
+    const HostRead ex = extra ? *extra : none;
+    if (ex.bytes) {
+      to_host_many(ctx, {{&tot32, nt > 0 ? (const void*)(P.off.p + nt) : (const void*)dk.p, sizeof(int32_t)},
+                         {&P.kmax, dk.p, sizeof(int)},
+                         ex});
+    } else {
+      to_host_many(ctx, {{&tot32, nt > 0 ? (const void*)(P.off.p + nt) : (const void*)dk.p, sizeof(int32_t)},
+                         {&P.kmax, dk.p, sizeof(int)}});
+    }
+    total = nt > 0 ? tot32 : 0;
+    if (!want_kmax) P.kmax = 0;
   }
   if (total > (int64_t)0x7fffffff / (ROWS + COLS))
     fail(IFAC_ERR_TOO_LARGE, "tensor-core product: tile plan exceeds 2^31 entries");
-  if (want_kmax) to_host(ctx, &P.kmax, dk.p, sizeof(int));
   if (want_kmax && kmax_limit > 0 && P.kmax > kmax_limit) return P;
   P.rec = Buf<int32_t>(ctx, (size_t)std::max<int64_t>(total, 1) * (ROWS + COLS));
   if (nt > 0) {
     k_tile_plan<ROWS, COLS, false><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
         P.tiles.p, ntiles, P.off.p, bmA.p, nb, W, dense_maps ? imA.p : nullptr, dense_maps ? imB.p : nullptr,
-        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, P.rec.p, nullptr, nullptr);
+        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, amap, P.rec.p, nullptr, nullptr);
     IFAC_CK_LAUNCH();
   }
   // the plan kernel has read the maps and the bitmap before they are freed
@@ -822,10 +844,15 @@ static CUtensorMap make_map(void* base, int64_t nblk) {
 template <int ELT>
 static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
                 const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                unsigned long long* pairs, OperandCache* ac) {
+                unsigned long long* pairs, OperandCache* ac, OperandCache* bc) {
   using Cf = Cfg<ELT>;
   const int nb = A.nb;
   const size_t bbytes = (size_t)BS * BS * ELT;
+  // a cache filled by an earlier product's op(B) holds transposed blocks in
+  // the stored order: it serves op(A) = that matrix transposed, through the
+  // view's source indices, and nothing else
+  if (ac && ac->from_b && !(tA && ac->conv_elt == ELT)) ac = nullptr;
+  const int32_t* amap = (ac && ac->from_b) ? arows.src : nullptr;
   // low-precision, K-major copies of op(A) and op(B) plus one zero block each
   // (op(A)'s taken from the cache when it holds one of this format)
   Buf<uint8_t> la, lb(ctx, (size_t)(B.nnzb + 1) * bbytes);
@@ -852,13 +879,19 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   const CUtensorMap mapA = make_map<ELT>(la_p, A.nnzb + 1);
   const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
+  if (bc && !tB) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
+    bc->reset();
+    bc->conv = std::move(lb);
+    bc->conv_elt = ELT;
+    bc->from_b = true;
+  }
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
                                                                       upper ? 1 : 0, pairs, nullptr, 0);
   IFAC_CK_LAUNCH();
   // banded products (no 128 x 64 tile with more than KW K steps) run on
   // 128 x 64 tiles (gemm_band.cu); the others on the super-tiles below
   {
-    Plan Pb = make_plan<2, 1>(ctx, arows, A, tA, brows, B, C, crow, true, KW);
+    Plan Pb = make_plan<2, 1>(ctx, arows, A, tA, brows, B, C, crow, true, KW, amap);
     if (Pb.kmax >= 1 && Pb.kmax <= KW) {
       prof_begin(ctx, 1);
       band_lp_product(ctx, ELT, &mapA, &mapB, Pb.tiles.p, Pb.coff.p + Pb.nchunk, Pb.tnk.p, Pb.rec.p, Pb.off.p,
@@ -868,7 +901,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
       return;
     }
   }
-  Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false);
+  Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false, 0, amap);
   static std::atomic<unsigned long long> attr{0};
   if (first_on_device(attr, ctx->device))
     IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
@@ -1182,7 +1215,12 @@ struct BandArgs {
   const int32_t* rec_off;  // first record of each tile
   const int32_t* crp;      // C pattern
   const int32_t* cci;
-  longlong2* cpart;        // fixed-point sums, hand-over layout (as TileArgs::cpart)
+  double* cval;            // C's values and block norms (FP64)
+  double* cnorm;
+  const int* sige;         // scale exponents of the scalar rows of op(A) and columns of op(B)
+  const int* taue;
+  int ea;                  // C_ij = S_ij 2^(ea + e_i + e_j) * am, S_ij the 64-bit fixed-point sum
+  double am;               // +-1 (applied to the integer) or the mantissa of alpha
   int nb;
   int ns;                  // slices per operand (1..8)
   int slice_rows_a;        // tensor-map rows between consecutive slices of op(A): (nnzb_A + 1) * 64
@@ -1214,6 +1252,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ __align__(8) uint64_t acc_full, acc_empty, drain_bar;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
+  __shared__ double partial[4][2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -1343,9 +1382,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int row = q * 32 + lane;           // accumulator row 0..127
     const int et = threadIdx.x - 64;
     uint32_t acc_phase = 0;
+    const bool unit = (args.am == 1.0 || args.am == -1.0), neg = args.am < 0.0;
     for (int it = 0; it < mt; ++it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      const int I = args.tiles[2 * t] * TMB + row / BS, J = args.tiles[2 * t + 1];
+      const int I0 = args.tiles[2 * t] * TMB;
+      const int I = I0 + row / BS, J = args.tiles[2 * t + 1];
       int p = -1;  // position of C_IJ in C (warp-uniform: a warp's rows lie in one block row)
       if (I < args.nb && J < args.nb) {
         const int lo = args.crp[I], hi = args.crp[I + 1];
@@ -1372,17 +1413,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc_fence_before();
       epi_bar();
       if (et == 0) mbar_arrive(smem_u32(&acc_empty));
+      // every K of the tile is in these sums (one window): the FP64 result,
+      // S_ij 2^(ea + e_i + e_j) * am rounded once, and its squares for the norm
+      double ss = 0.0;
       if (p >= 0) {
-        longlong2* dst = args.cpart + (size_t)p * (BS * BS / 2) + (size_t)(((q & 1) * 2 + half) * 16) * 32 + lane;
+        const int r = (q & 1) * 32 + lane;  // row within the block
+        const int er = args.ea + args.sige[(size_t)I * BS + r];
+        const int* tj = args.taue + (size_t)J * BS + half * 32;
+        double* dst = args.cval + (size_t)p * BS * BS + (size_t)r * BS + half * 32;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          longlong2 d;
-          d.x = s[2 * e];
-          d.y = s[2 * e + 1];
-          dst[e * 32] = d;
+        for (int e = 0; e < 32; e += 2) {
+          const long long x0 = (unit && neg) ? -s[e] : s[e], x1 = (unit && neg) ? -s[e + 1] : s[e + 1];
+          double v0 = i64_ldexp(x0, er + tj[e]), v1 = i64_ldexp(x1, er + tj[e + 1]);
+          if (!unit) {
+            v0 *= args.am;
+            v1 *= args.am;
+          }
+          ss = fma(v0, v0, ss);
+          ss = fma(v1, v1, ss);
+          *reinterpret_cast<double2*>(dst + e) = make_double2(v0, v1);
         }
         if (bad) *args.ovf = 2;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) partial[q][half] = ss;
+      epi_bar();
+      // norms: block row b of the tile is covered by lane quarters 2b, 2b + 1
+      if (et < TMB) {
+        const int Ib = I0 + et;
+        if (Ib < args.nb && J < args.nb) {
+          const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
+          const int k = lower_bound_i32(args.cci, lo, hi, J);
+          if (k < hi && args.cci[k] == J)
+            args.cnorm[k] = sqrt((partial[2 * et][0] + partial[2 * et][1]) +
+                                 (partial[2 * et + 1][0] + partial[2 * et + 1][1]));
+        }
+      }
+      epi_bar();
     }
   }
   tc_fence_before();
@@ -1441,11 +1509,16 @@ static UnitTable unit_table(int ns, int kw) {
 
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                      unsigned long long* pairs, OperandCache* ac) {
+                      unsigned long long* pairs, OperandCache* ac, OperandCache* bc) {
   using Cf = Cfg<2>;
   const int nb = A.nb;
   const int64_t rows = (int64_t)nb * BS;
   if (ns < 1 || ns > 8) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 8 slices");
+  // a cache filled by an earlier product's op(B) (transposed blocks in the
+  // stored order, with that operand's column scales) serves op(A) = that
+  // matrix transposed, through the view's source indices, and nothing else
+  if (ac && ac->from_b && !(tA && ac->split_ns >= ns)) ac = nullptr;
+  const int32_t* amap = (ac && ac->from_b) ? arows.src : nullptr;
   // scales: sigma (rows of op(A)), tau (columns of op(B) = rows of op(B)^T);
   // op(A)'s scales and slices come from the cache when it holds at least ns
   const bool hit = ac && ac->split_ns >= ns;
@@ -1480,6 +1553,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   }
   uint8_t* const la_p = hit ? ac->split.p : la.p;
   const int* const sige_p = hit ? ac->sexp.p : sige.p;
+  const int* const taue_p = taue.p;
   if (B.nnzb) {
     k_split<<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, tB ? 0 : SPLIT_TILE_BYTES, ctx->stream>>>(
         B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, taue.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
@@ -1493,18 +1567,18 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   // tile plans: 128 x 64 tiles first; banded products (no tile with more
   // than KW K steps, at most band::MAX_U units at that bound) run on the
   // banded kernel, every other product on the super-tile plan
-  Plan Pb = make_plan<band::TMB, 1>(ctx, arows, A, tA, brows, B, C, crow, true, KW);
+  float l1h[2] = {0.f, 0.f};  // scaled 1-norm bounds of op(A) rows and op(B) columns (FP32 bits)
+  const HostRead l1read{l1h, l1.p, sizeof(l1h)};
+  Plan Pb = make_plan<band::TMB, 1>(ctx, arows, A, tA, brows, B, C, crow, true, KW, amap, &l1read);
   const bool banded = Pb.kmax >= 1 && Pb.kmax <= KW && unit_table(ns, Pb.kmax).nunits <= band::MAX_U;
   Plan P;
-  if (!banded) P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true);
+  if (!banded) P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true, 0, amap);
   // block pairs, and block pairs times the ns (ns + 1) / 2 slice pairs
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
                                                                       upper ? 1 : 0, pairs, pairs + 1,
                                                                       ns * (ns + 1) / 2);
   IFAC_CK_LAUNCH();
   const int kmax = banded ? Pb.kmax : P.kmax;
-  float l1h[2] = {0.f, 0.f};
-  to_host(ctx, l1h, l1.p, sizeof(l1h));
   if (hit) {
     l1h[0] = ac->l1;
   } else if (ac) {
@@ -1513,11 +1587,23 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     ac->sexp = std::move(sige);
     ac->split_ns = nsa;
   }
-  // the banded kernel writes every element of every C block once; the
-  // windowed kernel adds into zeroed sums
-  Buf<longlong2> part(ctx, (size_t)C.nnzb * (BS * BS / 2));
-  if (!banded)
+  if (bc && !tB) {  // op(B) = B in its stored order: keep its slices for a later op(A) = B^T
+    bc->reset();
+    bc->split = std::move(lb);
+    bc->sexp = std::move(taue);
+    bc->l1 = l1h[1];
+    bc->split_ns = ns;
+    bc->from_b = true;
+  }
+  // the windowed kernel adds into zeroed 64-bit sums that a second kernel
+  // converts; the banded kernel holds each tile's complete sums and writes FP64
+  Buf<longlong2> part;
+  if (!banded) {
+    part = Buf<longlong2>(ctx, (size_t)C.nnzb * (BS * BS / 2));
     IFAC_CK(cudaMemsetAsync(part.p, 0, sizeof(longlong2) * (size_t)C.nnzb * (BS * BS / 2), ctx->stream));
+  }
+  int ea_alpha = 0;
+  const double am = std::frexp(alpha, &ea_alpha) * 2.0;  // alpha = am 2^(ea_alpha - 1), am in [1, 2)
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   // fixed point, scale 2^-f relative to sigma_i tau_j, with every partial sum
@@ -1547,7 +1633,12 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     ba.rec_off = Pb.off.p;
     ba.crp = C.row_ptr;
     ba.cci = C.col_idx;
-    ba.cpart = part.p;
+    ba.cval = C.val;
+    ba.cnorm = C.norms;
+    ba.sige = sige_p;
+    ba.taue = taue_p;
+    ba.ea = ea_alpha - 1 - fbits;
+    ba.am = am;
     ba.nb = nb;
     ba.ns = ns;
     ba.slice_rows_a = (int)(A.nnzb + 1) * BS;
@@ -1622,13 +1713,11 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   }
   prof_end(ctx);
   ++ctx->split_launches;
-  {
-    int ea = 0;
-    const double am = std::frexp(alpha, &ea) * 2.0;  // alpha = am 2^(ea - 1), am in [1, 2)
+  if (!banded) {
     k_split_finish<<<(int)std::min<int64_t>(C.nnzb, 152 * 16), 256, 0, ctx->stream>>>(
-        crow, C.col_idx, C.nnzb, part.p, C.val, sige_p, taue.p, ea - 1 - fbits, am, C.norms);
+        crow, C.col_idx, C.nnzb, part.p, C.val, sige_p, taue_p, ea_alpha - 1 - fbits, am, C.norms);
+    IFAC_CK_LAUNCH();
   }
-  IFAC_CK_LAUNCH();
 }
 
 // Failure-path self-test of the bounded waits: one pair of CTAs over a
@@ -1677,13 +1766,16 @@ void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit) { tc::stall_s
 
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                     unsigned long long* pairs_dev, OperandCache* acache) {
+                     unsigned long long* pairs_dev, OperandCache* acache, OperandCache* bcache) {
   if (A.bs != tc::BS) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block product built for bs = 64");
   if (C.nnzb == 0) return;
-  if (prec == IFAC_BF16) tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache);
-  else if (prec == IFAC_TF32) tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache);
+  if (prec == IFAC_BF16)
+    tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache);
+  else if (prec == IFAC_TF32)
+    tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache);
   else if (prec == IFAC_FP64_SPLIT)
-    tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache);
+    tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache,
+                  bcache);
   else fail(IFAC_ERR_UNSUPPORTED, "unknown precision");
 }
 

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <initializer_list>
 #include <cstdint>
 #include <string>
 #include <utility>
@@ -29,6 +30,7 @@ struct ifac_ctx {
   int64_t gemm_launches = 0;
   int64_t tc_launches = 0, split_launches = 0;
   int64_t pairs_fp64 = 0, pairs_tc = 0, pairs_split = 0, slice_pairs = 0;
+  double bytes_fp64 = 0, bytes_tc = 0, bytes_split = 0;  // algorithmic bytes of the product launches
   std::vector<char> event_kind;  // per recorded event pair: 0 FP64, 1 tensor-core (TF32/BF16), 2 split kernel
   // optional event timing of the numeric product kernels
   bool profile = false;
@@ -107,6 +109,13 @@ Mat mat_alloc(ifac_ctx* ctx, int64_t n, int bs, int nb, int64_t nnzb);
 
 // Read back a few device ints/int64/doubles (synchronises the stream).
 void to_host(ifac_ctx* ctx, void* host, const void* dev, size_t bytes);
+// Several small read-backs (4096 bytes in all at most) behind one synchronisation.
+struct HostRead {
+  void* host;
+  const void* dev;
+  size_t bytes;
+};
+void to_host_many(ifac_ctx* ctx, std::initializer_list<HostRead> reads);
 
 // ---- pattern utilities (pattern.cu) ----
 int words_per_row(int nb);
@@ -151,12 +160,18 @@ Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const ui
 void gemm_numeric_fp64(ifac_ctx* ctx, const View& arows, bool tA_blocks, const ifac_bsr& A,
                        const View& bcols, bool tB_blocks, const ifac_bsr& B, double alpha,
                        ifac_bsr& C, const int32_t* crow, unsigned long long* pairs_dev);
-// Converted copies of an op(A) operand that several products share (S in
-// X = S Z across the sweeps of one refinement): the K-major TF32 / BF16 copy,
-// and the BF16 slices with their row scale exponents and scaled 1-norm bound.
-// Slice k does not depend on the slice count, so slices held for s serve any
-// split product with at most s.  The owner resets it when op(A) changes.
+// Converted copies of an operand that several products share: S as op(A) of
+// X = S Z across the sweeps of one refinement (from_b false: the K-major
+// copy in op(A)'s view order, filled by the first product that uses it), or
+// Z as op(B) of X = S Z and then as op(A) = Z^T of Z^T X (from_b true: filled
+// by the op(B) side, transposed blocks in Z's stored order; the Z^T product
+// reaches them through its view's source indices).  Holds the K-major
+// TF32 / BF16 copy, and the BF16 slices with their row (column) scale
+// exponents and scaled 1-norm bound.  Slice k does not depend on the slice
+// count, so slices held for s serve any split product with at most s.  The
+// owner resets it when the operand changes.
 struct OperandCache {
+  bool from_b = false;     // filled from an op(B) (see above)
   int conv_elt = 0;        // bytes per element of conv (4 TF32, 2 BF16); 0 empty
   Buf<uint8_t> conv;       // (nnzb + 1) blocks, the last one zero
   int split_ns = 0;        // slices held (0 empty)
@@ -165,6 +180,7 @@ struct OperandCache {
   Buf<int> sexp;           // row scale exponents of op(A)
   float l1 = 0.f;          // scaled row 1-norm bound of op(A)
   void reset() {
+    from_b = false;
     conv_elt = 0;
     conv.reset();
     split_ns = 0;
@@ -180,7 +196,8 @@ struct OperandCache {
 // split products pairs_dev[1] counts block pairs times slice pairs.
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                     unsigned long long* pairs_dev, OperandCache* acache = nullptr);
+                     unsigned long long* pairs_dev, OperandCache* acache = nullptr,
+                     OperandCache* bcache = nullptr);
 // TF32 (elt 4) / BF16 (elt 2) product of a banded pattern on 128 x 64 tiles
 // (gemm_band.cu).  mapA / mapB: CUtensorMap of the K-major low-precision
 // copies of op(A) and op(B); tiles, ntiles, tile_nk, rec, rec_off: the 2 x 1
@@ -244,7 +261,8 @@ Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 
 // ---- operations used by drivers (ops.cu) ----
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec = IFAC_FP64, bool upper = false, OperandCache* acache = nullptr);
+         int prec = IFAC_FP64, bool upper = false, OperandCache* acache = nullptr,
+         OperandCache* bcache = nullptr);
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma);
 // the symmetric matrix whose upper block triangle (J >= I) is held by U,
 // times alpha, plus beta B and gamma I: alpha (U + strict_upper(U)^T) +

@@ -11,8 +11,10 @@ namespace ifac {
 //   upper: only the blocks (I, J) with J >= I are formed (a product known to
 //   be symmetric, completed by sym_sum)
 //   acache: converted copies of op(A) kept across calls (tensor-core products)
+//   bcache: receives op(B)'s converted copies when op(B) = B (tensor-core
+//   products), for a following product with op(A) = B^T
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec, bool upper, OperandCache* acache) {
+         int prec, bool upper, OperandCache* acache, OperandCache* bcache) {
   const int nb = A.nb;
   if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && A.bs == 64) prec = IFAC_FP64_SPLIT;
   View arows = view_rows(ctx, A, tA);
@@ -26,6 +28,15 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   C.m.col_idx = P.ci.release();
   C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
+  // algorithmic bytes of the product launch: each operand block read once at
+  // the width the kernel reads it, each result block written once
+  {
+    const double blk = (double)A.bs * A.bs;
+    const double ab = (double)(A.nnzb + B.nnzb) * blk, cb = (double)P.nnzb * blk * 8.0;
+    if (prec == IFAC_FP64) ctx->bytes_fp64 += ab * 8.0 + cb;
+    else if (prec == IFAC_FP64_SPLIT) ctx->bytes_split += ab * 2.0 * ctx->split_slices + cb;
+    else ctx->bytes_tc += ab * (prec == IFAC_BF16 ? 2.0 : 4.0) + cb;
+  }
   // multiplied block pairs accumulate in the context's device counters
   if (prec == IFAC_FP64) {
     View bcols = view_rows(ctx, B, !tB);
@@ -33,7 +44,7 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   } else {
     View brows = view_rows(ctx, B, tB);
     gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, upper,
-                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache);
+                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache, bcache);
   }
   Mat R = compact(ctx, std::move(C), P.row.p, tau);
   ctx->products += 1;

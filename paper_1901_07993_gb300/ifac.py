@@ -63,7 +63,8 @@ class _Report(ctypes.Structure):
                 ("fp64_pairs", ctypes.c_int64), ("tc_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double),
                 ("tc_pairs", ctypes.c_int64), ("resid_fro", ctypes.c_double), ("split_launches", ctypes.c_int64),
                 ("split_ms", ctypes.c_double), ("split_pairs", ctypes.c_int64),
-                ("split_slice_pairs", ctypes.c_int64)]
+                ("split_slice_pairs", ctypes.c_int64), ("fp64_bytes", ctypes.c_double),
+                ("tc_bytes", ctypes.c_double), ("split_bytes", ctypes.c_double)]
 
 
 _lib = None
@@ -256,6 +257,9 @@ class Report:
     split_ms: float = 0.0
     split_pairs: int = 0
     split_slice_pairs: int = 0
+    fp64_bytes: float = 0.0
+    tc_bytes: float = 0.0
+    split_bytes: float = 0.0
 
 
 def upload(ctx: Context, host) -> DeviceBSR:
@@ -287,7 +291,8 @@ def _report(r: _Report, rc: int) -> Report:
     return Report(r.sweeps, r.stop_reason, r.levels, r.beta, [r.delta_fro[i] for i in range(r.n_delta)],
                   r.products, r.block_pairs, r.nnzb_Z, r.flops, r.fp64_delta_evals, r.low_sweeps, r.launches,
                   r.gemm_launches, r.gemm_ms, r.fp64_pairs, r.tc_launches, r.tc_ms, r.tc_pairs, r.resid_fro, rc,
-                  r.split_launches, r.split_ms, r.split_pairs, r.split_slice_pairs)
+                  r.split_launches, r.split_ms, r.split_pairs, r.split_slice_pairs, r.fp64_bytes, r.tc_bytes,
+                  r.split_bytes)
 
 
 def bsr_gemm_trunc(ctx: Context, A: DeviceBSR, transA: bool, B: DeviceBSR, transB: bool, alpha: float = 1.0,
