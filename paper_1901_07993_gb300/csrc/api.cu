@@ -506,7 +506,8 @@ int inv_factor_refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S
       validate(S[k], "S[k]");
       if (S[k]->bs != S[0]->bs) fail(IFAC_ERR_INVALID, "batched: members differ in block size");
     }
-    if (opts->prec != IFAC_FP64 && S[0]->bs != 64) fail(IFAC_ERR_UNSUPPORTED, "tensor-core products need bs = 64");
+    if (opts->prec != IFAC_FP64 && S[0]->bs != 64 && S[0]->bs != 32)
+      fail(IFAC_ERR_UNSUPPORTED, "batched mixed precision: bs 32 or 64");
     if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
     bool split = false;
     const ifac_opts o = split_opts(opts, S[0]->bs, &split);

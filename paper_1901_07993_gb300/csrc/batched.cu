@@ -194,7 +194,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         SlicesScope scope(ctx, ns);
         // with low-precision sweeps, the upper block triangle of the
         // symmetric Z^T S Z is formed and the lower one taken from it
-        const bool sym = low;
+        const bool sym = low && bs == 64;
         OperandCache zcache;  // Z's copy (op(B) of S Z) serves again as op(A) = Z^T
         Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd, false, nullptr, &zcache);  // S Z
         Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym, &zcache);               // Z^T (S Z)
@@ -270,12 +270,13 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         if (o.m < 2) P = add(ctx, 0.5, D.m, 0.0, nullptr, 0.0);
         for (int k = 2; k <= o.m; ++k) {
           b = b * (double)(2 * k - 1) / (double)(2 * k);
-          Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec, low);
-          if (low && k == 2 && o.m == 2) {  // delta^2 completed by symmetry inside the sum
+          const bool sym = low && bs == 64;
+          Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec, sym);
+          if (sym && k == 2 && o.m == 2) {  // delta^2 completed by symmetry inside the sum
             P = sym_sum(ctx, b, Dn.m, 0.5, &D.m, 0.0);
             break;
           }
-          if (low) Dn = sym_sum(ctx, 1.0, Dn.m, 0.0, nullptr, 0.0);
+          if (sym) Dn = sym_sum(ctx, 1.0, Dn.m, 0.0, nullptr, 0.0);
           Dk = std::move(Dn);
           P = (k == 2) ? add(ctx, 0.5, D.m, b, &Dk.m, 0.0) : add(ctx, 1.0, P.m, b, &Dk.m, 0.0);
         }

@@ -200,7 +200,10 @@ int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, 
 // ---------------------------------------------------------------------------
 int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, const ifac_opts& o,
                       ifac_bsr* Zout, ifac_report* rep) {
-  if (S_in.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "mixed precision needs bs = 64");
+  if (S_in.bs != 64 && S_in.bs != 32)
+    fail(IFAC_ERR_UNSUPPORTED, "mixed precision: bs 32 or 64 (FP64-accurate delta products at bs 128 are not built)");
+  // upper-triangle symmetric products (and their completion kernel) at bs 64
+  const bool sym = S_in.bs == 64;
   report_init(ctx, rep, o);
   const int low = o.prec;
   Mat S = truncate(ctx, S_in, tau);
@@ -229,9 +232,10 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       // Z's converted copy (op(B) of S Z) serves again as op(A) = Z^T
       OperandCache zcache;
       Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache, &zcache);  // S Z
-      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, true, &zcache);             // Z^T (S Z), J >= I
+      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, sym, &zcache);              // Z^T (S Z), J >= I
       X.reset();
-      D = sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);                     // I - Z^T S Z
+      D = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0)                // I - Z^T S Z
+              : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     }
     e = fro_host(ctx, D.m);
     if (dprec == IFAC_FP64_SPLIT && ns < ctx->split_slices && split_delta_error(ns, S.m.n) > delta_need(e, target, u)) {
@@ -262,7 +266,7 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       --it;
       continue;
     }
-    Mat P = poly_P(ctx, D.m, o.m, tau, low, true);
+    Mat P = poly_P(ctx, D.m, o.m, tau, low, sym);
     D.reset();
     Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low);      // M = Z sum b_k delta^k
     P.reset();

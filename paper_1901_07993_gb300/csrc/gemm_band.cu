@@ -1,28 +1,34 @@
-// gemm_band.cu -- TF32 / BF16 block products of banded patterns on narrow
-// tiles.
+// gemm_band.cu -- TF32 / BF16 block products on narrow tiles, for block
+// sizes 32, 64 and 128.
 //
 // A banded product (a 1D chain: a few stored blocks per block row) gives
 // every output tile only a few K steps, and the wide super-tiles of
-// gemm_tc.cu (up to 4 x 4 blocks) then multiply mostly zero blocks.  Here a
-// tile is 128 x 64: two block rows I0, I0 + 1 of C and one block column J;
-// its K steps are the K's at which op(B)_KJ is stored (the 2 x 1 tile plan).
-// The operands are the low-precision K-major copies gemm_tc.cu makes (one
-// zero block appended to each):
+// gemm_tc.cu (up to 4 x 4 blocks of 64) then multiply mostly zero blocks.
+// Here a tile is 128 x N accumulator elements: 128 / bs block rows I0.. of C
+// and N / bs block columns J0.. (N = 64 for bs 32 and 64, N = 128 for bs 128),
+// and its K steps are the K's at which some op(B)_KJ of its columns is stored
+// (the tile plan of gemm_tc.cu).  A K block is streamed in chunks of at most
+// 64 K elements, one chunk per ring stage.  The operands are K-major
+// low-precision copies of op(A) and op(B) (one zero block appended to each),
+// 128-byte swizzled, or 64-byte swizzled where a chunk row is 64 bytes (BF16
+// at bs 32).  This kernel serves every TF32/BF16 product at bs 32 and 128, and
+// the banded ones at bs 64.
 //
-//   warp 0      : TMA producer -- per K step, op(A)_{I0,K}, op(A)_{I0+1,K}
-//                 and op(B)_{K,J} (64-row boxes, one per 128-byte atom,
-//                 128-byte swizzle) into one stage of a ring;
+//   warp 0      : TMA producer -- per chunk, one box per block and swizzle
+//                 atom of the tile's op(A) block rows and op(B) block columns
+//                 into one stage of a ring;
 //   warp 1      : tensor-memory allocation and the single MMA-issuing thread
 //                 (accumulate in TMEM, commit releases the stage; a double
 //                 buffered accumulator lets the epilogue of one tile overlap
 //                 the next tile's MMAs);
-//   warps 2..9  : epilogue -- tcgen05.ld, alpha, block Frobenius norms
-//                 (compensated FP32 sums, about 2^-42), FP64 stores through a
-//                 shared-memory transpose so that stores are row segments.
+//   warps 2..9  : epilogue -- two warps per tensor-memory lane quarter, each
+//                 on half of the tile's columns: tcgen05.ld, alpha, block
+//                 Frobenius norms (compensated FP32 sums, about 2^-42), FP64
+//                 stores through a shared-memory transpose so that stores are
+//                 row segments.
 //
-// The inputs are the same rounded copies as the super-tile kernel's, so the
-// results are the same products.  Every mbarrier wait is bounded; on expiry
-// the CTA records the error flag and returns.
+// Every mbarrier wait is bounded; on expiry the CTA records the error flag and
+// all its warps leave their loops together.
 #include "internal.cuh"
 #include "tc_common.cuh"
 
@@ -30,39 +36,59 @@ namespace ifac {
 namespace tc {
 namespace bandlp {
 
-constexpr int BS = 64;
-constexpr int TMB = 2;                  // block rows per tile
-constexpr int M = TMB * BS;             // 128 accumulator rows
-constexpr int N = BS;                   // 64 accumulator columns
 constexpr int NEPI = 8;                 // epilogue warps: two per tensor-memory lane quarter
 constexpr int MMA_WARP = 1;
 constexpr int EPI0 = 2;                 // first epilogue warp
 constexpr int NTHREADS = 32 * (2 + NEPI);
-constexpr uint32_t TMEM_COLS = 2 * N;   // double-buffered FP32 accumulator
 
-template <int ELT>
+template <int ELT, int BS>
 struct LP {
-  static constexpr int ATOMS = BS * ELT / 128;  // 128-byte atoms along K per block (TF32 2, BF16 1)
-  static constexpr int A_ATOM = M * 128;        // one atom column of the A tile
-  static constexpr int B_ATOM = N * 128;
+  static constexpr int M = 128;
+  static constexpr int TMB = M / BS;               // block rows per tile (4, 2, 1)
+  static constexpr int N = BS < 64 ? 64 : BS;      // accumulator columns (64, 64, 128)
+  static constexpr int TNB = N / BS;               // block columns per tile (2, 1, 1)
+  static constexpr int KC = BS < 64 ? BS : 64;     // K elements per ring stage
+  static constexpr int KCH = BS / KC;              // stages per K block
+  static constexpr int ROWB = KC * ELT;            // bytes of one operand row's chunk (64, 128, 256)
+  static constexpr int ATOM = ROWB < 128 ? ROWB : 128;  // swizzle atom row: 64 or 128 bytes
+  static constexpr int ATOMS = ROWB / ATOM;        // atom columns per chunk
+  static constexpr int ATOM_ELEMS = ATOM / ELT;
+  static constexpr int A_ATOM = M * ATOM;          // one atom column of the op(A) tile
+  static constexpr int B_ATOM = N * ATOM;
   static constexpr int A_BYTES = ATOMS * A_ATOM;
   static constexpr int B_BYTES = ATOMS * B_ATOM;
-  static constexpr int STAGE = A_BYTES + B_BYTES;  // TF32 48 KB, BF16 24 KB (multiples of 1024)
-  static constexpr int STAGES = (ELT == 4) ? 4 : 8;
-  static constexpr int ATOM_ELEMS = 128 / ELT;
-  static constexpr uint32_t TX = (uint32_t)STAGE;
+  static constexpr int STAGE = A_BYTES + B_BYTES;  // a multiple of 1024
+  static constexpr int STAGES = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
   static constexpr int SMEM = STAGES * STAGE + 1024;
-  static constexpr int KSTEPS = BS * ELT / 32;     // MMAs of 32 bytes of K per block
+  static constexpr int KSTEPS = ROWB / 32;         // MMAs of 32 bytes of K per chunk
+  static constexpr uint32_t SBO = 8 * ATOM;        // 8-row group stride of the swizzled layout
+  static constexpr uint32_t SWZ = ATOM == 128 ? 2 : 4;  // descriptor layout: 128- / 64-byte swizzle
   static constexpr uint32_t IDESC = idesc_of<ELT, N, M>();
+  static constexpr uint32_t TMEM_COLS = 2 * N;     // double-buffered FP32 accumulator
+  static constexpr uint32_t TX = (uint32_t)STAGE;
+  static constexpr int RECW = TMB + TNB;           // plan record: op(A) rows, then op(B) columns
+  static_assert(STAGES >= 2, "ring too shallow");
+  static_assert(STAGE % 1024 == 0, "stages must keep the swizzle alignment");
 };
+
+// shared-memory matrix descriptor of a K-major swizzled operand
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, uint32_t sbo, uint32_t swz) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(sbo >> 4) << 32;          // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                   // version
+  d |= (uint64_t)swz << 61;                 // swizzle mode
+  return d;
+}
 
 }  // namespace bandlp
 
 struct BandLpArgs {
-  const int32_t* tiles;     // [2t] pair of block rows, [2t+1] block column
+  const int32_t* tiles;     // [2t] tile row (of TMB block rows), [2t+1] tile column (of TNB block columns)
   const int* ntiles;        // device: number of tiles
   const int32_t* tile_nk;   // device: K steps of each tile
-  const int32_t* rec;       // plan: per K step, copy indices of op(A)_{I0,K}, op(A)_{I0+1,K}, op(B)_{K,J}
+  const int32_t* rec;       // plan: per K step, copy indices of the tile's op(A)_IK and op(B)_KJ
   const int32_t* rec_off;   // first record of each tile
   const int32_t* crp;       // C pattern
   const int32_t* cci;
@@ -73,10 +99,13 @@ struct BandLpArgs {
   int* err;
 };
 
-template <int ELT>
-__global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, BandLpArgs args) {
+template <int ELT, int BS>
+__global__ void __launch_bounds__(bandlp::NTHREADS, 1)
+    k_gemm_band_lp(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   BandLpArgs args) {
   using namespace bandlp;
-  using L = LP<ELT>;
+  using L = LP<ELT, BS>;
+  constexpr int N = L::N, TMB = L::TMB, TNB = L::TNB;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[L::STAGES], empty_bar[L::STAGES];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain_bar;
@@ -103,7 +132,7 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
   }
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_slot)),
-                 "r"(TMEM_COLS));
+                 "r"(L::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -123,27 +152,32 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
       for (int it = 0; it < mt && ok; ++it) {
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
         const int nk = args.tile_nk[t];
-        const int32_t* r = args.rec + (size_t)args.rec_off[t] * 3;
-        for (int j = 0; j < nk; ++j, r += 3) {
-          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) {
-            ok = false;
-            break;
-          }
-          const uint32_t fb = smem_u32(&full_bar[stage]);
-          mbar_expect_tx(fb, L::TX);
-          issued_mask |= 1u << stage;
-          last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
-          const uint32_t sa = smem_base + (uint32_t)(stage * L::STAGE);
-          const uint32_t sb = sa + L::A_BYTES;
+        const int32_t* r = args.rec + (size_t)args.rec_off[t] * L::RECW;
+        for (int j = 0; j < nk && ok; ++j, r += L::RECW) {
+          for (int c = 0; c < L::KCH; ++c) {
+            if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = smem_u32(&full_bar[stage]);
+            mbar_expect_tx(fb, L::TX);
+            issued_mask |= 1u << stage;
+            last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+            const uint32_t sa = smem_base + (uint32_t)(stage * L::STAGE);
+            const uint32_t sb = sa + L::A_BYTES;
 #pragma unroll
-          for (int a = 0; a < L::ATOMS; ++a) {
-            tma_load_2d(sa + a * L::A_ATOM, &mapA, a * L::ATOM_ELEMS, r[0] * BS, fb);
-            tma_load_2d(sa + a * L::A_ATOM + BS * 128, &mapA, a * L::ATOM_ELEMS, r[1] * BS, fb);
-            tma_load_2d(sb + a * L::B_ATOM, &mapB, a * L::ATOM_ELEMS, r[2] * BS, fb);
-          }
-          if (++stage == L::STAGES) {
-            stage = 0;
-            phase ^= 1u;
+            for (int a = 0; a < L::ATOMS; ++a) {
+              const int x = c * L::KC + a * L::ATOM_ELEMS;
+#pragma unroll
+              for (int i = 0; i < TMB; ++i) tma_load_2d(sa + a * L::A_ATOM + i * BS * L::ATOM, &mapA, x, r[i] * BS, fb);
+#pragma unroll
+              for (int jb = 0; jb < TNB; ++jb)
+                tma_load_2d(sb + a * L::B_ATOM + jb * BS * L::ATOM, &mapB, x, r[TMB + jb] * BS, fb);
+            }
+            if (++stage == L::STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
       }
@@ -169,7 +203,7 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
         const uint32_t tacc = tmem + (uint32_t)(ab * N);
         if (!mbar_wait(smem_u32(&acc_empty[ab]), aphase ^ 1u, &abort_flag, args.err)) break;
         tc_fence_after();
-        for (int j = 0; j < nk; ++j) {
+        for (int j = 0; j < nk * L::KCH; ++j) {
           if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, args.err)) {
             ok = false;
             break;
@@ -179,9 +213,10 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
           const uint32_t sb = sa + L::A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < L::KSTEPS; ++kk) {
-            const int atom = kk / 4, off = (kk % 4) * 32;
-            mma_kstep<ELT>(tacc, smem_desc(sa + atom * L::A_ATOM + off), smem_desc(sb + atom * L::B_ATOM + off),
-                           L::IDESC, (j > 0 || kk > 0) ? 1u : 0u);
+            const int atom = (kk * 32) / L::ATOM, off = (kk * 32) % L::ATOM;
+            mma_kstep<ELT>(tacc, smem_desc_sw(sa + atom * L::A_ATOM + off, L::SBO, L::SWZ),
+                           smem_desc_sw(sb + atom * L::B_ATOM + off, L::SBO, L::SWZ), L::IDESC,
+                           (j > 0 || kk > 0) ? 1u : 0u);
           }
           mma_commit(smem_u32(&empty_bar[stage]));
           if (++stage == L::STAGES) {
@@ -198,19 +233,21 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
     }
   } else {
     // ------------------------------ epilogue ------------------------------
+    constexpr int HALF = N / 2;              // columns per warp
     const int ew = warp - EPI0;              // 0 .. NEPI - 1
     const int q = warp & 3;                  // tensor-memory lane quarter of this warp
-    const int half = ew >> 2;                // columns 32 half .. 32 half + 31 of the block
-    const int row = q * 32 + lane;           // accumulator row 0..127
-    const int rb = row / BS;                 // block row of the tile (warp-uniform)
+    const int half = ew >> 2;                // columns HALF half .. HALF half + HALF - 1 of the tile
+    const int rb = (q * 32) / BS;            // block row of the tile (a warp's rows lie in one)
+    const int rin = (q * 32) % BS;           // first row of the warp within that block
+    const int cb = (half * HALF) / BS;       // block column (a warp's columns lie in one)
     const int et = threadIdx.x - 32 * EPI0;  // 0 .. 32 NEPI - 1
     const float alpha_f = (float)args.alpha;
     for (int it = 0; it < mt; ++it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
       const int ab = it & 1;
       const uint32_t aphase = (uint32_t)(it >> 1) & 1u;
-      const int I0 = args.tiles[2 * t] * TMB, J = args.tiles[2 * t + 1];
-      const int I = I0 + rb;
+      const int I0 = args.tiles[2 * t] * TMB, J0 = args.tiles[2 * t + 1] * TNB;
+      const int I = I0 + rb, J = J0 + cb;
       int p = -1;  // position of C_IJ in C
       if (I < args.nb && J < args.nb) {
         const int lo = args.crp[I], hi = args.crp[I + 1];
@@ -220,27 +257,31 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
       const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
       if (!epi_all<32 * NEPI>(got)) break;  // all epilogue warps go on, or all stop
       tc_fence_after();
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * N + half * 32), v);
       SqAcc sq;
-      if (p >= 0) {  // warp-uniform
+#pragma unroll 1
+      for (int ch = 0; ch < HALF / 32; ++ch) {
+        const int col0 = half * HALF + ch * 32;  // tile column of this chunk
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * N + col0), v);
+        if (p >= 0) {  // warp-uniform
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] *= alpha_f;
-        sq.add32(v);
-        // 32 rows x 16 columns at a time through shared memory, so that each
-        // store instruction writes two 128-byte row segments
-        float* sw = ep_stage[ew];
-        double* blk = args.cval + (size_t)p * BS * BS + (size_t)((q & 1) * 32) * BS + half * 32;
-        const int cc = lane & 15, rr = lane >> 4;
+          for (int e = 0; e < 32; ++e) v[e] *= alpha_f;
+          sq.add32(v);
+          // 32 rows x 16 columns at a time through shared memory, so that each
+          // store instruction writes two row segments
+          float* sw = ep_stage[ew];
+          double* blk = args.cval + (size_t)p * BS * BS + (size_t)rin * BS + (col0 % BS);
+          const int cc = lane & 15, rr = lane >> 4;
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
+          for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) sw[lane * 17 + e] = v[hh * 16 + e];
-          __syncwarp();
+            for (int e = 0; e < 16; ++e) sw[lane * 17 + e] = v[hh * 16 + e];
+            __syncwarp();
 #pragma unroll 4
-          for (int k = 0; k < 32; k += 2)
-            blk[(size_t)(k + rr) * BS + hh * 16 + cc] = f32_to_f64(sw[(k + rr) * 17 + cc]);
-          __syncwarp();
+            for (int k = 0; k < 32; k += 2)
+              blk[(size_t)(k + rr) * BS + hh * 16 + cc] = f32_to_f64(sw[(k + rr) * 17 + cc]);
+            __syncwarp();
+          }
         }
       }
       double ss = sq.value();
@@ -249,15 +290,21 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
       if (lane == 0) partial[q][half] = ss;
       tc_fence_before();
       epi_bar<32 * NEPI>();
-      // norms: block row b of the tile is covered by lane quarters 2b, 2b + 1
-      if (et < TMB) {
-        const int Ib = I0 + et;
-        if (Ib < args.nb && J < args.nb) {
+      // norms: block (br, bc) of the tile sums the warps of its lane quarters
+      // and column halves, in a fixed order
+      if (et < TMB * TNB) {
+        const int br = et / TNB, bc = et % TNB;
+        const int Ib = I0 + br, Jb = J0 + bc;
+        if (Ib < args.nb && Jb < args.nb) {
           const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
-          const int k = lower_bound_i32(args.cci, lo, hi, J);
-          if (k < hi && args.cci[k] == J)
-            args.cnorm[k] = sqrt((partial[2 * et][0] + partial[2 * et][1]) +
-                                 (partial[2 * et + 1][0] + partial[2 * et + 1][1]));
+          const int k = lower_bound_i32(args.cci, lo, hi, Jb);
+          if (k < hi && args.cci[k] == Jb) {
+            double s = 0.0;
+            for (int qq = 0; qq < 4; ++qq)
+              for (int h = 0; h < 2; ++h)
+                if ((qq * 32) / BS == br && (h * HALF) / BS == bc) s += partial[qq][h];
+            args.cnorm[k] = sqrt(s);
+          }
         }
       }
       epi_bar<32 * NEPI>();
@@ -269,28 +316,36 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1) k_gemm_band_lp(const __gr
   if (warp == MMA_WARP) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS));
   }
 }
 
-template <int ELT>
+template <int ELT, int BS>
 void launch_band_lp(ifac_ctx* ctx, const CUtensorMap& mapA, const CUtensorMap& mapB, const BandLpArgs& args,
                     int tiles_bound) {
+  using L = bandlp::LP<ELT, BS>;
   static std::atomic<unsigned long long> attr{0};
   if (first_on_device(attr, ctx->device))
-    IFAC_CK(cudaFuncSetAttribute(k_gemm_band_lp<ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bandlp::LP<ELT>::SMEM));
+    IFAC_CK(cudaFuncSetAttribute(k_gemm_band_lp<ELT, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   const int grid = (int)std::min<int64_t>(std::max(tiles_bound, 1), sms);
-  k_gemm_band_lp<ELT><<<grid, bandlp::NTHREADS, bandlp::LP<ELT>::SMEM, ctx->stream>>>(mapA, mapB, args);
+  k_gemm_band_lp<ELT, BS><<<grid, bandlp::NTHREADS, L::SMEM, ctx->stream>>>(mapA, mapB, args);
   IFAC_CK_LAUNCH();
+}
+
+template <typename L>
+static void shape_of(BandShape* s) {
+  s->tmb = L::TMB;
+  s->tnb = L::TNB;
+  s->atom_elems = L::ATOM_ELEMS;
+  s->atom_bytes = L::ATOM;
 }
 
 }  // namespace tc
 
 // the host entry used by gemm_tc.cu's dispatcher
-void band_lp_product(ifac_ctx* ctx, int elt, const void* mapA, const void* mapB, const int32_t* tiles,
+void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const void* mapB, const int32_t* tiles,
                      const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
                      int tiles_bound, double alpha, ifac_bsr& C) {
   tc::BandLpArgs a{};
@@ -308,8 +363,33 @@ void band_lp_product(ifac_ctx* ctx, int elt, const void* mapA, const void* mapB,
   a.err = ctx->dev_err;
   const CUtensorMap& mA = *static_cast<const CUtensorMap*>(mapA);
   const CUtensorMap& mB = *static_cast<const CUtensorMap*>(mapB);
-  if (elt == 2) tc::launch_band_lp<2>(ctx, mA, mB, a, tiles_bound);
-  else tc::launch_band_lp<4>(ctx, mA, mB, a, tiles_bound);
+  if (elt == 2) {
+    if (bs == 32) tc::launch_band_lp<2, 32>(ctx, mA, mB, a, tiles_bound);
+    else if (bs == 64) tc::launch_band_lp<2, 64>(ctx, mA, mB, a, tiles_bound);
+    else if (bs == 128) tc::launch_band_lp<2, 128>(ctx, mA, mB, a, tiles_bound);
+    else fail(IFAC_ERR_UNSUPPORTED, "tensor-core products: bs 32, 64 or 128");
+  } else {
+    if (bs == 32) tc::launch_band_lp<4, 32>(ctx, mA, mB, a, tiles_bound);
+    else if (bs == 64) tc::launch_band_lp<4, 64>(ctx, mA, mB, a, tiles_bound);
+    else if (bs == 128) tc::launch_band_lp<4, 128>(ctx, mA, mB, a, tiles_bound);
+    else fail(IFAC_ERR_UNSUPPORTED, "tensor-core products: bs 32, 64 or 128");
+  }
+}
+
+BandShape band_lp_shape(int elt, int bs) {
+  BandShape s{};
+  if (elt == 2) {
+    if (bs == 32) tc::shape_of<tc::bandlp::LP<2, 32>>(&s);
+    else if (bs == 64) tc::shape_of<tc::bandlp::LP<2, 64>>(&s);
+    else if (bs == 128) tc::shape_of<tc::bandlp::LP<2, 128>>(&s);
+    else fail(IFAC_ERR_UNSUPPORTED, "tensor-core products: bs 32, 64 or 128");
+  } else {
+    if (bs == 32) tc::shape_of<tc::bandlp::LP<4, 32>>(&s);
+    else if (bs == 64) tc::shape_of<tc::bandlp::LP<4, 64>>(&s);
+    else if (bs == 128) tc::shape_of<tc::bandlp::LP<4, 128>>(&s);
+    else fail(IFAC_ERR_UNSUPPORTED, "tensor-core products: bs 32, 64 or 128");
+  }
+  return s;
 }
 
 }  // namespace ifac

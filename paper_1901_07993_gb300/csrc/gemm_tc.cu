@@ -474,31 +474,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // ---------------------------------------------------------------------------
 // operand conversion and tile list
 // ---------------------------------------------------------------------------
-// dst[q] = low-precision copy of block src[q] of X (K-major: transposed when
-// tr).  Reads are coalesced; a transposed copy goes through shared memory.
-template <int ELT>
+// dst[q] = low-precision copy of block src[q] of X (B x B blocks; K-major:
+// transposed when tr).  Reads are coalesced; a transposed copy goes through
+// shared memory in 32 x 32 sub-blocks.
+template <int ELT, int B>
 __global__ void __launch_bounds__(256) k_convert(const double* __restrict__ val, const int32_t* __restrict__ src,
                                                  int64_t nblk, int tr, void* __restrict__ dst) {
-  constexpr int BSZ = BS * BS;
+  constexpr int BSZ = B * B;
   using T = typename std::conditional<ELT == 2, uint16_t, uint32_t>::type;
-  __shared__ T tile[BS][BS + 1];
+  __shared__ T tile[32][33];
+  auto conv = [](double x) -> T {
+    if constexpr (ELT == 2) return f64_to_bf16_bits_rne(x);
+    else return f32_to_tf32(__uint_as_float(f64_to_f32_bits_rne(x)));
+  };
   T* out = reinterpret_cast<T*>(dst);
   for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
     const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
     T* d = out + (size_t)qb * BSZ;
-    for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
-      const double x = s[e];
-      T y;
-      if constexpr (ELT == 2) y = f64_to_bf16_bits_rne(x);
-      else y = f32_to_tf32(__uint_as_float(f64_to_f32_bits_rne(x)));
-      if (tr) tile[e / BS][e % BS] = y;
-      else d[e] = y;
+    if (!tr) {
+      for (int e = threadIdx.x; e < BSZ; e += blockDim.x) d[e] = conv(s[e]);
+      continue;
     }
-    if (tr) {
-      __syncthreads();
-      for (int e = threadIdx.x; e < BSZ; e += blockDim.x) d[e] = tile[e % BS][e / BS];
-      __syncthreads();
-    }
+    for (int ti = 0; ti < B / 32; ++ti)
+      for (int tj = 0; tj < B / 32; ++tj) {
+        // stored rows 32 ti.., columns 32 tj.. -> copy rows 32 tj.., columns 32 ti..
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+          const int r = e >> 5, c = e & 31;
+          tile[r][c] = conv(s[(size_t)(ti * 32 + r) * B + tj * 32 + c]);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+          const int r = e >> 5, c = e & 31;
+          d[(size_t)(tj * 32 + r) * B + ti * 32 + c] = tile[c][r];
+        }
+        __syncthreads();
+      }
   }
 }
 
@@ -841,13 +851,49 @@ static CUtensorMap make_map(void* base, int64_t nblk) {
   return m;
 }
 
+// the same for bs x bs blocks (rows = nblk * bs, bs elements per row) with
+// boxes of one swizzle atom (atom_elems elements, 64- or 128-byte swizzle) by
+// bs rows, as the narrow-tile kernel reads them
+static CUtensorMap make_map_bs(int elt, int bs, void* base, int64_t nblk, const BandShape& sh) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)bs, (cuuint64_t)nblk * bs};
+  cuuint64_t strides[1] = {(cuuint64_t)bs * elt};
+  cuuint32_t box[2] = {(cuuint32_t)sh.atom_elems, (cuuint32_t)bs};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encoder()(&m, elt == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         sh.atom_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(IFAC_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return m;
+}
+
+template <int ELT>
+static void convert_blocks(ifac_ctx* ctx, int bs, const double* val, const int32_t* src, int64_t nblk, bool tr,
+                           void* dst) {
+  const int grid = (int)std::min<int64_t>(nblk, 152 * 16);
+  if (bs == 32) k_convert<ELT, 32><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
+  else if (bs == 64) k_convert<ELT, 64><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
+  else k_convert<ELT, 128><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
+  IFAC_CK_LAUNCH();
+}
+
+// the narrow-tile plan of a block size (tile of 128 / bs x max(64, bs) / bs blocks)
+static Plan band_plan(ifac_ctx* ctx, int bs, const View& arows, const ifac_bsr& A, bool tA, const View& brows,
+                      const ifac_bsr& B, const ifac_bsr& C, const int32_t* crow, int kmax_limit,
+                      const int32_t* amap, const HostRead* extra = nullptr) {
+  if (bs == 32) return make_plan<4, 2>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra);
+  if (bs == 64) return make_plan<2, 1>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra);
+  return make_plan<1, 1>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra);
+}
+
 template <int ELT>
 static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
                 const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                 unsigned long long* pairs, OperandCache* ac, OperandCache* bc) {
   using Cf = Cfg<ELT>;
-  const int nb = A.nb;
-  const size_t bbytes = (size_t)BS * BS * ELT;
+  const int nb = A.nb, bs = A.bs;
+  const size_t bbytes = (size_t)bs * bs * ELT;
   // a cache filled by an earlier product's op(B) holds transposed blocks in
   // the stored order: it serves op(A) = that matrix transposed, through the
   // view's source indices, and nothing else
@@ -860,11 +906,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   if (!hit) {
     la = Buf<uint8_t>(ctx, (size_t)(A.nnzb + 1) * bbytes);
     IFAC_CK(cudaMemsetAsync(la.p + (size_t)A.nnzb * bbytes, 0, bbytes, ctx->stream));
-    if (A.nnzb) {
-      k_convert<ELT><<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, 0, ctx->stream>>>(A.val, arows.src, A.nnzb,
-                                                                                         tA ? 1 : 0, la.p);
-      IFAC_CK_LAUNCH();
-    }
+    if (A.nnzb) convert_blocks<ELT>(ctx, bs, A.val, arows.src, A.nnzb, tA, la.p);
     if (ac) {
       ac->conv = std::move(la);
       ac->conv_elt = ELT;
@@ -872,13 +914,8 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   uint8_t* const la_p = ac ? ac->conv.p : la.p;
   IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
-  if (B.nnzb) {
-    k_convert<ELT><<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, 0, ctx->stream>>>(B.val, brows.src, B.nnzb,
-                                                                                       tB ? 0 : 1, lb.p);
-    IFAC_CK_LAUNCH();
-  }
-  const CUtensorMap mapA = make_map<ELT>(la_p, A.nnzb + 1);
-  const CUtensorMap mapB = make_map<ELT>(lb.p, B.nnzb + 1);
+  if (B.nnzb) convert_blocks<ELT>(ctx, bs, B.val, brows.src, B.nnzb, !tB, lb.p);
+  uint8_t* const lb_p = lb.p;
   if (bc && !tB) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
     bc->reset();
     bc->conv = std::move(lb);
@@ -888,19 +925,25 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   k_count_pairs<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(arows.rp, arows.ci, nb, brows.rp, brows.ci,
                                                                       upper ? 1 : 0, pairs, nullptr, 0);
   IFAC_CK_LAUNCH();
-  // banded products (no 128 x 64 tile with more than KW K steps) run on
-  // 128 x 64 tiles (gemm_band.cu); the others on the super-tiles below
+  // narrow tiles (gemm_band.cu) for every product at bs 32 and 128, and for
+  // the banded ones at bs 64 (no 128 x 64 tile with more than KW K steps);
+  // the super-tiles below for the other bs-64 products
   {
-    Plan Pb = make_plan<2, 1>(ctx, arows, A, tA, brows, B, C, crow, true, KW, amap);
-    if (Pb.kmax >= 1 && Pb.kmax <= KW) {
+    const BandShape sh = band_lp_shape(ELT, bs);
+    Plan Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? KW : 0, amap);
+    if (bs != 64 || (Pb.kmax >= 1 && Pb.kmax <= KW)) {
+      const CUtensorMap mapA = make_map_bs(ELT, bs, la_p, A.nnzb + 1, sh);
+      const CUtensorMap mapB = make_map_bs(ELT, bs, lb_p, B.nnzb + 1, sh);
       prof_begin(ctx, 1);
-      band_lp_product(ctx, ELT, &mapA, &mapB, Pb.tiles.p, Pb.coff.p + Pb.nchunk, Pb.tnk.p, Pb.rec.p, Pb.off.p,
+      band_lp_product(ctx, ELT, bs, &mapA, &mapB, Pb.tiles.p, Pb.coff.p + Pb.nchunk, Pb.tnk.p, Pb.rec.p, Pb.off.p,
                       Pb.ntiles, alpha, C);
       prof_end(ctx);
       ++ctx->tc_launches;
       return;
     }
   }
+  const CUtensorMap mapA = make_map<ELT>(la_p, A.nnzb + 1);
+  const CUtensorMap mapB = make_map<ELT>(lb_p, B.nnzb + 1);
   Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false, 0, amap);
   static std::atomic<unsigned long long> attr{0};
   if (first_on_device(attr, ctx->device))
@@ -1767,8 +1810,9 @@ void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit) { tc::stall_s
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache, OperandCache* bcache) {
-  if (A.bs != tc::BS) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block product built for bs = 64");
   if (C.nnzb == 0) return;
+  if (A.bs != tc::BS && !((A.bs == 32 || A.bs == 128) && (prec == IFAC_TF32 || prec == IFAC_BF16)))
+    fail(IFAC_ERR_UNSUPPORTED, "tensor-core block products: TF32/BF16 at bs 32, 64, 128; split at bs 64");
   if (prec == IFAC_BF16)
     tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache);
   else if (prec == IFAC_TF32)

@@ -198,11 +198,19 @@ void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const 
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache = nullptr,
                      OperandCache* bcache = nullptr);
-// TF32 (elt 4) / BF16 (elt 2) product of a banded pattern on 128 x 64 tiles
-// (gemm_band.cu).  mapA / mapB: CUtensorMap of the K-major low-precision
-// copies of op(A) and op(B); tiles, ntiles, tile_nk, rec, rec_off: the 2 x 1
-// tile plan (copy indices of op(A)_{I0,K}, op(A)_{I0+1,K}, op(B)_{K,J}).
-void band_lp_product(ifac_ctx* ctx, int elt, const void* mapA, const void* mapB, const int32_t* tiles,
+// TF32 (elt 4) / BF16 (elt 2) product on narrow tiles of 128 accumulator
+// rows (gemm_band.cu), bs 32, 64 or 128.  mapA / mapB: CUtensorMap of the
+// K-major low-precision copies of op(A) and op(B), boxes of one swizzle atom
+// by bs rows (band_lp_shape); tiles, ntiles, tile_nk, rec, rec_off: the tile
+// plan for tmb x tnb blocks (copy indices of op(A)_IK of the tile's block
+// rows, then op(B)_KJ of its block columns).
+struct BandShape {
+  int tmb, tnb;      // block rows and columns of a tile
+  int atom_elems;    // elements of one swizzle atom row (the box's inner extent)
+  int atom_bytes;    // 128 (128-byte swizzle) or 64 (64-byte swizzle)
+};
+BandShape band_lp_shape(int elt, int bs);
+void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const void* mapB, const int32_t* tiles,
                      const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
                      int tiles_bound, double alpha, ifac_bsr& C);
 // Failure-path self-test: a tensor-core launch whose pipeline never fills, so

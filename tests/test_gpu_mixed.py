@@ -54,3 +54,20 @@ def test_mixed_refine_reaches_target(ctx, prec, kind, n):
     assert abs(resid_gpu - resid) <= 1e-3 * resid + 1e-13
     measured = {("chain", 1): 7.0e-5, ("chain", 2): 5.5e-4, ("cluster", 1): 7.2e-4, ("cluster", 2): 5.5e-3}
     assert rel <= 3 * measured[(kind, prec)]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_refine_bs32(ctx, prec):
+    """The mixed schedule at bs 32: TF32/BF16 sweeps on the narrow-tile
+    tensor-core kernel (full products: the symmetric completion is built for
+    bs 64), then delta with FP64-pipe products; the oracle's FP64 residual of
+    the returned factor reaches the target."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(4096, 32, seed=0)
+    tau, target = 1e-13, 1e-10
+    Z, rep = ifac.inv_factor_refine(ctx, ifac.upload(ctx, S), tau, target, ifac.opts(prec=prec, max_iter=80))
+    a = Z.download()
+    resid = oracle.resid(S, oracle.Mat(a.n, 32, a.row_ptr, a.col_idx, a.val))
+    print(f"bs 32 prec={prec}: resid {resid:.2e}, low sweeps {rep.low_sweeps}, FP64 delta evals {rep.fp64_delta_evals}")
+    assert rep.low_sweeps >= 2 and rep.fp64_delta_evals >= 1 and rep.tc_launches > 0
+    assert resid <= 10 * target

@@ -159,3 +159,40 @@ def test_tc_large_pattern_csr_lookups(ctx, prec):
         assert np.abs(got.val - ref.val).max() <= 1e-13 * np.abs(ref.val).max()
     else:
         _check(ctx, S, S, True, False, prec)
+
+
+@pytest.mark.parametrize("bs", [32, 128])
+@pytest.mark.parametrize("prec", [TF32, BF16])
+@pytest.mark.parametrize("tA,tB", [(False, False), (True, False), (False, True)])
+def test_tc_block_sizes_32_and_128(ctx, bs, prec, tA, tB):
+    """The narrow-tile kernel at bs 32 (tiles of 4 x 2 blocks; BF16 rows of
+    64 bytes, 64-byte swizzle) and bs 128 (tiles of one block, K in two
+    chunks): random patterns with empty rows, a ragged last tile (nb not a
+    multiple of the tile's block rows) and n not a multiple of bs."""
+    nb = 11 if bs == 32 else 5
+    A = synth.random_bsr(nb, bs, 0.45, seed=60 + bs, empty_rows=1, n=nb * bs - 5)
+    B = synth.random_bsr(nb, bs, 0.45, seed=61 + bs, empty_rows=1, n=nb * bs - 5)
+    _check(ctx, A, B, tA, tB, prec, alpha=0.75)
+
+
+@pytest.mark.parametrize("bs", [32, 128])
+@pytest.mark.parametrize("prec", [TF32, BF16])
+def test_tc_block_sizes_overlap_and_rounding(ctx, bs, prec):
+    """S S on a 1D chain and a dense 3D cluster at bs 32 / 128 against the
+    rounded-input bound, and C = A I reproducing the rounded A exactly."""
+    from paper_1901_07993_gb300 import ifac
+    for S in (synth.chain_overlap(3000, bs, seed=5), synth.cluster_overlap(1024, bs, seed=6)):
+        St = oracle.truncate(S, 1e-10)
+        St = synth.HostBSR(St.n, bs, St.row_ptr, St.col_idx, St.val)
+        _check(ctx, St, St, False, False, prec)
+    rng = np.random.default_rng(bs + prec)
+    nb = 3
+    v = rng.standard_normal((nb * nb, bs, bs))
+    rp = np.arange(0, nb * nb + 1, nb, dtype=np.int32)
+    ci = np.tile(np.arange(nb, dtype=np.int32), nb)
+    A = synth.HostBSR(nb * bs, bs, rp, ci, v)
+    eye = np.zeros((nb, bs, bs))
+    eye[:] = np.eye(bs)
+    I = synth.HostBSR(nb * bs, bs, np.arange(nb + 1, dtype=np.int32), np.arange(nb, dtype=np.int32), eye)
+    got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), False, ifac.upload(ctx, I), False, 1.0, 0.0, prec).download()
+    assert np.array_equal(got.val, rounded(A, prec).val)
