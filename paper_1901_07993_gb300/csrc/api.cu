@@ -441,7 +441,7 @@ static ifac_opts split_opts(const ifac_opts* in, int bs, bool* split) {
   ifac_opts o = *in;
   *split = o.prec == IFAC_FP64_SPLIT;
   if (*split) {
-    if (bs != 64) fail(IFAC_ERR_UNSUPPORTED, "split tensor-core products need bs = 64");
+    if (bs != 32 && bs != 64 && bs != 128) fail(IFAC_ERR_UNSUPPORTED, "split tensor-core products: bs 32, 64 or 128");
     o.prec = IFAC_FP64;
   }
   return o;
@@ -506,8 +506,8 @@ int inv_factor_refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S
       validate(S[k], "S[k]");
       if (S[k]->bs != S[0]->bs) fail(IFAC_ERR_INVALID, "batched: members differ in block size");
     }
-    if (opts->prec != IFAC_FP64 && S[0]->bs != 64 && S[0]->bs != 32)
-      fail(IFAC_ERR_UNSUPPORTED, "batched mixed precision: bs 32 or 64");
+    if (opts->prec != IFAC_FP64 && S[0]->bs != 32 && S[0]->bs != 64 && S[0]->bs != 128)
+      fail(IFAC_ERR_UNSUPPORTED, "batched mixed precision: bs 32, 64 or 128");
     if (!(tau >= 0) || !(target >= 0)) fail(IFAC_ERR_INVALID, "tau and target must be >= 0");
     bool split = false;
     const ifac_opts o = split_opts(opts, S[0]->bs, &split);

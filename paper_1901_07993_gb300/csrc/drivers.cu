@@ -64,9 +64,10 @@ void report_init(ifac_ctx* ctx, ifac_report* r, const ifac_opts& o) {
 }
 
 // precision of FP64-accurate delta products: the split tensor-core product
-// where the options ask for it and it is built (bs = 64), else the FP64 pipe
+// where the options ask for it and it is built (bs 32, 64, 128), else the
+// FP64 pipe
 int delta_prec_of(const ifac_opts& o, int bs) {
-  return (o.delta_prec == IFAC_FP64_SPLIT && bs == 64) ? IFAC_FP64_SPLIT : IFAC_FP64;
+  return (o.delta_prec == IFAC_FP64_SPLIT && (bs == 32 || bs == 64 || bs == 128)) ? IFAC_FP64_SPLIT : IFAC_FP64;
 }
 
 // A split product with s slices per operand errs by about 2^-(7 s - 3)
@@ -200,8 +201,10 @@ int refine_irsi(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, 
 // ---------------------------------------------------------------------------
 int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double target, const ifac_opts& o,
                       ifac_bsr* Zout, ifac_report* rep) {
-  if (S_in.bs != 64 && S_in.bs != 32)
-    fail(IFAC_ERR_UNSUPPORTED, "mixed precision: bs 32 or 64 (FP64-accurate delta products at bs 128 are not built)");
+  if (S_in.bs != 32 && S_in.bs != 64 && S_in.bs != 128)
+    fail(IFAC_ERR_UNSUPPORTED, "mixed precision: bs 32, 64 or 128");
+  if (S_in.bs == 128 && delta_prec_of(o, 128) != IFAC_FP64_SPLIT)
+    fail(IFAC_ERR_UNSUPPORTED, "mixed precision at bs 128 needs split delta products (the FP64 pipe kernel stops at 64)");
   // upper-triangle symmetric products (and their completion kernel) at bs 64
   const bool sym = S_in.bs == 64;
   report_init(ctx, rep, o);

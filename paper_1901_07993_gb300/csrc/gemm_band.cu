@@ -71,17 +71,6 @@ struct LP {
   static_assert(STAGE % 1024 == 0, "stages must keep the swizzle alignment");
 };
 
-// shared-memory matrix descriptor of a K-major swizzled operand
-__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, uint32_t sbo, uint32_t swz) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(sbo >> 4) << 32;          // stride byte offset: 8-row groups
-  d |= (uint64_t)1 << 46;                   // version
-  d |= (uint64_t)swz << 61;                 // swizzle mode
-  return d;
-}
-
 }  // namespace bandlp
 
 struct BandLpArgs {

@@ -868,6 +868,22 @@ static CUtensorMap make_map_bs(int elt, int bs, void* base, int64_t nblk, const 
   return m;
 }
 
+// BF16 slices of bs x bs blocks with boxes of inner x rows elements, 64- or
+// 128-byte swizzle (inner * 2 bytes)
+static CUtensorMap make_map_box(int bs, void* base, int64_t nblk, int inner, int rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)bs, (cuuint64_t)nblk * bs};
+  cuuint64_t strides[1] = {(cuuint64_t)bs * 2};
+  cuuint32_t box[2] = {(cuuint32_t)inner, (cuuint32_t)rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(IFAC_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return m;
+}
+
 template <int ELT>
 static void convert_blocks(ifac_ctx* ctx, int bs, const double* val, const int32_t* src, int64_t nblk, bool tr,
                            void* dst) {
@@ -1007,7 +1023,7 @@ constexpr int SPLIT_BITS = 7;
 // row view: max_k |x_rk| = m 2^e with m in [0.5, 1) (e = 0 for an all-zero row);
 // the largest scaled row 1-norm sum_k |x_rk| / sigma (FP32, magnitudes
 // truncated to 24 bits) into *l1max as FP32 bits
-__device__ __forceinline__ void row_scale_out(unsigned long long m, float l1, int nblocks, int* eout,
+__device__ __forceinline__ void row_scale_out(unsigned long long m, float l1, int nscalars, int* eout,
                                               unsigned int* l1max) {
   const int ea = (int)(m >> 52);
   int e = 0;
@@ -1016,7 +1032,7 @@ __device__ __forceinline__ void row_scale_out(unsigned long long m, float l1, in
   *eout = e;
   if (m != 0) {
     // entries below 2^-126 were left out: add their largest possible share
-    const float s = ldexpf(l1, -e) + (float)nblocks * (float)BS * ldexpf(1.0f, -126 - e);
+    const float s = ldexpf(l1, -e) + (float)nscalars * ldexpf(1.0f, -126 - e);
     atomicMax(l1max, __float_as_uint(fminf(s, 3.0e38f)));
   }
 }
@@ -1029,35 +1045,37 @@ __device__ __forceinline__ void row_scale_acc(double x, unsigned long long& m, f
     l1 += __uint_as_float(e32 > 254 ? 0x7f7fffffu : (((uint32_t)e32 << 23) | (uint32_t)((u >> 29) & 0x7fffffu)));
 }
 
-// transposed views: one CTA of BS threads per block row; thread r takes
+// transposed views: one CTA of B threads per block row; thread r takes
 // column r of each stored block (op(X) row r), reads coalesced across threads
-__global__ void __launch_bounds__(BS) k_row_scale_t(const int32_t* __restrict__ rp, const int32_t* __restrict__ src,
-                                                    int nb, const double* __restrict__ val, int* __restrict__ eout,
-                                                    unsigned int* __restrict__ l1max) {
+template <int B>
+__global__ void __launch_bounds__(B) k_row_scale_t(const int32_t* __restrict__ rp, const int32_t* __restrict__ src,
+                                                   int nb, const double* __restrict__ val, int* __restrict__ eout,
+                                                   unsigned int* __restrict__ l1max) {
   const int I = blockIdx.x, r = threadIdx.x;
   if (I >= nb) return;
   unsigned long long m = 0;
   float l1 = 0.0f;
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
-    const double* blk = val + (size_t)(src ? src[q] : q) * BS * BS;
+    const double* blk = val + (size_t)(src ? src[q] : q) * B * B;
 #pragma unroll 8
-    for (int k = 0; k < BS; ++k) row_scale_acc(blk[k * BS + r], m, l1);
+    for (int k = 0; k < B; ++k) row_scale_acc(blk[k * B + r], m, l1);
   }
-  row_scale_out(m, l1, rp[I + 1] - rp[I], eout + (size_t)I * BS + r, l1max);
+  row_scale_out(m, l1, (rp[I + 1] - rp[I]) * B, eout + (size_t)I * B + r, l1max);
 }
 
 // rows stored as rows: one warp per scalar row, lanes along the row (coalesced)
+template <int B>
 __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb,
                             const double* __restrict__ val, int* __restrict__ eout, unsigned int* __restrict__ l1max) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= (int64_t)nb * BS) return;
-  const int I = (int)(w / BS), r = (int)(w % BS);
+  if (w >= (int64_t)nb * B) return;
+  const int I = (int)(w / B), r = (int)(w % B);
   unsigned long long m = 0;  // |x| bit patterns order like the magnitudes
   float l1 = 0.0f;
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
-    const double* blk = val + (size_t)(src ? src[q] : q) * BS * BS;
-    for (int c = lane; c < BS; c += 32) row_scale_acc(blk[r * BS + c], m, l1);
+    const double* blk = val + (size_t)(src ? src[q] : q) * B * B;
+    for (int c = lane; c < B; c += 32) row_scale_acc(blk[r * B + c], m, l1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1065,26 +1083,30 @@ __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __res
     m = u > m ? u : m;
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
   }
-  if (lane == 0) row_scale_out(m, l1, rp[I + 1] - rp[I], eout + w, l1max);
+  if (lane == 0) row_scale_out(m, l1, (rp[I + 1] - rp[I]) * B, eout + w, l1max);
 }
 
 // sigma exponents (and the scaled 1-norm bound) of the rows of a row view
-static void row_scales(ifac_ctx* ctx, const int32_t* rp, const int32_t* src, int nb, bool tr, const double* val,
-                       int* eout, unsigned int* l1max) {
-  if (tr) {
-    k_row_scale_t<<<nb, BS, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+static void row_scales(ifac_ctx* ctx, int bs, const int32_t* rp, const int32_t* src, int nb, bool tr,
+                       const double* val, int* eout, unsigned int* l1max) {
+  const int g = cdiv((int64_t)nb * bs * 32, 256);
+  if (bs == 32) {
+    if (tr) k_row_scale_t<32><<<nb, 32, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+    else k_row_scale<32><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+  } else if (bs == 64) {
+    if (tr) k_row_scale_t<64><<<nb, 64, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+    else k_row_scale<64><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
   } else {
-    k_row_scale<<<cdiv((int64_t)nb * BS * 32, 256), 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+    if (tr) k_row_scale_t<128><<<nb, 128, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+    else k_row_scale<128><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
   }
   IFAC_CK_LAUNCH();
 }
 
 // NS BF16 slice copies (K-major, op() CSR order) of a view; row r of block qb
-// has scale exponent sexp[sblk[qb] * BS + r].  With Y = x 2^(62 - e) held as a
+// has scale exponent sexp[sblk[qb] * B + r].  With Y = x 2^(62 - e) held as a
 // 64-bit integer (|Y| < 2^62; bits below 2^-62 of sigma dropped by rounding),
 // digit k is q_k = round(Y_k / 2^(62 - 7k)), Y_{k+1} = Y_k - q_k 2^(62 - 7k).
-constexpr int SPLIT_TILE_BYTES = BS * (BS + 1) * (int)sizeof(double);
-
 __device__ __forceinline__ void split_digits(double x, int e, int ns, int (&q)[8]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int ea = (int)((u >> 52) & 0x7ff);
@@ -1108,36 +1130,66 @@ __device__ __forceinline__ void split_digits(double x, int e, int ns, int (&q)[8
   }
 }
 
+// digits of elements (r, c) and (r, c + 1) of op(X)'s block into the slices
+__device__ __forceinline__ void split_pair(double x0, double x1, int e, int ns, __nv_bfloat16* dst,
+                                           size_t slice_stride) {
+  int q0[8], q1[8];
+  split_digits(x0, e, ns, q0);
+  split_digits(x1, e, ns, q1);
+  for (int k = 0; k < ns; ++k) {
+    __nv_bfloat162 v;
+    v.x = __float2bfloat16_rn((float)q0[k]);
+    v.y = __float2bfloat16_rn((float)q1[k]);
+    *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)k * slice_stride) = v;
+  }
+}
+
+template <int B>
 __global__ void __launch_bounds__(256) k_split(const double* __restrict__ val, const int32_t* __restrict__ src,
                                                int64_t nblk, int tr, const int32_t* __restrict__ sblk,
                                                const int* __restrict__ sexp, int ns,
                                                __nv_bfloat16* __restrict__ dst) {
-  constexpr int BSZ = BS * BS;
-  extern __shared__ double tile_raw[];  // transposed views only: BS x (BS + 1) doubles
-  double(*tile)[BS + 1] = reinterpret_cast<double(*)[BS + 1]>(tile_raw);
+  constexpr int BSZ = B * B;
+  __shared__ double tile[32][33];  // transposed views: 32 x 32 sub-blocks
   const size_t slice_stride = (size_t)(nblk + 1) * BSZ;
   for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
     const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
-    const int* se = sexp + (size_t)sblk[qb] * BS;
-    if (tr) {  // coalesced read, transposed through shared memory
-      for (int e = threadIdx.x; e < BSZ; e += blockDim.x) tile[e / BS][e % BS] = s[e];
-      __syncthreads();
-    }
-    for (int e2 = threadIdx.x; e2 < BSZ / 2; e2 += blockDim.x) {
-      const int e = 2 * e2, r = e / BS, c = e % BS;  // elements (r, c) and (r, c + 1) of op(X)'s block
-      const double x0 = tr ? tile[c][r] : s[e], x1 = tr ? tile[c + 1][r] : s[e + 1];
-      int q0[8], q1[8];
-      split_digits(x0, se[r], ns, q0);
-      split_digits(x1, se[r], ns, q1);
-      for (int k = 0; k < ns; ++k) {
-        __nv_bfloat162 v;
-        v.x = __float2bfloat16_rn((float)q0[k]);
-        v.y = __float2bfloat16_rn((float)q1[k]);
-        *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)k * slice_stride + (size_t)qb * BSZ + e) = v;
+    const int* se = sexp + (size_t)sblk[qb] * B;
+    __nv_bfloat16* d = dst + (size_t)qb * BSZ;
+    if (!tr) {
+      for (int e2 = threadIdx.x; e2 < BSZ / 2; e2 += blockDim.x) {
+        const int e = 2 * e2, r = e / B;
+        split_pair(s[e], s[e + 1], se[r], ns, d + e, slice_stride);
       }
+      continue;
     }
-    if (tr) __syncthreads();
+    // op(X) row r = stored column r: stored rows 32 ti.., columns 32 tj.. give
+    // op rows 32 tj.., columns 32 ti.. (coalesced reads through shared memory)
+    for (int ti = 0; ti < B / 32; ++ti)
+      for (int tj = 0; tj < B / 32; ++tj) {
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+          const int r = e >> 5, c = e & 31;
+          tile[r][c] = s[(size_t)(ti * 32 + r) * B + tj * 32 + c];
+        }
+        __syncthreads();
+        for (int e2 = threadIdx.x; e2 < 512; e2 += blockDim.x) {
+          const int r = (2 * e2) >> 5, c = (2 * e2) & 31;  // op sub-block element (r, c), (r, c + 1)
+          const int orow = tj * 32 + r, ocol = ti * 32 + c;
+          split_pair(tile[c][r], tile[c + 1][r], se[orow], ns, d + (size_t)orow * B + ocol, slice_stride);
+        }
+        __syncthreads();
+      }
   }
+}
+
+static void split_blocks(ifac_ctx* ctx, int bs, const double* val, const int32_t* src, int64_t nblk, bool tr,
+                         const int32_t* sblk, const int* sexp, int ns, void* dst) {
+  const int grid = (int)std::min<int64_t>(nblk, 152 * 16);
+  __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(dst);
+  if (bs == 32) k_split<32><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, sblk, sexp, ns, d);
+  else if (bs == 64) k_split<64><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, sblk, sexp, ns, d);
+  else k_split<128><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, sblk, sexp, ns, d);
+  IFAC_CK_LAUNCH();
 }
 
 // x 2^E rounded to nearest (ties to even), built from the integer's bits;
@@ -1221,40 +1273,55 @@ __global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Split products of banded patterns.  Tiles of 128 x 64 (two block rows, one
-// block column), no cluster.  When no tile has more than KW K steps and the
-// accumulation units of that bound number at most 8, every unit keeps its own
-// FP32 accumulator in tensor memory (8 x 64 columns) for the whole tile.  Each
-// K step then loads every slice tile once -- slice k of the two op(A) blocks
-// and of the op(B) block share one ring slot -- and issues, as soon as slot k
-// has landed, the MMAs of the pairs (a, b) with max(a, b) = k; a slot is
-// released after the last pair that reads it.  At the end of the tile the
-// epilogue adds the units' accumulators into 64-bit fixed-point sums in
-// registers and stores them once, in the hand-over layout that k_split_finish
-// converts.
+// Split products on narrow tiles (bs 32, 64, 128).  A tile is 128 x 64
+// accumulator elements: 128 / bs block rows of C by 64 columns (two block
+// columns at bs 32, one at bs 64, half of one at bs 128, whose two halves the
+// same CTA takes one after the other).  Each K block is streamed in chunks of
+// at most 64 K elements; a chunk's slices are loaded once -- slice k of the
+// tile's op(A) rows and op(B) columns share one ring slot -- and, as soon as
+// slot k has landed, the MMAs of the slice pairs (a, b) with max(a, b) = k
+// are issued; a slot is released after the last pair that reads it.  Every
+// accumulation unit keeps its own FP32 accumulator in tensor memory (up to 8
+// units x 64 columns).  A window of K blocks is as long as every weight class
+// fits one unit; after each window the epilogue adds the units, scaled, into
+// 64-bit fixed-point sums held in registers, so a tile may span any number of
+// windows.  After the tile's last window the epilogue writes
+// S_ij 2^(ea + e_i + e_j) * am in FP64 and the block norms.
 // ---------------------------------------------------------------------------
 namespace band {
-constexpr int TMB = 2;                      // block rows per tile
-constexpr int M = TMB * BS;                 // 128 accumulator rows
-constexpr int N = BS;                       // 64 accumulator columns
 constexpr int MAX_U = 8;                    // units live at once: 8 x 64 = 512 columns
-constexpr int SLOT_A = M * 128;             // one BF16 slice of both op(A) blocks (K = 64: one 128-byte atom)
-constexpr int SLOT_B = N * 128;             // one BF16 slice of the op(B) block
-constexpr int SLOT_BYTES = SLOT_A + SLOT_B; // 24 KB, a multiple of 1024 (128-byte swizzle groups)
-constexpr int RING = 9;                     // slots: one K step of up to 8 slices plus prefetch
-constexpr int SMEM_BYTES = RING * SLOT_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t TX_BYTES = (uint32_t)SLOT_BYTES;
+constexpr int RING = 9;                     // slots: one chunk of up to 8 slices plus prefetch
 // FP32 accumulate, A = B = BF16, both K-major, N = 64, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-                           ((uint32_t)(M >> 4) << 24);
+constexpr uint32_t IDESC = idesc_of<2, 64, 128>();
+
+template <int B>
+struct SB {
+  static constexpr int M = 128, N = 64;
+  static constexpr int TMB = M / B;                 // block rows per tile (4, 2, 1)
+  static constexpr int TNB = B <= N ? N / B : 1;    // block columns per tile (2, 1, 1)
+  static constexpr int NSUB = B > N ? B / N : 1;    // column sub-tiles per block column (1, 1, 2)
+  static constexpr int BROWS = B < N ? B : N;       // rows of one op(B) box (32, 64, 64)
+  static constexpr int KC = B < 64 ? B : 64;        // K elements per chunk
+  static constexpr int KCH = B / KC;                // chunks per K block (1, 1, 2)
+  static constexpr int ATOM = KC * 2;               // bytes of one BF16 row chunk: one swizzle atom (64 or 128)
+  static constexpr int SLOT_A = M * ATOM;           // one slice of the tile's op(A) rows
+  static constexpr int SLOT_B = N * ATOM;           // one slice of its op(B) columns
+  static constexpr int SLOT_BYTES = SLOT_A + SLOT_B;  // 12, 24, 24 KB (multiples of 1024)
+  static constexpr int SMEM_BYTES = RING * SLOT_BYTES + 1024;
+  static constexpr int KSTEPS = ATOM / 32;          // MMAs per slice pair and chunk
+  static constexpr uint32_t SBO = 8 * ATOM;
+  static constexpr uint32_t SWZ = ATOM == 128 ? 2 : 4;
+  static constexpr int RECW = TMB + TNB;
+  static_assert(SLOT_BYTES % 1024 == 0, "slots must keep the swizzle alignment");
+};
 }  // namespace band
 
 struct BandArgs {
-  const int32_t* tiles;    // [2t] tile row (pairs of block rows), [2t+1] block column
+  const int32_t* tiles;    // [2t] tile row (of TMB block rows), [2t+1] tile column (of TNB block columns)
   const int* ntiles;       // device: number of tiles
-  const int* tile_nk;      // device: K steps of each tile
-  const int32_t* rec;      // plan: per K step, copy indices of op(A)_{I0,K}, op(A)_{I0+1,K}, op(B)_{K,J}
+  const int* tile_nk;      // device: K blocks of each tile
+  const int32_t* rec;      // plan: per K block, copy indices of the tile's op(A)_IK, then op(B)_KJ
   const int32_t* rec_off;  // first record of each tile
   const int32_t* crp;      // C pattern
   const int32_t* cci;
@@ -1266,7 +1333,8 @@ struct BandArgs {
   double am;               // +-1 (applied to the integer) or the mantissa of alpha
   int nb;
   int ns;                  // slices per operand (1..8)
-  int slice_rows_a;        // tensor-map rows between consecutive slices of op(A): (nnzb_A + 1) * 64
+  int kwin;                // K blocks per window (every weight class exact in one FP32 accumulator)
+  int slice_rows_a;        // tensor-map rows between consecutive slices of op(A): (nnzb_A + 1) bs
   int slice_rows_b;
   int nunits;
   int unit_sh[band::MAX_U];
@@ -1279,17 +1347,13 @@ struct BandArgs {
   int* ovf;
 };
 
-__device__ __forceinline__ void mma_band(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(band::IDESC), "r"(accumulate));
-}
-
+template <int B>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_split_band(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                       BandArgs args) {
   using namespace band;
+  using L = SB<B>;
+  constexpr int N = L::N, TMB = L::TMB, TNB = L::TNB;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[RING], empty_bar[RING];
   __shared__ __align__(8) uint64_t acc_full, acc_empty, drain_bar;
@@ -1333,26 +1397,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int it = 0; it < mt && ok; ++it) {
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
         const int nk = args.tile_nk[t];
-        const int32_t* r = args.rec + (size_t)args.rec_off[t] * 3;
-        for (int j = 0; j < nk && ok; ++j, r += 3) {
-          const int a0 = r[0], a1 = r[1], b0 = r[2];
-          for (int k = 0; k < args.ns; ++k) {
-            if (!mbar_wait(smem_u32(&empty_bar[slot]), phase ^ 1u, &abort_flag, args.err)) {
-              ok = false;
-              break;
-            }
-            const uint32_t fb = smem_u32(&full_bar[slot]);
-            mbar_expect_tx(fb, TX_BYTES);
-            issued_mask |= 1u << slot;
-            last_parity = (last_parity & ~(1u << slot)) | (phase << slot);
-            const uint32_t sa = smem_base + (uint32_t)(slot * SLOT_BYTES);
-            const int ya = k * args.slice_rows_a, yb = k * args.slice_rows_b;
-            tma_load_2d(sa, &mapA, 0, ya + a0 * BS, fb);
-            tma_load_2d(sa + BS * 128, &mapA, 0, ya + a1 * BS, fb);
-            tma_load_2d(sa + SLOT_A, &mapB, 0, yb + b0 * BS, fb);
-            if (++slot == RING) {
-              slot = 0;
-              phase ^= 1u;
+        for (int h = 0; h < L::NSUB && ok; ++h) {
+          const int32_t* r = args.rec + (size_t)args.rec_off[t] * L::RECW;
+          for (int j = 0; j < nk && ok; ++j, r += L::RECW) {
+            for (int c = 0; c < L::KCH && ok; ++c) {
+              for (int k = 0; k < args.ns; ++k) {
+                if (!mbar_wait(smem_u32(&empty_bar[slot]), phase ^ 1u, &abort_flag, args.err)) {
+                  ok = false;
+                  break;
+                }
+                const uint32_t fb = smem_u32(&full_bar[slot]);
+                mbar_expect_tx(fb, (uint32_t)L::SLOT_BYTES);
+                issued_mask |= 1u << slot;
+                last_parity = (last_parity & ~(1u << slot)) | (phase << slot);
+                const uint32_t sa = smem_base + (uint32_t)(slot * L::SLOT_BYTES);
+                const int ya = k * args.slice_rows_a, yb = k * args.slice_rows_b;
+#pragma unroll
+                for (int i = 0; i < TMB; ++i) tma_load_2d(sa + i * B * L::ATOM, &mapA, c * L::KC, ya + r[i] * B, fb);
+#pragma unroll
+                for (int jb = 0; jb < TNB; ++jb)
+                  tma_load_2d(sa + L::SLOT_A + jb * L::BROWS * L::ATOM, &mapB, c * L::KC,
+                              yb + r[TMB + jb] * B + h * N, fb);
+                if (++slot == RING) {
+                  slot = 0;
+                  phase ^= 1u;
+                }
+              }
             }
           }
         }
@@ -1373,46 +1443,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int it = 0; it < mt && ok; ++it) {
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
         const int nk = args.tile_nk[t];
-        // the epilogue has read the previous tile's accumulators
-        if (!mbar_wait(smem_u32(&acc_empty), acc_phase ^ 1u, &abort_flag, args.err)) break;
-        tc_fence_after();
-        uint32_t started = 0;  // units whose accumulator holds this tile's sum
-        for (int j = 0; j < nk && ok; ++j) {
-          const int base = slot;  // position of slice 0 of this K step
-          for (int k = 0; k < args.ns; ++k) {
-            if (!mbar_wait(smem_u32(&full_bar[slot]), phase, &abort_flag, args.err)) {
+        for (int h = 0; h < L::NSUB && ok; ++h) {
+          for (int w0 = 0; w0 < nk && ok; w0 += args.kwin) {
+            const int w1 = min(nk, w0 + args.kwin);
+            // the epilogue has read the previous window's accumulators
+            if (!mbar_wait(smem_u32(&acc_empty), acc_phase ^ 1u, &abort_flag, args.err)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            for (int q = args.slot_beg[k]; q < args.slot_beg[k + 1]; ++q) {
-              int pa = base + args.pair_a[q], pb = base + args.pair_b[q];
-              if (pa >= RING) pa -= RING;
-              if (pb >= RING) pb -= RING;
-              const int u = args.pair_u[q];
-              const uint32_t sa = smem_base + (uint32_t)(pa * SLOT_BYTES);
-              const uint32_t sb = smem_base + (uint32_t)(pb * SLOT_BYTES + SLOT_A);
-              const uint32_t tacc = tmem + (uint32_t)(u * N);
+            uint32_t started = 0;  // units whose accumulator holds this window's sum
+            for (int j = w0; j < w1 && ok; ++j) {
+              for (int c = 0; c < L::KCH && ok; ++c) {
+                const int base = slot;  // position of slice 0 of this chunk
+                for (int k = 0; k < args.ns; ++k) {
+                  if (!mbar_wait(smem_u32(&full_bar[slot]), phase, &abort_flag, args.err)) {
+                    ok = false;
+                    break;
+                  }
+                  tc_fence_after();
+                  for (int q = args.slot_beg[k]; q < args.slot_beg[k + 1]; ++q) {
+                    int pa = base + args.pair_a[q], pb = base + args.pair_b[q];
+                    if (pa >= RING) pa -= RING;
+                    if (pb >= RING) pb -= RING;
+                    const int u = args.pair_u[q];
+                    const uint32_t sa = smem_base + (uint32_t)(pa * L::SLOT_BYTES);
+                    const uint32_t sb = smem_base + (uint32_t)(pb * L::SLOT_BYTES + L::SLOT_A);
+                    const uint32_t tacc = tmem + (uint32_t)(u * N);
 #pragma unroll
-              for (int kk = 0; kk < BS / 16; ++kk)
-                mma_band(tacc, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32),
-                         (((started >> u) & 1u) || kk > 0) ? 1u : 0u);
-              started |= 1u << u;
+                    for (int kk = 0; kk < L::KSTEPS; ++kk)
+                      mma_kstep<2>(tacc, smem_desc_sw(sa + kk * 32, L::SBO, L::SWZ),
+                                   smem_desc_sw(sb + kk * 32, L::SBO, L::SWZ), IDESC,
+                                   (((started >> u) & 1u) || kk > 0) ? 1u : 0u);
+                    started |= 1u << u;
+                  }
+                  for (int e = args.rel_beg[k]; e < args.rel_beg[k + 1]; ++e) {
+                    int pr = base + args.rel[e];
+                    if (pr >= RING) pr -= RING;
+                    mma_commit(smem_u32(&empty_bar[pr]));
+                  }
+                  if (++slot == RING) {
+                    slot = 0;
+                    phase ^= 1u;
+                  }
+                }
+              }
             }
-            for (int e = args.rel_beg[k]; e < args.rel_beg[k + 1]; ++e) {
-              int pr = base + args.rel[e];
-              if (pr >= RING) pr -= RING;
-              mma_commit(smem_u32(&empty_bar[pr]));
-            }
-            if (++slot == RING) {
-              slot = 0;
-              phase ^= 1u;
-            }
+            if (!ok) break;
+            mma_commit(smem_u32(&acc_full));
+            acc_phase ^= 1u;
           }
         }
-        if (!ok) break;
-        mma_commit(smem_u32(&acc_full));
-        acc_phase ^= 1u;
       }
       // every MMA this thread issued completes before tensor memory is released
       mma_commit(smem_u32(&drain_bar));
@@ -1421,76 +1502,95 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     // ------------------------------ epilogue ------------------------------
     const int q = warp & 3;                  // tensor-memory lane quarter
-    const int half = (warp - 2) >> 2;        // column half of the block: columns 32 half .. 32 half + 31
-    const int row = q * 32 + lane;           // accumulator row 0..127
+    const int half = (warp - 2) >> 2;        // columns 32 half .. 32 half + 31 of the tile
+    const int rb = (q * 32) / B;             // block row of the tile (a warp's rows lie in one)
+    const int rin = (q * 32) % B + lane;     // this thread's row within that block
+    const int cb = (half * 32) / B;          // block column of the tile (at bs <= 64)
     const int et = threadIdx.x - 64;
     uint32_t acc_phase = 0;
     const bool unit = (args.am == 1.0 || args.am == -1.0), neg = args.am < 0.0;
-    for (int it = 0; it < mt; ++it) {
+    bool good = true;
+    for (int it = 0; it < mt && good; ++it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      const int I0 = args.tiles[2 * t] * TMB;
-      const int I = I0 + row / BS, J = args.tiles[2 * t + 1];
-      int p = -1;  // position of C_IJ in C (warp-uniform: a warp's rows lie in one block row)
+      const int nk = args.tile_nk[t];
+      const int I0 = args.tiles[2 * t] * TMB, J0 = args.tiles[2 * t + 1] * TNB;
+      const int I = I0 + rb, J = J0 + cb;
+      int p = -1;  // position of C_IJ in C (warp-uniform)
       if (I < args.nb && J < args.nb) {
         const int lo = args.crp[I], hi = args.crp[I + 1];
         const int k = lower_bound_i32(args.cci, lo, hi, J);
         if (k < hi && args.cci[k] == J) p = k;
       }
-      const bool got = mbar_wait(smem_u32(&acc_full), acc_phase, &abort_flag, args.err);
-      acc_phase ^= 1u;
-      if (!epi_all<32 * NEPI>(got)) break;  // all epilogue warps go on, or all stop
-      tc_fence_after();
-      long long s[32];
+      double ss = 0.0;  // this thread's squares over the tile's column sub-tiles
+      for (int h = 0; h < L::NSUB && good; ++h) {
+        const int cin = (h * N + half * 32) % B;  // first column of this warp within block J
+        long long s[32];
 #pragma unroll
-      for (int e = 0; e < 32; ++e) s[e] = 0;
-      bool bad = false;
-#pragma unroll 1
-      for (int u = 0; u < args.nunits; ++u) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * N + half * 32), v);
-        const int sh = args.unit_sh[u];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) s[e] = fixed_add(s[e], __float2int_rn(v[e]), sh, bad);
-      }
-      // the accumulators are read: the next tile's MMAs may overwrite them
-      tc_fence_before();
-      epi_bar();
-      if (et == 0) mbar_arrive(smem_u32(&acc_empty));
-      // every K of the tile is in these sums (one window): the FP64 result,
-      // S_ij 2^(ea + e_i + e_j) * am rounded once, and its squares for the norm
-      double ss = 0.0;
-      if (p >= 0) {
-        const int r = (q & 1) * 32 + lane;  // row within the block
-        const int er = args.ea + args.sige[(size_t)I * BS + r];
-        const int* tj = args.taue + (size_t)J * BS + half * 32;
-        double* dst = args.cval + (size_t)p * BS * BS + (size_t)r * BS + half * 32;
-#pragma unroll
-        for (int e = 0; e < 32; e += 2) {
-          const long long x0 = (unit && neg) ? -s[e] : s[e], x1 = (unit && neg) ? -s[e + 1] : s[e + 1];
-          double v0 = i64_ldexp(x0, er + tj[e]), v1 = i64_ldexp(x1, er + tj[e + 1]);
-          if (!unit) {
-            v0 *= args.am;
-            v1 *= args.am;
+        for (int e = 0; e < 32; ++e) s[e] = 0;
+        bool bad = false;
+        for (int w0 = 0; w0 < nk; w0 += args.kwin) {
+          const bool got = mbar_wait(smem_u32(&acc_full), acc_phase, &abort_flag, args.err);
+          acc_phase ^= 1u;
+          if (!epi_all<32 * NEPI>(got)) {  // all epilogue warps go on, or all stop
+            good = false;
+            break;
           }
-          ss = fma(v0, v0, ss);
-          ss = fma(v1, v1, ss);
-          *reinterpret_cast<double2*>(dst + e) = make_double2(v0, v1);
+          tc_fence_after();
+#pragma unroll 1
+          for (int u = 0; u < args.nunits; ++u) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * N + half * 32), v);
+            const int sh = args.unit_sh[u];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) s[e] = fixed_add(s[e], __float2int_rn(v[e]), sh, bad);
+          }
+          // the accumulators are read: the next window's MMAs may overwrite them
+          tc_fence_before();
+          epi_bar();
+          if (et == 0) mbar_arrive(smem_u32(&acc_empty));
         }
-        if (bad) *args.ovf = 2;
+        if (!good) break;
+        // every K of the tile is in these sums: the FP64 result,
+        // S_ij 2^(ea + e_i + e_j) * am rounded once, and its squares for the norm
+        if (p >= 0) {
+          const int er = args.ea + args.sige[(size_t)I * B + rin];
+          const int* tj = args.taue + (size_t)J * B + cin;
+          double* dst = args.cval + (size_t)p * B * B + (size_t)rin * B + cin;
+#pragma unroll
+          for (int e = 0; e < 32; e += 2) {
+            const long long x0 = (unit && neg) ? -s[e] : s[e], x1 = (unit && neg) ? -s[e + 1] : s[e + 1];
+            double v0 = i64_ldexp(x0, er + tj[e]), v1 = i64_ldexp(x1, er + tj[e + 1]);
+            if (!unit) {
+              v0 *= args.am;
+              v1 *= args.am;
+            }
+            ss = fma(v0, v0, ss);
+            ss = fma(v1, v1, ss);
+            *reinterpret_cast<double2*>(dst + e) = make_double2(v0, v1);
+          }
+          if (bad) *args.ovf = 2;
+        }
       }
+      if (!good) break;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == 0) partial[q][half] = ss;
       epi_bar();
-      // norms: block row b of the tile is covered by lane quarters 2b, 2b + 1
-      if (et < TMB) {
-        const int Ib = I0 + et;
-        if (Ib < args.nb && J < args.nb) {
+      // norms: block (br, bc) of the tile sums the warps of its lane quarters
+      // and column halves, in a fixed order
+      if (et < TMB * TNB) {
+        const int br = et / TNB, bc = et % TNB;
+        const int Ib = I0 + br, Jb = J0 + bc;
+        if (Ib < args.nb && Jb < args.nb) {
           const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
-          const int k = lower_bound_i32(args.cci, lo, hi, J);
-          if (k < hi && args.cci[k] == J)
-            args.cnorm[k] = sqrt((partial[2 * et][0] + partial[2 * et][1]) +
-                                 (partial[2 * et + 1][0] + partial[2 * et + 1][1]));
+          const int k = lower_bound_i32(args.cci, lo, hi, Jb);
+          if (k < hi && args.cci[k] == Jb) {
+            double sum = 0.0;
+            for (int qq = 0; qq < 4; ++qq)
+              for (int hh = 0; hh < 2; ++hh)
+                if ((qq * 32) / B == br && (hh * 32) / B == bc) sum += partial[qq][hh];
+            args.cnorm[k] = sqrt(sum);
+          }
         }
       }
       epi_bar();
@@ -1517,10 +1617,10 @@ struct UnitTable {
   int si[MAX_PAIRS] = {}, ti[MAX_PAIRS] = {}, pu[MAX_PAIRS] = {};  // slices (1-based) and unit of each pair
 };
 
-static UnitTable unit_table(int ns, int kw) {
+static UnitTable unit_table(int ns, int kw, int bs) {
   UnitTable t;
   const auto qmax = [](int s) { return s == 1 ? 128 : 64; };
-  const int64_t cap = ((int64_t)1 << 24) / (64 * std::max(1, std::min(KW, kw)));
+  const int64_t cap = ((int64_t)1 << 24) / ((int64_t)bs * std::max(1, kw));
   for (int g = 2; g <= ns + 1; ++g) {
     int64_t used = 0;
     bool open = false;
@@ -1550,12 +1650,24 @@ static UnitTable unit_table(int ns, int kw) {
   return t;
 }
 
+template <int B>
+static void launch_split_band(ifac_ctx* ctx, const CUtensorMap& mA, const CUtensorMap& mB, const BandArgs& ba,
+                              int tiles_bound, int sms) {
+  using L = band::SB<B>;
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr, ctx->device))
+    IFAC_CK(cudaFuncSetAttribute(k_gemm_split_band<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES));
+  const int grid = (int)std::min<int64_t>(std::max(tiles_bound, 1), sms);
+  k_gemm_split_band<B><<<grid, NTHREADS, L::SMEM_BYTES, ctx->stream>>>(mA, mB, ba);
+  IFAC_CK_LAUNCH();
+}
+
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                       unsigned long long* pairs, OperandCache* ac, OperandCache* bc) {
   using Cf = Cfg<2>;
-  const int nb = A.nb;
-  const int64_t rows = (int64_t)nb * BS;
+  const int nb = A.nb, bs = A.bs;
+  const int64_t rows = (int64_t)nb * bs;
   if (ns < 1 || ns > 8) fail(IFAC_ERR_UNSUPPORTED, "split product: 1 to 8 slices");
   // a cache filled by an earlier product's op(B) (transposed blocks in the
   // stored order, with that operand's column scales) serves op(A) = that
@@ -1571,14 +1683,14 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   IFAC_CK(cudaMemsetAsync(l1.p, 0, 2 * sizeof(unsigned int), ctx->stream));
   if (!hit) {
     sige = Buf<int>(ctx, rows);
-    row_scales(ctx, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p);
+    row_scales(ctx, bs, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p);
   }
   {
     View bt = view_rows(ctx, B, !tB);
-    row_scales(ctx, bt.rp, bt.src, nb, !tB, B.val, taue.p, l1.p + 1);
+    row_scales(ctx, bs, bt.rp, bt.src, nb, !tB, B.val, taue.p, l1.p + 1);
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
-  const size_t bbytes = (size_t)BS * BS * 2;
+  const size_t bbytes = (size_t)bs * bs * 2;
   Buf<uint8_t> la, lb(ctx, (size_t)ns * (B.nnzb + 1) * bbytes);
   for (int k = 0; k < ns; ++k)
     IFAC_CK(cudaMemsetAsync(lb.p + ((size_t)k * (B.nnzb + 1) + B.nnzb) * bbytes, 0, bbytes, ctx->stream));
@@ -1589,31 +1701,25 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     if (A.nnzb) {
       Buf<int32_t> arow(ctx, A.nnzb);
       expand_rows(ctx, arows.rp, nb, arow.p);
-      k_split<<<(int)std::min<int64_t>(A.nnzb, 152 * 16), 256, tA ? SPLIT_TILE_BYTES : 0, ctx->stream>>>(
-          A.val, arows.src, A.nnzb, tA ? 1 : 0, arow.p, sige.p, nsa, reinterpret_cast<__nv_bfloat16*>(la.p));
-      IFAC_CK_LAUNCH();
+      split_blocks(ctx, bs, A.val, arows.src, A.nnzb, tA, arow.p, sige.p, nsa, la.p);
     }
   }
   uint8_t* const la_p = hit ? ac->split.p : la.p;
   const int* const sige_p = hit ? ac->sexp.p : sige.p;
   const int* const taue_p = taue.p;
-  if (B.nnzb) {
-    k_split<<<(int)std::min<int64_t>(B.nnzb, 152 * 16), 256, tB ? 0 : SPLIT_TILE_BYTES, ctx->stream>>>(
-        B.val, brows.src, B.nnzb, tB ? 0 : 1, brows.ci, taue.p, ns, reinterpret_cast<__nv_bfloat16*>(lb.p));
-    IFAC_CK_LAUNCH();
-  }
-  // one tensor map over all slices of each operand (slice s at row s (nnzb + 1) BS)
-  if ((int64_t)ns * (std::max(A.nnzb, B.nnzb) + 1) * BS > (int64_t)0x7fffffff)
+  if (B.nnzb) split_blocks(ctx, bs, B.val, brows.src, B.nnzb, !tB, brows.ci, taue.p, ns, lb.p);
+  // one tensor map over all slices of each operand (slice s at row s (nnzb + 1) bs)
+  if ((int64_t)ns * (std::max(A.nnzb, B.nnzb) + 1) * bs > (int64_t)0x7fffffff)
     fail(IFAC_ERR_TOO_LARGE, "split product: slice copies exceed the 2^31-row tensor-map range");
-  const CUtensorMap mA = make_map<2>(la_p, (int64_t)ns * (A.nnzb + 1));
-  const CUtensorMap mB = make_map<2>(lb.p, (int64_t)ns * (B.nnzb + 1));
-  // tile plans: 128 x 64 tiles first; banded products (no tile with more
-  // than KW K steps, at most band::MAX_U units at that bound) run on the
-  // banded kernel, every other product on the super-tile plan
+  // tile plans: narrow tiles (128 x 64) first.  At bs 64 a product whose
+  // tiles all fit one window with at most band::MAX_U units runs on the
+  // narrow kernel, every other one on the windowed super-tile kernel; at bs
+  // 32 and 128 every product runs on the narrow kernel, window by window.
   float l1h[2] = {0.f, 0.f};  // scaled 1-norm bounds of op(A) rows and op(B) columns (FP32 bits)
   const HostRead l1read{l1h, l1.p, sizeof(l1h)};
-  Plan Pb = make_plan<band::TMB, 1>(ctx, arows, A, tA, brows, B, C, crow, true, KW, amap, &l1read);
-  const bool banded = Pb.kmax >= 1 && Pb.kmax <= KW && unit_table(ns, Pb.kmax).nunits <= band::MAX_U;
+  Plan Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? KW : 0, amap, &l1read);
+  const bool banded = bs != 64 || (Pb.kmax >= 1 && Pb.kmax <= KW &&
+                                   unit_table(ns, Pb.kmax, bs).nunits <= band::MAX_U);
   Plan P;
   if (!banded) P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true, 0, amap);
   // block pairs, and block pairs times the ns (ns + 1) / 2 slice pairs
@@ -1630,6 +1736,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     ac->sexp = std::move(sige);
     ac->split_ns = nsa;
   }
+  uint8_t* const lb_p = lb.p;
   if (bc && !tB) {  // op(B) = B in its stored order: keep its slices for a later op(A) = B^T
     bc->reset();
     bc->split = std::move(lb);
@@ -1638,8 +1745,13 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     bc->split_ns = ns;
     bc->from_b = true;
   }
+  // window of the narrow kernel: the K blocks (at most 1024 K elements) for
+  // which every unit stays exact, as long as at most band::MAX_U units
+  // result; the longest tile's K blocks when fewer
+  int kwin = std::min(1024 / bs, std::max(kmax, 1));
+  while (kwin > 1 && unit_table(ns, kwin, bs).nunits > band::MAX_U) --kwin;
   // the windowed kernel adds into zeroed 64-bit sums that a second kernel
-  // converts; the banded kernel holds each tile's complete sums and writes FP64
+  // converts; the narrow kernel holds each tile's complete sums and writes FP64
   Buf<longlong2> part;
   if (!banded) {
     part = Buf<longlong2>(ctx, (size_t)C.nnzb * (BS * BS / 2));
@@ -1656,16 +1768,15 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   // longest tile.  f <= 56 keeps every weight 2^(f - 7g) of the 7-slice
   // product integral.  An overflow would still be detected and reported.
   int lgK = 0;
-  while (((int64_t)1 << lgK) < (int64_t)std::max(kmax, 1) * BS) ++lgK;
+  while (((int64_t)1 << lgK) < (int64_t)std::max(kmax, 1) * bs) ++lgK;
   const double l1b = std::min((double)l1h[0], (double)l1h[1]) * 1.125 + 2.0;
   int lgB = 0;
   while (std::ldexp(1.0, lgB) < l1b && lgB < 62) ++lgB;
   const int fbits = std::min(56, 62 - std::min(lgK, lgB));
-  // units: kw = the K blocks a window can hold, KW or the longest tile's K
-  // steps when that is fewer (every window of every tile then has at most kw
-  // blocks, so each FP32 accumulator still sums integers of magnitude
-  // <= 2^24 exactly)
-  const UnitTable ut = unit_table(ns, std::min(KW, std::max(kmax, 1)));
+  // units: a window of kw K blocks (every window of every tile has at most kw
+  // blocks, so each FP32 accumulator sums integers of magnitude <= 2^24
+  // exactly)
+  const UnitTable ut = banded ? unit_table(ns, kwin, bs) : unit_table(ns, std::min(KW, std::max(kmax, 1)), bs);
   prof_begin(ctx, 2);
   if (banded) {
     BandArgs ba{};
@@ -1684,9 +1795,11 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     ba.am = am;
     ba.nb = nb;
     ba.ns = ns;
-    ba.slice_rows_a = (int)(A.nnzb + 1) * BS;
-    ba.slice_rows_b = (int)(B.nnzb + 1) * BS;
+    ba.kwin = kwin;
+    ba.slice_rows_a = (int)(A.nnzb + 1) * bs;
+    ba.slice_rows_b = (int)(B.nnzb + 1) * bs;
     ba.nunits = ut.nunits;
+    if (ut.nunits > band::MAX_U) fail(IFAC_ERR_UNSUPPORTED, "split product: too many units for the narrow kernel");
     for (int u = 0; u < ut.nunits; ++u) ba.unit_sh[u] = fbits - SPLIT_BITS * ut.unit_g[u];
     // issue order: by slot max(a, b); slice r is released after the last
     // slot whose pairs read it, max(r, ns - 1 - r)
@@ -1711,14 +1824,15 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     if (q != ut.npairs || e != ns) fail(IFAC_ERR_CUDA, "split product: inconsistent banded issue table");
     ba.err = ctx->dev_err;
     ba.ovf = ctx->dev_err;
-    static std::atomic<unsigned long long> attr_b{0};
-    if (first_on_device(attr_b, ctx->device))
-      IFAC_CK(cudaFuncSetAttribute(k_gemm_split_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   band::SMEM_BYTES));
-    const int grid = (int)std::min<int64_t>(std::max(Pb.ntiles, 1), sms);
-    k_gemm_split_band<<<grid, NTHREADS, band::SMEM_BYTES, ctx->stream>>>(mA, mB, ba);
-    IFAC_CK_LAUNCH();
+    const int kc = bs < 64 ? bs : 64;  // K elements per chunk
+    const CUtensorMap mA = make_map_box(bs, la_p, (int64_t)ns * (A.nnzb + 1), kc, bs);
+    const CUtensorMap mB = make_map_box(bs, lb_p, (int64_t)ns * (B.nnzb + 1), kc, bs < 64 ? bs : 64);
+    if (bs == 32) launch_split_band<32>(ctx, mA, mB, ba, Pb.ntiles, sms);
+    else if (bs == 64) launch_split_band<64>(ctx, mA, mB, ba, Pb.ntiles, sms);
+    else launch_split_band<128>(ctx, mA, mB, ba, Pb.ntiles, sms);
   } else {
+    const CUtensorMap mA = make_map<2>(la_p, (int64_t)ns * (A.nnzb + 1));
+    const CUtensorMap mB = make_map<2>(lb_p, (int64_t)ns * (B.nnzb + 1));
     static std::atomic<unsigned long long> attr{0};
     if (first_on_device(attr, ctx->device))
       IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));
@@ -1811,8 +1925,7 @@ void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const 
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache, OperandCache* bcache) {
   if (C.nnzb == 0) return;
-  if (A.bs != tc::BS && !((A.bs == 32 || A.bs == 128) && (prec == IFAC_TF32 || prec == IFAC_BF16)))
-    fail(IFAC_ERR_UNSUPPORTED, "tensor-core block products: TF32/BF16 at bs 32, 64, 128; split at bs 64");
+  if (A.bs != 32 && A.bs != 64 && A.bs != 128) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block products: bs 32, 64 or 128");
   if (prec == IFAC_BF16)
     tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache);
   else if (prec == IFAC_TF32)

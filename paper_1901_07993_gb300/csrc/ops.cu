@@ -16,7 +16,8 @@ namespace ifac {
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
          int prec, bool upper, OperandCache* acache, OperandCache* bcache) {
   const int nb = A.nb;
-  if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && A.bs == 64) prec = IFAC_FP64_SPLIT;
+  if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && (A.bs == 32 || A.bs == 64 || A.bs == 128))
+    prec = IFAC_FP64_SPLIT;
   View arows = view_rows(ctx, A, tA);
   Pattern P = product_pattern(ctx, arows, B, tB, nb, upper);
   Mat C(ctx);

@@ -78,6 +78,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
+// the same for another swizzle: sbo = the 8-row group stride (8 x the atom
+// row), swz = descriptor layout type (2: 128-byte swizzle, 4: 64-byte)
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, uint32_t sbo, uint32_t swz) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(sbo >> 4) << 32;          // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                   // version
+  d |= (uint64_t)swz << 61;                 // swizzle mode
+  return d;
+}
+
 // Instruction descriptor: FP32 accumulate, A/B format (ELT bytes: 2 BF16,
 // 4 TF32), both K-major, N x M.
 template <int ELT, int N, int M>

@@ -65,9 +65,27 @@ def test_mixed_refine_bs32(ctx, prec):
     from paper_1901_07993_gb300 import ifac
     S = synth.chain_overlap(4096, 32, seed=0)
     tau, target = 1e-13, 1e-10
-    Z, rep = ifac.inv_factor_refine(ctx, ifac.upload(ctx, S), tau, target, ifac.opts(prec=prec, max_iter=80))
+    Z, rep = ifac.inv_factor_refine(ctx, ifac.upload(ctx, S), tau, target,
+                                    ifac.opts(prec=prec, max_iter=80, delta_prec=0))
     a = Z.download()
     resid = oracle.resid(S, oracle.Mat(a.n, 32, a.row_ptr, a.col_idx, a.val))
     print(f"bs 32 prec={prec}: resid {resid:.2e}, low sweeps {rep.low_sweeps}, FP64 delta evals {rep.fp64_delta_evals}")
     assert rep.low_sweeps >= 2 and rep.fp64_delta_evals >= 1 and rep.tc_launches > 0
+    assert resid <= 10 * target
+
+
+@pytest.mark.parametrize("bs", [32, 128])
+def test_mixed_refine_split_delta_block_sizes(ctx, bs):
+    """The mixed schedule with split FP64-accurate delta at bs 32 and 128
+    (TF32 sweeps on the narrow-tile kernel, delta on the narrow split kernel):
+    the oracle's FP64 residual of the returned factor reaches the target."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(4096, bs, seed=0)
+    tau, target = 1e-13, 1e-10
+    Z, rep = ifac.inv_factor_refine(ctx, ifac.upload(ctx, S), tau, target,
+                                    ifac.opts(prec=1, max_iter=80, delta_prec=3))
+    a = Z.download()
+    resid = oracle.resid(S, oracle.Mat(a.n, bs, a.row_ptr, a.col_idx, a.val))
+    print(f"bs {bs}: resid {resid:.2e}, low sweeps {rep.low_sweeps}, split delta evals {rep.fp64_delta_evals}")
+    assert rep.split_launches > 0 and rep.tc_launches > 0
     assert resid <= 10 * target

@@ -232,3 +232,43 @@ def test_split_delta_phase_of_mixed_schedule(ctx, n):
         res[dp] = ifac.inv_factor_resid(ctx, dS, Z)
         assert res[dp] <= 1e-10
     print(f"n {n}: resid fp64-pipe delta {res[0]:.3e}, split delta {res[FP64_SPLIT]:.3e}")
+
+
+@pytest.mark.parametrize("bs", [32, 128])
+@pytest.mark.parametrize("tA,tB", [(False, False), (True, False), (False, True), (True, True)])
+def test_split_block_sizes_32_and_128(ctx, bs, tA, tB):
+    """The narrow split kernel at bs 32 (tiles of 4 x 2 blocks, 64-byte rows)
+    and bs 128 (one block row by half a block column, the two halves in one
+    CTA, K in two chunks): ragged n, empty rows, alpha not a power of two."""
+    nb = 11 if bs == 32 else 5
+    A = synth.random_bsr(nb, bs, 0.4, seed=71 + bs, empty_rows=1, n=nb * bs - 7)
+    B = synth.random_bsr(nb, bs, 0.4, seed=72 + bs, empty_rows=2, n=nb * bs - 7)
+    _, rel = _check(ctx, A, B, tA, tB, alpha=-1.25)
+    assert rel < 1e-13
+
+
+@pytest.mark.parametrize("bs,nb", [(32, 40), (128, 12)])
+def test_split_many_windows_block_sizes(ctx, bs, nb):
+    """Dense products whose tiles span several exact windows (at most 1024 K
+    elements and 8 accumulation units per window: 14 blocks of 32, 3 of 128):
+    the epilogue carries the 64-bit sums from window to window."""
+    A = synth.random_bsr(nb, bs, 1.0, seed=73)
+    B = synth.random_bsr(nb, bs, 1.0, seed=74)
+    _, rel = _check(ctx, A, B, False, True)
+    assert rel < 1e-13
+
+
+@pytest.mark.parametrize("bs", [32, 128])
+def test_split_refine_block_sizes_match_oracle(ctx, bs):
+    """IRSI with every product on the split kernel (prec = IFAC_FP64_SPLIT)
+    at bs 32 and 128: the FP64 oracle's factor within 1e-10, same sweeps."""
+    from paper_1901_07993_gb300 import ifac
+    S = synth.chain_overlap(2048, bs, seed=3)
+    tau, target = 1e-12, 1e-10
+    Z_ref, rep_ref = oracle.irsi(S, tau=tau, target=target)
+    Z, rep = ifac.inv_factor_refine(ctx, ifac.upload(ctx, S), tau, target, ifac.opts(prec=FP64_SPLIT))
+    assert rep.sweeps == rep_ref.sweeps and rep.split_launches > 0
+    a = Z.download()
+    za = oracle.Mat(a.n, bs, a.row_ptr, a.col_idx, a.val).to_dense()
+    zr = Z_ref.to_dense()
+    assert np.linalg.norm(za - zr) / np.linalg.norm(zr) <= 1e-10
