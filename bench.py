@@ -70,6 +70,16 @@ WORKLOADS = {
     "batch64-tf32-n512-8192": dict(geom="batch", n=0, bs=64, tau=1e-12, target=1e-10, method="batched", m=2,
                                    seed=3, leaf=512, prec="tf32", compare=(), sample_n=None,
                                    count=64, nmin=512, nmax=8192, split_slices=8),
+    # config 4 over [2048, 16384] (the upper half of [16384, 32768] does not
+    # fit the device with FP64 intermediates of the dense 3D members), block
+    # size and bs-64 tile schedule picked by the library's autotuner from
+    # timed probes of the generated members (generated at bs 64, re-blocked);
+    # tau = 1e-14: the 3D members hold up to 60,000 blocks, and delta
+    # evaluated from products truncated at 1e-12 misses about
+    # sqrt(blocks) x 1e-12 > 1e-10 of the true residual
+    "batch64-tf32-n2048-16384": dict(geom="batch", n=0, bs=64, tau=1e-14, target=1e-10, method="batched", m=2,
+                                     seed=3, leaf=512, prec="tf32", compare=(), sample_n=None,
+                                     count=64, nmin=2048, nmax=16384, split_slices=8, autotune=True),
     # the adjoint: L = tr(Z_6^T F Z_6) after 6 frozen-pattern sweeps on the
     # 16,384-row chain (bs 32), F = N(0,1) * S_ij symmetric (seed 5); one step =
     # recording run + reverse pass (dL/dS), FP64
@@ -529,6 +539,15 @@ def run_batched(args, w, world, rank, local, ctx, ifac):
     dS = [ifac.upload(ctx, S) for S in members]
     ctx.set_split_slices(w.get("split_slices", 7))
     o = ifac.opts(m=w["m"], prec=PREC[w["prec"]], profile=True, max_iter=100)
+    tune = None
+    if w.get("autotune"):
+        # block size and tile schedule from the library's timed probes (not
+        # part of the timed steps); the members are re-blocked on the device
+        t0 = time.perf_counter()
+        tune = ifac.autotune_batched(ctx, dS, w["tau"], o)
+        if tune["bs"] != w["bs"]:
+            dS = [ifac.bsr_reblock(ctx, S, tune["bs"]) for S in dS]
+        tune["seconds"] = time.perf_counter() - t0
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         Zs, reps, rc = ifac.inv_factor_refine_batched(ctx, dS, w["tau"], w["target"], o)
@@ -558,7 +577,8 @@ def run_batched(args, w, world, rank, local, ctx, ifac):
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[w["prec"]], "data": "synthetic",
             "config": {**config_of(w, args.workload, world), "count": w["count"],
                        "split_slices": w.get("split_slices", 7),
-                       "sizes": [int(S.n) for S in members]},
+                       "sizes": [int(S.n) for S in members],
+                       "bs_run": tune["bs"] if tune else w["bs"], "autotune": tune},
             "members": [{"n": int(S.n), "kind": "chain" if j % 2 == 0 else "cluster", "sweeps": r.sweeps,
                          "low_sweeps": r.low_sweeps, "fp64_delta_evals": r.fp64_delta_evals,
                          "resid_fro_fp64": r.resid_fro, "stop": r.stop_reason}

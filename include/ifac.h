@@ -90,6 +90,18 @@ typedef struct {
 
 typedef struct ifac_ctx ifac_ctx;
 
+/* Result of ifac_autotune_batched. */
+typedef struct {
+  int32_t bs;            /* chosen block size: 32, 64 or 128 */
+  int32_t narrow_kmax;   /* chosen tile schedule of bs-64 products (ifac_set_schedule) */
+  double probe_ms[3];    /* predicted product time of a batch refinement at bs 32, 64,
+                            128 (best schedule), from the timed probes */
+  double probe64_ms[3];  /* at bs 64 per schedule: default, super-tiles only,
+                            narrow tiles only */
+  int32_t low_sweeps_est;  /* sweeps and FP64-accurate delta evaluations the */
+  int32_t split_evals_est; /* prediction assumes */
+} ifac_tune_result;
+
 /* Options of the factorization drivers.  ifac_opts_default fills:
  * m = 2, max_iter = 50, fixed_iters = 0, c_rule = 0, leaf_size = 512,
  * prec = IFAC_FP64, profile = 0, delta_prec = IFAC_FP64_SPLIT, rinch_rows = 0,
@@ -298,6 +310,44 @@ int leaf_invchol_batched(ifac_ctx* ctx, int count, int nl, const double* S, doub
  * Returns IFAC_OK, IFAC_ERR_INVALID (bad arguments), IFAC_ERR_TOO_LARGE or
  * IFAC_ERR_CUDA (a launch or copy failed). */
 int leaf_invchol_batched_noalloc(void* stream, int count, int nl, const double* S, double* Z, int* info);
+
+/* The same matrix stored with block size bs (32, 64 or 128): exact.  Block
+ * (I', J') of the result holds rows [I' bs, (I'+1) bs) and columns
+ * [J' bs, (J'+1) bs) of the padded input, gathered from every stored input
+ * block that overlaps it; result blocks that come out all zero are dropped,
+ * except diagonal blocks; padding rows that the new block size adds past the
+ * input's padded size get a unit diagonal.  No truncation.  The paper stores
+ * its matrices with one block size throughout; this serves the block-size
+ * choice of ifac_autotune_batched.  IFAC_ERR_UNSUPPORTED for another bs. */
+int bsr_reblock(ifac_ctx* ctx, const ifac_bsr* A, int32_t bs, ifac_bsr* out);
+
+/* Tile schedule of the context's bs-64 tensor-core products (TF32, BF16 and
+ * split): -1 (default) narrow 128 x 64 tiles for products whose longest tile
+ * has at most 16 K blocks (split: and fits one exact window), super-tiles for
+ * the others; 0 super-tiles for every product; k > 0 narrow tiles for every
+ * product whose longest tile has at most k K blocks.  Results are the same
+ * products either way (TF32/BF16 up to FP32 summation order; split products
+ * within their error bound).  Products at bs 32 and 128 always use narrow
+ * tiles.  IFAC_ERR_INVALID below -1. */
+int ifac_set_schedule(ifac_ctx* ctx, int32_t narrow_kmax);
+
+/* Autotuner of the batched refinement (config 4's block size and tile
+ * schedule): for each block size 32, 64 and 128 the members are re-blocked
+ * (bsr_reblock) and placed on the diagonal of one matrix, truncated at tau,
+ * and a probe is timed with CUDA events on the context's stream -- two
+ * low-precision products (X = S S and X X, in opts->prec, TF32 unless that
+ * is BF16; X has about the pattern of the later iterates) and one split
+ * FP64-accurate product X X, best of two runs;
+ * at bs 64 each tile schedule of ifac_set_schedule (-1, 0, and narrow for
+ * all) is probed.  The predicted batch time weighs the probes by a typical
+ * sweep count (4 products in each of 6 low-precision sweeps, 2 in each of 4
+ * FP64-accurate delta evaluations); the fastest block size and schedule are
+ * returned in out, and the schedule is set on the context.  The caller
+ * re-blocks its members to out->bs (bsr_reblock) before
+ * inv_factor_refine_batched.  Synchronises the stream; allocates the probe's
+ * matrices through the context's allocator and frees them. */
+int ifac_autotune_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, const ifac_opts* opts,
+                          ifac_tune_result* out);
 
 /* ---------------------------------------------------------------- */
 /* Factorizations                                                    */

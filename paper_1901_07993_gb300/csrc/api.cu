@@ -541,6 +541,44 @@ int inv_factor_resid(ifac_ctx* ctx, const ifac_bsr* S, const ifac_bsr* Z, double
   });
 }
 
+int bsr_reblock(ifac_ctx* ctx, const ifac_bsr* A, int32_t bs, ifac_bsr* out) {
+  if (out) *out = ifac_bsr{};
+  return guarded(ctx, [&]() -> int {
+    validate(A, "A");
+    if (!out) fail(IFAC_ERR_INVALID, "out is NULL");
+    if (bs != 32 && bs != 64 && bs != 128) fail(IFAC_ERR_UNSUPPORTED, "reblock: bs 32, 64 or 128");
+    if (A->bs % 32 != 0) fail(IFAC_ERR_UNSUPPORTED, "reblock: input bs must be a multiple of 32");
+    Mat R = reblock(ctx, *A, bs);
+    IFAC_CK(cudaStreamSynchronize(ctx->stream));
+    *out = R.release();
+    return IFAC_OK;
+  });
+}
+
+int ifac_set_schedule(ifac_ctx* ctx, int32_t narrow_kmax) {
+  if (!ctx) return IFAC_ERR_INVALID;
+  if (narrow_kmax < -1) return IFAC_ERR_INVALID;
+  ctx->narrow_kmax = narrow_kmax;
+  return IFAC_OK;
+}
+
+int ifac_autotune_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, const ifac_opts* opts,
+                          ifac_tune_result* out) {
+  return guarded(ctx, [&]() -> int {
+    if (count <= 0 || !S || !out) fail(IFAC_ERR_INVALID, "autotune: empty batch or NULL arrays");
+    check_opts(opts, true);
+    for (int k = 0; k < count; ++k) {
+      validate(S[k], "S[k]");
+      if (S[k]->bs != S[0]->bs) fail(IFAC_ERR_INVALID, "autotune: members differ in block size");
+      if (S[k]->bs % 32 != 0) fail(IFAC_ERR_UNSUPPORTED, "autotune: block size must be a multiple of 32");
+    }
+    if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
+    autotune(ctx, count, S, tau, *opts, out);
+    ctx->narrow_kmax = out->narrow_kmax;
+    return IFAC_OK;
+  });
+}
+
 int ifac_selftest_wait_timeout(ifac_ctx* ctx, int64_t wait_limit) {
   return guarded(ctx, [&]() -> int {
     if (wait_limit < 1 || wait_limit > ((int64_t)1 << 30)) fail(IFAC_ERR_INVALID, "wait_limit must be in 1..2^30");

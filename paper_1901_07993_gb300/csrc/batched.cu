@@ -76,6 +76,37 @@ __global__ void k_seg_identity(const int32_t* __restrict__ seg, const double* __
 Mat filter_rows_active(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* seg, const uint8_t* active);
 void node_fro(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* nb0, const int32_t* nb1, int nn, double* out_dev);
 
+// the members on the diagonal of one matrix (block rows in member order)
+Mat block_diag(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv) {
+  const int bs = Sv[0]->bs;
+  std::vector<int32_t> boff(count + 1, 0);
+  std::vector<int64_t> poff(count + 1, 0);
+  for (int k = 0; k < count; ++k) {
+    boff[k + 1] = boff[k] + Sv[k]->nb;
+    poff[k + 1] = poff[k] + Sv[k]->nnzb;
+  }
+  const int nb = boff[count];
+  if (poff[count] > 0x7fffffffLL) fail(IFAC_ERR_UNSUPPORTED, "batch holds more than 2^31-1 blocks");
+  Mat Sbd = mat_alloc(ctx, (int64_t)nb * bs, bs, nb, poff[count]);
+  for (int k = 0; k < count; ++k) {
+    const ifac_bsr& A = *Sv[k];
+    k_concat_rows<<<cdiv(A.nb, 256), 256, 0, ctx->stream>>>(A.row_ptr, A.nb, boff[k], (int32_t)poff[k],
+                                                            Sbd.m.row_ptr);
+    IFAC_CK_LAUNCH();
+    if (A.nnzb) {
+      k_offset_cols<<<cdiv(A.nnzb, 256), 256, 0, ctx->stream>>>(A.col_idx, A.nnzb, boff[k],
+                                                                 Sbd.m.col_idx + poff[k]);
+      IFAC_CK_LAUNCH();
+      IFAC_CK(cudaMemcpyAsync(Sbd.m.val + (size_t)poff[k] * bs * bs, A.val, sizeof(double) * (size_t)A.nnzb * bs * bs,
+                              cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+  }
+  k_set_last<<<1, 32, 0, ctx->stream>>>(Sbd.m.row_ptr, nb, (int32_t)poff[count]);
+  IFAC_CK_LAUNCH();
+  if (poff[count]) block_norms(ctx, Sbd.m, Sbd.m.norms);
+  return Sbd;
+}
+
 int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double tau, double target,
                    const ifac_opts& o, ifac_bsr* Zout, ifac_report* reps) {
   const int bs = Sv[0]->bs;
@@ -97,23 +128,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   ctx->profile = o.profile != 0;
   reset_device_counters(ctx);
   // block-diagonal S
-  Mat Sbd = mat_alloc(ctx, (int64_t)nb * bs, bs, nb, poff[count]);
-  for (int k = 0; k < count; ++k) {
-    const ifac_bsr& A = *Sv[k];
-    k_concat_rows<<<cdiv(A.nb, 256), 256, 0, ctx->stream>>>(A.row_ptr, A.nb, boff[k], (int32_t)poff[k],
-                                                            Sbd.m.row_ptr);
-    IFAC_CK_LAUNCH();
-    if (A.nnzb) {
-      k_offset_cols<<<cdiv(A.nnzb, 256), 256, 0, ctx->stream>>>(A.col_idx, A.nnzb, boff[k],
-                                                                 Sbd.m.col_idx + poff[k]);
-      IFAC_CK_LAUNCH();
-      IFAC_CK(cudaMemcpyAsync(Sbd.m.val + (size_t)poff[k] * bs * bs, A.val, sizeof(double) * (size_t)A.nnzb * bs * bs,
-                              cudaMemcpyDeviceToDevice, ctx->stream));
-    }
-  }
-  k_set_last<<<1, 32, 0, ctx->stream>>>(Sbd.m.row_ptr, nb, (int32_t)poff[count]);
-  IFAC_CK_LAUNCH();
-  if (poff[count]) block_norms(ctx, Sbd.m, Sbd.m.norms);
+  Mat Sbd = block_diag(ctx, count, Sv);
   Mat S = truncate(ctx, Sbd.m, tau);
   Sbd.reset();
   // segments and per-member Gershgorin bounds

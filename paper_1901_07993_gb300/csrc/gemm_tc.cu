@@ -944,10 +944,13 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   // narrow tiles (gemm_band.cu) for every product at bs 32 and 128, and for
   // the banded ones at bs 64 (no 128 x 64 tile with more than KW K steps);
   // the super-tiles below for the other bs-64 products
-  {
+  // (the context's schedule can ask for super-tiles only, or narrow tiles up
+  // to another K length)
+  const int nk_lim = ctx->narrow_kmax < 0 ? KW : ctx->narrow_kmax;
+  if (bs != 64 || nk_lim > 0) {
     const BandShape sh = band_lp_shape(ELT, bs);
-    Plan Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? KW : 0, amap);
-    if (bs != 64 || (Pb.kmax >= 1 && Pb.kmax <= KW)) {
+    Plan Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? nk_lim : 0, amap);
+    if (bs != 64 || (Pb.kmax >= 1 && Pb.kmax <= nk_lim)) {
       const CUtensorMap mapA = make_map_bs(ELT, bs, la_p, A.nnzb + 1, sh);
       const CUtensorMap mapB = make_map_bs(ELT, bs, lb_p, B.nnzb + 1, sh);
       prof_begin(ctx, 1);
@@ -1715,11 +1718,21 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   // tiles all fit one window with at most band::MAX_U units runs on the
   // narrow kernel, every other one on the windowed super-tile kernel; at bs
   // 32 and 128 every product runs on the narrow kernel, window by window.
+  // The context's schedule can ask for super-tiles only at bs 64, or narrow
+  // tiles (window by window) up to another K length.
   float l1h[2] = {0.f, 0.f};  // scaled 1-norm bounds of op(A) rows and op(B) columns (FP32 bits)
   const HostRead l1read{l1h, l1.p, sizeof(l1h)};
-  Plan Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? KW : 0, amap, &l1read);
-  const bool banded = bs != 64 || (Pb.kmax >= 1 && Pb.kmax <= KW &&
-                                   unit_table(ns, Pb.kmax, bs).nunits <= band::MAX_U);
+  const int nk_lim = ctx->narrow_kmax < 0 ? KW : ctx->narrow_kmax;
+  Plan Pb;
+  bool banded = bs != 64;
+  if (bs != 64 || nk_lim > 0) {
+    Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? nk_lim : 0, amap, &l1read);
+    if (bs == 64)
+      banded = Pb.kmax >= 1 && Pb.kmax <= nk_lim &&
+               (ctx->narrow_kmax > 0 || unit_table(ns, Pb.kmax, bs).nunits <= band::MAX_U);
+  } else {
+    to_host(ctx, l1h, l1.p, sizeof(l1h));
+  }
   Plan P;
   if (!banded) P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, true, 0, amap);
   // block pairs, and block pairs times the ns (ns + 1) / 2 slice pairs

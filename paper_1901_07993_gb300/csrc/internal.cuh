@@ -44,6 +44,10 @@ struct ifac_ctx {
   int split_slices = 7;  // BF16 slices per operand for IFAC_FP64_SPLIT products
   int fp64_prec = IFAC_FP64;  // IFAC_FP64_SPLIT: gemm() runs FP64 products of bs = 64 on the split kernel
   unsigned long long* dev_pairs = nullptr;
+  // tile schedule of bs-64 tensor-core products: -1 narrow tiles when no
+  // tile has more than 16 K blocks (split: and one window holds them), 0
+  // super-tiles only, k > 0 narrow tiles when no tile has more than k
+  int narrow_kmax = -1;
 };
 
 namespace ifac {
@@ -213,6 +217,11 @@ BandShape band_lp_shape(int elt, int bs);
 void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const void* mapB, const int32_t* tiles,
                      const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
                      int tiles_bound, double alpha, ifac_bsr& C);
+// the same matrix with block size bs (32, 64, 128), exact (reblock.cu)
+Mat reblock(ifac_ctx* ctx, const ifac_bsr& A, int bs);
+// block size and bs-64 tile schedule of a batch from timed probe products
+void autotune(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, const ifac_opts& o,
+              ifac_tune_result* out);
 // Failure-path self-test: a tensor-core launch whose pipeline never fills, so
 // its bounded waits expire after wait_limit polls (sets the device error flag).
 void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit);

@@ -32,7 +32,8 @@ EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", 
            "bsr_add", "bsr_truncate", "bsr_fro", "bsr_gershgorin", "leaf_invchol_batched", "inv_factor_refine",
            "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
            "inv_factor_refine_adjoint", "inv_factor_refine_batched", "ifac_set_split_slices",
-           "inv_factor_rinch", "ifac_selftest_wait_timeout")
+           "inv_factor_rinch", "ifac_selftest_wait_timeout", "bsr_reblock", "ifac_set_schedule",
+           "ifac_autotune_batched")
 
 
 class IfacError(RuntimeError):
@@ -65,6 +66,12 @@ class _Report(ctypes.Structure):
                 ("split_ms", ctypes.c_double), ("split_pairs", ctypes.c_int64),
                 ("split_slice_pairs", ctypes.c_int64), ("fp64_bytes", ctypes.c_double),
                 ("tc_bytes", ctypes.c_double), ("split_bytes", ctypes.c_double)]
+
+
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("bs", ctypes.c_int32), ("narrow_kmax", ctypes.c_int32), ("probe_ms", ctypes.c_double * 3),
+                ("probe64_ms", ctypes.c_double * 3), ("low_sweeps_est", ctypes.c_int32),
+                ("split_evals_est", ctypes.c_int32)]
 
 
 _lib = None
@@ -105,6 +112,9 @@ def load(path: str = LIB_PATH):
         "inv_factor_refine_adjoint": ([p, PB, PB, i32, d, ctypes.POINTER(d), PB], i32),
         "inv_factor_refine_batched": ([p, i32, p, d, d, ctypes.POINTER(_Opts), p, p], i32),
         "ifac_selftest_wait_timeout": ([p, i64], i32),
+        "bsr_reblock": ([p, PB, i32, PB], i32),
+        "ifac_set_schedule": ([p, i32], i32),
+        "ifac_autotune_batched": ([p, i32, p, d, ctypes.POINTER(_Opts), ctypes.POINTER(_TuneResult)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -438,6 +448,33 @@ def inv_factor_resid(ctx: Context, S: DeviceBSR, Z: DeviceBSR) -> float:
     out = ctypes.c_double()
     ctx.check(ctx.lib.inv_factor_resid(ctx.h, S.ptr(), Z.ptr(), ctypes.byref(out)))
     return out.value
+
+
+def bsr_reblock(ctx: Context, A: DeviceBSR, bs: int) -> DeviceBSR:
+    """The same matrix with block size bs (32, 64, 128), exact."""
+    out = _Bsr()
+    ctx.check(ctx.lib.bsr_reblock(ctx.h, A.ptr(), int(bs), ctypes.byref(out)))
+    return DeviceBSR(ctx, out)
+
+
+def set_schedule(ctx: Context, narrow_kmax: int) -> None:
+    """Tile schedule of bs-64 tensor-core products (see include/ifac.h)."""
+    ctx.check(ctx.lib.ifac_set_schedule(ctx.h, int(narrow_kmax)))
+
+
+def autotune_batched(ctx: Context, members, tau: float, o) -> dict:
+    """Block size and bs-64 tile schedule of a batched refinement from timed
+    probes (sets the schedule on the context); returns the choice and the
+    predicted times."""
+    arr = (ctypes.POINTER(_Bsr) * len(members))(*[ctypes.pointer(m.raw) for m in members])
+    r = _TuneResult()
+    ctx.check(ctx.lib.ifac_autotune_batched(ctx.h, len(members), ctypes.cast(arr, ctypes.c_void_p), tau,
+                                            ctypes.byref(o), ctypes.byref(r)))
+    return {"bs": r.bs, "narrow_kmax": r.narrow_kmax, "probe_ms": {32: r.probe_ms[0], 64: r.probe_ms[1],
+                                                                   128: r.probe_ms[2]},
+            "probe64_ms": {"default": r.probe64_ms[0], "super_tiles": r.probe64_ms[1],
+                           "narrow": r.probe64_ms[2]},
+            "low_sweeps_est": r.low_sweeps_est, "split_evals_est": r.split_evals_est}
 
 
 def selftest_wait_timeout(ctx: Context, wait_limit: int) -> int:

@@ -46,7 +46,8 @@ def test_struct_layouts_match_header(tmp_path):
     gcc = shutil.which("gcc")
     if gcc is None:
         pytest.skip("no C compiler")
-    mirrors = {"ifac_bsr": ifac._Bsr, "ifac_opts": ifac._Opts, "ifac_report": ifac._Report}
+    mirrors = {"ifac_bsr": ifac._Bsr, "ifac_opts": ifac._Opts, "ifac_report": ifac._Report,
+               "ifac_tune_result": ifac._TuneResult}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ifac.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -272,3 +272,20 @@ def test_split_refine_block_sizes_match_oracle(ctx, bs):
     za = oracle.Mat(a.n, bs, a.row_ptr, a.col_idx, a.val).to_dense()
     zr = Z_ref.to_dense()
     assert np.linalg.norm(za - zr) / np.linalg.norm(zr) <= 1e-10
+
+
+@pytest.mark.parametrize("schedule", [-1, 0, 1 << 30])
+def test_split_schedules_bs64(ctx, schedule):
+    """bs 64 under each tile schedule: default (windowed super-tiles for a
+    dense product), super-tiles only, and narrow tiles for everything (the
+    narrow kernel then runs the dense product window by window)."""
+    from paper_1901_07993_gb300 import ifac
+    A = synth.random_bsr(30, 64, 1.0, seed=75)
+    B = synth.random_bsr(30, 64, 1.0, seed=76)
+    ifac.set_schedule(ctx, schedule)
+    try:
+        _, rel = _check(ctx, A, B, False, True)
+        _, rel2 = _check(ctx, A, B, True, False, alpha=0.3)
+    finally:
+        ifac.set_schedule(ctx, -1)
+    assert rel < 1e-13 and rel2 < 1e-13

@@ -196,3 +196,20 @@ def test_tc_block_sizes_overlap_and_rounding(ctx, bs, prec):
     I = synth.HostBSR(nb * bs, bs, np.arange(nb + 1, dtype=np.int32), np.arange(nb, dtype=np.int32), eye)
     got = ifac.bsr_gemm_trunc(ctx, ifac.upload(ctx, A), False, ifac.upload(ctx, I), False, 1.0, 0.0, prec).download()
     assert np.array_equal(got.val, rounded(A, prec).val)
+
+
+@pytest.mark.parametrize("schedule", [0, 1 << 30])
+@pytest.mark.parametrize("prec", [TF32, BF16])
+def test_tc_schedules_bs64(ctx, schedule, prec):
+    """bs 64 TF32/BF16 products under the super-tile-only and narrow-only
+    schedules, dense and banded patterns, against the rounded-input bound."""
+    from paper_1901_07993_gb300 import ifac
+    ifac.set_schedule(ctx, schedule)
+    try:
+        A = synth.random_bsr(24, 64, 1.0, seed=77)
+        B = synth.random_bsr(24, 64, 0.3, seed=78)
+        _check(ctx, A, B, False, True, prec)
+        S = synth.chain_overlap(2000, 64, seed=4)
+        _check(ctx, S, S, True, False, prec)
+    finally:
+        ifac.set_schedule(ctx, -1)
