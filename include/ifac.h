@@ -92,14 +92,15 @@ typedef struct ifac_ctx ifac_ctx;
 
 /* Result of ifac_autotune_batched. */
 typedef struct {
-  int32_t bs;            /* chosen block size: 32, 64 or 128 */
-  int32_t narrow_kmax;   /* chosen tile schedule of bs-64 products (ifac_set_schedule) */
-  double probe_ms[3];    /* predicted product time of a batch refinement at bs 32, 64,
-                            128 (best schedule), from the timed probes */
-  double probe64_ms[3];  /* at bs 64 per schedule: default, super-tiles only,
-                            narrow tiles only */
-  int32_t low_sweeps_est;  /* sweeps and FP64-accurate delta evaluations the */
-  int32_t split_evals_est; /* prediction assumes */
+  int32_t bs;                /* chosen block size: 32, 64 or 128 */
+  int32_t narrow_kmax;       /* chosen tile schedule of bs-64 TF32/BF16 products */
+  int32_t narrow_kmax_split; /* and of bs-64 split products (ifac_set_schedule) */
+  int32_t low_sweeps_est;    /* sweeps and FP64-accurate delta evaluations */
+  int32_t split_evals_est;   /* the prediction assumes */
+  double probe_ms[3];        /* predicted product time of a batch refinement at bs 32,
+                                64, 128 (best schedules), from the timed probes */
+  double probe64_lp_ms[3];   /* at bs 64, the low-precision and the split share of */
+  double probe64_split_ms[3];/* it per schedule: default, super-tiles only, narrow only */
 } ifac_tune_result;
 
 /* Options of the factorization drivers.  ifac_opts_default fills:
@@ -321,15 +322,16 @@ int leaf_invchol_batched_noalloc(void* stream, int count, int nl, const double* 
  * choice of ifac_autotune_batched.  IFAC_ERR_UNSUPPORTED for another bs. */
 int bsr_reblock(ifac_ctx* ctx, const ifac_bsr* A, int32_t bs, ifac_bsr* out);
 
-/* Tile schedule of the context's bs-64 tensor-core products (TF32, BF16 and
- * split): -1 (default) narrow 128 x 64 tiles for products whose longest tile
- * has at most 16 K blocks (split: and fits one exact window), super-tiles for
- * the others; 0 super-tiles for every product; k > 0 narrow tiles for every
- * product whose longest tile has at most k K blocks.  Results are the same
- * products either way (TF32/BF16 up to FP32 summation order; split products
- * within their error bound).  Products at bs 32 and 128 always use narrow
- * tiles.  IFAC_ERR_INVALID below -1. */
-int ifac_set_schedule(ifac_ctx* ctx, int32_t narrow_kmax);
+/* Tile schedules of the context's bs-64 tensor-core products, one for the
+ * TF32/BF16 products (narrow_kmax) and one for the split FP64-accurate ones
+ * (narrow_kmax_split): -1 (default) narrow 128 x 64 tiles for products whose
+ * longest tile has at most 16 K blocks (split: and fits one exact window),
+ * super-tiles for the others; 0 super-tiles for every product; k > 0 narrow
+ * tiles for every product whose longest tile has at most k K blocks.
+ * Results are the same products either way (TF32/BF16 up to FP32 summation
+ * order; split products within their error bound).  Products at bs 32 and
+ * 128 always use narrow tiles.  IFAC_ERR_INVALID below -1. */
+int ifac_set_schedule(ifac_ctx* ctx, int32_t narrow_kmax, int32_t narrow_kmax_split);
 
 /* Autotuner of the batched refinement (config 4's block size and tile
  * schedule): for each block size 32, 64 and 128 the members are re-blocked
@@ -339,10 +341,11 @@ int ifac_set_schedule(ifac_ctx* ctx, int32_t narrow_kmax);
  * is BF16; X has about the pattern of the later iterates) and one split
  * FP64-accurate product X X, best of two runs;
  * at bs 64 each tile schedule of ifac_set_schedule (-1, 0, and narrow for
- * all) is probed.  The predicted batch time weighs the probes by a typical
+ * all) is probed for each of the two kinds of product.  The predicted batch
+ * time weighs the probes by a typical
  * sweep count (4 products in each of 6 low-precision sweeps, 2 in each of 4
- * FP64-accurate delta evaluations); the fastest block size and schedule are
- * returned in out, and the schedule is set on the context.  The caller
+ * FP64-accurate delta evaluations); the fastest block size and schedules are
+ * returned in out, and the schedules are set on the context.  The caller
  * re-blocks its members to out->bs (bsr_reblock) before
  * inv_factor_refine_batched.  Synchronises the stream; allocates the probe's
  * matrices through the context's allocator and frees them. */

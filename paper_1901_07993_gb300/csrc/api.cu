@@ -555,10 +555,11 @@ int bsr_reblock(ifac_ctx* ctx, const ifac_bsr* A, int32_t bs, ifac_bsr* out) {
   });
 }
 
-int ifac_set_schedule(ifac_ctx* ctx, int32_t narrow_kmax) {
+int ifac_set_schedule(ifac_ctx* ctx, int32_t narrow_kmax, int32_t narrow_kmax_split) {
   if (!ctx) return IFAC_ERR_INVALID;
-  if (narrow_kmax < -1) return IFAC_ERR_INVALID;
+  if (narrow_kmax < -1 || narrow_kmax_split < -1) return IFAC_ERR_INVALID;
   ctx->narrow_kmax = narrow_kmax;
+  ctx->narrow_kmax_split = narrow_kmax_split;
   return IFAC_OK;
 }
 
@@ -575,6 +576,7 @@ int ifac_autotune_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, do
     if (!(tau >= 0)) fail(IFAC_ERR_INVALID, "tau must be >= 0");
     autotune(ctx, count, S, tau, *opts, out);
     ctx->narrow_kmax = out->narrow_kmax;
+    ctx->narrow_kmax_split = out->narrow_kmax_split;
     return IFAC_OK;
   });
 }

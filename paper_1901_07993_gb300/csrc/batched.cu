@@ -223,11 +223,13 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       node_fro(ctx, D.m, dnb0.p, dnb1.p, count, ne.p);
       to_host(ctx, e.data(), ne.p, sizeof(double) * count);
       if (ns < ctx->split_slices) {
-        // a member's delta far below its predicted size: evaluate again with
-        // all slices
+        // a member's delta far below its predicted size, or at the target
+        // (a stop must not rest on fewer slices): evaluate again with all
+        // slices
         bool redo = false;
         for (int k = 0; k < count; ++k)
-          if (active[k] && split_delta_error(ns, (int64_t)(nb1[k] - nb0[k]) * bs) > delta_need(e[k], target, u))
+          if (active[k] && (split_delta_error(ns, (int64_t)(nb1[k] - nb0[k]) * bs) > delta_need(e[k], target, u) ||
+                            e[k] <= target))
             redo = true;
         if (redo) {
           all_slices = true;

@@ -241,9 +241,12 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
               : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     }
     e = fro_host(ctx, D.m);
-    if (dprec == IFAC_FP64_SPLIT && ns < ctx->split_slices && split_delta_error(ns, S.m.n) > delta_need(e, target, u)) {
+    if (dprec == IFAC_FP64_SPLIT && ns < ctx->split_slices &&
+        (split_delta_error(ns, S.m.n) > delta_need(e, target, u) || e <= target)) {
       // delta came out below its predicted size, past what this many slices
-      // resolve: evaluate it again with all of them
+      // resolve, or at the target, where the stop must not rest on fewer
+      // slices (on dense operands the error of an s-slice evaluation is far
+      // above the chain-derived estimate): evaluate it again with all of them
       all_slices = true;
       --it;
       continue;

@@ -1025,9 +1025,11 @@ constexpr int SPLIT_BITS = 7;
 // exponent e of sigma = 2^e for every scalar row of a (possibly transposed)
 // row view: max_k |x_rk| = m 2^e with m in [0.5, 1) (e = 0 for an all-zero row);
 // the largest scaled row 1-norm sum_k |x_rk| / sigma (FP32, magnitudes
-// truncated to 24 bits) into *l1max as FP32 bits
-__device__ __forceinline__ void row_scale_out(unsigned long long m, float l1, int nscalars, int* eout,
-                                              unsigned int* l1max) {
+// truncated to 24 bits) into *l1max and the largest scaled row 2-norm
+// (sum_k x_rk^2)^(1/2) / sigma (FP64 sum, rounded up) into *l2max, both as
+// FP32 bits
+__device__ __forceinline__ void row_scale_out(unsigned long long m, float l1, double sq, int nscalars, int* eout,
+                                              unsigned int* l1max, unsigned int* l2max) {
   const int ea = (int)(m >> 52);
   int e = 0;
   if (ea > 0) e = ea - 1022;                       // [2^(ea-1023), 2^(ea-1022))
@@ -1037,10 +1039,13 @@ __device__ __forceinline__ void row_scale_out(unsigned long long m, float l1, in
     // entries below 2^-126 were left out: add their largest possible share
     const float s = ldexpf(l1, -e) + (float)nscalars * ldexpf(1.0f, -126 - e);
     atomicMax(l1max, __float_as_uint(fminf(s, 3.0e38f)));
+    const float s2 = (float)(ldexp(sqrt(sq), -e) * 1.0001) + 1e-30f;
+    atomicMax(l2max, __float_as_uint(fminf(s2, 3.0e38f)));
   }
 }
 
-__device__ __forceinline__ void row_scale_acc(double x, unsigned long long& m, float& l1) {
+__device__ __forceinline__ void row_scale_acc(double x, unsigned long long& m, float& l1, double& sq) {
+  sq = fma(x, x, sq);
   const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
   m = u > m ? u : m;
   const int e32 = (int)(u >> 52) - 896;  // FP32 exponent field of |x|
@@ -1053,55 +1058,59 @@ __device__ __forceinline__ void row_scale_acc(double x, unsigned long long& m, f
 template <int B>
 __global__ void __launch_bounds__(B) k_row_scale_t(const int32_t* __restrict__ rp, const int32_t* __restrict__ src,
                                                    int nb, const double* __restrict__ val, int* __restrict__ eout,
-                                                   unsigned int* __restrict__ l1max) {
+                                                   unsigned int* __restrict__ l1max, unsigned int* __restrict__ l2max) {
   const int I = blockIdx.x, r = threadIdx.x;
   if (I >= nb) return;
   unsigned long long m = 0;
   float l1 = 0.0f;
+  double sq = 0.0;
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
     const double* blk = val + (size_t)(src ? src[q] : q) * B * B;
 #pragma unroll 8
-    for (int k = 0; k < B; ++k) row_scale_acc(blk[k * B + r], m, l1);
+    for (int k = 0; k < B; ++k) row_scale_acc(blk[k * B + r], m, l1, sq);
   }
-  row_scale_out(m, l1, (rp[I + 1] - rp[I]) * B, eout + (size_t)I * B + r, l1max);
+  row_scale_out(m, l1, sq, (rp[I + 1] - rp[I]) * B, eout + (size_t)I * B + r, l1max, l2max);
 }
 
 // rows stored as rows: one warp per scalar row, lanes along the row (coalesced)
 template <int B>
 __global__ void k_row_scale(const int32_t* __restrict__ rp, const int32_t* __restrict__ src, int nb,
-                            const double* __restrict__ val, int* __restrict__ eout, unsigned int* __restrict__ l1max) {
+                            const double* __restrict__ val, int* __restrict__ eout, unsigned int* __restrict__ l1max,
+                            unsigned int* __restrict__ l2max) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (int64_t)nb * B) return;
   const int I = (int)(w / B), r = (int)(w % B);
   unsigned long long m = 0;  // |x| bit patterns order like the magnitudes
   float l1 = 0.0f;
+  double sq = 0.0;
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
     const double* blk = val + (size_t)(src ? src[q] : q) * B * B;
-    for (int c = lane; c < B; c += 32) row_scale_acc(blk[r * B + c], m, l1);
+    for (int c = lane; c < B; c += 32) row_scale_acc(blk[r * B + c], m, l1, sq);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
     m = u > m ? u : m;
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
   }
-  if (lane == 0) row_scale_out(m, l1, (rp[I + 1] - rp[I]) * B, eout + w, l1max);
+  if (lane == 0) row_scale_out(m, l1, sq, (rp[I + 1] - rp[I]) * B, eout + w, l1max, l2max);
 }
 
 // sigma exponents (and the scaled 1-norm bound) of the rows of a row view
 static void row_scales(ifac_ctx* ctx, int bs, const int32_t* rp, const int32_t* src, int nb, bool tr,
-                       const double* val, int* eout, unsigned int* l1max) {
+                       const double* val, int* eout, unsigned int* l1max, unsigned int* l2max) {
   const int g = cdiv((int64_t)nb * bs * 32, 256);
   if (bs == 32) {
-    if (tr) k_row_scale_t<32><<<nb, 32, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
-    else k_row_scale<32><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+    if (tr) k_row_scale_t<32><<<nb, 32, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max, l2max);
+    else k_row_scale<32><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max, l2max);
   } else if (bs == 64) {
-    if (tr) k_row_scale_t<64><<<nb, 64, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
-    else k_row_scale<64><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+    if (tr) k_row_scale_t<64><<<nb, 64, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max, l2max);
+    else k_row_scale<64><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max, l2max);
   } else {
-    if (tr) k_row_scale_t<128><<<nb, 128, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
-    else k_row_scale<128><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max);
+    if (tr) k_row_scale_t<128><<<nb, 128, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max, l2max);
+    else k_row_scale<128><<<g, 256, 0, ctx->stream>>>(rp, src, nb, val, eout, l1max, l2max);
   }
   IFAC_CK_LAUNCH();
 }
@@ -1682,15 +1691,16 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const bool hit = ac && ac->split_ns >= ns;
   const int nsa = hit ? ac->split_ns : (ac ? std::min(8, std::max(ns, ac->want_ns)) : ns);
   Buf<int> sige, taue(ctx, rows);
-  Buf<unsigned int> l1(ctx, 2);
-  IFAC_CK(cudaMemsetAsync(l1.p, 0, 2 * sizeof(unsigned int), ctx->stream));
+  // [0] / [1]: scaled 1-norm bounds of op(A) rows / op(B) columns, [2] / [3]: 2-norm bounds
+  Buf<unsigned int> l1(ctx, 4);
+  IFAC_CK(cudaMemsetAsync(l1.p, 0, 4 * sizeof(unsigned int), ctx->stream));
   if (!hit) {
     sige = Buf<int>(ctx, rows);
-    row_scales(ctx, bs, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p);
+    row_scales(ctx, bs, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p, l1.p + 2);
   }
   {
     View bt = view_rows(ctx, B, !tB);
-    row_scales(ctx, bs, bt.rp, bt.src, nb, !tB, B.val, taue.p, l1.p + 1);
+    row_scales(ctx, bs, bt.rp, bt.src, nb, !tB, B.val, taue.p, l1.p + 1, l1.p + 3);
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
   const size_t bbytes = (size_t)bs * bs * 2;
@@ -1720,16 +1730,16 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   // 32 and 128 every product runs on the narrow kernel, window by window.
   // The context's schedule can ask for super-tiles only at bs 64, or narrow
   // tiles (window by window) up to another K length.
-  float l1h[2] = {0.f, 0.f};  // scaled 1-norm bounds of op(A) rows and op(B) columns (FP32 bits)
+  float l1h[4] = {0.f, 0.f, 0.f, 0.f};  // scaled 1- and 2-norm bounds (as l1 above)
   const HostRead l1read{l1h, l1.p, sizeof(l1h)};
-  const int nk_lim = ctx->narrow_kmax < 0 ? KW : ctx->narrow_kmax;
+  const int nk_lim = ctx->narrow_kmax_split < 0 ? KW : ctx->narrow_kmax_split;
   Plan Pb;
   bool banded = bs != 64;
   if (bs != 64 || nk_lim > 0) {
     Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? nk_lim : 0, amap, &l1read);
     if (bs == 64)
       banded = Pb.kmax >= 1 && Pb.kmax <= nk_lim &&
-               (ctx->narrow_kmax > 0 || unit_table(ns, Pb.kmax, bs).nunits <= band::MAX_U);
+               (ctx->narrow_kmax_split > 0 || unit_table(ns, Pb.kmax, bs).nunits <= band::MAX_U);
   } else {
     to_host(ctx, l1h, l1.p, sizeof(l1h));
   }
@@ -1743,8 +1753,10 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   const int kmax = banded ? Pb.kmax : P.kmax;
   if (hit) {
     l1h[0] = ac->l1;
+    l1h[2] = ac->l2;
   } else if (ac) {
     ac->l1 = l1h[0];
+    ac->l2 = l1h[2];
     ac->split = std::move(la);
     ac->sexp = std::move(sige);
     ac->split_ns = nsa;
@@ -1755,6 +1767,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     bc->split = std::move(lb);
     bc->sexp = std::move(taue);
     bc->l1 = l1h[1];
+    bc->l2 = l1h[3];
     bc->split_ns = ns;
     bc->from_b = true;
   }
@@ -1777,12 +1790,19 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   // fixed point, scale 2^-f relative to sigma_i tau_j, with every partial sum
   // below 2^62: |sum_ij| <= min(sum_k |a_ik| / sigma_i, sum_k |b_kj| / tau_j)
   // (|a / sigma|, |b / tau| < 1), bounded by the largest scaled row / column
-  // 1-norm (FP32, so with a margin), and by the scalar inner length K of the
-  // longest tile.  f <= 56 keeps every weight 2^(f - 7g) of the 7-slice
-  // product integral.  An overflow would still be detected and reported.
+  // 1-norm (FP32, so with a margin), by the scalar inner length K of the
+  // longest tile, and (Cauchy-Schwarz) by the product of the largest scaled
+  // row and column 2-norms, each widened by 0.0125 sqrt(K) for the slices'
+  // rounding (sum_s |q_s| 2^-7s exceeds |a / sigma| by at most 0.0125).  The
+  // 2-norm bound is the tight one for dense operands, where every bit of f
+  // saved is a rounding the finest accumulation units escape in each window.
+  // f <= 56 keeps every weight 2^(f - 7g) of the 7-slice product integral.
+  // An overflow would still be detected and reported.
   int lgK = 0;
   while (((int64_t)1 << lgK) < (int64_t)std::max(kmax, 1) * bs) ++lgK;
-  const double l1b = std::min((double)l1h[0], (double)l1h[1]) * 1.125 + 2.0;
+  const double rk = 0.0125 * std::sqrt((double)std::max(kmax, 1) * bs);
+  const double l2b = ((double)l1h[2] + rk) * ((double)l1h[3] + rk);
+  const double l1b = std::min(std::min((double)l1h[0], (double)l1h[1]), l2b) * 1.125 + 2.0;
   int lgB = 0;
   while (std::ldexp(1.0, lgB) < l1b && lgB < 62) ++lgB;
   const int fbits = std::min(56, 62 - std::min(lgK, lgB));

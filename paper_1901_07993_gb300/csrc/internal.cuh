@@ -44,10 +44,12 @@ struct ifac_ctx {
   int split_slices = 7;  // BF16 slices per operand for IFAC_FP64_SPLIT products
   int fp64_prec = IFAC_FP64;  // IFAC_FP64_SPLIT: gemm() runs FP64 products of bs = 64 on the split kernel
   unsigned long long* dev_pairs = nullptr;
-  // tile schedule of bs-64 tensor-core products: -1 narrow tiles when no
-  // tile has more than 16 K blocks (split: and one window holds them), 0
-  // super-tiles only, k > 0 narrow tiles when no tile has more than k
+  // tile schedule of bs-64 tensor-core products (TF32/BF16, and split): -1
+  // narrow tiles when no tile has more than 16 K blocks (split: and one
+  // window holds them), 0 super-tiles only, k > 0 narrow tiles when no tile
+  // has more than k
   int narrow_kmax = -1;
+  int narrow_kmax_split = -1;
 };
 
 namespace ifac {
@@ -183,6 +185,7 @@ struct OperandCache {
   Buf<uint8_t> split;      // split_ns slices, slice-major, (nnzb + 1) blocks each
   Buf<int> sexp;           // row scale exponents of op(A)
   float l1 = 0.f;          // scaled row 1-norm bound of op(A)
+  float l2 = 0.f;          // scaled row 2-norm bound of op(A)
   void reset() {
     from_b = false;
     conv_elt = 0;
@@ -191,6 +194,7 @@ struct OperandCache {
     split.reset();
     sexp.reset();
     l1 = 0.f;
+    l2 = 0.f;
   }
 };
 

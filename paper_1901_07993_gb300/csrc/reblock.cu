@@ -199,7 +199,7 @@ void autotune(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, co
   const double w_lp = 4.0 * out->low_sweeps_est / 2.0;
   const double w_split = 2.0 * out->split_evals_est;
   const int bss[3] = {32, 64, 128};
-  const int old_kmax = ctx->narrow_kmax;
+  const int old_lp = ctx->narrow_kmax, old_sp = ctx->narrow_kmax_split;
   double best = INFINITY;
   for (int i = 0; i < 3; ++i) {
     const int bs = bss[i];
@@ -219,24 +219,40 @@ void autotune(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, co
     D.reset();
     held.clear();
     // tile schedules: at bs 64 the narrow tiles for tiles of at most KW K
-    // blocks (default), for none, or for all; the other sizes have one
+    // blocks (default), for none, or for all, chosen separately for the
+    // low-precision and the split products; the other sizes have one
     const int sched[3] = {-1, 0, 1 << 30};
     const int nsched = bs == 64 ? 3 : 1;
+    double best_lp = INFINITY, best_sp = INFINITY;
+    int sched_lp = -1, sched_sp = -1;
     for (int si = 0; si < nsched; ++si) {
-      ctx->narrow_kmax = bs == 64 ? sched[si] : -1;
+      ctx->narrow_kmax = ctx->narrow_kmax_split = bs == 64 ? sched[si] : -1;
       double lp = 0, sp = 0;
       probe(ctx, St.m, tau, prec, 2, &lp, &sp);
-      const double pred = w_lp * lp + w_split * sp;
-      if (bs == 64) out->probe64_ms[si] = pred;
-      out->probe_ms[i] = si == 0 ? pred : std::min(out->probe_ms[i], pred);
-      if (pred < best) {
-        best = pred;
-        out->bs = bs;
-        out->narrow_kmax = ctx->narrow_kmax;
+      if (bs == 64) {
+        out->probe64_lp_ms[si] = w_lp * lp;
+        out->probe64_split_ms[si] = w_split * sp;
+      }
+      if (lp < best_lp) {
+        best_lp = lp;
+        sched_lp = ctx->narrow_kmax;
+      }
+      if (sp < best_sp) {
+        best_sp = sp;
+        sched_sp = ctx->narrow_kmax_split;
       }
     }
+    const double pred = w_lp * best_lp + w_split * best_sp;
+    out->probe_ms[i] = pred;
+    if (pred < best) {
+      best = pred;
+      out->bs = bs;
+      out->narrow_kmax = sched_lp;
+      out->narrow_kmax_split = sched_sp;
+    }
   }
-  ctx->narrow_kmax = old_kmax;
+  ctx->narrow_kmax = old_lp;
+  ctx->narrow_kmax_split = old_sp;
 }
 
 }  // namespace ifac

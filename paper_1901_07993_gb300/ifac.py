@@ -69,9 +69,10 @@ class _Report(ctypes.Structure):
 
 
 class _TuneResult(ctypes.Structure):
-    _fields_ = [("bs", ctypes.c_int32), ("narrow_kmax", ctypes.c_int32), ("probe_ms", ctypes.c_double * 3),
-                ("probe64_ms", ctypes.c_double * 3), ("low_sweeps_est", ctypes.c_int32),
-                ("split_evals_est", ctypes.c_int32)]
+    _fields_ = [("bs", ctypes.c_int32), ("narrow_kmax", ctypes.c_int32), ("narrow_kmax_split", ctypes.c_int32),
+                ("low_sweeps_est", ctypes.c_int32), ("split_evals_est", ctypes.c_int32),
+                ("probe_ms", ctypes.c_double * 3), ("probe64_lp_ms", ctypes.c_double * 3),
+                ("probe64_split_ms", ctypes.c_double * 3)]
 
 
 _lib = None
@@ -113,7 +114,7 @@ def load(path: str = LIB_PATH):
         "inv_factor_refine_batched": ([p, i32, p, d, d, ctypes.POINTER(_Opts), p, p], i32),
         "ifac_selftest_wait_timeout": ([p, i64], i32),
         "bsr_reblock": ([p, PB, i32, PB], i32),
-        "ifac_set_schedule": ([p, i32], i32),
+        "ifac_set_schedule": ([p, i32, i32], i32),
         "ifac_autotune_batched": ([p, i32, p, d, ctypes.POINTER(_Opts), ctypes.POINTER(_TuneResult)], i32),
     }
     for name, (args, res) in sig.items():
@@ -457,9 +458,11 @@ def bsr_reblock(ctx: Context, A: DeviceBSR, bs: int) -> DeviceBSR:
     return DeviceBSR(ctx, out)
 
 
-def set_schedule(ctx: Context, narrow_kmax: int) -> None:
-    """Tile schedule of bs-64 tensor-core products (see include/ifac.h)."""
-    ctx.check(ctx.lib.ifac_set_schedule(ctx.h, int(narrow_kmax)))
+def set_schedule(ctx: Context, narrow_kmax: int, narrow_kmax_split: int | None = None) -> None:
+    """Tile schedules of bs-64 TF32/BF16 and split products (see
+    include/ifac.h); the split schedule defaults to the same value."""
+    s = narrow_kmax if narrow_kmax_split is None else narrow_kmax_split
+    ctx.check(ctx.lib.ifac_set_schedule(ctx.h, int(narrow_kmax), int(s)))
 
 
 def autotune_batched(ctx: Context, members, tau: float, o) -> dict:
@@ -470,10 +473,11 @@ def autotune_batched(ctx: Context, members, tau: float, o) -> dict:
     r = _TuneResult()
     ctx.check(ctx.lib.ifac_autotune_batched(ctx.h, len(members), ctypes.cast(arr, ctypes.c_void_p), tau,
                                             ctypes.byref(o), ctypes.byref(r)))
-    return {"bs": r.bs, "narrow_kmax": r.narrow_kmax, "probe_ms": {32: r.probe_ms[0], 64: r.probe_ms[1],
-                                                                   128: r.probe_ms[2]},
-            "probe64_ms": {"default": r.probe64_ms[0], "super_tiles": r.probe64_ms[1],
-                           "narrow": r.probe64_ms[2]},
+    names = ("default", "super_tiles", "narrow")
+    return {"bs": r.bs, "narrow_kmax": r.narrow_kmax, "narrow_kmax_split": r.narrow_kmax_split,
+            "probe_ms": {32: r.probe_ms[0], 64: r.probe_ms[1], 128: r.probe_ms[2]},
+            "probe64_lp_ms": dict(zip(names, r.probe64_lp_ms)),
+            "probe64_split_ms": dict(zip(names, r.probe64_split_ms)),
             "low_sweeps_est": r.low_sweeps_est, "split_evals_est": r.split_evals_est}
 
 

@@ -83,7 +83,8 @@ def test_autotune_and_batch_at_the_chosen_block_size(ctx):
     print("autotune:", tune)
     assert tune["bs"] in (32, 64, 128)
     assert all(v > 0 for v in tune["probe_ms"].values())
-    assert all(v > 0 for v in tune["probe64_ms"].values())
+    assert all(v > 0 for v in tune["probe64_lp_ms"].values())
+    assert all(v > 0 for v in tune["probe64_split_ms"].values())
     bs = tune["bs"]
     dT = [S if bs == 64 else ifac.bsr_reblock(ctx, S, bs) for S in dS]
     Zs, reps, rc = ifac.inv_factor_refine_batched(ctx, dT, 1e-12, 1e-10, o)
