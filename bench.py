@@ -57,6 +57,22 @@ WORKLOADS = {
     # same dense pattern at n = 8192: the profiling case of the split kernel
     "product-dense-split-n8192": dict(geom="dense", n=8192, bs=64, tau=0.0, target=0.0, method="product", m=2,
                                       seed=1, leaf=512, prec="split", compare=(), sample_n=None),
+    # config 3's recipe on its 3D geometry (random sequential addition at 0.1
+    # points per bohr^3, RCB order) at the largest size that fits in HBM with
+    # every intermediate in FP64: n = 32,768, bs 64, block-dense factor.  TF32
+    # sweeps, then delta with split FP64-accurate products of 8 slices (dense
+    # operands need the 8th: 7 slices err by about 2e-10 in ||delta||_F at
+    # n = 3072), tau = 1e-14 (at 1e-12 the truncated products of delta miss
+    # about sqrt(blocks) x tau of the residual)
+    "irsi-mixed-cluster-n32768-bs64": dict(geom="cluster", n=32768, bs=64, tau=1e-14, target=1e-10,
+                                           method="refine", m=2, seed=0, leaf=512, prec="tf32", compare=(),
+                                           sample_n=2048, cost_exp=3, split_slices=8),
+    # the same at n = 16,384 beside the FP64 schedule with every product on the
+    # split kernel (FP64-accurate throughout): the mixed-vs-FP64 comparison
+    # on the 3D geometry
+    "irsi-mixed-cluster-n16384-bs64": dict(geom="cluster", n=16384, bs=64, tau=1e-14, target=1e-10,
+                                           method="refine", m=2, seed=0, leaf=512, prec="tf32", compare=("split",),
+                                           sample_n=2048, cost_exp=3, split_slices=8),
     # the mixed-precision refinement at n = 65,536: the profiling case of the
     # kernels of the default workload (a quarter of its rows)
     "irsi-mixed-chain-n65536-bs64": dict(geom="chain", n=65536, bs=64, tau=1e-12, target=1e-10, method="refine",
@@ -761,6 +777,8 @@ def main():
         return
     S_h = make_input(w)
     S = ifac.upload(ctx, S_h)
+    if w.get("split_slices"):
+        ctx.set_split_slices(w["split_slices"])
     if w["method"] == "rinch":
         def factor(ctx_, S_, tau, target, o_):
             return ifac.inv_factor_rinch(ctx_, S_, tau, o_)

@@ -56,10 +56,10 @@ extern "C" {
 
 /* Product precision (the arithmetic of the block products). */
 #define IFAC_FP64 0 /* FP64 inputs, FP64 accumulation (FP64 pipe) */
-#define IFAC_TF32 1 /* inputs rounded to TF32, FP32 accumulation (tensor cores, bs = 64) */
-#define IFAC_BF16 2 /* inputs rounded to BF16, FP32 accumulation (tensor cores, bs = 64) */
+#define IFAC_TF32 1 /* inputs rounded to TF32, FP32 accumulation (tensor cores, bs 32/64/128) */
+#define IFAC_BF16 2 /* inputs rounded to BF16, FP32 accumulation (tensor cores, bs 32/64/128) */
 #define IFAC_FP64_SPLIT 3 /* FP64-accurate: error-free splitting into BF16 slices on the
-                             tensor cores (Ozaki et al. 2012), FP64 accumulation, bs = 64 */
+                             tensor cores (Ozaki et al. 2012), FP64 accumulation, bs 32/64/128 */
 
 /* Stop reasons reported by the refinement drivers. */
 #define IFAC_STOP_RULE 1     /* ||delta_{i+1}||_F > ||delta_i||_F^(m+1) (Section 2.2) */
@@ -118,7 +118,7 @@ typedef struct {
                       0 -> c = 1/sqrt(beta), 1 -> c = sqrt(2/beta) */
   int leaf_size;   /* inv_factor_localized: sub-problems with more rows are
                       split at the block-aligned midpoint (Algorithm 2) */
-  int prec;        /* IFAC_FP64; or IFAC_FP64_SPLIT (bs = 64): the FP64
+  int prec;        /* IFAC_FP64; or IFAC_FP64_SPLIT (bs 32, 64 or 128): the FP64
                       schedule with every block product on the split
                       tensor-core kernel; inv_factor_refine and the batched
                       call also take IFAC_TF32 or IFAC_BF16: the
@@ -129,7 +129,8 @@ typedef struct {
                       follow low-precision sweeps (inv_factor_refine with
                       prec TF32/BF16: the FP64 phase; batched: the final
                       residual): IFAC_FP64 (FP64 pipe) or IFAC_FP64_SPLIT
-                      (tensor cores; used when bs = 64, else IFAC_FP64) */
+                      (tensor cores; used when bs is 32, 64 or 128,
+                      else IFAC_FP64) */
   int rinch_rows;  /* inv_factor_localized: sub-problems with at most this
                       many rows (when above leaf_size) are factorized by
                       recursive inverse Cholesky (Algorithm 1, leaf_size
@@ -228,17 +229,19 @@ void ifac_bsr_free(ifac_ctx* ctx, ifac_bsr* a);
  * with norm smaller than the threshold are removed after every product).
  * The output pattern before truncation is every (I, J) for which some K has
  * op(A)_IK and op(B)_KJ stored.  A and B: same n and bs.  prec: IFAC_FP64 (any
- * bs in {16, 32, 64}), or IFAC_TF32 / IFAC_BF16 (bs = 64): the operands are
+ * bs in {16, 32, 64}), or IFAC_TF32 / IFAC_BF16 (bs 32, 64 or 128): the
+ * operands are
  * rounded to that format (BF16 round-to-nearest-even from FP64; TF32 via FP32,
  * round-to-nearest-even, then round-half-away; magnitudes below 2^-126 become
  * zero), products are accumulated in
  * FP32 on the tensor cores, and the result, its norms and the truncation are
- * FP64.  IFAC_FP64_SPLIT (bs = 64): an FP64-accurate product on the tensor
+ * FP64.  IFAC_FP64_SPLIT (bs 32, 64 or 128): an FP64-accurate product on the tensor
  * cores (error-free splitting, Ozaki et al. 2012): each scalar row i of op(A)
  * and column j of op(B) is scaled by a power of two sigma_i, tau_j above its
  * largest magnitude and split into s slices of 7-bit integers held exactly in
  * BF16 (s = 7 unless ifac_set_split_slices); slice products accumulate
- * exactly in FP32 over windows of 16 K blocks, pairs of slice orders
+ * exactly in FP32 over windows of at most 1024 scalar K terms (16 blocks at
+ * bs 64), pairs of slice orders
  * s_a + s_b <= s + 1, and are summed in 64-bit fixed point at 2^-f sigma_i
  * tau_j, f <= 56 chosen so that no partial sum can overflow; the result is
  * converted to FP64 once.  Element error about 2^-(7 s - 3) K_ij sigma_i tau_j
@@ -365,7 +368,9 @@ int ifac_autotune_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, do
  * evaluated).  Returns IFAC_WARN_TARGET_NOT_MET when the rule stopped it
  * above the target, IFAC_ERR_NO_CONVERGENCE at max_iter.  rep may be NULL.
  *
- * Mixed precision (opts->prec = IFAC_TF32 or IFAC_BF16, bs = 64): every
+ * Mixed precision (opts->prec = IFAC_TF32 or IFAC_BF16, bs 32, 64 or 128;
+ * at bs 128 delta_prec must be IFAC_FP64_SPLIT; at bs 64 the symmetric
+ * products Z^T (S Z) and delta delta form their upper block triangle only): every
  * block product of a sweep runs on the tensor cores with inputs rounded to
  * that format and FP32 accumulation, while sums, block norms, truncation and
  * delta = I - Y stay FP64, until the automatic rule of Section 2.2
@@ -415,7 +420,7 @@ int inv_factor_localized(ifac_ctx* ctx, const ifac_bsr* S, double tau, double ta
  * truncated at tau first; every product and every leaf factor is truncated
  * (Section 5).  Without truncation Z is the inverse Cholesky factor (block
  * upper triangular, Z^T S Z = I).  opts: leaf_size; prec IFAC_FP64 or
- * IFAC_FP64_SPLIT (bs = 64).  rep (may be NULL): levels = recursion depth,
+ * IFAC_FP64_SPLIT (bs 32, 64 or 128).  rep (may be NULL): levels = recursion depth,
  * products, block_pairs, nnzb_Z, flops.  IFAC_ERR_NOT_SPD if a leaf (S00 or
  * a Schur complement Q) is not positive definite. */
 int inv_factor_rinch(ifac_ctx* ctx, const ifac_bsr* S, double tau, const ifac_opts* opts, ifac_bsr* Z,
@@ -427,7 +432,7 @@ int inv_factor_rinch(ifac_ctx* ctx, const ifac_bsr* S, double tau, const ifac_op
  * product of a sweep serves all of them.  Each member has its own Gershgorin
  * bound, Z_0 = c_k I, ||delta||_F and stop test (target, the rule of Section
  * 2.2, or max_iter); a stopped member leaves the batch.  With opts->prec
- * TF32/BF16 (tensor cores, bs = 64) every member follows the mixed-precision
+ * TF32/BF16 (tensor cores, bs 32, 64 or 128) every member follows the mixed-precision
  * schedule of inv_factor_refine: low-precision sweeps until its floor, then
  * delta with FP64-accurate products (opts->delta_prec) and M in opts->prec
  * until the target or until ||delta||_F stops falling.  The final residual

@@ -193,12 +193,12 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       IFAC_CK(cudaStreamSynchronize(ctx->stream));  // the host flags are reused below
     }
     const int pd = stage == 0 ? o.prec : dprec;
-    bool all_slices = false;
+    bool all_slices = false, slices_fixed = false;
     for (int it = 0;; ++it) {
       // split evaluations take as many slices as the active member that needs
       // the most (from its last ||delta||_F)
       int ns = ctx->split_slices;
-      if (pd == IFAC_FP64_SPLIT && !all_slices) {
+      if (pd == IFAC_FP64_SPLIT && !all_slices && !slices_fixed) {
         ns = 3;
         for (int k = 0; k < count; ++k)
           if (active[k])
@@ -223,14 +223,25 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       node_fro(ctx, D.m, dnb0.p, dnb1.p, count, ne.p);
       to_host(ctx, e.data(), ne.p, sizeof(double) * count);
       if (ns < ctx->split_slices) {
-        // a member's delta far below its predicted size, or at the target
-        // (a stop must not rest on fewer slices): evaluate again with all
-        // slices
-        bool redo = false;
-        for (int k = 0; k < count; ++k)
-          if (active[k] && (split_delta_error(ns, (int64_t)(nb1[k] - nb0[k]) * bs) > delta_need(e[k], target, u) ||
-                            e[k] <= target))
+        // a member's delta far below its predicted size, at the target (a
+        // stop must not rest on fewer slices), or stalling (the sweeps then
+        // converge toward the s-slice evaluation's own error, kStallRatio):
+        // evaluate again with all slices; after a stall every evaluation of
+        // the stage takes all of them and the comparison restarts
+        bool redo = false, stall = false;
+        for (int k = 0; k < count; ++k) {
+          if (!active[k]) continue;
+          const bool st = stage == 1 && e[k] > kStallRatio * e_prev[k];
+          stall = stall || st;
+          if (split_delta_error(ns, (int64_t)(nb1[k] - nb0[k]) * bs) > delta_need(e[k], target, u) ||
+              e[k] <= target || st)
             redo = true;
+        }
+        if (stall) {
+          slices_fixed = true;
+          for (int k = 0; k < count; ++k)
+            if (active[k]) e_prev[k] = INFINITY;
+        }
         if (redo) {
           all_slices = true;
           --it;

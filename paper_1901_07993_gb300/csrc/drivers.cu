@@ -214,7 +214,7 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
   const double c = (o.c_rule == 1) ? std::sqrt(2.0 / beta) : 1.0 / std::sqrt(beta);
   Mat Z = scaled_identity(ctx, S.m.n, S.m.bs, S.m.nb, c);
   if (rep) rep->beta = beta;
-  bool fp64_phase = false, all_slices = false;
+  bool fp64_phase = false, all_slices = false, slices_fixed = false;
   double e_prev = INFINITY, e = 0.0, e_pred = INFINITY;
   const double u = unit_roundoff(low);
   // S's converted copies serve every X = S Z of the refinement
@@ -225,8 +225,9 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
     const int dprec = fp64_phase ? delta_prec_of(o, S.m.bs) : low;
     // split evaluations take as many slices as this delta needs (predicted
     // from the last one)
-    const int ns = (dprec == IFAC_FP64_SPLIT && !all_slices) ? delta_slices(ctx, e_pred, target, u, S.m.n)
-                                                             : ctx->split_slices;
+    const int ns = (dprec == IFAC_FP64_SPLIT && !all_slices && !slices_fixed)
+                       ? delta_slices(ctx, e_pred, target, u, S.m.n)
+                       : ctx->split_slices;
     Mat D;
     {
       SlicesScope scope(ctx, ns);
@@ -241,12 +242,18 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
               : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     }
     e = fro_host(ctx, D.m);
+    const bool stall = fp64_phase && e > kStallRatio * e_prev;
     if (dprec == IFAC_FP64_SPLIT && ns < ctx->split_slices &&
-        (split_delta_error(ns, S.m.n) > delta_need(e, target, u) || e <= target)) {
+        (split_delta_error(ns, S.m.n) > delta_need(e, target, u) || e <= target || stall)) {
       // delta came out below its predicted size, past what this many slices
       // resolve, or at the target, where the stop must not rest on fewer
       // slices (on dense operands the error of an s-slice evaluation is far
-      // above the chain-derived estimate): evaluate it again with all of them
+      // above the chain-derived estimate), or it stalls: evaluate it again
+      // with all of them; after a stall the comparison restarts
+      if (stall) {
+        slices_fixed = true;
+        e_prev = INFINITY;
+      }
       all_slices = true;
       --it;
       continue;

@@ -248,6 +248,14 @@ double split_delta_error(int slices, int64_t n);
 // the accuracy a delta evaluation of the mixed schedule needs when
 // ||delta||_F = e: a tenth of what the next low-precision sweep leaves
 double delta_need(double e, double target, double u);
+// In the FP64 phase a sweep reduces ||delta||_F by about u (below 1e-2 for
+// TF32 and BF16 on every input measured), so a ratio above this one means the
+// sweeps now converge toward the zero of the s-slice evaluation, which errs
+// by its own error: on block-dense factors far above split_delta_error
+// (n = 8192, 3D cluster, TF32: seven slices leave ||I - Z^T S Z||_F at 6e-10
+// while they evaluate it as 1.4e-10).  From there on every evaluation takes
+// all slices.
+constexpr double kStallRatio = 0.25;
 // slices for an evaluation whose ||delta||_F is predicted at e_pred
 int delta_slices(const ifac_ctx* ctx, double e_pred, double target, double u, int64_t n);
 // sets the context's split slice count for the scope's lifetime
