@@ -443,13 +443,14 @@ def kernel_rooflines(reps, bs, prec, traffic=None):
     """Live CUDA-event rooflines of the block-product kernels.
 
     Work per kernel is the method's (2 bs^3 flops per multiplied stored block
-    pair; zero blocks inside tiles and split slice pairs are not counted) and
-    its algorithmic bytes as the library reports them (every operand block
-    read once at the width the kernel reads it, every result block written
-    once).  The bound is the roofline that binds at that arithmetic
-    intensity: HBM (measured copy bandwidth) below the ridge point, the
-    tensor (TF32/BF16, split: BF16) or FP64 peak above it; both fractions are
-    given.  `traffic` maps a kernel key to (DRAM bytes per launch, source)
+    pair; zero blocks inside tiles are not counted; for the split kernel the
+    tensor work is its BF16 slice products, s (s + 1) / 2 per block pair at
+    s slices, and the FP64-equivalent rate is given beside it) and its
+    algorithmic bytes as the library reports them (every operand block read
+    once at the width the kernel reads it, every result block written once).
+    The bound is the roofline that binds at that arithmetic intensity: HBM
+    (measured copy bandwidth) below the ridge point, the tensor (TF32/BF16,
+    split: BF16) or FP64 peak above it; both fractions are given.  `traffic` maps a kernel key to (DRAM bytes per launch, source)
     from an ncu capture of the same kernel and workload; kernels without one
     report null."""
     out = {}
@@ -465,6 +466,9 @@ def kernel_rooflines(reps, bs, prec, traffic=None):
             continue
         launches = sum(getattr(r, launch_f) for r in reps)
         flops = sum(getattr(r, pairs_f) for r in reps) * fl
+        fp64_equiv = flops / (ms / 1e3) / 1e12
+        if key == "split":
+            flops = sum(r.split_slice_pairs for r in reps) * fl
         nbytes = sum(getattr(r, bytes_f) for r in reps)
         tflops = flops / (ms / 1e3) / 1e12
         gbs = nbytes / (ms / 1e3) / 1e9
@@ -495,9 +499,10 @@ def kernel_rooflines(reps, bs, prec, traffic=None):
         if key == "split":
             e["slice_pairs_per_block_pair"] = sum(r.split_slice_pairs for r in reps) / max(
                 sum(r.split_pairs for r in reps), 1)
-            e["bf16_slice_tflops"] = sum(r.split_slice_pairs for r in reps) * fl / (ms / 1e3) / 1e12
-            e["note"] = ("flops are the FP64 product's 2 bs^3 per stored block pair; the BF16 slice products "
-                         "(s (s + 1) / 2 per block pair) are bf16_slice_tflops")
+            e["bf16_slice_tflops"] = tflops
+            e["fp64_equivalent_tflops"] = fp64_equiv
+            e["note"] = ("flops are the BF16 slice products (2 bs^3 per slice pair); fp64_equivalent_tflops "
+                         "counts the FP64 product's 2 bs^3 per stored block pair")
         if e["traffic"] is not None:
             e["traffic_unit"] = "bytes per launch"
             e["traffic_source"] = traffic[key][1]

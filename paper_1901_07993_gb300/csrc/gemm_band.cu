@@ -79,8 +79,7 @@ struct BandLpArgs {
   const int32_t* tile_nk;   // device: K steps of each tile
   const int32_t* rec;       // plan: per K step, copy indices of the tile's op(A)_IK and op(B)_KJ
   const int32_t* rec_off;   // first record of each tile
-  const int32_t* crp;       // C pattern
-  const int32_t* cci;
+  const int32_t* cpos;      // per tile, the C positions of its TMB x TNB blocks (-1: not in C)
   double* cval;
   double* cnorm;
   int nb;
@@ -102,6 +101,7 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
   __shared__ volatile int abort_flag;
   __shared__ double partial[4][2];
   __shared__ float ep_stage[NEPI][32 * 17];
+  __shared__ int32_t srec[32 * L::RECW];  // the producer's current chunk of plan records
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -133,16 +133,27 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t issued_mask = 0, last_parity = 0;  // stages filled / parity of their last fill
-      bool ok = true;
-      for (int it = 0; it < mt && ok; ++it) {
-        const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        const int nk = args.tile_nk[t];
-        const int32_t* r = args.rec + (size_t)args.rec_off[t] * L::RECW;
-        for (int j = 0; j < nk && ok; ++j, r += L::RECW) {
+    // the warp loads the next chunk of plan records while lane 0 issues the
+    // copies of the current one
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t issued_mask = 0, last_parity = 0;  // stages filled / parity of their last fill
+    bool ok = true;
+    RecStream<L::RECW> rs;
+    rs.init(args.rec, args.rec_off, args.tile_nk, (int)blockIdx.x, (int)gridDim.x, mt, 1);
+    int32_t cur[L::RECW], nxt[L::RECW];
+    int c_it, c_rep, c_j0, c_cnt, n_it, n_rep, n_j0, n_cnt;
+    bool have = rs.next(lane, cur, c_it, c_rep, c_j0, c_cnt);
+    while (have && ok) {
+      if (lane < c_cnt) {
+#pragma unroll
+        for (int w = 0; w < L::RECW; ++w) srec[lane * L::RECW + w] = cur[w];
+      }
+      __syncwarp();
+      const bool nhave = rs.next(lane, nxt, n_it, n_rep, n_j0, n_cnt);
+      if (lane == 0) {
+        for (int j = 0; j < c_cnt && ok; ++j) {
+          const int32_t* r = srec + j * L::RECW;
           for (int c = 0; c < L::KCH; ++c) {
             if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, args.err)) {
               ok = false;
@@ -170,23 +181,35 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
           }
         }
       }
-      // before the CTA exits: the copies issued have landed and the MMAs have
-      // released every stage
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();  // srec is rewritten next round
+#pragma unroll
+      for (int w = 0; w < L::RECW; ++w) cur[w] = nxt[w];
+      c_it = n_it;
+      c_rep = n_rep;
+      c_j0 = n_j0;
+      c_cnt = n_cnt;
+      have = nhave;
+    }
+    // before the CTA exits: the copies issued have landed and the MMAs have
+    // released every stage
+    if (lane == 0)
       for (int s = 0; s < L::STAGES; ++s)
         if (issued_mask & (1u << s)) {
           mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
           mbar_wait(smem_u32(&empty_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
         }
-    }
   } else if (warp == MMA_WARP) {
     // ------------------------------ MMA issuer ------------------------------
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      int nk_next = mt > 0 ? args.tile_nk[blockIdx.x] : 0;  // loaded a tile ahead
       for (int it = 0; it < mt && ok; ++it) {
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        const int nk = args.tile_nk[t];
+        const int nk = nk_next;
+        if (it + 1 < mt) nk_next = args.tile_nk[t + (int)gridDim.x];
         const int ab = it & 1;
         const uint32_t aphase = (uint32_t)(it >> 1) & 1u;
         const uint32_t tacc = tmem + (uint32_t)(ab * N);
@@ -231,17 +254,24 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
     const int cb = (half * HALF) / BS;       // block column (a warp's columns lie in one)
     const int et = threadIdx.x - 32 * EPI0;  // 0 .. 32 NEPI - 1
     const float alpha_f = (float)args.alpha;
+    // C positions of this warp's block and (threads et < TMB TNB) of the block
+    // whose norm it writes, loaded a tile ahead
+    constexpr int CP = TMB * TNB;
+    int p_next = -1, kn_next = -1;
+    if (mt > 0) {
+      p_next = args.cpos[(size_t)blockIdx.x * CP + rb * TNB + cb];
+      if (et < CP) kn_next = args.cpos[(size_t)blockIdx.x * CP + et];
+    }
     for (int it = 0; it < mt; ++it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
       const int ab = it & 1;
       const uint32_t aphase = (uint32_t)(it >> 1) & 1u;
-      const int I0 = args.tiles[2 * t] * TMB, J0 = args.tiles[2 * t + 1] * TNB;
-      const int I = I0 + rb, J = J0 + cb;
-      int p = -1;  // position of C_IJ in C
-      if (I < args.nb && J < args.nb) {
-        const int lo = args.crp[I], hi = args.crp[I + 1];
-        const int k = lower_bound_i32(args.cci, lo, hi, J);
-        if (k < hi && args.cci[k] == J) p = k;
+      const int p = p_next;  // position of this warp's block of C (-1: not in C)
+      const int kn = kn_next;
+      if (it + 1 < mt) {
+        const size_t tn = (size_t)(t + (int)gridDim.x) * CP;
+        p_next = args.cpos[tn + rb * TNB + cb];
+        if (et < CP) kn_next = args.cpos[tn + et];
       }
       const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
       if (!epi_all<32 * NEPI>(got)) break;  // all epilogue warps go on, or all stop
@@ -257,18 +287,21 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
           for (int e = 0; e < 32; ++e) v[e] *= alpha_f;
           sq.add32(v);
           // 32 rows x 16 columns at a time through shared memory, so that each
-          // store instruction writes two row segments
+          // store instruction writes four row segments, two values per lane
           float* sw = ep_stage[ew];
           double* blk = args.cval + (size_t)p * BS * BS + (size_t)rin * BS + (col0 % BS);
-          const int cc = lane & 15, rr = lane >> 4;
+          const int c2 = (lane & 7) * 2, r4 = lane >> 3;
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) sw[lane * 17 + e] = v[hh * 16 + e];
             __syncwarp();
 #pragma unroll 4
-            for (int k = 0; k < 32; k += 2)
-              blk[(size_t)(k + rr) * BS + hh * 16 + cc] = f32_to_f64(sw[(k + rr) * 17 + cc]);
+            for (int k = 0; k < 32; k += 4) {
+              const float* q = sw + (k + r4) * 17 + c2;
+              *reinterpret_cast<double2*>(blk + (size_t)(k + r4) * BS + hh * 16 + c2) =
+                  make_double2(f32_to_f64(q[0]), f32_to_f64(q[1]));
+            }
             __syncwarp();
           }
         }
@@ -281,20 +314,13 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
       epi_bar<32 * NEPI>();
       // norms: block (br, bc) of the tile sums the warps of its lane quarters
       // and column halves, in a fixed order
-      if (et < TMB * TNB) {
+      if (et < CP && kn >= 0) {
         const int br = et / TNB, bc = et % TNB;
-        const int Ib = I0 + br, Jb = J0 + bc;
-        if (Ib < args.nb && Jb < args.nb) {
-          const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
-          const int k = lower_bound_i32(args.cci, lo, hi, Jb);
-          if (k < hi && args.cci[k] == Jb) {
-            double s = 0.0;
-            for (int qq = 0; qq < 4; ++qq)
-              for (int h = 0; h < 2; ++h)
-                if ((qq * 32) / BS == br && (h * HALF) / BS == bc) s += partial[qq][h];
-            args.cnorm[k] = sqrt(s);
-          }
-        }
+        double s = 0.0;
+        for (int qq = 0; qq < 4; ++qq)
+          for (int h = 0; h < 2; ++h)
+            if ((qq * 32) / BS == br && (h * HALF) / BS == bc) s += partial[qq][h];
+        args.cnorm[kn] = sqrt(s);
       }
       epi_bar<32 * NEPI>();
       if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
@@ -336,15 +362,14 @@ static void shape_of(BandShape* s) {
 // the host entry used by gemm_tc.cu's dispatcher
 void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const void* mapB, const int32_t* tiles,
                      const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
-                     int tiles_bound, double alpha, ifac_bsr& C) {
+                     const int32_t* cpos, int tiles_bound, double alpha, ifac_bsr& C) {
   tc::BandLpArgs a{};
   a.tiles = tiles;
   a.ntiles = ntiles;
   a.tile_nk = tile_nk;
   a.rec = rec;
   a.rec_off = rec_off;
-  a.crp = C.row_ptr;
-  a.cci = C.col_idx;
+  a.cpos = cpos;
   a.cval = C.val;
   a.cnorm = C.norms;
   a.nb = C.nb;

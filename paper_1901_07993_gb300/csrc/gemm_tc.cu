@@ -520,6 +520,32 @@ __global__ void k_tile_flags(const int32_t* __restrict__ row, const int32_t* __r
   flag[(size_t)(row[p] / tm) * ntc + ci[p] / tn] = 1;
 }
 
+// Tiles of a sparse C in one pass over its blocks: block p owns its tile
+// (I / tm, J / tn) when the tile holds no earlier block, i.e. neither the block
+// before it in row I nor a block of the tile's earlier rows lies in the tile's
+// column range.  The owners, in C's order, list every tile once.
+__global__ void k_tile_owner(const int32_t* __restrict__ row, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ ci, int64_t nnz, int tm, int tn, int32_t* __restrict__ own) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  const int I = row[p], c0 = (ci[p] / tn) * tn;
+  int o = (p > rp[I] && ci[p - 1] >= c0) ? 0 : 1;
+  for (int I2 = (I / tm) * tm; o && I2 < I; ++I2) {
+    const int hi = rp[I2 + 1];
+    const int q = lower_bound_i32(ci, rp[I2], hi, c0);
+    if (q < hi && ci[q] < c0 + tn) o = 0;
+  }
+  own[p] = o;
+}
+
+__global__ void k_tile_owner_write(const int32_t* __restrict__ row, const int32_t* __restrict__ ci, int64_t nnz,
+                                   int tm, int tn, const int32_t* __restrict__ off, int32_t* __restrict__ out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nnz || off[p + 1] == off[p]) return;
+  out[2 * (size_t)off[p]] = row[p] / tm;
+  out[2 * (size_t)off[p] + 1] = ci[p] / tn;
+}
+
 // Tile compaction in grouped order: linear index li runs over groups of GROUP
 // tile rows, column by column inside a group, so that CTAs running at the same
 // time share op(B) panels in L2.  Three passes: count per chunk, scan, write.
@@ -650,7 +676,10 @@ static EncodeTiledFn encoder() {
 // COLS block columns (the zero block when absent); K steps whose op(B) blocks
 // are all absent contribute nothing and are left out.  One warp per tile,
 // candidate K's 32 at a time, lane-parallel.  COUNT: the number of records
-// into nk[t] (and the largest into *kmax); else the records, from off[t] on.
+// into nk[t] (and the largest into *kmax); else the records, from off[t] on,
+// and (cpos non-null) the position in C's pattern of each of the tile's
+// ROWS x COLS blocks (-1 where C holds none), so that a product's epilogue
+// finds its output blocks with one load instead of a search.
 template <int ROWS, int COLS, bool COUNT>
 __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __restrict__ ntiles,
                             const int32_t* __restrict__ off, const uint32_t* __restrict__ bm, int nb, int W,
@@ -658,7 +687,9 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
                             const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                             const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, int a_zero, int b_zero,
                             const int32_t* __restrict__ amap, int32_t* __restrict__ rec, int32_t* __restrict__ nk_out,
-                            int* __restrict__ kmax) {
+                            int* __restrict__ kmax, const int32_t* __restrict__ crp = nullptr,
+                            const int32_t* __restrict__ cci = nullptr, int32_t* __restrict__ cpos = nullptr) {
+  static_assert(ROWS * COLS <= 32, "one lane per block of the tile");
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= *ntiles) {  // the grid covers an upper bound of the tile count
@@ -666,6 +697,16 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
     return;
   }
   const int I0 = tiles[2 * t] * ROWS, J0 = tiles[2 * t + 1] * COLS;
+  if (!COUNT && cpos && lane < ROWS * COLS) {
+    const int I = I0 + lane / COLS, J = J0 + lane % COLS;
+    int pos = -1;
+    if (I < nb && J < nb) {
+      const int hi = crp[I + 1];
+      const int q = lower_bound_i32(cci, crp[I], hi, J);
+      if (q < hi && cci[q] == J) pos = q;
+    }
+    cpos[(size_t)t * (ROWS * COLS) + lane] = pos;
+  }
   int e = COUNT ? 0 : off[t];
   for (int wbase = 0; wbase < W; wbase += 32) {
     const int w = wbase + lane;
@@ -734,7 +775,7 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
 // The tile plan of a product: super-tiles of ROWS x COLS blocks holding a
 // block of C's pattern (grouped order), their K-step counts and records.
 struct Plan {
-  Buf<int32_t> tiles, coff, tnk, off, rec;
+  Buf<int32_t> tiles, coff, tnk, off, rec, cpos;  // cpos: C positions of each tile's blocks
   int nchunk = 0;
   int64_t ntot = 0;
   int ntiles = 0;  // upper bound of the tile count (the count itself stays on the device)
@@ -774,19 +815,38 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
   }
   const int ntr = cdiv(nb, ROWS), ntc = cdiv(nb, COLS);
   P.ntot = (int64_t)ntr * ntc;
-  P.nchunk = cdiv(P.ntot, CHUNK);
-  Buf<uint8_t> flags(ctx, (size_t)P.ntot);
-  Buf<int32_t> ccnt(ctx, P.nchunk);
-  P.tiles = Buf<int32_t>(ctx, (size_t)2 * P.ntot);
-  P.coff = Buf<int32_t>(ctx, P.nchunk + 1);
-  IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)P.ntot, ctx->stream));
-  k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, ROWS, COLS, ntc, flags.p);
-  IFAC_CK_LAUNCH();
-  k_tile_count<<<P.nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
-  IFAC_CK_LAUNCH();
-  scan_counts(ctx, ccnt.p, P.coff.p, P.nchunk, false);
-  k_tile_write<<<P.nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, P.coff.p, P.tiles.p);
-  IFAC_CK_LAUNCH();
+  if ((int64_t)C.nnzb * 16 < P.ntot) {
+    // a sparse C (a banded product): its tiles from its blocks, in C's order
+    P.nchunk = (int)C.nnzb;
+    P.tiles = Buf<int32_t>(ctx, (size_t)2 * std::max<int64_t>(C.nnzb, 1));
+    P.coff = Buf<int32_t>(ctx, (size_t)C.nnzb + 1);
+    Buf<int32_t> own(ctx, (size_t)std::max<int64_t>(C.nnzb, 1));
+    if (C.nnzb) {
+      k_tile_owner<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.row_ptr, C.col_idx, C.nnzb, ROWS, COLS,
+                                                               own.p);
+      IFAC_CK_LAUNCH();
+    }
+    scan_counts(ctx, own.p, P.coff.p, (int)C.nnzb, false);
+    if (C.nnzb) {
+      k_tile_owner_write<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, ROWS, COLS,
+                                                                     P.coff.p, P.tiles.p);
+      IFAC_CK_LAUNCH();
+    }
+  } else {
+    P.nchunk = cdiv(P.ntot, CHUNK);
+    Buf<uint8_t> flags(ctx, (size_t)P.ntot);
+    Buf<int32_t> ccnt(ctx, P.nchunk);
+    P.tiles = Buf<int32_t>(ctx, (size_t)2 * P.ntot);
+    P.coff = Buf<int32_t>(ctx, P.nchunk + 1);
+    IFAC_CK(cudaMemsetAsync(flags.p, 0, (size_t)P.ntot, ctx->stream));
+    k_tile_flags<<<cdiv(C.nnzb, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, ROWS, COLS, ntc, flags.p);
+    IFAC_CK_LAUNCH();
+    k_tile_count<<<P.nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, ccnt.p);
+    IFAC_CK_LAUNCH();
+    scan_counts(ctx, ccnt.p, P.coff.p, P.nchunk, false);
+    k_tile_write<<<P.nchunk, CHUNK, 0, ctx->stream>>>(flags.p, ntr, ntc, P.coff.p, P.tiles.p);
+    IFAC_CK_LAUNCH();
+  }
   const int* ntiles = P.coff.p + P.nchunk;
   // the per-tile kernels and arrays are sized by a bound of the tile count
   // (every tile holds a block of C), not by all ntr x ntc positions
@@ -826,10 +886,12 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
     fail(IFAC_ERR_TOO_LARGE, "tensor-core product: tile plan exceeds 2^31 entries");
   if (want_kmax && kmax_limit > 0 && P.kmax > kmax_limit) return P;
   P.rec = Buf<int32_t>(ctx, (size_t)std::max<int64_t>(total, 1) * (ROWS + COLS));
+  P.cpos = Buf<int32_t>(ctx, (size_t)std::max(nt, 1) * (ROWS * COLS));
   if (nt > 0) {
     k_tile_plan<ROWS, COLS, false><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
         P.tiles.p, ntiles, P.off.p, bmA.p, nb, W, dense_maps ? imA.p : nullptr, dense_maps ? imB.p : nullptr,
-        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, amap, P.rec.p, nullptr, nullptr);
+        arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, amap, P.rec.p, nullptr, nullptr,
+        C.row_ptr, C.col_idx, P.cpos.p);
     IFAC_CK_LAUNCH();
   }
   // the plan kernel has read the maps and the bitmap before they are freed
@@ -955,7 +1017,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
       const CUtensorMap mapB = make_map_bs(ELT, bs, lb_p, B.nnzb + 1, sh);
       prof_begin(ctx, 1);
       band_lp_product(ctx, ELT, bs, &mapA, &mapB, Pb.tiles.p, Pb.coff.p + Pb.nchunk, Pb.tnk.p, Pb.rec.p, Pb.off.p,
-                      Pb.ntiles, alpha, C);
+                      Pb.cpos.p, Pb.ntiles, alpha, C);
       prof_end(ctx);
       ++ctx->tc_launches;
       return;
@@ -1302,8 +1364,14 @@ __global__ void __launch_bounds__(256) k_split_finish(const int32_t* __restrict_
 // ---------------------------------------------------------------------------
 namespace band {
 constexpr int MAX_U = 8;                    // units live at once: 8 x 64 = 512 columns
+// 16 epilogue warps, four per tensor-memory lane quarter, each on 16 of the
+// tile's 64 columns: the epilogue's adds of the units into the fixed-point
+// sums stand between the MMAs of consecutive tiles (the accumulators hold
+// every unit, so they are not double-buffered), and twice the warps of the
+// other kernels halve that time
+constexpr int EPW = 16;
+constexpr int NTB = 32 * (2 + EPW);
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int RING = 9;                     // slots: one chunk of up to 8 slices plus prefetch
 // FP32 accumulate, A = B = BF16, both K-major, N = 64, M = 128
 constexpr uint32_t IDESC = idesc_of<2, 64, 128>();
 
@@ -1314,18 +1382,28 @@ struct SB {
   static constexpr int TNB = B <= N ? N / B : 1;    // block columns per tile (2, 1, 1)
   static constexpr int NSUB = B > N ? B / N : 1;    // column sub-tiles per block column (1, 1, 2)
   static constexpr int BROWS = B < N ? B : N;       // rows of one op(B) box (32, 64, 64)
+  // K chunks of 64 elements (32 at bs 32); halving them at bs 64 and 128 was
+  // measured slower: the per-slot waits, copies and commits double while the
+  // products stay the same
   static constexpr int KC = B < 64 ? B : 64;        // K elements per chunk
   static constexpr int KCH = B / KC;                // chunks per K block (1, 1, 2)
   static constexpr int ATOM = KC * 2;               // bytes of one BF16 row chunk: one swizzle atom (64 or 128)
-  static constexpr int SLOT_A = M * ATOM;           // one slice of the tile's op(A) rows
-  static constexpr int SLOT_B = N * ATOM;           // one slice of its op(B) columns
-  static constexpr int SLOT_BYTES = SLOT_A + SLOT_B;  // 12, 24, 24 KB (multiples of 1024)
-  static constexpr int SMEM_BYTES = RING * SLOT_BYTES + 1024;
+  static constexpr int SLOT_A = M * ATOM;           // one slice of the tile's op(A) rows: 8, 16, 16 KB
+  static constexpr int SLOT_B = N * ATOM;           // one slice of its op(B) columns: 4, 8, 8 KB
+  static constexpr int MAXS = 8;                    // slices per operand at most
+  // every op(B) slice of a chunk stays in one of two buffers while the op(A)
+  // slices stream through a ring: slice a of op(A) meets slices 0 .. ns-1-a
+  // of op(B), and its slot is released as soon as those products are issued
+  static constexpr int B_BUF = MAXS * SLOT_B;
+  static constexpr int RA_FIT = (216 * 1024 - 2 * B_BUF) / SLOT_A;
+  static constexpr int RA = RA_FIT < 16 ? RA_FIT : 16;  // op(A) ring slots: 16, 5, 5
+  static constexpr int SMEM_BYTES = 2 * B_BUF + RA * SLOT_A + 1024;
   static constexpr int KSTEPS = ATOM / 32;          // MMAs per slice pair and chunk
   static constexpr uint32_t SBO = 8 * ATOM;
   static constexpr uint32_t SWZ = ATOM == 128 ? 2 : 4;
   static constexpr int RECW = TMB + TNB;
-  static_assert(SLOT_BYTES % 1024 == 0, "slots must keep the swizzle alignment");
+  static_assert(SLOT_A % 1024 == 0 && SLOT_B % 1024 == 0, "slots must keep the swizzle alignment");
+  static_assert(RA >= 2, "op(A) ring too shallow");
 };
 }  // namespace band
 
@@ -1335,8 +1413,7 @@ struct BandArgs {
   const int* tile_nk;      // device: K blocks of each tile
   const int32_t* rec;      // plan: per K block, copy indices of the tile's op(A)_IK, then op(B)_KJ
   const int32_t* rec_off;  // first record of each tile
-  const int32_t* crp;      // C pattern
-  const int32_t* cci;
+  const int32_t* cpos;     // per tile, the C positions of its TMB x TNB blocks (-1: not in C)
   double* cval;            // C's values and block norms (FP64)
   double* cnorm;
   const int* sige;         // scale exponents of the scalar rows of op(A) and columns of op(B)
@@ -1350,37 +1427,48 @@ struct BandArgs {
   int slice_rows_b;
   int nunits;
   int unit_sh[band::MAX_U];
-  int npairs;
-  int slot_beg[9];         // pairs issued once slot k has landed: [slot_beg[k], slot_beg[k + 1])
-  int pair_a[MAX_PAIRS], pair_b[MAX_PAIRS], pair_u[MAX_PAIRS];  // slices (0-based) and unit, issue order
-  int rel_beg[9];          // slots released after slot k's MMAs: rel[rel_beg[k] .. rel_beg[k + 1])
-  int rel[8];
+  // Horner groups of units: unit u with unit_step[u] >= 0 enters its group's
+  // 64-bit accumulator as g = (g << unit_step[u]) + x_u (the first unit of a
+  // group, bit u of unit_first, starts it); at the group's last unit (bit u of
+  // unit_last) g is added into the sums at scale 2^unit_sh[u].  A unit with
+  // unit_step[u] < 0 (below the fixed-point scale) is rounded into the sums
+  // on its own.
+  int unit_step[band::MAX_U];
+  uint32_t unit_first, unit_last;
+  int8_t unit_ab[band::SB<64>::MAXS * band::SB<64>::MAXS];  // unit of slice pair (a, b), a + b <= ns - 1
   int* err;
   int* ovf;
 };
 
 template <int B>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(band::NTB, 1)
     k_gemm_split_band(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                       BandArgs args) {
   using namespace band;
   using L = SB<B>;
-  constexpr int N = L::N, TMB = L::TMB, TNB = L::TNB;
+  constexpr int N = L::N, TMB = L::TMB, TNB = L::TNB, RA = L::RA;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[RING], empty_bar[RING];
+  __shared__ __align__(8) uint64_t afull[RA], aempty[RA], bfull[2], bempty[2];
   __shared__ __align__(8) uint64_t acc_full, acc_empty, drain_bar;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
-  __shared__ double partial[4][2];
+  __shared__ double partial[4][EPW / 4];
+  __shared__ int32_t srec[32 * L::RECW];  // the producer's current chunk of plan records
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t bbase = smem_base, abase = smem_base + 2u * (uint32_t)L::B_BUF;
   const int ntiles = *args.ntiles;
+  const int ns = args.ns;
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int s = 0; s < RING; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), 1);
+    for (int s = 0; s < RA; ++s) {
+      mbar_init(smem_u32(&afull[s]), 1);
+      mbar_init(smem_u32(&aempty[s]), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&bfull[s]), 1);
+      mbar_init(smem_u32(&bempty[s]), 1);
     }
     mbar_init(smem_u32(&acc_full), 1);
     mbar_init(smem_u32(&acc_empty), 1);
@@ -1401,60 +1489,106 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
-    if (lane == 0) {
-      int slot = 0;
-      uint32_t phase = 0;
-      uint32_t issued_mask = 0, last_parity = 0;
-      bool ok = true;
-      for (int it = 0; it < mt && ok; ++it) {
-        const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        const int nk = args.tile_nk[t];
-        for (int h = 0; h < L::NSUB && ok; ++h) {
-          const int32_t* r = args.rec + (size_t)args.rec_off[t] * L::RECW;
-          for (int j = 0; j < nk && ok; ++j, r += L::RECW) {
-            for (int c = 0; c < L::KCH && ok; ++c) {
-              for (int k = 0; k < args.ns; ++k) {
-                if (!mbar_wait(smem_u32(&empty_bar[slot]), phase ^ 1u, &abort_flag, args.err)) {
-                  ok = false;
-                  break;
-                }
-                const uint32_t fb = smem_u32(&full_bar[slot]);
-                mbar_expect_tx(fb, (uint32_t)L::SLOT_BYTES);
-                issued_mask |= 1u << slot;
-                last_parity = (last_parity & ~(1u << slot)) | (phase << slot);
-                const uint32_t sa = smem_base + (uint32_t)(slot * L::SLOT_BYTES);
-                const int ya = k * args.slice_rows_a, yb = k * args.slice_rows_b;
+    // the warp loads the next chunk of plan records while lane 0 issues the
+    // copies of the current one (column sub-tile h = the chunk's repetition).
+    // Per K chunk: every op(B) slice into the next buffer, then the op(A)
+    // slices one ring slot each.
+    int slot = 0, bb = 0;
+    uint32_t phase = 0, bphase = 0;
+    uint32_t issued_mask = 0, last_parity = 0, b_issued = 0, b_parity = 0;
+    bool ok = true;
+    RecStream<L::RECW> rs;
+    rs.init(args.rec, args.rec_off, args.tile_nk, (int)blockIdx.x, (int)gridDim.x, mt, L::NSUB);
+    int32_t cur[L::RECW], nxt[L::RECW];
+    int c_it, c_rep, c_j0, c_cnt, n_it, n_rep, n_j0, n_cnt;
+    bool have = rs.next(lane, cur, c_it, c_rep, c_j0, c_cnt);
+    while (have && ok) {
+      if (lane < c_cnt) {
 #pragma unroll
-                for (int i = 0; i < TMB; ++i) tma_load_2d(sa + i * B * L::ATOM, &mapA, c * L::KC, ya + r[i] * B, fb);
+        for (int w = 0; w < L::RECW; ++w) srec[lane * L::RECW + w] = cur[w];
+      }
+      __syncwarp();
+      const bool nhave = rs.next(lane, nxt, n_it, n_rep, n_j0, n_cnt);
+      if (lane == 0) {
+        const int h = c_rep;
+        for (int j = 0; j < c_cnt && ok; ++j) {
+          const int32_t* r = srec + j * L::RECW;
+          for (int c = 0; c < L::KCH && ok; ++c) {
+            if (!mbar_wait(smem_u32(&bempty[bb]), bphase ^ 1u, &abort_flag, args.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fbb = smem_u32(&bfull[bb]);
+            mbar_expect_tx(fbb, (uint32_t)(ns * L::SLOT_B));
+            b_issued |= 1u << bb;
+            b_parity = (b_parity & ~(1u << bb)) | (bphase << bb);
+            const uint32_t sb = bbase + (uint32_t)(bb * L::B_BUF);
+            for (int k = 0; k < ns; ++k) {
+              const int yb = k * args.slice_rows_b;
 #pragma unroll
-                for (int jb = 0; jb < TNB; ++jb)
-                  tma_load_2d(sa + L::SLOT_A + jb * L::BROWS * L::ATOM, &mapB, c * L::KC,
-                              yb + r[TMB + jb] * B + h * N, fb);
-                if (++slot == RING) {
-                  slot = 0;
-                  phase ^= 1u;
-                }
+              for (int jb = 0; jb < TNB; ++jb)
+                tma_load_2d(sb + k * L::SLOT_B + jb * L::BROWS * L::ATOM, &mapB, c * L::KC,
+                            yb + r[TMB + jb] * B + h * N, fbb);
+            }
+            if (++bb == 2) {
+              bb = 0;
+              bphase ^= 1u;
+            }
+            for (int k = 0; k < ns; ++k) {
+              if (!mbar_wait(smem_u32(&aempty[slot]), phase ^ 1u, &abort_flag, args.err)) {
+                ok = false;
+                break;
+              }
+              const uint32_t fb = smem_u32(&afull[slot]);
+              mbar_expect_tx(fb, (uint32_t)L::SLOT_A);
+              issued_mask |= 1u << slot;
+              last_parity = (last_parity & ~(1u << slot)) | (phase << slot);
+              const uint32_t sa = abase + (uint32_t)(slot * L::SLOT_A);
+              const int ya = k * args.slice_rows_a;
+#pragma unroll
+              for (int i = 0; i < TMB; ++i) tma_load_2d(sa + i * B * L::ATOM, &mapA, c * L::KC, ya + r[i] * B, fb);
+              if (++slot == RA) {
+                slot = 0;
+                phase ^= 1u;
               }
             }
           }
         }
       }
-      // the copies issued have landed and the MMAs have released every slot
-      for (int s = 0; s < RING; ++s)
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();  // srec is rewritten next round
+#pragma unroll
+      for (int w = 0; w < L::RECW; ++w) cur[w] = nxt[w];
+      c_it = n_it;
+      c_rep = n_rep;
+      c_j0 = n_j0;
+      c_cnt = n_cnt;
+      have = nhave;
+    }
+    // the copies issued have landed and the MMAs have released every slot
+    if (lane == 0) {
+      for (int s = 0; s < RA; ++s)
         if (issued_mask & (1u << s)) {
-          mbar_wait(smem_u32(&full_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
-          mbar_wait(smem_u32(&empty_bar[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+          mbar_wait(smem_u32(&afull[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+          mbar_wait(smem_u32(&aempty[s]), (last_parity >> s) & 1u, &abort_flag, args.err, false);
+        }
+      for (int s = 0; s < 2; ++s)
+        if (b_issued & (1u << s)) {
+          mbar_wait(smem_u32(&bfull[s]), (b_parity >> s) & 1u, &abort_flag, args.err, false);
+          mbar_wait(smem_u32(&bempty[s]), (b_parity >> s) & 1u, &abort_flag, args.err, false);
         }
     }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer ------------------------------
     if (lane == 0) {
-      int slot = 0;  // ring position of the next slot to consume
-      uint32_t phase = 0, acc_phase = 0;
+      int slot = 0, bb = 0;  // ring position of the next op(A) slot, op(B) buffer
+      uint32_t phase = 0, bphase = 0, acc_phase = 0;
       bool ok = true;
+      int nk_next = mt > 0 ? args.tile_nk[blockIdx.x] : 0;  // loaded a tile ahead
       for (int it = 0; it < mt && ok; ++it) {
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        const int nk = args.tile_nk[t];
+        const int nk = nk_next;
+        if (it + 1 < mt) nk_next = args.tile_nk[t + (int)gridDim.x];
         for (int h = 0; h < L::NSUB && ok; ++h) {
           for (int w0 = 0; w0 < nk && ok; w0 += args.kwin) {
             const int w1 = min(nk, w0 + args.kwin);
@@ -1467,37 +1601,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint32_t started = 0;  // units whose accumulator holds this window's sum
             for (int j = w0; j < w1 && ok; ++j) {
               for (int c = 0; c < L::KCH && ok; ++c) {
-                const int base = slot;  // position of slice 0 of this chunk
-                for (int k = 0; k < args.ns; ++k) {
-                  if (!mbar_wait(smem_u32(&full_bar[slot]), phase, &abort_flag, args.err)) {
+                if (!mbar_wait(smem_u32(&bfull[bb]), bphase, &abort_flag, args.err)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint32_t sb = bbase + (uint32_t)(bb * L::B_BUF);
+                for (int a = 0; a < ns; ++a) {
+                  if (!mbar_wait(smem_u32(&afull[slot]), phase, &abort_flag, args.err)) {
                     ok = false;
                     break;
                   }
                   tc_fence_after();
-                  for (int q = args.slot_beg[k]; q < args.slot_beg[k + 1]; ++q) {
-                    int pa = base + args.pair_a[q], pb = base + args.pair_b[q];
-                    if (pa >= RING) pa -= RING;
-                    if (pb >= RING) pb -= RING;
-                    const int u = args.pair_u[q];
-                    const uint32_t sa = smem_base + (uint32_t)(pa * L::SLOT_BYTES);
-                    const uint32_t sb = smem_base + (uint32_t)(pb * L::SLOT_BYTES + L::SLOT_A);
+                  const uint32_t sa = abase + (uint32_t)(slot * L::SLOT_A);
+                  for (int b = 0; b < ns - a; ++b) {
+                    const int u = args.unit_ab[a * L::MAXS + b];
                     const uint32_t tacc = tmem + (uint32_t)(u * N);
+                    const uint32_t sbb = sb + (uint32_t)(b * L::SLOT_B);
 #pragma unroll
                     for (int kk = 0; kk < L::KSTEPS; ++kk)
                       mma_kstep<2>(tacc, smem_desc_sw(sa + kk * 32, L::SBO, L::SWZ),
-                                   smem_desc_sw(sb + kk * 32, L::SBO, L::SWZ), IDESC,
+                                   smem_desc_sw(sbb + kk * 32, L::SBO, L::SWZ), IDESC,
                                    (((started >> u) & 1u) || kk > 0) ? 1u : 0u);
                     started |= 1u << u;
                   }
-                  for (int e = args.rel_beg[k]; e < args.rel_beg[k + 1]; ++e) {
-                    int pr = base + args.rel[e];
-                    if (pr >= RING) pr -= RING;
-                    mma_commit(smem_u32(&empty_bar[pr]));
-                  }
-                  if (++slot == RING) {
+                  mma_commit(smem_u32(&aempty[slot]));  // op(A) slice a is used up
+                  if (++slot == RA) {
                     slot = 0;
                     phase ^= 1u;
                   }
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&bempty[bb]));  // the chunk's op(B) slices are used up
+                if (++bb == 2) {
+                  bb = 0;
+                  bphase ^= 1u;
                 }
               }
             }
@@ -1513,52 +1651,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ------------------------------ epilogue ------------------------------
+    constexpr int CW = N / (EPW / 4);        // columns per warp (16)
     const int q = warp & 3;                  // tensor-memory lane quarter
-    const int half = (warp - 2) >> 2;        // columns 32 half .. 32 half + 31 of the tile
+    const int cg = (warp - 2) >> 2;          // columns CW cg .. CW cg + CW - 1 of the tile
     const int rb = (q * 32) / B;             // block row of the tile (a warp's rows lie in one)
     const int rin = (q * 32) % B + lane;     // this thread's row within that block
-    const int cb = (half * 32) / B;          // block column of the tile (at bs <= 64)
+    const int cb = (cg * CW) / B;            // block column of the tile (at bs <= 64)
     const int et = threadIdx.x - 64;
     uint32_t acc_phase = 0;
     const bool unit = (args.am == 1.0 || args.am == -1.0), neg = args.am < 0.0;
     bool good = true;
+    // the tile's K-step count, its block coordinates, and the C positions of
+    // this warp's block and (threads et < TMB TNB) of the block whose norm it
+    // writes, loaded a tile ahead
+    constexpr int CP = TMB * TNB;
+    int nk_n = 0, ti_n = 0, tj_n = 0, p_n = -1, kn_n = -1;
+    const auto load_next = [&](int tn) {
+      nk_n = args.tile_nk[tn];
+      ti_n = args.tiles[2 * tn];
+      tj_n = args.tiles[2 * tn + 1];
+      p_n = args.cpos[(size_t)tn * CP + rb * TNB + cb];
+      if (et < CP) kn_n = args.cpos[(size_t)tn * CP + et];
+    };
+    if (mt > 0) load_next((int)blockIdx.x);
     for (int it = 0; it < mt && good; ++it) {
       const int t = (int)blockIdx.x + it * (int)gridDim.x;
-      const int nk = args.tile_nk[t];
-      const int I0 = args.tiles[2 * t] * TMB, J0 = args.tiles[2 * t + 1] * TNB;
+      const int nk = nk_n;
+      const int I0 = ti_n * TMB, J0 = tj_n * TNB;
       const int I = I0 + rb, J = J0 + cb;
-      int p = -1;  // position of C_IJ in C (warp-uniform)
-      if (I < args.nb && J < args.nb) {
-        const int lo = args.crp[I], hi = args.crp[I + 1];
-        const int k = lower_bound_i32(args.cci, lo, hi, J);
-        if (k < hi && args.cci[k] == J) p = k;
-      }
+      const int p = p_n;  // position of C_IJ in C (warp-uniform; -1: not in C)
+      const int kn = kn_n;
+      if (it + 1 < mt) load_next(t + (int)gridDim.x);
       double ss = 0.0;  // this thread's squares over the tile's column sub-tiles
       for (int h = 0; h < L::NSUB && good; ++h) {
-        const int cin = (h * N + half * 32) % B;  // first column of this warp within block J
-        long long s[32];
+        const int cin = (h * N + cg * CW) % B;  // first column of this warp within block J
+        long long s[CW];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) s[e] = 0;
+        for (int e = 0; e < CW; ++e) s[e] = 0;
         bool bad = false;
         for (int w0 = 0; w0 < nk; w0 += args.kwin) {
           const bool got = mbar_wait(smem_u32(&acc_full), acc_phase, &abort_flag, args.err);
           acc_phase ^= 1u;
-          if (!epi_all<32 * NEPI>(got)) {  // all epilogue warps go on, or all stop
+          if (!epi_all<32 * EPW>(got)) {  // all epilogue warps go on, or all stop
             good = false;
             break;
           }
           tc_fence_after();
-#pragma unroll 1
-          for (int u = 0; u < args.nunits; ++u) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * N + half * 32), v);
-            const int sh = args.unit_sh[u];
+          // units of equal or adjacent weight combine in 64-bit Horner
+          // groups first, so a group costs one checked shift-and-add into
+          // the sums instead of one per unit (8 columns at a time)
 #pragma unroll
-            for (int e = 0; e < 32; ++e) s[e] = fixed_add(s[e], __float2int_rn(v[e]), sh, bad);
+          for (int hf = 0; hf < CW / 8; ++hf) {
+            long long g[8];
+#pragma unroll 1
+            for (int u = 0; u < args.nunits; ++u) {
+              float v[8];
+              tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * N + cg * CW + hf * 8), v);
+              const int sh = args.unit_sh[u], st = args.unit_step[u];
+              if (st < 0) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) s[hf * 8 + e] = fixed_add(s[hf * 8 + e], __float2int_rn(v[e]), sh, bad);
+              } else {
+                if ((args.unit_first >> u) & 1u) {
+#pragma unroll
+                  for (int e = 0; e < 8; ++e) g[e] = (long long)__float2int_rn(v[e]);
+                } else {
+#pragma unroll
+                  for (int e = 0; e < 8; ++e)
+                    g[e] = (long long)((unsigned long long)g[e] << st) + (long long)__float2int_rn(v[e]);
+                }
+                if ((args.unit_last >> u) & 1u) {
+#pragma unroll
+                  for (int e = 0; e < 8; ++e) s[hf * 8 + e] = fixed_add64(s[hf * 8 + e], g[e], sh, bad);
+                }
+              }
+            }
           }
           // the accumulators are read: the next window's MMAs may overwrite them
           tc_fence_before();
-          epi_bar();
+          epi_bar<32 * EPW>();
           if (et == 0) mbar_arrive(smem_u32(&acc_empty));
         }
         if (!good) break;
@@ -1569,7 +1740,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int* tj = args.taue + (size_t)J * B + cin;
           double* dst = args.cval + (size_t)p * B * B + (size_t)rin * B + cin;
 #pragma unroll
-          for (int e = 0; e < 32; e += 2) {
+          for (int e = 0; e < CW; e += 2) {
             const long long x0 = (unit && neg) ? -s[e] : s[e], x1 = (unit && neg) ? -s[e + 1] : s[e + 1];
             double v0 = i64_ldexp(x0, er + tj[e]), v1 = i64_ldexp(x1, er + tj[e + 1]);
             if (!unit) {
@@ -1586,26 +1757,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!good) break;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) partial[q][half] = ss;
-      epi_bar();
+      if (lane == 0) partial[q][cg] = ss;
+      epi_bar<32 * EPW>();
       // norms: block (br, bc) of the tile sums the warps of its lane quarters
-      // and column halves, in a fixed order
-      if (et < TMB * TNB) {
+      // and column groups, in a fixed order
+      if (et < CP && kn >= 0) {
         const int br = et / TNB, bc = et % TNB;
-        const int Ib = I0 + br, Jb = J0 + bc;
-        if (Ib < args.nb && Jb < args.nb) {
-          const int lo = args.crp[Ib], hi = args.crp[Ib + 1];
-          const int k = lower_bound_i32(args.cci, lo, hi, Jb);
-          if (k < hi && args.cci[k] == Jb) {
-            double sum = 0.0;
-            for (int qq = 0; qq < 4; ++qq)
-              for (int hh = 0; hh < 2; ++hh)
-                if ((qq * 32) / B == br && (hh * 32) / B == bc) sum += partial[qq][hh];
-            args.cnorm[k] = sqrt(sum);
-          }
-        }
+        double sum = 0.0;
+        for (int qq = 0; qq < 4; ++qq)
+          for (int cc = 0; cc < EPW / 4; ++cc)
+            if ((qq * 32) / B == br && (cc * CW) / B == bc) sum += partial[qq][cc];
+        args.cnorm[kn] = sqrt(sum);
       }
-      epi_bar();
+      epi_bar<32 * EPW>();
     }
   }
   tc_fence_before();
@@ -1670,7 +1834,7 @@ static void launch_split_band(ifac_ctx* ctx, const CUtensorMap& mA, const CUtens
   if (first_on_device(attr, ctx->device))
     IFAC_CK(cudaFuncSetAttribute(k_gemm_split_band<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES));
   const int grid = (int)std::min<int64_t>(std::max(tiles_bound, 1), sms);
-  k_gemm_split_band<B><<<grid, NTHREADS, L::SMEM_BYTES, ctx->stream>>>(mA, mB, ba);
+  k_gemm_split_band<B><<<grid, band::NTB, L::SMEM_BYTES, ctx->stream>>>(mA, mB, ba);
   IFAC_CK_LAUNCH();
 }
 
@@ -1818,8 +1982,7 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     ba.tile_nk = Pb.tnk.p;
     ba.rec = Pb.rec.p;
     ba.rec_off = Pb.off.p;
-    ba.crp = C.row_ptr;
-    ba.cci = C.col_idx;
+    ba.cpos = Pb.cpos.p;
     ba.cval = C.val;
     ba.cnorm = C.norms;
     ba.sige = sige_p;
@@ -1834,30 +1997,45 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     ba.nunits = ut.nunits;
     if (ut.nunits > band::MAX_U) fail(IFAC_ERR_UNSUPPORTED, "split product: too many units for the narrow kernel");
     for (int u = 0; u < ut.nunits; ++u) ba.unit_sh[u] = fbits - SPLIT_BITS * ut.unit_g[u];
-    // issue order: by slot max(a, b); slice r is released after the last
-    // slot whose pairs read it, max(r, ns - 1 - r)
-    ba.npairs = ut.npairs;
-    int q = 0, e = 0;
-    for (int k = 0; k < ns; ++k) {
-      ba.slot_beg[k] = q;
-      for (int p = 0; p < ut.npairs; ++p) {
-        const int a = ut.si[p] - 1, b = ut.ti[p] - 1;
-        if (std::max(a, b) != k) continue;
-        ba.pair_a[q] = a;
-        ba.pair_b[q] = b;
-        ba.pair_u[q] = ut.pu[p];
-        ++q;
+    // Horner groups: consecutive units with shifts >= 0 (descending, so each
+    // step is 0 or 7 bits); a group's value is below ngroup 2^(24 + span),
+    // kept within int64 by a span of at most 35 bits with at most 8 units
+    {
+      ba.unit_first = ba.unit_last = 0u;
+      int start = -1;
+      for (int u = 0; u < ut.nunits; ++u) {
+        const int sh = ba.unit_sh[u];
+        if (sh < 0) {
+          if (start >= 0) ba.unit_last |= 1u << (u - 1);
+          start = -1;
+          ba.unit_step[u] = -1;
+          continue;
+        }
+        if (start >= 0 && ba.unit_sh[start] - sh <= 35) {
+          ba.unit_step[u] = ba.unit_sh[u - 1] - sh;
+        } else {
+          if (start >= 0) ba.unit_last |= 1u << (u - 1);
+          start = u;
+          ba.unit_first |= 1u << u;
+          ba.unit_step[u] = 0;
+        }
       }
-      ba.rel_beg[k] = e;
-      for (int r = 0; r < ns; ++r)
-        if (std::max(r, ns - 1 - r) == k) ba.rel[e++] = r;
+      if (start >= 0) ba.unit_last |= 1u << (ut.nunits - 1);
     }
-    ba.slot_beg[ns] = q;
-    ba.rel_beg[ns] = e;
-    if (q != ut.npairs || e != ns) fail(IFAC_ERR_CUDA, "split product: inconsistent banded issue table");
+    // the unit of each slice pair (a, b) with a + b <= ns - 1 (0-based)
+    for (int k = 0; k < band::SB<64>::MAXS * band::SB<64>::MAXS; ++k) ba.unit_ab[k] = -1;
+    for (int p = 0; p < ut.npairs; ++p) {
+      const int a = ut.si[p] - 1, b = ut.ti[p] - 1;
+      if (a < 0 || b < 0 || a + b > ns - 1) fail(IFAC_ERR_CUDA, "split product: slice pair outside the table");
+      ba.unit_ab[a * band::SB<64>::MAXS + b] = (int8_t)ut.pu[p];
+    }
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns - a; ++b)
+        if (ba.unit_ab[a * band::SB<64>::MAXS + b] < 0)
+          fail(IFAC_ERR_CUDA, "split product: inconsistent banded issue table");
     ba.err = ctx->dev_err;
     ba.ovf = ctx->dev_err;
-    const int kc = bs < 64 ? bs : 64;  // K elements per chunk
+    const int kc = bs < 64 ? bs : 64;  // K elements per chunk (band::SB<bs>::KC)
     const CUtensorMap mA = make_map_box(bs, la_p, (int64_t)ns * (A.nnzb + 1), kc, bs);
     const CUtensorMap mB = make_map_box(bs, lb_p, (int64_t)ns * (B.nnzb + 1), kc, bs < 64 ? bs : 64);
     if (bs == 32) launch_split_band<32>(ctx, mA, mB, ba, Pb.ntiles, sms);

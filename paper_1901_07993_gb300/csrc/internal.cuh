@@ -220,7 +220,7 @@ struct BandShape {
 BandShape band_lp_shape(int elt, int bs);
 void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const void* mapB, const int32_t* tiles,
                      const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
-                     int tiles_bound, double alpha, ifac_bsr& C);
+                     const int32_t* cpos, int tiles_bound, double alpha, ifac_bsr& C);
 // the same matrix with block size bs (32, 64, 128), exact (reblock.cu)
 Mat reblock(ifac_ctx* ctx, const ifac_bsr& A, int bs);
 // block size and bs-64 tile schedule of a batch from timed probe products

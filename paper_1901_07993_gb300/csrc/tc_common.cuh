@@ -142,6 +142,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // FP32 -> FP64 by moving the fields (exact, subnormals normalised; inf and
 // NaN take the conversion instruction), keeping the epilogue off the FP64 pipe
 __device__ __forceinline__ double f32_to_f64(float f) {
@@ -170,6 +193,16 @@ __device__ __forceinline__ long long fixed_add(long long d, int x, int sh, bool&
   } else {
     t = (sh < -30) ? 0 : (long long)((x + (1 << (-sh - 1))) >> (-sh));
   }
+  const long long r = (long long)((unsigned long long)d + (unsigned long long)t);
+  bad |= ((d ^ r) & (t ^ r)) < 0;
+  return r;
+}
+
+// d + (x << sh) for a 64-bit x, sh >= 0, flagging a shift or sum that
+// overflows
+__device__ __forceinline__ long long fixed_add64(long long d, long long x, int sh, bool& bad) {
+  const long long t = (long long)((unsigned long long)x << sh);
+  bad |= (t >> sh) != x;
   const long long r = (long long)((unsigned long long)d + (unsigned long long)t);
   bad |= ((d ^ r) & (t ^ r)) < 0;
   return r;
@@ -242,6 +275,70 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, in
   }
   return lo;
 }
+
+// Plan records streamed to a producer warp.  A CTA's tiles are t0, t0 + tstep,
+// ... (mt of them); each tile's records are visited `reps` times in a row (the
+// column sub-tiles of a split product at bs 128) in chunks of up to 32 K
+// steps.  next() has the 32 lanes load one chunk (lane j: the record of K step
+// j0 + j) into registers and moves on; the producer calls it for the following
+// chunk before lane 0 issues the copies of the current one, so the loads are
+// in flight while lane 0 waits on the ring, and no record load sits on the
+// issue path.  The next tile's K-step count and record offset are loaded as
+// soon as its predecessor's last chunk has been handed out.
+template <int RECW>
+struct RecStream {
+  const int32_t* rec;
+  const int32_t* rec_off;
+  const int32_t* tile_nk;
+  int t0, tstep, mt, reps;
+  int it, rep, j0, nk;  // the next chunk to load, and the K-step count of its tile
+  const int32_t* base;  // first record of tile it
+
+  __device__ __forceinline__ void meta() {
+    if (it < mt) {
+      const int t = t0 + it * tstep;
+      nk = tile_nk[t];
+      base = rec + (size_t)rec_off[t] * RECW;
+    }
+  }
+  __device__ __forceinline__ void init(const int32_t* rec_, const int32_t* rec_off_, const int32_t* tile_nk_, int t0_,
+                                       int tstep_, int mt_, int reps_) {
+    rec = rec_;
+    rec_off = rec_off_;
+    tile_nk = tile_nk_;
+    t0 = t0_;
+    tstep = tstep_;
+    mt = mt_;
+    reps = reps_;
+    it = rep = j0 = nk = 0;
+    base = nullptr;
+    meta();
+  }
+  // false past the last chunk; else the chunk's tile (position it in the
+  // CTA's list), repetition, first K step and record count
+  __device__ __forceinline__ bool next(int lane, int32_t (&v)[RECW], int& c_it, int& c_rep, int& c_j0, int& c_cnt) {
+    if (it >= mt) return false;
+    c_it = it;
+    c_rep = rep;
+    c_j0 = j0;
+    c_cnt = nk - j0 < 32 ? nk - j0 : 32;
+    if (lane < c_cnt) {
+      const int32_t* r = base + (size_t)(j0 + lane) * RECW;
+#pragma unroll
+      for (int w = 0; w < RECW; ++w) v[w] = r[w];
+    }
+    j0 += 32;
+    if (j0 >= nk) {
+      j0 = 0;
+      if (++rep >= reps) {
+        rep = 0;
+        ++it;
+        meta();
+      }
+    }
+    return true;
+  }
+};
 
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   uint32_t r;

@@ -54,17 +54,24 @@ def test_compute_bound_above_the_ridge_point():
     assert k["achieved"] == pytest.approx(want) and k["frac"] == pytest.approx(want / peak)
 
 
-def test_split_counts_the_fp64_products_work():
+def test_split_counts_its_slice_products():
     bs = 64
     # 100 stored pairs, each formed from 28 slice pairs, in 1 ms; FP64 pipe kernel beside it
     reps = [_rep(split_ms=1.0, split_pairs=100, split_slice_pairs=2800, split_launches=1, split_bytes=1e8,
                  gemm_ms=2.0, fp64_pairs=1000, gemm_launches=2, fp64_bytes=1e6)]
     k = bench.kernel_rooflines(reps, bs, "tf32")
     s = k["split"]
-    assert s["tflops"] == pytest.approx(100 * 2 * bs ** 3 / 1e-3 / 1e12)
-    assert s["bf16_slice_tflops"] == pytest.approx(2800 * 2 * bs ** 3 / 1e-3 / 1e12)
+    assert s["fp64_equivalent_tflops"] == pytest.approx(100 * 2 * bs ** 3 / 1e-3 / 1e12)
+    assert s["tflops"] == s["bf16_slice_tflops"] == pytest.approx(2800 * 2 * bs ** 3 / 1e-3 / 1e12)
     assert s["slice_pairs_per_block_pair"] == pytest.approx(28.0)
+    # 1.47e9 slice flops over 1e8 bytes: 14.7 flop/byte, below the BF16 ridge (~284)
     assert s["bound"] == "hbm" and s["achieved"] == pytest.approx(1e8 / 1e-3 / 1e9)
+    # a hundred times fewer bytes (1468 flop/byte): the BF16 peak binds the slice products
+    reps[0].split_bytes = 1e6
+    s = bench.kernel_rooflines(reps, bs, "tf32")["split"]
+    peak, _ = bench.tensor_peak_tflops("bf16")
+    assert s["bound"] == "tensor" and s["achieved"] == pytest.approx(s["bf16_slice_tflops"])
+    assert s["frac"] == pytest.approx(s["bf16_slice_tflops"] / peak)
     f = k["fp64"]  # 1.05e9 flops over 1e6 bytes: far above the FP64 ridge (~0.16)
     assert f["bound"] == "alu" and f["achieved"] == pytest.approx(1000 * 2 * bs ** 3 / 2e-3 / 1e12)
 
