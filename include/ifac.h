@@ -327,10 +327,11 @@ int bsr_reblock(ifac_ctx* ctx, const ifac_bsr* A, int32_t bs, ifac_bsr* out);
 
 /* Tile schedules of the context's bs-64 tensor-core products, one for the
  * TF32/BF16 products (narrow_kmax) and one for the split FP64-accurate ones
- * (narrow_kmax_split): -1 (default) narrow 128 x 64 tiles for products whose
- * longest tile has at most 16 K blocks (split: and fits one exact window),
- * super-tiles for the others; 0 super-tiles for every product; k > 0 narrow
- * tiles for every product whose longest tile has at most k K blocks.
+ * (narrow_kmax_split): -1 (default) narrow 128 x 64 tiles for TF32/BF16
+ * products whose longest tile has at most 16 K blocks and super-tiles for
+ * the others, narrow tiles for every split product; 0 super-tiles for every
+ * product; k > 0 narrow tiles for every product whose longest tile has at
+ * most k K blocks.
  * Results are the same products either way (TF32/BF16 up to FP32 summation
  * order; split products within their error bound).  Products at bs 32 and
  * 128 always use narrow tiles.  IFAC_ERR_INVALID below -1. */

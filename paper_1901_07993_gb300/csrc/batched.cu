@@ -194,6 +194,17 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
     }
     const int pd = stage == 0 ? o.prec : dprec;
     bool all_slices = false, slices_fixed = false;
+    if (stage == 1 && pd == IFAC_FP64_SPLIT) {
+      // a parked member whose factor is block-dense: every evaluation of the
+      // stage takes all slices (the slice rule's error estimate holds for
+      // banded factors only; reading of the refinement's driver)
+      std::vector<int32_t> zrp(nb + 1);
+      to_host(ctx, zrp.data(), Z.m.row_ptr, sizeof(int32_t) * (nb + 1));
+      for (int k = 0; k < count; ++k) {
+        const int64_t m = nb1[k] - nb0[k];
+        if (parked[k] && 2 * (int64_t)(zrp[nb1[k]] - zrp[nb0[k]]) > m * m) slices_fixed = true;
+      }
+    }
     for (int it = 0;; ++it) {
       // split evaluations take as many slices as the active member that needs
       // the most (from its last ||delta||_F)

@@ -275,6 +275,11 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       fp64_phase = true;
       e_prev = INFINITY;
       e_pred = 0.1 * e;  // the same Z; its low-precision ||delta||_F may sit on that format's floor
+      // a block-dense factor: the slice rule's error estimate (from banded
+      // factors, where each product sums a few blocks) is far too small, and
+      // the first evaluations it allows would stall (kStallRatio); every
+      // evaluation takes all slices
+      if (2 * Z.m.nnzb > (int64_t)Z.m.nb * Z.m.nb) slices_fixed = true;
       if (rep && rep->n_delta > 0) --rep->n_delta;
       --it;
       continue;

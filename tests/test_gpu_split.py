@@ -276,9 +276,10 @@ def test_split_refine_block_sizes_match_oracle(ctx, bs):
 
 @pytest.mark.parametrize("schedule", [-1, 0, 1 << 30])
 def test_split_schedules_bs64(ctx, schedule):
-    """bs 64 under each tile schedule: default (windowed super-tiles for a
-    dense product), super-tiles only, and narrow tiles for everything (the
-    narrow kernel then runs the dense product window by window)."""
+    """bs 64 under each tile schedule: default (narrow tiles for every split
+    product), super-tiles only (windowed, fixed-point sums in HBM), and narrow
+    tiles up to an explicit K length (the narrow kernel runs the dense
+    product window by window)."""
     from paper_1901_07993_gb300 import ifac
     A = synth.random_bsr(30, 64, 1.0, seed=75)
     B = synth.random_bsr(30, 64, 1.0, seed=76)
@@ -291,12 +292,11 @@ def test_split_schedules_bs64(ctx, schedule):
     assert rel < 1e-13 and rel2 < 1e-13
 
 
-@pytest.mark.parametrize("schedule", [-1, 1 << 30])
+@pytest.mark.parametrize("schedule", [-1, 0])
 def test_split_delta_of_dense_cluster_factor(ctx, schedule):
     """||I - Z^T S Z||_F of a dense 3D-cluster factor (n = 3072, bs 64, about
-    2300 blocks per product) from split products, under the default and the
-    narrow-only schedule (the narrow kernel then runs 8 exact windows per
-    tile), against the same residual from FP64-pipe products.  With 8 slices
+    2300 blocks per product) from split products, under the default schedule
+    (narrow tiles, 8 exact windows per tile) and super-tiles only, against the same residual from FP64-pipe products.  With 8 slices
     they agree to 1e-11; with 7 (2^-7 less) to 1e-9 -- on dense operands the
     split error of the delta norm is about 270 x the chain-derived estimate,
     which is why a refinement confirms a stop at the target with all slices
