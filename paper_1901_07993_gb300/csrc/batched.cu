@@ -303,6 +303,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
       Sa = filter_rows_active(ctx, Sa.m, dseg.p, dactive.p);
       IFAC_CK(cudaStreamSynchronize(ctx->stream));  // the host flags are reused next sweep
       Mat P;
+      OperandCache pcache;
       {  // P = sum_{k=1}^{m} b_k delta^k (first two terms in one sum)
         Mat Dk;
         double b = 0.5;
@@ -312,7 +313,8 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
           const bool sym = low && bs == 64;
           Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec, sym);
           if (sym && k == 2 && o.m == 2) {  // delta^2 completed by symmetry inside the sum
-            P = sym_sum(ctx, b, Dn.m, 0.5, &D.m, 0.0);
+            // P only as the low-precision op(B) copy that M = Z P reads
+            P = poly2_operand(ctx, Dn.m, D.m, 0.5, b, o.prec, &pcache);
             break;
           }
           if (sym) Dn = sym_sum(ctx, 1.0, Dn.m, 0.0, nullptr, 0.0);
@@ -321,7 +323,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         }
       }
       D.reset();
-      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec);   // M = Z sum b_k delta^k
+      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec, false, nullptr, nullptr, &pcache);  // M = Z P
       P.reset();
       Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);
       for (int k = 0; k < count; ++k)

@@ -5,10 +5,16 @@
 // round-to-nearest multiplies and adds (no fused multiply-add), in that
 // order, so each element is rounded exactly as the plain definition is.
 // Reductions run in a fixed order (per row, then over rows), so results are
-// deterministic from run to run.
+// deterministic from run to run.  The block norms of sums are summed through
+// FP32 (SqAcc: about 2^-44 relative) so that these kernels spend the FP64
+// pipe -- GB300 runs about two FP64 operations per clock per SM -- on the
+// sums alone.
 #include <cmath>
 
 #include "internal.cuh"
+#include "tc_common.cuh"
+
+using ifac::tc::SqAcc;
 
 namespace ifac {
 
@@ -111,7 +117,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
     const double* b = qb >= 0 ? bval + (size_t)qb * bsz : nullptr;
     double* c = cval + (size_t)p * bsz;
     const bool dblk = I == J && gamma != 0.0;
-    double ss = 0.0;
+    SqAcc sq;
 #pragma unroll 4
     for (int e = lane * VEC; e < bsz; e += 32 * VEC) {
       if constexpr (VEC == 2) {
@@ -119,16 +125,15 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
         v.x = add_elem(sa, a, sb, b, dblk && e / bs == e % bs, gamma, e);
         v.y = add_elem(sa, a, sb, b, dblk && (e + 1) / bs == (e + 1) % bs, gamma, e + 1);
         *reinterpret_cast<double2*>(c + e) = v;
-        ss = fma(v.x, v.x, ss);
-        ss = fma(v.y, v.y, ss);
+        sq.add_f64(v.x);
+        sq.add_f64(v.y);
       } else {
         const double v = add_elem(sa, a, sb, b, dblk && e / bs == e % bs, gamma, e);
         c[e] = v;
-        ss = fma(v, v, ss);
+        sq.add_f64(v);
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double ss = sq.warp_total();
     if (lane == 0) cnorm[p] = sqrt(ss);
   }
 }
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
     const double* b = qb >= 0 ? bval + (size_t)qb * BSZ : nullptr;
     double* out = cval + (size_t)p * BSZ;
     const bool dblk = I == J && gamma != 0.0;
-    double ss = 0.0;
+    SqAcc sq;
     if (!lower || !u) {
 #pragma unroll 4
       for (int e = lane * 2; e < BSZ; e += 64) {
@@ -196,8 +201,8 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
         v.x = add_elem(sa, lower ? nullptr : u, sb, b, dblk && e / BS == e % BS, gamma, e);
         v.y = add_elem(sa, lower ? nullptr : u, sb, b, dblk && (e + 1) / BS == (e + 1) % BS, gamma, e + 1);
         *reinterpret_cast<double2*>(out + e) = v;
-        ss = fma(v.x, v.x, ss);
-        ss = fma(v.y, v.y, ss);
+        sq.add_f64(v.x);
+        sq.add_f64(v.y);
       }
     } else {
       for (int r0 = 0; r0 < BS; r0 += 4) {
@@ -220,14 +225,13 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
             v.y = __dadd_rn(v.y, scaled(sb, b[e + 1]));
           }
           *reinterpret_cast<double2*>(out + e) = v;
-          ss = fma(v.x, v.x, ss);
-          ss = fma(v.y, v.y, ss);
+          sq.add_f64(v.x);
+          sq.add_f64(v.y);
         }
         __syncwarp();
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double ss = sq.warp_total();
     if (lane == 0) cnorm[p] = sqrt(ss);
   }
 }

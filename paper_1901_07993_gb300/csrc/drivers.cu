@@ -28,11 +28,15 @@ static double coef_b(int k) {
 // terms are summed in one call, b_1 delta + b_2 delta^2, which rounds exactly
 // as (0 + b_1 delta) + b_2 delta^2 (b_1 = 1/2 scales exactly).  sym: delta is
 // symmetric, and each power (a polynomial in delta, so symmetric too) is formed
-// on its upper block triangle only and completed by symmetry.
+// on its upper block triangle only and completed by symmetry.  pc (sym, m =
+// 2, TF32/BF16): P is returned as its pattern with its low-precision op(B)
+// copy in *pc, all M = Z P needs (poly2_operand).
 static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int prec = IFAC_FP64,
-                  bool sym = false) {
+                  bool sym = false, OperandCache* pc = nullptr) {
   if (m < 2) return add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
   Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym);
+  if (sym && m == 2 && pc && (prec == IFAC_TF32 || prec == IFAC_BF16))
+    return poly2_operand(ctx, D.m, delta, coef_b(1), coef_b(2), prec, pc);
   if (sym && m == 2) return sym_sum(ctx, coef_b(2), D.m, coef_b(1), &delta, 0.0);
   if (sym) D = sym_sum(ctx, 1.0, D.m, 0.0, nullptr, 0.0);
   Mat P = add(ctx, coef_b(1), delta, coef_b(2), &D.m, 0.0);
@@ -284,9 +288,10 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       --it;
       continue;
     }
-    Mat P = poly_P(ctx, D.m, o.m, tau, low, sym);
+    OperandCache pcache;  // P's low-precision op(B) copy, written with P
+    Mat P = poly_P(ctx, D.m, o.m, tau, low, sym, &pcache);
     D.reset();
-    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low);      // M = Z sum b_k delta^k
+    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low, false, nullptr, nullptr, &pcache);  // M = Z P
     P.reset();
     Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);
     ++sweeps;

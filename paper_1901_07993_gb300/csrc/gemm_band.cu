@@ -21,11 +21,11 @@
 //                 (accumulate in TMEM, commit releases the stage; a double
 //                 buffered accumulator lets the epilogue of one tile overlap
 //                 the next tile's MMAs);
-//   warps 2..9  : epilogue -- two warps per tensor-memory lane quarter, each
-//                 on half of the tile's columns: tcgen05.ld, alpha, block
-//                 Frobenius norms (compensated FP32 sums, about 2^-42), FP64
-//                 stores through a shared-memory transpose so that stores are
-//                 row segments.
+//   warps 2..17 : epilogue -- four warps per tensor-memory lane quarter,
+//                 each on a quarter of the tile's columns: tcgen05.ld, alpha,
+//                 block Frobenius norms (compensated FP32 sums, about 2^-42),
+//                 FP64 stores through a shared-memory transpose so that stores
+//                 are row segments; one named barrier per tile.
 //
 // Every mbarrier wait is bounded; on expiry the CTA records the error flag and
 // all its warps leave their loops together.
@@ -36,7 +36,12 @@ namespace ifac {
 namespace tc {
 namespace bandlp {
 
-constexpr int NEPI = 8;                 // epilogue warps: two per tensor-memory lane quarter
+// epilogue warps: four per tensor-memory lane quarter, each on a quarter of
+// the tile's columns.  The epilogue (tensor-memory reads, block norms, FP64
+// stores) sets the pace of a banded product -- with eight warps the MMA
+// thread waited two thirds of its time for a free accumulator -- so it has
+// twice the warps of the MMA-bound kernels
+constexpr int NEPI = 16;
 constexpr int MMA_WARP = 1;
 constexpr int EPI0 = 2;                 // first epilogue warp
 constexpr int NTHREADS = 32 * (2 + NEPI);
@@ -99,8 +104,8 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain_bar;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
-  __shared__ double partial[4][2];
-  __shared__ float ep_stage[NEPI][32 * 17];
+  __shared__ double partial[2][4][4];       // per tile parity: lane quarter x column quarter
+  __shared__ float ep_stage[NEPI][32 * 9];  // 32 rows x 8 columns per warp
   __shared__ int32_t srec[32 * L::RECW];  // the producer's current chunk of plan records
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -245,13 +250,13 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
     }
   } else {
     // ------------------------------ epilogue ------------------------------
-    constexpr int HALF = N / 2;              // columns per warp
+    constexpr int CW = N / 4;                // columns per warp (16, or 32 at N = 128)
     const int ew = warp - EPI0;              // 0 .. NEPI - 1
     const int q = warp & 3;                  // tensor-memory lane quarter of this warp
-    const int half = ew >> 2;                // columns HALF half .. HALF half + HALF - 1 of the tile
+    const int cg = ew >> 2;                  // columns CW cg .. CW cg + CW - 1 of the tile
     const int rb = (q * 32) / BS;            // block row of the tile (a warp's rows lie in one)
     const int rin = (q * 32) % BS;           // first row of the warp within that block
-    const int cb = (half * HALF) / BS;       // block column (a warp's columns lie in one)
+    const int cb = (cg * CW) / BS;           // block column (a warp's columns lie in one)
     const int et = threadIdx.x - 32 * EPI0;  // 0 .. 32 NEPI - 1
     const float alpha_f = (float)args.alpha;
     // C positions of this warp's block and (threads et < TMB TNB) of the block
@@ -273,57 +278,55 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
         p_next = args.cpos[tn + rb * TNB + cb];
         if (et < CP) kn_next = args.cpos[tn + et];
       }
+      // a wait that failed is voted on after the tile (its reads of tensor
+      // memory are harmless; the call returns the error)
       const bool got = mbar_wait(smem_u32(&acc_full[ab]), aphase, &abort_flag, args.err);
-      if (!epi_all<32 * NEPI>(got)) break;  // all epilogue warps go on, or all stop
       tc_fence_after();
       SqAcc sq;
 #pragma unroll 1
-      for (int ch = 0; ch < HALF / 32; ++ch) {
-        const int col0 = half * HALF + ch * 32;  // tile column of this chunk
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * N + col0), v);
+      for (int ch = 0; ch < CW / 8; ++ch) {
+        const int col0 = cg * CW + ch * 8;  // tile column of this chunk
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * N + col0), v);
         if (p >= 0) {  // warp-uniform
 #pragma unroll
-          for (int e = 0; e < 32; ++e) v[e] *= alpha_f;
-          sq.add32(v);
-          // 32 rows x 16 columns at a time through shared memory, so that each
-          // store instruction writes four row segments, two values per lane
+          for (int e = 0; e < 8; ++e) v[e] *= alpha_f;
+          sq.add<8>(v);
+          // 32 rows x 8 columns through shared memory, so that each store
+          // instruction writes eight 64-byte row segments, two values per lane
           float* sw = ep_stage[ew];
           double* blk = args.cval + (size_t)p * BS * BS + (size_t)rin * BS + (col0 % BS);
-          const int c2 = (lane & 7) * 2, r4 = lane >> 3;
+          const int c2 = (lane & 3) * 2, r8 = lane >> 2;
 #pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
+          for (int e = 0; e < 8; ++e) sw[lane * 9 + e] = v[e];
+          __syncwarp();
 #pragma unroll
-            for (int e = 0; e < 16; ++e) sw[lane * 17 + e] = v[hh * 16 + e];
-            __syncwarp();
-#pragma unroll 4
-            for (int k = 0; k < 32; k += 4) {
-              const float* q = sw + (k + r4) * 17 + c2;
-              *reinterpret_cast<double2*>(blk + (size_t)(k + r4) * BS + hh * 16 + c2) =
-                  make_double2(f32_to_f64(q[0]), f32_to_f64(q[1]));
-            }
-            __syncwarp();
+          for (int k = 0; k < 32; k += 8) {
+            const float* qv = sw + (k + r8) * 9 + c2;
+            *reinterpret_cast<double2*>(blk + (size_t)(k + r8) * BS + c2) =
+                make_double2(f32_to_f64(qv[0]), f32_to_f64(qv[1]));
           }
+          __syncwarp();
         }
       }
-      double ss = sq.value();
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) partial[q][half] = ss;
+      const double ss = sq.warp_total();
+      if (lane == 0) partial[ab][q][cg] = ss;
       tc_fence_before();
-      epi_bar<32 * NEPI>();
+      // one barrier per tile: every warp has read the accumulator and written
+      // its partial norm (the partials alternate between two buffers, so the
+      // next tile's writes cannot meet this tile's reads)
+      if (!epi_all<32 * NEPI>(got)) break;  // all epilogue warps go on, or all stop
+      if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
       // norms: block (br, bc) of the tile sums the warps of its lane quarters
-      // and column halves, in a fixed order
+      // and column quarters, in a fixed order
       if (et < CP && kn >= 0) {
         const int br = et / TNB, bc = et % TNB;
-        double s = 0.0;
+        double sum = 0.0;
         for (int qq = 0; qq < 4; ++qq)
-          for (int h = 0; h < 2; ++h)
-            if ((qq * 32) / BS == br && (h * HALF) / BS == bc) s += partial[qq][h];
-        args.cnorm[kn] = sqrt(s);
+          for (int cc = 0; cc < 4; ++cc)
+            if ((qq * 32) / BS == br && (cc * CW) / BS == bc) sum += partial[ab][qq][cc];
+        args.cnorm[kn] = sqrt(sum);
       }
-      epi_bar<32 * NEPI>();
-      if (et == 0) mbar_arrive(smem_u32(&acc_empty[ab]));
     }
   }
   tc_fence_before();

@@ -399,9 +399,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
             }
           }
-          double ss = sq.value();
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          const double ss = sq.warp_total();
           if (lane == 0) partial[q][c] = ss;
         }
         tc_fence_before();
@@ -510,6 +508,62 @@ __global__ void __launch_bounds__(256) k_convert(const double* __restrict__ val,
         }
         __syncthreads();
       }
+  }
+}
+
+// P = b1 D + b2 W, the correction polynomial of Eq. (2.1) at m = 2 in the
+// mixed schedule, written straight into the low-precision op(B) copy that
+// M = Z P reads (P itself is never stored in FP64): block p of P's pattern,
+// (I, J), is stored transposed ([j][k], as op(B) blocks are), W_IJ = U_IJ for
+// J >= I and U_JI^T below, U the upper block triangle of delta^2.  The block
+// is assembled in FP32 in shared memory (inputs rounded to FP32 on their bit
+// patterns, one FMA per element), then rounded to TF32 / BF16 as k_convert
+// rounds.  One CTA per block (grid-stride).
+template <int ELT>
+__global__ void __launch_bounds__(256)
+    k_poly2_lp(const int32_t* __restrict__ prow, const int32_t* __restrict__ pci, int64_t pnnz,
+               const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval,
+               const int32_t* __restrict__ drp, const int32_t* __restrict__ dci, const double* __restrict__ dval,
+               float b1, float b2, void* __restrict__ dst) {
+  constexpr int B = 64, BSZ = B * B;
+  using T = typename std::conditional<ELT == 2, uint16_t, uint32_t>::type;
+  __shared__ float t[B][B + 1];
+  __shared__ int sq[2];
+  const auto f32 = [](double x) { return __uint_as_float(f64_to_f32_bits_rne(x)); };
+  T* out = reinterpret_cast<T*>(dst);
+  for (int64_t p = blockIdx.x; p < pnnz; p += gridDim.x) {
+    const int I = prow[p], J = pci[p];
+    if (threadIdx.x == 0) {
+      int k = lower_bound_i32(dci, drp[I], drp[I + 1], J);
+      sq[0] = (k < drp[I + 1] && dci[k] == J) ? k : -1;
+      const int r = I < J ? I : J, c = I < J ? J : I;
+      k = lower_bound_i32(uci, urp[r], urp[r + 1], c);
+      sq[1] = (k < urp[r + 1] && uci[k] == c) ? k : -1;
+    }
+    __syncthreads();
+    const int qd = sq[0], qu = sq[1];
+    for (int e = threadIdx.x; e < BSZ; e += blockDim.x)
+      t[e >> 6][e & 63] = qd >= 0 ? b1 * f32(dval[(size_t)qd * BSZ + e]) : 0.0f;
+    __syncthreads();
+    if (qu >= 0) {
+      const double* u = uval + (size_t)qu * BSZ;
+      if (J >= I) {
+        for (int e = threadIdx.x; e < BSZ; e += blockDim.x)
+          t[e >> 6][e & 63] = fmaf(b2, f32(u[e]), t[e >> 6][e & 63]);
+      } else {  // U_JI read in its stored order, added transposed
+        for (int e = threadIdx.x; e < BSZ; e += blockDim.x)
+          t[e & 63][e >> 6] = fmaf(b2, f32(u[e]), t[e & 63][e >> 6]);
+      }
+      __syncthreads();
+    }
+    // row c of the copy is column c of P_IJ
+    T* d = out + (size_t)p * BSZ;
+    for (int e = threadIdx.x; e < BSZ; e += blockDim.x) {
+      const float v = t[e & 63][e >> 6];
+      if constexpr (ELT == 2) d[e] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      else d[e] = f32_to_tf32(v);
+    }
+    __syncthreads();  // t is rewritten for the next block
   }
 }
 
@@ -969,7 +1023,7 @@ static Plan band_plan(ifac_ctx* ctx, int bs, const View& arows, const ifac_bsr& 
 template <int ELT>
 static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
                 const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                unsigned long long* pairs, OperandCache* ac, OperandCache* bc) {
+                unsigned long long* pairs, OperandCache* ac, OperandCache* bc, const OperandCache* bpre) {
   using Cf = Cfg<ELT>;
   const int nb = A.nb, bs = A.bs;
   const size_t bbytes = (size_t)bs * bs * ELT;
@@ -979,8 +1033,10 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   if (ac && ac->from_b && !(tA && ac->conv_elt == ELT)) ac = nullptr;
   const int32_t* amap = (ac && ac->from_b) ? arows.src : nullptr;
   // low-precision, K-major copies of op(A) and op(B) plus one zero block each
-  // (op(A)'s taken from the cache when it holds one of this format)
-  Buf<uint8_t> la, lb(ctx, (size_t)(B.nnzb + 1) * bbytes);
+  // (op(A)'s taken from the cache when it holds one of this format, op(B)'s
+  // from bpre when its producer wrote it in this format)
+  const bool bhit = bpre && bpre->b_ready && bpre->conv_elt == ELT && !tB;
+  Buf<uint8_t> la, lb;
   const bool hit = ac && ac->conv_elt == ELT;
   if (!hit) {
     la = Buf<uint8_t>(ctx, (size_t)(A.nnzb + 1) * bbytes);
@@ -992,10 +1048,13 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
     }
   }
   uint8_t* const la_p = ac ? ac->conv.p : la.p;
-  IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
-  if (B.nnzb) convert_blocks<ELT>(ctx, bs, B.val, brows.src, B.nnzb, !tB, lb.p);
-  uint8_t* const lb_p = lb.p;
-  if (bc && !tB) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
+  if (!bhit) {
+    lb = Buf<uint8_t>(ctx, (size_t)(B.nnzb + 1) * bbytes);
+    IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
+    if (B.nnzb) convert_blocks<ELT>(ctx, bs, B.val, brows.src, B.nnzb, !tB, lb.p);
+  }
+  uint8_t* const lb_p = bhit ? bpre->conv.p : lb.p;
+  if (bc && !tB && !bhit) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
     bc->reset();
     bc->conv = std::move(lb);
     bc->conv_elt = ELT;
@@ -1685,7 +1744,7 @@ __global__ void __launch_bounds__(band::NTB, 1)
       const int p = p_n;  // position of C_IJ in C (warp-uniform; -1: not in C)
       const int kn = kn_n;
       if (it + 1 < mt) load_next(t + (int)gridDim.x);
-      double ss = 0.0;  // this thread's squares over the tile's column sub-tiles
+      SqAcc sq;  // this thread's squares over the tile's column sub-tiles
       for (int h = 0; h < L::NSUB && good; ++h) {
         const int cin = (h * N + cg * CW) % B;  // first column of this warp within block J
         long long s[CW];
@@ -1750,16 +1809,15 @@ __global__ void __launch_bounds__(band::NTB, 1)
               v0 *= args.am;
               v1 *= args.am;
             }
-            ss = fma(v0, v0, ss);
-            ss = fma(v1, v1, ss);
+            sq.add_f64(v0);
+            sq.add_f64(v1);
             *reinterpret_cast<double2*>(dst + e) = make_double2(v0, v1);
           }
           if (bad) *args.ovf = 2;
         }
       }
       if (!good) break;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      const double ss = sq.warp_total();
       if (lane == 0) partial[q][cg] = ss;
       epi_bar<32 * EPW>();
       // norms: block (br, bc) of the tile sums the warps of its lane quarters
@@ -2140,17 +2198,36 @@ void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit) { tc::stall_s
 
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                     unsigned long long* pairs_dev, OperandCache* acache, OperandCache* bcache) {
+                     unsigned long long* pairs_dev, OperandCache* acache, OperandCache* bcache,
+                     const OperandCache* bpre) {
   if (C.nnzb == 0) return;
   if (A.bs != 32 && A.bs != 64 && A.bs != 128) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block products: bs 32, 64 or 128");
+  if (!B.val && !(bpre && bpre->b_ready)) fail(IFAC_ERR_INVALID, "tensor-core product: op(B) has no values");
   if (prec == IFAC_BF16)
-    tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache);
+    tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre);
   else if (prec == IFAC_TF32)
-    tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache);
+    tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre);
   else if (prec == IFAC_FP64_SPLIT)
     tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache,
                   bcache);
   else fail(IFAC_ERR_UNSUPPORTED, "unknown precision");
+}
+
+// the mixed schedule's P at m = 2 as a low-precision op(B) copy (k_poly2_lp)
+void poly2_lp(ifac_ctx* ctx, int elt, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2,
+              const ifac_bsr& P, const int32_t* prow, void* out) {
+  if (U.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "correction operand: bs 64");
+  const size_t bb = (size_t)64 * 64 * elt;
+  IFAC_CK(cudaMemsetAsync(static_cast<uint8_t*>(out) + (size_t)P.nnzb * bb, 0, bb, ctx->stream));
+  if (P.nnzb == 0) return;
+  const int grid = (int)std::min<int64_t>(P.nnzb, 152 * 8);
+  if (elt == 2)
+    tc::k_poly2_lp<2><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val,
+                                                      D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
+  else
+    tc::k_poly2_lp<4><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val,
+                                                      D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
+  IFAC_CK_LAUNCH();
 }
 
 }  // namespace ifac

@@ -178,6 +178,8 @@ void gemm_numeric_fp64(ifac_ctx* ctx, const View& arows, bool tA_blocks, const i
 // owner resets it when the operand changes.
 struct OperandCache {
   bool from_b = false;     // filled from an op(B) (see above)
+  bool b_ready = false;    // conv is this matrix's op(B) copy (transposed blocks, stored order),
+                           // written by its producer (poly2_operand): the product uses it as is
   int conv_elt = 0;        // bytes per element of conv (4 TF32, 2 BF16); 0 empty
   Buf<uint8_t> conv;       // (nnzb + 1) blocks, the last one zero
   int split_ns = 0;        // slices held (0 empty)
@@ -188,6 +190,7 @@ struct OperandCache {
   float l2 = 0.f;          // scaled row 2-norm bound of op(A)
   void reset() {
     from_b = false;
+    b_ready = false;
     conv_elt = 0;
     conv.reset();
     split_ns = 0;
@@ -205,7 +208,12 @@ struct OperandCache {
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache = nullptr,
-                     OperandCache* bcache = nullptr);
+                     OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr);
+// the mixed schedule's P = b1 D + b2 (U + strict_upper(U)^T) at m = 2 written
+// as the low-precision (elt 4 TF32, 2 BF16) op(B) copy of P's pattern (row
+// index of each block in prow) into out ((P.nnzb + 1) blocks), bs 64
+void poly2_lp(ifac_ctx* ctx, int elt, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2,
+              const ifac_bsr& P, const int32_t* prow, void* out);
 // TF32 (elt 4) / BF16 (elt 2) product on narrow tiles of 128 accumulator
 // rows (gemm_band.cu), bs 32, 64 or 128.  mapA / mapB: CUtensorMap of the
 // K-major low-precision copies of op(A) and op(B), boxes of one swizzle atom
@@ -291,7 +299,13 @@ Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 // ---- operations used by drivers (ops.cu) ----
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
          int prec = IFAC_FP64, bool upper = false, OperandCache* acache = nullptr,
-         OperandCache* bcache = nullptr);
+         OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr);
+// P = b1 D + b2 (U + strict_upper(U)^T) (Eq. 2.1 at m = 2, U the upper block
+// triangle of delta^2, D = delta) for a following low-precision product
+// Z P: the returned matrix holds P's pattern only (no values); its op(B)
+// copy in precision prec (TF32 or BF16) is in *pc
+Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2, int prec,
+                  OperandCache* pc);
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma);
 // the symmetric matrix whose upper block triangle (J >= I) is held by U,
 // times alpha, plus beta B and gamma I: alpha (U + strict_upper(U)^T) +

@@ -13,8 +13,10 @@ namespace ifac {
 //   acache: converted copies of op(A) kept across calls (tensor-core products)
 //   bcache: receives op(B)'s converted copies when op(B) = B (tensor-core
 //   products), for a following product with op(A) = B^T
+//   bpre: op(B)'s low-precision copy written by B's producer (poly2_operand);
+//   B then needs no values
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec, bool upper, OperandCache* acache, OperandCache* bcache) {
+         int prec, bool upper, OperandCache* acache, OperandCache* bcache, const OperandCache* bpre) {
   const int nb = A.nb;
   if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && (A.bs == 32 || A.bs == 64 || A.bs == 128))
     prec = IFAC_FP64_SPLIT;
@@ -45,7 +47,7 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   } else {
     View brows = view_rows(ctx, B, tB);
     gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, upper,
-                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache, bcache);
+                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache, bcache, bpre);
   }
   Mat R = compact(ctx, std::move(C), P.row.p, tau);
   ctx->products += 1;
@@ -65,6 +67,25 @@ Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const i
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
   sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p);
   return C;
+}
+
+Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2, int prec,
+                  OperandCache* pc) {
+  Pattern Pp = sym_pattern(ctx, U, &D, false);
+  Mat P(ctx);
+  P.m.n = U.n;
+  P.m.bs = U.bs;
+  P.m.nb = U.nb;
+  P.m.nnzb = Pp.nnzb;
+  P.m.row_ptr = Pp.rp.release();
+  P.m.col_idx = Pp.ci.release();
+  const int elt = prec == IFAC_BF16 ? 2 : 4;
+  pc->reset();
+  pc->conv = Buf<uint8_t>(ctx, (size_t)(Pp.nnzb + 1) * U.bs * U.bs * elt);
+  pc->conv_elt = elt;
+  pc->b_ready = true;
+  poly2_lp(ctx, elt, U, D, b1, b2, P.m, Pp.row.p, pc->conv.p);
+  return P;
 }
 
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma) {

@@ -229,19 +229,70 @@ struct SqAcc {
     hi = s;
     lo += err + e;
   }
-  // 32 values: the FP32 path when all are below 2^28 (the usual case), else
-  // FP64 squares (a separate branch of 32 FP64 FMAs)
-  __device__ __forceinline__ void add32(const float (&v)[32]) {
+  // K values: the FP32 path when all are below 2^28 (the usual case), else
+  // FP64 squares (a separate branch of K FP64 FMAs)
+  template <int K>
+  __device__ __forceinline__ void add(const float (&v)[K]) {
     float mx = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[i]));
+    for (int i = 0; i < K; ++i) mx = fmaxf(mx, fabsf(v[i]));
     if (mx < 268435456.0f) {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) add_small(v[i]);
+      for (int i = 0; i < K; ++i) add_small(v[i]);
     } else {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) big = fma((double)v[i], (double)v[i], big);
+      for (int i = 0; i < K; ++i) big = fma((double)v[i], (double)v[i], big);
     }
+  }
+  __device__ __forceinline__ void add32(const float (&v)[32]) { add<32>(v); }
+  // an FP64 value, squared through FP32 without the FP64 pipe: its top 24
+  // significand bits hi and the next 29 bits lo (rounded to 24) give
+  // v^2 = hi^2 + 2 hi lo + lo^2 with lo^2 < 2^-46 v^2 left out.  |v| in
+  // [2^-95, 2^28): FP32 path (lo dropped below 2^-74); larger: FP64; smaller:
+  // below 2^-190 each, left out.
+  __device__ __forceinline__ void add_f64(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int f = (int)((b >> 52) & 0x7ffu);
+    if (f >= 1023 - 95 && f < 1023 + 28) {
+      // hi 2^32 and lo 2^32 (exponent fields offset by +32)
+      const float y = __uint_as_float(((uint32_t)(f - 896 + 32) << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+      const float z = f >= 949 ? __int2float_rn((int)(b & 0x1fffffffu)) *
+                                     __uint_as_float((uint32_t)(f - 948 + 32) << 23)
+                               : 0.0f;
+      const float p = y * y;
+      const float e = fmaf(y, y, -p);
+      const float c = 2.0f * y * z;
+      const float s = hi + p;
+      const float bp = s - hi;
+      const float err = (hi - (s - bp)) + (p - bp);
+      hi = s;
+      lo += err + (e + c);
+    } else if (f >= 1023 + 28) {
+      big = fma(v, v, big);
+    }
+  }
+  // the sum over the warp's 32 lanes (every lane gets it): hi and lo reduced
+  // in FP32 with error-free two-sums, converted once; the FP64 part only when
+  // some lane holds one
+  __device__ __forceinline__ double warp_total() const {
+    float h = hi, l = lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      const float s = h + h2;
+      const float bp = s - h;
+      const float err = (h - (s - bp)) + (h2 - bp);
+      h = s;
+      l = l + l2 + err;
+    }
+    double r = ((double)h + (double)l) * 5.421010862427522e-20;  // 2^-64
+    if (__any_sync(0xffffffffu, big != 0.0)) {
+      double bsum = big;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+      r += bsum;
+    }
+    return r;
   }
   __device__ __forceinline__ double value() const {
     return ((double)hi + (double)lo) * 5.421010862427522e-20 + big;  // 2^-64
