@@ -222,10 +222,14 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         // symmetric Z^T S Z is formed and the lower one taken from it
         const bool sym = low && bs == 64;
         OperandCache zcache;  // Z's copy (op(B) of S Z) serves again as op(A) = Z^T
-        Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd, false, nullptr, &zcache);  // S Z
-        Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym, &zcache);               // Z^T (S Z)
+        // truncated products keep their kept blocks in place where the next
+        // step reads them through a value map (no compaction copies)
+        const bool inplace = pd != IFAC_FP64;
+        Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd, false, nullptr, &zcache, nullptr, inplace);  // S Z
+        Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym, &zcache, nullptr, nullptr, sym, nullptr,
+                     X.map());  // Z^T (S Z)
         X.reset();
-        Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0)          // I - Z^T S Z
+        Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map())  // I - Z^T S Z
                    : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
       }
       IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
@@ -311,10 +315,12 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         for (int k = 2; k <= o.m; ++k) {
           b = b * (double)(2 * k - 1) / (double)(2 * k);
           const bool sym = low && bs == 64;
-          Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec, sym);
-          if (sym && k == 2 && o.m == 2) {  // delta^2 completed by symmetry inside the sum
+          const bool fused = sym && k == 2 && o.m == 2;
+          Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec, sym, nullptr, nullptr, nullptr,
+                        fused);
+          if (fused) {  // delta^2 completed by symmetry inside the sum
             // P only as the low-precision op(B) copy that M = Z P reads
-            P = poly2_operand(ctx, Dn.m, D.m, 0.5, b, o.prec, &pcache);
+            P = poly2_operand(ctx, Dn.m, D.m, 0.5, b, o.prec, &pcache, Dn.map());
             break;
           }
           if (sym) Dn = sym_sum(ctx, 1.0, Dn.m, 0.0, nullptr, 0.0);
@@ -323,9 +329,9 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         }
       }
       D.reset();
-      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec, false, nullptr, nullptr, &pcache);  // M = Z P
+      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec, false, nullptr, nullptr, &pcache, true);  // M = Z P
       P.reset();
-      Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);
+      Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map());
       for (int k = 0; k < count; ++k)
         if (active[k]) {
           ++sweeps[k];

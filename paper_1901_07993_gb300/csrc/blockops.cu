@@ -94,8 +94,9 @@ template <int VEC>
 __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t cnnz, int bs,
                       Scale sa, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                       const double* __restrict__ aval, Scale sb, const int32_t* __restrict__ brp,
-                      const int32_t* __restrict__ bci, const double* __restrict__ bval, double gamma,
-                      double* __restrict__ cval, double* __restrict__ cnorm) {
+                      const int32_t* __restrict__ bci, const double* __restrict__ bval,
+                      const int32_t* __restrict__ bmap, double gamma, double* __restrict__ cval,
+                      double* __restrict__ cnorm) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -114,7 +115,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
     qa = __shfl_sync(0xffffffffu, qa, 0);
     qb = __shfl_sync(0xffffffffu, qb, 0);
     const double* a = qa >= 0 ? aval + (size_t)qa * bsz : nullptr;
-    const double* b = qb >= 0 ? bval + (size_t)qb * bsz : nullptr;
+    const double* b = qb >= 0 ? bval + (size_t)(bmap ? bmap[qb] : qb) * bsz : nullptr;
     double* c = cval + (size_t)p * bsz;
     const bool dblk = I == J && gamma != 0.0;
     SqAcc sq;
@@ -139,7 +140,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
 }
 
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow) {
+                 ifac_bsr& C, const int32_t* crow, const int32_t* bmap) {
   if (C.nnzb == 0) return;
   const int64_t warps = std::min<int64_t>(C.nnzb, 152 * 64);
   const Scale sa = make_scale(alpha), sb = make_scale(beta);
@@ -148,10 +149,10 @@ void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, co
   const double* bv = B ? B->val : nullptr;
   if ((C.bs * C.bs) % 2 == 0)  // pairs never straddle two blocks
     k_add<2><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
-                                                             A.val, sb, brp, bci, bv, gamma, C.val, C.norms);
+                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms);
   else
     k_add<1><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
-                                                             A.val, sb, brp, bci, bv, gamma, C.val, C.norms);
+                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms);
   IFAC_CK_LAUNCH();
 }
 
@@ -165,7 +166,8 @@ constexpr int SYM_WARPS = 8;
 
 __global__ void __launch_bounds__(32 * SYM_WARPS)
     k_sym(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t cnnz, Scale sa,
-          const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval, Scale sb,
+          const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval,
+          const int32_t* __restrict__ umap, Scale sb,
           const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bval,
           double gamma, double* __restrict__ cval, double* __restrict__ cnorm) {
   constexpr int BS = 64, BSZ = BS * BS;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
     }
     qu = __shfl_sync(0xffffffffu, qu, 0);
     qb = __shfl_sync(0xffffffffu, qb, 0);
-    const double* u = qu >= 0 ? uval + (size_t)qu * BSZ : nullptr;
+    const double* u = qu >= 0 ? uval + (size_t)(umap ? umap[qu] : qu) * BSZ : nullptr;
     const double* b = qb >= 0 ? bval + (size_t)qb * BSZ : nullptr;
     double* out = cval + (size_t)p * BSZ;
     const bool dblk = I == J && gamma != 0.0;
@@ -237,12 +239,12 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
 }
 
 void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow) {
+                 ifac_bsr& C, const int32_t* crow, const int32_t* umap) {
   if (C.nnzb == 0) return;
   if (U.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "symmetric completion needs bs = 64");
   const int64_t ctas = std::min<int64_t>(cdiv(C.nnzb, SYM_WARPS), 152 * 8);
   k_sym<<<(int)ctas, 32 * SYM_WARPS, 0, ctx->stream>>>(
-      crow, C.col_idx, C.nnzb, make_scale(alpha), U.row_ptr, U.col_idx, U.val, make_scale(beta),
+      crow, C.col_idx, C.nnzb, make_scale(alpha), U.row_ptr, U.col_idx, U.val, umap, make_scale(beta),
       B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr, gamma, C.val, C.norms);
   IFAC_CK_LAUNCH();
 }

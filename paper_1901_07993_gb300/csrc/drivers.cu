@@ -34,9 +34,10 @@ static double coef_b(int k) {
 static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int prec = IFAC_FP64,
                   bool sym = false, OperandCache* pc = nullptr) {
   if (m < 2) return add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
-  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym);
-  if (sym && m == 2 && pc && (prec == IFAC_TF32 || prec == IFAC_BF16))
-    return poly2_operand(ctx, D.m, delta, coef_b(1), coef_b(2), prec, pc);
+  const bool fused = sym && m == 2 && pc && (prec == IFAC_TF32 || prec == IFAC_BF16);
+  // (fused: delta^2's kept blocks stay in place for the P kernel)
+  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym, nullptr, nullptr, nullptr, fused);
+  if (fused) return poly2_operand(ctx, D.m, delta, coef_b(1), coef_b(2), prec, pc, D.map());
   if (sym && m == 2) return sym_sum(ctx, coef_b(2), D.m, coef_b(1), &delta, 0.0);
   if (sym) D = sym_sum(ctx, 1.0, D.m, 0.0, nullptr, 0.0);
   Mat P = add(ctx, coef_b(1), delta, coef_b(2), &D.m, 0.0);
@@ -238,11 +239,15 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       // Z^T S Z is symmetric: its upper block triangle is formed and the
       // lower one taken from it, halving the second product
       // Z's converted copy (op(B) of S Z) serves again as op(A) = Z^T
+      // truncated products keep their kept blocks in place where the next
+      // step reads them through a value map (no compaction copies)
       OperandCache zcache;
-      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache, &zcache);  // S Z
-      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, sym, &zcache);              // Z^T (S Z), J >= I
+      const bool inplace = dprec != IFAC_FP64;
+      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache, &zcache, nullptr, inplace);  // S Z
+      Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, sym, &zcache, nullptr, nullptr, sym, nullptr,
+                   X.map());  // Z^T (S Z), J >= I
       X.reset();
-      D = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0)                // I - Z^T S Z
+      D = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map())      // I - Z^T S Z
               : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     }
     e = fro_host(ctx, D.m);
@@ -291,9 +296,9 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
     OperandCache pcache;  // P's low-precision op(B) copy, written with P
     Mat P = poly_P(ctx, D.m, o.m, tau, low, sym, &pcache);
     D.reset();
-    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low, false, nullptr, nullptr, &pcache);  // M = Z P
+    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low, false, nullptr, nullptr, &pcache, true);  // M = Z P
     P.reset();
-    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0);
+    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map());
     ++sweeps;
     if (!fp64_phase) ++low_sweeps;
     e_prev = e;

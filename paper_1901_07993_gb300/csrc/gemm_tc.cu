@@ -511,6 +511,25 @@ __global__ void __launch_bounds__(256) k_convert(const double* __restrict__ val,
   }
 }
 
+// out[q] = vmap[src[q]] (src null: identity): the value position of view entry
+// q of a matrix whose kept blocks stayed in place after truncation
+__global__ void k_compose(const int32_t* __restrict__ src, const int32_t* __restrict__ vmap, int64_t n,
+                          int32_t* __restrict__ out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < n) out[q] = vmap[src ? src[q] : q];
+}
+
+static const int32_t* value_src(ifac_ctx* ctx, const int32_t* src, const int32_t* vmap, int64_t n,
+                                Buf<int32_t>& keep) {
+  if (!vmap) return src;
+  keep = Buf<int32_t>(ctx, (size_t)std::max<int64_t>(n, 1));
+  if (n > 0) {
+    k_compose<<<cdiv(n, 256), 256, 0, ctx->stream>>>(src, vmap, n, keep.p);
+    IFAC_CK_LAUNCH();
+  }
+  return keep.p;
+}
+
 // P = b1 D + b2 W, the correction polynomial of Eq. (2.1) at m = 2 in the
 // mixed schedule, written straight into the low-precision op(B) copy that
 // M = Z P reads (P itself is never stored in FP64): block p of P's pattern,
@@ -523,8 +542,8 @@ template <int ELT>
 __global__ void __launch_bounds__(256)
     k_poly2_lp(const int32_t* __restrict__ prow, const int32_t* __restrict__ pci, int64_t pnnz,
                const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval,
-               const int32_t* __restrict__ drp, const int32_t* __restrict__ dci, const double* __restrict__ dval,
-               float b1, float b2, void* __restrict__ dst) {
+               const int32_t* __restrict__ umap, const int32_t* __restrict__ drp, const int32_t* __restrict__ dci,
+               const double* __restrict__ dval, float b1, float b2, void* __restrict__ dst) {
   constexpr int B = 64, BSZ = B * B;
   using T = typename std::conditional<ELT == 2, uint16_t, uint32_t>::type;
   __shared__ float t[B][B + 1];
@@ -538,7 +557,7 @@ __global__ void __launch_bounds__(256)
       sq[0] = (k < drp[I + 1] && dci[k] == J) ? k : -1;
       const int r = I < J ? I : J, c = I < J ? J : I;
       k = lower_bound_i32(uci, urp[r], urp[r + 1], c);
-      sq[1] = (k < urp[r + 1] && uci[k] == c) ? k : -1;
+      sq[1] = (k < urp[r + 1] && uci[k] == c) ? (umap ? umap[k] : k) : -1;
     }
     __syncthreads();
     const int qd = sq[0], qu = sq[1];
@@ -1023,7 +1042,8 @@ static Plan band_plan(ifac_ctx* ctx, int bs, const View& arows, const ifac_bsr& 
 template <int ELT>
 static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
                 const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                unsigned long long* pairs, OperandCache* ac, OperandCache* bc, const OperandCache* bpre) {
+                unsigned long long* pairs, OperandCache* ac, OperandCache* bc, const OperandCache* bpre,
+                const int32_t* avmap, const int32_t* bvmap) {
   using Cf = Cfg<ELT>;
   const int nb = A.nb, bs = A.bs;
   const size_t bbytes = (size_t)bs * bs * ELT;
@@ -1041,7 +1061,8 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   if (!hit) {
     la = Buf<uint8_t>(ctx, (size_t)(A.nnzb + 1) * bbytes);
     IFAC_CK(cudaMemsetAsync(la.p + (size_t)A.nnzb * bbytes, 0, bbytes, ctx->stream));
-    if (A.nnzb) convert_blocks<ELT>(ctx, bs, A.val, arows.src, A.nnzb, tA, la.p);
+    Buf<int32_t> asrc;
+    if (A.nnzb) convert_blocks<ELT>(ctx, bs, A.val, value_src(ctx, arows.src, avmap, A.nnzb, asrc), A.nnzb, tA, la.p);
     if (ac) {
       ac->conv = std::move(la);
       ac->conv_elt = ELT;
@@ -1051,7 +1072,8 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   if (!bhit) {
     lb = Buf<uint8_t>(ctx, (size_t)(B.nnzb + 1) * bbytes);
     IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
-    if (B.nnzb) convert_blocks<ELT>(ctx, bs, B.val, brows.src, B.nnzb, !tB, lb.p);
+    Buf<int32_t> bsrc;
+    if (B.nnzb) convert_blocks<ELT>(ctx, bs, B.val, value_src(ctx, brows.src, bvmap, B.nnzb, bsrc), B.nnzb, !tB, lb.p);
   }
   uint8_t* const lb_p = bhit ? bpre->conv.p : lb.p;
   if (bc && !tB && !bhit) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
@@ -1901,7 +1923,9 @@ static void launch_split_band(ifac_ctx* ctx, const CUtensorMap& mA, const CUtens
 
 static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                       bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
-                      unsigned long long* pairs, OperandCache* ac, OperandCache* bc) {
+                      unsigned long long* pairs, OperandCache* ac, OperandCache* bc, const int32_t* avmap,
+                      const int32_t* bvmap) {
+  Buf<int32_t> asrc, bsrc;  // value positions of op(A) / op(B) view entries under value maps
   using Cf = Cfg<2>;
   const int nb = A.nb, bs = A.bs;
   const int64_t rows = (int64_t)nb * bs;
@@ -1921,11 +1945,14 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
   IFAC_CK(cudaMemsetAsync(l1.p, 0, 4 * sizeof(unsigned int), ctx->stream));
   if (!hit) {
     sige = Buf<int>(ctx, rows);
-    row_scales(ctx, bs, arows.rp, arows.src, nb, tA, A.val, sige.p, l1.p, l1.p + 2);
+    row_scales(ctx, bs, arows.rp, value_src(ctx, arows.src, avmap, A.nnzb, asrc), nb, tA, A.val, sige.p, l1.p,
+               l1.p + 2);
   }
   {
     View bt = view_rows(ctx, B, !tB);
-    row_scales(ctx, bs, bt.rp, bt.src, nb, !tB, B.val, taue.p, l1.p + 1, l1.p + 3);
+    Buf<int32_t> btsrc;
+    row_scales(ctx, bs, bt.rp, value_src(ctx, bt.src, bvmap, B.nnzb, btsrc), nb, !tB, B.val, taue.p, l1.p + 1,
+               l1.p + 3);
   }
   // slices: row scale block of an op(A) entry is its CSR row; of an op(B) entry its CSR column
   const size_t bbytes = (size_t)bs * bs * 2;
@@ -1939,13 +1966,16 @@ static void run_split(ifac_ctx* ctx, int ns, const View& arows, bool tA, const i
     if (A.nnzb) {
       Buf<int32_t> arow(ctx, A.nnzb);
       expand_rows(ctx, arows.rp, nb, arow.p);
-      split_blocks(ctx, bs, A.val, arows.src, A.nnzb, tA, arow.p, sige.p, nsa, la.p);
+      split_blocks(ctx, bs, A.val, value_src(ctx, arows.src, avmap, A.nnzb, asrc), A.nnzb, tA, arow.p, sige.p, nsa,
+                   la.p);
     }
   }
   uint8_t* const la_p = hit ? ac->split.p : la.p;
   const int* const sige_p = hit ? ac->sexp.p : sige.p;
   const int* const taue_p = taue.p;
-  if (B.nnzb) split_blocks(ctx, bs, B.val, brows.src, B.nnzb, !tB, brows.ci, taue.p, ns, lb.p);
+  if (B.nnzb)
+    split_blocks(ctx, bs, B.val, value_src(ctx, brows.src, bvmap, B.nnzb, bsrc), B.nnzb, !tB, brows.ci, taue.p, ns,
+                 lb.p);
   // one tensor map over all slices of each operand (slice s at row s (nnzb + 1) bs)
   if ((int64_t)ns * (std::max(A.nnzb, B.nnzb) + 1) * bs > (int64_t)0x7fffffff)
     fail(IFAC_ERR_TOO_LARGE, "split product: slice copies exceed the 2^31-row tensor-map range");
@@ -2199,33 +2229,33 @@ void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit) { tc::stall_s
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache, OperandCache* bcache,
-                     const OperandCache* bpre) {
+                     const OperandCache* bpre, const int32_t* avmap, const int32_t* bvmap) {
   if (C.nnzb == 0) return;
   if (A.bs != 32 && A.bs != 64 && A.bs != 128) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block products: bs 32, 64 or 128");
   if (!B.val && !(bpre && bpre->b_ready)) fail(IFAC_ERR_INVALID, "tensor-core product: op(B) has no values");
   if (prec == IFAC_BF16)
-    tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre);
+    tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre, avmap, bvmap);
   else if (prec == IFAC_TF32)
-    tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre);
+    tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre, avmap, bvmap);
   else if (prec == IFAC_FP64_SPLIT)
     tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache,
-                  bcache);
+                  bcache, avmap, bvmap);
   else fail(IFAC_ERR_UNSUPPORTED, "unknown precision");
 }
 
 // the mixed schedule's P at m = 2 as a low-precision op(B) copy (k_poly2_lp)
 void poly2_lp(ifac_ctx* ctx, int elt, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2,
-              const ifac_bsr& P, const int32_t* prow, void* out) {
+              const ifac_bsr& P, const int32_t* prow, void* out, const int32_t* umap) {
   if (U.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "correction operand: bs 64");
   const size_t bb = (size_t)64 * 64 * elt;
   IFAC_CK(cudaMemsetAsync(static_cast<uint8_t*>(out) + (size_t)P.nnzb * bb, 0, bb, ctx->stream));
   if (P.nnzb == 0) return;
   const int grid = (int)std::min<int64_t>(P.nnzb, 152 * 8);
   if (elt == 2)
-    tc::k_poly2_lp<2><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val,
+    tc::k_poly2_lp<2><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val, umap,
                                                       D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
   else
-    tc::k_poly2_lp<4><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val,
+    tc::k_poly2_lp<4><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val, umap,
                                                       D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
   IFAC_CK_LAUNCH();
 }

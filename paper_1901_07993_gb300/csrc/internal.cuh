@@ -92,18 +92,23 @@ struct Buf {
 };
 
 // A library-owned block-sparse matrix (all arrays device, norms always set).
+// vmap (optional, internal to the drivers): block p's values are at
+// m.val + vmap[p] bs^2 -- a product truncated without moving its kept blocks
+// (compact with nocopy); only the consumers that take a value map read it.
 struct Mat {
   ifac_ctx* ctx = nullptr;
   ifac_bsr m{};
+  Buf<int32_t> vmap;
   Mat() = default;
   explicit Mat(ifac_ctx* c) : ctx(c) {}
   Mat(const Mat&) = delete;
   Mat& operator=(const Mat&) = delete;
-  Mat(Mat&& o) noexcept : ctx(o.ctx), m(o.m) { o.m = ifac_bsr{}; }
+  Mat(Mat&& o) noexcept : ctx(o.ctx), m(o.m), vmap(std::move(o.vmap)) { o.m = ifac_bsr{}; }
   Mat& operator=(Mat&& o) noexcept {
-    if (this != &o) { reset(); ctx = o.ctx; m = o.m; o.m = ifac_bsr{}; }
+    if (this != &o) { reset(); ctx = o.ctx; m = o.m; o.m = ifac_bsr{}; vmap = std::move(o.vmap); }
     return *this;
   }
+  const int32_t* map() const { return vmap.p; }
   ~Mat() { reset(); }
   void reset();
   ifac_bsr release() { ifac_bsr r = m; m = ifac_bsr{}; return r; }
@@ -156,7 +161,8 @@ Pattern sym_pattern(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr* B, bool di
 // Expand row_ptr to a per-block row index.
 void expand_rows(ifac_ctx* ctx, const int32_t* rp, int nb, int32_t* row);
 // Keep blocks with !(norm < tau) of an (uncompacted) matrix; returns the compacted one.
-Mat compact(ifac_ctx* ctx, Mat&& full, const int32_t* row, double tau);
+// nocopy: the kept blocks stay where they are (the result's vmap points to them).
+Mat compact(ifac_ctx* ctx, Mat&& full, const int32_t* row, double tau, bool nocopy = false);
 // Keep blocks selected by a per-block mask (1 keep / 0 drop).
 Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const uint8_t* keep);
 
@@ -208,12 +214,13 @@ struct OperandCache {
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache = nullptr,
-                     OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr);
+                     OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr,
+                     const int32_t* avmap = nullptr, const int32_t* bvmap = nullptr);
 // the mixed schedule's P = b1 D + b2 (U + strict_upper(U)^T) at m = 2 written
 // as the low-precision (elt 4 TF32, 2 BF16) op(B) copy of P's pattern (row
 // index of each block in prow) into out ((P.nnzb + 1) blocks), bs 64
 void poly2_lp(ifac_ctx* ctx, int elt, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2,
-              const ifac_bsr& P, const int32_t* prow, void* out);
+              const ifac_bsr& P, const int32_t* prow, void* out, const int32_t* umap = nullptr);
 // TF32 (elt 4) / BF16 (elt 2) product on narrow tiles of 128 accumulator
 // rows (gemm_band.cu), bs 32, 64 or 128.  mapA / mapB: CUtensorMap of the
 // K-major low-precision copies of op(A) and op(B), boxes of one swizzle atom
@@ -237,11 +244,12 @@ void autotune(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, co
 // Failure-path self-test: a tensor-core launch whose pipeline never fills, so
 // its bounded waits expire after wait_limit polls (sets the device error flag).
 void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit);
+// bmap / umap: value maps of B / U (Mat::vmap), or null
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
-                 double gamma, ifac_bsr& C, const int32_t* crow);
+                 double gamma, ifac_bsr& C, const int32_t* crow, const int32_t* bmap = nullptr);
 // C = alpha (U + strict_upper(U)^T) + beta B + gamma I on the pattern of sym_pattern
 void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow);
+                 ifac_bsr& C, const int32_t* crow, const int32_t* umap = nullptr);
 void block_norms(ifac_ctx* ctx, const ifac_bsr& A, double* norms);
 // per block-row sum of squared block norms
 void row_sq_norms(ifac_ctx* ctx, const ifac_bsr& A, double* rowsq);
@@ -297,20 +305,25 @@ void gershgorin_rows(ifac_ctx* ctx, const ifac_bsr& A, double* rs);
 Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 
 // ---- operations used by drivers (ops.cu) ----
+// nocopy: the truncated result keeps its kept blocks in place (Mat::vmap);
+// avmap / bvmap: value maps of A and B (tensor-core and split products only)
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
          int prec = IFAC_FP64, bool upper = false, OperandCache* acache = nullptr,
-         OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr);
+         OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr, bool nocopy = false,
+         const int32_t* avmap = nullptr, const int32_t* bvmap = nullptr);
 // P = b1 D + b2 (U + strict_upper(U)^T) (Eq. 2.1 at m = 2, U the upper block
 // triangle of delta^2, D = delta) for a following low-precision product
 // Z P: the returned matrix holds P's pattern only (no values); its op(B)
 // copy in precision prec (TF32 or BF16) is in *pc
 Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2, int prec,
-                  OperandCache* pc);
-Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma);
+                  OperandCache* pc, const int32_t* umap = nullptr);
+Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
+        const int32_t* bmap = nullptr);
 // the symmetric matrix whose upper block triangle (J >= I) is held by U,
 // times alpha, plus beta B and gamma I: alpha (U + strict_upper(U)^T) +
 // beta B + gamma I, rounded as add() rounds alpha A + beta B + gamma I
-Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma);
+Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
+            const int32_t* umap = nullptr);
 Mat truncate(ifac_ctx* ctx, const ifac_bsr& A, double tau);
 Mat copy_mat(ifac_ctx* ctx, const ifac_bsr& A);
 void validate(const ifac_bsr* A, const char* name);

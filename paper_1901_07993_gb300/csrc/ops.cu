@@ -15,11 +15,15 @@ namespace ifac {
 //   products), for a following product with op(A) = B^T
 //   bpre: op(B)'s low-precision copy written by B's producer (poly2_operand);
 //   B then needs no values
+//   nocopy: truncation leaves the kept blocks in place (the result's vmap)
+//   avmap / bvmap: value maps of A / B (tensor-core and split products)
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
-         int prec, bool upper, OperandCache* acache, OperandCache* bcache, const OperandCache* bpre) {
+         int prec, bool upper, OperandCache* acache, OperandCache* bcache, const OperandCache* bpre, bool nocopy,
+         const int32_t* avmap, const int32_t* bvmap) {
   const int nb = A.nb;
   if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && (A.bs == 32 || A.bs == 64 || A.bs == 128))
     prec = IFAC_FP64_SPLIT;
+  if ((avmap || bvmap) && prec == IFAC_FP64) fail(IFAC_ERR_INVALID, "FP64 products take no value maps");
   View arows = view_rows(ctx, A, tA);
   Pattern P = product_pattern(ctx, arows, B, tB, nb, upper);
   Mat C(ctx);
@@ -47,14 +51,15 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   } else {
     View brows = view_rows(ctx, B, tB);
     gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, upper,
-                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache, bcache, bpre);
+                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache, bcache, bpre, avmap, bvmap);
   }
-  Mat R = compact(ctx, std::move(C), P.row.p, tau);
+  Mat R = compact(ctx, std::move(C), P.row.p, tau, nocopy);
   ctx->products += 1;
   return R;
 }
 
-Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma) {
+Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
+            const int32_t* umap) {
   Pattern P = sym_pattern(ctx, U, B, gamma != 0.0);
   Mat C(ctx);
   C.m.n = U.n;
@@ -65,12 +70,12 @@ Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const i
   C.m.col_idx = P.ci.release();
   C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * U.bs * U.bs));
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
-  sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p);
+  sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p, umap);
   return C;
 }
 
 Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2, int prec,
-                  OperandCache* pc) {
+                  OperandCache* pc, const int32_t* umap) {
   Pattern Pp = sym_pattern(ctx, U, &D, false);
   Mat P(ctx);
   P.m.n = U.n;
@@ -84,11 +89,12 @@ Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1
   pc->conv = Buf<uint8_t>(ctx, (size_t)(Pp.nnzb + 1) * U.bs * U.bs * elt);
   pc->conv_elt = elt;
   pc->b_ready = true;
-  poly2_lp(ctx, elt, U, D, b1, b2, P.m, Pp.row.p, pc->conv.p);
+  poly2_lp(ctx, elt, U, D, b1, b2, P.m, Pp.row.p, pc->conv.p, umap);
   return P;
 }
 
-Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma) {
+Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
+        const int32_t* bmap) {
   Pattern P = union_pattern(ctx, A, B, gamma != 0.0);
   Mat C(ctx);
   C.m.n = A.n;
@@ -99,7 +105,7 @@ Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_
   C.m.col_idx = P.ci.release();
   C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
-  add_numeric(ctx, alpha, A, beta, B, gamma, C.m, P.row.p);
+  add_numeric(ctx, alpha, A, beta, B, gamma, C.m, P.row.p, bmap);
   return C;
 }
 

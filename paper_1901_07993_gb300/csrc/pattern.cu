@@ -300,10 +300,13 @@ __global__ void k_row_keep_count(const int32_t* __restrict__ rp, int nb, const u
   if (lane == 0) cnt[row] = c;
 }
 
+// dest[p]: the new position of block p (-1: dropped); vmap (optional):
+// vmap[new position] = p
 __global__ void k_row_keep_dest(const int32_t* __restrict__ rp, int nb, const uint8_t* __restrict__ keep,
                                 const int32_t* __restrict__ rp_new, const int32_t* __restrict__ ci,
                                 const double* __restrict__ norms, int32_t* __restrict__ ci_new,
-                                double* __restrict__ norms_new, int32_t* __restrict__ dest) {
+                                double* __restrict__ norms_new, int32_t* __restrict__ dest,
+                                int32_t* __restrict__ vmap = nullptr) {
   int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (row >= nb) return;
   int pos = rp_new[row];
@@ -313,10 +316,11 @@ __global__ void k_row_keep_dest(const int32_t* __restrict__ rp, int nb, const ui
     unsigned m = __ballot_sync(0xffffffffu, k);
     if (p < rp[row + 1]) {
       int d = k ? pos + __popc(m & ((1u << lane) - 1u)) : -1;
-      dest[p] = d;
+      if (dest) dest[p] = d;
       if (k) {
         ci_new[d] = ci[p];
         norms_new[d] = norms[p];
+        if (vmap) vmap[d] = p;
       }
     }
     pos += __popc(m);
@@ -384,7 +388,7 @@ Mat select_blocks(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, const ui
   return gather_kept(ctx, A, keep, std::move(rp_new), tot);
 }
 
-Mat compact(ifac_ctx* ctx, Mat&& full, const int32_t* row, double tau) {
+Mat compact(ifac_ctx* ctx, Mat&& full, const int32_t* row, double tau, bool nocopy) {
   (void)row;
   if (full.m.nnzb == 0 || !(tau > 0)) return std::move(full);
   Buf<uint8_t> keep(ctx, full.m.nnzb);
@@ -393,7 +397,27 @@ Mat compact(ifac_ctx* ctx, Mat&& full, const int32_t* row, double tau) {
   Buf<int32_t> rp_new;
   const int64_t tot = count_kept(ctx, full.m, keep.p, rp_new);
   if (tot == full.m.nnzb) return std::move(full);  // nothing dropped: no copy
-  return gather_kept(ctx, full.m, keep.p, std::move(rp_new), tot);
+  if (!nocopy) return gather_kept(ctx, full.m, keep.p, std::move(rp_new), tot);
+  // the kept blocks stay in full's value array, which the result takes over
+  const int nb = full.m.nb;
+  Mat R(ctx);
+  R.m.n = full.m.n;
+  R.m.bs = full.m.bs;
+  R.m.nb = nb;
+  R.m.nnzb = tot;
+  R.m.row_ptr = rp_new.release();
+  R.m.col_idx = static_cast<int32_t*>(dalloc(ctx, sizeof(int32_t) * (tot ? tot : 1)));
+  R.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (tot ? tot : 1)));
+  R.vmap = Buf<int32_t>(ctx, (size_t)(tot ? tot : 1));
+  if (tot > 0) {
+    k_row_keep_dest<<<cdiv((int64_t)nb * 32, 256), 256, 0, ctx->stream>>>(
+        full.m.row_ptr, nb, keep.p, R.m.row_ptr, full.m.col_idx, full.m.norms, R.m.col_idx, R.m.norms, nullptr,
+        R.vmap.p);
+    IFAC_CK_LAUNCH();
+  }
+  R.m.val = full.m.val;
+  full.m.val = nullptr;
+  return R;
 }
 
 }  // namespace ifac
