@@ -178,6 +178,7 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
   Buf<uint8_t> dactive(ctx, count);
   Buf<double> ne(ctx, count);
   Mat Sa = copy_mat(ctx, S.m);
+  OperandCache znat;  // Z's low-precision op(A) copy for M = Z P, written with Z
   for (int stage = 0; stage < (low ? 2 : 1); ++stage) {
     if (stage == 1) {
       bool any_parked = false;
@@ -329,9 +330,9 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         }
       }
       D.reset();
-      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec, false, nullptr, nullptr, &pcache, true);  // M = Z P
+      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec, false, &znat, nullptr, &pcache, true);  // M = Z P
       P.reset();
-      Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map());
+      Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map(), o.prec, &znat);  // with Z's copy for the next M
       for (int k = 0; k < count; ++k)
         if (active[k]) {
           ++sweeps[k];

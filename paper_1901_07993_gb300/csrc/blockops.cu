@@ -75,15 +75,31 @@ __device__ __forceinline__ double scaled(const Scale& s, double x) {
 }
 
 __device__ __forceinline__ double add_elem(const Scale& sa, const double* a, const Scale& sb, const double* b,
-                                           bool diag, double gamma, int e) {
+                                           bool diag, double gamma, int e, int ea = -1) {
   double v = 0.0;
-  if (a) v = scaled(sa, a[e]);
+  if (a) v = scaled(sa, a[ea < 0 ? e : ea]);
   if (b) {
     const double t = scaled(sb, b[e]);
     v = a ? __dadd_rn(v, t) : t;
   }
   if (diag) v = (a || b) ? __dadd_rn(v, gamma) : gamma;
   return v;
+}
+
+// the K-major low-precision copy that the tensor-core products read (TF32:
+// FP32 round-to-nearest-even then TF32 round-half-away; BF16 round-to-
+// nearest-even, as their operand conversion rounds), written beside the
+// FP64 result: lp_elt 4 TF32, 2 BF16, 0 none
+__device__ __forceinline__ void lp_store2(void* lp, int lp_elt, size_t i, double x, double y) {
+  if (lp_elt == 4) {
+    uint2 w;
+    w.x = ifac::tc::f32_to_tf32(__uint_as_float(ifac::tc::f64_to_f32_bits_rne(x)));
+    w.y = ifac::tc::f32_to_tf32(__uint_as_float(ifac::tc::f64_to_f32_bits_rne(y)));
+    *reinterpret_cast<uint2*>(static_cast<uint32_t*>(lp) + i) = w;
+  } else if (lp_elt == 2) {
+    const uint32_t w = (uint32_t)ifac::tc::f64_to_bf16_bits_rne(x) | ((uint32_t)ifac::tc::f64_to_bf16_bits_rne(y) << 16);
+    *reinterpret_cast<uint32_t*>(static_cast<uint16_t*>(lp) + i) = w;
+  }
 }
 
 // one warp per output block (grid-stride over blocks).  Element by element
@@ -96,7 +112,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
                       const double* __restrict__ aval, Scale sb, const int32_t* __restrict__ brp,
                       const int32_t* __restrict__ bci, const double* __restrict__ bval,
                       const int32_t* __restrict__ bmap, double gamma, double* __restrict__ cval,
-                      double* __restrict__ cnorm) {
+                      double* __restrict__ cnorm, void* __restrict__ lp, int lp_elt) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -126,6 +142,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
         v.x = add_elem(sa, a, sb, b, dblk && e / bs == e % bs, gamma, e);
         v.y = add_elem(sa, a, sb, b, dblk && (e + 1) / bs == (e + 1) % bs, gamma, e + 1);
         *reinterpret_cast<double2*>(c + e) = v;
+        if (lp_elt) lp_store2(lp, lp_elt, (size_t)p * bsz + e, v.x, v.y);
         sq.add_f64(v.x);
         sq.add_f64(v.y);
       } else {
@@ -140,7 +157,8 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
 }
 
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow, const int32_t* bmap) {
+                 ifac_bsr& C, const int32_t* crow, const int32_t* bmap, void* lp, int lp_elt) {
+  if (lp_elt && (C.bs * C.bs) % 2 != 0) fail(IFAC_ERR_UNSUPPORTED, "low-precision copy: even bs * bs");
   if (C.nnzb == 0) return;
   const int64_t warps = std::min<int64_t>(C.nnzb, 152 * 64);
   const Scale sa = make_scale(alpha), sb = make_scale(beta);
@@ -149,10 +167,12 @@ void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, co
   const double* bv = B ? B->val : nullptr;
   if ((C.bs * C.bs) % 2 == 0)  // pairs never straddle two blocks
     k_add<2><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
-                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms);
+                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms, lp,
+                                                             lp_elt);
   else
     k_add<1><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
-                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms);
+                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms, nullptr,
+                                                             0);
   IFAC_CK_LAUNCH();
 }
 
@@ -169,7 +189,8 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
           const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval,
           const int32_t* __restrict__ umap, Scale sb,
           const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bval,
-          double gamma, double* __restrict__ cval, double* __restrict__ cnorm) {
+          double gamma, double* __restrict__ cval, double* __restrict__ cnorm, int mirror, void* __restrict__ lp,
+          int lp_elt) {
   constexpr int BS = 64, BSZ = BS * BS;
   __shared__ double stripe[SYM_WARPS][4][BS + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -195,14 +216,20 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
     const double* b = qb >= 0 ? bval + (size_t)qb * BSZ : nullptr;
     double* out = cval + (size_t)p * BSZ;
     const bool dblk = I == J && gamma != 0.0;
+    // mirror: a diagonal block takes its strictly lower triangle from its
+    // upper one as well, so the result is exactly symmetric
+    const bool mir = mirror && I == J;
     SqAcc sq;
     if (!lower || !u) {
 #pragma unroll 4
       for (int e = lane * 2; e < BSZ; e += 64) {
+        const int rr = e / BS, c0 = e % BS;
+        const int e0 = (mir && c0 < rr) ? c0 * BS + rr : -1, e1 = (mir && c0 + 1 < rr) ? (c0 + 1) * BS + rr : -1;
         double2 v;
-        v.x = add_elem(sa, lower ? nullptr : u, sb, b, dblk && e / BS == e % BS, gamma, e);
-        v.y = add_elem(sa, lower ? nullptr : u, sb, b, dblk && (e + 1) / BS == (e + 1) % BS, gamma, e + 1);
+        v.x = add_elem(sa, lower ? nullptr : u, sb, b, dblk && rr == c0, gamma, e, e0);
+        v.y = add_elem(sa, lower ? nullptr : u, sb, b, dblk && rr == c0 + 1, gamma, e + 1, e1);
         *reinterpret_cast<double2*>(out + e) = v;
+        if (lp_elt) lp_store2(lp, lp_elt, (size_t)p * BSZ + e, v.x, v.y);
         sq.add_f64(v.x);
         sq.add_f64(v.y);
       }
@@ -227,6 +254,7 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
             v.y = __dadd_rn(v.y, scaled(sb, b[e + 1]));
           }
           *reinterpret_cast<double2*>(out + e) = v;
+          if (lp_elt) lp_store2(lp, lp_elt, (size_t)p * BSZ + e, v.x, v.y);
           sq.add_f64(v.x);
           sq.add_f64(v.y);
         }
@@ -239,13 +267,14 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
 }
 
 void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow, const int32_t* umap) {
+                 ifac_bsr& C, const int32_t* crow, const int32_t* umap, bool mirror, void* lp, int lp_elt) {
   if (C.nnzb == 0) return;
   if (U.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "symmetric completion needs bs = 64");
   const int64_t ctas = std::min<int64_t>(cdiv(C.nnzb, SYM_WARPS), 152 * 8);
   k_sym<<<(int)ctas, 32 * SYM_WARPS, 0, ctx->stream>>>(
       crow, C.col_idx, C.nnzb, make_scale(alpha), U.row_ptr, U.col_idx, U.val, umap, make_scale(beta),
-      B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr, gamma, C.val, C.norms);
+      B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr, gamma, C.val, C.norms,
+      mirror ? 1 : 0, lp, lp_elt);
   IFAC_CK_LAUNCH();
 }
 

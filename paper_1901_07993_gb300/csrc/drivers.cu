@@ -32,11 +32,12 @@ static double coef_b(int k) {
 // 2, TF32/BF16): P is returned as its pattern with its low-precision op(B)
 // copy in *pc, all M = Z P needs (poly2_operand).
 static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int prec = IFAC_FP64,
-                  bool sym = false, OperandCache* pc = nullptr) {
+                  bool sym = false, OperandCache* pc = nullptr, OperandCache* dc = nullptr) {
   if (m < 2) return add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
   const bool fused = sym && m == 2 && pc && (prec == IFAC_TF32 || prec == IFAC_BF16);
-  // (fused: delta^2's kept blocks stay in place for the P kernel)
-  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym, nullptr, nullptr, nullptr, fused);
+  // (fused: delta^2's kept blocks stay in place for the P kernel; dc: delta's
+  // low-precision copy from its producer, serving both operands)
+  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym, dc, nullptr, dc, fused);
   if (fused) return poly2_operand(ctx, D.m, delta, coef_b(1), coef_b(2), prec, pc, D.map());
   if (sym && m == 2) return sym_sum(ctx, coef_b(2), D.m, coef_b(1), &delta, 0.0);
   if (sym) D = sym_sum(ctx, 1.0, D.m, 0.0, nullptr, 0.0);
@@ -225,6 +226,9 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
   // S's converted copies serve every X = S Z of the refinement
   OperandCache scache;
   scache.want_ns = ctx->split_slices;
+  // low-precision copies written by the sums that produce delta (for
+  // delta^2) and Z (for M = Z P), so neither is converted in a separate pass
+  OperandCache dcache, znat;
   int stop = 0, sweeps = 0, fp64_evals = 0, low_sweeps = 0;
   for (int it = 0;; ++it) {
     const int dprec = fp64_phase ? delta_prec_of(o, S.m.bs) : low;
@@ -247,7 +251,8 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, sym, &zcache, nullptr, nullptr, sym, nullptr,
                    X.map());  // Z^T (S Z), J >= I
       X.reset();
-      D = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map())      // I - Z^T S Z
+      // I - Z^T S Z, exactly symmetric, with its low-precision copy for delta^2
+      D = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map(), true, low, &dcache)
               : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     }
     e = fro_host(ctx, D.m);
@@ -294,11 +299,12 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       continue;
     }
     OperandCache pcache;  // P's low-precision op(B) copy, written with P
-    Mat P = poly_P(ctx, D.m, o.m, tau, low, sym, &pcache);
+    Mat P = poly_P(ctx, D.m, o.m, tau, low, sym, &pcache, sym ? &dcache : nullptr);
     D.reset();
-    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low, false, nullptr, nullptr, &pcache, true);  // M = Z P
+    dcache.reset();
+    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low, false, &znat, nullptr, &pcache, true);  // M = Z P
     P.reset();
-    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map());
+    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map(), low, &znat);  // with Z's copy for the next M
     ++sweeps;
     if (!fp64_phase) ++low_sweeps;
     e_prev = e;

@@ -762,7 +762,8 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
                             const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, int a_zero, int b_zero,
                             const int32_t* __restrict__ amap, int32_t* __restrict__ rec, int32_t* __restrict__ nk_out,
                             int* __restrict__ kmax, const int32_t* __restrict__ crp = nullptr,
-                            const int32_t* __restrict__ cci = nullptr, int32_t* __restrict__ cpos = nullptr) {
+                            const int32_t* __restrict__ cci = nullptr, int32_t* __restrict__ cpos = nullptr,
+                            const int32_t* __restrict__ bmap = nullptr) {
   static_assert(ROWS * COLS <= 32, "one lane per block of the tile");
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -835,7 +836,7 @@ __global__ void k_tile_plan(const int32_t* __restrict__ tiles, const int* __rest
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) out[r] = (amap && ra[r] != a_zero) ? amap[ra[r]] : ra[r];
 #pragma unroll
-        for (int c = 0; c < COLS; ++c) out[ROWS + c] = rb[c];
+        for (int c = 0; c < COLS; ++c) out[ROWS + c] = (bmap && rb[c] != b_zero) ? bmap[rb[c]] : rb[c];
       }
       e += __popc(m);
     }
@@ -859,10 +860,12 @@ struct Plan {
 template <int ROWS, int COLS>
 static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool tA, const View& brows,
                       const ifac_bsr& B, const ifac_bsr& C, const int32_t* crow, bool want_kmax,
-                      int kmax_limit = 0, const int32_t* amap = nullptr, const HostRead* extra = nullptr) {
+                      int kmax_limit = 0, const int32_t* amap = nullptr, const HostRead* extra = nullptr,
+                      const int32_t* bmap = nullptr) {
   // amap (nullable): copy index of each op(A) view position, when op(A)'s
   // low-precision copy is not in view order (a shared copy of a transposed
-  // operand, held in the stored order).  extra (nullable): one more small
+  // operand, held in the stored order).  bmap (nullable): the same for
+  // op(B) (a symmetric op(B) read from its op(A) copy).  extra (nullable): one more small
   // read-back the caller needs, taken with the plan's sizes in one
   // synchronisation.
   // kmax_limit > 0: a plan whose longest tile has more K steps is not wanted;
@@ -965,7 +968,7 @@ static Plan make_plan(ifac_ctx* ctx, const View& arows, const ifac_bsr& A, bool 
     k_tile_plan<ROWS, COLS, false><<<cdiv((int64_t)nt * 32, 256), 256, 0, ctx->stream>>>(
         P.tiles.p, ntiles, P.off.p, bmA.p, nb, W, dense_maps ? imA.p : nullptr, dense_maps ? imB.p : nullptr,
         arows.rp, arows.ci, brows.rp, brows.ci, (int)A.nnzb, (int)B.nnzb, amap, P.rec.p, nullptr, nullptr,
-        C.row_ptr, C.col_idx, P.cpos.p);
+        C.row_ptr, C.col_idx, P.cpos.p, bmap);
     IFAC_CK_LAUNCH();
   }
   // the plan kernel has read the maps and the bitmap before they are freed
@@ -1033,10 +1036,10 @@ static void convert_blocks(ifac_ctx* ctx, int bs, const double* val, const int32
 // the narrow-tile plan of a block size (tile of 128 / bs x max(64, bs) / bs blocks)
 static Plan band_plan(ifac_ctx* ctx, int bs, const View& arows, const ifac_bsr& A, bool tA, const View& brows,
                       const ifac_bsr& B, const ifac_bsr& C, const int32_t* crow, int kmax_limit,
-                      const int32_t* amap, const HostRead* extra = nullptr) {
-  if (bs == 32) return make_plan<4, 2>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra);
-  if (bs == 64) return make_plan<2, 1>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra);
-  return make_plan<1, 1>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra);
+                      const int32_t* amap, const HostRead* extra = nullptr, const int32_t* bmap = nullptr) {
+  if (bs == 32) return make_plan<4, 2>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra, bmap);
+  if (bs == 64) return make_plan<2, 1>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra, bmap);
+  return make_plan<1, 1>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra, bmap);
 }
 
 template <int ELT>
@@ -1056,6 +1059,10 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   // (op(A)'s taken from the cache when it holds one of this format, op(B)'s
   // from bpre when its producer wrote it in this format)
   const bool bhit = bpre && bpre->b_ready && bpre->conv_elt == ELT && !tB;
+  // an exactly symmetric op(B) = B whose op(A) copy is at hand: block (K, J)
+  // of the op(B) copy, B_KJ^T = B_JK, is that copy's block at tpos
+  const bool bsym = !bhit && bpre && bpre->tpos.p && bpre->conv_elt == ELT && !tB;
+  const int32_t* bmap = bsym ? bpre->tpos.p : nullptr;
   Buf<uint8_t> la, lb;
   const bool hit = ac && ac->conv_elt == ELT;
   if (!hit) {
@@ -1069,14 +1076,14 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
     }
   }
   uint8_t* const la_p = ac ? ac->conv.p : la.p;
-  if (!bhit) {
+  if (!bhit && !bsym) {
     lb = Buf<uint8_t>(ctx, (size_t)(B.nnzb + 1) * bbytes);
     IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
     Buf<int32_t> bsrc;
     if (B.nnzb) convert_blocks<ELT>(ctx, bs, B.val, value_src(ctx, brows.src, bvmap, B.nnzb, bsrc), B.nnzb, !tB, lb.p);
   }
-  uint8_t* const lb_p = bhit ? bpre->conv.p : lb.p;
-  if (bc && !tB && !bhit) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
+  uint8_t* const lb_p = (bhit || bsym) ? bpre->conv.p : lb.p;
+  if (bc && !tB && !bhit && !bsym) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
     bc->reset();
     bc->conv = std::move(lb);
     bc->conv_elt = ELT;
@@ -1093,7 +1100,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   const int nk_lim = ctx->narrow_kmax < 0 ? KW : ctx->narrow_kmax;
   if (bs != 64 || nk_lim > 0) {
     const BandShape sh = band_lp_shape(ELT, bs);
-    Plan Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? nk_lim : 0, amap);
+    Plan Pb = band_plan(ctx, bs, arows, A, tA, brows, B, C, crow, bs == 64 ? nk_lim : 0, amap, nullptr, bmap);
     if (bs != 64 || (Pb.kmax >= 1 && Pb.kmax <= nk_lim)) {
       const CUtensorMap mapA = make_map_bs(ELT, bs, la_p, A.nnzb + 1, sh);
       const CUtensorMap mapB = make_map_bs(ELT, bs, lb_p, B.nnzb + 1, sh);
@@ -1107,7 +1114,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   }
   const CUtensorMap mapA = make_map<ELT>(la_p, A.nnzb + 1);
   const CUtensorMap mapB = make_map<ELT>(lb_p, B.nnzb + 1);
-  Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false, 0, amap);
+  Plan P = make_plan<PAIR * TM, Cf::TN>(ctx, arows, A, tA, brows, B, C, crow, false, 0, amap, nullptr, bmap);
   static std::atomic<unsigned long long> attr{0};
   if (first_on_device(attr, ctx->device))
     IFAC_CK(cudaFuncSetAttribute(k_gemm_tc<ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM_BYTES));

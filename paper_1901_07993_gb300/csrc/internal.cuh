@@ -186,6 +186,8 @@ struct OperandCache {
   bool from_b = false;     // filled from an op(B) (see above)
   bool b_ready = false;    // conv is this matrix's op(B) copy (transposed blocks, stored order),
                            // written by its producer (poly2_operand): the product uses it as is
+  Buf<int32_t> tpos;       // an exactly symmetric matrix with its op(A) copy in conv: the
+                           // position of each block's transpose, so conv serves op(B) too
   int conv_elt = 0;        // bytes per element of conv (4 TF32, 2 BF16); 0 empty
   Buf<uint8_t> conv;       // (nnzb + 1) blocks, the last one zero
   int split_ns = 0;        // slices held (0 empty)
@@ -197,6 +199,7 @@ struct OperandCache {
   void reset() {
     from_b = false;
     b_ready = false;
+    tpos.reset();
     conv_elt = 0;
     conv.reset();
     split_ns = 0;
@@ -245,11 +248,19 @@ void autotune(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, co
 // its bounded waits expire after wait_limit polls (sets the device error flag).
 void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit);
 // bmap / umap: value maps of B / U (Mat::vmap), or null
+// lp / lp_elt: a low-precision copy of C in the layout of an op(A) operand
+// ((C.nnzb + 1) blocks, the caller zeroes the last), lp_elt 4 TF32, 2 BF16
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
-                 double gamma, ifac_bsr& C, const int32_t* crow, const int32_t* bmap = nullptr);
+                 double gamma, ifac_bsr& C, const int32_t* crow, const int32_t* bmap = nullptr, void* lp = nullptr,
+                 int lp_elt = 0);
 // C = alpha (U + strict_upper(U)^T) + beta B + gamma I on the pattern of sym_pattern
+// mirror: diagonal blocks are completed from their upper triangle too
 void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow, const int32_t* umap = nullptr);
+                 ifac_bsr& C, const int32_t* crow, const int32_t* umap = nullptr, bool mirror = false,
+                 void* lp = nullptr, int lp_elt = 0);
+// out[q]: the position in A of the transpose (J, I) of A's block q = (I, J)
+// (row: each block's row index); A's pattern symmetric
+void transposed_positions(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, int32_t* out);
 void block_norms(ifac_ctx* ctx, const ifac_bsr& A, double* norms);
 // per block-row sum of squared block norms
 void row_sq_norms(ifac_ctx* ctx, const ifac_bsr& A, double* rowsq);
@@ -317,13 +328,17 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
 // copy in precision prec (TF32 or BF16) is in *pc
 Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2, int prec,
                   OperandCache* pc, const int32_t* umap = nullptr);
+// lp_prec (IFAC_TF32 / IFAC_BF16) with lpc: the result's op(A) copy in that
+// format is written into *lpc with the FP64 values (no conversion pass later)
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
-        const int32_t* bmap = nullptr);
+        const int32_t* bmap = nullptr, int lp_prec = 0, OperandCache* lpc = nullptr);
 // the symmetric matrix whose upper block triangle (J >= I) is held by U,
 // times alpha, plus beta B and gamma I: alpha (U + strict_upper(U)^T) +
 // beta B + gamma I, rounded as add() rounds alpha A + beta B + gamma I
+// mirror: the result is made exactly symmetric (diagonal blocks from their
+// upper triangle), and with lpc its copy serves op(B) as well (lpc->tpos)
 Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-            const int32_t* umap = nullptr);
+            const int32_t* umap = nullptr, bool mirror = false, int lp_prec = 0, OperandCache* lpc = nullptr);
 Mat truncate(ifac_ctx* ctx, const ifac_bsr& A, double tau);
 Mat copy_mat(ifac_ctx* ctx, const ifac_bsr& A);
 void validate(const ifac_bsr* A, const char* name);

@@ -58,8 +58,21 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   return R;
 }
 
+// the low-precision copy of a sum's result (op(A) layout, one zero block appended)
+static void* lp_copy_alloc(ifac_ctx* ctx, const ifac_bsr& C, int lp_prec, OperandCache* lpc, int* elt) {
+  *elt = 0;
+  if (!lpc || (lp_prec != IFAC_TF32 && lp_prec != IFAC_BF16)) return nullptr;
+  *elt = lp_prec == IFAC_BF16 ? 2 : 4;
+  const size_t bb = (size_t)C.bs * C.bs * (*elt);
+  lpc->reset();
+  lpc->conv = Buf<uint8_t>(ctx, (size_t)(C.nnzb + 1) * bb);
+  lpc->conv_elt = *elt;
+  IFAC_CK(cudaMemsetAsync(lpc->conv.p + (size_t)C.nnzb * bb, 0, bb, ctx->stream));
+  return lpc->conv.p;
+}
+
 Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-            const int32_t* umap) {
+            const int32_t* umap, bool mirror, int lp_prec, OperandCache* lpc) {
   Pattern P = sym_pattern(ctx, U, B, gamma != 0.0);
   Mat C(ctx);
   C.m.n = U.n;
@@ -70,7 +83,13 @@ Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const i
   C.m.col_idx = P.ci.release();
   C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * U.bs * U.bs));
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
-  sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p, umap);
+  int elt = 0;
+  void* lp = lp_copy_alloc(ctx, C.m, lp_prec, lpc, &elt);
+  sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p, umap, mirror, lp, elt);
+  if (lp && mirror) {
+    lpc->tpos = Buf<int32_t>(ctx, (size_t)(C.m.nnzb ? C.m.nnzb : 1));
+    transposed_positions(ctx, C.m, P.row.p, lpc->tpos.p);
+  }
   return C;
 }
 
@@ -94,7 +113,7 @@ Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1
 }
 
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
-        const int32_t* bmap) {
+        const int32_t* bmap, int lp_prec, OperandCache* lpc) {
   Pattern P = union_pattern(ctx, A, B, gamma != 0.0);
   Mat C(ctx);
   C.m.n = A.n;
@@ -105,7 +124,9 @@ Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_
   C.m.col_idx = P.ci.release();
   C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
-  add_numeric(ctx, alpha, A, beta, B, gamma, C.m, P.row.p, bmap);
+  int elt = 0;
+  void* lp = lp_copy_alloc(ctx, C.m, lp_prec, lpc, &elt);
+  add_numeric(ctx, alpha, A, beta, B, gamma, C.m, P.row.p, bmap, lp, elt);
   return C;
 }
 

@@ -170,6 +170,12 @@ __global__ void k_find_src(const int32_t* __restrict__ rp, const int32_t* __rest
   src[q] = lo;
 }
 
+void transposed_positions(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, int32_t* out) {
+  if (A.nnzb == 0) return;
+  k_find_src<<<cdiv(A.nnzb, 256), 256, 0, ctx->stream>>>(A.row_ptr, A.col_idx, A.nnzb, row, A.col_idx, out);
+  IFAC_CK_LAUNCH();
+}
+
 View view_rows(ifac_ctx* ctx, const ifac_bsr& A, bool trans) {
   View v;
   if (!trans) {
