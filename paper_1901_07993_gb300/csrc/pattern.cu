@@ -14,39 +14,52 @@ namespace ifac {
 int words_per_row(int nb) { return (nb + 31) / 32; }
 
 // ---------------------------------------------------------------------------
-// exclusive scan of n int32 (single CTA, chunked, carries between chunks)
+// exclusive scan of n int32 (single CTA): each thread takes 16 consecutive
+// entries (loads issued together), the CTA scans the thread totals, carries
+// between chunks of 16 blockDim entries; out[n] = the total
 // ---------------------------------------------------------------------------
 __global__ void k_scan_excl(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n) {
+  constexpr int K = 16;
   __shared__ int32_t wsum[32];
   __shared__ int32_t carry;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < n; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    int v = (i < n) ? in[i] : 0;
-    int x = v;
+  for (int base = 0; base < n; base += blockDim.x * K) {
+    const int i0 = base + threadIdx.x * K;
+    int v[K];
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      v[k] = (i0 + k < n) ? in[i0 + k] : 0;
+      t += v[k];
+    }
+    int x = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, x, o);
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-      int s = (lane < nw) ? wsum[lane] : 0;
+      int sw = (lane < nw) ? wsum[lane] : 0;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += y;
+        const int y = __shfl_up_sync(0xffffffffu, sw, o);
+        if (lane >= o) sw += y;
       }
-      wsum[lane] = s;
+      wsum[lane] = sw;
     }
     __syncthreads();
-    int excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
-    if (i < n) out[i] = excl;
+    int run = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - t;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (i0 + k < n) out[i0 + k] = run;
+      run += v[k];
+    }
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    if (threadIdx.x == blockDim.x - 1) carry = run;
     __syncthreads();
   }
   if (threadIdx.x == 0) out[n] = carry;
