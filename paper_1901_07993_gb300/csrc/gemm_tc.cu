@@ -1299,12 +1299,13 @@ __device__ __forceinline__ void split_pair(double x0, double x1, int e, int ns, 
   int q0[8], q1[8];
   split_digits(x0, e, ns, q0);
   split_digits(x1, e, ns, q1);
-  for (int k = 0; k < ns; ++k) {
-    __nv_bfloat162 v;
-    v.x = __float2bfloat16_rn((float)q0[k]);
-    v.y = __float2bfloat16_rn((float)q1[k]);
-    *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)k * slice_stride) = v;
-  }
+  // |q| <= 128 is exact in BF16: the upper half of its FP32 pattern, formed
+  // with one integer and one FP32 add (2^23 + 2^22 + q, minus that offset)
+  const auto bf = [](int q) -> uint32_t {
+    return __float_as_uint(__int_as_float(0x4B400000 + q) - 12582912.0f) >> 16;
+  };
+  for (int k = 0; k < ns; ++k)
+    *reinterpret_cast<uint32_t*>(dst + (size_t)k * slice_stride) = bf(q0[k]) | (bf(q1[k]) << 16);
 }
 
 template <int B>
