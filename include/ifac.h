@@ -186,7 +186,11 @@ typedef struct {
 /* ---------------------------------------------------------------- */
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL
- * = legacy default stream).  alloc: NULL for the built-in pool, else copied. */
+ * = legacy default stream).  alloc: NULL for the built-in pool, else copied.
+ * With the built-in pool the context keeps device blocks of up to 4 GB that
+ * it frees (24 GB in all at most) and hands them out again in the order of
+ * its stream; ifac_destroy returns them, and a failed allocation returns
+ * them before it is retried.  ifac_set_stream waits for the old stream. */
 int ifac_create(ifac_ctx** ctx, void* stream, const ifac_allocator* alloc);
 void ifac_destroy(ifac_ctx* ctx);
 int ifac_set_stream(ifac_ctx* ctx, void* stream);
