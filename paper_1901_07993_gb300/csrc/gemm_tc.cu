@@ -1212,15 +1212,22 @@ __global__ void __launch_bounds__(B) k_row_scale_t(const int32_t* __restrict__ r
                                                    unsigned int* __restrict__ l1max, unsigned int* __restrict__ l2max) {
   const int I = blockIdx.x, r = threadIdx.x;
   if (I >= nb) return;
-  unsigned long long m = 0;
-  float l1 = 0.0f;
-  double sq = 0.0;
+  // four independent accumulators (rows k mod 4 of each block) so that the
+  // FP64 FMA and FP32 add chains overlap; combined at the end
+  unsigned long long m[4] = {0, 0, 0, 0};
+  float l1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  double sq[4] = {0.0, 0.0, 0.0, 0.0};
   for (int q = rp[I]; q < rp[I + 1]; ++q) {
     const double* blk = val + (size_t)(src ? src[q] : q) * B * B;
-#pragma unroll 8
-    for (int k = 0; k < B; ++k) row_scale_acc(blk[k * B + r], m, l1, sq);
+#pragma unroll 4
+    for (int k = 0; k < B; k += 4) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) row_scale_acc(blk[(k + j) * B + r], m[j], l1[j], sq[j]);
+    }
   }
-  row_scale_out(m, l1, sq, (rp[I + 1] - rp[I]) * B, eout + (size_t)I * B + r, l1max, l2max);
+  const unsigned long long m01 = m[0] > m[1] ? m[0] : m[1], m23 = m[2] > m[3] ? m[2] : m[3];
+  row_scale_out(m01 > m23 ? m01 : m23, (l1[0] + l1[1]) + (l1[2] + l1[3]), (sq[0] + sq[1]) + (sq[2] + sq[3]),
+                (rp[I + 1] - rp[I]) * B, eout + (size_t)I * B + r, l1max, l2max);
 }
 
 // rows stored as rows: one warp per scalar row, lanes along the row (coalesced)
