@@ -202,6 +202,14 @@ int ifac_set_stream(ifac_ctx* ctx, void* stream);
  * count as its maximum and uses fewer slices for delta evaluations whose
  * result only needs to resolve the next sweep (see inv_factor_refine). */
 int ifac_set_split_slices(ifac_ctx* ctx, int slices);
+/* Whether the mixed-precision refinements (inv_factor_refine and
+ * inv_factor_refine_batched with TF32/BF16) keep the results of their
+ * low-precision products -- X = S Z, the upper triangle of Z^T X, delta^2
+ * and M = Z P -- in FP32 (on, the default) or in FP64 (off).  These results
+ * are FP32 accumulators, so both settings give bitwise the same factors; FP32
+ * halves the bytes these intermediates take in memory and move through HBM.
+ * Returns IFAC_ERR_INVALID for a NULL context. */
+int ifac_set_fp32_intermediates(ifac_ctx* ctx, int on);
 const char* ifac_last_error(const ifac_ctx* ctx);
 void ifac_opts_default(ifac_opts* opts);
 

@@ -107,6 +107,7 @@ void Mat::reset() {
   dfree(ctx, m.val);
   dfree(ctx, m.norms);
   m = ifac_bsr{};
+  f32 = false;
 }
 
 Mat mat_alloc(ifac_ctx* ctx, int64_t n, int bs, int nb, int64_t nnzb) {
@@ -328,6 +329,12 @@ int ifac_set_stream(ifac_ctx* ctx, void* stream) {
 int ifac_set_split_slices(ifac_ctx* ctx, int slices) {
   if (!ctx || slices < 3 || slices > 8) return IFAC_ERR_INVALID;
   ctx->split_slices = slices;
+  return IFAC_OK;
+}
+
+int ifac_set_fp32_intermediates(ifac_ctx* ctx, int on) {
+  if (!ctx) return IFAC_ERR_INVALID;
+  ctx->fp32_mid = on != 0;
   return IFAC_OK;
 }
 

@@ -225,12 +225,16 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         OperandCache zcache;  // Z's copy (op(B) of S Z) serves again as op(A) = Z^T
         // truncated products keep their kept blocks in place where the next
         // step reads them through a value map (no compaction copies)
+        // (low-precision sweeps keep X and Y's upper triangle in FP32, as
+        // their products accumulated them)
         const bool inplace = pd != IFAC_FP64;
-        Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd, false, nullptr, &zcache, nullptr, inplace);  // S Z
+        const bool lp = (pd == IFAC_TF32 || pd == IFAC_BF16) && ctx->fp32_mid;
+        Mat X = gemm(ctx, Sa.m, false, Z.m, false, 1.0, tau, pd, false, nullptr, &zcache, nullptr, inplace, nullptr,
+                     nullptr, lp);  // S Z
         Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, pd, sym, &zcache, nullptr, nullptr, sym, nullptr,
-                     X.map());  // Z^T (S Z)
+                     X.map(), lp && sym, X.f32);  // Z^T (S Z)
         X.reset();
-        Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map())  // I - Z^T S Z
+        Dall = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map(), false, 0, nullptr, Y.f32)  // I - Z^T S Z
                    : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
       }
       IFAC_CK(cudaMemcpyAsync(dactive.p, active.data(), count, cudaMemcpyHostToDevice, ctx->stream));
@@ -318,10 +322,10 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
           const bool sym = low && bs == 64;
           const bool fused = sym && k == 2 && o.m == 2;
           Mat Dn = gemm(ctx, k == 2 ? D.m : Dk.m, false, D.m, false, 1.0, tau, o.prec, sym, nullptr, nullptr, nullptr,
-                        fused);
-          if (fused) {  // delta^2 completed by symmetry inside the sum
+                        fused, nullptr, nullptr, fused && ctx->fp32_mid);
+          if (fused) {  // delta^2 (in FP32) completed by symmetry inside the sum
             // P only as the low-precision op(B) copy that M = Z P reads
-            P = poly2_operand(ctx, Dn.m, D.m, 0.5, b, o.prec, &pcache, Dn.map());
+            P = poly2_operand(ctx, Dn.m, D.m, 0.5, b, o.prec, &pcache, Dn.map(), Dn.f32);
             break;
           }
           if (sym) Dn = sym_sum(ctx, 1.0, Dn.m, 0.0, nullptr, 0.0);
@@ -330,9 +334,10 @@ int refine_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* Sv, double t
         }
       }
       D.reset();
-      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec, false, &znat, nullptr, &pcache, true);  // M = Z P
+      Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, o.prec, false, &znat, nullptr, &pcache, true, nullptr,
+                   nullptr, ctx->fp32_mid);  // M = Z P (FP32 when low precision)
       P.reset();
-      Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map(), o.prec, &znat);  // with Z's copy for the next M
+      Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map(), o.prec, &znat, M.f32);  // with Z's copy for the next M
       for (int k = 0; k < count; ++k)
         if (active[k]) {
           ++sweeps[k];

@@ -74,12 +74,18 @@ __device__ __forceinline__ double scaled(const Scale& s, double x) {
   return __dmul_rn(s.alpha, x);
 }
 
-__device__ __forceinline__ double add_elem(const Scale& sa, const double* a, const Scale& sb, const double* b,
-                                           bool diag, double gamma, int e, int ea = -1) {
+// an operand value as FP64: FP32 values (the exact results of a TF32/BF16
+// product) are widened on the bit pattern, off the FP64 pipe
+__device__ __forceinline__ double as_f64(double x) { return x; }
+__device__ __forceinline__ double as_f64(float x) { return ifac::tc::f32_to_f64(x); }
+
+template <typename TA, typename TB>
+__device__ __forceinline__ double add_elem(const Scale& sa, const TA* a, const Scale& sb, const TB* b, bool diag,
+                                           double gamma, int e, int ea = -1) {
   double v = 0.0;
-  if (a) v = scaled(sa, a[ea < 0 ? e : ea]);
+  if (a) v = scaled(sa, as_f64(a[ea < 0 ? e : ea]));
   if (b) {
-    const double t = scaled(sb, b[e]);
+    const double t = scaled(sb, as_f64(b[e]));
     v = a ? __dadd_rn(v, t) : t;
   }
   if (diag) v = (a || b) ? __dadd_rn(v, gamma) : gamma;
@@ -105,12 +111,13 @@ __device__ __forceinline__ void lp_store2(void* lp, int lp_elt, size_t i, double
 // one warp per output block (grid-stride over blocks).  Element by element
 // v = 0 + alpha a + beta b + gamma [diagonal], left to right, each step
 // rounded; the leading 0 + x is x.  The FP64 Frobenius norm of the block.
-// Lanes take consecutive elements (VEC of them: two for even bs * bs).
-template <int VEC>
+// Lanes take consecutive elements (VEC of them: two for even bs * bs).  B's
+// values are FP64 or FP32 (TB).
+template <int VEC, typename TB>
 __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t cnnz, int bs,
                       Scale sa, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                       const double* __restrict__ aval, Scale sb, const int32_t* __restrict__ brp,
-                      const int32_t* __restrict__ bci, const double* __restrict__ bval,
+                      const int32_t* __restrict__ bci, const TB* __restrict__ bval,
                       const int32_t* __restrict__ bmap, double gamma, double* __restrict__ cval,
                       double* __restrict__ cnorm, void* __restrict__ lp, int lp_elt) {
   const int lane = threadIdx.x & 31;
@@ -131,7 +138,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
     qa = __shfl_sync(0xffffffffu, qa, 0);
     qb = __shfl_sync(0xffffffffu, qb, 0);
     const double* a = qa >= 0 ? aval + (size_t)qa * bsz : nullptr;
-    const double* b = qb >= 0 ? bval + (size_t)(bmap ? bmap[qb] : qb) * bsz : nullptr;
+    const TB* b = qb >= 0 ? bval + (size_t)(bmap ? bmap[qb] : qb) * bsz : nullptr;
     double* c = cval + (size_t)p * bsz;
     const bool dblk = I == J && gamma != 0.0;
     SqAcc sq;
@@ -157,7 +164,7 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
 }
 
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow, const int32_t* bmap, void* lp, int lp_elt) {
+                 ifac_bsr& C, const int32_t* crow, const int32_t* bmap, void* lp, int lp_elt, bool b32) {
   if (lp_elt && (C.bs * C.bs) % 2 != 0) fail(IFAC_ERR_UNSUPPORTED, "low-precision copy: even bs * bs");
   if (C.nnzb == 0) return;
   const int64_t warps = std::min<int64_t>(C.nnzb, 152 * 64);
@@ -165,14 +172,19 @@ void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, co
   const int32_t* brp = B ? B->row_ptr : nullptr;
   const int32_t* bci = B ? B->col_idx : nullptr;
   const double* bv = B ? B->val : nullptr;
-  if ((C.bs * C.bs) % 2 == 0)  // pairs never straddle two blocks
-    k_add<2><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
-                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms, lp,
-                                                             lp_elt);
-  else
-    k_add<1><<<cdiv(warps * 32, 256), 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx,
-                                                             A.val, sb, brp, bci, bv, bmap, gamma, C.val, C.norms, nullptr,
-                                                             0);
+  const int grid = cdiv(warps * 32, 256);
+  if (b32 && B) {
+    if ((C.bs * C.bs) % 2 != 0) fail(IFAC_ERR_UNSUPPORTED, "FP32 operand values: even bs * bs");
+    k_add<2, float><<<grid, 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx, A.val, sb,
+                                                   brp, bci, reinterpret_cast<const float*>(bv), bmap, gamma, C.val,
+                                                   C.norms, lp, lp_elt);
+  } else if ((C.bs * C.bs) % 2 == 0) {  // pairs never straddle two blocks
+    k_add<2, double><<<grid, 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx, A.val,
+                                                    sb, brp, bci, bv, bmap, gamma, C.val, C.norms, lp, lp_elt);
+  } else {
+    k_add<1, double><<<grid, 256, 0, ctx->stream>>>(crow, C.col_idx, C.nnzb, C.bs, sa, A.row_ptr, A.col_idx, A.val,
+                                                    sb, brp, bci, bv, bmap, gamma, C.val, C.norms, nullptr, 0);
+  }
   IFAC_CK_LAUNCH();
 }
 
@@ -181,12 +193,13 @@ void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, co
 // block (I, J), J < I, takes alpha U_JI^T in place of alpha U_IJ, moved
 // through shared memory in stripes of four output rows (four 32-byte column
 // segments of U_JI per source row), so reads and writes are whole sectors.
-// bs = 64.
+// bs = 64.  U's values are FP64 or FP32 (TU).
 constexpr int SYM_WARPS = 8;
 
+template <typename TU>
 __global__ void __launch_bounds__(32 * SYM_WARPS)
     k_sym(const int32_t* __restrict__ crow, const int32_t* __restrict__ cci, int64_t cnnz, Scale sa,
-          const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval,
+          const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const TU* __restrict__ uval,
           const int32_t* __restrict__ umap, Scale sb,
           const int32_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bval,
           double gamma, double* __restrict__ cval, double* __restrict__ cnorm, int mirror, void* __restrict__ lp,
@@ -212,7 +225,7 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
     }
     qu = __shfl_sync(0xffffffffu, qu, 0);
     qb = __shfl_sync(0xffffffffu, qb, 0);
-    const double* u = qu >= 0 ? uval + (size_t)(umap ? umap[qu] : qu) * BSZ : nullptr;
+    const TU* u = qu >= 0 ? uval + (size_t)(umap ? umap[qu] : qu) * BSZ : nullptr;
     const double* b = qb >= 0 ? bval + (size_t)qb * BSZ : nullptr;
     double* out = cval + (size_t)p * BSZ;
     const bool dblk = I == J && gamma != 0.0;
@@ -239,7 +252,7 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int idx = k * 32 + lane, s = idx >> 2, j = idx & 3;
-          st[j][s] = scaled(sa, u[s * BS + r0 + j]);
+          st[j][s] = scaled(sa, as_f64(u[s * BS + r0 + j]));
         }
         __syncwarp();
         // output rows r0..r0+3: alpha U_JI^T (+ beta B_IJ), columns 0..63
@@ -267,14 +280,20 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
 }
 
 void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-                 ifac_bsr& C, const int32_t* crow, const int32_t* umap, bool mirror, void* lp, int lp_elt) {
+                 ifac_bsr& C, const int32_t* crow, const int32_t* umap, bool mirror, void* lp, int lp_elt, bool u32) {
   if (C.nnzb == 0) return;
   if (U.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "symmetric completion needs bs = 64");
   const int64_t ctas = std::min<int64_t>(cdiv(C.nnzb, SYM_WARPS), 152 * 8);
-  k_sym<<<(int)ctas, 32 * SYM_WARPS, 0, ctx->stream>>>(
-      crow, C.col_idx, C.nnzb, make_scale(alpha), U.row_ptr, U.col_idx, U.val, umap, make_scale(beta),
-      B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr, gamma, C.val, C.norms,
-      mirror ? 1 : 0, lp, lp_elt);
+  if (u32)
+    k_sym<float><<<(int)ctas, 32 * SYM_WARPS, 0, ctx->stream>>>(
+        crow, C.col_idx, C.nnzb, make_scale(alpha), U.row_ptr, U.col_idx, reinterpret_cast<const float*>(U.val), umap,
+        make_scale(beta), B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr, gamma, C.val,
+        C.norms, mirror ? 1 : 0, lp, lp_elt);
+  else
+    k_sym<double><<<(int)ctas, 32 * SYM_WARPS, 0, ctx->stream>>>(
+        crow, C.col_idx, C.nnzb, make_scale(alpha), U.row_ptr, U.col_idx, U.val, umap, make_scale(beta),
+        B ? B->row_ptr : nullptr, B ? B->col_idx : nullptr, B ? B->val : nullptr, gamma, C.val, C.norms,
+        mirror ? 1 : 0, lp, lp_elt);
   IFAC_CK_LAUNCH();
 }
 

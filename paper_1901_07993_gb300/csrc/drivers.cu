@@ -35,10 +35,11 @@ static Mat poly_P(ifac_ctx* ctx, const ifac_bsr& delta, int m, double tau, int p
                   bool sym = false, OperandCache* pc = nullptr, OperandCache* dc = nullptr) {
   if (m < 2) return add(ctx, coef_b(1), delta, 0.0, nullptr, 0.0);
   const bool fused = sym && m == 2 && pc && (prec == IFAC_TF32 || prec == IFAC_BF16);
-  // (fused: delta^2's kept blocks stay in place for the P kernel; dc: delta's
-  // low-precision copy from its producer, serving both operands)
-  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym, dc, nullptr, dc, fused);
-  if (fused) return poly2_operand(ctx, D.m, delta, coef_b(1), coef_b(2), prec, pc, D.map());
+  // (fused: delta^2's kept blocks stay in place, in FP32, for the P kernel;
+  // dc: delta's low-precision copy from its producer, serving both operands)
+  Mat D = gemm(ctx, delta, false, delta, false, 1.0, tau, prec, sym, dc, nullptr, dc, fused, nullptr, nullptr,
+               fused && ctx->fp32_mid);
+  if (fused) return poly2_operand(ctx, D.m, delta, coef_b(1), coef_b(2), prec, pc, D.map(), D.f32);
   if (sym && m == 2) return sym_sum(ctx, coef_b(2), D.m, coef_b(1), &delta, 0.0);
   if (sym) D = sym_sum(ctx, 1.0, D.m, 0.0, nullptr, 0.0);
   Mat P = add(ctx, coef_b(1), delta, coef_b(2), &D.m, 0.0);
@@ -245,14 +246,18 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
       // Z's converted copy (op(B) of S Z) serves again as op(A) = Z^T
       // truncated products keep their kept blocks in place where the next
       // step reads them through a value map (no compaction copies)
+      // low-precision sweeps keep X and the upper triangle of Y in FP32, as
+      // their products accumulated them (the next step reads them exactly)
       OperandCache zcache;
       const bool inplace = dprec != IFAC_FP64;
-      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache, &zcache, nullptr, inplace);  // S Z
+      const bool lp = (dprec == IFAC_TF32 || dprec == IFAC_BF16) && ctx->fp32_mid;
+      Mat X = gemm(ctx, S.m, false, Z.m, false, 1.0, tau, dprec, false, &scache, &zcache, nullptr, inplace, nullptr,
+                   nullptr, lp);  // S Z
       Mat Y = gemm(ctx, Z.m, true, X.m, false, 1.0, tau, dprec, sym, &zcache, nullptr, nullptr, sym, nullptr,
-                   X.map());  // Z^T (S Z), J >= I
+                   X.map(), lp && sym, X.f32);  // Z^T (S Z), J >= I
       X.reset();
       // I - Z^T S Z, exactly symmetric, with its low-precision copy for delta^2
-      D = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map(), true, low, &dcache)
+      D = sym ? sym_sum(ctx, -1.0, Y.m, 0.0, nullptr, 1.0, Y.map(), true, low, &dcache, Y.f32)
               : add(ctx, -1.0, Y.m, 0.0, nullptr, 1.0);
     }
     e = fro_host(ctx, D.m);
@@ -302,9 +307,10 @@ int refine_irsi_mixed(ifac_ctx* ctx, const ifac_bsr& S_in, double tau, double ta
     Mat P = poly_P(ctx, D.m, o.m, tau, low, sym, &pcache, sym ? &dcache : nullptr);
     D.reset();
     dcache.reset();
-    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low, false, &znat, nullptr, &pcache, true);  // M = Z P
+    Mat M = gemm(ctx, Z.m, false, P.m, false, 1.0, tau, low, false, &znat, nullptr, &pcache, true, nullptr, nullptr,
+                 ctx->fp32_mid);  // M = Z P, kept in FP32
     P.reset();
-    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map(), low, &znat);  // with Z's copy for the next M
+    Z = add(ctx, 1.0, Z.m, 1.0, &M.m, 0.0, M.map(), low, &znat, M.f32);  // with Z's copy for the next M
     ++sweeps;
     e_prev = e;
     if (!fp64_phase) {

@@ -24,7 +24,8 @@
 //   warps 2..17 : epilogue -- four warps per tensor-memory lane quarter,
 //                 each on a quarter of the tile's columns: tcgen05.ld, alpha,
 //                 block Frobenius norms (compensated FP32 sums, about 2^-42),
-//                 FP64 stores through a shared-memory transpose so that stores
+//                 FP64 (or, for the mixed refinement's intermediates, FP32)
+//                 stores through a shared-memory transpose so that stores
 //                 are row segments; one named barrier per tile.
 //
 // Every mbarrier wait is bounded; on expiry the CTA records the error flag and
@@ -86,6 +87,7 @@ struct BandLpArgs {
   const int32_t* rec_off;   // first record of each tile
   const int32_t* cpos;      // per tile, the C positions of its TMB x TNB blocks (-1: not in C)
   double* cval;
+  float* cval32;  // non-null: C's values as FP32 (the accumulators exactly) in place of cval
   double* cnorm;
   int nb;
   double alpha;
@@ -295,16 +297,26 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
           // 32 rows x 8 columns through shared memory, so that each store
           // instruction writes eight 64-byte row segments, two values per lane
           float* sw = ep_stage[ew];
-          double* blk = args.cval + (size_t)p * BS * BS + (size_t)rin * BS + (col0 % BS);
+          const size_t boff = (size_t)p * BS * BS + (size_t)rin * BS + (col0 % BS);
           const int c2 = (lane & 3) * 2, r8 = lane >> 2;
 #pragma unroll
           for (int e = 0; e < 8; ++e) sw[lane * 9 + e] = v[e];
           __syncwarp();
+          if (args.cval32) {  // kernel-uniform: FP32 values, eight 32-byte row segments per store
+            float* blk = args.cval32 + boff;
 #pragma unroll
-          for (int k = 0; k < 32; k += 8) {
-            const float* qv = sw + (k + r8) * 9 + c2;
-            *reinterpret_cast<double2*>(blk + (size_t)(k + r8) * BS + c2) =
-                make_double2(f32_to_f64(qv[0]), f32_to_f64(qv[1]));
+            for (int k = 0; k < 32; k += 8) {
+              const float* qv = sw + (k + r8) * 9 + c2;
+              *reinterpret_cast<float2*>(blk + (size_t)(k + r8) * BS + c2) = make_float2(qv[0], qv[1]);
+            }
+          } else {
+            double* blk = args.cval + boff;
+#pragma unroll
+            for (int k = 0; k < 32; k += 8) {
+              const float* qv = sw + (k + r8) * 9 + c2;
+              *reinterpret_cast<double2*>(blk + (size_t)(k + r8) * BS + c2) =
+                  make_double2(f32_to_f64(qv[0]), f32_to_f64(qv[1]));
+            }
           }
           __syncwarp();
         }
@@ -365,7 +377,7 @@ static void shape_of(BandShape* s) {
 // the host entry used by gemm_tc.cu's dispatcher
 void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const void* mapB, const int32_t* tiles,
                      const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
-                     const int32_t* cpos, int tiles_bound, double alpha, ifac_bsr& C) {
+                     const int32_t* cpos, int tiles_bound, double alpha, ifac_bsr& C, bool out32) {
   tc::BandLpArgs a{};
   a.tiles = tiles;
   a.ntiles = ntiles;
@@ -373,7 +385,8 @@ void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const voi
   a.rec = rec;
   a.rec_off = rec_off;
   a.cpos = cpos;
-  a.cval = C.val;
+  a.cval = out32 ? nullptr : C.val;
+  a.cval32 = out32 ? reinterpret_cast<float*>(C.val) : nullptr;
   a.cnorm = C.norms;
   a.nb = C.nb;
   a.alpha = alpha;

@@ -99,6 +99,8 @@ struct TileArgs {
   const int32_t* crp;    // C pattern
   const int32_t* cci;
   double* cval;
+  float* cval32;  // TF32/BF16 products: non-null, C's values as FP32 (the
+                  // accumulators exactly, half the bytes of cval) in place of cval
   double* cnorm;
   // split mode: fixed-point sums, per C block 2048 longlong2 in hand-over
   // order ((row half, column half, pair e) x 32 lanes), so that a warp's
@@ -385,16 +387,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               // 32 rows x 16 columns at a time through shared memory, so that
               // each store instruction writes two 128-byte row segments
               float* sw = ep_stage[warp - 2];
-              double* blk = args.cval + (size_t)p * BS * BS + (size_t)((q & 1) * 32) * BS + h * 32;
+              const size_t boff = (size_t)p * BS * BS + (size_t)((q & 1) * 32) * BS + h * 32;
               const int cc = lane & 15, rr = lane >> 4;
 #pragma unroll
               for (int half = 0; half < 2; ++half) {
 #pragma unroll
                 for (int e = 0; e < 16; ++e) sw[lane * 17 + e] = v[half * 16 + e];
                 __syncwarp();
+                if (args.cval32) {  // kernel-uniform
+                  float* blk = args.cval32 + boff;
 #pragma unroll 4
-                for (int k = 0; k < 32; k += 2)
-                  blk[(size_t)(k + rr) * BS + half * 16 + cc] = f32_to_f64(sw[(k + rr) * 17 + cc]);
+                  for (int k = 0; k < 32; k += 2) blk[(size_t)(k + rr) * BS + half * 16 + cc] = sw[(k + rr) * 17 + cc];
+                } else {
+                  double* blk = args.cval + boff;
+#pragma unroll 4
+                  for (int k = 0; k < 32; k += 2)
+                    blk[(size_t)(k + rr) * BS + half * 16 + cc] = f32_to_f64(sw[(k + rr) * 17 + cc]);
+                }
                 __syncwarp();
               }
             }
@@ -475,20 +484,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // ---------------------------------------------------------------------------
 // dst[q] = low-precision copy of block src[q] of X (B x B blocks; K-major:
 // transposed when tr).  Reads are coalesced; a transposed copy goes through
-// shared memory in 32 x 32 sub-blocks.
-template <int ELT, int B>
-__global__ void __launch_bounds__(256) k_convert(const double* __restrict__ val, const int32_t* __restrict__ src,
+// shared memory in 32 x 32 sub-blocks.  X's values are FP64 (V = double) or
+// the FP32 results of a TF32/BF16 product (V = float), rounded alike.
+template <int ELT, int B, typename V>
+__global__ void __launch_bounds__(256) k_convert(const V* __restrict__ val, const int32_t* __restrict__ src,
                                                  int64_t nblk, int tr, void* __restrict__ dst) {
   constexpr int BSZ = B * B;
   using T = typename std::conditional<ELT == 2, uint16_t, uint32_t>::type;
   __shared__ T tile[32][33];
-  auto conv = [](double x) -> T {
-    if constexpr (ELT == 2) return f64_to_bf16_bits_rne(x);
-    else return f32_to_tf32(__uint_as_float(f64_to_f32_bits_rne(x)));
+  auto conv = [](V x) -> T {
+    if constexpr (std::is_same<V, float>::value) {
+      if constexpr (ELT == 2) return f32_to_bf16_bits_rne(x);
+      else return f32_to_tf32(f32_flush(x));
+    } else {
+      if constexpr (ELT == 2) return f64_to_bf16_bits_rne(x);
+      else return f32_to_tf32(__uint_as_float(f64_to_f32_bits_rne(x)));
+    }
   };
   T* out = reinterpret_cast<T*>(dst);
   for (int64_t qb = blockIdx.x; qb < nblk; qb += gridDim.x) {
-    const double* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
+    const V* s = val + (size_t)(src ? src[qb] : qb) * BSZ;
     T* d = out + (size_t)qb * BSZ;
     if (!tr) {
       for (int e = threadIdx.x; e < BSZ; e += blockDim.x) d[e] = conv(s[e]);
@@ -537,11 +552,12 @@ static const int32_t* value_src(ifac_ctx* ctx, const int32_t* src, const int32_t
 // J >= I and U_JI^T below, U the upper block triangle of delta^2.  The block
 // is assembled in FP32 in shared memory (inputs rounded to FP32 on their bit
 // patterns, one FMA per element), then rounded to TF32 / BF16 as k_convert
-// rounds.  One CTA per block (grid-stride).
-template <int ELT>
+// rounds.  One CTA per block (grid-stride).  U's values are FP64 or the FP32
+// results of its TF32/BF16 product (UV = float), rounded alike.
+template <int ELT, typename UV>
 __global__ void __launch_bounds__(256)
     k_poly2_lp(const int32_t* __restrict__ prow, const int32_t* __restrict__ pci, int64_t pnnz,
-               const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const double* __restrict__ uval,
+               const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, const UV* __restrict__ uval,
                const int32_t* __restrict__ umap, const int32_t* __restrict__ drp, const int32_t* __restrict__ dci,
                const double* __restrict__ dval, float b1, float b2, void* __restrict__ dst) {
   constexpr int B = 64, BSZ = B * B;
@@ -549,6 +565,10 @@ __global__ void __launch_bounds__(256)
   __shared__ float t[B][B + 1];
   __shared__ int sq[2];
   const auto f32 = [](double x) { return __uint_as_float(f64_to_f32_bits_rne(x)); };
+  const auto u32 = [](UV x) {
+    if constexpr (std::is_same<UV, float>::value) return f32_flush(x);
+    else return __uint_as_float(f64_to_f32_bits_rne(x));
+  };
   T* out = reinterpret_cast<T*>(dst);
   for (int64_t p = blockIdx.x; p < pnnz; p += gridDim.x) {
     const int I = prow[p], J = pci[p];
@@ -565,13 +585,13 @@ __global__ void __launch_bounds__(256)
       t[e >> 6][e & 63] = qd >= 0 ? b1 * f32(dval[(size_t)qd * BSZ + e]) : 0.0f;
     __syncthreads();
     if (qu >= 0) {
-      const double* u = uval + (size_t)qu * BSZ;
+      const UV* u = uval + (size_t)qu * BSZ;
       if (J >= I) {
         for (int e = threadIdx.x; e < BSZ; e += blockDim.x)
-          t[e >> 6][e & 63] = fmaf(b2, f32(u[e]), t[e >> 6][e & 63]);
+          t[e >> 6][e & 63] = fmaf(b2, u32(u[e]), t[e >> 6][e & 63]);
       } else {  // U_JI read in its stored order, added transposed
         for (int e = threadIdx.x; e < BSZ; e += blockDim.x)
-          t[e & 63][e >> 6] = fmaf(b2, f32(u[e]), t[e & 63][e >> 6]);
+          t[e & 63][e >> 6] = fmaf(b2, u32(u[e]), t[e & 63][e >> 6]);
       }
       __syncthreads();
     }
@@ -1023,13 +1043,13 @@ static CUtensorMap make_map_box(int bs, void* base, int64_t nblk, int inner, int
   return m;
 }
 
-template <int ELT>
-static void convert_blocks(ifac_ctx* ctx, int bs, const double* val, const int32_t* src, int64_t nblk, bool tr,
+template <int ELT, typename V = double>
+static void convert_blocks(ifac_ctx* ctx, int bs, const V* val, const int32_t* src, int64_t nblk, bool tr,
                            void* dst) {
   const int grid = (int)std::min<int64_t>(nblk, 152 * 16);
-  if (bs == 32) k_convert<ELT, 32><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
-  else if (bs == 64) k_convert<ELT, 64><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
-  else k_convert<ELT, 128><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
+  if (bs == 32) k_convert<ELT, 32, V><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
+  else if (bs == 64) k_convert<ELT, 64, V><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
+  else k_convert<ELT, 128, V><<<grid, 256, 0, ctx->stream>>>(val, src, nblk, tr ? 1 : 0, dst);
   IFAC_CK_LAUNCH();
 }
 
@@ -1042,11 +1062,13 @@ static Plan band_plan(ifac_ctx* ctx, int bs, const View& arows, const ifac_bsr& 
   return make_plan<1, 1>(ctx, arows, A, tA, brows, B, C, crow, true, kmax_limit, amap, extra, bmap);
 }
 
+// out32: C's values are written as FP32 (C.val holds floats); b32: B's values
+// are FP32 (an earlier product's out32 result)
 template <int ELT>
 static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, const View& brows, bool tB,
                 const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                 unsigned long long* pairs, OperandCache* ac, OperandCache* bc, const OperandCache* bpre,
-                const int32_t* avmap, const int32_t* bvmap) {
+                const int32_t* avmap, const int32_t* bvmap, bool out32, bool b32) {
   using Cf = Cfg<ELT>;
   const int nb = A.nb, bs = A.bs;
   const size_t bbytes = (size_t)bs * bs * ELT;
@@ -1080,7 +1102,11 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
     lb = Buf<uint8_t>(ctx, (size_t)(B.nnzb + 1) * bbytes);
     IFAC_CK(cudaMemsetAsync(lb.p + (size_t)B.nnzb * bbytes, 0, bbytes, ctx->stream));
     Buf<int32_t> bsrc;
-    if (B.nnzb) convert_blocks<ELT>(ctx, bs, B.val, value_src(ctx, brows.src, bvmap, B.nnzb, bsrc), B.nnzb, !tB, lb.p);
+    if (B.nnzb) {
+      const int32_t* vs = value_src(ctx, brows.src, bvmap, B.nnzb, bsrc);
+      if (b32) convert_blocks<ELT, float>(ctx, bs, reinterpret_cast<const float*>(B.val), vs, B.nnzb, !tB, lb.p);
+      else convert_blocks<ELT>(ctx, bs, B.val, vs, B.nnzb, !tB, lb.p);
+    }
   }
   uint8_t* const lb_p = (bhit || bsym) ? bpre->conv.p : lb.p;
   if (bc && !tB && !bhit && !bsym) {  // op(B) = B in its stored order: keep the copy for a later op(A) = B^T
@@ -1106,7 +1132,7 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
       const CUtensorMap mapB = make_map_bs(ELT, bs, lb_p, B.nnzb + 1, sh);
       prof_begin(ctx, 1);
       band_lp_product(ctx, ELT, bs, &mapA, &mapB, Pb.tiles.p, Pb.coff.p + Pb.nchunk, Pb.tnk.p, Pb.rec.p, Pb.off.p,
-                      Pb.cpos.p, Pb.ntiles, alpha, C);
+                      Pb.cpos.p, Pb.ntiles, alpha, C, out32);
       prof_end(ctx);
       ++ctx->tc_launches;
       return;
@@ -1130,7 +1156,8 @@ static void run(ifac_ctx* ctx, const View& arows, bool tA, const ifac_bsr& A, co
   args.rec_off = P.off.p;
   args.crp = C.row_ptr;
   args.cci = C.col_idx;
-  args.cval = C.val;
+  args.cval = out32 ? nullptr : C.val;
+  args.cval32 = out32 ? reinterpret_cast<float*>(C.val) : nullptr;
   args.cnorm = C.norms;
   args.alpha = alpha;
   args.err = ctx->dev_err;
@@ -2244,14 +2271,18 @@ void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit) { tc::stall_s
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache, OperandCache* bcache,
-                     const OperandCache* bpre, const int32_t* avmap, const int32_t* bvmap) {
+                     const OperandCache* bpre, const int32_t* avmap, const int32_t* bvmap, bool out32, bool b32) {
   if (C.nnzb == 0) return;
+  if ((out32 || b32) && prec != IFAC_TF32 && prec != IFAC_BF16)
+    fail(IFAC_ERR_INVALID, "FP32 values: TF32/BF16 products only");
   if (A.bs != 32 && A.bs != 64 && A.bs != 128) fail(IFAC_ERR_UNSUPPORTED, "tensor-core block products: bs 32, 64 or 128");
   if (!B.val && !(bpre && bpre->b_ready)) fail(IFAC_ERR_INVALID, "tensor-core product: op(B) has no values");
   if (prec == IFAC_BF16)
-    tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre, avmap, bvmap);
+    tc::run<2>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre, avmap, bvmap,
+               out32, b32);
   else if (prec == IFAC_TF32)
-    tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre, avmap, bvmap);
+    tc::run<4>(ctx, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache, bcache, bpre, avmap, bvmap,
+               out32, b32);
   else if (prec == IFAC_FP64_SPLIT)
     tc::run_split(ctx, ctx->split_slices, arows, tA, A, brows, tB, B, alpha, C, crow, upper, pairs_dev, acache,
                   bcache, avmap, bvmap);
@@ -2260,18 +2291,27 @@ void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const 
 
 // the mixed schedule's P at m = 2 as a low-precision op(B) copy (k_poly2_lp)
 void poly2_lp(ifac_ctx* ctx, int elt, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2,
-              const ifac_bsr& P, const int32_t* prow, void* out, const int32_t* umap) {
+              const ifac_bsr& P, const int32_t* prow, void* out, const int32_t* umap, bool u32) {
   if (U.bs != 64) fail(IFAC_ERR_UNSUPPORTED, "correction operand: bs 64");
   const size_t bb = (size_t)64 * 64 * elt;
   IFAC_CK(cudaMemsetAsync(static_cast<uint8_t*>(out) + (size_t)P.nnzb * bb, 0, bb, ctx->stream));
   if (P.nnzb == 0) return;
   const int grid = (int)std::min<int64_t>(P.nnzb, 152 * 8);
-  if (elt == 2)
-    tc::k_poly2_lp<2><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val, umap,
-                                                      D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
+  const float* u32v = reinterpret_cast<const float*>(U.val);
+  if (elt == 2 && u32)
+    tc::k_poly2_lp<2, float><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, u32v, umap,
+                                                             D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
+  else if (elt == 2)
+    tc::k_poly2_lp<2, double><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val,
+                                                              umap, D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2,
+                                                              out);
+  else if (u32)
+    tc::k_poly2_lp<4, float><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, u32v, umap,
+                                                             D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
   else
-    tc::k_poly2_lp<4><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val, umap,
-                                                      D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2, out);
+    tc::k_poly2_lp<4, double><<<grid, 256, 0, ctx->stream>>>(prow, P.col_idx, P.nnzb, U.row_ptr, U.col_idx, U.val,
+                                                              umap, D.row_ptr, D.col_idx, D.val, (float)b1, (float)b2,
+                                                              out);
   IFAC_CK_LAUNCH();
 }
 

@@ -43,6 +43,7 @@ struct ifac_ctx {
   // counters [1] FP64 and [2] tensor-core block pairs of the current call
   int* dev_err = nullptr;
   int split_slices = 7;  // BF16 slices per operand for IFAC_FP64_SPLIT products
+  bool fp32_mid = true;  // mixed refinements keep low-precision product results in FP32
   int fp64_prec = IFAC_FP64;  // IFAC_FP64_SPLIT: gemm() runs FP64 products of bs = 64 on the split kernel
   unsigned long long* dev_pairs = nullptr;
   // tile schedule of bs-64 tensor-core products (TF32/BF16, and split): -1
@@ -104,17 +105,32 @@ struct Buf {
 // vmap (optional, internal to the drivers): block p's values are at
 // m.val + vmap[p] bs^2 -- a product truncated without moving its kept blocks
 // (compact with nocopy); only the consumers that take a value map read it.
+// f32 (internal to the mixed drivers): m.val holds FP32 values (bs^2 floats
+// per block), the exact results of a TF32/BF16 product; only the consumers
+// given a matching flag read them.
 struct Mat {
   ifac_ctx* ctx = nullptr;
   ifac_bsr m{};
   Buf<int32_t> vmap;
+  bool f32 = false;
   Mat() = default;
   explicit Mat(ifac_ctx* c) : ctx(c) {}
   Mat(const Mat&) = delete;
   Mat& operator=(const Mat&) = delete;
-  Mat(Mat&& o) noexcept : ctx(o.ctx), m(o.m), vmap(std::move(o.vmap)) { o.m = ifac_bsr{}; }
+  Mat(Mat&& o) noexcept : ctx(o.ctx), m(o.m), vmap(std::move(o.vmap)), f32(o.f32) {
+    o.m = ifac_bsr{};
+    o.f32 = false;
+  }
   Mat& operator=(Mat&& o) noexcept {
-    if (this != &o) { reset(); ctx = o.ctx; m = o.m; o.m = ifac_bsr{}; vmap = std::move(o.vmap); }
+    if (this != &o) {
+      reset();
+      ctx = o.ctx;
+      m = o.m;
+      o.m = ifac_bsr{};
+      vmap = std::move(o.vmap);
+      f32 = o.f32;
+      o.f32 = false;
+    }
     return *this;
   }
   const int32_t* map() const { return vmap.p; }
@@ -220,19 +236,23 @@ struct OperandCache {
 };
 
 // Tensor-core (TF32/BF16 in, FP32 accumulate, or split FP64-accurate)
-// numeric block product, bs = 64.  brows: rows of op(B).  upper: C holds only
-// blocks with J >= I.  pairs_dev[0] counts the block pairs multiplied; for
-// split products pairs_dev[1] counts block pairs times slice pairs.
+// numeric block product, bs 32, 64 or 128.  brows: rows of op(B).  upper: C
+// holds only blocks with J >= I.  pairs_dev[0] counts the block pairs
+// multiplied; for split products pairs_dev[1] counts block pairs times slice
+// pairs.  TF32/BF16 only: out32, C.val receives FP32 values; b32, B.val holds
+// FP32 values.
 void gemm_numeric_tc(ifac_ctx* ctx, int prec, const View& arows, bool tA, const ifac_bsr& A, const View& brows,
                      bool tB, const ifac_bsr& B, double alpha, ifac_bsr& C, const int32_t* crow, bool upper,
                      unsigned long long* pairs_dev, OperandCache* acache = nullptr,
                      OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr,
-                     const int32_t* avmap = nullptr, const int32_t* bvmap = nullptr);
+                     const int32_t* avmap = nullptr, const int32_t* bvmap = nullptr, bool out32 = false,
+                     bool b32 = false);
 // the mixed schedule's P = b1 D + b2 (U + strict_upper(U)^T) at m = 2 written
 // as the low-precision (elt 4 TF32, 2 BF16) op(B) copy of P's pattern (row
-// index of each block in prow) into out ((P.nnzb + 1) blocks), bs 64
+// index of each block in prow) into out ((P.nnzb + 1) blocks), bs 64; u32:
+// U's values are FP32
 void poly2_lp(ifac_ctx* ctx, int elt, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2,
-              const ifac_bsr& P, const int32_t* prow, void* out, const int32_t* umap = nullptr);
+              const ifac_bsr& P, const int32_t* prow, void* out, const int32_t* umap = nullptr, bool u32 = false);
 // TF32 (elt 4) / BF16 (elt 2) product on narrow tiles of 128 accumulator
 // rows (gemm_band.cu), bs 32, 64 or 128.  mapA / mapB: CUtensorMap of the
 // K-major low-precision copies of op(A) and op(B), boxes of one swizzle atom
@@ -247,7 +267,7 @@ struct BandShape {
 BandShape band_lp_shape(int elt, int bs);
 void band_lp_product(ifac_ctx* ctx, int elt, int bs, const void* mapA, const void* mapB, const int32_t* tiles,
                      const int* ntiles, const int32_t* tile_nk, const int32_t* rec, const int32_t* rec_off,
-                     const int32_t* cpos, int tiles_bound, double alpha, ifac_bsr& C);
+                     const int32_t* cpos, int tiles_bound, double alpha, ifac_bsr& C, bool out32 = false);
 // the same matrix with block size bs (32, 64, 128), exact (reblock.cu)
 Mat reblock(ifac_ctx* ctx, const ifac_bsr& A, int bs);
 // block size and bs-64 tile schedule of a batch from timed probe products
@@ -256,17 +276,18 @@ void autotune(ifac_ctx* ctx, int count, const ifac_bsr* const* S, double tau, co
 // Failure-path self-test: a tensor-core launch whose pipeline never fills, so
 // its bounded waits expire after wait_limit polls (sets the device error flag).
 void tc_wait_timeout_selftest(ifac_ctx* ctx, long long wait_limit);
-// bmap / umap: value maps of B / U (Mat::vmap), or null
+// bmap / umap: value maps of B / U (Mat::vmap), or null; b32 / u32: B's / U's
+// values are FP32 (Mat::f32)
 // lp / lp_elt: a low-precision copy of C in the layout of an op(A) operand
 // ((C.nnzb + 1) blocks, the caller zeroes the last), lp_elt 4 TF32, 2 BF16
 void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B,
                  double gamma, ifac_bsr& C, const int32_t* crow, const int32_t* bmap = nullptr, void* lp = nullptr,
-                 int lp_elt = 0);
+                 int lp_elt = 0, bool b32 = false);
 // C = alpha (U + strict_upper(U)^T) + beta B + gamma I on the pattern of sym_pattern
 // mirror: diagonal blocks are completed from their upper triangle too
 void sym_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
                  ifac_bsr& C, const int32_t* crow, const int32_t* umap = nullptr, bool mirror = false,
-                 void* lp = nullptr, int lp_elt = 0);
+                 void* lp = nullptr, int lp_elt = 0, bool u32 = false);
 // out[q]: the position in A of the transpose (J, I) of A's block q = (I, J)
 // (row: each block's row index); A's pattern symmetric
 void transposed_positions(ifac_ctx* ctx, const ifac_bsr& A, const int32_t* row, int32_t* out);
@@ -327,27 +348,30 @@ Mat scaled_identity(ifac_ctx* ctx, int64_t n, int bs, int nb, double c);
 // ---- operations used by drivers (ops.cu) ----
 // nocopy: the truncated result keeps its kept blocks in place (Mat::vmap);
 // avmap / bvmap: value maps of A and B (tensor-core and split products only)
+// out32 (TF32/BF16 with nocopy): the result's values stay FP32 (Mat::f32),
+// exactly as accumulated, at half the bytes; b32: B's values are FP32
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
          int prec = IFAC_FP64, bool upper = false, OperandCache* acache = nullptr,
          OperandCache* bcache = nullptr, const OperandCache* bpre = nullptr, bool nocopy = false,
-         const int32_t* avmap = nullptr, const int32_t* bvmap = nullptr);
+         const int32_t* avmap = nullptr, const int32_t* bvmap = nullptr, bool out32 = false, bool b32 = false);
 // P = b1 D + b2 (U + strict_upper(U)^T) (Eq. 2.1 at m = 2, U the upper block
 // triangle of delta^2, D = delta) for a following low-precision product
 // Z P: the returned matrix holds P's pattern only (no values); its op(B)
 // copy in precision prec (TF32 or BF16) is in *pc
 Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2, int prec,
-                  OperandCache* pc, const int32_t* umap = nullptr);
+                  OperandCache* pc, const int32_t* umap = nullptr, bool u32 = false);
 // lp_prec (IFAC_TF32 / IFAC_BF16) with lpc: the result's op(A) copy in that
 // format is written into *lpc with the FP64 values (no conversion pass later)
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
-        const int32_t* bmap = nullptr, int lp_prec = 0, OperandCache* lpc = nullptr);
+        const int32_t* bmap = nullptr, int lp_prec = 0, OperandCache* lpc = nullptr, bool b32 = false);
 // the symmetric matrix whose upper block triangle (J >= I) is held by U,
 // times alpha, plus beta B and gamma I: alpha (U + strict_upper(U)^T) +
 // beta B + gamma I, rounded as add() rounds alpha A + beta B + gamma I
 // mirror: the result is made exactly symmetric (diagonal blocks from their
 // upper triangle), and with lpc its copy serves op(B) as well (lpc->tpos)
 Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-            const int32_t* umap = nullptr, bool mirror = false, int lp_prec = 0, OperandCache* lpc = nullptr);
+            const int32_t* umap = nullptr, bool mirror = false, int lp_prec = 0, OperandCache* lpc = nullptr,
+            bool u32 = false);
 Mat truncate(ifac_ctx* ctx, const ifac_bsr& A, double tau);
 Mat copy_mat(ifac_ctx* ctx, const ifac_bsr& A);
 void validate(const ifac_bsr* A, const char* name);

@@ -17,13 +17,18 @@ namespace ifac {
 //   B then needs no values
 //   nocopy: truncation leaves the kept blocks in place (the result's vmap)
 //   avmap / bvmap: value maps of A / B (tensor-core and split products)
+//   out32: a TF32/BF16 product truncated with nocopy keeps its values in FP32
+//   (the accumulators exactly; Mat::f32); b32: B's values are FP32
 Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, double alpha, double tau,
          int prec, bool upper, OperandCache* acache, OperandCache* bcache, const OperandCache* bpre, bool nocopy,
-         const int32_t* avmap, const int32_t* bvmap) {
+         const int32_t* avmap, const int32_t* bvmap, bool out32, bool b32) {
   const int nb = A.nb;
   if (prec == IFAC_FP64 && ctx->fp64_prec == IFAC_FP64_SPLIT && (A.bs == 32 || A.bs == 64 || A.bs == 128))
     prec = IFAC_FP64_SPLIT;
   if ((avmap || bvmap) && prec == IFAC_FP64) fail(IFAC_ERR_INVALID, "FP64 products take no value maps");
+  const bool lowp = prec == IFAC_TF32 || prec == IFAC_BF16;
+  if (b32 && !lowp) fail(IFAC_ERR_INVALID, "FP32 operand values: TF32/BF16 products only");
+  out32 = out32 && lowp && nocopy;  // compaction copies would move FP64 values
   View arows = view_rows(ctx, A, tA);
   Pattern P = product_pattern(ctx, arows, B, tB, nb, upper);
   Mat C(ctx);
@@ -33,13 +38,15 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   C.m.nnzb = P.nnzb;
   C.m.row_ptr = P.rp.release();
   C.m.col_idx = P.ci.release();
-  C.m.val = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
+  const size_t vbytes = out32 ? sizeof(float) : sizeof(double);
+  C.m.val = static_cast<double*>(dalloc(ctx, vbytes * (size_t)(P.nnzb ? P.nnzb : 1) * A.bs * A.bs));
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
+  C.f32 = out32;
   // algorithmic bytes of the product launch: each operand block read once at
   // the width the kernel reads it, each result block written once
   {
     const double blk = (double)A.bs * A.bs;
-    const double ab = (double)(A.nnzb + B.nnzb) * blk, cb = (double)P.nnzb * blk * 8.0;
+    const double ab = (double)(A.nnzb + B.nnzb) * blk, cb = (double)P.nnzb * blk * (double)vbytes;
     if (prec == IFAC_FP64) ctx->bytes_fp64 += ab * 8.0 + cb;
     else if (prec == IFAC_FP64_SPLIT) ctx->bytes_split += ab * 2.0 * ctx->split_slices + cb;
     else ctx->bytes_tc += ab * (prec == IFAC_BF16 ? 2.0 : 4.0) + cb;
@@ -51,9 +58,11 @@ Mat gemm(ifac_ctx* ctx, const ifac_bsr& A, bool tA, const ifac_bsr& B, bool tB, 
   } else {
     View brows = view_rows(ctx, B, tB);
     gemm_numeric_tc(ctx, prec, arows, tA, A, brows, tB, B, alpha, C.m, P.row.p, upper,
-                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache, bcache, bpre, avmap, bvmap);
+                    ctx->dev_pairs + (prec == IFAC_FP64_SPLIT ? 2 : 1), acache, bcache, bpre, avmap, bvmap, out32,
+                    b32);
   }
   Mat R = compact(ctx, std::move(C), P.row.p, tau, nocopy);
+  R.f32 = out32;
   ctx->products += 1;
   return R;
 }
@@ -72,7 +81,7 @@ static void* lp_copy_alloc(ifac_ctx* ctx, const ifac_bsr& C, int lp_prec, Operan
 }
 
 Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const ifac_bsr* B, double gamma,
-            const int32_t* umap, bool mirror, int lp_prec, OperandCache* lpc) {
+            const int32_t* umap, bool mirror, int lp_prec, OperandCache* lpc, bool u32) {
   Pattern P = sym_pattern(ctx, U, B, gamma != 0.0);
   Mat C(ctx);
   C.m.n = U.n;
@@ -85,7 +94,7 @@ Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const i
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
   int elt = 0;
   void* lp = lp_copy_alloc(ctx, C.m, lp_prec, lpc, &elt);
-  sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p, umap, mirror, lp, elt);
+  sym_numeric(ctx, alpha, U, beta, B, gamma, C.m, P.row.p, umap, mirror, lp, elt, u32);
   if (lp && mirror) {
     lpc->tpos = Buf<int32_t>(ctx, (size_t)(C.m.nnzb ? C.m.nnzb : 1));
     transposed_positions(ctx, C.m, P.row.p, lpc->tpos.p);
@@ -94,7 +103,7 @@ Mat sym_sum(ifac_ctx* ctx, double alpha, const ifac_bsr& U, double beta, const i
 }
 
 Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1, double b2, int prec,
-                  OperandCache* pc, const int32_t* umap) {
+                  OperandCache* pc, const int32_t* umap, bool u32) {
   Pattern Pp = sym_pattern(ctx, U, &D, false);
   Mat P(ctx);
   P.m.n = U.n;
@@ -108,12 +117,12 @@ Mat poly2_operand(ifac_ctx* ctx, const ifac_bsr& U, const ifac_bsr& D, double b1
   pc->conv = Buf<uint8_t>(ctx, (size_t)(Pp.nnzb + 1) * U.bs * U.bs * elt);
   pc->conv_elt = elt;
   pc->b_ready = true;
-  poly2_lp(ctx, elt, U, D, b1, b2, P.m, Pp.row.p, pc->conv.p, umap);
+  poly2_lp(ctx, elt, U, D, b1, b2, P.m, Pp.row.p, pc->conv.p, umap, u32);
   return P;
 }
 
 Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_bsr* B, double gamma,
-        const int32_t* bmap, int lp_prec, OperandCache* lpc) {
+        const int32_t* bmap, int lp_prec, OperandCache* lpc, bool b32) {
   Pattern P = union_pattern(ctx, A, B, gamma != 0.0);
   Mat C(ctx);
   C.m.n = A.n;
@@ -126,7 +135,7 @@ Mat add(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, const ifac_
   C.m.norms = static_cast<double*>(dalloc(ctx, sizeof(double) * (P.nnzb ? P.nnzb : 1)));
   int elt = 0;
   void* lp = lp_copy_alloc(ctx, C.m, lp_prec, lpc, &elt);
-  add_numeric(ctx, alpha, A, beta, B, gamma, C.m, P.row.p, bmap, lp, elt);
+  add_numeric(ctx, alpha, A, beta, B, gamma, C.m, P.row.p, bmap, lp, elt, b32);
   return C;
 }
 

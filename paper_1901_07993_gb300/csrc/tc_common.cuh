@@ -418,6 +418,27 @@ __device__ __forceinline__ uint32_t f64_to_f32_bits_rne(double x) {
   return sign | bits;
 }
 
+// The same roundings from FP32 values (the FP32 results of TF32/BF16
+// products): identical to the FP64 routines above applied to the same value,
+// FP32 subnormals included (they become zero).
+__device__ __forceinline__ float f32_flush(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return ((u & 0x7f800000u) == 0u) ? __uint_as_float(u & 0x80000000u) : x;
+}
+
+__device__ __forceinline__ uint16_t f32_to_bf16_bits_rne(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  if (ex == 0xffu) return sign | 0x7f80u | (((u & 0x7fffffu) != 0) ? 0x40u : 0u);
+  if (ex == 0u) return sign;
+  const uint32_t mant = (u >> 16) & 0x7fu, rem = u & 0xffffu;
+  uint32_t bits = (ex << 7) | mant;
+  if (rem > 0x8000u || (rem == 0x8000u && (mant & 1u))) ++bits;
+  if (bits >= 0x7f80u) return sign | 0x7f80u;
+  return sign | (uint16_t)bits;
+}
+
 __device__ __forceinline__ uint16_t f64_to_bf16_bits_rne(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const uint16_t sign = (uint16_t)((u >> 48) & 0x8000u);

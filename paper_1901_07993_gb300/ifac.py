@@ -33,7 +33,7 @@ EXPORTS = ("ifac_create", "ifac_destroy", "ifac_set_stream", "ifac_last_error", 
            "inv_factor_localized", "inv_factor_resid", "leaf_invchol_batched_noalloc",
            "inv_factor_refine_adjoint", "inv_factor_refine_batched", "ifac_set_split_slices",
            "inv_factor_rinch", "ifac_selftest_wait_timeout", "bsr_reblock", "ifac_set_schedule",
-           "ifac_autotune_batched")
+           "ifac_autotune_batched", "ifac_set_fp32_intermediates")
 
 
 class IfacError(RuntimeError):
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "ifac_destroy": ([p], None),
         "ifac_set_stream": ([p, p], i32),
         "ifac_set_split_slices": ([p, i32], i32),
+        "ifac_set_fp32_intermediates": ([p, i32], i32),
         "ifac_last_error": ([p], ctypes.c_char_p),
         "ifac_opts_default": ([ctypes.POINTER(_Opts)], None),
         "ifac_bsr_upload": ([p, i64, i32, i32, i64, p, p, p, PB], i32),
@@ -177,6 +178,9 @@ class Context:
 
     def set_split_slices(self, slices: int):
         self.check(self.lib.ifac_set_split_slices(self.h, int(slices)))
+
+    def set_fp32_intermediates(self, on: bool):
+        self.check(self.lib.ifac_set_fp32_intermediates(self.h, 1 if on else 0))
 
     def close(self):
         if getattr(self, "h", None):

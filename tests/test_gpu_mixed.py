@@ -89,3 +89,47 @@ def test_mixed_refine_split_delta_block_sizes(ctx, bs):
     print(f"bs {bs}: resid {resid:.2e}, low sweeps {rep.low_sweeps}, split delta evals {rep.fp64_delta_evals}")
     assert rep.split_launches > 0 and rep.tc_launches > 0
     assert resid <= 10 * target
+
+
+def _same_factor(a, b):
+    return (np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col_idx, b.col_idx)
+            and np.array_equal(a.val.view(np.uint64), b.val.view(np.uint64)))
+
+
+@pytest.mark.parametrize("case", ["chain-tf32-narrow", "chain-bf16-narrow", "cluster-tf32-supertile",
+                                  "chain-tf32-bs32", "batch-tf32"])
+def test_fp32_intermediates_are_bitwise_neutral(ctx, case):
+    """The low-precision products' results are FP32 accumulators, so keeping
+    X, Z^T X, delta^2 and M in FP32 (ifac_set_fp32_intermediates, the default)
+    must give bitwise the factors and delta norms of keeping them in FP64:
+    narrow-tile and super-tile kernels, bs 64 and 32, single and batched."""
+    from paper_1901_07993_gb300 import ifac
+    prec = 2 if "bf16" in case else 1
+    bs = 32 if "bs32" in case else 64
+    if case.startswith("batch"):
+        Ss = [synth.chain_overlap(1500, bs, seed=5), synth.cluster_overlap(700, bs, seed=2),
+              synth.chain_overlap(2600, bs, seed=3)]
+    elif case.startswith("cluster"):
+        Ss = [synth.cluster_overlap(1024, bs, seed=0)]
+    else:
+        Ss = [synth.chain_overlap(4096, bs, seed=0)]
+    dS = [ifac.upload(ctx, S) for S in Ss]
+    if "supertile" in case:
+        ifac.set_schedule(ctx, 0, -1)
+    out = {}
+    try:
+        for on in (True, False):
+            ctx.set_fp32_intermediates(on)
+            if case.startswith("batch"):
+                Zs, reps, rc = ifac.inv_factor_refine_batched(ctx, dS, 1e-12, 1e-10, ifac.opts(prec=prec))
+            else:
+                Z, rep = ifac.inv_factor_refine(ctx, dS[0], 1e-13, 1e-10, ifac.opts(prec=prec, max_iter=80))
+                Zs, reps = [Z], [rep]
+            out[on] = ([Z.download() for Z in Zs], [list(r.delta_fro) for r in reps], [r.sweeps for r in reps])
+    finally:
+        ctx.set_fp32_intermediates(True)
+        ifac.set_schedule(ctx, -1, -1)
+    (z1, d1, s1), (z0, d0, s0) = out[True], out[False]
+    assert s1 == s0 and d1 == d0
+    for a, b in zip(z1, z0):
+        assert _same_factor(a, b)
