@@ -176,7 +176,9 @@ typedef struct {
                           product (nnzb(A) + nnzb(B) + nnzb(C)) bs^2 8, C before
                           truncation (each block read or written once) */
   double tc_bytes;     /* the same for the TF32/BF16 launches: operands at 4 / 2
-                          bytes (the converted copies), C at 8 (FP64) */
+                          bytes (the converted copies), C at 8 (FP64), or at 4
+                          where a mixed refinement keeps it in FP32
+                          (ifac_set_fp32_intermediates) */
   double split_bytes;  /* the same for the split launches: s BF16 slices of
                           each operand (2 s bytes), C as 64-bit sums (8) */
 } ifac_report;
@@ -385,8 +387,9 @@ int ifac_autotune_batched(ifac_ctx* ctx, int count, const ifac_bsr* const* S, do
  * at bs 128 delta_prec must be IFAC_FP64_SPLIT; at bs 64 the symmetric
  * products Z^T (S Z) and delta delta form their upper block triangle only): every
  * block product of a sweep runs on the tensor cores with inputs rounded to
- * that format and FP32 accumulation, while sums, block norms, truncation and
- * delta = I - Y stay FP64, until the automatic rule of Section 2.2
+ * that format and FP32 accumulation (the products' results are kept as those
+ * FP32 values, ifac_set_fp32_intermediates), while sums, block norms,
+ * truncation and delta = I - Y stay FP64, until the automatic rule of Section 2.2
  * (||delta_{i+1}||_F > ||delta_i||_F^(m+1): rounding dominates) fires or
  * ||delta||_F stops decreasing (the rule cannot fire once the rounding floor
  * of ||delta||_F, which grows like sqrt(n), lies above 1).  From

@@ -79,6 +79,31 @@ __device__ __forceinline__ double scaled(const Scale& s, double x) {
 __device__ __forceinline__ double as_f64(double x) { return x; }
 __device__ __forceinline__ double as_f64(float x) { return ifac::tc::f32_to_f64(x); }
 
+// two consecutive operand values (8- or 16-byte aligned) as FP64
+__device__ __forceinline__ void load2(const double* p, double& x, double& y) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  x = t.x;
+  y = t.y;
+}
+__device__ __forceinline__ void load2(const float* p, double& x, double& y) {
+  const float2 t = *reinterpret_cast<const float2*>(p);
+  x = as_f64(t.x);
+  y = as_f64(t.y);
+}
+
+// add_elem on loaded values: ha / hb say whether a / b exist
+__device__ __forceinline__ double add_vals(const Scale& sa, bool ha, double a, const Scale& sb, bool hb, double b,
+                                           bool diag, double gamma) {
+  double v = 0.0;
+  if (ha) v = scaled(sa, a);
+  if (hb) {
+    const double t = scaled(sb, b);
+    v = ha ? __dadd_rn(v, t) : t;
+  }
+  if (diag) v = (ha || hb) ? __dadd_rn(v, gamma) : gamma;
+  return v;
+}
+
 template <typename TA, typename TB>
 __device__ __forceinline__ double add_elem(const Scale& sa, const TA* a, const Scale& sb, const TB* b, bool diag,
                                            double gamma, int e, int ea = -1) {
@@ -145,9 +170,13 @@ __global__ void k_add(const int32_t* __restrict__ crow, const int32_t* __restric
 #pragma unroll 4
     for (int e = lane * VEC; e < bsz; e += 32 * VEC) {
       if constexpr (VEC == 2) {
+        // one vector load per operand (pairs never straddle two blocks)
+        double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+        if (a) load2(a + e, ax, ay);
+        if (b) load2(b + e, bx, by);
         double2 v;
-        v.x = add_elem(sa, a, sb, b, dblk && e / bs == e % bs, gamma, e);
-        v.y = add_elem(sa, a, sb, b, dblk && (e + 1) / bs == (e + 1) % bs, gamma, e + 1);
+        v.x = add_vals(sa, a != nullptr, ax, sb, b != nullptr, bx, dblk && e / bs == e % bs, gamma);
+        v.y = add_vals(sa, a != nullptr, ay, sb, b != nullptr, by, dblk && (e + 1) / bs == (e + 1) % bs, gamma);
         *reinterpret_cast<double2*>(c + e) = v;
         if (lp_elt) lp_store2(lp, lp_elt, (size_t)p * bsz + e, v.x, v.y);
         sq.add_f64(v.x);
@@ -191,9 +220,9 @@ void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, co
 // C = alpha (U + strict_upper(U)^T) + beta B + gamma I, one warp per output
 // block.  Block (I, J), J >= I, is add_elem of alpha U_IJ and beta B_IJ;
 // block (I, J), J < I, takes alpha U_JI^T in place of alpha U_IJ, moved
-// through shared memory in stripes of four output rows (four 32-byte column
-// segments of U_JI per source row), so reads and writes are whole sectors.
-// bs = 64.  U's values are FP64 or FP32 (TU).
+// through shared memory in stripes of output rows (32-byte column segments of
+// U_JI per source row: four FP64 or eight FP32 values), so reads and writes
+// are whole sectors.  bs = 64.  U's values are FP64 or FP32 (TU).
 constexpr int SYM_WARPS = 8;
 
 template <typename TU>
@@ -205,11 +234,12 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
           double gamma, double* __restrict__ cval, double* __restrict__ cnorm, int mirror, void* __restrict__ lp,
           int lp_elt) {
   constexpr int BS = 64, BSZ = BS * BS;
-  __shared__ double stripe[SYM_WARPS][4][BS + 1];
+  constexpr int RW = 32 / (int)sizeof(TU);  // output rows per stripe
+  __shared__ double stripe[SYM_WARPS][RW][BS + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double(*st)[BS + 1] = stripe[wid];
+  double(*st)[BS + 1] = stripe[wid];  // RW rows
   for (int64_t p = w0; p < cnnz; p += nw) {
     const int I = crow[p], J = cci[p];
     const bool lower = J < I;
@@ -237,27 +267,36 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
 #pragma unroll 4
       for (int e = lane * 2; e < BSZ; e += 64) {
         const int rr = e / BS, c0 = e % BS;
-        const int e0 = (mir && c0 < rr) ? c0 * BS + rr : -1, e1 = (mir && c0 + 1 < rr) ? (c0 + 1) * BS + rr : -1;
         double2 v;
-        v.x = add_elem(sa, lower ? nullptr : u, sb, b, dblk && rr == c0, gamma, e, e0);
-        v.y = add_elem(sa, lower ? nullptr : u, sb, b, dblk && rr == c0 + 1, gamma, e + 1, e1);
+        if (!mir) {  // one vector load per operand
+          const TU* uu = lower ? nullptr : u;
+          double ux = 0.0, uy = 0.0, bx = 0.0, by = 0.0;
+          if (uu) load2(uu + e, ux, uy);
+          if (b) load2(b + e, bx, by);
+          v.x = add_vals(sa, uu != nullptr, ux, sb, b != nullptr, bx, dblk && rr == c0, gamma);
+          v.y = add_vals(sa, uu != nullptr, uy, sb, b != nullptr, by, dblk && rr == c0 + 1, gamma);
+        } else {
+          const int e0 = c0 < rr ? c0 * BS + rr : -1, e1 = c0 + 1 < rr ? (c0 + 1) * BS + rr : -1;
+          v.x = add_elem(sa, lower ? nullptr : u, sb, b, dblk && rr == c0, gamma, e, e0);
+          v.y = add_elem(sa, lower ? nullptr : u, sb, b, dblk && rr == c0 + 1, gamma, e + 1, e1);
+        }
         *reinterpret_cast<double2*>(out + e) = v;
         if (lp_elt) lp_store2(lp, lp_elt, (size_t)p * BSZ + e, v.x, v.y);
         sq.add_f64(v.x);
         sq.add_f64(v.y);
       }
     } else {
-      for (int r0 = 0; r0 < BS; r0 += 4) {
-        // alpha U_JI, source rows s = 0..63, columns r0..r0+3
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int idx = k * 32 + lane, s = idx >> 2, j = idx & 3;
+      for (int r0 = 0; r0 < BS; r0 += RW) {
+        // alpha U_JI, source rows s = 0..63, columns r0..r0+RW-1
+#pragma unroll 8
+        for (int k = 0; k < 2 * RW; ++k) {
+          const int idx = k * 32 + lane, s = idx / RW, j = idx % RW;
           st[j][s] = scaled(sa, as_f64(u[s * BS + r0 + j]));
         }
         __syncwarp();
-        // output rows r0..r0+3: alpha U_JI^T (+ beta B_IJ), columns 0..63
+        // output rows r0..r0+RW-1: alpha U_JI^T (+ beta B_IJ), columns 0..63
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < RW; ++k) {
           const int idx = k * 64 + lane * 2, j = idx >> 6, col = idx & 63, e = (r0 + j) * BS + col;
           double2 v;
           v.x = st[j][col];

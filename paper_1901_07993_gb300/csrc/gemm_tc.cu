@@ -1303,7 +1303,7 @@ static void row_scales(ifac_ctx* ctx, int bs, const int32_t* rp, const int32_t* 
 // NS BF16 slice copies (K-major, op() CSR order) of a view; row r of block qb
 // has scale exponent sexp[sblk[qb] * B + r].  With Y = x 2^(62 - e) held as a
 // 64-bit integer (|Y| < 2^62; bits below 2^-62 of sigma dropped by rounding),
-// digit k is q_k = round(Y_k / 2^(62 - 7k)), Y_{k+1} = Y_k - q_k 2^(62 - 7k).
+// digit k is q_k = round(Y_k / 2^(62 - 7k)) (ties up), Y_{k+1} = Y_k - q_k 2^(62 - 7k).
 __device__ __forceinline__ void split_digits(double x, int e, int ns, int (&q)[8]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int ea = (int)((u >> 52) & 0x7ff);
@@ -1316,14 +1316,21 @@ __device__ __forceinline__ void split_digits(double x, int e, int ns, int (&q)[8
   unsigned long long Y = 0;
   if (sh >= 0) Y = mant << sh;  // sh <= 9 since |x| < sigma
   else if (sh > -63) Y = (mant + (1ull << (-sh - 1))) >> (-sh);
-  long long y = (u >> 63) ? -(long long)Y : (long long)Y;
+  const long long y = (u >> 63) ? -(long long)Y : (long long)Y;
+  // the digits in closed form: with R_k = floor((y + 2^(d_k - 1)) / 2^d_k),
+  // y rounded (half up) to a multiple of 2^d_k, the digits so far sum to
+  // R_k 2^d_k, so q_1 = R_1 and q_k = R_k - 2^7 R_(k-1).  Each q_k is small,
+  // so 32-bit arithmetic on the low words of the R_k suffices.
+  int rprev = 0;
 #pragma unroll
   for (int k = 1; k <= 8; ++k) {
     if (k > ns) break;
     const int d = 62 - SPLIT_BITS * k;
-    const long long qk = (y + (1ll << (d - 1))) >> d;
-    y -= qk << d;
-    q[k - 1] = (int)qk;
+    const unsigned long long t = (unsigned long long)y + (1ull << (d - 1));
+    const uint32_t lo = (uint32_t)t, hi = (uint32_t)(t >> 32);
+    const int r = d >= 32 ? ((int)hi >> (d - 32)) : (int)__funnelshift_r(lo, hi, d);
+    q[k - 1] = k == 1 ? r : (int)((uint32_t)r - ((uint32_t)rprev << 7));
+    rprev = r;
   }
 }
 
