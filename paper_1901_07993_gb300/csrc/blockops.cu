@@ -220,9 +220,11 @@ void add_numeric(ifac_ctx* ctx, double alpha, const ifac_bsr& A, double beta, co
 // C = alpha (U + strict_upper(U)^T) + beta B + gamma I, one warp per output
 // block.  Block (I, J), J >= I, is add_elem of alpha U_IJ and beta B_IJ;
 // block (I, J), J < I, takes alpha U_JI^T in place of alpha U_IJ, moved
-// through shared memory in stripes of output rows (32-byte column segments of
-// U_JI per source row: four FP64 or eight FP32 values), so reads and writes
-// are whole sectors.  bs = 64.  U's values are FP64 or FP32 (TU).
+// through shared memory in stripes of four output rows (four-value column
+// segments of U_JI per source row: whole 32-byte sectors for FP64 values, half
+// sectors for FP32 values, whose other half the next stripe reads from cache;
+// eight-row stripes for FP32 measured slower: the doubled shared memory cuts
+// the resident warps).  bs = 64.  U's values are FP64 or FP32 (TU).
 constexpr int SYM_WARPS = 8;
 
 template <typename TU>
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(32 * SYM_WARPS)
           double gamma, double* __restrict__ cval, double* __restrict__ cnorm, int mirror, void* __restrict__ lp,
           int lp_elt) {
   constexpr int BS = 64, BSZ = BS * BS;
-  constexpr int RW = 32 / (int)sizeof(TU);  // output rows per stripe
+  constexpr int RW = 4;  // output rows per stripe
   __shared__ double stripe[SYM_WARPS][RW][BS + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
