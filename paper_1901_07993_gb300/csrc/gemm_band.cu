@@ -333,10 +333,13 @@ __global__ void __launch_bounds__(bandlp::NTHREADS, 1)
       // and column quarters, in a fixed order
       if (et < CP && kn >= 0) {
         const int br = et / TNB, bc = et % TNB;
+        // the lane quarters qq with (32 qq) / BS == br and column quarters cc
+        // with (CW cc) / BS == bc, in increasing order
+        const int q1 = (br + 1) * BS / 32 < 4 ? (br + 1) * BS / 32 : 4;
+        const int c1 = (bc + 1) * BS / CW < 4 ? (bc + 1) * BS / CW : 4;
         double sum = 0.0;
-        for (int qq = 0; qq < 4; ++qq)
-          for (int cc = 0; cc < 4; ++cc)
-            if ((qq * 32) / BS == br && (cc * CW) / BS == bc) sum += partial[ab][qq][cc];
+        for (int qq = br * BS / 32; qq < q1; ++qq)
+          for (int cc = bc * BS / CW; cc < c1; ++cc) sum += partial[ab][qq][cc];
         args.cnorm[kn] = sqrt(sum);
       }
     }

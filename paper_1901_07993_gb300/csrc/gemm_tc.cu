@@ -1895,10 +1895,13 @@ __global__ void __launch_bounds__(band::NTB, 1)
       // and column groups, in a fixed order
       if (et < CP && kn >= 0) {
         const int br = et / TNB, bc = et % TNB;
+        // the lane quarters qq with (32 qq) / B == br and column groups cc
+        // with (CW cc) / B == bc, in increasing order
+        const int q1 = (br + 1) * B / 32 < 4 ? (br + 1) * B / 32 : 4;
+        const int c1 = (bc + 1) * B / CW < EPW / 4 ? (bc + 1) * B / CW : EPW / 4;
         double sum = 0.0;
-        for (int qq = 0; qq < 4; ++qq)
-          for (int cc = 0; cc < EPW / 4; ++cc)
-            if ((qq * 32) / B == br && (cc * CW) / B == bc) sum += partial[qq][cc];
+        for (int qq = br * B / 32; qq < q1; ++qq)
+          for (int cc = bc * B / CW; cc < c1; ++cc) sum += partial[qq][cc];
         args.cnorm[kn] = sqrt(sum);
       }
       epi_bar<32 * EPW>();

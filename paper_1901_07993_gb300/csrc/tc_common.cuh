@@ -167,6 +167,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 
 // FP32 -> FP64 by moving the fields (exact, subnormals normalised; inf and
 // NaN take the conversion instruction), keeping the epilogue off the FP64 pipe
+__device__ __forceinline__ double f32_to_f64(float f);
+
+// f 2^-64 as FP64 (exact: the result is far inside FP64's normal range), on
+// the bit pattern for zeros and normal values; subnormal, inf and NaN inputs
+// (never seen in the sums below) take the general route
+__device__ __forceinline__ double f32_to_f64_m64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return f32_to_f64(f) * 5.421010862427522e-20;  // 2^-64
+  const uint32_t hi = (u & 0x80000000u) | ((ex + 896u - 64u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 __device__ __forceinline__ double f32_to_f64(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
@@ -285,8 +299,10 @@ struct SqAcc {
       h = s;
       l = l + l2 + err;
     }
-    double r = ((double)h + (double)l) * 5.421010862427522e-20;  // 2^-64
-    if (__any_sync(0xffffffffu, big != 0.0)) {
+    // (h + l) 2^-64 rounded once, as ((double)h + (double)l) 2^-64: the
+    // scaling moves to the exponent fields, so one FP64 add remains
+    double r = f32_to_f64_m64(h) + f32_to_f64_m64(l);
+    if (__any_sync(0xffffffffu, __double_as_longlong(big) != 0)) {  // big >= +0
       double bsum = big;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
@@ -295,7 +311,7 @@ struct SqAcc {
     return r;
   }
   __device__ __forceinline__ double value() const {
-    return ((double)hi + (double)lo) * 5.421010862427522e-20 + big;  // 2^-64
+    return (f32_to_f64_m64(hi) + f32_to_f64_m64(lo)) + big;  // (hi + lo) 2^-64 + big
   }
 };
 
