@@ -125,6 +125,10 @@ WORKLOADS = {
     "lif-split-cluster-n8192-bs64": dict(geom="cluster", n=8192, bs=64, tau=1e-10, target=1e-10,
                                          method="localized", m=2, seed=0, leaf=512, prec="split", compare=(),
                                          sample_n=1024, cost_exp=3),
+    # the same recipe at n = 16,384: the size scaling of LIF on the 3D geometry
+    "lif-split-cluster-n16384-bs64": dict(geom="cluster", n=16384, bs=64, tau=1e-10, target=1e-10,
+                                          method="localized", m=2, seed=0, leaf=512, prec="split", compare=(),
+                                          sample_n=1024, cost_exp=3),
     # the 4096-row chain through localized inverse factorization (512-row leaves)
     "lif-chain-n4096-bs32": dict(geom="chain", n=4096, bs=32, tau=1e-10, target=1e-10, method="localized", m=2,
                                  seed=0, leaf=512, prec="fp64", compare=(), sample_n=None),
