@@ -64,3 +64,14 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_context_setters_reject_a_null_context():
+    """The context switches validate their arguments before touching a
+    device, so they can be called (and fail cleanly) without a GPU."""
+    lib = ctypes.CDLL(libbuild.build())
+    for name, args in (("ifac_set_split_slices", (None, 5)), ("ifac_set_fp32_intermediates", (None, 1)),
+                       ("ifac_set_schedule", (None, -1, -1))):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        assert fn(*args) == ifac.ERR_INVALID, name
